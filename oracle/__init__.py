@@ -1,0 +1,441 @@
+"""CPU oracle for the outer-volume / Lloyd path (arXiv 2203.10521).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the product library
+never does.  The arithmetic lives in ``obb_oracle.c`` (plain C, one lattice
+point at a time); this module is ctypes marshalling plus the orchestration
+of the Lloyd step and the top-down tree build written as plain loops.
+
+Every function states the passage of the paper it follows.  Pins (tests that
+tie the oracle to something other than itself) live in
+``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "obb_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+
+S_BITS = 8    # fixed-point fraction bits of the snapped vertices
+Q_BITS = 24   # fraction bits of the quantised box normals
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FP contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+class RoundStats(C.Structure):
+    _fields_ = [("proposals", C.c_int64), ("accepted", C.c_int64),
+                ("gain", C.c_int64), ("evals", C.c_int64)]
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _declare(L):
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    L.orc_lattice_frame.argtypes = [vp, i64, i32, vp, vp]
+    L.orc_snap.argtypes = [vp, i64, vp, vp, vp]
+    L.orc_occupancy_columns.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp]
+    L.orc_column_crossing_counts.argtypes = [vp, vp, i64, vp, i64, vp]
+    L.orc_frame_normals.argtypes = [vp, i64, vp, vp]
+    L.orc_quantize_boxes.argtypes = [vp, i64, vp, vp, vp, vp]
+    L.orc_quantize_boxes.restype = C.c_int
+    L.orc_box_aabb.argtypes = [vp, vp, vp]
+    L.orc_box_aabb.restype = C.c_int
+    L.orc_outer_volume.argtypes = [vp, vp, i32, vp, vp, i64, vp, vp]
+    L.orc_outer_volume.restype = C.c_int
+    L.orc_tight_bounds.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+    L.orc_lloyd_moves.argtypes = [vp, vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp, i32, i32, vp]
+    L.orc_lloyd_moves.restype = C.c_int
+    L.orc_moments.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+    L.orc_covariance_from_moments.argtypes = [vp, vp]
+    L.orc_covariance_from_moments.restype = C.c_int
+    L.orc_jacobi3.argtypes = [vp, vp, vp]
+    L.orc_refit.argtypes = [vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
+    L.orc_refit.restype = C.c_int
+    L.orc_cluster_frames.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp]
+    L.orc_median_split.argtypes = [vp, vp, i64, vp, i32, vp, vp]
+    L.orc_median_split.restype = C.c_int
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+# ---------------------------------------------------------------------------
+# Lattice (Sec. 3: the solid Omega(X); lattice discretisation of Eq. 3-4)
+# ---------------------------------------------------------------------------
+
+def lattice_frame(verts, N):
+    """lo, h of the N^3 cell-centred lattice over the vertex AABB."""
+    V = _c(verts, np.float32)
+    lo = np.zeros(3)
+    h = np.zeros(3)
+    lib().orc_lattice_frame(_p(V), V.shape[0], int(N), _p(lo), _p(h))
+    return lo, h
+
+
+def snap(verts, lo, h):
+    """Fixed-point vertices U = rint(((x - lo)/h - 1/2) * 2^S)."""
+    V = _c(verts, np.float32)
+    U = np.zeros(V.shape, dtype=np.int32)
+    lib().orc_snap(_p(V), V.shape[0], _p(_c(lo, np.float64)), _p(_c(h, np.float64)), _p(U))
+    return U
+
+
+@dataclass
+class Occupancy:
+    """Per-point solid occupancy, filled column by column.
+
+    occ[k, j, i] in {0, 1}; known[k, j] marks the columns computed so far."""
+    N: int
+    U: np.ndarray
+    F: np.ndarray
+    occ: np.ndarray = None
+    known: np.ndarray = None
+
+    def __post_init__(self):
+        if self.occ is None:
+            self.occ = np.zeros((self.N, self.N, self.N), dtype=np.uint8)
+            self.known = np.zeros((self.N, self.N), dtype=np.uint8)
+
+    def fill_columns(self, cols):
+        """Compute the columns cols[:, (j, k)] not yet known."""
+        cols = np.asarray(cols, dtype=np.int64).reshape(-1, 2)
+        if cols.size == 0:
+            return
+        need = cols[self.known[cols[:, 1], cols[:, 0]] == 0]
+        if need.size == 0:
+            return
+        need = _c(np.unique(need, axis=0), np.int32)
+        lib().orc_occupancy_columns(_p(self.U), _p(self.F), self.F.shape[0], self.N,
+                                    _p(need), need.shape[0], _p(self.occ), _p(self.known))
+
+    def fill_all(self):
+        j, k = np.meshgrid(np.arange(self.N), np.arange(self.N), indexing="ij")
+        self.fill_columns(np.stack([j.ravel(), k.ravel()], -1))
+
+    def fill_boxes(self, n, bnd):
+        """Compute every in-domain column that the given boxes' AABBs cover."""
+        cols = []
+        for b in range(n.shape[0]):
+            ab = box_aabb(n[b], bnd[b])
+            j0, j1 = max(ab[2], 0), min(ab[3], self.N - 1)
+            k0, k1 = max(ab[4], 0), min(ab[5], self.N - 1)
+            if j0 > j1 or k0 > k1:
+                continue
+            jj, kk = np.meshgrid(np.arange(j0, j1 + 1), np.arange(k0, k1 + 1), indexing="ij")
+            m = self.known[kk, jj] == 0
+            if m.any():
+                cols.append(np.stack([jj[m], kk[m]], -1))
+        if cols:
+            self.fill_columns(np.concatenate(cols))
+
+
+def occupancy(U, F, N, cols=None):
+    """Occupancy object; all columns when cols is None."""
+    o = Occupancy(int(N), _c(U, np.int32), _c(F, np.int32))
+    if cols is None:
+        o.fill_all()
+    else:
+        o.fill_columns(cols)
+    return o
+
+
+def column_crossings(U, F, cols):
+    U = _c(U, np.int32)
+    F = _c(F, np.int32)
+    cols = _c(cols, np.int32).reshape(-1, 2)
+    out = np.zeros(cols.shape[0], dtype=np.int64)
+    lib().orc_column_crossing_counts(_p(U), _p(F), F.shape[0], _p(cols), cols.shape[0], _p(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Boxes (Eq. 4 per box) and their quantisation
+# ---------------------------------------------------------------------------
+
+def frame_normals(R, h):
+    R = _c(R, np.float64).reshape(-1, 9)
+    n = np.zeros((R.shape[0], 9), dtype=np.int32)
+    lib().orc_frame_normals(_p(R), R.shape[0], _p(_c(h, np.float64)), _p(n))
+    return n
+
+
+def quantize_boxes(boxes, lo, h):
+    """FP32 boxes [K, 12] (c, axis0, axis1, half) -> (n [K, 9] int32, bounds [K, 6] int64)."""
+    B = _c(boxes, np.float32).reshape(-1, 12)
+    n = np.zeros((B.shape[0], 9), dtype=np.int32)
+    bnd = np.zeros((B.shape[0], 6), dtype=np.int64)
+    rc = lib().orc_quantize_boxes(_p(B), B.shape[0], _p(_c(lo, np.float64)), _p(_c(h, np.float64)),
+                                  _p(n), _p(bnd))
+    if rc:
+        raise ValueError("invalid box")
+    return n, bnd
+
+
+def box_aabb(n, bnd):
+    out = np.zeros(6, dtype=np.int64)
+    rc = lib().orc_box_aabb(_p(_c(n, np.int32)), _p(_c(bnd, np.int64)), _p(out))
+    if rc:
+        raise ValueError(f"box_aabb failed ({rc})")
+    return out
+
+
+def outer_volume(occ: Occupancy, n, bnd):
+    """Eq. 4: exact count of unoccupied lattice points in each box, and the box's point count."""
+    n = _c(n, np.int32).reshape(-1, 9)
+    bnd = _c(bnd, np.int64).reshape(-1, 6)
+    occ.fill_boxes(n, bnd)
+    cnt = np.zeros(n.shape[0], dtype=np.uint64)
+    tot = np.zeros(n.shape[0], dtype=np.uint64)
+    rc = lib().orc_outer_volume(_p(occ.occ), _p(occ.known), occ.N, _p(n), _p(bnd), n.shape[0],
+                                _p(cnt), _p(tot))
+    if rc:
+        raise RuntimeError(f"orc_outer_volume failed ({rc})")
+    return cnt, tot
+
+
+def tight_bounds(U, F, assign, K, n):
+    bnd = np.zeros((K, 6), dtype=np.int64)
+    lib().orc_tight_bounds(_p(_c(U, np.int32)), _p(_c(F, np.int32)), F.shape[0],
+                           _p(_c(assign, np.int32)), int(K), _p(_c(n, np.int32)), _p(bnd))
+    return bnd
+
+
+# ---------------------------------------------------------------------------
+# Refit pieces (covariance frame, FP64 Jacobi)
+# ---------------------------------------------------------------------------
+
+def moments(V, F, assign, K, center):
+    mom = np.zeros((K, 10))
+    lib().orc_moments(_p(_c(V, np.float32)), _p(_c(F, np.int32)), F.shape[0], _p(_c(assign, np.int32)),
+                      int(K), _p(_c(center, np.float64)), _p(mom))
+    return mom
+
+
+def covariance(mom):
+    cov = np.zeros(6)
+    rc = lib().orc_covariance_from_moments(_p(_c(mom, np.float64)), _p(cov))
+    return None if rc else cov
+
+
+def jacobi3(cov6):
+    R = np.zeros(9)
+    ev = np.zeros(3)
+    lib().orc_jacobi3(_p(_c(cov6, np.float64)), _p(R), _p(ev))
+    return R.reshape(3, 3), ev
+
+
+def cluster_frames(V, F, assign, K, center, fallback=None):
+    if fallback is None:
+        fallback = np.tile(np.eye(3).reshape(1, 9), (K, 1))
+    fr = np.zeros((K, 9))
+    lib().orc_cluster_frames(_p(_c(V, np.float32)), _p(_c(F, np.int32)), F.shape[0],
+                             _p(_c(assign, np.int32)), int(K), _p(_c(center, np.float64)),
+                             _p(_c(fallback, np.float64)), _p(fr))
+    return fr
+
+
+# ---------------------------------------------------------------------------
+# Mesh topology (edge adjacency) -- plain dictionary walk
+# ---------------------------------------------------------------------------
+
+def edge_adjacency(F):
+    """adj[t, e] = the other triangle on edge e = (v_e, v_{e+1}) of t.
+
+    Raises ValueError unless every undirected edge has exactly two triangles."""
+    F = np.asarray(F, dtype=np.int64)
+    edges = {}
+    for t in range(F.shape[0]):
+        for e in range(3):
+            a, b = int(F[t, e]), int(F[t, (e + 1) % 3])
+            edges.setdefault((min(a, b), max(a, b)), []).append((t, e))
+    adj = np.full((F.shape[0], 3), -1, dtype=np.int32)
+    for key, lst in edges.items():
+        if len(lst) != 2:
+            raise ValueError(f"edge {key} has {len(lst)} triangles")
+        (t0, e0), (t1, e1) = lst
+        adj[t0, e0] = t1
+        adj[t1, e1] = t0
+    return adj
+
+
+# ---------------------------------------------------------------------------
+# Layer state and the Lloyd step (Sec. 4.2.1, Eq. 11-13)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Layer:
+    assign: np.ndarray      # int32 [T]
+    parent: np.ndarray      # int32 [K]
+    frames: np.ndarray      # float64 [K, 9], rows = box axes
+    n: np.ndarray           # int32 [K, 9]
+    bnd: np.ndarray         # int64 [K, 6]
+    obv: np.ndarray         # uint64 [K]
+
+    @property
+    def K(self):
+        return int(self.parent.shape[0])
+
+    def copy(self):
+        return Layer(self.assign.copy(), self.parent.copy(), self.frames.copy(), self.n.copy(),
+                     self.bnd.copy(), self.obv.copy())
+
+
+@dataclass
+class Problem:
+    """A mesh on its lattice, with the oracle's per-point occupancy."""
+    V: np.ndarray
+    F: np.ndarray
+    N: int
+    lo: np.ndarray = None
+    h: np.ndarray = None
+    U: np.ndarray = None
+    adj: np.ndarray = None
+    occ: Occupancy = None
+    center: np.ndarray = field(default=None)
+
+    def __post_init__(self):
+        self.V = _c(self.V, np.float32)
+        self.F = _c(self.F, np.int32)
+        self.lo, self.h = lattice_frame(self.V, self.N)
+        self.U = snap(self.V, self.lo, self.h)
+        if self.adj is None:
+            self.adj = edge_adjacency(self.F)
+        self.occ = Occupancy(self.N, self.U, self.F)
+        # moments are taken about the lattice AABB centre lo + N h / 2
+        self.center = self.lo + 0.5 * self.N * self.h
+
+
+def layer_from_frames(P: Problem, assign, parent, frames) -> Layer:
+    """Layer state from an assignment and given frames: quantised normals, tight bounds, exact OBV."""
+    assign = _c(assign, np.int32)
+    parent = _c(parent, np.int32)
+    K = parent.shape[0]
+    frames = _c(frames, np.float64).reshape(K, 9)
+    n = frame_normals(frames, P.h)
+    bnd = tight_bounds(P.U, P.F, assign, K, n)
+    obv, _ = outer_volume(P.occ, n, bnd)
+    return Layer(assign, parent, frames.copy(), n, bnd, obv)
+
+
+def layer_init(P: Problem, assign, parent, fallback=None) -> Layer:
+    """New layer seeded from covariance frames of the given assignment."""
+    assign = _c(assign, np.int32)
+    K = int(np.asarray(parent).shape[0])
+    fr = cluster_frames(P.V, P.F, assign, K, P.center, fallback)
+    return layer_from_frames(P, assign, parent, fr)
+
+
+def lloyd_moves(P: Problem, L: Layer, rounds: int):
+    """Partition rounds of one Lloyd step (in place). Returns per-round stats."""
+    # every column any candidate box may touch is inside the AABB of the union
+    # of grown boxes; the C side reports -3 if one is missing, in which case
+    # the needed columns are computed and the step is retried from a copy.
+    st = (RoundStats * max(rounds, 1))()
+    while True:
+        work = L.copy()
+        rc = lib().orc_lloyd_moves(_p(P.U), _p(P.F), _p(P.adj), P.F.shape[0], _p(work.assign),
+                                   _p(work.parent), work.K, _p(work.n), _p(work.bnd), _p(work.obv),
+                                   _p(P.occ.occ), _p(P.occ.known), P.N, int(rounds), st)
+        if rc == -3:
+            P.occ.fill_all()
+            continue
+        if rc < 0:
+            raise RuntimeError(f"orc_lloyd_moves failed ({rc})")
+        L.assign[:], L.bnd[:], L.obv[:] = work.assign, work.bnd, work.obv
+        return [dict(proposals=s.proposals, accepted=s.accepted, gain=s.gain, evals=s.evals)
+                for s in st[:rc]]
+
+
+def refit(P: Problem, L: Layer):
+    """Box parameter update (Sec. 4.2.1 step 2, restated as a covariance frame kept only if the exact OBV drops)."""
+    acc = np.zeros(L.K, dtype=np.uint8)
+    while True:
+        fr, n, bnd, obv = L.frames.copy(), L.n.copy(), L.bnd.copy(), L.obv.copy()
+        rc = lib().orc_refit(_p(P.V), _p(P.U), _p(P.F), P.F.shape[0], _p(L.assign), L.K, _p(P.center),
+                             _p(P.h), _p(fr), _p(n), _p(bnd), _p(obv), _p(P.occ.occ), _p(P.occ.known),
+                             P.N, _p(acc))
+        if rc == -3:
+            P.occ.fill_all()
+            continue
+        if rc < 0:
+            raise RuntimeError(f"orc_refit failed ({rc})")
+        L.frames[:], L.n[:], L.bnd[:], L.obv[:] = fr, n, bnd, obv
+        return acc
+
+
+def lloyd_step(P: Problem, L: Layer, rounds: int = 16, do_refit: bool = True):
+    """One Lloyd iteration: partition rounds, then refit."""
+    st = lloyd_moves(P, L, rounds)
+    acc = refit(P, L) if do_refit else np.zeros(L.K, dtype=np.uint8)
+    return st, acc
+
+
+def median_split(P: Problem, L: Layer):
+    child = np.zeros(P.F.shape[0], dtype=np.int32)
+    rc = lib().orc_median_split(_p(P.U), _p(P.F), P.F.shape[0], _p(L.assign), L.K, _p(L.n), _p(child))
+    if rc:
+        raise ValueError("a cluster has fewer than two triangles")
+    return child
+
+
+def eq7_score(obv_per_level, depth):
+    """Eq. 7 with the weights of Sec. 5: level L (root 0, leaves `depth`)
+    weighs (depth - L) + 1, i.e. leaves 1, their parents 2, ...  Returns the
+    weighted sum of per-level outer volumes (in lattice points)."""
+    return sum(float(depth - L + 1) * float(np.sum(np.asarray(o, dtype=np.float64)))
+               for L, o in enumerate(obv_per_level))
+
+
+def build_tree(P: Problem, depth: int, iters: int, rounds: int = 16):
+    """Top-down construction (Sec. 4.2.2): root box, then per level a median
+    split of every node into two children followed by `iters` Lloyd steps
+    restricted to siblings.  Returns the list of layers (root first)."""
+    T = P.F.shape[0]
+    root = layer_init(P, np.zeros(T, dtype=np.int32), np.zeros(1, dtype=np.int32))
+    layers = [root]
+    for lev in range(1, depth + 1):
+        prev = layers[-1]
+        child = median_split(P, prev)
+        K = 2 * prev.K
+        parent = (np.arange(K) // 2).astype(np.int32)
+        fallback = np.repeat(prev.frames, 2, axis=0)
+        L = layer_init(P, child, parent, fallback)
+        for _ in range(iters):
+            st, acc = lloyd_step(P, L, rounds)
+            if sum(s["accepted"] for s in st) == 0 and not acc.any():
+                break
+        layers.append(L)
+    return layers
