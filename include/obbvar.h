@@ -1,0 +1,260 @@
+/*
+ * obbvar — exact outer volume of oriented bounding boxes and the variational
+ * OBB-tree construction of "Variational Hierarchical Directed Bounding Box
+ * Construction for Solid Mesh Models" (arXiv 2203.10521), on one GPU.
+ *
+ * C ABI.  Plain pointers and sizes; no C++ or framework types cross it.
+ *
+ * Conventions
+ *  - Every function returning obb_status returns OBB_OK (0) or a negative
+ *    code; obb_last_error(ctx) gives a one-line explanation of the last
+ *    failure on that context.  No exception crosses the ABI.
+ *  - Opaque handles (obb_ctx, obb_mesh, obb_lattice, obb_layer, obb_tree) are
+ *    owned by the library and released with their *_free / obb_destroy call.
+ *    A lattice borrows its mesh, a layer its lattice, a tree its lattice:
+ *    free in the reverse order of creation.
+ *  - Input arrays are borrowed for the duration of the call.  Output arrays
+ *    are owned by the caller.  Arguments named on_device say whether the
+ *    caller's arrays live in device memory (1) or host memory (0).
+ *  - Work is enqueued on the context's CUDA stream.  Calls whose outputs are
+ *    host arrays synchronise that stream before returning; calls with device
+ *    outputs return as soon as the work is enqueued.  Errors detected on the
+ *    device (range overflow of a box) are reported by the next call that
+ *    synchronises.
+ *  - One GPU, no CPU fallback: a context fails to create without a device.
+ *
+ * Geometry (readings of the paper shared by every call)
+ *  - Lattice: N points per axis, cell centred over the vertex AABB:
+ *    x_b(i) = lo_b + (i + 1/2) h_b with h_b = (hi_b - lo_b) / N.  The solid
+ *    Omega(X) of Sec. 3 is sampled at these points; the lattice continues
+ *    over all of Z^3 with every point outside [0, N)^3 outside the solid.
+ *  - Fixed point: vertex coordinates snap to U_b = rint(((x_b - lo_b) / h_b
+ *    - 1/2) * 2^8) (FP64, round half to even); lattice point i sits at
+ *    U = 256 i.  All inside/outside decisions are exact integer predicates
+ *    on U.
+ *  - Box: frame R (rows = unit axes), quantised normals
+ *    n_ab = rint(2^24 R_ab h_b / h_max) and integer slab bounds:
+ *    a lattice point p is in the box iff lo_a <= n_a . (256 p) <= hi_a for
+ *    a = 0, 1, 2 (closed box).
+ *  - Outer volume (Eq. 4, Sec. 3): the number of lattice points inside the
+ *    box and outside the solid.  Multiply by h_0 h_1 h_2 for a volume.
+ */
+#ifndef OBBVAR_H
+#define OBBVAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t obb_status;
+
+enum {
+    OBB_OK = 0,
+    OBB_ERR_ARG = -1,             /* null pointer, bad size, non-finite or negative box extent */
+    OBB_ERR_NOT_WATERTIGHT = -2,  /* an undirected edge is not shared by exactly two triangles */
+    OBB_ERR_RANGE = -3,           /* lattice size, fixed-point or box range out of bounds */
+    OBB_ERR_EMPTY_CLUSTER = -4,   /* a cluster with no triangle, or one too small to split */
+    OBB_ERR_CUDA = -5,            /* a CUDA runtime call failed */
+    OBB_ERR_TIMEOUT = -6,         /* a bounded device wait gave up */
+    OBB_ERR_OOM = -7,             /* device allocation failed */
+    OBB_ERR_STATE = -8            /* handle used with the wrong context or in the wrong order */
+};
+
+typedef struct obb_ctx obb_ctx;
+typedef struct obb_mesh obb_mesh;
+typedef struct obb_lattice obb_lattice;
+typedef struct obb_layer obb_layer;
+typedef struct obb_tree obb_tree;
+
+/* A world-space oriented box: centre, first two unit axes (axis2 = axis0 x
+ * axis1), half extents along the three axes.  48 bytes. */
+typedef struct {
+    float c[3];
+    float axis0[3];
+    float axis1[3];
+    float half[3];
+} obb_box;
+
+/* A quantised box (the exact form every count uses): normals n[a*3+b]
+ * (int32, row a = normal of slab a) and bounds b[2a] = lo_a, b[2a+1] = hi_a
+ * in fixed-point units.  88 bytes, 8-byte aligned. */
+typedef struct {
+    int32_t n[9];
+    int32_t reserved;
+    int64_t b[6];
+} obb_qbox;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, enqueuing on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream may be
+ * one owned by another framework; it must outlive the context. */
+obb_status obb_create(obb_ctx** out, int32_t device, void* stream);
+/* Point the context at another stream (same device). */
+obb_status obb_set_stream(obb_ctx* ctx, void* stream);
+/* Wait for all work enqueued by the context; reports pending device errors. */
+obb_status obb_synchronize(obb_ctx* ctx);
+void obb_destroy(obb_ctx* ctx);
+const char* obb_last_error(const obb_ctx* ctx);
+
+/* ------------------------------------------------------------------- mesh */
+
+/* The closed triangle mesh X of Sec. 3 (Definition 1 needs a solid):
+ * verts float32 [n_verts][3], tris int32 [n_tris][3], host memory.
+ * Validates that every undirected edge is shared by exactly two triangles
+ * (OBB_ERR_NOT_WATERTIGHT otherwise) and that every index is in range, builds
+ * the edge adjacency used by the Lloyd step (Sec. 4.2.1 "adjacent faces")
+ * and copies everything to the device. */
+obb_status obb_mesh_create(obb_ctx* ctx, const float* verts, int64_t n_verts, const int32_t* tris,
+                           int64_t n_tris, obb_mesh** out);
+void obb_mesh_free(obb_mesh* mesh);
+
+/* ---------------------------------------------------------- occupancy (a) */
+
+/* Solid occupancy Omega(X) (Sec. 3) on the N^3 lattice, 1 <= N <= 2048,
+ * by per-column crossing parity: snap the vertices (fixed point above); for
+ * every column (j, k) covered by a triangle's (y, z) projection, decide
+ * containment of the column point with Simulation of Simplicity (query point
+ * perturbed by (+eps, +eps^2)), compute the first index i* = ceil(x* / 256)
+ * whose point is at or beyond the crossing, and flip bit i*; a prefix XOR
+ * along each row then gives inside = odd number of crossings at or before
+ * the point.  Bit-exact.
+ * Layout (device, owned by the lattice): uint64 words, row (j, k) starts at
+ * word (k*N + j) * W with W = 2 * ceil(N / 128) (rows padded to 16 bytes);
+ * point i is bit (i & 63) of word (i >> 6); padding bits are 0.
+ * Synchronises once (reads back the lattice frame and the error word). */
+obb_status obb_build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_lattice** out);
+
+/* Borrowed view of a lattice: frame (lo, h), N, words per row, device
+ * pointers to the occupancy words and to the snapped vertices (int32 [n][3]).
+ * Any pointer argument may be NULL. */
+obb_status obb_lattice_desc(const obb_lattice* lat, double lo[3], double h[3], int32_t* N,
+                            int64_t* row_words, const uint64_t** d_words, const int32_t** d_fixed);
+void obb_lattice_free(obb_lattice* lat);
+
+/* -------------------------------------------------------- outer volume (b) */
+
+/* Quantise K world-space boxes to the exact integer form (Sec. 4.2.1: a box
+ * is its position and axes plus the extents; here normals and slab bounds):
+ * axis2 = axis0 x axis1 (FP64), n_ab = rint(2^24 R_ab h_b / h_max),
+ * m_a = sum_b R_ab ((c_b - lo_b) - h_b / 2), s = 2^32 / h_max,
+ * lo_a = floor((m_a - half_a) s), hi_a = ceil((m_a + half_a) s), every step a
+ * correctly rounded FP64 operation in this order.  A box with a non-finite
+ * value or a negative half extent flags OBB_ERR_ARG. */
+obb_status obb_quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* boxes, int64_t K,
+                              obb_qbox* out, int32_t on_device);
+
+/* Outer volume OBV(X, O) of Eq. 4 for K quantised boxes: counts[k] = number
+ * of lattice points of Z^3 in box k that are outside the solid (exact);
+ * points[k] (optional, may be NULL) = number of lattice points in box k.
+ * Each box's index-space bounding box must lie within +-2^20 of the lattice
+ * (OBB_ERR_RANGE otherwise).  counts/points are uint64 [K]. */
+obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* boxes, int64_t K,
+                              uint64_t* counts, uint64_t* points, int32_t on_device);
+
+/* obb_quantize_boxes followed by obb_outer_volume_q. */
+obb_status obb_outer_volume(obb_ctx* ctx, const obb_lattice* lat, const obb_box* boxes, int64_t K,
+                            uint64_t* counts, uint64_t* points, int32_t on_device);
+
+/* ------------------------------------------------------ Lloyd layer (c) */
+
+/* One layer Z of Sec. 3: K clusters of triangles (the partition of Eq. 11)
+ * with their boxes.  assign int32 [n_tris] in [0, K); parent int32 [K]:
+ * moves are allowed only between clusters with the same parent (siblings),
+ * which keeps the tree nested.  frames (optional, float64 [K][9], rows =
+ * axes): when NULL each cluster's frame comes from the eigenvectors of its
+ * area-weighted triangle covariance (FP32 compensated sums, FP64 Jacobi).
+ * Boxes are the tight slabs of the cluster's vertices; the outer volume of
+ * each is counted exactly.  Every cluster must be non-empty
+ * (OBB_ERR_EMPTY_CLUSTER). */
+obb_status obb_layer_init(obb_ctx* ctx, const obb_lattice* lat, const int32_t* assign,
+                          const int32_t* parent, int32_t K, const double* frames, int32_t on_device,
+                          obb_layer** out);
+
+typedef struct {
+    int32_t rounds;   /* partition rounds per step (stop earlier when a round accepts nothing); <= 0: 16 */
+    int32_t refit;    /* 1: run the box-parameter update after the partition rounds */
+} obb_step_opts;
+
+typedef struct {
+    int32_t rounds_run;
+    int32_t refits_accepted;
+    int64_t proposals;         /* over all rounds */
+    int64_t moves;             /* accepted triangle moves */
+    int64_t gain;              /* sum of accepted gains, lattice points */
+    int64_t box_evals;         /* exact box counts performed */
+    uint64_t points_counted;   /* lattice points inside the boxes counted */
+    uint64_t total_obv;        /* sum of the layer's outer volumes after the step */
+} obb_step_stats;
+
+/* One Lloyd iteration on the layer (Sec. 4.2.1, Eq. 11-13), in place.
+ * Partition rounds: every triangle t of a cluster s with >= 2 triangles that
+ * is extremal in s (attains one of s's six slab bounds) evaluates moving to
+ * each sibling cluster k of its edge neighbours with the exact gain
+ *   [OBV(s) - OBV(s without t)] - [OBV(k with t) - OBV(k)]
+ * (boxes keep their frames; bounds follow the new membership); it proposes
+ * its best k (largest gain, ties to the smaller k) when the gain is > 0.
+ * A proposal is accepted when its key (gain, then smaller t) is the largest
+ * among all proposals whose source or target cluster is its source or
+ * target, so accepted moves touch disjoint clusters and the layer total
+ * drops by exactly the sum of their gains.
+ * Refit (opts->refit): new frame from the covariance eigenvectors, tight
+ * bounds, exact count; kept only when the outer volume strictly drops.
+ * stats may be NULL; when given, the call synchronises. */
+obb_status obb_lloyd_step(obb_ctx* ctx, obb_layer* layer, const obb_step_opts* opts, obb_step_stats* stats);
+
+/* Read a layer: assign int32 [n_tris], frames float64 [K][9], qboxes [K],
+ * boxes [K] (world-space report form of the quantised boxes), obv uint64 [K].
+ * Any output may be NULL. */
+obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* layer, int32_t* assign, double* frames,
+                          obb_qbox* qboxes, obb_box* boxes, uint64_t* obv, int32_t on_device);
+int32_t obb_layer_clusters(const obb_layer* layer);
+
+/* Median split of every cluster of the layer into two children, the seeding
+ * step of the top-down decomposition (Sec. 4.2.2): triangles of cluster c are
+ * ordered by key n_0 . (U_p + U_q + U_r) (the cluster's quantised major axis
+ * applied to three times the fixed-point centroid, exact int64), ties by
+ * triangle index; the first ceil(size / 2) get child[t] = 2c, the rest 2c + 1.
+ * child is int32 [n_tris].  OBB_ERR_EMPTY_CLUSTER if a cluster has fewer
+ * than two triangles.  Synchronises. */
+obb_status obb_layer_split(obb_ctx* ctx, const obb_layer* layer, int32_t* child, int32_t on_device);
+void obb_layer_free(obb_layer* layer);
+
+/* --------------------------------------------------------- tree (d) */
+
+typedef struct {
+    int32_t depth;    /* levels below the root; 2^depth leaves */
+    int32_t iters;    /* Lloyd iterations per level (stop early when one changes nothing) */
+    int32_t rounds;   /* partition rounds per iteration; <= 0: 16 */
+    int32_t refit;    /* run the box-parameter update in each iteration */
+} obb_tree_opts;
+
+/* Binary OBB tree by top-down decomposition (Sec. 4.2.2): the root box
+ * holds every triangle; each level splits every node into two children at
+ * the median of its triangles along the node's major axis (key n_0 . (U_p +
+ * U_q + U_r), ties by triangle index, first ceil(size/2) to the first child)
+ * and then runs `iters` Lloyd iterations restricted to siblings.  Needs
+ * n_tris >= 2^depth (OBB_ERR_EMPTY_CLUSTER when a node has fewer than two
+ * triangles to split). */
+obb_status obb_build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts* opts, obb_tree** out);
+
+/* Layer `level` (0 = root) of a tree, as obb_layer_read (host arrays). */
+obb_status obb_tree_read(obb_ctx* ctx, const obb_tree* tree, int32_t level, int32_t* assign,
+                         double* frames, obb_qbox* qboxes, obb_box* boxes, uint64_t* obv);
+int32_t obb_tree_depth(const obb_tree* tree);
+
+/* Eq. 7 with the layer weights of Sec. 5 (a level's weight = its number of
+ * levels to the leaves plus one: leaves 1, their parents 2, ...), each layer's
+ * OMV replaced by the sum of its boxes' outer volumes (Eq. 6, Eq. 8):
+ * *points = weighted sum in lattice points, *volume = the same times
+ * h_0 h_1 h_2.  Either pointer may be NULL. */
+obb_status obb_tree_score(obb_ctx* ctx, const obb_tree* tree, double* points, double* volume);
+void obb_tree_free(obb_tree* tree);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OBBVAR_H */

@@ -1,0 +1,390 @@
+"""Python binding of libobbvar (include/obbvar.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module converts
+numpy arrays / torch CUDA tensors to pointers, calls the C ABI and raises on
+error.  There is no CPU fallback: importing works without a GPU, but creating
+a Context needs the built library and a CUDA device.
+
+Host arrays (numpy) are passed with on_device=0; torch CUDA tensors with
+on_device=1 (they must be contiguous and on the context's device).  The
+context enqueues on torch's current CUDA stream unless told otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+OBB_OK = 0
+_ERRORS = {-1: "OBB_ERR_ARG", -2: "OBB_ERR_NOT_WATERTIGHT", -3: "OBB_ERR_RANGE", -4: "OBB_ERR_EMPTY_CLUSTER",
+           -5: "OBB_ERR_CUDA", -6: "OBB_ERR_TIMEOUT", -7: "OBB_ERR_OOM", -8: "OBB_ERR_STATE"}
+
+BOX_DTYPE = np.dtype([("c", "<f4", (3,)), ("axis0", "<f4", (3,)), ("axis1", "<f4", (3,)), ("half", "<f4", (3,))])
+QBOX_DTYPE = np.dtype([("n", "<i4", (9,)), ("reserved", "<i4"), ("b", "<i8", (6,))])
+assert BOX_DTYPE.itemsize == 48 and QBOX_DTYPE.itemsize == 88
+
+
+class ObbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class StepOpts(C.Structure):
+    _fields_ = [("rounds", C.c_int32), ("refit", C.c_int32)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("rounds_run", C.c_int32), ("refits_accepted", C.c_int32), ("proposals", C.c_int64),
+                ("moves", C.c_int64), ("gain", C.c_int64), ("box_evals", C.c_int64),
+                ("points_counted", C.c_uint64), ("total_obv", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TreeOpts(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("iters", C.c_int32), ("rounds", C.c_int32), ("refit", C.c_int32)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libobbvar.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libobbvar.so is not built ({LIB_PATH}); run paper_2203_10521_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    sig = {
+        "obb_create": [C.POINTER(vp), i32, vp],
+        "obb_set_stream": [vp, vp],
+        "obb_synchronize": [vp],
+        "obb_mesh_create": [vp, vp, i64, vp, i64, C.POINTER(vp)],
+        "obb_build_occupancy": [vp, vp, i32, C.POINTER(vp)],
+        "obb_lattice_desc": [vp, vp, vp, vp, vp, vp, vp],
+        "obb_quantize_boxes": [vp, vp, vp, i64, vp, i32],
+        "obb_outer_volume_q": [vp, vp, vp, i64, vp, vp, i32],
+        "obb_outer_volume": [vp, vp, vp, i64, vp, vp, i32],
+        "obb_layer_init": [vp, vp, vp, vp, i32, vp, i32, C.POINTER(vp)],
+        "obb_lloyd_step": [vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
+        "obb_layer_read": [vp, vp, vp, vp, vp, vp, vp, i32],
+        "obb_layer_split": [vp, vp, vp, i32],
+        "obb_build_tree": [vp, vp, C.POINTER(TreeOpts), C.POINTER(vp)],
+        "obb_tree_read": [vp, vp, i32, vp, vp, vp, vp, vp],
+        "obb_tree_score": [vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int32
+    for name in ("obb_destroy", "obb_mesh_free", "obb_lattice_free", "obb_layer_free", "obb_tree_free"):
+        getattr(L, name).argtypes = [vp]
+        getattr(L, name).restype = None
+    L.obb_last_error.argtypes = [vp]
+    L.obb_last_error.restype = C.c_char_p
+    L.obb_layer_clusters.argtypes = [vp]
+    L.obb_layer_clusters.restype = C.c_int32
+    L.obb_tree_depth.argtypes = [vp]
+    L.obb_tree_depth.restype = C.c_int32
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C entry points declared in include/obbvar.h."""
+    return ["obb_create", "obb_set_stream", "obb_synchronize", "obb_destroy", "obb_last_error",
+            "obb_mesh_create", "obb_mesh_free", "obb_build_occupancy", "obb_lattice_desc", "obb_lattice_free",
+            "obb_quantize_boxes", "obb_outer_volume_q", "obb_outer_volume", "obb_layer_init", "obb_lloyd_step",
+            "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
+            "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free"]
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _host(x, dtype):
+    """Contiguous numpy copy/view of x with the given dtype (boxes may be [K, 12] float32)."""
+    a = np.asarray(x)
+    if dtype is BOX_DTYPE and a.dtype != BOX_DTYPE:
+        a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1, 12).view(BOX_DTYPE).reshape(-1)
+    elif dtype is not None and a.dtype != dtype:
+        a = a.astype(dtype)
+    return np.ascontiguousarray(a)
+
+
+def _arg(x, dtype=None):
+    """(pointer, on_device, keepalive) for a numpy array or a torch CUDA tensor."""
+    if x is None:
+        return None, 0, None
+    if _is_torch(x):
+        if x.is_cuda:
+            if not x.is_contiguous():
+                raise ValueError("CUDA tensors must be contiguous")
+            return C.c_void_p(x.data_ptr()), 1, x
+        x = x.numpy()
+    a = _host(x, dtype)
+    return a.ctypes.data_as(C.c_void_p), 0, a
+
+
+def _count(x, keep, itemsize):
+    if _is_torch(x) and x.is_cuda:
+        return x.numel() * x.element_size() // itemsize
+    return len(keep)
+
+
+class _DevArray:
+    """__cuda_array_interface__ view of library-owned device memory."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class Context:
+    """A library context bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = 0
+        h = C.c_void_p()
+        rc = self.lib.obb_create(C.byref(h), int(device), C.c_void_p(stream))
+        if rc != OBB_OK:
+            raise ObbError(rc, "cannot create a context (no CUDA device?)")
+        self.h = h
+        self.device = device
+
+    def check(self, rc):
+        if rc != OBB_OK:
+            raise ObbError(rc, self.lib.obb_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.obb_destroy(self.h)
+            self.h = None
+
+    def set_stream(self, stream):
+        self.check(self.lib.obb_set_stream(self.h, C.c_void_p(stream)))
+
+    def synchronize(self):
+        self.check(self.lib.obb_synchronize(self.h))
+
+    # ------------------------------------------------------------------ mesh
+    def mesh_create(self, verts, tris):
+        V = np.ascontiguousarray(verts, dtype=np.float32)
+        F = np.ascontiguousarray(tris, dtype=np.int32)
+        h = C.c_void_p()
+        self.check(self.lib.obb_mesh_create(self.h, V.ctypes.data_as(C.c_void_p), V.shape[0],
+                                            F.ctypes.data_as(C.c_void_p), F.shape[0], C.byref(h)))
+        return Mesh(self, h, V.shape[0], F.shape[0])
+
+    # ------------------------------------------------------------- occupancy
+    def build_occupancy(self, mesh, N: int):
+        h = C.c_void_p()
+        self.check(self.lib.obb_build_occupancy(self.h, mesh.h, int(N), C.byref(h)))
+        return Lattice(self, h, mesh)
+
+    # ---------------------------------------------------------- outer volume
+    def quantize_boxes(self, lat, boxes, out=None):
+        p, dev, keep = _arg(boxes, BOX_DTYPE)
+        K = _count(boxes, keep, 48)
+        if out is None:
+            out = self._out_like(dev, K, QBOX_DTYPE, 88)
+        po, _, _ = _arg(out) if dev else (out.ctypes.data_as(C.c_void_p), 0, out)
+        self.check(self.lib.obb_quantize_boxes(self.h, lat.h, p, K, po, dev))
+        return out
+
+    def outer_volume(self, lat, boxes, counts=None, points=None, want_points=False):
+        p, dev, keep = _arg(boxes, BOX_DTYPE)
+        K = _count(boxes, keep, 48)
+        return self._ov(self.lib.obb_outer_volume, lat, p, dev, K, counts, points, want_points)
+
+    def outer_volume_q(self, lat, qboxes, counts=None, points=None, want_points=False):
+        p, dev, keep = _arg(qboxes, QBOX_DTYPE)
+        K = _count(qboxes, keep, 88)
+        return self._ov(self.lib.obb_outer_volume_q, lat, p, dev, K, counts, points, want_points)
+
+    def _out_like(self, dev, K, dtype, itemsize, torch_dtype=None):
+        if dev:
+            import torch
+            if torch_dtype is not None:
+                return torch.empty(K, dtype=torch_dtype, device=f"cuda:{self.device}")
+            return torch.empty(K * itemsize, dtype=torch.uint8, device=f"cuda:{self.device}")
+        return np.zeros(K, dtype=dtype)
+
+    def _ov(self, fn, lat, p, dev, K, counts, points, want_points):
+        import_torch = dev
+        if counts is None:
+            if import_torch:
+                import torch
+                counts = torch.empty(K, dtype=torch.int64, device=f"cuda:{self.device}")
+            else:
+                counts = np.zeros(K, dtype=np.uint64)
+        if points is None and want_points:
+            if import_torch:
+                import torch
+                points = torch.empty(K, dtype=torch.int64, device=f"cuda:{self.device}")
+            else:
+                points = np.zeros(K, dtype=np.uint64)
+        pc = C.c_void_p(counts.data_ptr()) if dev else counts.ctypes.data_as(C.c_void_p)
+        pp = None
+        if points is not None:
+            pp = C.c_void_p(points.data_ptr()) if dev else points.ctypes.data_as(C.c_void_p)
+        self.check(fn(self.h, lat.h, p, K, pc, pp, dev))
+        return (counts, points) if want_points or points is not None else counts
+
+    # ----------------------------------------------------------------- layer
+    def layer_init(self, lat, assign, parent, frames=None):
+        dev = 1 if _is_torch(assign) and assign.is_cuda else 0
+        pa, _, ka = _arg(assign, np.int32)
+        pp, _, kp = _arg(parent, np.int32)
+        pf, _, kf = _arg(frames, np.float64)
+        K = len(parent)
+        h = C.c_void_p()
+        self.check(self.lib.obb_layer_init(self.h, lat.h, pa, pp, int(K), pf, dev, C.byref(h)))
+        return Layer(self, h, lat, K)
+
+    def lloyd_step(self, layer, rounds=16, refit=True, stats=True):
+        o = StepOpts(int(rounds), 1 if refit else 0)
+        st = StepStats()
+        self.check(self.lib.obb_lloyd_step(self.h, layer.h, C.byref(o), C.byref(st) if stats else None))
+        return st.as_dict() if stats else None
+
+    def layer_read(self, layer):
+        T, K = layer.lat.mesh.nt, layer.K
+        assign = np.zeros(T, np.int32)
+        frames = np.zeros((K, 9), np.float64)
+        q = np.zeros(K, QBOX_DTYPE)
+        boxes = np.zeros(K, BOX_DTYPE)
+        obv = np.zeros(K, np.uint64)
+        self.check(self.lib.obb_layer_read(self.h, layer.h, assign.ctypes.data_as(C.c_void_p),
+                                           frames.ctypes.data_as(C.c_void_p), q.ctypes.data_as(C.c_void_p),
+                                           boxes.ctypes.data_as(C.c_void_p), obv.ctypes.data_as(C.c_void_p), 0))
+        return dict(assign=assign, frames=frames, qboxes=q, boxes=boxes, obv=obv)
+
+    def layer_split(self, layer):
+        child = np.zeros(layer.lat.mesh.nt, np.int32)
+        self.check(self.lib.obb_layer_split(self.h, layer.h, child.ctypes.data_as(C.c_void_p), 0))
+        return child
+
+    # ------------------------------------------------------------------ tree
+    def build_tree(self, lat, depth, iters, rounds=16, refit=True):
+        o = TreeOpts(int(depth), int(iters), int(rounds), 1 if refit else 0)
+        h = C.c_void_p()
+        self.check(self.lib.obb_build_tree(self.h, lat.h, C.byref(o), C.byref(h)))
+        return Tree(self, h, lat)
+
+    def tree_read(self, tree, level):
+        T = tree.lat.mesh.nt
+        K = 1 << level
+        assign = np.zeros(T, np.int32)
+        frames = np.zeros((K, 9), np.float64)
+        q = np.zeros(K, QBOX_DTYPE)
+        boxes = np.zeros(K, BOX_DTYPE)
+        obv = np.zeros(K, np.uint64)
+        self.check(self.lib.obb_tree_read(self.h, tree.h, int(level), assign.ctypes.data_as(C.c_void_p),
+                                          frames.ctypes.data_as(C.c_void_p), q.ctypes.data_as(C.c_void_p),
+                                          boxes.ctypes.data_as(C.c_void_p), obv.ctypes.data_as(C.c_void_p)))
+        return dict(assign=assign, frames=frames, qboxes=q, boxes=boxes, obv=obv)
+
+    def tree_score(self, tree):
+        p = C.c_double()
+        v = C.c_double()
+        self.check(self.lib.obb_tree_score(self.h, tree.h, C.byref(p), C.byref(v)))
+        return p.value, v.value
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+
+    def free(self):
+        if getattr(self, "h", None) and self.ctx.h:
+            getattr(self.ctx.lib, self._free)(self.h)
+            self.h = None
+
+
+class Mesh(_Handle):
+    _free = "obb_mesh_free"
+
+    def __init__(self, ctx, h, nv, nt):
+        super().__init__(ctx, h)
+        self.nv, self.nt = nv, nt
+
+
+class Lattice(_Handle):
+    _free = "obb_lattice_free"
+
+    def __init__(self, ctx, h, mesh):
+        super().__init__(ctx, h)
+        self.mesh = mesh
+        lo = (C.c_double * 3)()
+        hh = (C.c_double * 3)()
+        N = C.c_int32()
+        W = C.c_int64()
+        words = C.c_void_p()
+        fixed = C.c_void_p()
+        ctx.check(ctx.lib.obb_lattice_desc(h, lo, hh, C.byref(N), C.byref(W), C.byref(words), C.byref(fixed)))
+        self.lo = np.array(lo[:])
+        self.h_ = np.array(hh[:])
+        self.N = N.value
+        self.W = W.value
+        self._words = words.value
+        self._fixed = fixed.value
+
+    @property
+    def spacing(self):
+        return self.h_
+
+    def words(self):
+        """The occupancy words as a torch uint64-typed view (int64 tensor) of library memory."""
+        import torch
+        return torch.as_tensor(_DevArray(self._words, (self.N * self.N * self.W,), "<i8"),
+                               device=f"cuda:{self.ctx.device}")
+
+    def fixed(self):
+        import torch
+        return torch.as_tensor(_DevArray(self._fixed, (self.mesh.nv, 3), "<i4"), device=f"cuda:{self.ctx.device}")
+
+    def bits(self):
+        """Occupancy as a numpy uint8 array [k, j, i] (copies to the host)."""
+        w = self.words().cpu().numpy().view(np.uint64).reshape(self.N, self.N, self.W)
+        b = np.unpackbits(w.view(np.uint8), axis=-1, bitorder="little")
+        return b[..., :self.N]
+
+
+class Layer(_Handle):
+    _free = "obb_layer_free"
+
+    def __init__(self, ctx, h, lat, K):
+        super().__init__(ctx, h)
+        self.lat = lat
+        self.K = K
+
+
+class Tree(_Handle):
+    _free = "obb_tree_free"
+
+    def __init__(self, ctx, h, lat):
+        super().__init__(ctx, h)
+        self.lat = lat
+        self.depth = ctx.lib.obb_tree_depth(h)

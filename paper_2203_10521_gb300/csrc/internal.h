@@ -1,0 +1,175 @@
+// Internal declarations shared by the translation units of libobbvar.
+// Nothing here crosses the C ABI (include/obbvar.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/obbvar.h"
+
+namespace obbv {
+
+constexpr int kS = 8;            // fixed-point fraction bits of snapped vertices
+constexpr int kQ = 24;           // fraction bits of quantised normals
+constexpr int kMaxN = 2048;      // lattice points per axis
+constexpr int64_t kBoxRange = int64_t(1) << 20;  // |index-space AABB| limit of a counted box
+constexpr int kRowsPerChunk = 32;                // rows of one box handled by one warp pass
+
+// device error word bits
+enum : int32_t {
+    kErrRange = 1,
+    kErrArg = 2,
+    kErrEmpty = 4,
+    kErrDegenerate = 8,
+    kErrOverflow = 16,
+};
+
+// Lattice frame; identical copies on the host and the device.
+struct LatticeFrame {
+    double lo[3];
+    double h[3];
+    double hmax;
+    double center[3];   // lo + N h / 2, origin of the covariance moments
+    int32_t N;
+    int32_t W;          // uint64 words per row (even)
+};
+
+// Per-box data the counting kernel needs, prepared once per box.
+struct BoxPrep {
+    int32_t n[9];
+    int32_t i0, i1;     // index-space AABB along x
+    int32_t j0, k0;     // first row
+    int32_t nj;         // rows along y
+    int32_t flags;
+    int64_t Lq[3], Hq[3];   // ceil(lo / 256), floor(hi / 256)
+    float rcp[3];           // 1 / n_a0, 0 when n_a0 == 0
+    int32_t pad;
+    uint64_t rows;          // nj * nk (0 = empty)
+};
+
+// Stream-ordered device allocation that only grows.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t n, cudaStream_t s);
+    void release(cudaStream_t s);
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace obbv
+
+struct obb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+    int32_t* d_err = nullptr;        // device error word
+    int32_t* h_small = nullptr;      // pinned host staging (64 ints)
+    // scratch reused across calls
+    obbv::DevBuf prep, chunk_off, qscratch, cscratch, pscratch, kdev, tmp_a, tmp_b, tmp_c, tmp_d,
+        cub_tmp;
+};
+
+struct obb_mesh {
+    obb_ctx* ctx = nullptr;
+    int64_t nv = 0, nt = 0;
+    float* d_verts = nullptr;        // [nv][3]
+    int32_t* d_tris = nullptr;       // [nt][3]
+    int32_t* d_adj = nullptr;        // [nt][3] neighbour across edge (v_e, v_e+1)
+};
+
+struct obb_lattice {
+    obb_ctx* ctx = nullptr;
+    const obb_mesh* mesh = nullptr;
+    obbv::LatticeFrame frame{};      // host copy
+    obbv::LatticeFrame* d_frame = nullptr;
+    int32_t* d_fixed = nullptr;      // [nv][3] snapped vertices
+    uint64_t* d_words = nullptr;     // occupancy
+    size_t n_words = 0;
+};
+
+// per-cluster top-2 extents along the six slab sides (2a = low side, 2a+1 = high side)
+struct ClusterExt {
+    int64_t v1[6];   // extreme value (min for low sides, max for high sides)
+    int64_t v2[6];   // extreme over the members other than arg[side]
+    int32_t arg[6];  // smallest triangle index attaining v1
+    int32_t pad[2];
+};
+
+struct obb_layer {
+    obb_ctx* ctx = nullptr;
+    const obb_lattice* lat = nullptr;
+    int32_t K = 0;
+    int64_t T = 0;
+    int32_t* d_assign = nullptr;
+    int32_t* d_parent = nullptr;
+    double* d_frames = nullptr;      // [K][9]
+    obb_qbox* d_q = nullptr;         // [K]
+    uint64_t* d_obv = nullptr;       // [K]
+    int32_t* d_size = nullptr;       // [K]
+    int32_t* d_start = nullptr;      // [K + 1]
+    int32_t* d_members = nullptr;    // [T] triangles sorted by cluster (stable)
+    ClusterExt* d_ext = nullptr;     // [K]
+    unsigned long long* d_best = nullptr;  // [K] best proposal key per cluster
+    int64_t* d_stats = nullptr;      // device counters (see lloyd.cu)
+    void* aux = nullptr;             // per-layer scratch owned by lloyd.cu
+};
+
+struct obb_tree {
+    obb_ctx* ctx = nullptr;
+    const obb_lattice* lat = nullptr;
+    std::vector<obb_layer*> layers;
+};
+
+namespace obbv {
+
+obb_status fail(obb_ctx* ctx, obb_status code, const std::string& msg);
+obb_status cuda_fail(obb_ctx* ctx, cudaError_t e, const char* what);
+obb_status check_device_error(obb_ctx* ctx);   // synchronises, reads and clears the error word
+
+#define OBB_CK(ctx, call)                                              \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::obbv::cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+#define OBB_TRY(expr)                         \
+    do {                                      \
+        obb_status s_ = (expr);               \
+        if (s_ != OBB_OK) return s_;          \
+    } while (0)
+
+// occupancy.cu
+obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_lattice* lat);
+
+// outer_volume.cu
+obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d_boxes, int64_t K,
+                          obb_qbox* d_out);
+// counts / points (points may be null) for K boxes whose count is held on the device at
+// d_K (int32); K_cap bounds it for scratch sizing.  counts/points are zeroed here.
+obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes,
+                       const int32_t* d_K, int64_t K_cap, uint64_t* d_counts, uint64_t* d_points);
+obb_status set_device_int(obb_ctx* ctx, int32_t* d_dst, int32_t value);
+// exclusive scan of n int32 values into out[n + 1] (out[n] = total), single block
+void launch_scan_i32(const int32_t* in, int32_t* out, const int32_t* d_n, int32_t n_cap,
+                     cudaStream_t s);
+void launch_box_report(const obb_lattice* lat, const double* d_frames, const obb_qbox* d_q, int32_t K,
+                       obb_box* d_out, cudaStream_t s);
+
+// lloyd.cu
+obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_assign,
+                        const int32_t* d_parent, int32_t K, const double* d_frames,
+                        const double* d_fallback, obb_layer** out);
+obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb_step_stats* st);
+void layer_destroy(obb_layer* L);
+obb_status rebuild_members(obb_ctx* ctx, obb_layer* L);
+
+// tree.cu
+obb_status build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts* opts, obb_tree* tree);
+obb_status split_layer(obb_ctx* ctx, const obb_layer* up, int32_t* d_child);
+
+}  // namespace obbv

@@ -1,0 +1,818 @@
+// Lloyd iteration on one layer of boxes (Sec. 4.2.1, Eq. 11-13), data parallel.
+//
+// Layer state lives on the device: triangle -> cluster map, per-cluster
+// frame (FP64), quantised box, exact outer volume, and the member list of
+// every cluster (triangles sorted by cluster, stable).
+//
+// Partition round (all exact integers):
+//   extents     block per cluster: for each of the six slab sides the extreme
+//               projection of the members, the smallest triangle attaining
+//               it, and the extreme over the other members;
+//   candidates  thread per triangle: a triangle that alone attains a side of
+//               its cluster s (size >= 2) shrinks s's box when it leaves; for
+//               each sibling cluster k of its edge neighbours the grown box of
+//               k is formed; every box that differs from the current one is
+//               appended to an evaluation list;
+//   count       the outer-volume kernel on the evaluation list;
+//   gains       gain = [OBV(s) - OBV(s - t)] - [OBV(k + t) - OBV(k)]; best k per
+//               triangle (ties -> smaller k); a positive proposal posts its key
+//               (gain << 24 | (2^24 - 1 - t)) with atomicMax at both clusters;
+//   accept      a proposal holding the maximum key at both of its clusters is
+//               applied; accepted moves touch disjoint clusters.
+// Refit: area-weighted covariance with compensated FP32 sums (TwoProduct +
+// TwoSum), cyclic Jacobi in FP64, quantised normals, tight bounds, exact count;
+// the new box is kept iff its outer volume is strictly smaller.
+#include <cub/cub.cuh>
+
+#include "internal.h"
+
+namespace obbv {
+namespace {
+
+enum { kStProposals = 0, kStAccepted, kStGain, kStEvals, kStRefits, kStPoints, kStCount };
+enum { kCtrCand = 0, kCtrEval, kCtrCount };
+
+struct Cand {
+    int32_t t, s;
+    int32_t k[3];
+    int32_t nk;
+    int32_t e_shr;
+    int32_t e_gro[3];
+    int32_t best;
+    int32_t pad;
+    int64_t gain;
+    unsigned long long key;
+};
+
+__device__ __forceinline__ void proj3(const int32_t* __restrict__ U, const int32_t* __restrict__ F, int32_t t,
+                                      const int32_t* n, int64_t* dmin, int64_t* dmax)
+{
+    int32_t v[3] = {F[3 * t], F[3 * t + 1], F[3 * t + 2]};
+    for (int a = 0; a < 3; ++a) {
+        dmin[a] = INT64_MAX;
+        dmax[a] = INT64_MIN;
+    }
+    for (int q = 0; q < 3; ++q) {
+        const int32_t* P = U + 3 * (int64_t)v[q];
+        int64_t x = P[0], y = P[1], z = P[2];
+        for (int a = 0; a < 3; ++a) {
+            int64_t d = (int64_t)n[3 * a] * x + (int64_t)n[3 * a + 1] * y + (int64_t)n[3 * a + 2] * z;
+            dmin[a] = min(dmin[a], d);
+            dmax[a] = max(dmax[a], d);
+        }
+    }
+}
+
+// ------------------------------------------------------- membership
+
+__global__ void k_hist(const int32_t* __restrict__ assign, int64_t T, int32_t K, int32_t* __restrict__ size,
+                       int32_t* err)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int32_t k = assign[t];
+    if (k < 0 || k >= K) {
+        atomicOr(err, kErrArg);
+        return;
+    }
+    atomicAdd(&size[k], 1);
+}
+
+__global__ void k_check_nonempty(const int32_t* __restrict__ size, int32_t K, int32_t* err)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K && size[k] == 0) atomicOr(err, kErrEmpty);
+}
+
+__global__ void k_iota(int32_t* p, int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (int32_t)i;
+}
+
+// ------------------------------------------------------- extents (a6)
+
+struct VT {
+    int64_t v;
+    int32_t t;
+};
+
+__device__ __forceinline__ bool better(const VT& a, const VT& b, bool lowside)
+{
+    if (a.v != b.v) return lowside ? (a.v < b.v) : (a.v > b.v);
+    return a.t < b.t;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_extents(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
+                                                const int32_t* __restrict__ members,
+                                                const int32_t* __restrict__ start,
+                                                const obb_qbox* __restrict__ q, ClusterExt* __restrict__ ext)
+{
+    const int32_t k = blockIdx.x;
+    const int32_t b0 = start[k], b1 = start[k + 1];
+    int32_t n[9];
+    for (int i = 0; i < 9; ++i) n[i] = q[k].n[i];
+    VT best[6];
+    for (int s = 0; s < 6; ++s) best[s] = VT{(s & 1) ? INT64_MIN : INT64_MAX, INT32_MAX};
+    for (int32_t i = b0 + threadIdx.x; i < b1; i += NT) {
+        int32_t t = members[i];
+        int64_t dmin[3], dmax[3];
+        proj3(U, F, t, n, dmin, dmax);
+        for (int a = 0; a < 3; ++a) {
+            VT lo{dmin[a], t}, hi{dmax[a], t};
+            if (better(lo, best[2 * a], true)) best[2 * a] = lo;
+            if (better(hi, best[2 * a + 1], false)) best[2 * a + 1] = hi;
+        }
+    }
+    __shared__ VT sh[6][NT / 32];
+    __shared__ VT fin[6];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int s = 0; s < 6; ++s) {
+        VT x = best[s];
+        for (int o = 16; o > 0; o >>= 1) {
+            VT y{(int64_t)__shfl_xor_sync(0xffffffffu, (long long)x.v, o), __shfl_xor_sync(0xffffffffu, x.t, o)};
+            if (better(y, x, (s & 1) == 0)) x = y;
+        }
+        if (lane == 0) sh[s][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int s = threadIdx.x;
+        VT x = sh[s][0];
+        for (int i = 1; i < NT / 32; ++i)
+            if (better(sh[s][i], x, (s & 1) == 0)) x = sh[s][i];
+        fin[s] = x;
+    }
+    __syncthreads();
+    // second pass: extreme over members other than the arg of each side
+    int64_t v2[6];
+    for (int s = 0; s < 6; ++s) v2[s] = (s & 1) ? INT64_MIN : INT64_MAX;
+    for (int32_t i = b0 + threadIdx.x; i < b1; i += NT) {
+        int32_t t = members[i];
+        int64_t dmin[3], dmax[3];
+        proj3(U, F, t, n, dmin, dmax);
+        for (int a = 0; a < 3; ++a) {
+            if (t != fin[2 * a].t) v2[2 * a] = min(v2[2 * a], dmin[a]);
+            if (t != fin[2 * a + 1].t) v2[2 * a + 1] = max(v2[2 * a + 1], dmax[a]);
+        }
+    }
+    __shared__ int64_t sh2[6][NT / 32];
+    for (int s = 0; s < 6; ++s) {
+        int64_t x = v2[s];
+        for (int o = 16; o > 0; o >>= 1) {
+            int64_t y = (int64_t)__shfl_xor_sync(0xffffffffu, (long long)x, o);
+            x = (s & 1) ? max(x, y) : min(x, y);
+        }
+        if (lane == 0) sh2[s][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int s = threadIdx.x;
+        int64_t x = sh2[s][0];
+        for (int i = 1; i < NT / 32; ++i) x = (s & 1) ? max(x, sh2[s][i]) : min(x, sh2[s][i]);
+        ext[k].v1[s] = fin[s].v;
+        ext[k].arg[s] = fin[s].t;
+        ext[k].v2[s] = x;
+    }
+}
+
+// ------------------------------------------------------- candidates (a7)
+
+__global__ void k_candidates(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
+                             const int32_t* __restrict__ adj, int64_t T, const int32_t* __restrict__ assign,
+                             const int32_t* __restrict__ parent, const int32_t* __restrict__ size,
+                             const ClusterExt* __restrict__ ext, const obb_qbox* __restrict__ q,
+                             Cand* __restrict__ cand, obb_qbox* __restrict__ evals, int32_t* __restrict__ ctr,
+                             int32_t cand_cap, int32_t eval_cap, int32_t* err)
+{
+    int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (tt >= T) return;
+    const int32_t t = (int32_t)tt;
+    const int32_t s = assign[t];
+    if (size[s] < 2) return;
+    const ClusterExt& e = ext[s];
+    obb_qbox shr = q[s];
+    bool changed = false;
+    for (int side = 0; side < 6; ++side)
+        if (e.arg[side] == t && e.v2[side] != e.v1[side]) {
+            shr.b[side] = e.v2[side];
+            changed = true;
+        }
+    if (!changed) return;
+    int32_t ks[3];
+    int nk = 0;
+    const int32_t ps = parent[s];
+    for (int i = 0; i < 3; ++i) {
+        int32_t k = assign[adj[3 * t + i]];
+        if (k == s || parent[k] != ps) continue;
+        bool dup = false;
+        for (int j = 0; j < nk; ++j) dup |= ks[j] == k;
+        if (!dup) ks[nk++] = k;
+    }
+    if (nk == 0) return;
+    const int32_t r = atomicAdd(&ctr[kCtrCand], 1);
+    if (r >= cand_cap) {
+        atomicOr(err, kErrOverflow);
+        return;
+    }
+    Cand c;
+    c.t = t;
+    c.s = s;
+    c.nk = nk;
+    c.best = -1;
+    c.pad = 0;
+    c.gain = 0;
+    c.key = 0;
+    for (int i = 0; i < 3; ++i) {
+        c.k[i] = i < nk ? ks[i] : -1;
+        c.e_gro[i] = -1;
+    }
+    c.e_shr = atomicAdd(&ctr[kCtrEval], 1);
+    if (c.e_shr >= eval_cap) {
+        atomicOr(err, kErrOverflow);
+        return;
+    }
+    evals[c.e_shr] = shr;
+    for (int i = 0; i < nk; ++i) {
+        const obb_qbox& qk = q[ks[i]];
+        int64_t dmin[3], dmax[3];
+        proj3(U, F, t, qk.n, dmin, dmax);
+        obb_qbox g = qk;
+        bool grew = false;
+        for (int a = 0; a < 3; ++a) {
+            if (dmin[a] < g.b[2 * a]) {
+                g.b[2 * a] = dmin[a];
+                grew = true;
+            }
+            if (dmax[a] > g.b[2 * a + 1]) {
+                g.b[2 * a + 1] = dmax[a];
+                grew = true;
+            }
+        }
+        if (grew) {
+            int32_t ei = atomicAdd(&ctr[kCtrEval], 1);
+            if (ei >= eval_cap) {
+                atomicOr(err, kErrOverflow);
+                return;
+            }
+            evals[ei] = g;
+            c.e_gro[i] = ei;
+        }
+    }
+    cand[r] = c;
+}
+
+// ------------------------------------------------------- gains + matching (a8)
+
+__global__ void k_gains(Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
+                        const uint64_t* __restrict__ obv, const uint64_t* __restrict__ ecount,
+                        unsigned long long* __restrict__ best, int64_t* __restrict__ stats)
+{
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ctr[kCtrCand]) return;
+    Cand c = cand[r];
+    const int64_t rem = (int64_t)obv[c.s] - (int64_t)ecount[c.e_shr];
+    int bi = -1;
+    int64_t bg = 0;
+    for (int i = 0; i < c.nk; ++i) {
+        int64_t add = c.e_gro[i] >= 0 ? (int64_t)ecount[c.e_gro[i]] - (int64_t)obv[c.k[i]] : 0;
+        int64_t g = rem - add;
+        if (g > 0 && (bi < 0 || g > bg || (g == bg && c.k[i] < c.k[bi]))) {
+            bi = i;
+            bg = g;
+        }
+    }
+    cand[r].best = bi;
+    if (bi < 0) return;
+    const unsigned long long key = ((unsigned long long)bg << 24) | (unsigned long long)(0xffffff - c.t);
+    cand[r].gain = bg;
+    cand[r].key = key;
+    atomicMax(&best[c.s], key);
+    atomicMax(&best[c.k[bi]], key);
+    atomicAdd((unsigned long long*)&stats[kStProposals], 1ull);
+}
+
+__global__ void k_accept(const Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
+                         const unsigned long long* __restrict__ best, const obb_qbox* __restrict__ evals,
+                         const uint64_t* __restrict__ ecount, int32_t* __restrict__ assign,
+                         obb_qbox* __restrict__ q, uint64_t* __restrict__ obv, int32_t* __restrict__ size,
+                         int64_t* __restrict__ stats)
+{
+    int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ctr[kCtrCand]) return;
+    const Cand c = cand[r];
+    if (c.best < 0) return;
+    const int32_t k = c.k[c.best];
+    if (best[c.s] != c.key || best[k] != c.key) return;
+    assign[c.t] = k;
+    for (int i = 0; i < 6; ++i) q[c.s].b[i] = evals[c.e_shr].b[i];
+    obv[c.s] = ecount[c.e_shr];
+    const int32_t eg = c.e_gro[c.best];
+    if (eg >= 0) {
+        for (int i = 0; i < 6; ++i) q[k].b[i] = evals[eg].b[i];
+        obv[k] = ecount[eg];
+    }
+    size[c.s] -= 1;
+    size[k] += 1;
+    atomicAdd((unsigned long long*)&stats[kStAccepted], 1ull);
+    atomicAdd((unsigned long long*)&stats[kStGain], (unsigned long long)c.gain);
+}
+
+__global__ void k_sum_points(const uint64_t* __restrict__ pts, const int32_t* __restrict__ d_n,
+                             int64_t* __restrict__ stats)
+{
+    const int32_t n = *d_n;
+    unsigned long long s = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += pts[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd((unsigned long long*)&stats[kStPoints], s);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)&stats[kStEvals], (unsigned long long)n);
+}
+
+// ------------------------------------------------------- refit (a9-a11)
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+struct Comp {
+    float s, c;
+};
+
+// s += x * y with the product error (FMA) and the addition error (TwoSum) kept in c
+__device__ __forceinline__ void comp_fma(Comp& A, float x, float y)
+{
+    float p = __fmul_rn(x, y);
+    float pe = fmaf(x, y, -p);
+    float s, e;
+    two_sum(A.s, p, s, e);
+    A.s = s;
+    A.c = __fadd_rn(A.c, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ Comp comp_merge(Comp a, Comp b)
+{
+    float s, e;
+    two_sum(a.s, b.s, s, e);
+    return Comp{s, __fadd_rn(__fadd_rn(a.c, b.c), e)};
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_moments(const float* __restrict__ V, const int32_t* __restrict__ F,
+                                                const int32_t* __restrict__ members,
+                                                const int32_t* __restrict__ start,
+                                                const LatticeFrame* __restrict__ f, double* __restrict__ mom)
+{
+    const int32_t k = blockIdx.x;
+    const int32_t b0 = start[k], b1 = start[k + 1];
+    const double cx = f->center[0], cy = f->center[1], cz = f->center[2];
+    Comp acc[10];
+    for (int i = 0; i < 10; ++i) acc[i] = Comp{0.f, 0.f};
+    for (int32_t i = b0 + threadIdx.x; i < b1; i += NT) {
+        const int32_t t = members[i];
+        float P[3][3];
+        for (int v = 0; v < 3; ++v) {
+            const float* X = V + 3 * (int64_t)F[3 * t + v];
+            P[v][0] = (float)__dsub_rn((double)X[0], cx);
+            P[v][1] = (float)__dsub_rn((double)X[1], cy);
+            P[v][2] = (float)__dsub_rn((double)X[2], cz);
+        }
+        float e1[3], e2[3];
+        for (int b = 0; b < 3; ++b) {
+            e1[b] = P[1][b] - P[0][b];
+            e2[b] = P[2][b] - P[0][b];
+        }
+        float nx = fmaf(e1[1], e2[2], -e1[2] * e2[1]);
+        float ny = fmaf(e1[2], e2[0], -e1[0] * e2[2]);
+        float nz = fmaf(e1[0], e2[1], -e1[1] * e2[0]);
+        float A = 0.5f * sqrtf(nx * nx + ny * ny + nz * nz);
+        float m[3];
+        for (int b = 0; b < 3; ++b) m[b] = (P[0][b] + P[1][b] + P[2][b]) / 3.0f;
+        comp_fma(acc[0], A, 1.0f);
+        for (int b = 0; b < 3; ++b) comp_fma(acc[1 + b], A, m[b]);
+        const float a12 = A / 12.0f;
+        const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+        for (int qd = 0; qd < 6; ++qd) {
+            const int x = ia[qd], y = ib[qd];
+            float sxy = 9.0f * m[x] * m[y] + P[0][x] * P[0][y] + P[1][x] * P[1][y] + P[2][x] * P[2][y];
+            comp_fma(acc[4 + qd], a12, sxy);
+        }
+    }
+    __shared__ Comp sh[10][NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = 0; i < 10; ++i) {
+        Comp x = acc[i];
+        for (int o = 16; o > 0; o >>= 1) {
+            Comp y{__shfl_xor_sync(0xffffffffu, x.s, o), __shfl_xor_sync(0xffffffffu, x.c, o)};
+            // combine in lane order so every lane holds the same bits
+            x = (lane & o) ? comp_merge(y, x) : comp_merge(x, y);
+        }
+        if (lane == 0) sh[i][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        Comp x = sh[threadIdx.x][0];
+        for (int i = 1; i < NT / 32; ++i) x = comp_merge(x, sh[threadIdx.x][i]);
+        mom[10 * (int64_t)k + threadIdx.x] = (double)x.s + (double)x.c;
+    }
+}
+
+// Cyclic Jacobi on the symmetric 3x3 covariance, FP64; frame rows = eigenvectors
+// sorted by decreasing eigenvalue, rows 0 and 1 with a positive largest-magnitude
+// component, row 2 = row 0 x row 1.
+__device__ void jacobi3(const double c6[6], double R[9])
+{
+    double A[3][3] = {{c6[0], c6[3], c6[4]}, {c6[3], c6[1], c6[5]}, {c6[4], c6[5], c6[2]}};
+    double Vm[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    double fro = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) fro += A[i][j] * A[i][j];
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        double off = 2.0 * (A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2]);
+        if (off <= 1e-30 * fro) break;
+        for (int r = 0; r < 3; ++r) {
+            const int p = r == 2 ? 1 : 0, qq = r == 0 ? 1 : 2;
+            if (A[p][qq] == 0.0) continue;
+            double theta = (A[qq][qq] - A[p][p]) / (2.0 * A[p][qq]);
+            double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            double c = 1.0 / sqrt(t * t + 1.0);
+            double s = t * c;
+            for (int k = 0; k < 3; ++k) {
+                double akp = A[k][p], akq = A[k][qq];
+                A[k][p] = c * akp - s * akq;
+                A[k][qq] = s * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                double apk = A[p][k], aqk = A[qq][k];
+                A[p][k] = c * apk - s * aqk;
+                A[qq][k] = s * apk + c * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {
+                double vkp = Vm[k][p], vkq = Vm[k][qq];
+                Vm[k][p] = c * vkp - s * vkq;
+                Vm[k][qq] = s * vkp + c * vkq;
+            }
+        }
+    }
+    double ev[3] = {A[0][0], A[1][1], A[2][2]};
+    int o[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (ev[o[j]] > ev[o[i]]) {
+                int tmp = o[i];
+                o[i] = o[j];
+                o[j] = tmp;
+            }
+    for (int a = 0; a < 2; ++a) {
+        double row[3] = {Vm[0][o[a]], Vm[1][o[a]], Vm[2][o[a]]};
+        int big = 0;
+        for (int b = 1; b < 3; ++b)
+            if (fabs(row[b]) > fabs(row[big])) big = b;
+        double sg = row[big] < 0.0 ? -1.0 : 1.0;
+        for (int b = 0; b < 3; ++b) R[3 * a + b] = sg * row[b];
+    }
+    R[6] = R[1] * R[5] - R[2] * R[4];
+    R[7] = R[2] * R[3] - R[0] * R[5];
+    R[8] = R[0] * R[4] - R[1] * R[3];
+}
+
+__global__ void k_frames_from_moments(const double* __restrict__ mom, const double* __restrict__ fallback,
+                                      int32_t K, double* __restrict__ out)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const double* m = mom + 10 * (int64_t)k;
+    double* R = out + 9 * (int64_t)k;
+    const double A = m[0];
+    if (!(A > 0.0)) {
+        for (int i = 0; i < 9; ++i) R[i] = fallback ? fallback[9 * (int64_t)k + i] : (i % 4 == 0 ? 1.0 : 0.0);
+        return;
+    }
+    const double mu[3] = {m[1] / A, m[2] / A, m[3] / A};
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    double c6[6];
+    for (int q = 0; q < 6; ++q) c6[q] = m[4 + q] / A - mu[ia[q]] * mu[ib[q]];
+    jacobi3(c6, R);
+}
+
+// n_ab = rint(2^24 ((R_ab h_b) / h_max)), each step correctly rounded
+__global__ void k_normals(const double* __restrict__ frames, int32_t K, const LatticeFrame* __restrict__ f,
+                          obb_qbox* __restrict__ q)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const double hm = f->hmax;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double t = __dmul_rn(frames[9 * (int64_t)k + 3 * a + b], f->h[b]);
+            t = __ddiv_rn(t, hm);
+            t = __dmul_rn(t, 16777216.0);
+            q[k].n[3 * a + b] = (int32_t)rint(t);
+        }
+    q[k].reserved = 0;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_tight(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
+                                              const int32_t* __restrict__ members,
+                                              const int32_t* __restrict__ start, obb_qbox* __restrict__ q)
+{
+    const int32_t k = blockIdx.x;
+    const int32_t b0 = start[k], b1 = start[k + 1];
+    int32_t n[9];
+    for (int i = 0; i < 9; ++i) n[i] = q[k].n[i];
+    int64_t v[6];
+    for (int s = 0; s < 6; ++s) v[s] = (s & 1) ? INT64_MIN : INT64_MAX;
+    for (int32_t i = b0 + threadIdx.x; i < b1; i += NT) {
+        int64_t dmin[3], dmax[3];
+        proj3(U, F, members[i], n, dmin, dmax);
+        for (int a = 0; a < 3; ++a) {
+            v[2 * a] = min(v[2 * a], dmin[a]);
+            v[2 * a + 1] = max(v[2 * a + 1], dmax[a]);
+        }
+    }
+    __shared__ int64_t sh[6][NT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int s = 0; s < 6; ++s) {
+        int64_t x = v[s];
+        for (int o = 16; o > 0; o >>= 1) {
+            int64_t y = (int64_t)__shfl_xor_sync(0xffffffffu, (long long)x, o);
+            x = (s & 1) ? max(x, y) : min(x, y);
+        }
+        if (lane == 0) sh[s][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int s = threadIdx.x;
+        int64_t x = sh[s][0];
+        for (int i = 1; i < NT / 32; ++i) x = (s & 1) ? max(x, sh[s][i]) : min(x, sh[s][i]);
+        q[k].b[s] = x;
+    }
+}
+
+__global__ void k_refit_accept(const double* __restrict__ newframe, const obb_qbox* __restrict__ newq,
+                               const uint64_t* __restrict__ cnt, int32_t K, double* __restrict__ frames,
+                               obb_qbox* __restrict__ q, uint64_t* __restrict__ obv, int64_t* __restrict__ stats)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    if (cnt[k] < obv[k]) {
+        for (int i = 0; i < 9; ++i) frames[9 * (int64_t)k + i] = newframe[9 * (int64_t)k + i];
+        q[k] = newq[k];
+        obv[k] = cnt[k];
+        atomicAdd((unsigned long long*)&stats[kStRefits], 1ull);
+    }
+}
+
+__global__ void k_total(const uint64_t* __restrict__ obv, int32_t K, int64_t* __restrict__ out)
+{
+    unsigned long long s = 0;
+    for (int32_t i = threadIdx.x; i < K; i += blockDim.x) s += obv[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ unsigned long long sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+        *out = (int64_t)t;
+    }
+}
+
+constexpr int kNT = 128;
+
+}  // namespace
+
+// -------------------------------------------------------------- host side
+
+// Per-layer scratch that is not part of the layer's state, allocated with it.
+struct LayerMem {
+    int32_t* iota = nullptr;
+    int32_t* keys_out = nullptr;
+    int32_t* ctr = nullptr;
+    Cand* cand = nullptr;
+    obb_qbox* evals = nullptr;
+    uint64_t* ecount = nullptr;
+    uint64_t* epoints = nullptr;
+    double* mom = nullptr;
+    double* newframe = nullptr;
+    obb_qbox* newq = nullptr;
+    uint64_t* ncount = nullptr;
+    int32_t* dK = nullptr;          // device copy of K
+    int32_t cand_cap = 0, eval_cap = 0;
+    void* cub_tmp = nullptr;
+    size_t cub_bytes = 0;
+    int end_bit = 1;
+    bool members_valid = false;
+};
+
+static LayerMem* mem_of(const obb_layer* L) { return static_cast<LayerMem*>(L->aux); }
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t n, cudaStream_t s)
+{
+    return cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(T) * (n > 0 ? n : 1), s);
+}
+
+obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
+{
+    cudaStream_t s = ctx->stream;
+    LayerMem* M = mem_of(L);
+    OBB_CK(ctx, cudaMemsetAsync(L->d_size, 0, sizeof(int32_t) * L->K, s));
+    k_hist<<<(unsigned)((L->T + 255) / 256), 256, 0, s>>>(L->d_assign, L->T, L->K, L->d_size, ctx->d_err);
+    launch_scan_i32(L->d_size, L->d_start, M->dK, L->K, s);
+    size_t bytes = M->cub_bytes;
+    OBB_CK(ctx, cub::DeviceRadixSort::SortPairs(M->cub_tmp, bytes, L->d_assign, M->keys_out, M->iota,
+                                                 L->d_members, (int)L->T, 0, M->end_bit, s));
+    OBB_CK(ctx, cudaGetLastError());
+    M->members_valid = true;
+    return OBB_OK;
+}
+
+void layer_destroy(obb_layer* L)
+{
+    if (!L) return;
+    cudaStream_t s = L->ctx ? L->ctx->stream : nullptr;
+    LayerMem* M = mem_of(L);
+    void* ptrs[] = {L->d_assign, L->d_parent, L->d_frames, L->d_q, L->d_obv, L->d_size, L->d_start,
+                    L->d_members, L->d_ext, L->d_best, L->d_stats};
+    for (void* p : ptrs)
+        if (p) cudaFreeAsync(p, s);
+    if (M) {
+        void* mp[] = {M->iota, M->keys_out, M->ctr, M->cand, M->evals, M->ecount, M->epoints, M->mom,
+                      M->newframe, M->newq, M->ncount, M->dK, M->cub_tmp};
+        for (void* p : mp)
+            if (p) cudaFreeAsync(p, s);
+        delete M;
+    }
+    delete L;
+}
+
+// Frames (given, or from the covariance), normals, tight bounds, exact OBV.
+static obb_status init_boxes(obb_ctx* ctx, obb_layer* L, const double* d_frames, const double* d_fallback)
+{
+    cudaStream_t s = ctx->stream;
+    LayerMem* M = mem_of(L);
+    const obb_lattice* lat = L->lat;
+    const int K = L->K;
+    if (d_frames) {
+        OBB_CK(ctx, cudaMemcpyAsync(L->d_frames, d_frames, sizeof(double) * 9 * K, cudaMemcpyDeviceToDevice, s));
+    } else {
+        k_moments<kNT><<<K, kNT, 0, s>>>(lat->mesh->d_verts, lat->mesh->d_tris, L->d_members, L->d_start,
+                                         lat->d_frame, M->mom);
+        k_frames_from_moments<<<(K + 127) / 128, 128, 0, s>>>(M->mom, d_fallback, K, L->d_frames);
+    }
+    k_normals<<<(K + 127) / 128, 128, 0, s>>>(L->d_frames, K, lat->d_frame, L->d_q);
+    k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, L->d_q);
+    OBB_CK(ctx, cudaGetLastError());
+    return count_boxes(ctx, lat, L->d_q, M->dK, K, L->d_obv, nullptr);
+}
+
+obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_assign, const int32_t* d_parent,
+                        int32_t K, const double* d_frames, const double* d_fallback, obb_layer** out)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t T = lat->mesh->nt;
+    if (K < 1) return fail(ctx, OBB_ERR_ARG, "K must be >= 1");
+    if (T >= (int64_t(1) << 24)) return fail(ctx, OBB_ERR_RANGE, "at most 2^24 - 1 triangles");
+    if (K > T) return fail(ctx, OBB_ERR_EMPTY_CLUSTER, "more clusters than triangles");
+    obb_layer* L = new obb_layer();
+    LayerMem* M = new LayerMem();
+    L->aux = M;
+    L->ctx = ctx;
+    L->lat = lat;
+    L->K = K;
+    L->T = T;
+    M->cand_cap = 6 * K + 32;
+    M->eval_cap = 4 * M->cand_cap;
+    while ((1 << M->end_bit) < K) ++M->end_bit;
+    cudaError_t e = cudaSuccess;
+#define A_(x)                        \
+    if (e == cudaSuccess) e = (x);
+    A_(dalloc(&L->d_assign, T, s));
+    A_(dalloc(&L->d_parent, K, s));
+    A_(dalloc(&L->d_frames, 9 * (size_t)K, s));
+    A_(dalloc(&L->d_q, K, s));
+    A_(dalloc(&L->d_obv, K, s));
+    A_(dalloc(&L->d_size, K, s));
+    A_(dalloc(&L->d_start, (size_t)K + 1, s));
+    A_(dalloc(&L->d_members, T, s));
+    A_(dalloc(&L->d_ext, K, s));
+    A_(dalloc(&L->d_best, K, s));
+    A_(dalloc(&L->d_stats, kStCount, s));
+    A_(dalloc(&M->iota, T, s));
+    A_(dalloc(&M->keys_out, T, s));
+    A_(dalloc(&M->ctr, kCtrCount, s));
+    A_(dalloc(&M->cand, M->cand_cap, s));
+    A_(dalloc(&M->evals, M->eval_cap, s));
+    A_(dalloc(&M->ecount, M->eval_cap, s));
+    A_(dalloc(&M->epoints, M->eval_cap, s));
+    A_(dalloc(&M->mom, 10 * (size_t)K, s));
+    A_(dalloc(&M->newframe, 9 * (size_t)K, s));
+    A_(dalloc(&M->newq, K, s));
+    A_(dalloc(&M->ncount, K, s));
+    A_(dalloc(&M->dK, 1, s));
+#undef A_
+    if (e == cudaSuccess) {
+        size_t bytes = 0;
+        e = cub::DeviceRadixSort::SortPairs(nullptr, bytes, (int32_t*)nullptr, (int32_t*)nullptr,
+                                            (int32_t*)nullptr, (int32_t*)nullptr, (int)T, 0, M->end_bit, s);
+        M->cub_bytes = bytes;
+        if (e == cudaSuccess) e = cudaMallocAsync(&M->cub_tmp, bytes > 0 ? bytes : 16, s);
+    }
+    if (e != cudaSuccess) {
+        layer_destroy(L);
+        return cuda_fail(ctx, e, "layer allocation");
+    }
+    OBB_CK(ctx, cudaMemcpyAsync(L->d_assign, d_assign, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, s));
+    OBB_CK(ctx, cudaMemcpyAsync(L->d_parent, d_parent, sizeof(int32_t) * K, cudaMemcpyDeviceToDevice, s));
+    OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
+    OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
+    k_iota<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(M->iota, T);
+    obb_status st = set_device_int(ctx, M->dK, K);
+    if (st == OBB_OK) st = rebuild_members(ctx, L);
+    if (st == OBB_OK) {
+        k_check_nonempty<<<(K + 255) / 256, 256, 0, s>>>(L->d_size, K, ctx->d_err);
+        st = check_device_error(ctx);   // assignment range / empty clusters before any box work
+    }
+    if (st == OBB_OK) st = init_boxes(ctx, L, d_frames, d_fallback);
+    if (st == OBB_OK) st = check_device_error(ctx);
+    if (st != OBB_OK) {
+        layer_destroy(L);
+        return st;
+    }
+    *out = L;
+    return OBB_OK;
+}
+
+obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb_step_stats* st)
+{
+    cudaStream_t s = ctx->stream;
+    LayerMem* M = mem_of(L);
+    const obb_lattice* lat = L->lat;
+    const obb_mesh* mesh = lat->mesh;
+    const int K = L->K;
+    const int rounds = (opts && opts->rounds > 0) ? opts->rounds : 16;
+    const bool refit = opts ? opts->refit != 0 : true;
+    OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
+    int64_t* h = reinterpret_cast<int64_t*>(ctx->h_small);
+    int ran = 0;
+    for (int r = 0; r < rounds; ++r) {
+        if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
+        k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, L->d_q, L->d_ext);
+        OBB_CK(ctx, cudaMemsetAsync(M->ctr, 0, sizeof(int32_t) * kCtrCount, s));
+        OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
+        k_candidates<<<(unsigned)((L->T + 127) / 128), 128, 0, s>>>(
+            lat->d_fixed, mesh->d_tris, mesh->d_adj, L->T, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
+            M->cand, M->evals, M->ctr, M->cand_cap, M->eval_cap, ctx->d_err);
+        OBB_TRY(count_boxes(ctx, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->ecount, M->epoints));
+        k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->ctr + kCtrEval, L->d_stats);
+        const unsigned cb = (unsigned)((M->cand_cap + 127) / 128);
+        k_gains<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->ecount, L->d_best, L->d_stats);
+        const int64_t before = (r == 0) ? 0 : h[1];
+        k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, M->evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
+                                    L->d_size, L->d_stats);
+        OBB_CK(ctx, cudaGetLastError());
+        OBB_CK(ctx, cudaMemcpyAsync(h, L->d_stats, sizeof(int64_t) * kStCount, cudaMemcpyDeviceToHost, s));
+        OBB_CK(ctx, cudaStreamSynchronize(s));
+        ++ran;
+        const int64_t moved = h[kStAccepted] - before;
+        if (moved > 0) M->members_valid = false;
+        if (moved == 0) break;
+    }
+    if (refit) {
+        if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
+        k_moments<kNT><<<K, kNT, 0, s>>>(mesh->d_verts, mesh->d_tris, L->d_members, L->d_start, lat->d_frame,
+                                         M->mom);
+        k_frames_from_moments<<<(K + 127) / 128, 128, 0, s>>>(M->mom, L->d_frames, K, M->newframe);
+        k_normals<<<(K + 127) / 128, 128, 0, s>>>(M->newframe, K, lat->d_frame, M->newq);
+        k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, M->newq);
+        OBB_TRY(count_boxes(ctx, lat, M->newq, M->dK, K, M->ncount, M->epoints));
+        k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->dK, L->d_stats);
+        k_refit_accept<<<(K + 127) / 128, 128, 0, s>>>(M->newframe, M->newq, M->ncount, K, L->d_frames, L->d_q,
+                                                       L->d_obv, L->d_stats);
+        OBB_CK(ctx, cudaGetLastError());
+    }
+    if (st) {
+        OBB_CK(ctx, ctx->tmp_d.reserve(sizeof(int64_t), s));
+        k_total<<<1, 1024, 0, s>>>(L->d_obv, K, ctx->tmp_d.as<int64_t>());
+        OBB_CK(ctx, cudaMemcpyAsync(h, L->d_stats, sizeof(int64_t) * kStCount, cudaMemcpyDeviceToHost, s));
+        OBB_CK(ctx, cudaMemcpyAsync(h + kStCount, ctx->tmp_d.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        OBB_TRY(check_device_error(ctx));
+        st->rounds_run = ran;
+        st->refits_accepted = (int32_t)h[kStRefits];
+        st->proposals = h[kStProposals];
+        st->moves = h[kStAccepted];
+        st->gain = h[kStGain];
+        st->box_evals = h[kStEvals];
+        st->points_counted = (uint64_t)h[kStPoints];
+        st->total_obv = (uint64_t)h[kStCount];
+    }
+    return OBB_OK;
+}
+
+}  // namespace obbv

@@ -1,0 +1,233 @@
+// Solid occupancy of the lattice by per-column crossing parity.
+//
+// The paper's outer volume (Eq. 4) needs the solid Omega(X) of Sec. 3; here
+// it is sampled at the N^3 cell-centred lattice points, exactly:
+//   1. AABB of the vertices (ordered-integer atomics, order independent);
+//   2. snap every vertex to fixed point U = rint(((x - lo)/h - 1/2) 2^8);
+//   3. per triangle, per covered column: Simulation-of-Simplicity containment
+//      of the column point in the (y, z) projection, exact int64 crossing
+//      x* = num / den, flip bit i* = ceil(x* / 256) (clamped below at 0,
+//      dropped at >= N) with atomicXor: every crossing toggles one bit;
+//   4. prefix XOR along each row: bit i = parity of crossings with i* <= i.
+// Row layout: row (j, k) at word (k N + j) W, W = 2 ceil(N / 128), bit i of
+// word i >> 6; the scan clears padding bits >= N.
+#include "internal.h"
+
+namespace obbv {
+namespace {
+
+__device__ __forceinline__ uint32_t f2key(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void k_init_aabb(uint32_t* keys)
+{
+    if (threadIdx.x < 3) keys[threadIdx.x] = 0xffffffffu;
+    else if (threadIdx.x < 6) keys[threadIdx.x] = 0u;
+}
+
+__global__ void k_aabb(const float* __restrict__ V, int64_t nv, uint32_t* keys)
+{
+    uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x)
+        for (int b = 0; b < 3; ++b) {
+            uint32_t k = f2key(V[3 * v + b]);
+            mn[b] = min(mn[b], k);
+            mx[b] = max(mx[b], k);
+        }
+    for (int b = 0; b < 3; ++b)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[b] = min(mn[b], __shfl_xor_sync(0xffffffffu, mn[b], o));
+            mx[b] = max(mx[b], __shfl_xor_sync(0xffffffffu, mx[b], o));
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int b = 0; b < 3; ++b) {
+            atomicMin(&keys[b], mn[b]);
+            atomicMax(&keys[3 + b], mx[b]);
+        }
+}
+
+__global__ void k_frame(const uint32_t* keys, int32_t N, LatticeFrame* f, int32_t* err)
+{
+    if (threadIdx.x != 0) return;
+    double hm = 0.0;
+    for (int b = 0; b < 3; ++b) {
+        double lo = (double)key2f(keys[b]);
+        double hi = (double)key2f(keys[3 + b]);
+        double h = __ddiv_rn(__dsub_rn(hi, lo), (double)N);
+        f->lo[b] = lo;
+        f->h[b] = h;
+        if (!(h > 0.0)) atomicOr(err, kErrDegenerate);
+        hm = fmax(hm, h);
+    }
+    f->hmax = hm;
+    for (int b = 0; b < 3; ++b) f->center[b] = __dadd_rn(f->lo[b], __dmul_rn(0.5 * N, f->h[b]));
+    f->N = N;
+    f->W = 2 * ((N + 127) / 128);
+}
+
+__global__ void k_snap(const float* __restrict__ V, int64_t nv, const LatticeFrame* __restrict__ f,
+                       int32_t* __restrict__ U)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * nv) return;
+    int b = (int)(i % 3);
+    double d = __dsub_rn((double)V[i], f->lo[b]);
+    double q = __ddiv_rn(d, f->h[b]);
+    q = __dsub_rn(q, 0.5);
+    q = __dmul_rn(q, 256.0);
+    U[i] = (int32_t)rint(q);
+}
+
+__device__ __forceinline__ int64_t orient_yz(int64_t ay, int64_t az, int64_t by, int64_t bz,
+                                             int64_t py, int64_t pz)
+{
+    return (by - ay) * (pz - az) - (bz - az) * (py - ay);
+}
+
+// sign of orient2d((a, b), p + (eps, eps^2)) for eps -> 0+
+__device__ __forceinline__ int sos_side(int64_t ay, int64_t az, int64_t by, int64_t bz, int64_t py,
+                                        int64_t pz, int64_t* o)
+{
+    *o = orient_yz(ay, az, by, bz, py, pz);
+    if (*o != 0) return *o > 0 ? 1 : -1;
+    if (bz != az) return bz > az ? -1 : 1;
+    if (by != ay) return by > ay ? 1 : -1;
+    return 0;
+}
+
+__device__ __forceinline__ int64_t floordiv_pos(int64_t a, int64_t d)   // d > 0
+{
+    int64_t q = a / d;
+    return (q * d > a) ? q - 1 : q;
+}
+
+__global__ void k_flip(const int32_t* __restrict__ U, const int32_t* __restrict__ F, int64_t nt,
+                       int32_t N, int32_t W, unsigned long long* __restrict__ words)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int32_t* A = U + 3 * (int64_t)F[3 * t];
+    const int32_t* B = U + 3 * (int64_t)F[3 * t + 1];
+    const int32_t* C = U + 3 * (int64_t)F[3 * t + 2];
+    int32_t ay = A[1], az = A[2], by = B[1], bz = B[2], cy = C[1], cz = C[2];
+    int64_t ax = A[0], bx = B[0], cx = C[0];
+    int32_t ymin = min(ay, min(by, cy)), ymax = max(ay, max(by, cy));
+    int32_t zmin = min(az, min(bz, cz)), zmax = max(az, max(bz, cz));
+    // columns with 256 j in [ymin, ymax], 256 k in [zmin, zmax]
+    int32_t j0 = max(-((-ymin) >> kS), 0), j1 = min(ymax >> kS, N - 1);
+    int32_t k0 = max(-((-zmin) >> kS), 0), k1 = min(zmax >> kS, N - 1);
+    for (int32_t k = k0; k <= k1; ++k) {
+        int64_t pz = (int64_t)k << kS;
+        for (int32_t j = j0; j <= j1; ++j) {
+            int64_t py = (int64_t)j << kS;
+            int64_t wa, wb, wc;
+            int sa = sos_side(by, bz, cy, cz, py, pz, &wa);
+            int sb = sos_side(cy, cz, ay, az, py, pz, &wb);
+            int sc = sos_side(ay, az, by, bz, py, pz, &wc);
+            if (sa == 0 || sa != sb || sb != sc) continue;
+            int64_t den = wa + wb + wc;
+            int64_t num = wa * ax + wb * bx + wc * cx;
+            if (den < 0) {
+                den = -den;
+                num = -num;
+            }
+            // first index with 256 i >= num / den
+            int64_t istar = -floordiv_pos(-num, den << kS);
+            if (istar < 0) istar = 0;
+            if (istar >= N) continue;
+            atomicXor(&words[((int64_t)k * N + j) * W + (istar >> 6)], 1ull << (istar & 63));
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t prefix_xor(uint64_t x)
+{
+    x ^= x << 1;
+    x ^= x << 2;
+    x ^= x << 4;
+    x ^= x << 8;
+    x ^= x << 16;
+    x ^= x << 32;
+    return x;
+}
+
+// One lane per 128-bit chunk; a row's G = W / 2 chunks sit on consecutive lanes.
+__global__ void k_row_scan(uint64_t* __restrict__ words, int32_t N, int32_t W)
+{
+    const int G = W >> 1;
+    const int rpw = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lr = lane / G, c = lane - lr * G;
+    const int64_t row = warp * rpw + lr;
+    const bool active = lr < rpw && row < (int64_t)N * N;
+    uint64_t w0 = 0, w1 = 0;
+    uint4* p = reinterpret_cast<uint4*>(words + row * W + 2 * c);
+    if (active) {
+        uint4 v = *p;
+        w0 = ((uint64_t)v.y << 32) | v.x;
+        w1 = ((uint64_t)v.w << 32) | v.z;
+    }
+    int par0 = __popcll(w0) & 1;
+    uint64_t p0 = prefix_xor(w0);
+    uint64_t p1 = prefix_xor(w1) ^ (par0 ? ~0ull : 0ull);
+    int x = (__popcll(w0) + __popcll(w1)) & 1;
+    const int mine = x;
+    for (int off = 1; off < G; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (c >= off) x ^= y;
+    }
+    if (x ^ mine) {
+        p0 = ~p0;
+        p1 = ~p1;
+    }
+    const int base = 128 * c;
+    uint64_t m0 = (base + 64 <= N) ? ~0ull : (base >= N ? 0ull : ((1ull << (N - base)) - 1));
+    uint64_t m1 = (base + 128 <= N) ? ~0ull : (base + 64 >= N ? 0ull : ((1ull << (N - base - 64)) - 1));
+    p0 &= m0;
+    p1 &= m1;
+    if (active) *p = make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), (uint32_t)p1, (uint32_t)(p1 >> 32));
+}
+
+}  // namespace
+
+obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_lattice* lat)
+{
+    cudaStream_t s = ctx->stream;
+    if (N < 1 || N > kMaxN) return fail(ctx, OBB_ERR_RANGE, "lattice size N must be in [1, 2048]");
+    const int32_t W = 2 * ((N + 127) / 128);
+    lat->ctx = ctx;
+    lat->mesh = mesh;
+    lat->n_words = (size_t)N * N * W;
+    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_frame, sizeof(LatticeFrame), s));
+    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_fixed, sizeof(int32_t) * 3 * mesh->nv, s));
+    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words, sizeof(uint64_t) * lat->n_words, s));
+    OBB_CK(ctx, ctx->tmp_a.reserve(64, s));
+    uint32_t* keys = ctx->tmp_a.as<uint32_t>();
+    k_init_aabb<<<1, 32, 0, s>>>(keys);
+    int64_t nb64 = (mesh->nv + 255) / 256;
+    int nb = (int)(nb64 < 4 * ctx->num_sms ? nb64 : 4 * ctx->num_sms);
+    k_aabb<<<max(nb, 1), 256, 0, s>>>(mesh->d_verts, mesh->nv, keys);
+    k_frame<<<1, 32, 0, s>>>(keys, N, lat->d_frame, ctx->d_err);
+    k_snap<<<(unsigned)((3 * mesh->nv + 255) / 256), 256, 0, s>>>(mesh->d_verts, mesh->nv, lat->d_frame,
+                                                                 lat->d_fixed);
+    OBB_CK(ctx, cudaMemsetAsync(lat->d_words, 0, sizeof(uint64_t) * lat->n_words, s));
+    k_flip<<<(unsigned)((mesh->nt + 127) / 128), 128, 0, s>>>(
+        lat->d_fixed, mesh->d_tris, mesh->nt, N, W, reinterpret_cast<unsigned long long*>(lat->d_words));
+    const int G = W / 2, rpw = 32 / G;
+    int64_t warps = ((int64_t)N * N + rpw - 1) / rpw;
+    k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, N, W);
+    OBB_CK(ctx, cudaGetLastError());
+    OBB_CK(ctx, cudaMemcpyAsync(&lat->frame, lat->d_frame, sizeof(LatticeFrame), cudaMemcpyDeviceToHost, s));
+    return check_device_error(ctx);
+}
+
+}  // namespace obbv

@@ -1,0 +1,422 @@
+// Exact outer volume of oriented boxes on the occupancy lattice (Eq. 4).
+//
+// A box is the integer slab set lo_a <= n_a . (256 p) <= hi_a.  Counting:
+//   prep   per box: index-space bounds Lq = ceil(lo / 256), Hq = floor(hi / 256),
+//          a conservative integer AABB from the FP64 corners (+-2), the
+//          number of (j, k) rows of that AABB, float reciprocals of n_a0;
+//   scan   exclusive prefix of ceil(rows / 32) over the boxes (one block);
+//   count  persistent warps; a warp takes 32 rows of one box, one row per
+//          lane: the exact x-interval of the row from three slab constraints
+//          (a float estimate of each quotient corrected by exact int64
+//          products), then popcount of the occupied bits inside the interval
+//          over 128-bit loads.  Outer volume = interval length - occupied
+//          bits; rows or points outside [0, N)^3 are all empty.
+// Counts are integer sums (warp reduction + one 64-bit atomic per warp pass),
+// so the result does not depend on scheduling.
+#include "internal.h"
+
+namespace obbv {
+namespace {
+
+// ---------------------------------------------------------------- quantise
+
+__global__ void k_quantize(const obb_box* __restrict__ boxes, int64_t K, const LatticeFrame* __restrict__ f,
+                           obb_qbox* __restrict__ out, int32_t* err)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const obb_box B = boxes[k];
+    const float* raw = reinterpret_cast<const float*>(&B);
+    bool bad = false;
+    for (int q = 0; q < 12; ++q) bad |= !isfinite(raw[q]);
+    double R[9];
+    for (int b = 0; b < 3; ++b) {
+        R[b] = (double)B.axis0[b];
+        R[3 + b] = (double)B.axis1[b];
+    }
+    R[6] = __dsub_rn(__dmul_rn(R[1], R[5]), __dmul_rn(R[2], R[4]));
+    R[7] = __dsub_rn(__dmul_rn(R[2], R[3]), __dmul_rn(R[0], R[5]));
+    R[8] = __dsub_rn(__dmul_rn(R[0], R[4]), __dmul_rn(R[1], R[3]));
+    const double hm = f->hmax;
+    const double s = __ddiv_rn(4294967296.0, hm);
+    obb_qbox o;
+    o.reserved = 0;
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) {
+            double t = __dmul_rn(R[3 * a + b], f->h[b]);
+            t = __ddiv_rn(t, hm);
+            t = __dmul_rn(t, 16777216.0);
+            o.n[3 * a + b] = (int32_t)rint(t);
+        }
+        double half = (double)B.half[a];
+        bad |= !(half >= 0.0);
+        double m = 0.0;
+        for (int b = 0; b < 3; ++b) {
+            double d = __dsub_rn((double)B.c[b], f->lo[b]);
+            d = __dsub_rn(d, 0.5 * f->h[b]);
+            m = __dadd_rn(m, __dmul_rn(R[3 * a + b], d));
+        }
+        double lo = floor(__dmul_rn(__dsub_rn(m, half), s));
+        double hi = ceil(__dmul_rn(__dadd_rn(m, half), s));
+        if (!(fabs(lo) < 4.0e18 && fabs(hi) < 4.0e18)) bad = true;
+        o.b[2 * a] = bad ? 0 : (int64_t)lo;
+        o.b[2 * a + 1] = bad ? -1 : (int64_t)hi;
+    }
+    if (bad) {
+        atomicOr(err, kErrArg);
+        for (int q = 0; q < 9; ++q) o.n[q] = (q % 4 == 0) ? 1 : 0;
+        for (int a = 0; a < 3; ++a) {
+            o.b[2 * a] = 0;
+            o.b[2 * a + 1] = -1;   // empty
+        }
+    }
+    out[k] = o;
+}
+
+// ------------------------------------------------------------------- prep
+
+__global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __restrict__ d_K, int32_t N,
+                       BoxPrep* __restrict__ prep, int64_t* __restrict__ chunks, int32_t* err)
+{
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= *d_K) return;
+    const obb_qbox q = boxes[k];
+    BoxPrep p;
+    for (int i = 0; i < 9; ++i) p.n[i] = q.n[i];
+    bool empty = false;
+    for (int a = 0; a < 3; ++a) {
+        p.Lq[a] = -((-q.b[2 * a]) >> kS);
+        p.Hq[a] = q.b[2 * a + 1] >> kS;
+        empty |= p.Lq[a] > p.Hq[a];
+        p.rcp[a] = p.n[3 * a] != 0 ? 1.0f / (float)p.n[3 * a] : 0.0f;
+    }
+    p.flags = 0;
+    p.pad = 0;
+    p.rows = 0;
+    p.i0 = 0;
+    p.i1 = -1;
+    p.j0 = p.k0 = 0;
+    p.nj = 0;
+    if (!empty) {
+        double M[9];
+        for (int i = 0; i < 9; ++i) M[i] = (double)p.n[i];
+        double c00 = M[4] * M[8] - M[5] * M[7];
+        double c01 = M[5] * M[6] - M[3] * M[8];
+        double c02 = M[3] * M[7] - M[4] * M[6];
+        double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+        if (det == 0.0) {
+            atomicOr(err, kErrArg);
+            empty = true;
+        } else {
+            double inv[9] = {c00, M[2] * M[7] - M[1] * M[8], M[1] * M[5] - M[2] * M[4],
+                             c01, M[0] * M[8] - M[2] * M[6], M[2] * M[3] - M[0] * M[5],
+                             c02, M[1] * M[6] - M[0] * M[7], M[0] * M[4] - M[1] * M[3]};
+            double id = 1.0 / det;
+            double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+            for (int c = 0; c < 8; ++c) {
+                double b0 = (double)((c & 1) ? p.Hq[0] : p.Lq[0]);
+                double b1 = (double)((c & 2) ? p.Hq[1] : p.Lq[1]);
+                double b2 = (double)((c & 4) ? p.Hq[2] : p.Lq[2]);
+                for (int r = 0; r < 3; ++r) {
+                    double v = (inv[3 * r] * b0 + inv[3 * r + 1] * b1 + inv[3 * r + 2] * b2) * id;
+                    mn[r] = fmin(mn[r], v);
+                    mx[r] = fmax(mx[r], v);
+                }
+            }
+            const double lim = (double)kBoxRange;
+            for (int r = 0; r < 3; ++r)
+                if (!(mn[r] > -lim && mx[r] < lim + N)) {
+                    atomicOr(err, kErrRange);
+                    empty = true;
+                }
+            if (!empty) {
+                const double span_j = mx[1] - mn[1] + 5.0, span_k = mx[2] - mn[2] + 5.0;
+                if (span_j * span_k > 2147483647.0) {
+                    atomicOr(err, kErrRange);
+                    empty = true;
+                }
+            }
+            if (!empty) {
+                p.i0 = (int32_t)floor(mn[0]) - 2;
+                p.i1 = (int32_t)ceil(mx[0]) + 2;
+                p.j0 = (int32_t)floor(mn[1]) - 2;
+                int32_t j1 = (int32_t)ceil(mx[1]) + 2;
+                p.k0 = (int32_t)floor(mn[2]) - 2;
+                int32_t k1 = (int32_t)ceil(mx[2]) + 2;
+                p.nj = j1 - p.j0 + 1;
+                p.rows = (uint64_t)p.nj * (uint64_t)(k1 - p.k0 + 1);
+            }
+        }
+    }
+    prep[k] = p;
+    chunks[k] = (int64_t)((p.rows + kRowsPerChunk - 1) / kRowsPerChunk);
+}
+
+// ------------------------------------------------------------------- scan
+
+// Exclusive scan of n = *d_n int32 values (n <= cap) into out[0..n]; one block.
+__global__ void k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                           const int32_t* __restrict__ d_n)
+{
+    __shared__ int32_t part[1024];
+    const int32_t n = *d_n;
+    const int T = blockDim.x;
+    const int32_t per = (n + T - 1) / T;
+    const int32_t b0 = threadIdx.x * per;
+    const int32_t b1 = min(n, b0 + per);
+    int32_t s = 0;
+    for (int32_t i = b0; i < b1; ++i) s += in[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = part[threadIdx.x] - s;
+    for (int32_t i = b0; i < b1; ++i) {
+        out[i] = run;
+        run += in[i];
+    }
+    if (threadIdx.x == T - 1) out[n] = part[T - 1];
+}
+
+// Exclusive scan of n = *d_n int64 values into out[0..n]; one block.
+__global__ void k_scan_i64(const int64_t* __restrict__ in, int64_t* __restrict__ out,
+                           const int32_t* __restrict__ d_n)
+{
+    __shared__ int64_t part[1024];
+    const int32_t n = *d_n;
+    const int T = blockDim.x;
+    const int32_t per = (n + T - 1) / T;
+    const int32_t b0 = threadIdx.x * per;
+    const int32_t b1 = min(n, b0 + per);
+    int64_t s = 0;
+    for (int32_t i = b0; i < b1; ++i) s += in[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        int64_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = part[threadIdx.x] - s;
+    for (int32_t i = b0; i < b1; ++i) {
+        out[i] = run;
+        run += in[i];
+    }
+    if (threadIdx.x == T - 1) out[n] = part[T - 1];
+}
+
+// ------------------------------------------------------------------ count
+
+// Intersect [lo, hi] with { i : L <= d i + c <= H } (d != 0 case handled by caller).
+__device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64_t L, int64_t H,
+                                          int32_t& lo, int32_t& hi)
+{
+    if (d == 0) {
+        if (c < L || c > H) hi = lo - 1;
+        return;
+    }
+    int64_t A, B;
+    int64_t dd;
+    float r;
+    if (d > 0) {
+        A = L - c;
+        B = H - c;
+        dd = d;
+        r = rcp;
+    } else {
+        A = c - H;
+        B = c - L;
+        dd = -(int64_t)d;
+        r = -rcp;
+    }
+    // g = max(ceil(A / dd), lo), capped at hi + 1
+    float ea = __ll2float_rn(A) * r;
+    float fl = fminf(fmaxf(ceilf(ea), (float)lo), (float)hi + 1.0f);
+    int32_t g = (int32_t)fl;
+    while (g > lo && (int64_t)(g - 1) * dd >= A) --g;
+    while (g <= hi && (int64_t)g * dd < A) ++g;
+    // u = min(floor(B / dd), hi), floored at lo - 1
+    float eb = __ll2float_rn(B) * r;
+    float fu = fminf(fmaxf(floorf(eb), (float)lo - 1.0f), (float)hi);
+    int32_t u = (int32_t)fu;
+    while (u < hi && (int64_t)(u + 1) * dd <= B) ++u;
+    while (u >= lo && (int64_t)u * dd > B) --u;
+    lo = g;
+    hi = u;
+}
+
+__device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
+{
+    uint32_t cnt = 0;
+    const int32_t q0 = a >> 7, q1 = e >> 7;
+    for (int32_t q = q0; q <= q1; ++q) {
+        uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + q);
+        uint64_t w0 = ((uint64_t)v.y << 32) | v.x;
+        uint64_t w1 = ((uint64_t)v.w << 32) | v.z;
+        const int32_t base = q << 7;
+        int32_t l0 = max(a - base, 0), h0 = min(e - base, 63);
+        if (l0 <= h0) cnt += __popcll(w0 & ((~0ull << l0) & (~0ull >> (63 - h0))));
+        int32_t l1 = max(a - base - 64, 0), h1 = min(e - base - 64, 63);
+        if (l1 <= h1) cnt += __popcll(w1 & ((~0ull << l1) & (~0ull >> (63 - h1))));
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
+                                               const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ d_K,
+                                               const uint64_t* __restrict__ words, int32_t N, int32_t W,
+                                               unsigned long long* __restrict__ counts,
+                                               unsigned long long* __restrict__ points)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t K = *d_K;
+    const int64_t total = off[K];
+    for (int64_t c = warp; c < total; c += nwarps) {
+        // box b with off[b] <= c < off[b + 1]
+        int32_t lo = 0, hi = K - 1;
+        while (lo < hi) {
+            int32_t mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t b = lo;
+        const BoxPrep& p = prep[b];
+        const uint32_t r = (uint32_t)(c - off[b]) * kRowsPerChunk + lane;
+        uint32_t empty = 0, inbox = 0;
+        if (r < p.rows) {
+            const uint32_t nj = (uint32_t)p.nj;
+            const int32_t rk = (int32_t)(r / nj);
+            const int32_t j = p.j0 + (int32_t)(r - (uint32_t)rk * nj);
+            const int32_t k = p.k0 + rk;
+            int32_t i0 = p.i0, i1 = p.i1;
+            for (int a = 0; a < 3 && i0 <= i1; ++a) {
+                int64_t cc = (int64_t)p.n[3 * a + 1] * j + (int64_t)p.n[3 * a + 2] * k;
+                clip_slab(p.n[3 * a], p.rcp[a], cc, p.Lq[a], p.Hq[a], i0, i1);
+            }
+            if (i0 <= i1) {
+                inbox = (uint32_t)(i1 - i0 + 1);
+                uint32_t occ = 0;
+                if (j >= 0 && j < N && k >= 0 && k < N) {
+                    int32_t a = max(i0, 0), e = min(i1, N - 1);
+                    if (a <= e) occ = popc_range(words + ((int64_t)k * N + j) * W, a, e);
+                }
+                empty = inbox - occ;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            empty += __shfl_xor_sync(0xffffffffu, empty, o);
+            inbox += __shfl_xor_sync(0xffffffffu, inbox, o);
+        }
+        if (lane == 0) {
+            if (empty) atomicAdd(&counts[b], (unsigned long long)empty);
+            if (points && inbox) atomicAdd(&points[b], (unsigned long long)inbox);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- report
+
+__global__ void k_report(const LatticeFrame* __restrict__ f, const double* __restrict__ frames,
+                         const obb_qbox* __restrict__ q, int32_t K, obb_box* __restrict__ out)
+{
+    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const double* R = frames + 9 * (int64_t)k;
+    const double s = 4294967296.0 / f->hmax;
+    double c[3] = {0, 0, 0};
+    obb_box o;
+    for (int a = 0; a < 3; ++a) {
+        double base = 0.0;
+        for (int b = 0; b < 3; ++b) base += R[3 * a + b] * (f->lo[b] + 0.5 * f->h[b]);
+        double lo = (double)q[k].b[2 * a] / s + base;
+        double hi = (double)q[k].b[2 * a + 1] / s + base;
+        double mid = 0.5 * (lo + hi);
+        for (int b = 0; b < 3; ++b) c[b] += R[3 * a + b] * mid;
+        o.half[a] = (float)(0.5 * (hi - lo));
+    }
+    for (int b = 0; b < 3; ++b) {
+        o.c[b] = (float)c[b];
+        o.axis0[b] = (float)R[b];
+        o.axis1[b] = (float)R[3 + b];
+    }
+    out[k] = o;
+}
+
+__global__ void k_set_i32(int32_t* dst, int32_t v)
+{
+    *dst = v;
+}
+
+}  // namespace
+
+obb_status set_device_int(obb_ctx* ctx, int32_t* d_dst, int32_t value)
+{
+    k_set_i32<<<1, 1, 0, ctx->stream>>>(d_dst, value);
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
+
+void launch_scan_i32(const int32_t* in, int32_t* out, const int32_t* d_n, int32_t n_cap, cudaStream_t s)
+{
+    (void)n_cap;
+    k_scan_i32<<<1, 1024, 0, s>>>(in, out, d_n);
+}
+
+void launch_box_report(const obb_lattice* lat, const double* d_frames, const obb_qbox* d_q, int32_t K,
+                       obb_box* d_out, cudaStream_t s)
+{
+    if (K > 0) k_report<<<(K + 127) / 128, 128, 0, s>>>(lat->d_frame, d_frames, d_q, K, d_out);
+}
+
+obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d_boxes, int64_t K,
+                          obb_qbox* d_out)
+{
+    if (K <= 0) return OBB_OK;
+    k_quantize<<<(unsigned)((K + 127) / 128), 128, 0, ctx->stream>>>(d_boxes, K, lat->d_frame, d_out,
+                                                                    ctx->d_err);
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
+
+static int count_grid(obb_ctx* ctx)
+{
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, 256, 0) != cudaSuccess || nb < 1) nb = 1;
+        blocks_per_sm = nb;
+    }
+    return blocks_per_sm * ctx->num_sms;
+}
+
+obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes, const int32_t* d_K,
+                       int64_t K_cap, uint64_t* d_counts, uint64_t* d_points)
+{
+    cudaStream_t s = ctx->stream;
+    if (K_cap <= 0) return OBB_OK;
+    if (K_cap > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_RANGE, "too many boxes in one call");
+    OBB_CK(ctx, ctx->prep.reserve(sizeof(BoxPrep) * K_cap, s));
+    OBB_CK(ctx, ctx->chunk_off.reserve(sizeof(int64_t) * (2 * K_cap + 1), s));
+    BoxPrep* prep = ctx->prep.as<BoxPrep>();
+    int64_t* chunks = ctx->chunk_off.as<int64_t>();
+    int64_t* off = chunks + K_cap;
+    OBB_CK(ctx, cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * K_cap, s));
+    if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K_cap, s));
+    k_prep<<<(unsigned)((K_cap + 127) / 128), 128, 0, s>>>(d_boxes, d_K, lat->frame.N, prep, chunks, ctx->d_err);
+    k_scan_i64<<<1, 1024, 0, s>>>(chunks, off, d_K);
+    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, lat->d_words, lat->frame.N, lat->frame.W,
+                                            reinterpret_cast<unsigned long long*>(d_counts),
+                                            reinterpret_cast<unsigned long long*>(d_points));
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
+
+}  // namespace obbv

@@ -1,0 +1,468 @@
+// Host runtime and the C ABI of include/obbvar.h: contexts, mesh validation
+// and adjacency, handle lifetimes, host<->device marshalling, error mapping.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace obbv {
+
+cudaError_t DevBuf::reserve(size_t n, cudaStream_t s)
+{
+    if (n <= bytes && p) return cudaSuccess;
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+    size_t want = n < 256 ? 256 : n + n / 4;
+    cudaError_t e = cudaMallocAsync(&p, want, s);
+    if (e == cudaSuccess) bytes = want;
+    return e;
+}
+
+void DevBuf::release(cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    bytes = 0;
+}
+
+obb_status fail(obb_ctx* ctx, obb_status code, const std::string& msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+obb_status cuda_fail(obb_ctx* ctx, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, OBB_ERR_OOM, m);
+    return fail(ctx, OBB_ERR_CUDA, m);
+}
+
+obb_status check_device_error(obb_ctx* ctx)
+{
+    OBB_CK(ctx, cudaMemcpyAsync(ctx->h_small, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    OBB_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const int32_t w = ctx->h_small[0];
+    if (w == 0) return OBB_OK;
+    OBB_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream));
+    if (w & kErrArg) return fail(ctx, OBB_ERR_ARG, "invalid box or assignment (non-finite, negative extent, singular or out of range)");
+    if (w & kErrEmpty) return fail(ctx, OBB_ERR_EMPTY_CLUSTER, "a cluster is empty or too small to split");
+    if (w & kErrDegenerate) return fail(ctx, OBB_ERR_RANGE, "degenerate lattice: the vertex AABB has zero extent on an axis");
+    if (w & kErrRange) return fail(ctx, OBB_ERR_RANGE, "a box's lattice bounding box exceeds the supported range");
+    return fail(ctx, OBB_ERR_STATE, "internal capacity exceeded");
+}
+
+}  // namespace obbv
+
+using namespace obbv;
+
+namespace {
+
+struct HostTmp {
+    obb_ctx* ctx;
+    void* p = nullptr;
+    explicit HostTmp(obb_ctx* c) : ctx(c) {}
+    ~HostTmp()
+    {
+        if (p) cudaFreeAsync(p, ctx->stream);
+    }
+};
+
+// Device copy of a caller array (or the caller's device pointer itself).
+template <class T>
+obb_status to_device(obb_ctx* ctx, const T* src, size_t n, int on_device, HostTmp& hold, const T** out)
+{
+    if (on_device || n == 0) {
+        *out = src;
+        return OBB_OK;
+    }
+    OBB_CK(ctx, cudaMallocAsync(&hold.p, sizeof(T) * n, ctx->stream));
+    OBB_CK(ctx, cudaMemcpyAsync(hold.p, src, sizeof(T) * n, cudaMemcpyHostToDevice, ctx->stream));
+    *out = static_cast<const T*>(hold.p);
+    return OBB_OK;
+}
+
+// Output buffer: the caller's device array, or a temporary copied back after.
+template <class T>
+obb_status out_device(obb_ctx* ctx, T* dst, size_t n, int on_device, HostTmp& hold, T** out)
+{
+    if (!dst) {
+        *out = nullptr;
+        return OBB_OK;
+    }
+    if (on_device) {
+        *out = dst;
+        return OBB_OK;
+    }
+    OBB_CK(ctx, cudaMallocAsync(&hold.p, sizeof(T) * (n > 0 ? n : 1), ctx->stream));
+    *out = static_cast<T*>(hold.p);
+    return OBB_OK;
+}
+
+template <class T>
+obb_status copy_back(obb_ctx* ctx, T* host, const T* dev, size_t n, int on_device)
+{
+    if (!host || on_device || n == 0) return OBB_OK;
+    OBB_CK(ctx, cudaMemcpyAsync(host, dev, sizeof(T) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    return OBB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+obb_status obb_create(obb_ctx** out, int32_t device, void* stream)
+{
+    if (!out) return OBB_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return OBB_ERR_CUDA;
+    if (device < 0 || device >= n) return OBB_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return OBB_ERR_CUDA;
+    obb_ctx* c = new (std::nothrow) obb_ctx();
+    if (!c) return OBB_ERR_OOM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&c->d_err, sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost(&c->h_small, 64 * sizeof(int64_t)) != cudaSuccess ||
+        cudaMemset(c->d_err, 0, sizeof(int32_t)) != cudaSuccess) {
+        obb_destroy(c);
+        return OBB_ERR_CUDA;
+    }
+    *out = c;
+    return OBB_OK;
+}
+
+obb_status obb_set_stream(obb_ctx* ctx, void* stream)
+{
+    if (!ctx) return OBB_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return OBB_OK;
+}
+
+obb_status obb_synchronize(obb_ctx* ctx)
+{
+    if (!ctx) return OBB_ERR_ARG;
+    return check_device_error(ctx);
+}
+
+void obb_destroy(obb_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    DevBuf* bufs[] = {&ctx->prep, &ctx->chunk_off, &ctx->qscratch, &ctx->cscratch, &ctx->pscratch, &ctx->kdev,
+                      &ctx->tmp_a, &ctx->tmp_b, &ctx->tmp_c, &ctx->tmp_d, &ctx->cub_tmp};
+    for (DevBuf* b : bufs) b->release(ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    delete ctx;
+}
+
+const char* obb_last_error(const obb_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+obb_status obb_mesh_create(obb_ctx* ctx, const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                           obb_mesh** out)
+{
+    if (!ctx || !out || !verts || !tris) return fail(ctx, OBB_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (n_verts < 3 || n_tris < 4) return fail(ctx, OBB_ERR_ARG, "a closed mesh needs >= 3 vertices and >= 4 triangles");
+    if (n_tris >= (int64_t(1) << 30) || n_verts >= (int64_t(1) << 31))
+        return fail(ctx, OBB_ERR_RANGE, "mesh too large");
+    for (int64_t i = 0; i < 3 * n_verts; ++i)
+        if (!std::isfinite(verts[i])) return fail(ctx, OBB_ERR_ARG, "non-finite vertex coordinate");
+    // undirected edges (key, triangle, edge slot), sorted: every key must appear exactly twice
+    std::vector<uint64_t> key(3 * n_tris);
+    std::vector<int64_t> who(3 * n_tris);
+    for (int64_t t = 0; t < n_tris; ++t)
+        for (int e = 0; e < 3; ++e) {
+            int64_t a = tris[3 * t + e], b = tris[3 * t + (e + 1) % 3];
+            if (a < 0 || a >= n_verts || b < 0 || b >= n_verts)
+                return fail(ctx, OBB_ERR_ARG, "triangle index out of range");
+            if (a == b) return fail(ctx, OBB_ERR_NOT_WATERTIGHT, "triangle with a repeated vertex");
+            uint64_t lo = (uint64_t)std::min(a, b), hi = (uint64_t)std::max(a, b);
+            key[3 * t + e] = (lo << 32) | hi;
+            who[3 * t + e] = 3 * t + e;
+        }
+    std::vector<int64_t> order(3 * n_tris);
+    for (int64_t i = 0; i < 3 * n_tris; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        return key[x] != key[y] ? key[x] < key[y] : x < y;
+    });
+    std::vector<int32_t> adj(3 * n_tris, -1);
+    for (int64_t i = 0; i < 3 * n_tris;) {
+        int64_t j = i;
+        while (j < 3 * n_tris && key[order[j]] == key[order[i]]) ++j;
+        if (j - i != 2)
+            return fail(ctx, OBB_ERR_NOT_WATERTIGHT,
+                        "edge (" + std::to_string(key[order[i]] >> 32) + ", " +
+                            std::to_string(key[order[i]] & 0xffffffffu) + ") is shared by " + std::to_string(j - i) +
+                            " triangles (need exactly 2)");
+        int64_t x = who[order[i]], y = who[order[i + 1]];
+        adj[x] = (int32_t)(y / 3);
+        adj[y] = (int32_t)(x / 3);
+        i = j;
+    }
+    obb_mesh* m = new (std::nothrow) obb_mesh();
+    if (!m) return fail(ctx, OBB_ERR_OOM, "host allocation");
+    m->ctx = ctx;
+    m->nv = n_verts;
+    m->nt = n_tris;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMallocAsync((void**)&m->d_verts, sizeof(float) * 3 * n_verts, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_tris, sizeof(int32_t) * 3 * n_tris, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_adj, sizeof(int32_t) * 3 * n_tris, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_verts, verts, sizeof(float) * 3 * n_verts, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_tris, tris, sizeof(int32_t) * 3 * n_tris, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_adj, adj.data(), sizeof(int32_t) * 3 * n_tris, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // adj is a local vector
+    if (e != cudaSuccess) {
+        obb_mesh_free(m);
+        return cuda_fail(ctx, e, "mesh upload");
+    }
+    *out = m;
+    return OBB_OK;
+}
+
+void obb_mesh_free(obb_mesh* m)
+{
+    if (!m) return;
+    cudaStream_t s = m->ctx ? m->ctx->stream : nullptr;
+    if (m->d_verts) cudaFreeAsync(m->d_verts, s);
+    if (m->d_tris) cudaFreeAsync(m->d_tris, s);
+    if (m->d_adj) cudaFreeAsync(m->d_adj, s);
+    delete m;
+}
+
+obb_status obb_build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_lattice** out)
+{
+    if (!ctx || !mesh || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (mesh->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "mesh belongs to another context");
+    *out = nullptr;
+    obb_lattice* lat = new (std::nothrow) obb_lattice();
+    if (!lat) return fail(ctx, OBB_ERR_OOM, "host allocation");
+    obb_status st = build_occupancy(ctx, mesh, N, lat);
+    if (st != OBB_OK) {
+        obb_lattice_free(lat);
+        return st;
+    }
+    *out = lat;
+    return OBB_OK;
+}
+
+obb_status obb_lattice_desc(const obb_lattice* lat, double lo[3], double h[3], int32_t* N, int64_t* row_words,
+                            const uint64_t** d_words, const int32_t** d_fixed)
+{
+    if (!lat) return OBB_ERR_ARG;
+    for (int b = 0; b < 3; ++b) {
+        if (lo) lo[b] = lat->frame.lo[b];
+        if (h) h[b] = lat->frame.h[b];
+    }
+    if (N) *N = lat->frame.N;
+    if (row_words) *row_words = lat->frame.W;
+    if (d_words) *d_words = lat->d_words;
+    if (d_fixed) *d_fixed = lat->d_fixed;
+    return OBB_OK;
+}
+
+void obb_lattice_free(obb_lattice* lat)
+{
+    if (!lat) return;
+    cudaStream_t s = lat->ctx ? lat->ctx->stream : nullptr;
+    if (lat->d_frame) cudaFreeAsync(lat->d_frame, s);
+    if (lat->d_fixed) cudaFreeAsync(lat->d_fixed, s);
+    if (lat->d_words) cudaFreeAsync(lat->d_words, s);
+    delete lat;
+}
+
+obb_status obb_quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* boxes, int64_t K, obb_qbox* out,
+                              int32_t on_device)
+{
+    if (!ctx || !lat || (K > 0 && (!boxes || !out))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (K < 0) return fail(ctx, OBB_ERR_ARG, "negative K");
+    if (K == 0) return OBB_OK;
+    HostTmp hb(ctx), hq(ctx);
+    const obb_box* db;
+    obb_qbox* dq;
+    OBB_TRY(to_device(ctx, boxes, (size_t)K, on_device, hb, &db));
+    OBB_TRY(out_device(ctx, out, (size_t)K, on_device, hq, &dq));
+    OBB_TRY(quantize_boxes(ctx, lat, db, K, dq));
+    OBB_TRY(copy_back(ctx, out, dq, (size_t)K, on_device));
+    if (!on_device) return check_device_error(ctx);
+    return OBB_OK;
+}
+
+static obb_status outer_volume_impl(obb_ctx* ctx, const obb_lattice* lat, const obb_box* boxes,
+                                    const obb_qbox* qboxes, int64_t K, uint64_t* counts, uint64_t* points,
+                                    int32_t on_device)
+{
+    if (!ctx || !lat || (K > 0 && (!counts || !(boxes || qboxes)))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (K < 0 || K > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_ARG, "K out of range");
+    if (K == 0) return OBB_OK;
+    HostTmp hb(ctx), hc(ctx), hp(ctx);
+    const obb_qbox* dq = nullptr;
+    if (boxes) {
+        const obb_box* db;
+        OBB_TRY(to_device(ctx, boxes, (size_t)K, on_device, hb, &db));
+        OBB_CK(ctx, ctx->qscratch.reserve(sizeof(obb_qbox) * K, ctx->stream));
+        OBB_TRY(quantize_boxes(ctx, lat, db, K, ctx->qscratch.as<obb_qbox>()));
+        dq = ctx->qscratch.as<obb_qbox>();
+    } else {
+        OBB_TRY(to_device(ctx, qboxes, (size_t)K, on_device, hb, &dq));
+    }
+    uint64_t *dc, *dp;
+    OBB_TRY(out_device(ctx, counts, (size_t)K, on_device, hc, &dc));
+    OBB_TRY(out_device(ctx, points, (size_t)K, on_device, hp, &dp));
+    OBB_CK(ctx, ctx->kdev.reserve(sizeof(int32_t), ctx->stream));
+    OBB_TRY(set_device_int(ctx, ctx->kdev.as<int32_t>(), (int32_t)K));
+    OBB_TRY(count_boxes(ctx, lat, dq, ctx->kdev.as<int32_t>(), K, dc, dp));
+    OBB_TRY(copy_back(ctx, counts, dc, (size_t)K, on_device));
+    OBB_TRY(copy_back(ctx, points, dp, (size_t)K, on_device));
+    if (!on_device) return check_device_error(ctx);
+    return OBB_OK;
+}
+
+obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* boxes, int64_t K,
+                              uint64_t* counts, uint64_t* points, int32_t on_device)
+{
+    return outer_volume_impl(ctx, lat, nullptr, boxes, K, counts, points, on_device);
+}
+
+obb_status obb_outer_volume(obb_ctx* ctx, const obb_lattice* lat, const obb_box* boxes, int64_t K, uint64_t* counts,
+                            uint64_t* points, int32_t on_device)
+{
+    if (!boxes && K > 0) return fail(ctx, OBB_ERR_ARG, "null boxes");
+    return outer_volume_impl(ctx, lat, boxes, nullptr, K, counts, points, on_device);
+}
+
+obb_status obb_layer_init(obb_ctx* ctx, const obb_lattice* lat, const int32_t* assign, const int32_t* parent,
+                          int32_t K, const double* frames, int32_t on_device, obb_layer** out)
+{
+    if (!ctx || !lat || !assign || !parent || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (K < 1) return fail(ctx, OBB_ERR_ARG, "K must be >= 1");
+    const int64_t T = lat->mesh->nt;
+    HostTmp ha(ctx), hp(ctx), hf(ctx);
+    const int32_t *da, *dp;
+    const double* df = nullptr;
+    OBB_TRY(to_device(ctx, assign, (size_t)T, on_device, ha, &da));
+    OBB_TRY(to_device(ctx, parent, (size_t)K, on_device, hp, &dp));
+    if (frames) OBB_TRY(to_device(ctx, frames, (size_t)9 * K, on_device, hf, &df));
+    if (!on_device) {
+        // parents must name clusters of the layer above; only their equality matters here
+        for (int32_t k = 0; k < K; ++k)
+            if (parent[k] < 0) return fail(ctx, OBB_ERR_ARG, "negative parent id");
+    }
+    return layer_create(ctx, lat, da, dp, K, df, nullptr, out);
+}
+
+obb_status obb_lloyd_step(obb_ctx* ctx, obb_layer* layer, const obb_step_opts* opts, obb_step_stats* stats)
+{
+    if (!ctx || !layer) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (layer->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
+    return lloyd_step(ctx, layer, opts, stats);
+}
+
+obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* L, int32_t* assign, double* frames, obb_qbox* qboxes,
+                          obb_box* boxes, uint64_t* obv, int32_t on_device)
+{
+    if (!ctx || !L) return fail(ctx, OBB_ERR_ARG, "null argument");
+    cudaStream_t s = ctx->stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (assign) OBB_CK(ctx, cudaMemcpyAsync(assign, L->d_assign, sizeof(int32_t) * L->T, kind, s));
+    if (frames) OBB_CK(ctx, cudaMemcpyAsync(frames, L->d_frames, sizeof(double) * 9 * L->K, kind, s));
+    if (qboxes) OBB_CK(ctx, cudaMemcpyAsync(qboxes, L->d_q, sizeof(obb_qbox) * L->K, kind, s));
+    if (obv) OBB_CK(ctx, cudaMemcpyAsync(obv, L->d_obv, sizeof(uint64_t) * L->K, kind, s));
+    if (boxes) {
+        HostTmp hb(ctx);
+        obb_box* db;
+        OBB_TRY(out_device(ctx, boxes, (size_t)L->K, on_device, hb, &db));
+        launch_box_report(L->lat, L->d_frames, L->d_q, L->K, db, s);
+        OBB_CK(ctx, cudaGetLastError());
+        OBB_TRY(copy_back(ctx, boxes, db, (size_t)L->K, on_device));
+        if (!on_device) return check_device_error(ctx);
+    }
+    if (!on_device) return check_device_error(ctx);
+    return OBB_OK;
+}
+
+int32_t obb_layer_clusters(const obb_layer* L) { return L ? L->K : 0; }
+
+void obb_layer_free(obb_layer* L) { layer_destroy(L); }
+
+obb_status obb_layer_split(obb_ctx* ctx, const obb_layer* L, int32_t* child, int32_t on_device)
+{
+    if (!ctx || !L || !child) return fail(ctx, OBB_ERR_ARG, "null argument");
+    HostTmp hc(ctx);
+    int32_t* dc;
+    OBB_TRY(out_device(ctx, child, (size_t)L->T, on_device, hc, &dc));
+    OBB_TRY(split_layer(ctx, L, dc));
+    OBB_TRY(copy_back(ctx, child, dc, (size_t)L->T, on_device));
+    return check_device_error(ctx);
+}
+
+obb_status obb_build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts* opts, obb_tree** out)
+{
+    if (!ctx || !lat || !opts || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
+    *out = nullptr;
+    obb_tree* t = new (std::nothrow) obb_tree();
+    if (!t) return fail(ctx, OBB_ERR_OOM, "host allocation");
+    obb_status st = build_tree(ctx, lat, opts, t);
+    if (st == OBB_OK) st = check_device_error(ctx);
+    if (st != OBB_OK) {
+        obb_tree_free(t);
+        return st;
+    }
+    *out = t;
+    return OBB_OK;
+}
+
+obb_status obb_tree_read(obb_ctx* ctx, const obb_tree* tree, int32_t level, int32_t* assign, double* frames,
+                         obb_qbox* qboxes, obb_box* boxes, uint64_t* obv)
+{
+    if (!ctx || !tree) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (level < 0 || level >= (int32_t)tree->layers.size()) return fail(ctx, OBB_ERR_ARG, "level out of range");
+    return obb_layer_read(ctx, tree->layers[level], assign, frames, qboxes, boxes, obv, 0);
+}
+
+int32_t obb_tree_depth(const obb_tree* tree) { return tree ? (int32_t)tree->layers.size() - 1 : -1; }
+
+obb_status obb_tree_score(obb_ctx* ctx, const obb_tree* tree, double* points, double* volume)
+{
+    if (!ctx || !tree) return fail(ctx, OBB_ERR_ARG, "null argument");
+    const int depth = (int)tree->layers.size() - 1;
+    double acc = 0.0;
+    for (int L = 0; L <= depth; ++L) {
+        const obb_layer* ly = tree->layers[L];
+        std::vector<uint64_t> o(ly->K);
+        OBB_CK(ctx, cudaMemcpyAsync(o.data(), ly->d_obv, sizeof(uint64_t) * ly->K, cudaMemcpyDeviceToHost, ctx->stream));
+        OBB_TRY(check_device_error(ctx));
+        double sum = 0.0;
+        for (uint64_t v : o) sum += (double)v;
+        acc += (double)(depth - L + 1) * sum;
+    }
+    if (points) *points = acc;
+    if (volume) {
+        const LatticeFrame& f = tree->lat->frame;
+        *volume = acc * f.h[0] * f.h[1] * f.h[2];
+    }
+    return OBB_OK;
+}
+
+void obb_tree_free(obb_tree* tree)
+{
+    if (!tree) return;
+    for (auto it = tree->layers.rbegin(); it != tree->layers.rend(); ++it) layer_destroy(*it);
+    delete tree;
+}
+
+}  // extern "C"
