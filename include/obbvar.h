@@ -99,6 +99,25 @@ obb_status obb_synchronize(obb_ctx* ctx);
 void obb_destroy(obb_ctx* ctx);
 const char* obb_last_error(const obb_ctx* ctx);
 
+/* Instrumentation.  `launches` counts every kernel this context has enqueued
+ * (library kernels and the radix-sort kernels compiled into the library).
+ * With profiling enabled, each launch of the outer-volume counting kernel is
+ * bracketed by CUDA events on the context stream and the kernel adds up its
+ * algorithmic traffic: 16 bytes per 128-bit occupancy chunk that a box row's
+ * x-interval touches inside the lattice, the lattice points counted and the
+ * rows visited.  obb_profile_enable resets the totals; obb_profile_read
+ * synchronises and reports them. */
+typedef struct {
+    int64_t launches;        /* kernels enqueued by the context since creation */
+    int64_t count_launches;  /* counting-kernel launches since profiling was enabled */
+    double count_ms;         /* their summed duration (CUDA events) */
+    double count_bytes;      /* their summed algorithmic bytes */
+    double count_points;     /* lattice points they counted */
+    double count_rows;       /* (j, k) rows they visited */
+} obb_profile_stats;
+obb_status obb_profile_enable(obb_ctx* ctx, int32_t on);
+obb_status obb_profile_read(obb_ctx* ctx, obb_profile_stats* out);
+
 /* ------------------------------------------------------------------- mesh */
 
 /* The closed triangle mesh X of Sec. 3 (Definition 1 needs a solid):
@@ -126,6 +145,11 @@ void obb_mesh_free(obb_mesh* mesh);
  * point i is bit (i & 63) of word (i >> 6); padding bits are 0.
  * Synchronises once (reads back the lattice frame and the error word). */
 obb_status obb_build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_lattice** out);
+
+/* Recompute the occupancy of an existing lattice from its mesh in place
+ * (same N, same buffers, no allocation): the work of obb_build_occupancy
+ * without the handle creation.  Synchronises once. */
+obb_status obb_occupancy_rebuild(obb_ctx* ctx, obb_lattice* lat);
 
 /* Borrowed view of a lattice: frame (lo, h), N, words per row, device
  * pointers to the occupancy words and to the snapped vertices (int32 [n][3]).

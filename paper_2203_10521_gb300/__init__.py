@@ -48,6 +48,14 @@ class StepStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ProfileStats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("count_launches", C.c_int64), ("count_ms", C.c_double),
+                ("count_bytes", C.c_double), ("count_points", C.c_double), ("count_rows", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class TreeOpts(C.Structure):
     _fields_ = [("depth", C.c_int32), ("iters", C.c_int32), ("rounds", C.c_int32), ("refit", C.c_int32)]
 
@@ -72,6 +80,9 @@ def load(build_if_missing: bool = True):
         "obb_synchronize": [vp],
         "obb_mesh_create": [vp, vp, i64, vp, i64, C.POINTER(vp)],
         "obb_build_occupancy": [vp, vp, i32, C.POINTER(vp)],
+        "obb_occupancy_rebuild": [vp, vp],
+        "obb_profile_enable": [vp, i32],
+        "obb_profile_read": [vp, C.POINTER(ProfileStats)],
         "obb_lattice_desc": [vp, vp, vp, vp, vp, vp, vp],
         "obb_quantize_boxes": [vp, vp, vp, i64, vp, i32],
         "obb_outer_volume_q": [vp, vp, vp, i64, vp, vp, i32],
@@ -104,6 +115,7 @@ def load(build_if_missing: bool = True):
 def exported_symbols():
     """Names of the C entry points declared in include/obbvar.h."""
     return ["obb_create", "obb_set_stream", "obb_synchronize", "obb_destroy", "obb_last_error",
+            "obb_profile_enable", "obb_profile_read", "obb_occupancy_rebuild",
             "obb_mesh_create", "obb_mesh_free", "obb_build_occupancy", "obb_lattice_desc", "obb_lattice_free",
             "obb_quantize_boxes", "obb_outer_volume_q", "obb_outer_volume", "obb_layer_init", "obb_lloyd_step",
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
@@ -199,6 +211,18 @@ class Context:
         h = C.c_void_p()
         self.check(self.lib.obb_build_occupancy(self.h, mesh.h, int(N), C.byref(h)))
         return Lattice(self, h, mesh)
+
+    def occupancy_rebuild(self, lat):
+        self.check(self.lib.obb_occupancy_rebuild(self.h, lat.h))
+
+    # ------------------------------------------------------- instrumentation
+    def profile_enable(self, on=True):
+        self.check(self.lib.obb_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        st = ProfileStats()
+        self.check(self.lib.obb_profile_read(self.h, C.byref(st)))
+        return st.as_dict()
 
     # ---------------------------------------------------------- outer volume
     def quantize_boxes(self, lat, boxes, out=None):

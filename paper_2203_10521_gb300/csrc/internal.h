@@ -5,7 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/obbvar.h"
@@ -72,6 +75,13 @@ struct obb_ctx {
     // scratch reused across calls
     obbv::DevBuf prep, chunk_off, qscratch, cscratch, pscratch, kdev, tmp_a, tmp_b, tmp_c, tmp_d,
         cub_tmp;
+    // instrumentation: kernels launched by this context, and the optional
+    // profile of the outer-volume counting kernel (CUDA events + byte totals)
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+    unsigned long long* d_prof = nullptr;   // [0] algorithmic bytes, [1] lattice points, [2] rows
+    std::map<std::pair<int64_t, int>, int> sort_launch_cache;
 };
 
 struct obb_mesh {
@@ -127,6 +137,11 @@ struct obb_tree {
 
 namespace obbv {
 
+inline void note_launch(obb_ctx* ctx, int n = 1) { ctx->launches += n; }
+// Number of kernels one library call enqueues, found once per shape by
+// capturing the call into a CUDA graph on a side stream (nothing runs).
+int captured_launches(obb_ctx* ctx, int64_t key0, int key1, const std::function<cudaError_t(cudaStream_t)>& fn);
+
 obb_status fail(obb_ctx* ctx, obb_status code, const std::string& msg);
 obb_status cuda_fail(obb_ctx* ctx, cudaError_t e, const char* what);
 obb_status check_device_error(obb_ctx* ctx);   // synchronises, reads and clears the error word
@@ -145,6 +160,7 @@ obb_status check_device_error(obb_ctx* ctx);   // synchronises, reads and clears
 
 // occupancy.cu
 obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_lattice* lat);
+obb_status rebuild_occupancy(obb_ctx* ctx, obb_lattice* lat);
 
 // outer_volume.cu
 obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d_boxes, int64_t K,
@@ -155,10 +171,9 @@ obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_b
                        const int32_t* d_K, int64_t K_cap, uint64_t* d_counts, uint64_t* d_points);
 obb_status set_device_int(obb_ctx* ctx, int32_t* d_dst, int32_t value);
 // exclusive scan of n int32 values into out[n + 1] (out[n] = total), single block
-void launch_scan_i32(const int32_t* in, int32_t* out, const int32_t* d_n, int32_t n_cap,
-                     cudaStream_t s);
-void launch_box_report(const obb_lattice* lat, const double* d_frames, const obb_qbox* d_q, int32_t K,
-                       obb_box* d_out, cudaStream_t s);
+void launch_scan_i32(obb_ctx* ctx, const int32_t* in, int32_t* out, const int32_t* d_n);
+void launch_box_report(obb_ctx* ctx, const obb_lattice* lat, const double* d_frames, const obb_qbox* d_q,
+                       int32_t K, obb_box* d_out);
 
 // lloyd.cu
 obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_assign,

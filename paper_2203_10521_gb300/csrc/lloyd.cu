@@ -624,10 +624,16 @@ obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
     LayerMem* M = mem_of(L);
     OBB_CK(ctx, cudaMemsetAsync(L->d_size, 0, sizeof(int32_t) * L->K, s));
     k_hist<<<(unsigned)((L->T + 255) / 256), 256, 0, s>>>(L->d_assign, L->T, L->K, L->d_size, ctx->d_err);
-    launch_scan_i32(L->d_size, L->d_start, M->dK, L->K, s);
-    size_t bytes = M->cub_bytes;
-    OBB_CK(ctx, cub::DeviceRadixSort::SortPairs(M->cub_tmp, bytes, L->d_assign, M->keys_out, M->iota,
-                                                 L->d_members, (int)L->T, 0, M->end_bit, s));
+    note_launch(ctx);
+    launch_scan_i32(ctx, L->d_size, L->d_start, M->dK);
+    note_launch(ctx);
+    auto sort = [&](cudaStream_t cs) {
+        size_t bytes = M->cub_bytes;
+        return cub::DeviceRadixSort::SortPairs(M->cub_tmp, bytes, L->d_assign, M->keys_out, M->iota, L->d_members,
+                                               (int)L->T, 0, M->end_bit, cs);
+    };
+    OBB_CK(ctx, sort(s));
+    note_launch(ctx, captured_launches(ctx, L->T, M->end_bit, sort));
     OBB_CK(ctx, cudaGetLastError());
     M->members_valid = true;
     return OBB_OK;
@@ -664,10 +670,14 @@ static obb_status init_boxes(obb_ctx* ctx, obb_layer* L, const double* d_frames,
     } else {
         k_moments<kNT><<<K, kNT, 0, s>>>(lat->mesh->d_verts, lat->mesh->d_tris, L->d_members, L->d_start,
                                          lat->d_frame, M->mom);
+        note_launch(ctx);
         k_frames_from_moments<<<(K + 127) / 128, 128, 0, s>>>(M->mom, d_fallback, K, L->d_frames);
+        note_launch(ctx);
     }
     k_normals<<<(K + 127) / 128, 128, 0, s>>>(L->d_frames, K, lat->d_frame, L->d_q);
+    note_launch(ctx);
     k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, L->d_q);
+    note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return count_boxes(ctx, lat, L->d_q, M->dK, K, L->d_obv, nullptr);
 }
@@ -733,10 +743,12 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
     OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
     k_iota<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(M->iota, T);
+    note_launch(ctx);
     obb_status st = set_device_int(ctx, M->dK, K);
     if (st == OBB_OK) st = rebuild_members(ctx, L);
     if (st == OBB_OK) {
         k_check_nonempty<<<(K + 255) / 256, 256, 0, s>>>(L->d_size, K, ctx->d_err);
+        note_launch(ctx);
         st = check_device_error(ctx);   // assignment range / empty clusters before any box work
     }
     if (st == OBB_OK) st = init_boxes(ctx, L, d_frames, d_fallback);
@@ -764,18 +776,23 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
     for (int r = 0; r < rounds; ++r) {
         if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
         k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, L->d_q, L->d_ext);
+        note_launch(ctx);
         OBB_CK(ctx, cudaMemsetAsync(M->ctr, 0, sizeof(int32_t) * kCtrCount, s));
         OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
         k_candidates<<<(unsigned)((L->T + 127) / 128), 128, 0, s>>>(
             lat->d_fixed, mesh->d_tris, mesh->d_adj, L->T, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
             M->cand, M->evals, M->ctr, M->cand_cap, M->eval_cap, ctx->d_err);
+        note_launch(ctx);
         OBB_TRY(count_boxes(ctx, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->ecount, M->epoints));
         k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->ctr + kCtrEval, L->d_stats);
+        note_launch(ctx);
         const unsigned cb = (unsigned)((M->cand_cap + 127) / 128);
         k_gains<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->ecount, L->d_best, L->d_stats);
+        note_launch(ctx);
         const int64_t before = (r == 0) ? 0 : h[1];
         k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, M->evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
                                     L->d_size, L->d_stats);
+        note_launch(ctx);
         OBB_CK(ctx, cudaGetLastError());
         OBB_CK(ctx, cudaMemcpyAsync(h, L->d_stats, sizeof(int64_t) * kStCount, cudaMemcpyDeviceToHost, s));
         OBB_CK(ctx, cudaStreamSynchronize(s));
@@ -788,18 +805,25 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
         if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
         k_moments<kNT><<<K, kNT, 0, s>>>(mesh->d_verts, mesh->d_tris, L->d_members, L->d_start, lat->d_frame,
                                          M->mom);
+        note_launch(ctx);
         k_frames_from_moments<<<(K + 127) / 128, 128, 0, s>>>(M->mom, L->d_frames, K, M->newframe);
+        note_launch(ctx);
         k_normals<<<(K + 127) / 128, 128, 0, s>>>(M->newframe, K, lat->d_frame, M->newq);
+        note_launch(ctx);
         k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, M->newq);
+        note_launch(ctx);
         OBB_TRY(count_boxes(ctx, lat, M->newq, M->dK, K, M->ncount, M->epoints));
         k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->dK, L->d_stats);
+        note_launch(ctx);
         k_refit_accept<<<(K + 127) / 128, 128, 0, s>>>(M->newframe, M->newq, M->ncount, K, L->d_frames, L->d_q,
                                                        L->d_obv, L->d_stats);
+        note_launch(ctx);
         OBB_CK(ctx, cudaGetLastError());
     }
     if (st) {
         OBB_CK(ctx, ctx->tmp_d.reserve(sizeof(int64_t), s));
         k_total<<<1, 1024, 0, s>>>(L->d_obv, K, ctx->tmp_d.as<int64_t>());
+        note_launch(ctx);
         OBB_CK(ctx, cudaMemcpyAsync(h, L->d_stats, sizeof(int64_t) * kStCount, cudaMemcpyDeviceToHost, s));
         OBB_CK(ctx, cudaMemcpyAsync(h + kStCount, ctx->tmp_d.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         OBB_TRY(check_device_error(ctx));

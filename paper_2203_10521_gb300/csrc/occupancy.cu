@@ -199,6 +199,38 @@ __global__ void k_row_scan(uint64_t* __restrict__ words, int32_t N, int32_t W)
 
 }  // namespace
 
+obb_status rebuild_occupancy(obb_ctx* ctx, obb_lattice* lat)
+{
+    cudaStream_t s = ctx->stream;
+    const obb_mesh* mesh = lat->mesh;
+    const int32_t N = lat->frame.N;
+    const int32_t W = 2 * ((N + 127) / 128);
+    OBB_CK(ctx, ctx->tmp_d.reserve(64, s));
+    uint32_t* keys = ctx->tmp_d.as<uint32_t>();
+    k_init_aabb<<<1, 32, 0, s>>>(keys);
+    note_launch(ctx);
+    int64_t nb64 = (mesh->nv + 255) / 256;
+    int nb = (int)(nb64 < 4 * ctx->num_sms ? nb64 : 4 * ctx->num_sms);
+    k_aabb<<<max(nb, 1), 256, 0, s>>>(mesh->d_verts, mesh->nv, keys);
+    note_launch(ctx);
+    k_frame<<<1, 32, 0, s>>>(keys, N, lat->d_frame, ctx->d_err);
+    note_launch(ctx);
+    k_snap<<<(unsigned)((3 * mesh->nv + 255) / 256), 256, 0, s>>>(mesh->d_verts, mesh->nv, lat->d_frame,
+                                                                 lat->d_fixed);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaMemsetAsync(lat->d_words, 0, sizeof(uint64_t) * lat->n_words, s));
+    k_flip<<<(unsigned)((mesh->nt + 127) / 128), 128, 0, s>>>(
+        lat->d_fixed, mesh->d_tris, mesh->nt, N, W, reinterpret_cast<unsigned long long*>(lat->d_words));
+    note_launch(ctx);
+    const int G = W / 2, rpw = 32 / G;
+    int64_t warps = ((int64_t)N * N + rpw - 1) / rpw;
+    k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, N, W);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    OBB_CK(ctx, cudaMemcpyAsync(&lat->frame, lat->d_frame, sizeof(LatticeFrame), cudaMemcpyDeviceToHost, s));
+    return check_device_error(ctx);
+}
+
 obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_lattice* lat)
 {
     cudaStream_t s = ctx->stream;
@@ -207,27 +239,12 @@ obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_la
     lat->ctx = ctx;
     lat->mesh = mesh;
     lat->n_words = (size_t)N * N * W;
+    lat->frame.N = N;
+    lat->frame.W = W;
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_frame, sizeof(LatticeFrame), s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_fixed, sizeof(int32_t) * 3 * mesh->nv, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words, sizeof(uint64_t) * lat->n_words, s));
-    OBB_CK(ctx, ctx->tmp_a.reserve(64, s));
-    uint32_t* keys = ctx->tmp_a.as<uint32_t>();
-    k_init_aabb<<<1, 32, 0, s>>>(keys);
-    int64_t nb64 = (mesh->nv + 255) / 256;
-    int nb = (int)(nb64 < 4 * ctx->num_sms ? nb64 : 4 * ctx->num_sms);
-    k_aabb<<<max(nb, 1), 256, 0, s>>>(mesh->d_verts, mesh->nv, keys);
-    k_frame<<<1, 32, 0, s>>>(keys, N, lat->d_frame, ctx->d_err);
-    k_snap<<<(unsigned)((3 * mesh->nv + 255) / 256), 256, 0, s>>>(mesh->d_verts, mesh->nv, lat->d_frame,
-                                                                 lat->d_fixed);
-    OBB_CK(ctx, cudaMemsetAsync(lat->d_words, 0, sizeof(uint64_t) * lat->n_words, s));
-    k_flip<<<(unsigned)((mesh->nt + 127) / 128), 128, 0, s>>>(
-        lat->d_fixed, mesh->d_tris, mesh->nt, N, W, reinterpret_cast<unsigned long long*>(lat->d_words));
-    const int G = W / 2, rpw = 32 / G;
-    int64_t warps = ((int64_t)N * N + rpw - 1) / rpw;
-    k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, N, W);
-    OBB_CK(ctx, cudaGetLastError());
-    OBB_CK(ctx, cudaMemcpyAsync(&lat->frame, lat->d_frame, sizeof(LatticeFrame), cudaMemcpyDeviceToHost, s));
-    return check_device_error(ctx);
+    return rebuild_occupancy(ctx, lat);
 }
 
 }  // namespace obbv

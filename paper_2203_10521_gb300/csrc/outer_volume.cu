@@ -272,8 +272,11 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
                                                const int32_t* __restrict__ d_K,
                                                const uint64_t* __restrict__ words, int32_t N, int32_t W,
                                                unsigned long long* __restrict__ counts,
-                                               unsigned long long* __restrict__ points)
+                                               unsigned long long* __restrict__ points,
+                                               unsigned long long* __restrict__ acc)
 {
+    uint32_t my_chunks = 0, my_rows = 0;
+    unsigned long long my_pts = 0;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -306,9 +309,14 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
                 uint32_t occ = 0;
                 if (j >= 0 && j < N && k >= 0 && k < N) {
                     int32_t a = max(i0, 0), e = min(i1, N - 1);
-                    if (a <= e) occ = popc_range(words + ((int64_t)k * N + j) * W, a, e);
+                    if (a <= e) {
+                        occ = popc_range(words + ((int64_t)k * N + j) * W, a, e);
+                        my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                    }
                 }
                 empty = inbox - occ;
+                my_rows += 1;
+                my_pts += inbox;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -319,6 +327,24 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
             if (empty) atomicAdd(&counts[b], (unsigned long long)empty);
             if (points && inbox) atomicAdd(&points[b], (unsigned long long)inbox);
         }
+    }
+    if (acc) {   // profiling: algorithmic bytes, points and rows of this launch
+        __shared__ unsigned long long sh[3];
+        if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+        __syncthreads();
+        unsigned long long c = my_chunks, r = my_rows, p = my_pts;
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            r += __shfl_xor_sync(0xffffffffu, r, o);
+            p += __shfl_xor_sync(0xffffffffu, p, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&sh[0], c * 16ull);
+            atomicAdd(&sh[1], p);
+            atomicAdd(&sh[2], r);
+        }
+        __syncthreads();
+        if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
     }
 }
 
@@ -360,20 +386,24 @@ __global__ void k_set_i32(int32_t* dst, int32_t v)
 obb_status set_device_int(obb_ctx* ctx, int32_t* d_dst, int32_t value)
 {
     k_set_i32<<<1, 1, 0, ctx->stream>>>(d_dst, value);
+    note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return OBB_OK;
 }
 
-void launch_scan_i32(const int32_t* in, int32_t* out, const int32_t* d_n, int32_t n_cap, cudaStream_t s)
+void launch_scan_i32(obb_ctx* ctx, const int32_t* in, int32_t* out, const int32_t* d_n)
 {
-    (void)n_cap;
-    k_scan_i32<<<1, 1024, 0, s>>>(in, out, d_n);
+    k_scan_i32<<<1, 1024, 0, ctx->stream>>>(in, out, d_n);
+    note_launch(ctx);
 }
 
-void launch_box_report(const obb_lattice* lat, const double* d_frames, const obb_qbox* d_q, int32_t K,
-                       obb_box* d_out, cudaStream_t s)
+void launch_box_report(obb_ctx* ctx, const obb_lattice* lat, const double* d_frames, const obb_qbox* d_q, int32_t K,
+                       obb_box* d_out)
 {
-    if (K > 0) k_report<<<(K + 127) / 128, 128, 0, s>>>(lat->d_frame, d_frames, d_q, K, d_out);
+    if (K > 0) {
+        k_report<<<(K + 127) / 128, 128, 0, ctx->stream>>>(lat->d_frame, d_frames, d_q, K, d_out);
+        note_launch(ctx);
+    }
 }
 
 obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d_boxes, int64_t K,
@@ -382,6 +412,7 @@ obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d
     if (K <= 0) return OBB_OK;
     k_quantize<<<(unsigned)((K + 127) / 128), 128, 0, ctx->stream>>>(d_boxes, K, lat->d_frame, d_out,
                                                                     ctx->d_err);
+    note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return OBB_OK;
 }
@@ -411,10 +442,24 @@ obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_b
     OBB_CK(ctx, cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * K_cap, s));
     if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K_cap, s));
     k_prep<<<(unsigned)((K_cap + 127) / 128), 128, 0, s>>>(d_boxes, d_K, lat->frame.N, prep, chunks, ctx->d_err);
+    note_launch(ctx);
     k_scan_i64<<<1, 1024, 0, s>>>(chunks, off, d_K);
+    note_launch(ctx);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->prof) {
+        OBB_CK(ctx, cudaEventCreate(&e0));
+        OBB_CK(ctx, cudaEventCreate(&e1));
+        OBB_CK(ctx, cudaEventRecord(e0, s));
+    }
     k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, lat->d_words, lat->frame.N, lat->frame.W,
                                             reinterpret_cast<unsigned long long*>(d_counts),
-                                            reinterpret_cast<unsigned long long*>(d_points));
+                                            reinterpret_cast<unsigned long long*>(d_points),
+                                            ctx->prof ? ctx->d_prof : nullptr);
+    note_launch(ctx);
+    if (ctx->prof) {
+        OBB_CK(ctx, cudaEventRecord(e1, s));
+        ctx->prof_ev.emplace_back(e0, e1);
+    }
     OBB_CK(ctx, cudaGetLastError());
     return OBB_OK;
 }

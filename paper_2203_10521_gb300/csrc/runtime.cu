@@ -57,6 +57,36 @@ obb_status check_device_error(obb_ctx* ctx)
     return fail(ctx, OBB_ERR_STATE, "internal capacity exceeded");
 }
 
+int captured_launches(obb_ctx* ctx, int64_t key0, int key1, const std::function<cudaError_t(cudaStream_t)>& fn)
+{
+    auto key = std::make_pair(key0, key1);
+    auto it = ctx->sort_launch_cache.find(key);
+    if (it != ctx->sort_launch_cache.end()) return it->second;
+    int n = 0;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return 0;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        cudaError_t e = fn(cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess && e2 == cudaSuccess && g) {
+            size_t nn = 0;
+            cudaGraphGetNodes(g, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            cudaGraphGetNodes(g, nodes.data(), &nn);
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++n;
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    cudaStreamDestroy(cs);
+    ctx->sort_launch_cache[key] = n;
+    return n;
+}
+
 }  // namespace obbv
 
 using namespace obbv;
@@ -160,6 +190,11 @@ void obb_destroy(obb_ctx* ctx)
                       &ctx->tmp_a, &ctx->tmp_b, &ctx->tmp_c, &ctx->tmp_d, &ctx->cub_tmp};
     for (DevBuf* b : bufs) b->release(ctx->stream);
     cudaStreamSynchronize(ctx->stream);
+    for (auto& ev : ctx->prof_ev) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    if (ctx->d_prof) cudaFree(ctx->d_prof);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
     delete ctx;
@@ -256,6 +291,49 @@ obb_status obb_build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, ob
         return st;
     }
     *out = lat;
+    return OBB_OK;
+}
+
+obb_status obb_occupancy_rebuild(obb_ctx* ctx, obb_lattice* lat)
+{
+    if (!ctx || !lat) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (lat->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
+    return rebuild_occupancy(ctx, lat);
+}
+
+obb_status obb_profile_enable(obb_ctx* ctx, int32_t on)
+{
+    if (!ctx) return OBB_ERR_ARG;
+    OBB_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& ev : ctx->prof_ev) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    ctx->prof_ev.clear();
+    if (!ctx->d_prof) OBB_CK(ctx, cudaMalloc((void**)&ctx->d_prof, 4 * sizeof(unsigned long long)));
+    OBB_CK(ctx, cudaMemset(ctx->d_prof, 0, 4 * sizeof(unsigned long long)));
+    ctx->prof = on != 0;
+    return OBB_OK;
+}
+
+obb_status obb_profile_read(obb_ctx* ctx, obb_profile_stats* out)
+{
+    if (!ctx || !out) return OBB_ERR_ARG;
+    OBB_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    out->launches = ctx->launches;
+    out->count_launches = (int64_t)ctx->prof_ev.size();
+    double ms = 0.0;
+    for (auto& ev : ctx->prof_ev) {
+        float t = 0.f;
+        OBB_CK(ctx, cudaEventElapsedTime(&t, ev.first, ev.second));
+        ms += t;
+    }
+    out->count_ms = ms;
+    unsigned long long acc[4] = {0, 0, 0, 0};
+    if (ctx->d_prof) OBB_CK(ctx, cudaMemcpy(acc, ctx->d_prof, sizeof(acc), cudaMemcpyDeviceToHost));
+    out->count_bytes = (double)acc[0];
+    out->count_points = (double)acc[1];
+    out->count_rows = (double)acc[2];
     return OBB_OK;
 }
 
@@ -386,7 +464,7 @@ obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* L, int32_t* assign, dou
         HostTmp hb(ctx);
         obb_box* db;
         OBB_TRY(out_device(ctx, boxes, (size_t)L->K, on_device, hb, &db));
-        launch_box_report(L->lat, L->d_frames, L->d_q, L->K, db, s);
+        launch_box_report(ctx, L->lat, L->d_frames, L->d_q, L->K, db);
         OBB_CK(ctx, cudaGetLastError());
         OBB_TRY(copy_back(ctx, boxes, db, (size_t)L->K, on_device));
         if (!on_device) return check_device_error(ctx);

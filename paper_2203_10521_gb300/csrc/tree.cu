@@ -80,18 +80,28 @@ obb_status split_layer(obb_ctx* ctx, const obb_layer* up, int32_t* d_child)
     while ((1 << end_bit) < K) ++end_bit;
     const unsigned gb = (unsigned)((T + 255) / 256);
     k_split_keys<<<gb, 256, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, T, up->d_assign, up->d_q, keys, iota);
+    note_launch(ctx);
     size_t b1 = 0, b2 = 0;
     OBB_CK(ctx, cub::DeviceRadixSort::SortPairs(nullptr, b1, keys, keys_sorted, iota, order1, (int)T, 0, 64, s));
     OBB_CK(ctx, cub::DeviceRadixSort::SortPairs(nullptr, b2, cl, cl_sorted, order1, order2, (int)T, 0, end_bit, s));
     OBB_CK(ctx, ctx->cub_tmp.reserve(b1 > b2 ? b1 : b2, s));
-    b1 = ctx->cub_tmp.bytes;
-    OBB_CK(ctx, cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, b1, keys, keys_sorted, iota, order1, (int)T, 0, 64,
-                                                 s));
+    auto sort1 = [&](cudaStream_t cs) {
+        size_t bb = ctx->cub_tmp.bytes;
+        return cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, bb, keys, keys_sorted, iota, order1, (int)T, 0, 64, cs);
+    };
+    OBB_CK(ctx, sort1(s));
+    note_launch(ctx, captured_launches(ctx, T, 1000 + 64, sort1));
     k_gather<<<gb, 256, 0, s>>>(up->d_assign, order1, T, cl);
-    b2 = ctx->cub_tmp.bytes;
-    OBB_CK(ctx, cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, b2, cl, cl_sorted, order1, order2, (int)T, 0,
-                                                 end_bit, s));
+    note_launch(ctx);
+    auto sort2 = [&](cudaStream_t cs) {
+        size_t bb = ctx->cub_tmp.bytes;
+        return cub::DeviceRadixSort::SortPairs(ctx->cub_tmp.p, bb, cl, cl_sorted, order1, order2, (int)T, 0, end_bit,
+                                               cs);
+    };
+    OBB_CK(ctx, sort2(s));
+    note_launch(ctx, captured_launches(ctx, T, end_bit, sort2));
     k_split_assign<<<gb, 256, 0, s>>>(order2, cl_sorted, up->d_start, T, d_child, ctx->d_err);
+    note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return check_device_error(ctx);
 }
@@ -124,6 +134,7 @@ obb_status build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts*
         OBB_TRY(split_layer(ctx, up, child));
         const int32_t K2 = 2 * up->K;
         k_children<<<(K2 + 127) / 128, 128, 0, s>>>(K2, up->d_frames, parent, fallback);
+        note_launch(ctx);
         OBB_CK(ctx, cudaGetLastError());
         obb_layer* L = nullptr;
         OBB_TRY(layer_create(ctx, lat, child, parent, K2, nullptr, fallback, &L));

@@ -219,3 +219,30 @@ def test_build_tree_invariants():
     child = O.median_split(P, layers[0])
     init = O.layer_init(P, child, np.zeros(2, np.int32), np.repeat(layers[0].frames, 2, 0))
     assert int(L1.obv.sum()) <= int(init.obv.sum())
+
+
+def test_median_split_order_and_sizes():
+    """Median split (seeding of Sec. 4.2.2): children sizes ceil/floor of the
+    parent's, every key of child 2c at most every key of child 2c+1 (key =
+    major-axis projection of the fixed-point centroid), ties broken by index."""
+    m = M.torus_4096()
+    P = O.Problem(m.verts, m.tris, 32)
+    P.occ.fill_all()
+    K = 4
+    c = m.verts[m.tris].mean(1)
+    ang = np.arctan2(c[:, 1], c[:, 0])
+    assign = np.minimum(((ang + np.pi) / (2 * np.pi) * K).astype(np.int32), K - 1)
+    L = O.layer_init(P, assign, np.zeros(K, np.int32))
+    child = O.median_split(P, L)
+    cen3 = P.U[P.F].astype(np.int64).sum(1)
+    for k in range(K):
+        mem = np.nonzero(assign == k)[0]
+        key = cen3[mem] @ L.n[k, 0:3].astype(np.int64)
+        c0 = child[mem] == 2 * k
+        assert c0.sum() == (len(mem) + 1) // 2 and (~c0).sum() == len(mem) // 2
+        assert np.all(np.isin(child[mem], [2 * k, 2 * k + 1]))
+        assert key[c0].max() <= key[~c0].min()
+        # ties at the boundary key go to child 0 in ascending triangle order
+        b = key[c0].max()
+        tied = mem[key == b]
+        assert np.all(np.diff(child[tied]) >= 0)
