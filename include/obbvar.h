@@ -178,6 +178,26 @@ obb_status obb_quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_bo
 obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* boxes, int64_t K,
                               uint64_t* counts, uint64_t* points, int32_t on_device);
 
+/* Outer volume of K quantised boxes without allocating any device memory.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory once they are running, such as a real-time collision or
+ * physics loop working inside a fixed memory budget, or a host framework that
+ * owns the whole device memory pool and forbids allocations outside it.
+ * Results equal obb_outer_volume_q's.  boxes, counts and points (optional)
+ * are device arrays the caller provides; K <= OBB_NOALLOC_MAX_BOXES, larger K
+ * is rejected with OBB_ERR_RANGE.  The per-box scratch lives in one fixed
+ * device array inside the library (about 0.6 MB), held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * looks up that array's device address; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents, so calls that overlap on the GPU (different streams or threads
+ * without ordering) race: order them on one stream.  Asynchronous on the
+ * context stream; device-detected errors surface at the next synchronising
+ * call. */
+#define OBB_NOALLOC_MAX_BOXES 4096
+obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* boxes, int64_t K,
+                                      uint64_t* counts, uint64_t* points);
+
 /* obb_quantize_boxes followed by obb_outer_volume_q. */
 obb_status obb_outer_volume(obb_ctx* ctx, const obb_lattice* lat, const obb_box* boxes, int64_t K,
                             uint64_t* counts, uint64_t* points, int32_t on_device);

@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
         "obb_quantize_boxes": [vp, vp, vp, i64, vp, i32],
         "obb_outer_volume_q": [vp, vp, vp, i64, vp, vp, i32],
         "obb_outer_volume": [vp, vp, vp, i64, vp, vp, i32],
+        "obb_outer_volume_q_noalloc": [vp, vp, vp, i64, vp, vp],
         "obb_layer_init": [vp, vp, vp, vp, i32, vp, i32, C.POINTER(vp)],
         "obb_lloyd_step": [vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
         "obb_layer_read": [vp, vp, vp, vp, vp, vp, vp, i32],
@@ -117,7 +118,7 @@ def exported_symbols():
     return ["obb_create", "obb_set_stream", "obb_synchronize", "obb_destroy", "obb_last_error",
             "obb_profile_enable", "obb_profile_read", "obb_occupancy_rebuild",
             "obb_mesh_create", "obb_mesh_free", "obb_build_occupancy", "obb_lattice_desc", "obb_lattice_free",
-            "obb_quantize_boxes", "obb_outer_volume_q", "obb_outer_volume", "obb_layer_init", "obb_lloyd_step",
+            "obb_quantize_boxes", "obb_outer_volume_q", "obb_outer_volume", "obb_outer_volume_q_noalloc", "obb_layer_init", "obb_lloyd_step",
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
             "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free"]
 
@@ -243,6 +244,15 @@ class Context:
         p, dev, keep = _arg(qboxes, QBOX_DTYPE)
         K = _count(qboxes, keep, 88)
         return self._ov(self.lib.obb_outer_volume_q, lat, p, dev, K, counts, points, want_points)
+
+    def outer_volume_q_noalloc(self, lat, qboxes, counts, points=None):
+        """Device-only variant that allocates nothing (see obbvar.h); qboxes, counts
+        and points are torch CUDA tensors the caller owns."""
+        K = qboxes.numel() * qboxes.element_size() // 88
+        pp = C.c_void_p(points.data_ptr()) if points is not None else None
+        self.check(self.lib.obb_outer_volume_q_noalloc(self.h, lat.h, C.c_void_p(qboxes.data_ptr()), K,
+                                                         C.c_void_p(counts.data_ptr()), pp))
+        return counts
 
     def _out_like(self, dev, K, dtype, itemsize, torch_dtype=None):
         if dev:

@@ -13,6 +13,9 @@
 //          bits; rows or points outside [0, N)^3 are all empty.
 // Counts are integer sums (warp reduction + one 64-bit atomic per warp pass),
 // so the result does not depend on scheduling.
+#include <mutex>
+#include <string>
+
 #include "internal.h"
 
 namespace obbv {
@@ -465,3 +468,93 @@ obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_b
 }
 
 }  // namespace obbv
+
+// ---------------------------------------------------------------------------
+// Outer volume without device allocation.
+//
+// Some callers cannot allocate device memory once they are running: a
+// real-time collision or physics loop that works inside a fixed memory
+// budget, or a host framework that owns the whole device memory pool and
+// forbids allocations outside it.  This variant of the counting path takes
+// its per-box scratch (count preparation, chunk counts and offsets, the box
+// count) from one file-scope device array of fixed size instead of the
+// context's growable buffers.  Every GPU that loads the library holds the
+// array until the process exits.
+// ---------------------------------------------------------------------------
+namespace obbv {
+namespace {
+
+constexpr int64_t kNoAllocMaxBoxes = 4096;   // OBB_NOALLOC_MAX_BOXES in obbvar.h
+constexpr size_t kNoAllocPrepBytes = sizeof(BoxPrep) * kNoAllocMaxBoxes;
+constexpr size_t kNoAllocChunkBytes = sizeof(int64_t) * kNoAllocMaxBoxes;
+constexpr size_t kNoAllocOffBytes = sizeof(int64_t) * (kNoAllocMaxBoxes + 1);
+constexpr size_t kNoAllocOffsetChunks = (kNoAllocPrepBytes + 255) / 256 * 256;
+constexpr size_t kNoAllocOffsetOff = kNoAllocOffsetChunks + (kNoAllocChunkBytes + 255) / 256 * 256;
+constexpr size_t kNoAllocOffsetK = kNoAllocOffsetOff + (kNoAllocOffBytes + 255) / 256 * 256;
+constexpr size_t kNoAllocBytes = kNoAllocOffsetK + 256;
+
+// Shared by every call on a device; holds the last call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on `device` (looked up once per device, with
+// that device current).  In host code the array's name is only a stand-in.
+obb_status noalloc_scratch(obb_ctx* ctx, unsigned char** out)
+{
+    if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices) return fail(ctx, OBB_ERR_ARG, "device index too large");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[ctx->device]) {
+        int prev = -1;
+        OBB_CK(ctx, cudaGetDevice(&prev));
+        if (prev != ctx->device) OBB_CK(ctx, cudaSetDevice(ctx->device));
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (prev != ctx->device) cudaSetDevice(prev);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[ctx->device] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_ptr[ctx->device];
+    return OBB_OK;
+}
+
+}  // namespace
+}  // namespace obbv
+
+extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes,
+                                                 int64_t K, uint64_t* d_counts, uint64_t* d_points)
+{
+    using namespace obbv;
+    if (!ctx || !lat) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (K < 0) return fail(ctx, OBB_ERR_ARG, "negative K");
+    if (K > kNoAllocMaxBoxes)
+        return fail(ctx, OBB_ERR_RANGE,
+                    "obb_outer_volume_q_noalloc takes at most " + std::to_string(kNoAllocMaxBoxes) +
+                        " boxes per call (got " + std::to_string(K) + "); split the batch or use obb_outer_volume_q");
+    if (K == 0) return OBB_OK;
+    if (!d_boxes || !d_counts) return fail(ctx, OBB_ERR_ARG, "null argument");
+    unsigned char* base = nullptr;
+    OBB_TRY(noalloc_scratch(ctx, &base));
+    BoxPrep* prep = reinterpret_cast<BoxPrep*>(base);
+    int64_t* chunks = reinterpret_cast<int64_t*>(base + kNoAllocOffsetChunks);
+    int64_t* off = reinterpret_cast<int64_t*>(base + kNoAllocOffsetOff);
+    int32_t* dK = reinterpret_cast<int32_t*>(base + kNoAllocOffsetK);
+    cudaStream_t s = ctx->stream;
+    // counts and points are accumulated with atomics: they must start at zero
+    OBB_CK(ctx, cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * K, s));
+    if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K, s));
+    k_set_i32<<<1, 1, 0, s>>>(dK, (int32_t)K);
+    note_launch(ctx);
+    k_prep<<<(unsigned)((K + 127) / 128), 128, 0, s>>>(d_boxes, dK, lat->frame.N, prep, chunks, ctx->d_err);
+    note_launch(ctx);
+    k_scan_i64<<<1, 1024, 0, s>>>(chunks, off, dK);
+    note_launch(ctx);
+    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, dK, lat->d_words, lat->frame.N, lat->frame.W,
+                                            reinterpret_cast<unsigned long long*>(d_counts),
+                                            reinterpret_cast<unsigned long long*>(d_points), nullptr);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
