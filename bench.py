@@ -42,7 +42,7 @@ UNIT = "lattice pts/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--small", action="store_true", help="4,096-triangle torus on 64^3 (the oracle-sized case)")
@@ -289,9 +289,11 @@ def main():
         flush.fill_(1)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_step")
         e0.record(stream)
         st = step()
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         evs.append((e0, e1))
         pts_total += batch_points + st["points_counted"]
         lloyd.append(st)
@@ -334,7 +336,7 @@ def main():
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_count (outer-volume counting)", "peak_kind": peak_kind,
                 "count_launches": prof["count_launches"], "count_ms_total": prof["count_ms"],
-                "count_bytes_total": prof["count_bytes"],
+                "count_bytes_total": prof["count_bytes"], "count_rows": prof["count_rows"],
                 "count_share_of_step_time": prof["count_ms"] / sum(ms)}
 
     # end to end through the public API with host buffers

@@ -103,17 +103,16 @@ const char* obb_last_error(const obb_ctx* ctx);
  * (library kernels and the radix-sort kernels compiled into the library).
  * With profiling enabled, each launch of the outer-volume counting kernel is
  * bracketed by CUDA events on the context stream and the kernel adds up its
- * algorithmic traffic: 16 bytes per 128-bit occupancy chunk that a box row's
- * x-interval touches inside the lattice, the lattice points counted and the
- * rows visited.  obb_profile_enable resets the totals; obb_profile_read
+ * algorithmic traffic (16 bytes per 128-bit occupancy chunk that a box row's
+ * x-interval touches inside the lattice) and the rows with a non-empty
+ * interval.  obb_profile_enable resets the totals; obb_profile_read
  * synchronises and reports them. */
 typedef struct {
     int64_t launches;        /* kernels enqueued by the context since creation */
     int64_t count_launches;  /* counting-kernel launches since profiling was enabled */
     double count_ms;         /* their summed duration (CUDA events) */
     double count_bytes;      /* their summed algorithmic bytes */
-    double count_points;     /* lattice points they counted */
-    double count_rows;       /* (j, k) rows they visited */
+    double count_rows;       /* (j, k) rows with a non-empty interval inside the lattice or not */
 } obb_profile_stats;
 obb_status obb_profile_enable(obb_ctx* ctx, int32_t on);
 obb_status obb_profile_read(obb_ctx* ctx, obb_profile_stats* out);
@@ -186,7 +185,7 @@ obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qb
  * Results equal obb_outer_volume_q's.  boxes, counts and points (optional)
  * are device arrays the caller provides; K <= OBB_NOALLOC_MAX_BOXES, larger K
  * is rejected with OBB_ERR_RANGE.  The per-box scratch lives in one fixed
- * device array inside the library (about 0.6 MB), held by every GPU that
+ * device array inside the library (under 1 MB), held by every GPU that
  * loads the library until the process exits.  The first call on a device
  * looks up that array's device address; make that first call before any
  * stream capture.  All calls share the array and it keeps the last call's

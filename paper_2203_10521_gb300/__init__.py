@@ -50,7 +50,7 @@ class StepStats(C.Structure):
 
 class ProfileStats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("count_launches", C.c_int64), ("count_ms", C.c_double),
-                ("count_bytes", C.c_double), ("count_points", C.c_double), ("count_rows", C.c_double)]
+                ("count_bytes", C.c_double), ("count_rows", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -41,14 +41,18 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra=(), out_dir: str = None) -> str:
+    """Compile and link; `extra` adds nvcc flags (e.g. tuning -D values) and
+    `out_dir` redirects the objects and the library (default: _build/)."""
+    lib = LIB if out_dir is None else os.path.join(out_dir, "libobbvar.so")
+    out = OUT if out_dir is None else out_dir
+    if not force and out_dir is None and up_to_date():
         return LIB
-    os.makedirs(OUT, exist_ok=True)
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
 
     def one(unit):
-        obj = os.path.join(OUT, unit.replace(".cu", ".o"))
+        obj = os.path.join(out, unit.replace(".cu", ".o"))
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(SRC, unit), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -59,12 +63,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(one, UNITS))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -19,7 +19,10 @@ constexpr int kS = 8;            // fixed-point fraction bits of snapped vertice
 constexpr int kQ = 24;           // fraction bits of quantised normals
 constexpr int kMaxN = 2048;      // lattice points per axis
 constexpr int64_t kBoxRange = int64_t(1) << 20;  // |index-space AABB| limit of a counted box
-constexpr int kRowsPerChunk = 32;                // rows of one box handled by one warp pass
+#ifndef OBB_TILE_K
+#define OBB_TILE_K 16
+#endif
+constexpr int kTileK = OBB_TILE_K;               // rows along z one lane steps through per tile
 
 // device error word bits
 enum : int32_t {
@@ -41,16 +44,27 @@ struct LatticeFrame {
 };
 
 // Per-box data the counting kernel needs, prepared once per box.
+// Rows (j, k) of the box's index-space AABB are cut into tiles of wj rows
+// along y by wk * kTileK rows along z (wj * wk = 32 lanes); each lane owns one
+// j and visits kTileK rows spaced wk apart along z.  Slab a bounds i through
+// quotients by dd_a = |n_a0|; from one visited row to the next the quotient
+// moves by qstep_a with remainder carry rstep_a (an integer DDA).
 struct BoxPrep {
     int32_t n[9];
-    int32_t i0, i1;     // index-space AABB along x
-    int32_t j0, k0;     // first row
-    int32_t nj;         // rows along y
-    int32_t flags;
-    int64_t Lq[3], Hq[3];   // ceil(lo / 256), floor(hi / 256)
-    float rcp[3];           // 1 / n_a0, 0 when n_a0 == 0
-    int32_t pad;
-    uint64_t rows;          // nj * nk (0 = empty)
+    int32_t i0, i1;          // index-space AABB along x
+    int32_t j0, k0;          // first row
+    int32_t nj, nk;          // rows along y and z
+    int32_t ntj;             // tiles along y: ceil(nj / wj)
+    int32_t lwj;             // log2 of wj, the lanes of a tile along y (wk = 32 / wj along z)
+    int32_t mode;            // bit a: n_a0 != 0 (slab a bounds i by quotients)
+    int32_t pad0;
+    int32_t dd[3];           // |n_a0|
+    int32_t sg[3];           // sign of n_a0
+    int32_t rstep[3];        // remainder of that step, in [0, dd)
+    int32_t qstep[3];        // quotient of the step between a lane's rows (|.| < 2^25 for DDA slabs)
+    int64_t Lq[3], Hq[3];    // ceil(lo / 256), floor(hi / 256)
+    float rcp[3];            // 1 / dd (seed of the exact initial division)
+    uint64_t rows;           // nj * nk (0 = empty)
 };
 
 // Stream-ordered device allocation that only grows.

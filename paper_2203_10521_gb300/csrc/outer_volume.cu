@@ -2,21 +2,32 @@
 //
 // A box is the integer slab set lo_a <= n_a . (256 p) <= hi_a.  Counting:
 //   prep   per box: index-space bounds Lq = ceil(lo / 256), Hq = floor(hi / 256),
-//          a conservative integer AABB from the FP64 corners (+-2), the
-//          number of (j, k) rows of that AABB, float reciprocals of n_a0;
-//   scan   exclusive prefix of ceil(rows / 32) over the boxes (one block);
-//   count  persistent warps; a warp takes 32 rows of one box, one row per
-//          lane: the exact x-interval of the row from three slab constraints
-//          (a float estimate of each quotient corrected by exact int64
-//          products), then popcount of the occupied bits inside the interval
-//          over 128-bit loads.  Outer volume = interval length - occupied
-//          bits; rows or points outside [0, N)^3 are all empty.
-// Counts are integer sums (warp reduction + one 64-bit atomic per warp pass),
-// so the result does not depend on scheduling.
+//          a conservative integer AABB from the FP64 corners (+-2), and the
+//          per-z step of each slab's quotient (exact, int64);
+//   scan   exclusive prefix of the boxes' tile counts (one block);
+//   count  persistent warps over tiles of 32 (j) x kTileK (k) rows of one box.
+//          Each lane owns one j and walks kTileK rows along z: it divides the
+//          six slab bounds exactly once per tile (float seed + int64
+//          correction) and then advances every quotient by an integer DDA
+//          (add the step, carry the remainder), so each row's exact
+//          x-interval costs adds and compares only.  The occupied bits of the
+//          interval are popcounted over 128-bit loads; outer volume = interval
+//          length - occupied bits, and rows or points outside [0, N)^3 are all
+//          empty.
+// Counts are integer sums (warp reduction + one 64-bit atomic per tile), so
+// the result does not depend on scheduling.
 #include <mutex>
 #include <string>
 
 #include "internal.h"
+
+#ifndef OBB_COUNT_UNROLL
+#define OBB_COUNT_UNROLL 1
+#endif
+namespace obbv {
+// unroll factor of the counting kernel's row loop (a tuning parameter)
+constexpr int kCountUnroll = OBB_COUNT_UNROLL;
+}  // namespace obbv
 
 namespace obbv {
 namespace {
@@ -78,8 +89,14 @@ __global__ void k_quantize(const obb_box* __restrict__ boxes, int64_t K, const L
 
 // ------------------------------------------------------------------- prep
 
+__device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t d)   // d > 0
+{
+    int64_t q = a / d;
+    return (q * d > a) ? q - 1 : q;
+}
+
 __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __restrict__ d_K, int32_t N,
-                       BoxPrep* __restrict__ prep, int64_t* __restrict__ chunks, int32_t* err)
+                       BoxPrep* __restrict__ prep, int64_t* __restrict__ tiles, int32_t* err)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= *d_K) return;
@@ -87,19 +104,27 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
     BoxPrep p;
     for (int i = 0; i < 9; ++i) p.n[i] = q.n[i];
     bool empty = false;
+    p.mode = 0;
     for (int a = 0; a < 3; ++a) {
         p.Lq[a] = -((-q.b[2 * a]) >> kS);
         p.Hq[a] = q.b[2 * a + 1] >> kS;
         empty |= p.Lq[a] > p.Hq[a];
-        p.rcp[a] = p.n[3 * a] != 0 ? 1.0f / (float)p.n[3 * a] : 0.0f;
+        const int32_t d = p.n[3 * a];
+        p.sg[a] = d > 0 ? 1 : (d < 0 ? -1 : 0);
+        p.dd[a] = d >= 0 ? d : -d;
+        p.rcp[a] = d != 0 ? 1.0f / (float)p.dd[a] : 0.0f;
+        p.qstep[a] = 0;
+        p.rstep[a] = 0;
+        // slab kind: 0 = n_a0 == 0 (a band in (y, z)), 1 = quotient DDA in 32 bits,
+        // 2 = quotient DDA in 64 bits (|n_a0| < 32: the slab is almost parallel to x)
+        const int kind = d == 0 ? 0 : (p.dd[a] >= 32 ? 1 : 2);
+        p.mode |= kind << (2 * a);
     }
-    p.flags = 0;
-    p.pad = 0;
     p.rows = 0;
     p.i0 = 0;
     p.i1 = -1;
     p.j0 = p.k0 = 0;
-    p.nj = 0;
+    p.nj = p.nk = p.ntj = 0;
     if (!empty) {
         double M[9];
         for (int i = 0; i < 9; ++i) M[i] = (double)p.n[i];
@@ -147,12 +172,39 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
                 p.k0 = (int32_t)floor(mn[2]) - 2;
                 int32_t k1 = (int32_t)ceil(mx[2]) + 2;
                 p.nj = j1 - p.j0 + 1;
-                p.rows = (uint64_t)p.nj * (uint64_t)(k1 - p.k0 + 1);
+                p.nk = k1 - p.k0 + 1;
+                p.rows = (uint64_t)p.nj * (uint64_t)p.nk;
             }
         }
     }
+    // tile shape: wj lanes along y, wk = 32 / wj along z; the least padding wins
+    // (ties to the wider wj, whose rows sit next to each other in memory)
+    int best = 5;
+    int64_t best_slots = INT64_MAX;
+    if (p.rows) {
+        for (int l = 5; l >= 0; --l) {
+            const int64_t wj = 1 << l, wk = 32 >> l;
+            const int64_t slots = ((p.nj + wj - 1) / wj) * wj * ((p.nk + wk * kTileK - 1) / (wk * kTileK)) * wk * kTileK;
+            if (slots < best_slots) {
+                best_slots = slots;
+                best = l;
+            }
+        }
+    }
+    p.lwj = best;
+    const int32_t wj = 1 << best, wk = 32 >> best;
+    p.ntj = p.rows ? (p.nj + wj - 1) / wj : 0;
+    p.pad0 = 0;
+    for (int a = 0; a < 3; ++a)
+        if ((p.mode >> (2 * a)) & 3) {
+            // between a lane's rows k advances by wk: X_lo and X_hi move by -sign(d) * n_a2 * wk
+            const int64_t delta = -(int64_t)p.sg[a] * (int64_t)p.n[3 * a + 2] * wk;
+            const int64_t qs = floordiv64(delta, p.dd[a]);
+            p.qstep[a] = (int32_t)qs;   // |qs| <= 32 * 2^24 / 32 for |n_a0| >= 32
+            p.rstep[a] = (int32_t)(delta - qs * p.dd[a]);
+        }
     prep[k] = p;
-    chunks[k] = (int64_t)((p.rows + kRowsPerChunk - 1) / kRowsPerChunk);
+    tiles[k] = p.rows ? (int64_t)p.ntj * ((p.nk + wk * kTileK - 1) / (wk * kTileK)) : 0;
 }
 
 // ------------------------------------------------------------------- scan
@@ -215,16 +267,34 @@ __global__ void k_scan_i64(const int64_t* __restrict__ in, int64_t* __restrict__
 
 // ------------------------------------------------------------------ count
 
-// Intersect [lo, hi] with { i : L <= d i + c <= H } (d != 0 case handled by caller).
-__device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64_t L, int64_t H,
-                                          int32_t& lo, int32_t& hi)
+// Exact floor division of a signed int64 by 0 < d < 2^31: a float seed, one
+// float refinement of the remainder, then at most a couple of unit fixes.
+__device__ __forceinline__ void floordiv_exact(int64_t x, int32_t d, float rcp, int64_t& q, int32_t& r)
 {
-    if (d == 0) {
-        if (c < L || c > H) hi = lo - 1;
-        return;
+    int64_t q0 = __float2ll_rd(__ll2float_rn(x) * rcp);
+    int64_t rem = x - q0 * (int64_t)d;
+    int64_t q1 = __float2ll_rd(__ll2float_rn(rem) * rcp);
+    q0 += q1;
+    rem -= q1 * (int64_t)d;
+    while (rem < 0) {
+        rem += d;
+        --q0;
     }
-    int64_t A, B;
-    int64_t dd;
+    while (rem >= d) {
+        rem -= d;
+        ++q0;
+    }
+    q = q0;
+    r = (int32_t)rem;
+}
+
+// Intersect [lo, hi] with { i : L <= d i + c <= H } exactly (d != 0): float
+// estimates of the two quotients, clamped to [lo - 1, hi + 1] and corrected
+// with exact int64 products.  Used per row for slabs almost parallel to x.
+__device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64_t L, int64_t H, int32_t& lo,
+                                          int32_t& hi)
+{
+    int64_t A, B, dd;
     float r;
     if (d > 0) {
         A = L - c;
@@ -235,17 +305,15 @@ __device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64
         A = c - H;
         B = c - L;
         dd = -(int64_t)d;
-        r = -rcp;
+        r = rcp;
     }
     // g = max(ceil(A / dd), lo), capped at hi + 1
-    float ea = __ll2float_rn(A) * r;
-    float fl = fminf(fmaxf(ceilf(ea), (float)lo), (float)hi + 1.0f);
+    float fl = fminf(fmaxf(ceilf(__ll2float_rn(A) * r), (float)lo), (float)hi + 1.0f);
     int32_t g = (int32_t)fl;
     while (g > lo && (int64_t)(g - 1) * dd >= A) --g;
     while (g <= hi && (int64_t)g * dd < A) ++g;
     // u = min(floor(B / dd), hi), floored at lo - 1
-    float eb = __ll2float_rn(B) * r;
-    float fu = fminf(fmaxf(floorf(eb), (float)lo - 1.0f), (float)hi);
+    float fu = fminf(fmaxf(floorf(__ll2float_rn(B) * r), (float)lo - 1.0f), (float)hi);
     int32_t u = (int32_t)fu;
     while (u < hi && (int64_t)(u + 1) * dd <= B) ++u;
     while (u >= lo && (int64_t)u * dd > B) --u;
@@ -253,21 +321,34 @@ __device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64
     hi = u;
 }
 
+// popcount of the occupied bits i in [a, e] of one row (0 <= a <= e < N)
 __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
 {
-    uint32_t cnt = 0;
+    const uint4* r4 = reinterpret_cast<const uint4*>(row);
     const int32_t q0 = a >> 7, q1 = e >> 7;
-    for (int32_t q = q0; q <= q1; ++q) {
-        uint4 v = __ldg(reinterpret_cast<const uint4*>(row) + q);
-        uint64_t w0 = ((uint64_t)v.y << 32) | v.x;
-        uint64_t w1 = ((uint64_t)v.w << 32) | v.z;
-        const int32_t base = q << 7;
-        int32_t l0 = max(a - base, 0), h0 = min(e - base, 63);
-        if (l0 <= h0) cnt += __popcll(w0 & ((~0ull << l0) & (~0ull >> (63 - h0))));
-        int32_t l1 = max(a - base - 64, 0), h1 = min(e - base - 64, 63);
-        if (l1 <= h1) cnt += __popcll(w1 & ((~0ull << l1) & (~0ull >> (63 - h1))));
+    // first and last 128-bit chunks carry masks; interior chunks count whole
+    const uint32_t la = a & 127, he = e & 127;
+    uint4 v = __ldg(r4 + q0);
+    uint64_t w0 = ((uint64_t)v.y << 32) | v.x, w1 = ((uint64_t)v.w << 32) | v.z;
+    // keep bits >= la of the first chunk
+    uint64_t m0 = la < 64 ? (~0ull << la) : 0ull;
+    uint64_t m1 = la < 64 ? ~0ull : (~0ull << (la - 64));
+    if (q0 == q1) {
+        m0 &= he >= 63 ? ~0ull : (~0ull >> (63 - he));
+        m1 &= he < 64 ? 0ull : (he >= 127 ? ~0ull : (~0ull >> (127 - he)));
+        return __popcll(w0 & m0) + __popcll(w1 & m1);
     }
-    return cnt;
+    uint32_t cnt = __popcll(w0 & m0) + __popcll(w1 & m1);
+    for (int32_t qq = q0 + 1; qq < q1; ++qq) {
+        v = __ldg(r4 + qq);
+        cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    }
+    v = __ldg(r4 + q1);
+    w0 = ((uint64_t)v.y << 32) | v.x;
+    w1 = ((uint64_t)v.w << 32) | v.z;
+    m0 = he >= 63 ? ~0ull : (~0ull >> (63 - he));
+    m1 = he < 64 ? 0ull : (he >= 127 ? ~0ull : (~0ull >> (127 - he)));
+    return cnt + __popcll(w0 & m0) + __popcll(w1 & m1);
 }
 
 __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
@@ -279,47 +360,123 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
                                                unsigned long long* __restrict__ acc)
 {
     uint32_t my_chunks = 0, my_rows = 0;
-    unsigned long long my_pts = 0;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t K = *d_K;
     const int64_t total = off[K];
-    for (int64_t c = warp; c < total; c += nwarps) {
-        // box b with off[b] <= c < off[b + 1]
+    // each warp takes one contiguous range of tiles: the box and the tile
+    // coordinates then advance incrementally
+    const int64_t c_begin = total * warp / nwarps, c_end = total * (warp + 1) / nwarps;
+    int32_t b = 0;
+    if (c_begin < c_end) {
         int32_t lo = 0, hi = K - 1;
         while (lo < hi) {
             int32_t mid = (lo + hi + 1) >> 1;
-            if (off[mid] <= c) lo = mid;
+            if (off[mid] <= c_begin) lo = mid;
             else hi = mid - 1;
         }
-        const int32_t b = lo;
+        b = lo;
+    }
+    int32_t tj = 0, tk = 0;
+    int64_t box_end = 0;
+    bool fresh = true;
+    for (int64_t c = c_begin; c < c_end; ++c) {
+        if (fresh || c >= box_end) {
+            if (!fresh) ++b;
+            while (off[b + 1] <= c) ++b;   // skip boxes without tiles
+            const int32_t u = (int32_t)(c - off[b]);
+            const int32_t ntj0 = prep[b].ntj;
+            tk = u / ntj0;
+            tj = u - tk * ntj0;
+            box_end = off[b + 1];
+            fresh = false;
+        }
         const BoxPrep& p = prep[b];
-        const uint32_t r = (uint32_t)(c - off[b]) * kRowsPerChunk + lane;
-        uint32_t empty = 0, inbox = 0;
-        if (r < p.rows) {
-            const uint32_t nj = (uint32_t)p.nj;
-            const int32_t rk = (int32_t)(r / nj);
-            const int32_t j = p.j0 + (int32_t)(r - (uint32_t)rk * nj);
-            const int32_t k = p.k0 + rk;
-            int32_t i0 = p.i0, i1 = p.i1;
-            for (int a = 0; a < 3 && i0 <= i1; ++a) {
-                int64_t cc = (int64_t)p.n[3 * a + 1] * j + (int64_t)p.n[3 * a + 2] * k;
-                clip_slab(p.n[3 * a], p.rcp[a], cc, p.Lq[a], p.Hq[a], i0, i1);
+        const int32_t mode = p.mode;
+        const int32_t lwj = p.lwj;
+        const int32_t wk = 32 >> lwj;
+        const int32_t jl = (tj << lwj) + (lane & ((1 << lwj) - 1));
+        const int32_t j = p.j0 + jl;
+        const bool jvalid = jl < p.nj;
+        const int32_t kb = p.k0 + tk * (wk * kTileK) + (lane >> lwj);   // this lane's first row
+        const int32_t kend = p.k0 + p.nk;
+        const int32_t i0 = p.i0, span = p.i1 - p.i0;
+        // Kind-1 slabs carry exact quotient bounds relative to i0 in 32 bits,
+        // saturated at +-2^30: a bound that far out moves less than 2^29 within a
+        // tile, so it stays outside [0, span].  Kind 0 (n_a0 = 0) and kind 2
+        // (|n_a0| < 32) slabs are evaluated from scratch on each row.
+        int32_t qa[3], qb[3], ra[3], rb[3], dd[3], rs[3], qs[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            qa[a] = qb[a] = ra[a] = rb[a] = rs[a] = qs[a] = 0;
+            dd[a] = 1;
+            if (((mode >> (2 * a)) & 3) == 1) {
+                dd[a] = p.dd[a];
+                rs[a] = p.rstep[a];
+                qs[a] = p.qstep[a];
+                const int64_t cc = (int64_t)p.n[3 * a + 1] * j + (int64_t)p.n[3 * a + 2] * kb;
+                const int64_t xlo = p.sg[a] > 0 ? p.Lq[a] - cc : cc - p.Hq[a];
+                const int64_t xhi = p.sg[a] > 0 ? p.Hq[a] - cc : cc - p.Lq[a];
+                int64_t wlo, whi;
+                floordiv_exact(xlo + dd[a] - 1, dd[a], p.rcp[a], wlo, ra[a]);   // ceil(xlo / dd)
+                floordiv_exact(xhi, dd[a], p.rcp[a], whi, rb[a]);               // floor(xhi / dd)
+                const int64_t lim = int64_t(1) << 30;
+                qa[a] = (int32_t)min(max(wlo - i0, -lim), lim);
+                qb[a] = (int32_t)min(max(whi - i0, -lim), lim);
             }
-            if (i0 <= i1) {
-                inbox = (uint32_t)(i1 - i0 + 1);
+        }
+        uint32_t empty = 0, inbox = 0;
+        const bool jin = j >= 0 && j < N;
+#pragma unroll kCountUnroll
+        for (int r = 0; r < kTileK; ++r) {
+            const int32_t k = kb + r * wk;
+            int32_t lo = 0, hi = span;
+            bool ok = jvalid && k < kend;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int kind = (mode >> (2 * a)) & 3;
+                if (kind == 1) {
+                    lo = max(lo, qa[a]);
+                    hi = min(hi, qb[a]);
+                    qa[a] += qs[a];
+                    ra[a] += rs[a];
+                    if (ra[a] >= dd[a]) {
+                        ra[a] -= dd[a];
+                        qa[a] += 1;
+                    }
+                    qb[a] += qs[a];
+                    rb[a] += rs[a];
+                    if (rb[a] >= dd[a]) {
+                        rb[a] -= dd[a];
+                        qb[a] += 1;
+                    }
+                } else if (ok && lo <= hi) {
+                    const int64_t cc = (int64_t)p.n[3 * a + 1] * j + (int64_t)p.n[3 * a + 2] * k;
+                    if (kind == 0) {
+                        ok = cc >= p.Lq[a] && cc <= p.Hq[a];
+                    } else {
+                        int32_t l2 = i0 + lo, h2 = i0 + hi;
+                        clip_slab(p.n[3 * a], p.rcp[a], cc, p.Lq[a], p.Hq[a], l2, h2);
+                        lo = l2 - i0;
+                        hi = h2 - i0;
+                    }
+                }
+            }
+            if (ok && lo <= hi) {
+                const int32_t ia = i0 + lo, ie = i0 + hi;
+                const uint32_t len = (uint32_t)(hi - lo + 1);
                 uint32_t occ = 0;
-                if (j >= 0 && j < N && k >= 0 && k < N) {
-                    int32_t a = max(i0, 0), e = min(i1, N - 1);
+                if (jin && k >= 0 && k < N) {
+                    const int32_t a = max(ia, 0), e = min(ie, N - 1);
                     if (a <= e) {
                         occ = popc_range(words + ((int64_t)k * N + j) * W, a, e);
                         my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
                     }
                 }
-                empty = inbox - occ;
+                empty += len - occ;
+                inbox += len;
                 my_rows += 1;
-                my_pts += inbox;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -330,24 +487,22 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
             if (empty) atomicAdd(&counts[b], (unsigned long long)empty);
             if (points && inbox) atomicAdd(&points[b], (unsigned long long)inbox);
         }
+        if (++tj == p.ntj) {
+            tj = 0;
+            ++tk;
+        }
     }
-    if (acc) {   // profiling: algorithmic bytes, points and rows of this launch
-        __shared__ unsigned long long sh[3];
-        if (threadIdx.x < 3) sh[threadIdx.x] = 0;
+    if (acc) {   // profiling: algorithmic bytes and non-empty rows of this launch
+        __shared__ unsigned long long sh[2];
+        if (threadIdx.x < 2) sh[threadIdx.x] = 0;
         __syncthreads();
-        unsigned long long c = my_chunks, r = my_rows, p = my_pts;
-        for (int o = 16; o > 0; o >>= 1) {
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            r += __shfl_xor_sync(0xffffffffu, r, o);
-            p += __shfl_xor_sync(0xffffffffu, p, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&sh[0], c * 16ull);
-            atomicAdd(&sh[1], p);
-            atomicAdd(&sh[2], r);
+        unsigned long long v[2] = {my_chunks * 16ull, my_rows};
+        for (int i = 0; i < 2; ++i) {
+            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+            if (lane == 0) atomicAdd(&sh[i], v[i]);
         }
         __syncthreads();
-        if (threadIdx.x < 3 && sh[threadIdx.x]) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
+        if (threadIdx.x < 2 && sh[threadIdx.x]) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
     }
 }
 
@@ -440,13 +595,13 @@ obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_b
     OBB_CK(ctx, ctx->prep.reserve(sizeof(BoxPrep) * K_cap, s));
     OBB_CK(ctx, ctx->chunk_off.reserve(sizeof(int64_t) * (2 * K_cap + 1), s));
     BoxPrep* prep = ctx->prep.as<BoxPrep>();
-    int64_t* chunks = ctx->chunk_off.as<int64_t>();
-    int64_t* off = chunks + K_cap;
+    int64_t* tiles = ctx->chunk_off.as<int64_t>();
+    int64_t* off = tiles + K_cap;
     OBB_CK(ctx, cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * K_cap, s));
     if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K_cap, s));
-    k_prep<<<(unsigned)((K_cap + 127) / 128), 128, 0, s>>>(d_boxes, d_K, lat->frame.N, prep, chunks, ctx->d_err);
+    k_prep<<<(unsigned)((K_cap + 127) / 128), 128, 0, s>>>(d_boxes, d_K, lat->frame.N, prep, tiles, ctx->d_err);
     note_launch(ctx);
-    k_scan_i64<<<1, 1024, 0, s>>>(chunks, off, d_K);
+    k_scan_i64<<<1, 1024, 0, s>>>(tiles, off, d_K);
     note_launch(ctx);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->prof) {

@@ -310,8 +310,8 @@ obb_status obb_profile_enable(obb_ctx* ctx, int32_t on)
         cudaEventDestroy(ev.second);
     }
     ctx->prof_ev.clear();
-    if (!ctx->d_prof) OBB_CK(ctx, cudaMalloc((void**)&ctx->d_prof, 4 * sizeof(unsigned long long)));
-    OBB_CK(ctx, cudaMemset(ctx->d_prof, 0, 4 * sizeof(unsigned long long)));
+    if (!ctx->d_prof) OBB_CK(ctx, cudaMalloc((void**)&ctx->d_prof, 8 * sizeof(unsigned long long)));
+    OBB_CK(ctx, cudaMemset(ctx->d_prof, 0, 8 * sizeof(unsigned long long)));
     ctx->prof = on != 0;
     return OBB_OK;
 }
@@ -329,11 +329,10 @@ obb_status obb_profile_read(obb_ctx* ctx, obb_profile_stats* out)
         ms += t;
     }
     out->count_ms = ms;
-    unsigned long long acc[4] = {0, 0, 0, 0};
+    unsigned long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (ctx->d_prof) OBB_CK(ctx, cudaMemcpy(acc, ctx->d_prof, sizeof(acc), cudaMemcpyDeviceToHost));
     out->count_bytes = (double)acc[0];
-    out->count_points = (double)acc[1];
-    out->count_rows = (double)acc[2];
+    out->count_rows = (double)acc[1];
     return OBB_OK;
 }
 
