@@ -24,9 +24,13 @@
 #ifndef OBB_COUNT_UNROLL
 #define OBB_COUNT_UNROLL 1
 #endif
+#ifndef OBB_GRAB
+#define OBB_GRAB 1
+#endif
 namespace obbv {
-// unroll factor of the counting kernel's row loop (a tuning parameter)
+// tuning parameters: unroll factor of the counting kernel's row loop, tiles per work grab
 constexpr int kCountUnroll = OBB_COUNT_UNROLL;
+constexpr int kGrab = OBB_GRAB;
 }  // namespace obbv
 
 namespace obbv {
@@ -237,7 +241,8 @@ __global__ void k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__
     if (threadIdx.x == T - 1) out[n] = part[T - 1];
 }
 
-// Exclusive scan of n = *d_n int64 values into out[0..n]; one block.
+// Exclusive scan of n = *d_n int64 values into out[0..n]; one block.  Also
+// clears out[n + 1], the tile counter the counting kernel hands work out from.
 __global__ void k_scan_i64(const int64_t* __restrict__ in, int64_t* __restrict__ out,
                            const int32_t* __restrict__ d_n)
 {
@@ -262,7 +267,10 @@ __global__ void k_scan_i64(const int64_t* __restrict__ in, int64_t* __restrict__
         out[i] = run;
         run += in[i];
     }
-    if (threadIdx.x == T - 1) out[n] = part[T - 1];
+    if (threadIdx.x == T - 1) {
+        out[n] = part[T - 1];
+        out[n + 1] = 0;   // work counter of the counting kernel
+    }
 }
 
 // ------------------------------------------------------------------ count
@@ -361,36 +369,37 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
 {
     uint32_t my_chunks = 0, my_rows = 0;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t K = *d_K;
     const int64_t total = off[K];
-    // each warp takes one contiguous range of tiles: the box and the tile
-    // coordinates then advance incrementally
-    const int64_t c_begin = total * warp / nwarps, c_end = total * (warp + 1) / nwarps;
-    int32_t b = 0;
-    if (c_begin < c_end) {
-        int32_t lo = 0, hi = K - 1;
-        while (lo < hi) {
-            int32_t mid = (lo + hi + 1) >> 1;
-            if (off[mid] <= c_begin) lo = mid;
-            else hi = mid - 1;
-        }
-        b = lo;
-    }
-    int32_t tj = 0, tk = 0;
-    int64_t box_end = 0;
-    bool fresh = true;
-    for (int64_t c = c_begin; c < c_end; ++c) {
-        if (fresh || c >= box_end) {
-            if (!fresh) ++b;
-            while (off[b + 1] <= c) ++b;   // skip boxes without tiles
+    unsigned long long* next = reinterpret_cast<unsigned long long*>(const_cast<int64_t*>(off + K + 1));
+    // warps take runs of kGrab consecutive tiles from a global counter; within a
+    // run the box and the tile coordinates advance incrementally
+    int64_t c = 0, c_end = 0, box_end = 0;
+    int32_t b = 0, tj = 0, tk = 0;
+    for (;;) {
+        if (c == c_end) {
+            unsigned long long g = 0;
+            if (lane == 0) g = atomicAdd(next, (unsigned long long)kGrab);
+            c = (int64_t)__shfl_sync(0xffffffffu, g, 0);
+            if (c >= total) break;
+            c_end = min(c + (int64_t)kGrab, total);
+            int32_t lo = 0, hi = K - 1;
+            while (lo < hi) {
+                int32_t mid = (lo + hi + 1) >> 1;
+                if (off[mid] <= c) lo = mid;
+                else hi = mid - 1;
+            }
+            b = lo;
+            box_end = off[b + 1];
             const int32_t u = (int32_t)(c - off[b]);
             const int32_t ntj0 = prep[b].ntj;
             tk = u / ntj0;
             tj = u - tk * ntj0;
+        } else if (c >= box_end) {
+            ++b;
+            while (off[b + 1] <= c) ++b;   // skip boxes without tiles
             box_end = off[b + 1];
-            fresh = false;
+            tj = tk = 0;
         }
         const BoxPrep& p = prep[b];
         const int32_t mode = p.mode;
@@ -491,6 +500,7 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
             tj = 0;
             ++tk;
         }
+        ++c;
     }
     if (acc) {   // profiling: algorithmic bytes and non-empty rows of this launch
         __shared__ unsigned long long sh[2];
@@ -593,7 +603,7 @@ obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_b
     if (K_cap <= 0) return OBB_OK;
     if (K_cap > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_RANGE, "too many boxes in one call");
     OBB_CK(ctx, ctx->prep.reserve(sizeof(BoxPrep) * K_cap, s));
-    OBB_CK(ctx, ctx->chunk_off.reserve(sizeof(int64_t) * (2 * K_cap + 1), s));
+    OBB_CK(ctx, ctx->chunk_off.reserve(sizeof(int64_t) * (2 * K_cap + 2), s));
     BoxPrep* prep = ctx->prep.as<BoxPrep>();
     int64_t* tiles = ctx->chunk_off.as<int64_t>();
     int64_t* off = tiles + K_cap;
@@ -642,7 +652,7 @@ namespace {
 constexpr int64_t kNoAllocMaxBoxes = 4096;   // OBB_NOALLOC_MAX_BOXES in obbvar.h
 constexpr size_t kNoAllocPrepBytes = sizeof(BoxPrep) * kNoAllocMaxBoxes;
 constexpr size_t kNoAllocChunkBytes = sizeof(int64_t) * kNoAllocMaxBoxes;
-constexpr size_t kNoAllocOffBytes = sizeof(int64_t) * (kNoAllocMaxBoxes + 1);
+constexpr size_t kNoAllocOffBytes = sizeof(int64_t) * (kNoAllocMaxBoxes + 2);
 constexpr size_t kNoAllocOffsetChunks = (kNoAllocPrepBytes + 255) / 256 * 256;
 constexpr size_t kNoAllocOffsetOff = kNoAllocOffsetChunks + (kNoAllocChunkBytes + 255) / 256 * 256;
 constexpr size_t kNoAllocOffsetK = kNoAllocOffsetOff + (kNoAllocOffBytes + 255) / 256 * 256;
