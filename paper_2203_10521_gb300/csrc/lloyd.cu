@@ -671,10 +671,10 @@ static obb_status init_boxes(obb_ctx* ctx, obb_layer* L, const double* d_frames,
         k_moments<kNT><<<K, kNT, 0, s>>>(lat->mesh->d_verts, lat->mesh->d_tris, L->d_members, L->d_start,
                                          lat->d_frame, M->mom);
         note_launch(ctx);
-        k_frames_from_moments<<<(K + 127) / 128, 128, 0, s>>>(M->mom, d_fallback, K, L->d_frames);
+        k_frames_from_moments<<<(K + 31) / 32, 32, 0, s>>>(M->mom, d_fallback, K, L->d_frames);
         note_launch(ctx);
     }
-    k_normals<<<(K + 127) / 128, 128, 0, s>>>(L->d_frames, K, lat->d_frame, L->d_q);
+    k_normals<<<(K + 31) / 32, 32, 0, s>>>(L->d_frames, K, lat->d_frame, L->d_q);
     note_launch(ctx);
     k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, L->d_q);
     note_launch(ctx);
@@ -806,9 +806,9 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
         k_moments<kNT><<<K, kNT, 0, s>>>(mesh->d_verts, mesh->d_tris, L->d_members, L->d_start, lat->d_frame,
                                          M->mom);
         note_launch(ctx);
-        k_frames_from_moments<<<(K + 127) / 128, 128, 0, s>>>(M->mom, L->d_frames, K, M->newframe);
+        k_frames_from_moments<<<(K + 31) / 32, 32, 0, s>>>(M->mom, L->d_frames, K, M->newframe);
         note_launch(ctx);
-        k_normals<<<(K + 127) / 128, 128, 0, s>>>(M->newframe, K, lat->d_frame, M->newq);
+        k_normals<<<(K + 31) / 32, 32, 0, s>>>(M->newframe, K, lat->d_frame, M->newq);
         note_launch(ctx);
         k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, M->newq);
         note_launch(ctx);

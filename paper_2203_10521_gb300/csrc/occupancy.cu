@@ -86,15 +86,17 @@ __global__ void k_snap(const float* __restrict__ V, int64_t nv, const LatticeFra
     U[i] = (int32_t)rint(q);
 }
 
-__device__ __forceinline__ int64_t orient_yz(int64_t ay, int64_t az, int64_t by, int64_t bz,
-                                             int64_t py, int64_t pz)
+// orient2d in the (y, z) plane; coordinates are |U| <= 2^19, so every factor
+// fits in 32 bits and each product in 64 (one wide multiply-add).
+__device__ __forceinline__ int64_t orient_yz(int32_t ay, int32_t az, int32_t by, int32_t bz, int32_t py,
+                                             int32_t pz)
 {
-    return (by - ay) * (pz - az) - (bz - az) * (py - ay);
+    return (int64_t)(by - ay) * (pz - az) - (int64_t)(bz - az) * (py - ay);
 }
 
 // sign of orient2d((a, b), p + (eps, eps^2)) for eps -> 0+
-__device__ __forceinline__ int sos_side(int64_t ay, int64_t az, int64_t by, int64_t bz, int64_t py,
-                                        int64_t pz, int64_t* o)
+__device__ __forceinline__ int sos_side(int32_t ay, int32_t az, int32_t by, int32_t bz, int32_t py, int32_t pz,
+                                        int64_t* o)
 {
     *o = orient_yz(ay, az, by, bz, py, pz);
     if (*o != 0) return *o > 0 ? 1 : -1;
@@ -103,10 +105,18 @@ __device__ __forceinline__ int sos_side(int64_t ay, int64_t az, int64_t by, int6
     return 0;
 }
 
-__device__ __forceinline__ int64_t floordiv_pos(int64_t a, int64_t d)   // d > 0
+// ceil(num / (256 den)) for den > 0, clamped to [-1, N]: a float estimate
+// corrected by exact int64 products (the quotient is a lattice index).
+__device__ __forceinline__ int32_t first_index_at_or_after(int64_t num, int64_t den, int32_t N)
 {
-    int64_t q = a / d;
-    return (q * d > a) ? q - 1 : q;
+    const int64_t D = den << kS;
+    float e = __ll2float_rn(num) / __ll2float_rn(D);
+    e = fminf(fmaxf(e, -2.0f), (float)N + 1.0f);
+    int32_t q = (int32_t)ceilf(e);
+    // smallest q with q * D >= num, searched within [-1, N]
+    while (q > -1 && (int64_t)(q - 1) * D >= num) --q;
+    while (q < N && (int64_t)q * D < num) ++q;
+    return q;
 }
 
 __global__ void k_flip(const int32_t* __restrict__ U, const int32_t* __restrict__ F, int64_t nt,
@@ -117,21 +127,21 @@ __global__ void k_flip(const int32_t* __restrict__ U, const int32_t* __restrict_
     const int32_t* A = U + 3 * (int64_t)F[3 * t];
     const int32_t* B = U + 3 * (int64_t)F[3 * t + 1];
     const int32_t* C = U + 3 * (int64_t)F[3 * t + 2];
-    int32_t ay = A[1], az = A[2], by = B[1], bz = B[2], cy = C[1], cz = C[2];
-    int64_t ax = A[0], bx = B[0], cx = C[0];
-    int32_t ymin = min(ay, min(by, cy)), ymax = max(ay, max(by, cy));
-    int32_t zmin = min(az, min(bz, cz)), zmax = max(az, max(bz, cz));
+    const int32_t ay = A[1], az = A[2], by = B[1], bz = B[2], cy = C[1], cz = C[2];
+    const int64_t ax = A[0], bx = B[0], cx = C[0];
+    const int32_t ymin = min(ay, min(by, cy)), ymax = max(ay, max(by, cy));
+    const int32_t zmin = min(az, min(bz, cz)), zmax = max(az, max(bz, cz));
     // columns with 256 j in [ymin, ymax], 256 k in [zmin, zmax]
-    int32_t j0 = max(-((-ymin) >> kS), 0), j1 = min(ymax >> kS, N - 1);
-    int32_t k0 = max(-((-zmin) >> kS), 0), k1 = min(zmax >> kS, N - 1);
+    const int32_t j0 = max(-((-ymin) >> kS), 0), j1 = min(ymax >> kS, N - 1);
+    const int32_t k0 = max(-((-zmin) >> kS), 0), k1 = min(zmax >> kS, N - 1);
     for (int32_t k = k0; k <= k1; ++k) {
-        int64_t pz = (int64_t)k << kS;
+        const int32_t pz = k << kS;
         for (int32_t j = j0; j <= j1; ++j) {
-            int64_t py = (int64_t)j << kS;
+            const int32_t py = j << kS;
             int64_t wa, wb, wc;
-            int sa = sos_side(by, bz, cy, cz, py, pz, &wa);
-            int sb = sos_side(cy, cz, ay, az, py, pz, &wb);
-            int sc = sos_side(ay, az, by, bz, py, pz, &wc);
+            const int sa = sos_side(by, bz, cy, cz, py, pz, &wa);
+            const int sb = sos_side(cy, cz, ay, az, py, pz, &wb);
+            const int sc = sos_side(ay, az, by, bz, py, pz, &wc);
             if (sa == 0 || sa != sb || sb != sc) continue;
             int64_t den = wa + wb + wc;
             int64_t num = wa * ax + wb * bx + wc * cx;
@@ -139,8 +149,8 @@ __global__ void k_flip(const int32_t* __restrict__ U, const int32_t* __restrict_
                 den = -den;
                 num = -num;
             }
-            // first index with 256 i >= num / den
-            int64_t istar = -floordiv_pos(-num, den << kS);
+            // first index with 256 i >= num / den; below 0 every point counts the crossing
+            int32_t istar = first_index_at_or_after(num, den, N);
             if (istar < 0) istar = 0;
             if (istar >= N) continue;
             atomicXor(&words[((int64_t)k * N + j) * W + (istar >> 6)], 1ull << (istar & 63));

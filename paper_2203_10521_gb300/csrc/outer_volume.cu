@@ -143,17 +143,19 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
             double inv[9] = {c00, M[2] * M[7] - M[1] * M[8], M[1] * M[5] - M[2] * M[4],
                              c01, M[0] * M[8] - M[2] * M[6], M[2] * M[3] - M[0] * M[5],
                              c02, M[1] * M[6] - M[0] * M[7], M[0] * M[4] - M[1] * M[3]};
-            double id = 1.0 / det;
-            double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
-            for (int c = 0; c < 8; ++c) {
-                double b0 = (double)((c & 1) ? p.Hq[0] : p.Lq[0]);
-                double b1 = (double)((c & 2) ? p.Hq[1] : p.Lq[1]);
-                double b2 = (double)((c & 4) ? p.Hq[2] : p.Lq[2]);
-                for (int r = 0; r < 3; ++r) {
-                    double v = (inv[3 * r] * b0 + inv[3 * r + 1] * b1 + inv[3 * r + 2] * b2) * id;
-                    mn[r] = fmin(mn[r], v);
-                    mx[r] = fmax(mx[r], v);
+            // the parallelepiped {L <= M p <= H} has centre M^-1 (L + H) / 2 and
+            // half extent sum_a |M^-1_ra| (H_a - L_a) / 2 along index axis r
+            const double id = 1.0 / det;
+            double mn[3], mx[3];
+            for (int r = 0; r < 3; ++r) {
+                double cen = 0.0, ext = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double w = inv[3 * r + a] * id;
+                    cen += w * (0.5 * ((double)p.Lq[a] + (double)p.Hq[a]));
+                    ext += fabs(w) * (0.5 * ((double)p.Hq[a] - (double)p.Lq[a]));
                 }
+                mn[r] = cen - ext;
+                mx[r] = cen + ext;
             }
             const double lim = (double)kBoxRange;
             for (int r = 0; r < 3; ++r)
