@@ -67,6 +67,7 @@ typedef struct obb_mesh obb_mesh;
 typedef struct obb_lattice obb_lattice;
 typedef struct obb_layer obb_layer;
 typedef struct obb_tree obb_tree;
+typedef struct obb_mlp obb_mlp;
 
 /* A world-space oriented box: centre, first two unit axes (axis2 = axis0 x
  * axis1), half extents along the three axes.  48 bytes. */
@@ -217,8 +218,11 @@ obb_status obb_layer_init(obb_ctx* ctx, const obb_lattice* lat, const int32_t* a
                           obb_layer** out);
 
 typedef struct {
-    int32_t rounds;   /* partition rounds per step (stop earlier when a round accepts nothing); <= 0: 16 */
-    int32_t refit;    /* 1: run the box-parameter update after the partition rounds */
+    int32_t rounds;         /* partition rounds per step (stop earlier when a round accepts nothing); <= 0: 16 */
+    int32_t refit;          /* box-parameter update after the rounds: 0 none, 1 covariance frame,
+                               2 rotation descent, 3 both (covariance first) */
+    int32_t descent_steps;  /* descent steps per iteration when refit & 2; <= 0: 2 */
+    int32_t reserved;
 } obb_step_opts;
 
 typedef struct {
@@ -243,8 +247,16 @@ typedef struct {
  * among all proposals whose source or target cluster is its source or
  * target, so accepted moves touch disjoint clusters and the layer total
  * drops by exactly the sum of their gains.
- * Refit (opts->refit): new frame from the covariance eigenvectors, tight
- * bounds, exact count; kept only when the outer volume strictly drops.
+ * Box update (opts->refit), each kept only when the exact outer volume
+ * strictly drops: (1) covariance frame -- eigenvectors of the cluster's
+ * area-weighted covariance, tight bounds, exact count; only clusters whose
+ * membership changed since their last try are recomputed (the others would
+ * rebuild the frame already tried); (2) rotation descent, the perturbation
+ * search of Sec. 4.2.1 step 2 -- six probes per cluster rotate its frame
+ * about each of its axes by +-theta, rational rotation cos = (1 - t^2)/(1 +
+ * t^2), sin = 2t/(1 + t^2), t = 2^-(5 + level), the best probe kept when it
+ * lowers the exact count, else level += 1 (theta halves; clusters at level 8
+ * stop; a membership change resets level to 0).
  * stats may be NULL; when given, the call synchronises. */
 obb_status obb_lloyd_step(obb_ctx* ctx, obb_layer* layer, const obb_step_opts* opts, obb_step_stats* stats);
 
@@ -271,7 +283,7 @@ typedef struct {
     int32_t depth;    /* levels below the root; 2^depth leaves */
     int32_t iters;    /* Lloyd iterations per level (stop early when one changes nothing) */
     int32_t rounds;   /* partition rounds per iteration; <= 0: 16 */
-    int32_t refit;    /* run the box-parameter update in each iteration */
+    int32_t refit;    /* box-parameter update in each iteration (obb_step_opts.refit) */
 } obb_tree_opts;
 
 /* Binary OBB tree by top-down decomposition (Sec. 4.2.2): the root box
@@ -295,6 +307,55 @@ int32_t obb_tree_depth(const obb_tree* tree);
  * h_0 h_1 h_2.  Either pointer may be NULL. */
 obb_status obb_tree_score(obb_ctx* ctx, const obb_tree* tree, double* points, double* volume);
 void obb_tree_free(obb_tree* tree);
+
+/* ---------------------------------------------------- learned surrogate (e) */
+
+/* A learned screen for the partition rounds of obb_lloyd_step (the paper
+ * counts every candidate with its GPU estimator, Sec. 4.1 and Sec. 5; here a
+ * small network predicts outer volumes so that only the most promising moves
+ * are counted exactly -- the exact count still decides every move).
+ * Features of a quantised box (OBB_SURROGATE_INPUTS floats): centre of the
+ * box in index space / N (3), unit normals of slabs 0 and 1 (6), half widths
+ * (H_a - L_a) / (2 |n_a|) / N (3), then an 8^3 patch of occupancy bits sampled
+ * at the points M^-1 v, v_a = L_a + (H_a - L_a)(2 s_a + 1) / 16 (x fastest),
+ * rounded to the nearest lattice point (0 outside [0, N)^3); L = ceil(lo/256),
+ * H = floor(hi/256), M = n; FP64 in a fixed order.
+ * Network: 524 -> 128 -> 128 -> 128 -> 1, ReLU, sigmoid output = predicted
+ * empty fraction; predicted outer volume = fraction x prod(H_a - L_a + 1) /
+ * |det n|.  Parameters (flat float32, obb_mlp_num_params()): W1 [524][128],
+ * b1, W2 [128][128], b2, W3 [128][128], b3, W4 [128][1], b4.  Training: mean
+ * squared error of the fraction, Adam (0.9, 0.999, 1e-8) on FP32 master
+ * weights; inference with half_weights uses an FP16 copy, FP32 accumulation. */
+#define OBB_SURROGATE_INPUTS 524
+obb_status obb_mlp_create(obb_ctx* ctx, uint64_t seed, obb_mlp** out);
+void obb_mlp_free(obb_mlp* mlp);
+int64_t obb_mlp_num_params(void);
+obb_status obb_mlp_params(obb_ctx* ctx, const obb_mlp* mlp, float* out, int32_t on_device);
+obb_status obb_mlp_set_params(obb_ctx* ctx, obb_mlp* mlp, const float* in, int32_t on_device);
+/* features float [K][524] of K quantised boxes on a lattice */
+obb_status obb_surrogate_features(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* boxes, int64_t K, float* feats,
+                                  int32_t on_device);
+/* out float [B]: predicted empty fractions */
+obb_status obb_mlp_forward(obb_ctx* ctx, const obb_mlp* mlp, const float* feats, int64_t B, float* out,
+                           int32_t half_weights, int32_t on_device);
+/* loss and gradients (flat, obb_mlp_num_params() floats) of the mean squared
+ * error against target fractions float [B], FP32 weights; no update */
+obb_status obb_mlp_gradients(obb_ctx* ctx, obb_mlp* mlp, const float* feats, const float* target, int64_t B,
+                             float* grads, float* loss, int32_t on_device);
+/* one Adam step on a mini-batch; *loss (optional) = the batch loss before the step */
+obb_status obb_mlp_train_step(obb_ctx* ctx, obb_mlp* mlp, const float* feats, const float* target, int64_t B,
+                              float lr, float* loss, int32_t on_device);
+/* Screen the layer's Lloyd iterations with a surrogate (mlp = NULL turns it
+ * off): in the partition rounds keep, per source cluster, the topk candidate
+ * moves by predicted gain (topk = 0: no move screening); in the refit count
+ * exactly only the new boxes whose predicted outer volume is below 1.05 x the
+ * current exact one.  Every accepted move and refit is still decided by the
+ * exact count.  The surrogate must outlive its use by the layer. */
+obb_status obb_layer_set_surrogate(obb_ctx* ctx, obb_layer* layer, const obb_mlp* mlp, int32_t topk);
+/* The boxes counted exactly in the layer's last partition round and their
+ * exact outer volumes (host arrays, up to cap); *n = how many there were. */
+obb_status obb_layer_last_candidates(obb_ctx* ctx, const obb_layer* layer, obb_qbox* boxes, uint64_t* counts,
+                                     int64_t cap, int64_t* n);
 
 #ifdef __cplusplus
 }

@@ -303,6 +303,11 @@ class Layer:
     n: np.ndarray           # int32 [K, 9]
     bnd: np.ndarray         # int64 [K, 6]
     obv: np.ndarray         # uint64 [K]
+    level: np.ndarray = None  # int32 [K], descent level (theta = 2^-(5 + level))
+
+    def __post_init__(self):
+        if self.level is None:
+            self.level = np.zeros(self.parent.shape[0], dtype=np.int32)
 
     @property
     def K(self):
@@ -310,7 +315,7 @@ class Layer:
 
     def copy(self):
         return Layer(self.assign.copy(), self.parent.copy(), self.frames.copy(), self.n.copy(),
-                     self.bnd.copy(), self.obv.copy())
+                     self.bnd.copy(), self.obv.copy(), self.level.copy())
 
 
 @dataclass
@@ -374,6 +379,9 @@ def lloyd_moves(P: Problem, L: Layer, rounds: int):
             continue
         if rc < 0:
             raise RuntimeError(f"orc_lloyd_moves failed ({rc})")
+        moved = np.nonzero(L.assign != work.assign)[0]
+        L.level[L.assign[moved]] = 0       # a new member set restarts the descent
+        L.level[work.assign[moved]] = 0
         L.assign[:], L.bnd[:], L.obv[:] = work.assign, work.bnd, work.obv
         return [dict(proposals=s.proposals, accepted=s.accepted, gain=s.gain, evals=s.evals)
                 for s in st[:rc]]
@@ -396,10 +404,45 @@ def refit(P: Problem, L: Layer):
         return acc
 
 
-def lloyd_step(P: Problem, L: Layer, rounds: int = 16, do_refit: bool = True):
-    """One Lloyd iteration: partition rounds, then refit."""
+def probe_frame(R, level, p):
+    out = np.zeros(9)
+    L = lib()
+    if not hasattr(L, "_pf_declared"):
+        L.orc_probe_frame.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]
+        L.orc_descent_step.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_int32]
+        L.orc_descent_step.restype = C.c_int
+        L._pf_declared = True
+    L.orc_probe_frame(_p(_c(R, np.float64)), int(level), int(p), _p(out))
+    return out.reshape(3, 3)
+
+
+def descent_step(P: Problem, L: Layer):
+    """One rotation-probe step of the box update (Sec. 4.2.1 step 2, restated)."""
+    probe_frame(np.eye(3), 0, 0)     # declares the C signatures
+    while True:
+        fr, n, bnd, obv, lev = L.frames.copy(), L.n.copy(), L.bnd.copy(), L.obv.copy(), L.level.copy()
+        rc = lib().orc_descent_step(_p(P.U), _p(P.F), P.F.shape[0], _p(L.assign), L.K, _p(P.h), _p(fr), _p(n),
+                                    _p(bnd), _p(obv), _p(lev), _p(P.occ.occ), _p(P.occ.known), P.N)
+        if rc == -3:
+            P.occ.fill_all()
+            continue
+        if rc < 0:
+            raise RuntimeError(f"orc_descent_step failed ({rc})")
+        L.frames[:], L.n[:], L.bnd[:], L.obv[:], L.level[:] = fr, n, bnd, obv, lev
+        return rc
+
+
+def lloyd_step(P: Problem, L: Layer, rounds: int = 16, do_refit=1, descent_steps: int = 2):
+    """One Lloyd iteration: partition rounds, then the box update
+    (do_refit: 0 none, 1 covariance frame, 2 rotation descent, 3 both)."""
     st = lloyd_moves(P, L, rounds)
-    acc = refit(P, L) if do_refit else np.zeros(L.K, dtype=np.uint8)
+    mode = int(do_refit)
+    acc = refit(P, L) if mode & 1 else np.zeros(L.K, dtype=np.uint8)
+    if mode & 2:
+        for _ in range(descent_steps):
+            descent_step(P, L)
     return st, acc
 
 
@@ -439,3 +482,79 @@ def build_tree(P: Problem, depth: int, iters: int, rounds: int = 16):
                 break
         layers.append(L)
     return layers
+
+
+# ---------------------------------------------------------------------------
+# Learned surrogate: its input features and a plain FP64 network
+# ---------------------------------------------------------------------------
+
+SURROGATE_INPUTS = 524
+MLP_HIDDEN = 128
+
+
+def surrogate_features(occ: Occupancy, n, bnd):
+    """Features of quantised boxes: 12 box parameters + an 8^3 occupancy patch
+    sampled in the box's own frame (FP64, fixed order)."""
+    n = _c(n, np.int32).reshape(-1, 9)
+    bnd = _c(bnd, np.int64).reshape(-1, 6)
+    L = lib()
+    if not hasattr(L, "_sf_declared"):
+        L.orc_surrogate_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                             C.c_int64, C.c_void_p]
+        L.orc_surrogate_features.restype = C.c_int
+        L._sf_declared = True
+    occ.fill_boxes(n, bnd)
+    out = np.zeros((n.shape[0], SURROGATE_INPUTS), np.float32)
+    rc = L.orc_surrogate_features(_p(occ.occ), _p(occ.known), occ.N, _p(n), _p(bnd), n.shape[0], _p(out))
+    if rc == -3:
+        occ.fill_all()
+        rc = L.orc_surrogate_features(_p(occ.occ), _p(occ.known), occ.N, _p(n), _p(bnd), n.shape[0], _p(out))
+    if rc:
+        raise RuntimeError(f"orc_surrogate_features failed ({rc})")
+    return out
+
+
+def mlp_unpack(params):
+    """Flat parameter vector -> [(W, b)] for 524 -> 128 -> 128 -> 128 -> 1 (W [in][out])."""
+    p = np.asarray(params, dtype=np.float64)
+    sizes = [(SURROGATE_INPUTS, MLP_HIDDEN), (MLP_HIDDEN, MLP_HIDDEN), (MLP_HIDDEN, MLP_HIDDEN), (MLP_HIDDEN, 1)]
+    out, o = [], 0
+    for fi, fo in sizes:
+        W = p[o:o + fi * fo].reshape(fi, fo)
+        o += fi * fo
+        b = p[o:o + fo]
+        o += fo
+        out.append((W, b))
+    assert o == p.size
+    return out
+
+
+def mlp_forward(params, X):
+    """ReLU hidden layers, sigmoid output (the predicted empty fraction); FP64."""
+    layers = mlp_unpack(params)
+    h = np.asarray(X, dtype=np.float64)
+    acts = [h]
+    for i, (W, b) in enumerate(layers):
+        z = h @ W + b
+        h = np.maximum(z, 0.0) if i < 3 else 1.0 / (1.0 + np.exp(-z))
+        acts.append(h)
+    return h[:, 0], acts
+
+
+def mlp_loss_grad(params, X, T):
+    """Mean squared error of the fraction and its gradient (backpropagation), FP64."""
+    layers = mlp_unpack(params)
+    y, acts = mlp_forward(params, X)
+    B = y.shape[0]
+    T = np.asarray(T, dtype=np.float64)
+    loss = float(np.mean((y - T) ** 2))
+    dz = (2.0 * (y - T) / B * y * (1.0 - y))[:, None]
+    grads = [None] * 4
+    for i in range(3, -1, -1):
+        W, b = layers[i]
+        h_in = acts[i]
+        grads[i] = (h_in.T @ dz, dz.sum(axis=0))
+        if i > 0:
+            dz = (dz @ W.T) * (acts[i] > 0.0)
+    flat = np.concatenate([np.concatenate([g[0].ravel(), g[1].ravel()]) for g in grads])
+    return loss, flat

@@ -838,3 +838,155 @@ int orc_median_split(const int32_t* U, const int32_t* F, int64_t nt, const int32
     free(size); free(buf); free(start); free(fill); free(grp);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Surrogate features (the learned screen's inputs), FP64 in a fixed order    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * For each quantised box: 12 box parameters (centre of the index-space box /
+ * N, unit normals of slabs 0 and 1, half widths / N) and the occupancy bits of
+ * an 8^3 patch of points M^-1 v, v_a = L_a + (H_a - L_a)(2 s_a + 1)/16, each
+ * rounded to the nearest lattice point (floor(p + 1/2)); 0 outside [0,N)^3.
+ * Returns 0, or -3 if an in-domain column needed is not computed.
+ */
+int orc_surrogate_features(const uint8_t* occ, const uint8_t* colmask, int32_t N, const int32_t* n,
+                           const int64_t* bnd, int64_t K, float* feats)
+{
+    for (int64_t b = 0; b < K; ++b) {
+        const int32_t* nb = n + 9 * b;
+        double M[9], L[3], H[3];
+        for (int i = 0; i < 9; ++i) M[i] = (double)nb[i];
+        for (int a = 0; a < 3; ++a) {
+            L[a] = (double)(-floordiv64(-bnd[6 * b + 2 * a], 256));
+            H[a] = (double)floordiv64(bnd[6 * b + 2 * a + 1], 256);
+        }
+        double c00 = M[4] * M[8] - M[5] * M[7];
+        double c01 = M[5] * M[6] - M[3] * M[8];
+        double c02 = M[3] * M[7] - M[4] * M[6];
+        double det = (M[0] * c00 + M[1] * c01) + M[2] * c02;
+        double adj[9] = {c00, M[2] * M[7] - M[1] * M[8], M[1] * M[5] - M[2] * M[4],
+                         c01, M[0] * M[8] - M[2] * M[6], M[2] * M[3] - M[0] * M[5],
+                         c02, M[1] * M[6] - M[0] * M[7], M[0] * M[4] - M[1] * M[3]};
+        double inv[9];
+        for (int i = 0; i < 9; ++i) inv[i] = det != 0.0 ? adj[i] / det : 0.0;
+        float* f = feats + 524 * b;
+        for (int t = 0; t < 12; ++t) {
+            double v;
+            if (t < 3) {
+                double mid[3];
+                for (int a = 0; a < 3; ++a) mid[a] = (L[a] + H[a]) * 0.5;
+                v = (inv[3 * t] * mid[0] + inv[3 * t + 1] * mid[1]) + inv[3 * t + 2] * mid[2];
+                v = v / (double)N;
+            } else if (t < 9) {
+                int a = (t - 3) / 3, c = (t - 3) % 3;
+                double nn = sqrt((M[3 * a] * M[3 * a] + M[3 * a + 1] * M[3 * a + 1]) + M[3 * a + 2] * M[3 * a + 2]);
+                v = nn > 0.0 ? M[3 * a + c] / nn : 0.0;
+            } else {
+                int a = t - 9;
+                double nn = sqrt((M[3 * a] * M[3 * a] + M[3 * a + 1] * M[3 * a + 1]) + M[3 * a + 2] * M[3 * a + 2]);
+                v = nn > 0.0 ? ((H[a] - L[a]) * 0.5 / nn) / (double)N : 0.0;
+            }
+            f[t] = (float)v;
+        }
+        for (int s = 0; s < 512; ++s) {
+            int sx = s & 7, sy = (s >> 3) & 7, sz = s >> 6;
+            double fr[3] = {(double)(2 * sx + 1) / 16.0, (double)(2 * sy + 1) / 16.0, (double)(2 * sz + 1) / 16.0};
+            double v[3];
+            for (int a = 0; a < 3; ++a) v[a] = L[a] + (H[a] - L[a]) * fr[a];
+            int64_t idx[3];
+            for (int r = 0; r < 3; ++r) {
+                double p = (inv[3 * r] * v[0] + inv[3 * r + 1] * v[1]) + inv[3 * r + 2] * v[2];
+                double c = floor(p + 0.5);
+                idx[r] = fabs(c) < 1e15 ? (int64_t)c : -1;
+            }
+            float bit = 0.f;
+            if (idx[0] >= 0 && idx[0] < N && idx[1] >= 0 && idx[1] < N && idx[2] >= 0 && idx[2] < N) {
+                if (!colmask[idx[2] * N + idx[1]]) return -3;
+                bit = (float)occ[(idx[2] * N + idx[1]) * (int64_t)N + idx[0]];
+            }
+            f[12 + s] = bit;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Box-parameter descent: rotation probes (the perturbation search of the   */
+/* box update, Sec. 4.2.1 step 2)                                             */
+/* ------------------------------------------------------------------------- */
+
+/* Frame of probe p (axis p / 2, sign + for even p) rotated by the rational
+ * rotation cos = (1 - t^2)/(1 + t^2), sin = 2t/(1 + t^2), t = 2^-(5 + level). */
+void orc_probe_frame(const double* R, int32_t level, int32_t p, double* O)
+{
+    double t = ldexp(1.0, -(5 + level));
+    double t2 = t * t;
+    double den = 1.0 + t2;
+    double c = (1.0 - t2) / den;
+    double sn = (2.0 * t) / den;
+    double ss = (p & 1) ? -sn : sn;
+    int a = p >> 1, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+    for (int j = 0; j < 3; ++j) {
+        O[3 * a + j] = R[3 * a + j];
+        O[3 * b1 + j] = c * R[3 * b1 + j] + ss * R[3 * b2 + j];
+        O[3 * b2 + j] = c * R[3 * b2 + j] - ss * R[3 * b1 + j];
+    }
+}
+
+/*
+ * One descent step for every cluster below level 8: the six probes' tight
+ * boxes are counted exactly; the lowest count (ties -> smaller probe index)
+ * replaces the cluster's box when strictly below its outer volume, otherwise
+ * the cluster's level rises by one.  Returns the number of boxes replaced.
+ */
+int orc_descent_step(const int32_t* U, const int32_t* F, int64_t nt, const int32_t* assign, int32_t K,
+                     const double* h, double* frames, int32_t* n, int64_t* bnd, uint64_t* obv, int32_t* level,
+                     const uint8_t* occ, const uint8_t* colmask, int32_t N)
+{
+    int64_t* size = (int64_t*)calloc((size_t)K, sizeof(int64_t));
+    int64_t* start = (int64_t*)calloc((size_t)K + 1, sizeof(int64_t));
+    int64_t* fill = (int64_t*)calloc((size_t)K, sizeof(int64_t));
+    int32_t* members = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nt > 0 ? nt : 1));
+    for (int64_t t = 0; t < nt; ++t) size[assign[t]]++;
+    for (int32_t k = 0; k < K; ++k) start[k + 1] = start[k] + size[k];
+    for (int64_t t = 0; t < nt; ++t) members[start[assign[t]] + fill[assign[t]]++] = (int32_t)t;
+    int kept = 0, err = 0;
+    for (int32_t k = 0; k < K && !err; ++k) {
+        if (level[k] >= 8) continue;
+        uint64_t best = UINT64_MAX;
+        int bp = -1;
+        double bR[9];
+        int32_t bn[9];
+        int64_t bb[6];
+        for (int p = 0; p < 6; ++p) {
+            double R[9];
+            int32_t nn[9];
+            int64_t b6[6];
+            orc_probe_frame(frames + 9 * k, level[k], p, R);
+            orc_frame_normals(R, 1, h, nn);
+            bounds_without(U, F, members + start[k], size[k], -1, nn, b6);
+            uint64_t c;
+            if (count_one(occ, colmask, N, nn, b6, &c)) { err = -3; break; }
+            if (c < best) {
+                best = c;
+                bp = p;
+                memcpy(bR, R, sizeof(bR));
+                memcpy(bn, nn, sizeof(bn));
+                memcpy(bb, b6, sizeof(bb));
+            }
+        }
+        if (err) break;
+        if (bp >= 0 && best < obv[k]) {
+            memcpy(frames + 9 * k, bR, sizeof(bR));
+            memcpy(n + 9 * k, bn, sizeof(bn));
+            memcpy(bnd + 6 * k, bb, sizeof(bb));
+            obv[k] = best;
+            ++kept;
+        } else {
+            level[k] += 1;
+        }
+    }
+    free(size); free(start); free(fill); free(members);
+    return err ? err : kept;
+}

@@ -36,7 +36,8 @@ class ObbError(RuntimeError):
 
 
 class StepOpts(C.Structure):
-    _fields_ = [("rounds", C.c_int32), ("refit", C.c_int32)]
+    _fields_ = [("rounds", C.c_int32), ("refit", C.c_int32), ("descent_steps", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -95,12 +96,24 @@ def load(build_if_missing: bool = True):
         "obb_build_tree": [vp, vp, C.POINTER(TreeOpts), C.POINTER(vp)],
         "obb_tree_read": [vp, vp, i32, vp, vp, vp, vp, vp],
         "obb_tree_score": [vp, vp, vp, vp],
+        "obb_mlp_create": [vp, C.c_uint64, C.POINTER(vp)],
+        "obb_mlp_params": [vp, vp, vp, i32],
+        "obb_mlp_set_params": [vp, vp, vp, i32],
+        "obb_surrogate_features": [vp, vp, vp, i64, vp, i32],
+        "obb_mlp_forward": [vp, vp, vp, i64, vp, i32, i32],
+        "obb_mlp_gradients": [vp, vp, vp, vp, i64, vp, vp, i32],
+        "obb_mlp_train_step": [vp, vp, vp, vp, i64, C.c_float, vp, i32],
+        "obb_layer_set_surrogate": [vp, vp, vp, i32],
+        "obb_layer_last_candidates": [vp, vp, vp, vp, i64, C.POINTER(i64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = C.c_int32
-    for name in ("obb_destroy", "obb_mesh_free", "obb_lattice_free", "obb_layer_free", "obb_tree_free"):
+    L.obb_mlp_num_params.argtypes = []
+    L.obb_mlp_num_params.restype = C.c_int64
+    for name in ("obb_destroy", "obb_mesh_free", "obb_lattice_free", "obb_layer_free", "obb_tree_free",
+                 "obb_mlp_free"):
         getattr(L, name).argtypes = [vp]
         getattr(L, name).restype = None
     L.obb_last_error.argtypes = [vp]
@@ -120,7 +133,10 @@ def exported_symbols():
             "obb_mesh_create", "obb_mesh_free", "obb_build_occupancy", "obb_lattice_desc", "obb_lattice_free",
             "obb_quantize_boxes", "obb_outer_volume_q", "obb_outer_volume", "obb_outer_volume_q_noalloc", "obb_layer_init", "obb_lloyd_step",
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
-            "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free"]
+            "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free",
+            "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
+            "obb_surrogate_features", "obb_mlp_forward", "obb_mlp_gradients", "obb_mlp_train_step",
+            "obb_layer_set_surrogate", "obb_layer_last_candidates"]
 
 
 def _is_torch(x):
@@ -294,8 +310,9 @@ class Context:
         self.check(self.lib.obb_layer_init(self.h, lat.h, pa, pp, int(K), pf, dev, C.byref(h)))
         return Layer(self, h, lat, K)
 
-    def lloyd_step(self, layer, rounds=16, refit=True, stats=True):
-        o = StepOpts(int(rounds), 1 if refit else 0)
+    def lloyd_step(self, layer, rounds=16, refit=True, stats=True, descent_steps=0):
+        """refit: False/0 none, True/1 covariance frame, 2 rotation descent, 3 both."""
+        o = StepOpts(int(rounds), int(refit), int(descent_steps), 0)
         st = StepStats()
         self.check(self.lib.obb_lloyd_step(self.h, layer.h, C.byref(o), C.byref(st) if stats else None))
         return st.as_dict() if stats else None
@@ -317,9 +334,95 @@ class Context:
         self.check(self.lib.obb_layer_split(self.h, layer.h, child.ctypes.data_as(C.c_void_p), 0))
         return child
 
+    # ------------------------------------------------------------- surrogate
+    SURROGATE_INPUTS = 524
+
+    def mlp_create(self, seed=0):
+        h = C.c_void_p()
+        self.check(self.lib.obb_mlp_create(self.h, C.c_uint64(seed), C.byref(h)))
+        return Mlp(self, h)
+
+    def mlp_num_params(self):
+        return int(self.lib.obb_mlp_num_params())
+
+    def mlp_params(self, mlp):
+        out = np.zeros(self.mlp_num_params(), np.float32)
+        self.check(self.lib.obb_mlp_params(self.h, mlp.h, out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def mlp_set_params(self, mlp, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.mlp_num_params()
+        self.check(self.lib.obb_mlp_set_params(self.h, mlp.h, p.ctypes.data_as(C.c_void_p), 0))
+
+    def surrogate_features(self, lat, qboxes, out=None):
+        """[K, 524] float32 features (numpy in -> numpy out, CUDA tensors -> CUDA tensor)."""
+        p, dev, keep = _arg(qboxes, QBOX_DTYPE)
+        K = _count(qboxes, keep, 88)
+        if out is None:
+            if dev:
+                import torch
+                out = torch.empty((K, self.SURROGATE_INPUTS), dtype=torch.float32, device=f"cuda:{self.device}")
+            else:
+                out = np.zeros((K, self.SURROGATE_INPUTS), np.float32)
+        po = C.c_void_p(out.data_ptr()) if dev else out.ctypes.data_as(C.c_void_p)
+        self.check(self.lib.obb_surrogate_features(self.h, lat.h, p, K, po, dev))
+        return out
+
+    def mlp_forward(self, mlp, feats, half=True):
+        p, dev, keep = _arg(feats, np.float32)
+        B = (feats.shape[0] if dev else keep.shape[0])
+        if dev:
+            import torch
+            out = torch.empty(B, dtype=torch.float32, device=f"cuda:{self.device}")
+            po = C.c_void_p(out.data_ptr())
+        else:
+            out = np.zeros(B, np.float32)
+            po = out.ctypes.data_as(C.c_void_p)
+        self.check(self.lib.obb_mlp_forward(self.h, mlp.h, p, B, po, 1 if half else 0, dev))
+        return out
+
+    def mlp_gradients(self, mlp, feats, target):
+        X = np.ascontiguousarray(feats, np.float32)
+        T = np.ascontiguousarray(target, np.float32)
+        g = np.zeros(self.mlp_num_params(), np.float32)
+        loss = np.zeros(1, np.float32)
+        self.check(self.lib.obb_mlp_gradients(self.h, mlp.h, X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p),
+                                              X.shape[0], g.ctypes.data_as(C.c_void_p),
+                                              loss.ctypes.data_as(C.c_void_p), 0))
+        return g, float(loss[0])
+
+    def mlp_train_step(self, mlp, feats, target, lr, want_loss=False):
+        """One Adam step; feats/target are CUDA tensors (device) or numpy arrays."""
+        if _is_torch(feats) and feats.is_cuda:
+            loss = np.zeros(1, np.float32)
+            self.check(self.lib.obb_mlp_train_step(self.h, mlp.h, C.c_void_p(feats.data_ptr()),
+                                                   C.c_void_p(target.data_ptr()), feats.shape[0], C.c_float(lr),
+                                                   None, 1))
+            return None
+        X = np.ascontiguousarray(feats, np.float32)
+        T = np.ascontiguousarray(target, np.float32)
+        loss = np.zeros(1, np.float32)
+        self.check(self.lib.obb_mlp_train_step(self.h, mlp.h, X.ctypes.data_as(C.c_void_p),
+                                               T.ctypes.data_as(C.c_void_p), X.shape[0], C.c_float(lr),
+                                               loss.ctypes.data_as(C.c_void_p), 0))
+        return float(loss[0])
+
+    def layer_set_surrogate(self, layer, mlp, topk):
+        self.check(self.lib.obb_layer_set_surrogate(self.h, layer.h, mlp.h if mlp is not None else None, int(topk)))
+
+    def layer_last_candidates(self, layer, cap=1 << 20):
+        q = np.zeros(cap, QBOX_DTYPE)
+        c = np.zeros(cap, np.uint64)
+        n = C.c_int64()
+        self.check(self.lib.obb_layer_last_candidates(self.h, layer.h, q.ctypes.data_as(C.c_void_p),
+                                                      c.ctypes.data_as(C.c_void_p), cap, C.byref(n)))
+        m = min(n.value, cap)
+        return q[:m].copy(), c[:m].copy()
+
     # ------------------------------------------------------------------ tree
     def build_tree(self, lat, depth, iters, rounds=16, refit=True):
-        o = TreeOpts(int(depth), int(iters), int(rounds), 1 if refit else 0)
+        o = TreeOpts(int(depth), int(iters), int(rounds), int(refit))
         h = C.c_void_p()
         self.check(self.lib.obb_build_tree(self.h, lat.h, C.byref(o), C.byref(h)))
         return Tree(self, h, lat)
@@ -413,6 +516,10 @@ class Layer(_Handle):
         super().__init__(ctx, h)
         self.lat = lat
         self.K = K
+
+
+class Mlp(_Handle):
+    _free = "obb_mlp_free"
 
 
 class Tree(_Handle):

@@ -18,6 +18,7 @@ namespace obbv {
 constexpr int kS = 8;            // fixed-point fraction bits of snapped vertices
 constexpr int kQ = 24;           // fraction bits of quantised normals
 constexpr int kMaxN = 2048;      // lattice points per axis
+constexpr int kSurrogateInputs = 524;   // 12 box parameters + 8^3 occupancy patch
 constexpr int64_t kBoxRange = int64_t(1) << 20;  // |index-space AABB| limit of a counted box
 #ifndef OBB_TILE_K
 #define OBB_TILE_K 16
@@ -141,6 +142,8 @@ struct obb_layer {
     unsigned long long* d_best = nullptr;  // [K] best proposal key per cluster
     int64_t* d_stats = nullptr;      // device counters (see lloyd.cu)
     void* aux = nullptr;             // per-layer scratch owned by lloyd.cu
+    const obb_mlp* mlp = nullptr;    // optional surrogate screening candidate moves
+    int32_t topk = 0;                // candidates kept per source cluster when screening
 };
 
 struct obb_tree {
@@ -196,6 +199,13 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
 obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb_step_stats* st);
 void layer_destroy(obb_layer* L);
 obb_status rebuild_members(obb_ctx* ctx, obb_layer* L);
+obb_status layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, int32_t topk);
+obb_status layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox* out, uint64_t* counts, int64_t cap,
+                                 int64_t* n);
+
+// surrogate.cu: features of boxes [0, *d_K) and predicted outer volumes (FP16 weights)
+obb_status surrogate_predict(obb_ctx* ctx, const obb_mlp* mlp, const obb_lattice* lat, const obb_qbox* d_boxes,
+                             const int32_t* d_K, int64_t cap, float* d_feats, float* d_pred);
 
 // tree.cu
 obb_status build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts* opts, obb_tree* tree);

@@ -297,7 +297,7 @@ __global__ void k_accept(const Cand* __restrict__ cand, const int32_t* __restric
                          const unsigned long long* __restrict__ best, const obb_qbox* __restrict__ evals,
                          const uint64_t* __restrict__ ecount, int32_t* __restrict__ assign,
                          obb_qbox* __restrict__ q, uint64_t* __restrict__ obv, int32_t* __restrict__ size,
-                         int64_t* __restrict__ stats)
+                         int64_t* __restrict__ stats, uint8_t* __restrict__ dirty, int32_t* __restrict__ level)
 {
     int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ctr[kCtrCand]) return;
@@ -315,6 +315,10 @@ __global__ void k_accept(const Cand* __restrict__ cand, const int32_t* __restric
     }
     size[c.s] -= 1;
     size[k] += 1;
+    dirty[c.s] = 1;
+    dirty[k] = 1;
+    level[c.s] = 0;   // a new member set restarts the box-parameter search
+    level[k] = 0;
     atomicAdd((unsigned long long*)&stats[kStAccepted], 1ull);
     atomicAdd((unsigned long long*)&stats[kStGain], (unsigned long long)c.gain);
 }
@@ -365,9 +369,11 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_moments(const float* __restrict__ V, const int32_t* __restrict__ F,
                                                 const int32_t* __restrict__ members,
                                                 const int32_t* __restrict__ start,
-                                                const LatticeFrame* __restrict__ f, double* __restrict__ mom)
+                                                const LatticeFrame* __restrict__ f, double* __restrict__ mom,
+                                                const uint8_t* __restrict__ dirty)
 {
     const int32_t k = blockIdx.x;
+    if (dirty && !dirty[k]) return;
     const int32_t b0 = start[k], b1 = start[k + 1];
     const double cx = f->center[0], cy = f->center[1], cz = f->center[2];
     Comp acc[10];
@@ -481,10 +487,10 @@ __device__ void jacobi3(const double c6[6], double R[9])
 }
 
 __global__ void k_frames_from_moments(const double* __restrict__ mom, const double* __restrict__ fallback,
-                                      int32_t K, double* __restrict__ out)
+                                      int32_t K, double* __restrict__ out, const uint8_t* __restrict__ dirty)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
+    if (k >= K || (dirty && !dirty[k])) return;
     const double* m = mom + 10 * (int64_t)k;
     double* R = out + 9 * (int64_t)k;
     const double A = m[0];
@@ -501,10 +507,10 @@ __global__ void k_frames_from_moments(const double* __restrict__ mom, const doub
 
 // n_ab = rint(2^24 ((R_ab h_b) / h_max)), each step correctly rounded
 __global__ void k_normals(const double* __restrict__ frames, int32_t K, const LatticeFrame* __restrict__ f,
-                          obb_qbox* __restrict__ q)
+                          obb_qbox* __restrict__ q, const uint8_t* __restrict__ active)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
+    if (k >= K || (active && !active[k])) return;
     const double hm = f->hmax;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
@@ -519,10 +525,15 @@ __global__ void k_normals(const double* __restrict__ frames, int32_t K, const La
 template <int NT>
 __global__ void __launch_bounds__(NT) k_tight(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
                                               const int32_t* __restrict__ members,
-                                              const int32_t* __restrict__ start, obb_qbox* __restrict__ q)
+                                              const int32_t* __restrict__ start, obb_qbox* __restrict__ q,
+                                              int32_t per_cluster, const uint8_t* __restrict__ active)
 {
-    const int32_t k = blockIdx.x;
-    const int32_t b0 = start[k], b1 = start[k + 1];
+    // box blockIdx.x belongs to cluster blockIdx.x / per_cluster
+    const int32_t bx = blockIdx.x;
+    if (active && !active[bx]) return;
+    const int32_t cl = bx / per_cluster;
+    const int32_t b0 = start[cl], b1 = start[cl + 1];
+    const int32_t k = bx;
     int32_t n[9];
     for (int i = 0; i < 9; ++i) n[i] = q[k].n[i];
     int64_t v[6];
@@ -583,6 +594,215 @@ __global__ void k_total(const uint64_t* __restrict__ obv, int32_t K, int64_t* __
     }
 }
 
+// ------------------------------------------------------- surrogate screening
+
+__device__ __forceinline__ uint32_t float_key(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// predicted gain of each candidate record from predicted outer volumes of its boxes
+__global__ void k_screen_score(const Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
+                               const uint64_t* __restrict__ obv, const float* __restrict__ pred,
+                               unsigned long long* __restrict__ key, uint8_t* __restrict__ kept)
+{
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ctr[kCtrCand]) return;
+    const Cand c = cand[r];
+    const float rem = (float)obv[c.s] - pred[c.e_shr];
+    float best = -3.0e38f;
+    for (int i = 0; i < c.nk; ++i) {
+        const float add = c.e_gro[i] >= 0 ? pred[c.e_gro[i]] - (float)obv[c.k[i]] : 0.f;
+        best = fmaxf(best, rem - add);
+    }
+    key[r] = ((unsigned long long)float_key(best) << 32) | (unsigned long long)(0xffffffffu - (uint32_t)c.t);
+    kept[r] = 0;
+}
+
+__global__ void k_screen_pick(const Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
+                              const unsigned long long* __restrict__ key, const uint8_t* __restrict__ kept,
+                              unsigned long long* __restrict__ slot)
+{
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ctr[kCtrCand] || kept[r]) return;
+    atomicMax(&slot[cand[r].s], key[r]);
+}
+
+__global__ void k_screen_mark(const Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
+                              const unsigned long long* __restrict__ key, uint8_t* __restrict__ kept,
+                              const unsigned long long* __restrict__ slot)
+{
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ctr[kCtrCand] || kept[r]) return;
+    if (slot[cand[r].s] == key[r]) kept[r] = 1;
+}
+
+// keep the selected records' boxes in a new evaluation list; the others propose nothing
+__global__ void k_screen_compact(Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
+                                 const uint8_t* __restrict__ kept, const obb_qbox* __restrict__ evals,
+                                 obb_qbox* __restrict__ evals2, int32_t* __restrict__ n2)
+{
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ctr[kCtrCand]) return;
+    Cand c = cand[r];
+    if (!kept[r]) {
+        cand[r].nk = 0;
+        return;
+    }
+    int need = 1;
+    for (int i = 0; i < c.nk; ++i) need += c.e_gro[i] >= 0;
+    int32_t base = atomicAdd(n2, need);
+    evals2[base] = evals[c.e_shr];
+    c.e_shr = base++;
+    for (int i = 0; i < c.nk; ++i)
+        if (c.e_gro[i] >= 0) {
+            evals2[base] = evals[c.e_gro[i]];
+            c.e_gro[i] = base++;
+        }
+    cand[r] = c;
+}
+
+// refit screening: count exactly only the new boxes predicted to improve
+__global__ void k_refit_screen(const float* __restrict__ pred, const uint64_t* __restrict__ obv, int32_t K,
+                               const obb_qbox* __restrict__ newq, obb_qbox* __restrict__ evals2,
+                               int32_t* __restrict__ map, int32_t* __restrict__ n2, float slack)
+{
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    if (!(pred[k] < (float)obv[k] * (1.0f + slack))) return;
+    const int32_t i = atomicAdd(n2, 1);
+    evals2[i] = newq[k];
+    map[i] = k;
+}
+
+__global__ void k_refit_accept_mapped(const double* __restrict__ newframe, const obb_qbox* __restrict__ newq,
+                                      const uint64_t* __restrict__ cnt, const int32_t* __restrict__ map,
+                                      const int32_t* __restrict__ n2, double* __restrict__ frames,
+                                      obb_qbox* __restrict__ q, uint64_t* __restrict__ obv,
+                                      int64_t* __restrict__ stats)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *n2) return;
+    const int32_t k = map[i];
+    if (cnt[i] < obv[k]) {
+        for (int t = 0; t < 9; ++t) frames[9 * (int64_t)k + t] = newframe[9 * (int64_t)k + t];
+        q[k] = newq[k];
+        obv[k] = cnt[i];
+        atomicAdd((unsigned long long*)&stats[kStRefits], 1ull);
+    }
+}
+
+// clusters whose membership changed since their last covariance refit
+__global__ void k_dirty_compact(const uint8_t* __restrict__ dirty, const uint8_t* __restrict__ screen, int32_t K,
+                                const obb_qbox* __restrict__ newq, obb_qbox* __restrict__ evals2,
+                                int32_t* __restrict__ map, int32_t* __restrict__ n2)
+{
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K || !dirty[k] || (screen && !screen[k])) return;
+    const int32_t i = atomicAdd(n2, 1);
+    evals2[i] = newq[k];
+    map[i] = k;
+}
+
+// surrogate screen of the covariance refit: keep predicted improvements (5% slack)
+__global__ void k_refit_keep(const float* __restrict__ pred, const uint64_t* __restrict__ obv, int32_t K,
+                             uint8_t* __restrict__ keep)
+{
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    keep[k] = pred[k] < (float)obv[k] * 1.05f;
+}
+
+// ---- box-parameter descent (the perturbation search of the box update) ----
+//
+// Probe p of cluster k rotates k's frame about its own axis a = p / 2 by
+// +-theta with the rational rotation cos = (1 - t^2) / (1 + t^2),
+// sin = 2 t / (1 + t^2), t = 2^-(5 + level_k): every probe frame is a fixed
+// sequence of correctly rounded FP64 operations.
+constexpr int kProbes = 6;
+constexpr int kDescentMaxLevel = 8;
+
+__global__ void k_probe_frames(const double* __restrict__ frames, const int32_t* __restrict__ level, int32_t K,
+                               double* __restrict__ pf, uint8_t* __restrict__ active)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K * kProbes) return;
+    const int32_t k = i / kProbes, p = i % kProbes;
+    const bool on = level[k] < kDescentMaxLevel;
+    active[i] = on;
+    if (!on) return;
+    const double t = ldexp(1.0, -(5 + level[k]));
+    const double t2 = __dmul_rn(t, t);
+    const double den = __dadd_rn(1.0, t2);
+    const double c = __ddiv_rn(__dsub_rn(1.0, t2), den);
+    const double sn = __ddiv_rn(__dmul_rn(2.0, t), den);
+    const double ss = (p & 1) ? -sn : sn;
+    const int a = p >> 1, b1 = (a + 1) % 3, b2 = (a + 2) % 3;
+    const double* R = frames + 9 * (int64_t)k;
+    double* O = pf + 9 * (int64_t)i;
+    for (int j = 0; j < 3; ++j) {
+        O[3 * a + j] = R[3 * a + j];
+        O[3 * b1 + j] = __dadd_rn(__dmul_rn(c, R[3 * b1 + j]), __dmul_rn(ss, R[3 * b2 + j]));
+        O[3 * b2 + j] = __dsub_rn(__dmul_rn(c, R[3 * b2 + j]), __dmul_rn(ss, R[3 * b1 + j]));
+    }
+}
+
+// surrogate screen of the probes: keep the m lowest predicted outer volumes of each cluster
+__global__ void k_probe_keep(const float* __restrict__ pred, int32_t K, int32_t m, uint8_t* __restrict__ active)
+{
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    float v[kProbes];
+    for (int p = 0; p < kProbes; ++p) v[p] = active[k * kProbes + p] ? pred[k * kProbes + p] : 3.0e38f;
+    for (int p = 0; p < kProbes; ++p) {
+        if (!active[k * kProbes + p]) continue;
+        int rank = 0;
+        for (int o = 0; o < kProbes; ++o) rank += (v[o] < v[p]) || (v[o] == v[p] && o < p);
+        if (rank >= m) active[k * kProbes + p] = 0;
+    }
+}
+
+__global__ void k_probe_compact(const uint8_t* __restrict__ active, int32_t n, const obb_qbox* __restrict__ pq,
+                                obb_qbox* __restrict__ evals2, int32_t* __restrict__ map, int32_t* __restrict__ n2)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !active[i]) return;
+    const int32_t j = atomicAdd(n2, 1);
+    evals2[j] = pq[i];
+    map[j] = i;
+}
+
+__global__ void k_probe_best(const uint64_t* __restrict__ cnt, const int32_t* __restrict__ map,
+                             const int32_t* __restrict__ n2, unsigned long long* __restrict__ best)
+{
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= *n2) return;
+    const int32_t i = map[j];
+    atomicMin(&best[i / kProbes], ((unsigned long long)cnt[j] << 3) | (unsigned long long)(i % kProbes));
+}
+
+// keep the best probe when its exact outer volume is strictly smaller, else halve theta
+__global__ void k_probe_apply(const unsigned long long* __restrict__ best, const double* __restrict__ pf,
+                              const obb_qbox* __restrict__ pq, int32_t K, int32_t* __restrict__ level,
+                              double* __restrict__ frames, obb_qbox* __restrict__ q, uint64_t* __restrict__ obv,
+                              int64_t* __restrict__ stats)
+{
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K || level[k] >= kDescentMaxLevel) return;
+    const unsigned long long b = best[k];
+    const uint64_t c = b >> 3;
+    if (b != ~0ull && c < obv[k]) {
+        const int32_t i = k * kProbes + (int32_t)(b & 7);
+        for (int t = 0; t < 9; ++t) frames[9 * (int64_t)k + t] = pf[9 * (int64_t)i + t];
+        q[k] = pq[i];
+        obv[k] = c;
+        atomicAdd((unsigned long long*)&stats[kStRefits], 1ull);
+    } else {
+        level[k] += 1;
+    }
+}
+
 constexpr int kNT = 128;
 
 }  // namespace
@@ -602,7 +822,23 @@ struct LayerMem {
     double* newframe = nullptr;
     obb_qbox* newq = nullptr;
     uint64_t* ncount = nullptr;
+    uint64_t* pcount = nullptr;     // [K * 6] exact counts of the probes
     int32_t* dK = nullptr;          // device copy of K
+    // surrogate screening scratch (allocated when a surrogate is attached)
+    float* feats = nullptr;
+    float* pred = nullptr;
+    unsigned long long* skey = nullptr;
+    uint8_t* kept = nullptr;
+    unsigned long long* slot = nullptr;
+    obb_qbox* evals2 = nullptr;
+    int32_t* n2 = nullptr;
+    int32_t* map = nullptr;
+    uint8_t* dirty = nullptr;       // [K] membership changed since the last covariance refit
+    uint8_t* keep = nullptr;        // [K * 6] refit / probe activity
+    int32_t* level = nullptr;       // [K] descent step level (theta = 2^-(5 + level))
+    double* pframes = nullptr;      // [K * 6][9] probe frames
+    obb_qbox* pq = nullptr;         // [K * 6] probe boxes
+    unsigned long long* pbest = nullptr;  // [K]
     int32_t cand_cap = 0, eval_cap = 0;
     void* cub_tmp = nullptr;
     size_t cub_bytes = 0;
@@ -650,7 +886,9 @@ void layer_destroy(obb_layer* L)
         if (p) cudaFreeAsync(p, s);
     if (M) {
         void* mp[] = {M->iota, M->keys_out, M->ctr, M->cand, M->evals, M->ecount, M->epoints, M->mom,
-                      M->newframe, M->newq, M->ncount, M->dK, M->cub_tmp};
+                      M->newframe, M->newq, M->ncount, M->dK, M->cub_tmp, M->feats, M->pred, M->skey,
+                      M->kept, M->slot, M->evals2, M->n2, M->map, M->dirty, M->keep, M->level,
+                      M->pframes, M->pq, M->pbest, M->pcount};
         for (void* p : mp)
             if (p) cudaFreeAsync(p, s);
         delete M;
@@ -669,14 +907,14 @@ static obb_status init_boxes(obb_ctx* ctx, obb_layer* L, const double* d_frames,
         OBB_CK(ctx, cudaMemcpyAsync(L->d_frames, d_frames, sizeof(double) * 9 * K, cudaMemcpyDeviceToDevice, s));
     } else {
         k_moments<kNT><<<K, kNT, 0, s>>>(lat->mesh->d_verts, lat->mesh->d_tris, L->d_members, L->d_start,
-                                         lat->d_frame, M->mom);
+                                         lat->d_frame, M->mom, nullptr);
         note_launch(ctx);
-        k_frames_from_moments<<<(K + 31) / 32, 32, 0, s>>>(M->mom, d_fallback, K, L->d_frames);
+        k_frames_from_moments<<<(K + 31) / 32, 32, 0, s>>>(M->mom, d_fallback, K, L->d_frames, nullptr);
         note_launch(ctx);
     }
-    k_normals<<<(K + 31) / 32, 32, 0, s>>>(L->d_frames, K, lat->d_frame, L->d_q);
+    k_normals<<<(K + 31) / 32, 32, 0, s>>>(L->d_frames, K, lat->d_frame, L->d_q, nullptr);
     note_launch(ctx);
-    k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, L->d_q);
+    k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, L->d_q, 1, nullptr);
     note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return count_boxes(ctx, lat, L->d_q, M->dK, K, L->d_obv, nullptr);
@@ -720,12 +958,23 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     A_(dalloc(&M->cand, M->cand_cap, s));
     A_(dalloc(&M->evals, M->eval_cap, s));
     A_(dalloc(&M->ecount, M->eval_cap, s));
-    A_(dalloc(&M->epoints, M->eval_cap, s));
+    A_(dalloc(&M->epoints, std::max<int64_t>(M->eval_cap, (int64_t)kProbes * K), s));
     A_(dalloc(&M->mom, 10 * (size_t)K, s));
     A_(dalloc(&M->newframe, 9 * (size_t)K, s));
     A_(dalloc(&M->newq, K, s));
     A_(dalloc(&M->ncount, K, s));
     A_(dalloc(&M->dK, 1, s));
+    const size_t cap2 = (size_t)std::max<int64_t>(M->eval_cap, (int64_t)kProbes * K);
+    A_(dalloc(&M->evals2, cap2, s));
+    A_(dalloc(&M->map, cap2, s));
+    A_(dalloc(&M->n2, 1, s));
+    A_(dalloc(&M->dirty, K, s));
+    A_(dalloc(&M->keep, (size_t)kProbes * K, s));
+    A_(dalloc(&M->level, K, s));
+    A_(dalloc(&M->pframes, (size_t)9 * kProbes * K, s));
+    A_(dalloc(&M->pq, (size_t)kProbes * K, s));
+    A_(dalloc(&M->pbest, K, s));
+    A_(dalloc(&M->pcount, (size_t)kProbes * K, s));
 #undef A_
     if (e == cudaSuccess) {
         size_t bytes = 0;
@@ -742,6 +991,8 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     OBB_CK(ctx, cudaMemcpyAsync(L->d_parent, d_parent, sizeof(int32_t) * K, cudaMemcpyDeviceToDevice, s));
     OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
     OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
+    OBB_CK(ctx, cudaMemsetAsync(M->dirty, 1, K, s));
+    OBB_CK(ctx, cudaMemsetAsync(M->level, 0, sizeof(int32_t) * K, s));
     k_iota<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(M->iota, T);
     note_launch(ctx);
     obb_status st = set_device_int(ctx, M->dK, K);
@@ -769,7 +1020,8 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
     const obb_mesh* mesh = lat->mesh;
     const int K = L->K;
     const int rounds = (opts && opts->rounds > 0) ? opts->rounds : 16;
-    const bool refit = opts ? opts->refit != 0 : true;
+    const int refit_mode = opts ? opts->refit : 1;
+    const int dsteps = (opts && opts->descent_steps > 0) ? opts->descent_steps : 2;
     OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
     int64_t* h = reinterpret_cast<int64_t*>(ctx->h_small);
     int ran = 0;
@@ -783,15 +1035,36 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
             lat->d_fixed, mesh->d_tris, mesh->d_adj, L->T, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
             M->cand, M->evals, M->ctr, M->cand_cap, M->eval_cap, ctx->d_err);
         note_launch(ctx);
-        OBB_TRY(count_boxes(ctx, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->ecount, M->epoints));
-        k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->ctr + kCtrEval, L->d_stats);
+        const obb_qbox* evals = M->evals;
+        const int32_t* n_eval = M->ctr + kCtrEval;
+        if (L->mlp && L->topk > 0) {
+            // surrogate screening: predicted gains keep the top-k candidates of each
+            // source cluster; only their boxes are counted exactly
+            OBB_TRY(surrogate_predict(ctx, L->mlp, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->feats, M->pred));
+            const unsigned cb0 = (unsigned)((M->cand_cap + 127) / 128);
+            k_screen_score<<<cb0, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->pred, M->skey, M->kept);
+            note_launch(ctx);
+            for (int pass = 0; pass < L->topk; ++pass) {
+                OBB_CK(ctx, cudaMemsetAsync(M->slot, 0, sizeof(unsigned long long) * K, s));
+                k_screen_pick<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->kept, M->slot);
+                k_screen_mark<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->kept, M->slot);
+                note_launch(ctx, 2);
+            }
+            OBB_CK(ctx, cudaMemsetAsync(M->n2, 0, sizeof(int32_t), s));
+            k_screen_compact<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->kept, M->evals, M->evals2, M->n2);
+            note_launch(ctx);
+            evals = M->evals2;
+            n_eval = M->n2;
+        }
+        OBB_TRY(count_boxes(ctx, lat, evals, n_eval, M->eval_cap, M->ecount, M->epoints));
+        k_sum_points<<<32, 256, 0, s>>>(M->epoints, n_eval, L->d_stats);
         note_launch(ctx);
         const unsigned cb = (unsigned)((M->cand_cap + 127) / 128);
         k_gains<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->ecount, L->d_best, L->d_stats);
         note_launch(ctx);
         const int64_t before = (r == 0) ? 0 : h[1];
-        k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, M->evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
-                                    L->d_size, L->d_stats);
+        k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
+                                    L->d_size, L->d_stats, M->dirty, M->level);
         note_launch(ctx);
         OBB_CK(ctx, cudaGetLastError());
         OBB_CK(ctx, cudaMemcpyAsync(h, L->d_stats, sizeof(int64_t) * kStCount, cudaMemcpyDeviceToHost, s));
@@ -801,23 +1074,64 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
         if (moved > 0) M->members_valid = false;
         if (moved == 0) break;
     }
-    if (refit) {
+    if (refit_mode & 1) {
+        // covariance refit of the clusters whose membership changed (the others
+        // would rebuild the frame they already tried and keep their box)
         if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
         k_moments<kNT><<<K, kNT, 0, s>>>(mesh->d_verts, mesh->d_tris, L->d_members, L->d_start, lat->d_frame,
-                                         M->mom);
+                                         M->mom, M->dirty);
+        k_frames_from_moments<<<(K + 31) / 32, 32, 0, s>>>(M->mom, L->d_frames, K, M->newframe, M->dirty);
+        k_normals<<<(K + 31) / 32, 32, 0, s>>>(M->newframe, K, lat->d_frame, M->newq, M->dirty);
+        k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, M->newq, 1, M->dirty);
+        note_launch(ctx, 4);
+        const uint8_t* screen = nullptr;
+        if (L->mlp) {
+            // surrogate screen: exact counts only for the boxes predicted to improve
+            OBB_TRY(surrogate_predict(ctx, L->mlp, lat, M->newq, M->dK, K, M->feats, M->pred));
+            k_refit_keep<<<(K + 127) / 128, 128, 0, s>>>(M->pred, L->d_obv, K, M->keep);
+            note_launch(ctx);
+            screen = M->keep;
+        }
+        OBB_CK(ctx, cudaMemsetAsync(M->n2, 0, sizeof(int32_t), s));
+        k_dirty_compact<<<(K + 127) / 128, 128, 0, s>>>(M->dirty, screen, K, M->newq, M->evals2, M->map, M->n2);
         note_launch(ctx);
-        k_frames_from_moments<<<(K + 31) / 32, 32, 0, s>>>(M->mom, L->d_frames, K, M->newframe);
-        note_launch(ctx);
-        k_normals<<<(K + 31) / 32, 32, 0, s>>>(M->newframe, K, lat->d_frame, M->newq);
-        note_launch(ctx);
-        k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, M->newq);
-        note_launch(ctx);
-        OBB_TRY(count_boxes(ctx, lat, M->newq, M->dK, K, M->ncount, M->epoints));
-        k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->dK, L->d_stats);
-        note_launch(ctx);
-        k_refit_accept<<<(K + 127) / 128, 128, 0, s>>>(M->newframe, M->newq, M->ncount, K, L->d_frames, L->d_q,
-                                                       L->d_obv, L->d_stats);
-        note_launch(ctx);
+        OBB_TRY(count_boxes(ctx, lat, M->evals2, M->n2, K, M->ncount, M->epoints));
+        k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->n2, L->d_stats);
+        k_refit_accept_mapped<<<(K + 127) / 128, 128, 0, s>>>(M->newframe, M->newq, M->ncount, M->map, M->n2,
+                                                              L->d_frames, L->d_q, L->d_obv, L->d_stats);
+        note_launch(ctx, 2);
+        OBB_CK(ctx, cudaMemsetAsync(M->dirty, 0, K, s));
+        OBB_CK(ctx, cudaGetLastError());
+    }
+    if (refit_mode & 2) {
+        // box-parameter descent: six rotation probes per cluster per step, the
+        // best kept when its exact outer volume is strictly smaller
+        if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
+        const int32_t KP = kProbes * K;
+        for (int step = 0; step < dsteps; ++step) {
+            k_probe_frames<<<(KP + 127) / 128, 128, 0, s>>>(L->d_frames, M->level, K, M->pframes, M->keep);
+            k_normals<<<(KP + 31) / 32, 32, 0, s>>>(M->pframes, KP, lat->d_frame, M->pq, M->keep);
+            k_tight<kNT><<<KP, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, M->pq, kProbes,
+                                            M->keep);
+            note_launch(ctx, 3);
+            if (L->mlp) {
+                OBB_CK(ctx, ctx->kdev.reserve(sizeof(int32_t), s));
+                OBB_TRY(set_device_int(ctx, ctx->kdev.as<int32_t>(), KP));
+                OBB_TRY(surrogate_predict(ctx, L->mlp, lat, M->pq, ctx->kdev.as<int32_t>(), KP, M->feats, M->pred));
+                k_probe_keep<<<(K + 127) / 128, 128, 0, s>>>(M->pred, K, L->topk > 0 ? L->topk : 2, M->keep);
+                note_launch(ctx);
+            }
+            OBB_CK(ctx, cudaMemsetAsync(M->n2, 0, sizeof(int32_t), s));
+            k_probe_compact<<<(KP + 127) / 128, 128, 0, s>>>(M->keep, KP, M->pq, M->evals2, M->map, M->n2);
+            note_launch(ctx);
+            OBB_TRY(count_boxes(ctx, lat, M->evals2, M->n2, KP, M->pcount, M->epoints));
+            OBB_CK(ctx, cudaMemsetAsync(M->pbest, 0xff, sizeof(unsigned long long) * K, s));
+            k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->n2, L->d_stats);
+            k_probe_best<<<(KP + 127) / 128, 128, 0, s>>>(M->pcount, M->map, M->n2, M->pbest);
+            k_probe_apply<<<(K + 127) / 128, 128, 0, s>>>(M->pbest, M->pframes, M->pq, K, M->level, L->d_frames, L->d_q,
+                                                          L->d_obv, L->d_stats);
+            note_launch(ctx, 3);
+        }
         OBB_CK(ctx, cudaGetLastError());
     }
     if (st) {
@@ -837,6 +1151,41 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
         st->total_obv = (uint64_t)h[kStCount];
     }
     return OBB_OK;
+}
+
+obb_status layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, int32_t topk)
+{
+    cudaStream_t s = ctx->stream;
+    LayerMem* M = mem_of(L);
+    if (mlp && !M->feats) {
+        const size_t cap2 = (size_t)std::max<int64_t>(M->eval_cap, (int64_t)kProbes * L->K);
+        cudaError_t e = dalloc(&M->feats, cap2 * kSurrogateInputs, s);
+        if (e == cudaSuccess) e = dalloc(&M->pred, cap2, s);
+        if (e == cudaSuccess) e = dalloc(&M->skey, M->cand_cap, s);
+        if (e == cudaSuccess) e = dalloc(&M->kept, M->cand_cap, s);
+        if (e == cudaSuccess) e = dalloc(&M->slot, L->K, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate screening scratch");
+    }
+    L->mlp = mlp;
+    L->topk = topk;
+    return OBB_OK;
+}
+
+obb_status layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox* out, uint64_t* counts, int64_t cap,
+                                 int64_t* n)
+{
+    LayerMem* M = mem_of(L);
+    int32_t ne = 0;
+    OBB_CK(ctx, cudaMemcpyAsync(&ne, M->ctr + kCtrEval, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    OBB_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t m = ne < cap ? ne : cap;
+    if (m > 0) {
+        OBB_CK(ctx, cudaMemcpyAsync(out, M->evals, sizeof(obb_qbox) * m, cudaMemcpyDeviceToHost, ctx->stream));
+        if (counts)
+            OBB_CK(ctx, cudaMemcpyAsync(counts, M->ecount, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    *n = ne;
+    return check_device_error(ctx);
 }
 
 }  // namespace obbv

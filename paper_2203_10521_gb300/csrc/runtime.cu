@@ -474,6 +474,20 @@ obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* L, int32_t* assign, dou
 
 int32_t obb_layer_clusters(const obb_layer* L) { return L ? L->K : 0; }
 
+obb_status obb_layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, int32_t topk)
+{
+    if (!ctx || !L) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (topk < 0 || topk > 6) return fail(ctx, OBB_ERR_ARG, "topk must be in [0, 6]");
+    return layer_set_surrogate(ctx, L, mlp, topk);
+}
+
+obb_status obb_layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox* boxes, uint64_t* counts, int64_t cap,
+                                     int64_t* n)
+{
+    if (!ctx || !L || !n || (cap > 0 && !boxes)) return fail(ctx, OBB_ERR_ARG, "null argument");
+    return layer_last_candidates(ctx, L, boxes, counts, cap, n);
+}
+
 void obb_layer_free(obb_layer* L) { layer_destroy(L); }
 
 obb_status obb_layer_split(obb_ctx* ctx, const obb_layer* L, int32_t* child, int32_t on_device)

@@ -1,0 +1,555 @@
+// Learned surrogate of the outer volume: a small MLP that predicts the empty
+// fraction of a box from its parameters and an 8^3 occupancy patch sampled in
+// the box's own frame.  The partition rounds of the Lloyd step use it to keep
+// only the most promising candidate moves per cluster; the exact lattice count
+// still decides every accepted move.
+//
+// Features (524 per box), from the quantised box alone, FP64 with a fixed
+// operation order (so the patch bits are reproducible):
+//   Lq, Hq = ceil(lo / 256), floor(hi / 256); M = n (3x3), M^-1 by cofactors;
+//   sample s in {0..7}^3: v_a = Lq_a + (Hq_a - Lq_a) (2 s_a + 1) / 16,
+//   p = M^-1 v, index = floor(p + 1/2), bit = occupancy (0 outside [0, N)^3);
+//   box parameters: centre M^-1 (Lq + Hq) / 2 / N, axes n_0 / |n_0|, n_1 / |n_1|,
+//   half widths (Hq_a - Lq_a) / (2 |n_a|) / N.
+// Network: 524 -> 128 -> 128 -> 128 -> 1, ReLU, sigmoid output (the empty
+// fraction); predicted outer volume = fraction x box volume in lattice cells
+// (prod (Hq_a - Lq_a + 1) / |det M|).  Training: mean squared error on the
+// fraction, Adam, FP32 master weights; inference reads an FP16 copy of the
+// weights and accumulates in FP32.  The contraction is 100k multiply-adds per
+// box on a few thousand boxes, so it runs on CUDA cores (tiled GEMM in shared
+// memory), not tensor cores.
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <random>
+#include <vector>
+
+#include "internal.h"
+
+namespace obbv {
+namespace {
+
+constexpr int kIn = kSurrogateInputs;
+constexpr int kH = 128;
+
+// parameter offsets in the flat vector: W1 b1 W2 b2 W3 b3 W4 b4 (W row-major [in][out])
+constexpr int64_t oW1 = 0, oB1 = oW1 + (int64_t)kIn * kH, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH,
+                  oB3 = oW3 + kH * kH, oW4 = oB3 + kH, oB4 = oW4 + kH, kParams = oB4 + 1;
+
+// ---------------------------------------------------------------- features
+
+__global__ void k_features(const obb_qbox* __restrict__ boxes, const int32_t* __restrict__ d_K,
+                           const uint64_t* __restrict__ words, int32_t N, int32_t W, float* __restrict__ feats)
+{
+    const int64_t b = blockIdx.x;
+    if (b >= *d_K) return;
+    const obb_qbox q = boxes[b];
+    double M[9], inv[9], Lq[3], Hq[3];
+    for (int i = 0; i < 9; ++i) M[i] = (double)q.n[i];
+    for (int a = 0; a < 3; ++a) {
+        Lq[a] = (double)(-((-q.b[2 * a]) >> kS));
+        Hq[a] = (double)(q.b[2 * a + 1] >> kS);
+    }
+    const double c00 = __dsub_rn(__dmul_rn(M[4], M[8]), __dmul_rn(M[5], M[7]));
+    const double c01 = __dsub_rn(__dmul_rn(M[5], M[6]), __dmul_rn(M[3], M[8]));
+    const double c02 = __dsub_rn(__dmul_rn(M[3], M[7]), __dmul_rn(M[4], M[6]));
+    const double det = __dadd_rn(__dadd_rn(__dmul_rn(M[0], c00), __dmul_rn(M[1], c01)), __dmul_rn(M[2], c02));
+    const double adj[9] = {c00, __dsub_rn(__dmul_rn(M[2], M[7]), __dmul_rn(M[1], M[8])),
+                           __dsub_rn(__dmul_rn(M[1], M[5]), __dmul_rn(M[2], M[4])),
+                           c01, __dsub_rn(__dmul_rn(M[0], M[8]), __dmul_rn(M[2], M[6])),
+                           __dsub_rn(__dmul_rn(M[2], M[3]), __dmul_rn(M[0], M[5])),
+                           c02, __dsub_rn(__dmul_rn(M[1], M[6]), __dmul_rn(M[0], M[7])),
+                           __dsub_rn(__dmul_rn(M[0], M[4]), __dmul_rn(M[1], M[3]))};
+    for (int i = 0; i < 9; ++i) inv[i] = det != 0.0 ? __ddiv_rn(adj[i], det) : 0.0;
+    float* f = feats + b * (int64_t)kIn;
+    if (threadIdx.x < 12) {
+        const int t = threadIdx.x;
+        double v = 0.0;
+        if (t < 3) {
+            double mid[3];
+            for (int a = 0; a < 3; ++a) mid[a] = __dmul_rn(__dadd_rn(Lq[a], Hq[a]), 0.5);
+            v = __dadd_rn(__dadd_rn(__dmul_rn(inv[3 * t], mid[0]), __dmul_rn(inv[3 * t + 1], mid[1])),
+                          __dmul_rn(inv[3 * t + 2], mid[2]));
+            v = __ddiv_rn(v, (double)N);
+        } else if (t < 9) {
+            const int a = (t - 3) / 3, c = (t - 3) % 3;
+            const double nn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(M[3 * a], M[3 * a]),
+                                                             __dmul_rn(M[3 * a + 1], M[3 * a + 1])),
+                                                   __dmul_rn(M[3 * a + 2], M[3 * a + 2])));
+            v = nn > 0.0 ? __ddiv_rn(M[3 * a + c], nn) : 0.0;
+        } else {
+            const int a = t - 9;
+            const double nn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(M[3 * a], M[3 * a]),
+                                                             __dmul_rn(M[3 * a + 1], M[3 * a + 1])),
+                                                   __dmul_rn(M[3 * a + 2], M[3 * a + 2])));
+            v = nn > 0.0 ? __ddiv_rn(__ddiv_rn(__dmul_rn(__dsub_rn(Hq[a], Lq[a]), 0.5), nn), (double)N) : 0.0;
+        }
+        f[t] = (float)v;
+    }
+    for (int s = threadIdx.x; s < 512; s += blockDim.x) {
+        const int sx = s & 7, sy = (s >> 3) & 7, sz = s >> 6;
+        const double fr[3] = {(double)(2 * sx + 1) / 16.0, (double)(2 * sy + 1) / 16.0, (double)(2 * sz + 1) / 16.0};
+        double v[3];
+        for (int a = 0; a < 3; ++a) v[a] = __dadd_rn(Lq[a], __dmul_rn(__dsub_rn(Hq[a], Lq[a]), fr[a]));
+        int64_t idx[3];
+        for (int r = 0; r < 3; ++r) {
+            const double p = __dadd_rn(__dadd_rn(__dmul_rn(inv[3 * r], v[0]), __dmul_rn(inv[3 * r + 1], v[1])),
+                                       __dmul_rn(inv[3 * r + 2], v[2]));
+            const double c = floor(__dadd_rn(p, 0.5));
+            idx[r] = (fabs(c) < 1e15) ? (int64_t)c : -1;
+        }
+        float bit = 0.f;
+        if (idx[0] >= 0 && idx[0] < N && idx[1] >= 0 && idx[1] < N && idx[2] >= 0 && idx[2] < N) {
+            const uint64_t w = words[(idx[2] * N + idx[1]) * W + (idx[0] >> 6)];
+            bit = (float)((w >> (idx[0] & 63)) & 1ull);
+        }
+        f[12 + s] = bit;
+    }
+}
+
+// box volume in lattice cells: prod (Hq_a - Lq_a + 1) / |det n|
+__device__ __forceinline__ float box_cells(const obb_qbox& q)
+{
+    double M[9];
+    for (int i = 0; i < 9; ++i) M[i] = (double)q.n[i];
+    const double det = M[0] * (M[4] * M[8] - M[5] * M[7]) + M[1] * (M[5] * M[6] - M[3] * M[8]) +
+                       M[2] * (M[3] * M[7] - M[4] * M[6]);
+    double v = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double w = (double)((q.b[2 * a + 1] >> kS) - (-((-q.b[2 * a]) >> kS)) + 1);
+        v *= w > 0.0 ? w : 0.0;
+    }
+    return det != 0.0 ? (float)(v / fabs(det)) : 0.f;
+}
+
+// ---------------------------------------------------------------- GEMM
+
+// C[m][n] = act(sum_k A(m, k) B(k, n) + bias[n]) (* (mask[m][n] > 0)), with
+// A(m, k) = A[m sAm + k sAk], B(k, n) = B[k sBk + n sBn]; rows m >= *d_M
+// (when given) are skipped.  act: 0 none, 1 ReLU, 2 sigmoid.  Tiles 64 x 64,
+// 256 threads, 4 x 4 outputs per thread, K in steps of 16 through shared memory.
+template <typename TB>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* __restrict__ A, int64_t sAm,
+                                              int64_t sAk, const TB* __restrict__ B, int64_t sBk, int64_t sBn,
+                                              float* __restrict__ C, int64_t ldc, const float* __restrict__ bias,
+                                              int act, const float* __restrict__ mask, int64_t ldm,
+                                              const int32_t* __restrict__ d_M)
+{
+    if (d_M) M = min(M, *d_M);
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    if (m0 >= M) return;
+    __shared__ float As[16][64 + 1];
+    __shared__ float Bs[16][64 + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+            const int kk = i >> 6, mm = i & 63;
+            const int m = m0 + mm, k = k0 + kk;
+            As[kk][mm] = (m < M && k < K) ? A[m * sAm + k * sAk] : 0.f;
+            const int n = n0 + mm;
+            Bs[kk][mm] = (n < N && k < K) ? (float)B[k * sBk + n * sBn] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a[i] = As[kk][ty * 4 + i];
+                bb[i] = Bs[kk][tx * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= N) continue;
+            float v = acc[i][j] + (bias ? bias[n] : 0.f);
+            if (mask && !(mask[m * ldm + n] > 0.f)) v = 0.f;
+            if (act == 1) v = fmaxf(v, 0.f);
+            else if (act == 2) v = 1.f / (1.f + __expf(-v));
+            C[m * ldc + n] = v;
+        }
+    }
+}
+
+// column sums: out[n] = sum_m X[m][n] (bias gradients)
+__global__ void k_colsum(const float* __restrict__ X, int M, int N, float* __restrict__ out)
+{
+    const int n = blockIdx.x;
+    float s = 0.f;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) s += X[(int64_t)m * N + n];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+        out[n] = t;
+    }
+}
+
+// dY = 2 (y - t) / B * y (1 - y); loss partial sums
+__global__ void k_out_grad(const float* __restrict__ y, const float* __restrict__ t, int B, float* __restrict__ dy,
+                           float* __restrict__ loss)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (i < B) {
+        const float e = y[i] - t[i];
+        dy[i] = 2.f * e / (float)B * y[i] * (1.f - y[i]);
+        l = e * e / (float)B;
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.f) atomicAdd(loss, l);
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       __half* __restrict__ wh, int64_t n, float lr, float b1t, float b2t)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.f - b1t), vh = vi / (1.f - b2t);
+    const float wi = w[i] - lr * mh / (sqrtf(vh) + eps);
+    w[i] = wi;
+    wh[i] = __float2half_rn(wi);
+}
+
+__global__ void k_to_half(const float* __restrict__ w, __half* __restrict__ wh, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) wh[i] = __float2half_rn(w[i]);
+}
+
+// predicted outer volume = fraction x cells
+__global__ void k_pred_obv(const float* __restrict__ frac, const obb_qbox* __restrict__ boxes,
+                           const int32_t* __restrict__ d_K, float* __restrict__ pred)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *d_K) return;
+    pred[i] = frac[i] * box_cells(boxes[i]);
+}
+
+template <typename TB>
+void gemm(obb_ctx* ctx, int M, int N, int K, const float* A, int64_t sAm, int64_t sAk, const TB* B, int64_t sBk,
+          int64_t sBn, float* C, int64_t ldc, const float* bias, int act, const float* mask, int64_t ldm,
+          const int32_t* d_M)
+{
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    k_gemm<TB><<<grid, 256, 0, ctx->stream>>>(M, N, K, A, sAm, sAk, B, sBk, sBn, C, ldc, bias, act, mask, ldm, d_M);
+    note_launch(ctx);
+}
+
+}  // namespace
+
+struct MlpImpl {
+    float* w = nullptr;    // FP32 master weights
+    __half* wh = nullptr;  // FP16 inference copy
+    float* g = nullptr;    // gradients
+    float* m = nullptr;    // Adam moments
+    float* v = nullptr;
+    int64_t step = 0;
+    int64_t cap = 0;       // batch capacity of the activation buffers
+    float *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *y = nullptr, *d1 = nullptr, *d2 = nullptr, *d3 = nullptr,
+          *dy = nullptr, *loss = nullptr;
+};
+
+}  // namespace obbv
+
+struct obb_mlp {
+    obb_ctx* ctx = nullptr;
+    obbv::MlpImpl* p = nullptr;
+};
+
+namespace obbv {
+
+static obb_status mlp_reserve(obb_ctx* ctx, MlpImpl* P, int64_t B)
+{
+    if (B <= P->cap) return OBB_OK;
+    cudaStream_t s = ctx->stream;
+    float** bufs[] = {&P->h1, &P->h2, &P->h3, &P->d1, &P->d2, &P->d3};
+    for (float** b : bufs) {
+        if (*b) cudaFreeAsync(*b, s);
+        OBB_CK(ctx, cudaMallocAsync((void**)b, sizeof(float) * kH * B, s));
+    }
+    if (P->y) cudaFreeAsync(P->y, s);
+    if (P->dy) cudaFreeAsync(P->dy, s);
+    OBB_CK(ctx, cudaMallocAsync((void**)&P->y, sizeof(float) * B, s));
+    OBB_CK(ctx, cudaMallocAsync((void**)&P->dy, sizeof(float) * B, s));
+    P->cap = B;
+    return OBB_OK;
+}
+
+// forward pass into P->h1..h3, P->y (fraction); FP32 or FP16 weights
+static void mlp_forward(obb_ctx* ctx, const MlpImpl* P, const float* X, int B, const int32_t* d_B, bool half)
+{
+    if (half) {
+        const __half* w = P->wh;
+        gemm<__half>(ctx, B, kH, kIn, X, kIn, 1, w + oW1, kH, 1, P->h1, kH, P->w + oB1, 1, nullptr, 0, d_B);
+        gemm<__half>(ctx, B, kH, kH, P->h1, kH, 1, w + oW2, kH, 1, P->h2, kH, P->w + oB2, 1, nullptr, 0, d_B);
+        gemm<__half>(ctx, B, kH, kH, P->h2, kH, 1, w + oW3, kH, 1, P->h3, kH, P->w + oB3, 1, nullptr, 0, d_B);
+        gemm<__half>(ctx, B, 1, kH, P->h3, kH, 1, w + oW4, 1, 1, P->y, 1, P->w + oB4, 2, nullptr, 0, d_B);
+    } else {
+        const float* w = P->w;
+        gemm<float>(ctx, B, kH, kIn, X, kIn, 1, w + oW1, kH, 1, P->h1, kH, w + oB1, 1, nullptr, 0, d_B);
+        gemm<float>(ctx, B, kH, kH, P->h1, kH, 1, w + oW2, kH, 1, P->h2, kH, w + oB2, 1, nullptr, 0, d_B);
+        gemm<float>(ctx, B, kH, kH, P->h2, kH, 1, w + oW3, kH, 1, P->h3, kH, w + oB3, 1, nullptr, 0, d_B);
+        gemm<float>(ctx, B, 1, kH, P->h3, kH, 1, w + oW4, 1, 1, P->y, 1, w + oB4, 2, nullptr, 0, d_B);
+    }
+}
+
+// loss and gradients (FP32 weights) into P->g; loss into P->loss (device)
+static obb_status mlp_backward(obb_ctx* ctx, MlpImpl* P, const float* X, const float* T, int B)
+{
+    cudaStream_t s = ctx->stream;
+    mlp_forward(ctx, P, X, B, nullptr, false);
+    OBB_CK(ctx, cudaMemsetAsync(P->loss, 0, sizeof(float), s));
+    k_out_grad<<<(B + 255) / 256, 256, 0, s>>>(P->y, T, B, P->dy, P->loss);
+    note_launch(ctx);
+    float* g = P->g;
+    const float* w = P->w;
+    // layer 4: dW4 = H3^T dY, db4 = sum dY, dH3 = dY W4^T * (H3 > 0)
+    gemm<float>(ctx, kH, 1, B, P->h3, 1, kH, P->dy, 1, 1, g + oW4, 1, nullptr, 0, nullptr, 0, nullptr);
+    k_colsum<<<1, 256, 0, s>>>(P->dy, B, 1, g + oB4);
+    note_launch(ctx);
+    gemm<float>(ctx, B, kH, 1, P->dy, 1, 1, w + oW4, 1, 1, P->d3, kH, nullptr, 0, P->h3, kH, nullptr);
+    // layer 3
+    gemm<float>(ctx, kH, kH, B, P->h2, 1, kH, P->d3, kH, 1, g + oW3, kH, nullptr, 0, nullptr, 0, nullptr);
+    k_colsum<<<kH, 256, 0, s>>>(P->d3, B, kH, g + oB3);
+    note_launch(ctx);
+    gemm<float>(ctx, B, kH, kH, P->d3, kH, 1, w + oW3, 1, kH, P->d2, kH, nullptr, 0, P->h2, kH, nullptr);
+    // layer 2
+    gemm<float>(ctx, kH, kH, B, P->h1, 1, kH, P->d2, kH, 1, g + oW2, kH, nullptr, 0, nullptr, 0, nullptr);
+    k_colsum<<<kH, 256, 0, s>>>(P->d2, B, kH, g + oB2);
+    note_launch(ctx);
+    gemm<float>(ctx, B, kH, kH, P->d2, kH, 1, w + oW2, 1, kH, P->d1, kH, nullptr, 0, P->h1, kH, nullptr);
+    // layer 1
+    gemm<float>(ctx, kIn, kH, B, X, 1, kIn, P->d1, kH, 1, g + oW1, kH, nullptr, 0, nullptr, 0, nullptr);
+    k_colsum<<<kH, 256, 0, s>>>(P->d1, B, kH, g + oB1);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
+
+obb_status surrogate_predict(obb_ctx* ctx, const obb_mlp* mlp, const obb_lattice* lat, const obb_qbox* d_boxes,
+                             const int32_t* d_K, int64_t cap, float* d_feats, float* d_pred)
+{
+    MlpImpl* P = mlp->p;
+    OBB_TRY(mlp_reserve(ctx, P, cap));
+    k_features<<<(unsigned)cap, 128, 0, ctx->stream>>>(d_boxes, d_K, lat->d_words, lat->frame.N, lat->frame.W,
+                                                       d_feats);
+    note_launch(ctx);
+    mlp_forward(ctx, P, d_feats, (int)cap, d_K, true);
+    k_pred_obv<<<(unsigned)((cap + 255) / 256), 256, 0, ctx->stream>>>(P->y, d_boxes, d_K, d_pred);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
+
+}  // namespace obbv
+
+using namespace obbv;
+
+namespace {
+template <class T>
+obb_status dev_in(obb_ctx* ctx, const T* src, size_t n, int on_device, void** hold, const T** out)
+{
+    if (on_device) {
+        *out = src;
+        return OBB_OK;
+    }
+    OBB_CK(ctx, cudaMallocAsync(hold, sizeof(T) * n, ctx->stream));
+    OBB_CK(ctx, cudaMemcpyAsync(*hold, src, sizeof(T) * n, cudaMemcpyHostToDevice, ctx->stream));
+    *out = static_cast<const T*>(*hold);
+    return OBB_OK;
+}
+}  // namespace
+
+extern "C" {
+
+obb_status obb_mlp_create(obb_ctx* ctx, uint64_t seed, obb_mlp** out)
+{
+    if (!ctx || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
+    *out = nullptr;
+    // He-uniform initial weights from a seeded host generator, zero biases
+    std::vector<float> w(kParams, 0.f);
+    std::mt19937_64 rng(seed);
+    auto fill = [&](int64_t off, int fan_in, int64_t count) {
+        std::uniform_real_distribution<float> U(-std::sqrt(6.f / fan_in), std::sqrt(6.f / fan_in));
+        for (int64_t i = 0; i < count; ++i) w[off + i] = U(rng);
+    };
+    fill(oW1, kIn, (int64_t)kIn * kH);
+    fill(oW2, kH, (int64_t)kH * kH);
+    fill(oW3, kH, (int64_t)kH * kH);
+    fill(oW4, kH, kH);
+    obb_mlp* m = new obb_mlp();
+    m->ctx = ctx;
+    m->p = new MlpImpl();
+    MlpImpl* P = m->p;
+    cudaStream_t s = ctx->stream;
+    cudaError_t e = cudaMallocAsync((void**)&P->w, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->wh, sizeof(__half) * kParams, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->g, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->m, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->v, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->loss, sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->w, w.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->m, 0, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->v, 0, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) {
+        k_to_half<<<(unsigned)((kParams + 255) / 256), 256, 0, s>>>(P->w, P->wh, kParams);
+        note_launch(ctx);
+        e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) {
+        obb_mlp_free(m);
+        return cuda_fail(ctx, e, "surrogate allocation");
+    }
+    *out = m;
+    return OBB_OK;
+}
+
+void obb_mlp_free(obb_mlp* m)
+{
+    if (!m) return;
+    cudaStream_t s = m->ctx ? m->ctx->stream : nullptr;
+    if (m->p) {
+        MlpImpl* P = m->p;
+        void* ptrs[] = {P->w, P->wh, P->g, P->m, P->v, P->h1, P->h2, P->h3, P->y, P->d1, P->d2, P->d3, P->dy, P->loss};
+        for (void* q : ptrs)
+            if (q) cudaFreeAsync(q, s);
+        delete P;
+    }
+    delete m;
+}
+
+int64_t obb_mlp_num_params(void) { return kParams; }
+
+obb_status obb_mlp_params(obb_ctx* ctx, const obb_mlp* m, float* out, int32_t on_device)
+{
+    if (!ctx || !m || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
+    OBB_CK(ctx, cudaMemcpyAsync(out, m->p->w, sizeof(float) * kParams,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    return on_device ? OBB_OK : check_device_error(ctx);
+}
+
+obb_status obb_mlp_set_params(obb_ctx* ctx, obb_mlp* m, const float* in, int32_t on_device)
+{
+    if (!ctx || !m || !in) return fail(ctx, OBB_ERR_ARG, "null argument");
+    MlpImpl* P = m->p;
+    OBB_CK(ctx, cudaMemcpyAsync(P->w, in, sizeof(float) * kParams,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    k_to_half<<<(unsigned)((kParams + 255) / 256), 256, 0, ctx->stream>>>(P->w, P->wh, kParams);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaMemsetAsync(P->m, 0, sizeof(float) * kParams, ctx->stream));
+    OBB_CK(ctx, cudaMemsetAsync(P->v, 0, sizeof(float) * kParams, ctx->stream));
+    P->step = 0;
+    return check_device_error(ctx);
+}
+
+obb_status obb_surrogate_features(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* boxes, int64_t K, float* feats,
+                                  int32_t on_device)
+{
+    if (!ctx || !lat || (K > 0 && (!boxes || !feats))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (K <= 0) return OBB_OK;
+    void* hb = nullptr;
+    const obb_qbox* db;
+    OBB_TRY(dev_in(ctx, boxes, (size_t)K, on_device, &hb, &db));
+    float* df = feats;
+    if (!on_device) OBB_CK(ctx, cudaMallocAsync((void**)&df, sizeof(float) * kIn * K, ctx->stream));
+    OBB_CK(ctx, ctx->kdev.reserve(sizeof(int32_t), ctx->stream));
+    OBB_TRY(set_device_int(ctx, ctx->kdev.as<int32_t>(), (int32_t)K));
+    k_features<<<(unsigned)K, 128, 0, ctx->stream>>>(db, ctx->kdev.as<int32_t>(), lat->d_words, lat->frame.N,
+                                                     lat->frame.W, df);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    if (!on_device) {
+        OBB_CK(ctx, cudaMemcpyAsync(feats, df, sizeof(float) * kIn * K, cudaMemcpyDeviceToHost, ctx->stream));
+        cudaFreeAsync(df, ctx->stream);
+    }
+    if (hb) cudaFreeAsync(hb, ctx->stream);
+    return on_device ? OBB_OK : check_device_error(ctx);
+}
+
+obb_status obb_mlp_forward(obb_ctx* ctx, const obb_mlp* m, const float* feats, int64_t B, float* out,
+                           int32_t half_weights, int32_t on_device)
+{
+    if (!ctx || !m || (B > 0 && (!feats || !out))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (B <= 0) return OBB_OK;
+    if (B > (1 << 24)) return fail(ctx, OBB_ERR_RANGE, "batch too large");
+    void* hx = nullptr;
+    const float* dx;
+    OBB_TRY(dev_in(ctx, feats, (size_t)B * kIn, on_device, &hx, &dx));
+    OBB_TRY(mlp_reserve(ctx, m->p, B));
+    mlp_forward(ctx, m->p, dx, (int)B, nullptr, half_weights != 0);
+    OBB_CK(ctx, cudaGetLastError());
+    OBB_CK(ctx, cudaMemcpyAsync(out, m->p->y, sizeof(float) * B,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (hx) cudaFreeAsync(hx, ctx->stream);
+    return on_device ? OBB_OK : check_device_error(ctx);
+}
+
+obb_status obb_mlp_gradients(obb_ctx* ctx, obb_mlp* m, const float* feats, const float* target, int64_t B,
+                             float* grads, float* loss, int32_t on_device)
+{
+    if (!ctx || !m || !feats || !target || B <= 0) return fail(ctx, OBB_ERR_ARG, "bad argument");
+    if (B > (1 << 24)) return fail(ctx, OBB_ERR_RANGE, "batch too large");
+    void *hx = nullptr, *ht = nullptr;
+    const float *dx, *dt;
+    OBB_TRY(dev_in(ctx, feats, (size_t)B * kIn, on_device, &hx, &dx));
+    OBB_TRY(dev_in(ctx, target, (size_t)B, on_device, &ht, &dt));
+    OBB_TRY(mlp_reserve(ctx, m->p, B));
+    OBB_TRY(mlp_backward(ctx, m->p, dx, dt, (int)B));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (grads) OBB_CK(ctx, cudaMemcpyAsync(grads, m->p->g, sizeof(float) * kParams, kind, ctx->stream));
+    if (loss) OBB_CK(ctx, cudaMemcpyAsync(loss, m->p->loss, sizeof(float), kind, ctx->stream));
+    if (hx) cudaFreeAsync(hx, ctx->stream);
+    if (ht) cudaFreeAsync(ht, ctx->stream);
+    return on_device ? OBB_OK : check_device_error(ctx);
+}
+
+obb_status obb_mlp_train_step(obb_ctx* ctx, obb_mlp* m, const float* feats, const float* target, int64_t B, float lr,
+                              float* loss, int32_t on_device)
+{
+    if (!ctx || !m || !feats || !target || B <= 0) return fail(ctx, OBB_ERR_ARG, "bad argument");
+    if (B > (1 << 24)) return fail(ctx, OBB_ERR_RANGE, "batch too large");
+    void *hx = nullptr, *ht = nullptr;
+    const float *dx, *dt;
+    OBB_TRY(dev_in(ctx, feats, (size_t)B * kIn, on_device, &hx, &dt));
+    dx = dt;
+    OBB_TRY(dev_in(ctx, target, (size_t)B, on_device, &ht, &dt));
+    MlpImpl* P = m->p;
+    OBB_TRY(mlp_reserve(ctx, P, B));
+    OBB_TRY(mlp_backward(ctx, P, dx, dt, (int)B));
+    P->step += 1;
+    const float b1t = std::pow(0.9f, (float)P->step), b2t = std::pow(0.999f, (float)P->step);
+    k_adam<<<(unsigned)((kParams + 255) / 256), 256, 0, ctx->stream>>>(P->w, P->g, P->m, P->v, P->wh, kParams, lr,
+                                                                      b1t, b2t);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    if (loss)
+        OBB_CK(ctx, cudaMemcpyAsync(loss, P->loss, sizeof(float),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (hx) cudaFreeAsync(hx, ctx->stream);
+    if (ht) cudaFreeAsync(ht, ctx->stream);
+    return (loss && !on_device) ? check_device_error(ctx) : OBB_OK;
+}
+
+}  // extern "C"

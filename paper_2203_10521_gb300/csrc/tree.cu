@@ -128,7 +128,7 @@ obb_status build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts*
     obb_layer* root = nullptr;
     OBB_TRY(layer_create(ctx, lat, child, parent, 1, nullptr, nullptr, &root));
     tree->layers.push_back(root);
-    obb_step_opts so{opts->rounds, opts->refit};
+    obb_step_opts so{opts->rounds, opts->refit, 0, 0};
     for (int lev = 1; lev <= depth; ++lev) {
         obb_layer* up = tree->layers.back();
         OBB_TRY(split_layer(ctx, up, child));

@@ -269,6 +269,28 @@ def test_refit_matches_oracle(ctx, torus_setup):
     layer.free()
 
 
+def test_descent_bit_exact(ctx, torus_setup):
+    """Rotation-probe descent from identical state: FP64 frames, quantised
+    boxes and exact outer volumes match the oracle bit for bit."""
+    m, mesh, lat, P = torus_setup
+    K = 8
+    assign = _wedges(m, K)
+    parent = (np.arange(K) // 2).astype(np.int32)
+    frames = O.cluster_frames(P.V, P.F, assign, K, P.center)
+    layer = ctx.layer_init(lat, assign, parent, frames)
+    L = O.layer_from_frames(P, assign, parent, frames)
+    for it in range(2):
+        st = ctx.lloyd_step(layer, rounds=4, refit=2, descent_steps=3)
+        O.lloyd_step(P, L, rounds=4, do_refit=2, descent_steps=3)
+        g = ctx.layer_read(layer)
+        assert np.array_equal(g["assign"], L.assign)
+        assert np.array_equal(g["frames"], L.frames)
+        assert np.array_equal(g["qboxes"]["n"], L.n) and np.array_equal(g["qboxes"]["b"], L.bnd)
+        assert np.array_equal(g["obv"], L.obv)
+    assert st["refits_accepted"] >= 0
+    layer.free()
+
+
 def test_layer_init_covariance_frames(ctx, torus_setup):
     m, mesh, lat, P = torus_setup
     K = 16

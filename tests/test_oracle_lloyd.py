@@ -246,3 +246,49 @@ def test_median_split_order_and_sizes():
         b = key[c0].max()
         tied = mem[key == b]
         assert np.all(np.diff(child[tied]) >= 0)
+
+
+def test_probe_frames_are_exact_rotations():
+    """A rotation probe turns the frame about one of its own axes by
+    2 atan(t), t = 2^-(5 + level), keeping it orthonormal and right-handed."""
+    rng = np.random.Generator(np.random.PCG64(31))
+    R = pins.random_rotation(rng)
+    for level in (0, 3):
+        t = 2.0 ** -(5 + level)
+        for p in range(6):
+            Q = O.probe_frame(R, level, p)
+            a = p // 2
+            assert np.allclose(Q @ Q.T, np.eye(3), atol=1e-15)
+            assert np.linalg.det(Q) > 0
+            assert np.array_equal(Q[a], R[a])
+            b1 = (a + 1) % 3
+            ang = np.arccos(np.clip(Q[b1] @ R[b1], -1, 1))
+            assert abs(ang - 2 * np.arctan(t)) < 1e-9
+            sign = 1 if p % 2 == 0 else -1
+            assert sign * (Q[b1] @ R[(a + 2) % 3]) > 0
+
+
+def test_descent_never_increases_and_escalates():
+    """Each descent step keeps a box only if its exact outer volume drops;
+    clusters that find no better probe halve their angle (level += 1)."""
+    m = M.torus_4096()
+    P = O.Problem(m.verts, m.tris, 40)
+    P.occ.fill_all()
+    c = m.verts[m.tris].mean(1)
+    ang = np.arctan2(c[:, 1], c[:, 0])
+    assign = np.minimum(((ang + np.pi) / (2 * np.pi) * 8).astype(np.int32), 7)
+    L = O.layer_init(P, assign, np.zeros(8, np.int32))
+    total = [int(L.obv.sum())]
+    for _ in range(6):
+        before_obv, before_lev = L.obv.copy(), L.level.copy()
+        kept = O.descent_step(P, L)
+        assert np.all(L.obv <= before_obv)
+        improved = L.obv < before_obv
+        assert improved.sum() == kept
+        assert np.array_equal(L.level[improved], before_lev[improved])
+        stuck = ~improved & (before_lev < 8)
+        assert np.array_equal(L.level[stuck], before_lev[stuck] + 1)
+        total.append(int(L.obv.sum()))
+        ref = O.layer_from_frames(P, L.assign, L.parent, L.frames)
+        assert np.array_equal(ref.obv, L.obv)
+    assert total[-1] < total[0]
