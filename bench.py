@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--lloyd-iters", type=int, default=10,
+                    help="Lloyd iterations timed for the plain vs surrogate comparison")
     return ap.parse_args()
 
 
@@ -136,6 +139,21 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def reduce_ranks(t_rank, points, launches, world, device):
+    """Whole-job figures over ranks: the slowest rank's time, and the summed
+    lattice points and kernel launches (one NCCL/gloo all-reduce each; no
+    data-path collective -- the ranks run independent meshes)."""
+    if world <= 1:
+        return float(t_rank), float(points), int(launches)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_rank)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([float(points), float(launches)], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p[0].item()), int(p[1].item())
 
 
 def tree_boxes(ctx, tree, depth):
@@ -283,7 +301,7 @@ def main():
     launches0 = ctx.profile_read()["launches"]
     evs = []
     pts_total = 0
-    lloyd = []
+    lloyd_steps = []
     wall0 = time.perf_counter()
     for _ in range(args.steps):
         flush.fill_(1)
@@ -296,7 +314,7 @@ def main():
         torch.cuda.nvtx.range_pop()
         evs.append((e0, e1))
         pts_total += batch_points + st["points_counted"]
-        lloyd.append(st)
+        lloyd_steps.append(st)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     prof = ctx.profile_read()
@@ -305,28 +323,54 @@ def main():
     ms = [a.elapsed_time(b) for a, b in evs]
     t_rank = sum(ms) / 1000.0
     launches = prof["launches"] - launches0
-    if world > 1:
-        t = torch.tensor([t_rank], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        p = torch.tensor([pts_total, launches], dtype=torch.float64, device="cuda")
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        t_max, pts_all, launches_all = float(t.item()), float(p[0].item()), int(p[1].item())
-    else:
-        t_max, pts_all, launches_all = t_rank, float(pts_total), int(launches)
+    t_max, pts_all, launches_all = reduce_ranks(t_rank, pts_total, launches, world, "cuda")
     value = pts_all / t_max
 
-    # lloyd iterations per second: the Lloyd part alone, timed separately
-    lt = []
-    for _ in range(3):
+    # Lloyd iterations per second, plain vs surrogate-screened: the same freshly
+    # split leaf layer, the rotation-descent box update (6 probes per cluster,
+    # 2 steps), timed with CUDA events; final layer totals compared
+    lloyd = {}
+    up = ctx.tree_read(tree, depth - 1)
+    Kp = 1 << (depth - 1)
+    up_layer = ctx.layer_init(lat, up["assign"], (np.arange(Kp) // 2).astype(np.int32), up["frames"])
+    child = ctx.layer_split(up_layer)
+    up_layer.free()
+    mlp = None
+    modes = ["plain"] if args.no_surrogate else ["plain", "surrogate"]
+    if not args.no_surrogate:
+        from paper_2203_10521_gb300 import surrogate as S
+        t0 = time.perf_counter()
+        mlp = ctx.mlp_create(7)
+        q, c = S.collect_pairs(ctx, lat, tree, depth, iters=2, perturb=6, seed=3)
+        _, mse0, mse1 = S.train(ctx, mlp, lat, q, c, steps=400, batch=1024, lr=2e-3, seed=4)
+        lloyd["surrogate_training"] = {"pairs": int(len(q)), "heldout_mse_before": mse0, "heldout_mse_after": mse1,
+                                       "seconds": time.perf_counter() - t0}
+    for mode in modes:
+        lay = ctx.layer_init(lat, child, parent)
+        if mode == "surrogate":
+            ctx.layer_set_surrogate(lay, mlp, 3)
         flush.fill_(1)
+        torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.lloyd_step(layer, rounds=16, refit=True)
+        evals = 0
+        for _ in range(args.lloyd_iters):
+            st = ctx.lloyd_step(lay, rounds=16, refit=2, descent_steps=2)
+            evals += st["box_evals"]
         e1.record(stream)
         torch.cuda.synchronize()
-        lt.append(e0.elapsed_time(e1))
-    lloyd_iter_per_s = 1000.0 / statistics.median(lt)
+        lms = e0.elapsed_time(e1)
+        lloyd[mode] = {"iter_per_s": 1000.0 * args.lloyd_iters / lms, "final_total_obv": int(st["total_obv"]),
+                       "exact_box_counts": int(evals)}
+        lay.free()
+    lloyd_iter_per_s = lloyd["plain"]["iter_per_s"]
+    surrogate_iter_per_s = lloyd["surrogate"]["iter_per_s"] if "surrogate" in lloyd else None
+    if "surrogate" in lloyd:
+        a, b = lloyd["plain"]["final_total_obv"], lloyd["surrogate"]["final_total_obv"]
+        lloyd["final_obv_rel_diff"] = (b - a) / a
+    if mlp is not None:
+        mlp.free()
 
     # roofline of the counting kernel (the dominant kernel), live over the timed region
     peak, peak_kind = measured_peaks()
@@ -383,8 +427,9 @@ def main():
                           "batch_boxes": len(boxes), "lloyd_rounds_per_iter": 16,
                           "l2": "flushed between steps (256 MiB write)", "per_rank": "independent mesh (seed + rank)"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_all,
-               "clocks": clocks, "lloyd_iter_per_s": lloyd_iter_per_s, "surrogate_lloyd_iter_per_s": None,
-               "lloyd_last_step": lloyd[-1], "tree_setup_s": tree_s, "wall_s_timed": wall}
+               "clocks": clocks, "lloyd_iter_per_s": lloyd_iter_per_s,
+               "surrogate_lloyd_iter_per_s": surrogate_iter_per_s, "lloyd_comparison": lloyd,
+               "lloyd_last_step": lloyd_steps[-1], "tree_setup_s": tree_s, "wall_s_timed": wall}
         print(json.dumps(out), flush=True)
     layer.free()
     tree.free()

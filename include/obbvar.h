@@ -198,6 +198,28 @@ obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qb
 obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* boxes, int64_t K,
                                       uint64_t* counts, uint64_t* points);
 
+/* obb_outer_volume_q over boxes of several lattices (many meshes) in one
+ * counting launch: box k is counted on lats[lattice_of_box[k]] (int32 [K]).
+ * lats is a host array of n_lats lattice handles of this context.  An index
+ * out of range flags OBB_ERR_ARG.  Synchronises. */
+obb_status obb_outer_volume_multi(obb_ctx* ctx, const obb_lattice* const* lats, int32_t n_lats, const obb_qbox* boxes,
+                                  const int32_t* lattice_of_box, int64_t K, uint64_t* counts, uint64_t* points,
+                                  int32_t on_device);
+
+/* The paper's own estimator of the outer volume (Sec. 4.1, Eq. 9-10), as ray
+ * casting in place of cube-map rasterisation: from each box centre o one ray
+ * per texel of a 6 x m x m cube map (through the texel centre, weighted by
+ * the texel's exact solid angle dOmega).  Mesh crossings at r_i below the box
+ * exit r_e carry s_i = +1 leaving the solid, -1 entering (Fig. 1a); with
+ * chi(o) = 1 inside the solid and chi_e = chi(o) - sum s_i, a texel adds
+ * dOmega / 3 (r_e^3 - sum s_i r_i^3 - chi_e r_e^3) (cone volumes; Eq. 10 read
+ * as a volume integral).  out[k] float64 is the estimate in world units^3 for
+ * box k; the mesh must be closed with outward-oriented triangles.  FP32 ray
+ * tests against every triangle: a cross-check, not the exact count.
+ * 1 <= m <= 256. */
+obb_status obb_directional_outer_volume(obb_ctx* ctx, const obb_mesh* mesh, const obb_box* boxes, int64_t K,
+                                        int32_t m, double* out, int32_t on_device);
+
 /* obb_quantize_boxes followed by obb_outer_volume_q. */
 obb_status obb_outer_volume(obb_ctx* ctx, const obb_lattice* lat, const obb_box* boxes, int64_t K,
                             uint64_t* counts, uint64_t* points, int32_t on_device);

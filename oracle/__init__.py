@@ -558,3 +558,72 @@ def mlp_loss_grad(params, X, T):
             dz = (dz @ W.T) * (acts[i] > 0.0)
     flat = np.concatenate([np.concatenate([g[0].ravel(), g[1].ravel()]) for g in grads])
     return loss, flat
+
+
+# ---------------------------------------------------------------------------
+# The paper's directional estimator (Sec. 4.1, Eq. 9-10), FP64
+# ---------------------------------------------------------------------------
+
+def l_out(r_e, r, s, chi_o):
+    """Outside length of the segment [o, p_e] along one ray (Eq. 9 generalised to
+    a segment that may end inside the solid): crossings at r with signs s (+1
+    leaving the solid)."""
+    r = np.asarray(r, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    chi_e = chi_o - s.sum()
+    return r_e - (s * r).sum() - chi_e * r_e
+
+
+def directional_outer_volume(V, F, box, m=32):
+    """Cube-map estimate of the outer volume of one box (c, axis0, axis1, half):
+    per texel dOmega / 3 (r_e^3 - sum s_i r_i^3 - chi_e r_e^3), FP64."""
+    V = np.asarray(V, dtype=np.float64)
+    F = np.asarray(F, dtype=np.int64)
+    b = np.asarray(box, dtype=np.float64).reshape(12)
+    o = b[:3]
+    R = np.stack([b[3:6], b[6:9], np.cross(b[3:6], b[6:9])])
+    half = b[9:12]
+    A, B, Cc = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    e1, e2 = B - A, Cc - A
+    nrm = np.cross(e1, e2)
+
+    def hits(d):
+        p = np.cross(d, e2)
+        det = (e1 * p).sum(-1)
+        ok = np.abs(det) > 1e-300
+        inv = np.where(ok, 1.0 / np.where(ok, det, 1.0), 0.0)
+        s_ = o - A
+        u = (s_ * p).sum(-1) * inv
+        q = np.cross(s_, e1)
+        v = (q @ d) * inv
+        t = (e2 * q).sum(-1) * inv
+        hit = ok & (u >= 0) & (u <= 1) & (v >= 0) & (u + v <= 1) & (t > 0)
+        sign = np.where((nrm @ d) > 0, 1.0, -1.0)
+        return t[hit], sign[hit]
+
+    _, s0 = hits(np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0))
+    chi_o = float(np.rint(s0.sum()))
+    edges = -1.0 + 2.0 * np.arange(m + 1) / m
+
+    def F_(u, v):
+        return np.arctan2(u * v, np.sqrt(u * u + v * v + 1.0))
+
+    total = 0.0
+    for face in range(6):
+        axis, sg = face // 2, (-1.0 if face % 2 else 1.0)
+        for iv in range(m):
+            for iu in range(m):
+                u0, u1, v0, v1 = edges[iu], edges[iu + 1], edges[iv], edges[iv + 1]
+                w = np.zeros(3)
+                w[axis] = sg
+                w[(axis + 1) % 3] = 0.5 * (u0 + u1)
+                w[(axis + 2) % 3] = 0.5 * (v0 + v1)
+                d = w / np.linalg.norm(w)
+                c = np.abs(R @ d)
+                re = np.min(np.where(c > 0, half / np.where(c > 0, c, 1.0), np.inf))
+                t, s = hits(d)
+                sel = t < re
+                dom = F_(u1, v1) - F_(u0, v1) - F_(u1, v0) + F_(u0, v0)
+                chi_e = chi_o - s[sel].sum()
+                total += dom / 3.0 * (re ** 3 - (s[sel] * t[sel] ** 3).sum() - chi_e * re ** 3)
+    return total

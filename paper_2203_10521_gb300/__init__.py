@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True):
         "obb_outer_volume_q": [vp, vp, vp, i64, vp, vp, i32],
         "obb_outer_volume": [vp, vp, vp, i64, vp, vp, i32],
         "obb_outer_volume_q_noalloc": [vp, vp, vp, i64, vp, vp],
+        "obb_outer_volume_multi": [vp, vp, i32, vp, vp, i64, vp, vp, i32],
+        "obb_directional_outer_volume": [vp, vp, vp, i64, i32, vp, i32],
         "obb_layer_init": [vp, vp, vp, vp, i32, vp, i32, C.POINTER(vp)],
         "obb_lloyd_step": [vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
         "obb_layer_read": [vp, vp, vp, vp, vp, vp, vp, i32],
@@ -131,7 +133,8 @@ def exported_symbols():
     return ["obb_create", "obb_set_stream", "obb_synchronize", "obb_destroy", "obb_last_error",
             "obb_profile_enable", "obb_profile_read", "obb_occupancy_rebuild",
             "obb_mesh_create", "obb_mesh_free", "obb_build_occupancy", "obb_lattice_desc", "obb_lattice_free",
-            "obb_quantize_boxes", "obb_outer_volume_q", "obb_outer_volume", "obb_outer_volume_q_noalloc", "obb_layer_init", "obb_lloyd_step",
+            "obb_quantize_boxes", "obb_outer_volume_q", "obb_outer_volume", "obb_outer_volume_q_noalloc",
+            "obb_outer_volume_multi", "obb_directional_outer_volume", "obb_layer_init", "obb_lloyd_step",
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
             "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free",
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
@@ -260,6 +263,27 @@ class Context:
         p, dev, keep = _arg(qboxes, QBOX_DTYPE)
         K = _count(qboxes, keep, 88)
         return self._ov(self.lib.obb_outer_volume_q, lat, p, dev, K, counts, points, want_points)
+
+    def directional_outer_volume(self, mesh, boxes, m=32):
+        """The paper's cube-map ray estimator of the outer volume (world units^3), host arrays."""
+        b = _host(boxes, BOX_DTYPE)
+        out = np.zeros(len(b), np.float64)
+        self.check(self.lib.obb_directional_outer_volume(self.h, mesh.h, b.ctypes.data_as(C.c_void_p), len(b), int(m),
+                                                         out.ctypes.data_as(C.c_void_p), 0))
+        return out
+
+    def outer_volume_multi(self, lats, qboxes, lattice_of_box, want_points=False):
+        """Counts of quantised boxes on several lattices in one launch (host arrays)."""
+        q = _host(qboxes, QBOX_DTYPE)
+        li = np.ascontiguousarray(lattice_of_box, dtype=np.int32)
+        K = len(q)
+        table = (C.c_void_p * len(lats))(*[l.h.value for l in lats])
+        cnt = np.zeros(K, np.uint64)
+        pts = np.zeros(K, np.uint64) if want_points else None
+        self.check(self.lib.obb_outer_volume_multi(self.h, table, len(lats), q.ctypes.data_as(C.c_void_p),
+                                                   li.ctypes.data_as(C.c_void_p), K, cnt.ctypes.data_as(C.c_void_p),
+                                                   pts.ctypes.data_as(C.c_void_p) if want_points else None, 0))
+        return (cnt, pts) if want_points else cnt
 
     def outer_volume_q_noalloc(self, lat, qboxes, counts, points=None):
         """Device-only variant that allocates nothing (see obbvar.h); qboxes, counts

@@ -66,6 +66,16 @@ struct BoxPrep {
     int64_t Lq[3], Hq[3];    // ceil(lo / 256), floor(hi / 256)
     float rcp[3];            // 1 / dd (seed of the exact initial division)
     uint64_t rows;           // nj * nk (0 = empty)
+    int32_t lat;             // index of the box's lattice in the launch's lattice table
+    int32_t pad1;
+};
+
+// One lattice as the counting kernel sees it (a table of these lets one launch
+// count boxes of many meshes).
+struct LatRef {
+    const uint64_t* words;
+    int32_t N;
+    int32_t W;
 };
 
 // Stream-ordered device allocation that only grows.
@@ -115,6 +125,8 @@ struct obb_lattice {
     int32_t* d_fixed = nullptr;      // [nv][3] snapped vertices
     uint64_t* d_words = nullptr;     // occupancy
     size_t n_words = 0;
+    obbv::LatRef ref{};              // host copy of the table entry below
+    obbv::LatRef* d_ref = nullptr;   // this lattice as a one-entry table
 };
 
 // per-cluster top-2 extents along the six slab sides (2a = low side, 2a+1 = high side)
@@ -186,6 +198,10 @@ obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d
 // d_K (int32); K_cap bounds it for scratch sizing.  counts/points are zeroed here.
 obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes,
                        const int32_t* d_K, int64_t K_cap, uint64_t* d_counts, uint64_t* d_points);
+// the same over boxes of several lattices: box k uses d_lats[d_lat_of_box[k]]
+obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats, const int32_t* d_lat_of_box,
+                             const obb_qbox* d_boxes, const int32_t* d_K, int64_t K_cap, uint64_t* d_counts,
+                             uint64_t* d_points);
 obb_status set_device_int(obb_ctx* ctx, int32_t* d_dst, int32_t value);
 // exclusive scan of n int32 values into out[n + 1] (out[n] = total), single block
 void launch_scan_i32(obb_ctx* ctx, const int32_t* in, int32_t* out, const int32_t* d_n);
@@ -206,6 +222,10 @@ obb_status layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox* out
 // surrogate.cu: features of boxes [0, *d_K) and predicted outer volumes (FP16 weights)
 obb_status surrogate_predict(obb_ctx* ctx, const obb_mlp* mlp, const obb_lattice* lat, const obb_qbox* d_boxes,
                              const int32_t* d_K, int64_t cap, float* d_feats, float* d_pred);
+
+// directional.cu: Eq. 9-10 estimator
+obb_status directional_outer_volume(obb_ctx* ctx, const obb_mesh* mesh, const obb_box* d_boxes, int64_t K, int32_t m,
+                                    double* d_out);
 
 // tree.cu
 obb_status build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts* opts, obb_tree* tree);

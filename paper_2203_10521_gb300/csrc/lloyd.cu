@@ -565,20 +565,6 @@ __global__ void __launch_bounds__(NT) k_tight(const int32_t* __restrict__ U, con
     }
 }
 
-__global__ void k_refit_accept(const double* __restrict__ newframe, const obb_qbox* __restrict__ newq,
-                               const uint64_t* __restrict__ cnt, int32_t K, double* __restrict__ frames,
-                               obb_qbox* __restrict__ q, uint64_t* __restrict__ obv, int64_t* __restrict__ stats)
-{
-    int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    if (cnt[k] < obv[k]) {
-        for (int i = 0; i < 9; ++i) frames[9 * (int64_t)k + i] = newframe[9 * (int64_t)k + i];
-        q[k] = newq[k];
-        obv[k] = cnt[k];
-        atomicAdd((unsigned long long*)&stats[kStRefits], 1ull);
-    }
-}
-
 __global__ void k_total(const uint64_t* __restrict__ obv, int32_t K, int64_t* __restrict__ out)
 {
     unsigned long long s = 0;
@@ -661,19 +647,6 @@ __global__ void k_screen_compact(Cand* __restrict__ cand, const int32_t* __restr
             c.e_gro[i] = base++;
         }
     cand[r] = c;
-}
-
-// refit screening: count exactly only the new boxes predicted to improve
-__global__ void k_refit_screen(const float* __restrict__ pred, const uint64_t* __restrict__ obv, int32_t K,
-                               const obb_qbox* __restrict__ newq, obb_qbox* __restrict__ evals2,
-                               int32_t* __restrict__ map, int32_t* __restrict__ n2, float slack)
-{
-    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    if (!(pred[k] < (float)obv[k] * (1.0f + slack))) return;
-    const int32_t i = atomicAdd(n2, 1);
-    evals2[i] = newq[k];
-    map[i] = k;
 }
 
 __global__ void k_refit_accept_mapped(const double* __restrict__ newframe, const obb_qbox* __restrict__ newq,

@@ -254,6 +254,9 @@ obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_la
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_frame, sizeof(LatticeFrame), s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_fixed, sizeof(int32_t) * 3 * mesh->nv, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words, sizeof(uint64_t) * lat->n_words, s));
+    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_ref, sizeof(LatRef), s));
+    lat->ref = LatRef{lat->d_words, N, W};
+    OBB_CK(ctx, cudaMemcpyAsync(lat->d_ref, &lat->ref, sizeof(LatRef), cudaMemcpyHostToDevice, s));
     return rebuild_occupancy(ctx, lat);
 }
 

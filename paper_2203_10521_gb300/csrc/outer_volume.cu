@@ -99,15 +99,24 @@ __device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t d)   // d > 0
     return (q * d > a) ? q - 1 : q;
 }
 
-__global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __restrict__ d_K, int32_t N,
+__global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __restrict__ d_K,
+                       const LatRef* __restrict__ lats, int32_t n_lats, const int32_t* __restrict__ lat_of_box,
                        BoxPrep* __restrict__ prep, int64_t* __restrict__ tiles, int32_t* err)
 {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= *d_K) return;
     const obb_qbox q = boxes[k];
     BoxPrep p;
+    p.lat = lat_of_box ? lat_of_box[k] : 0;
+    p.pad1 = 0;
+    bool bad_lat = p.lat < 0 || p.lat >= n_lats;
+    if (bad_lat) {
+        atomicOr(err, kErrArg);
+        p.lat = 0;
+    }
+    const int32_t N = lats[p.lat].N;
     for (int i = 0; i < 9; ++i) p.n[i] = q.n[i];
-    bool empty = false;
+    bool empty = bad_lat;
     p.mode = 0;
     for (int a = 0; a < 3; ++a) {
         p.Lq[a] = -((-q.b[2 * a]) >> kS);
@@ -364,7 +373,7 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
 __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
                                                const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ d_K,
-                                               const uint64_t* __restrict__ words, int32_t N, int32_t W,
+                                               const LatRef* __restrict__ lats,
                                                unsigned long long* __restrict__ counts,
                                                unsigned long long* __restrict__ points,
                                                unsigned long long* __restrict__ acc)
@@ -404,6 +413,9 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
             tj = tk = 0;
         }
         const BoxPrep& p = prep[b];
+        const LatRef lr = lats[p.lat];
+        const uint64_t* __restrict__ words = lr.words;
+        const int32_t N = lr.N, W = lr.W;
         const int32_t mode = p.mode;
         const int32_t lwj = p.lwj;
         const int32_t wk = 32 >> lwj;
@@ -601,6 +613,13 @@ static int count_grid(obb_ctx* ctx)
 obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes, const int32_t* d_K,
                        int64_t K_cap, uint64_t* d_counts, uint64_t* d_points)
 {
+    return count_boxes_multi(ctx, lat->d_ref, 1, nullptr, d_boxes, d_K, K_cap, d_counts, d_points);
+}
+
+obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats, const int32_t* d_lat_of_box,
+                             const obb_qbox* d_boxes, const int32_t* d_K, int64_t K_cap, uint64_t* d_counts,
+                             uint64_t* d_points)
+{
     cudaStream_t s = ctx->stream;
     if (K_cap <= 0) return OBB_OK;
     if (K_cap > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_RANGE, "too many boxes in one call");
@@ -611,7 +630,8 @@ obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_b
     int64_t* off = tiles + K_cap;
     OBB_CK(ctx, cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * K_cap, s));
     if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K_cap, s));
-    k_prep<<<(unsigned)((K_cap + 127) / 128), 128, 0, s>>>(d_boxes, d_K, lat->frame.N, prep, tiles, ctx->d_err);
+    k_prep<<<(unsigned)((K_cap + 127) / 128), 128, 0, s>>>(d_boxes, d_K, d_lats, n_lats, d_lat_of_box, prep, tiles,
+                                                          ctx->d_err);
     note_launch(ctx);
     k_scan_i64<<<1, 1024, 0, s>>>(tiles, off, d_K);
     note_launch(ctx);
@@ -621,7 +641,7 @@ obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_b
         OBB_CK(ctx, cudaEventCreate(&e1));
         OBB_CK(ctx, cudaEventRecord(e0, s));
     }
-    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, lat->d_words, lat->frame.N, lat->frame.W,
+    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, d_lats,
                                             reinterpret_cast<unsigned long long*>(d_counts),
                                             reinterpret_cast<unsigned long long*>(d_points),
                                             ctx->prof ? ctx->d_prof : nullptr);
@@ -714,11 +734,12 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
     if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K, s));
     k_set_i32<<<1, 1, 0, s>>>(dK, (int32_t)K);
     note_launch(ctx);
-    k_prep<<<(unsigned)((K + 127) / 128), 128, 0, s>>>(d_boxes, dK, lat->frame.N, prep, chunks, ctx->d_err);
+    k_prep<<<(unsigned)((K + 127) / 128), 128, 0, s>>>(d_boxes, dK, lat->d_ref, 1, nullptr, prep, chunks,
+                                                      ctx->d_err);
     note_launch(ctx);
     k_scan_i64<<<1, 1024, 0, s>>>(chunks, off, dK);
     note_launch(ctx);
-    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, dK, lat->d_words, lat->frame.N, lat->frame.W,
+    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, dK, lat->d_ref,
                                             reinterpret_cast<unsigned long long*>(d_counts),
                                             reinterpret_cast<unsigned long long*>(d_points), nullptr);
     note_launch(ctx);

@@ -358,6 +358,7 @@ void obb_lattice_free(obb_lattice* lat)
     if (lat->d_frame) cudaFreeAsync(lat->d_frame, s);
     if (lat->d_fixed) cudaFreeAsync(lat->d_fixed, s);
     if (lat->d_words) cudaFreeAsync(lat->d_words, s);
+    if (lat->d_ref) cudaFreeAsync(lat->d_ref, s);
     delete lat;
 }
 
@@ -412,6 +413,56 @@ obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qb
                               uint64_t* counts, uint64_t* points, int32_t on_device)
 {
     return outer_volume_impl(ctx, lat, nullptr, boxes, K, counts, points, on_device);
+}
+
+obb_status obb_directional_outer_volume(obb_ctx* ctx, const obb_mesh* mesh, const obb_box* boxes, int64_t K,
+                                        int32_t m, double* out, int32_t on_device)
+{
+    if (!ctx || !mesh || (K > 0 && (!boxes || !out))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (m < 1 || m > 256) return fail(ctx, OBB_ERR_ARG, "m must be in [1, 256]");
+    if (K < 0 || K > (int64_t(1) << 24)) return fail(ctx, OBB_ERR_ARG, "K out of range");
+    if (K == 0) return OBB_OK;
+    HostTmp hb(ctx), ho(ctx);
+    const obb_box* db;
+    double* dout;
+    OBB_TRY(to_device(ctx, boxes, (size_t)K, on_device, hb, &db));
+    OBB_TRY(out_device(ctx, out, (size_t)K, on_device, ho, &dout));
+    OBB_TRY(directional_outer_volume(ctx, mesh, db, K, m, dout));
+    OBB_TRY(copy_back(ctx, out, dout, (size_t)K, on_device));
+    return on_device ? OBB_OK : check_device_error(ctx);
+}
+
+obb_status obb_outer_volume_multi(obb_ctx* ctx, const obb_lattice* const* lats, int32_t n_lats, const obb_qbox* boxes,
+                                  const int32_t* lattice_of_box, int64_t K, uint64_t* counts, uint64_t* points,
+                                  int32_t on_device)
+{
+    if (!ctx || !lats || n_lats < 1 || (K > 0 && (!boxes || !lattice_of_box || !counts)))
+        return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (K < 0 || K > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_ARG, "K out of range");
+    if (K == 0) return OBB_OK;
+    std::vector<LatRef> table(n_lats);
+    for (int32_t i = 0; i < n_lats; ++i) {
+        if (!lats[i]) return fail(ctx, OBB_ERR_ARG, "null lattice in the table");
+        if (lats[i]->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
+        table[i] = lats[i]->ref;
+    }
+    HostTmp ht(ctx), hb(ctx), hl(ctx), hc(ctx), hp(ctx);
+    const LatRef* dt;
+    const obb_qbox* db;
+    const int32_t* dl;
+    OBB_TRY(to_device(ctx, table.data(), table.size(), 0, ht, &dt));
+    OBB_TRY(to_device(ctx, boxes, (size_t)K, on_device, hb, &db));
+    OBB_TRY(to_device(ctx, lattice_of_box, (size_t)K, on_device, hl, &dl));
+    uint64_t *dc, *dp;
+    OBB_TRY(out_device(ctx, counts, (size_t)K, on_device, hc, &dc));
+    OBB_TRY(out_device(ctx, points, (size_t)K, on_device, hp, &dp));
+    OBB_CK(ctx, ctx->kdev.reserve(sizeof(int32_t), ctx->stream));
+    OBB_TRY(set_device_int(ctx, ctx->kdev.as<int32_t>(), (int32_t)K));
+    OBB_TRY(count_boxes_multi(ctx, dt, n_lats, dl, db, ctx->kdev.as<int32_t>(), K, dc, dp));
+    OBB_TRY(copy_back(ctx, counts, dc, (size_t)K, on_device));
+    OBB_TRY(copy_back(ctx, points, dp, (size_t)K, on_device));
+    // the lattice table lives in a temporary: wait before it is released
+    return check_device_error(ctx);
 }
 
 obb_status obb_outer_volume(obb_ctx* ctx, const obb_lattice* lat, const obb_box* boxes, int64_t K, uint64_t* counts,

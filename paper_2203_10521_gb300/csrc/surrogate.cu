@@ -43,24 +43,41 @@ __global__ void k_features(const obb_qbox* __restrict__ boxes, const int32_t* __
 {
     const int64_t b = blockIdx.x;
     if (b >= *d_K) return;
-    const obb_qbox q = boxes[b];
-    double M[9], inv[9], Lq[3], Hq[3];
-    for (int i = 0; i < 9; ++i) M[i] = (double)q.n[i];
-    for (int a = 0; a < 3; ++a) {
-        Lq[a] = (double)(-((-q.b[2 * a]) >> kS));
-        Hq[a] = (double)(q.b[2 * a + 1] >> kS);
+    // the box's inverse is computed once per block and shared
+    __shared__ double sh_M[9], sh_inv[9], sh_L[3], sh_H[3];
+    if (threadIdx.x == 0) {
+        const obb_qbox q = boxes[b];
+        double M[9];
+        for (int i = 0; i < 9; ++i) M[i] = (double)q.n[i];
+        for (int a = 0; a < 3; ++a) {
+            sh_L[a] = (double)(-((-q.b[2 * a]) >> kS));
+            sh_H[a] = (double)(q.b[2 * a + 1] >> kS);
+        }
+        const double c00 = __dsub_rn(__dmul_rn(M[4], M[8]), __dmul_rn(M[5], M[7]));
+        const double c01 = __dsub_rn(__dmul_rn(M[5], M[6]), __dmul_rn(M[3], M[8]));
+        const double c02 = __dsub_rn(__dmul_rn(M[3], M[7]), __dmul_rn(M[4], M[6]));
+        const double det = __dadd_rn(__dadd_rn(__dmul_rn(M[0], c00), __dmul_rn(M[1], c01)), __dmul_rn(M[2], c02));
+        const double adj[9] = {c00, __dsub_rn(__dmul_rn(M[2], M[7]), __dmul_rn(M[1], M[8])),
+                               __dsub_rn(__dmul_rn(M[1], M[5]), __dmul_rn(M[2], M[4])),
+                               c01, __dsub_rn(__dmul_rn(M[0], M[8]), __dmul_rn(M[2], M[6])),
+                               __dsub_rn(__dmul_rn(M[2], M[3]), __dmul_rn(M[0], M[5])),
+                               c02, __dsub_rn(__dmul_rn(M[1], M[6]), __dmul_rn(M[0], M[7])),
+                               __dsub_rn(__dmul_rn(M[0], M[4]), __dmul_rn(M[1], M[3]))};
+        for (int i = 0; i < 9; ++i) {
+            sh_M[i] = M[i];
+            sh_inv[i] = det != 0.0 ? __ddiv_rn(adj[i], det) : 0.0;
+        }
     }
-    const double c00 = __dsub_rn(__dmul_rn(M[4], M[8]), __dmul_rn(M[5], M[7]));
-    const double c01 = __dsub_rn(__dmul_rn(M[5], M[6]), __dmul_rn(M[3], M[8]));
-    const double c02 = __dsub_rn(__dmul_rn(M[3], M[7]), __dmul_rn(M[4], M[6]));
-    const double det = __dadd_rn(__dadd_rn(__dmul_rn(M[0], c00), __dmul_rn(M[1], c01)), __dmul_rn(M[2], c02));
-    const double adj[9] = {c00, __dsub_rn(__dmul_rn(M[2], M[7]), __dmul_rn(M[1], M[8])),
-                           __dsub_rn(__dmul_rn(M[1], M[5]), __dmul_rn(M[2], M[4])),
-                           c01, __dsub_rn(__dmul_rn(M[0], M[8]), __dmul_rn(M[2], M[6])),
-                           __dsub_rn(__dmul_rn(M[2], M[3]), __dmul_rn(M[0], M[5])),
-                           c02, __dsub_rn(__dmul_rn(M[1], M[6]), __dmul_rn(M[0], M[7])),
-                           __dsub_rn(__dmul_rn(M[0], M[4]), __dmul_rn(M[1], M[3]))};
-    for (int i = 0; i < 9; ++i) inv[i] = det != 0.0 ? __ddiv_rn(adj[i], det) : 0.0;
+    __syncthreads();
+    double M[9], inv[9], Lq[3], Hq[3];
+    for (int i = 0; i < 9; ++i) {
+        M[i] = sh_M[i];
+        inv[i] = sh_inv[i];
+    }
+    for (int a = 0; a < 3; ++a) {
+        Lq[a] = sh_L[a];
+        Hq[a] = sh_H[a];
+    }
     float* f = feats + b * (int64_t)kIn;
     if (threadIdx.x < 12) {
         const int t = threadIdx.x;

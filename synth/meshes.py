@@ -312,8 +312,46 @@ def marching_tetrahedra(f: np.ndarray, origin, spacing) -> Mesh:
     return _mesh(P, tris)
 
 
+def _primitive_boxes(scene):
+    """(kind, index, lo, hi) bounding boxes of every primitive."""
+    out = []
+    for i, s in enumerate(scene.spheres):
+        out.append(("s", i, s[:3] - s[3], s[:3] + s[3]))
+    for i, c in enumerate(scene.capsules):
+        out.append(("c", i, np.minimum(c[:3], c[3:6]) - c[6], np.maximum(c[:3], c[3:6]) + c[6]))
+    for i, b in enumerate(scene.rboxes):
+        rad = np.linalg.norm(b[3:6]) + b[6]
+        out.append(("b", i, b[:3] - rad, b[:3] + rad))
+    return out
+
+
+def _primitive_sdf(scene, kind, i, P):
+    if kind == "s":
+        s = scene.spheres[i]
+        return np.linalg.norm(P - s[:3], axis=-1) - s[3]
+    if kind == "c":
+        c = scene.capsules[i]
+        a, b, r = c[:3], c[3:6], c[6]
+        ab = b - a
+        t = np.clip(((P - a) @ ab) / max(float(ab @ ab), 1e-300), 0.0, 1.0)
+        return np.linalg.norm(P - (a + t[..., None] * ab), axis=-1) - r
+    bx = scene.rboxes[i]
+    c, h, rr = bx[:3], bx[3:6], bx[6]
+    R = bx[7:16].reshape(3, 3)
+    L = (P - c) @ R.T
+    q = np.abs(L) - (h - rr)
+    return np.linalg.norm(np.maximum(q, 0.0), axis=-1) + np.minimum(np.max(q, axis=-1), 0.0) - rr
+
+
 def sdf_union_mesh(seed: int, grid: int, n_spheres=40, n_capsules=20, n_rboxes=0) -> Mesh:
-    """Watertight surface of a seeded SDF union on a grid^3 sampling of its padded AABB."""
+    """Watertight surface of a seeded SDF union on a grid^3 sampling of its padded AABB.
+
+    Each primitive updates the field only inside its bounding box widened by
+    three cells; elsewhere the field keeps a positive placeholder.  Every grid
+    edge that changes sign lies within one cell of the surface, hence inside
+    the widened box of each primitive that can be the minimum there, so the
+    sign everywhere and the values used for interpolation are those of the
+    full union."""
     scene = sdf_scene(seed, n_spheres, n_capsules, n_rboxes)
     lo, hi = scene.bounds()
     ext = hi - lo
@@ -321,20 +359,19 @@ def sdf_union_mesh(seed: int, grid: int, n_spheres=40, n_capsules=20, n_rboxes=0
     lo = lo - pad
     hi = hi + pad
     spacing = (hi - lo) / (grid - 1)
-    fld = np.empty((grid, grid, grid), dtype=np.float64)
-    ys = lo[1] + spacing[1] * np.arange(grid)
-    xs = lo[0] + spacing[0] * np.arange(grid)
-    for k in range(grid):
-        z = lo[2] + spacing[2] * k
-        X, Y = np.meshgrid(xs, ys, indexing="ij")
-        P = np.stack([X, Y, np.full_like(X, z)], -1)
-        fld[:, :, k] = scene.sdf(P)
-    # the outer grid layer is outside by construction of the padding; enforce it
-    fld[0, :, :] = fld[-1, :, :] = np.abs(fld[0, :, :]) + 1.0
-    fld[:, 0, :] = np.abs(fld[:, 0, :]) + 1.0
-    fld[:, -1, :] = np.abs(fld[:, -1, :]) + 1.0
-    fld[:, :, 0] = np.abs(fld[:, :, 0]) + 1.0
-    fld[:, :, -1] = np.abs(fld[:, :, -1]) + 1.0
+    fld = np.full((grid, grid, grid), 1.0, dtype=np.float64)
+    for kind, i, plo, phi in _primitive_boxes(scene):
+        a = np.maximum(np.floor((plo - lo) / spacing).astype(np.int64) - 3, 1)
+        b = np.minimum(np.ceil((phi - lo) / spacing).astype(np.int64) + 3, grid - 2)
+        if np.any(a > b):
+            continue
+        xs = lo[0] + spacing[0] * np.arange(a[0], b[0] + 1)
+        ys = lo[1] + spacing[1] * np.arange(a[1], b[1] + 1)
+        zs = lo[2] + spacing[2] * np.arange(a[2], b[2] + 1)
+        X, Y, Z = np.meshgrid(xs, ys, zs, indexing="ij")
+        d = _primitive_sdf(scene, kind, i, np.stack([X, Y, Z], -1))
+        sub = fld[a[0]:b[0] + 1, a[1]:b[1] + 1, a[2]:b[2] + 1]
+        np.minimum(sub, d, out=sub)
     return marching_tetrahedra(fld, lo, spacing)
 
 
@@ -354,6 +391,20 @@ SDF_GRID_200K = 74
 def sdf_union_200k(seed=2000, grid=SDF_GRID_200K) -> Mesh:
     """SDF union of 40 spheres and 20 capsules, ~200k watertight triangles."""
     return sdf_union_mesh(seed, grid, 40, 20, 0)
+
+
+SDF_GRID_1M = 165
+SDF_GRID_2M = 206
+
+
+def sdf_union_1m(seed=4000, grid=SDF_GRID_1M) -> Mesh:
+    """SDF union of 40 spheres and 20 capsules at a finer sampling, ~1M triangles."""
+    return sdf_union_mesh(seed, grid, 40, 20, 0)
+
+
+def sdf_union_2m(seed=5000, grid=SDF_GRID_2M) -> Mesh:
+    """SDF union of 200 spheres, 100 capsules and 50 rounded boxes, ~2M triangles."""
+    return sdf_union_mesh(seed, grid, 200, 100, 50)
 
 
 def watertight_edges(tris: np.ndarray) -> bool:
@@ -386,3 +437,17 @@ def subdivided_tetrahedron(jitter=0.0, seed=0) -> Mesh:
         rng = np.random.Generator(np.random.PCG64(seed))
         V = V + rng.uniform(-jitter, jitter, size=V.shape)
     return _mesh(V, nf)
+
+
+def sdf_batch(count: int, seed: int = 3000):
+    """Meshes of uneven size for batched runs: SDF unions of 10 spheres and 5
+    capsules sampled on a log-uniform grid (about 1k to 100k triangles), each
+    with a lattice size drawn from {128, 192, 256, 320, 384}.  Returns a list of
+    (mesh, N)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        grid = int(round(np.exp(rng.uniform(np.log(12), np.log(110)))))
+        N = int(rng.choice([128, 192, 256, 320, 384]))
+        out.append((sdf_union_mesh(seed + 1 + i, grid, 10, 5, 0), N))
+    return out

@@ -1,0 +1,95 @@
+"""GPU parity on the large workloads: the ~1M-triangle SDF union on a 768^3
+lattice and the ~2M-triangle union of spheres, capsules and rounded boxes on
+1024^3.  The oracle checks sampled occupancy rows and small boxes exactly."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import meshes as M
+from tests import pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2203_10521_gb300 as P
+    c = P.Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _small_boxes(rng, K, lo, hi, half_lo, half_hi):
+    out = np.zeros((K, 12), dtype=np.float32)
+    for i in range(K):
+        R = pins.random_rotation(rng)
+        out[i, :3] = rng.uniform(lo, hi)
+        out[i, 3:6], out[i, 6:9] = R[0], R[1]
+        out[i, 9:12] = rng.uniform(half_lo, half_hi, 3)
+    return out
+
+
+@pytest.mark.parametrize("name,N,ncols,nbox", [("1m", 768, 48, 4), ("2m", 1024, 32, 3)])
+def test_large_config_sampled_parity(ctx, name, N, ncols, nbox):
+    m = M.sdf_union_1m() if name == "1m" else M.sdf_union_2m()
+    assert m.n_tris > (900_000 if name == "1m" else 1_800_000)
+    mesh = ctx.mesh_create(m.verts, m.tris)
+    lat = ctx.build_occupancy(mesh, N)
+    P = O.Problem(m.verts, m.tris, N, adj=np.zeros((m.n_tris, 3), np.int32))
+    assert np.array_equal(lat.lo, P.lo) and np.array_equal(lat.spacing, P.h)
+    assert np.array_equal(lat.fixed().cpu().numpy(), P.U)
+    rng = np.random.Generator(np.random.PCG64(N))
+    cols = rng.integers(0, N, size=(ncols, 2))
+    P.occ.fill_columns(cols)
+    w = lat.words().cpu().numpy().view(np.uint64).reshape(N, N, lat.W)
+    for j, k in cols:
+        row = np.unpackbits(w[k, j].view(np.uint8), bitorder="little")
+        assert np.array_equal(row[:N], P.occ.occ[k, j])
+        assert not row[N:].any()
+    ext = P.lo + N * P.h
+    boxes = _small_boxes(rng, nbox, P.lo + 0.3 * (ext - P.lo), P.lo + 0.7 * (ext - P.lo), 0.004, 0.012)
+    cnt, pts = ctx.outer_volume(lat, boxes, want_points=True)
+    n, bnd = O.quantize_boxes(boxes, P.lo, P.h)
+    ref, tot = O.outer_volume(P.occ, n, bnd)
+    assert np.array_equal(cnt, ref) and np.array_equal(pts, tot)
+    assert tot.min() > 100
+    lat.free()
+    mesh.free()
+
+
+def test_batched_meshes_one_launch(ctx):
+    """Many meshes of uneven size (about 1k-100k triangles, lattices 128^3-384^3):
+    every box of every mesh counted in one launch, exact against the oracle."""
+    batch = M.sdf_batch(10, seed=3000)
+    lats, meshes, probs = [], [], []
+    for m, N in batch:
+        mesh = ctx.mesh_create(m.verts, m.tris)
+        meshes.append(mesh)
+        lats.append(ctx.build_occupancy(mesh, N))
+        probs.append(O.Problem(m.verts, m.tris, N, adj=np.zeros((m.n_tris, 3), np.int32)))
+    rng = np.random.Generator(np.random.PCG64(33))
+    qs, which = [], []
+    for i, P in enumerate(probs):
+        ext = P.lo + P.N * P.h
+        boxes = _small_boxes(rng, 12, P.lo + 0.2 * (ext - P.lo), P.lo + 0.8 * (ext - P.lo), 0.01, 0.06)
+        qs.append(ctx.quantize_boxes(lats[i], boxes))
+        which.append(np.full(12, i, np.int32))
+    q = np.concatenate(qs)
+    li = np.concatenate(which)
+    perm = rng.permutation(len(q))          # interleave the meshes' boxes
+    cnt, pts = ctx.outer_volume_multi(lats, q[perm], li[perm], want_points=True)
+    for i, P in enumerate(probs):
+        sel = li[perm] == i
+        ref, tot = O.outer_volume(P.occ, q[perm][sel]["n"], q[perm][sel]["b"])
+        assert np.array_equal(cnt[sel], ref) and np.array_equal(pts[sel], tot)
+        assert np.array_equal(ctx.outer_volume_q(lats[i], q[perm][sel]), ref)
+    import paper_2203_10521_gb300 as PK
+    with pytest.raises(PK.ObbError):
+        ctx.outer_volume_multi(lats, q[:1], np.array([len(lats)], np.int32))
+    for lat, mesh in zip(lats, meshes):
+        lat.free()
+        mesh.free()
