@@ -289,6 +289,30 @@ obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* layer, int32_t* assign,
                           obb_qbox* qboxes, obb_box* boxes, uint64_t* obv, int32_t on_device);
 int32_t obb_layer_clusters(const obb_layer* layer);
 
+/* The layer's parent map, int32 [K] (host array), as given to obb_layer_init
+ * and as changed by obb_unit_step on the layer above.  Synchronises. */
+obb_status obb_layer_parents(obb_ctx* ctx, const obb_layer* layer, int32_t* parent);
+
+/* One Lloyd iteration of `upper` whose division units are the boxes of
+ * `lower` (Sec. 4.2.2, bottom-up merging: the same-layer method with boxes,
+ * not triangles, as the unit).  The two layers must nest: for every triangle
+ * t, upper.assign[t] == lower.parent[lower.assign[t]], else OBB_ERR_ARG.
+ * A unit u of cluster s moves as a whole to a cluster k != s with the same
+ * parent (upper's parent map) that holds a triangle edge-adjacent to one of
+ * u's triangles, provided s keeps another unit; the exact gain is
+ *   [OBV(s) - OBV(s without u)] - [OBV(k with u) - OBV(k)]
+ * with tight slab bounds in the clusters' own frames.  Each unit proposes
+ * its best k (gain > 0, ties -> smallest k); proposals are matched as in
+ * obb_lloyd_step (key: gain desc, unit asc), so accepted moves touch
+ * disjoint clusters and the total falls by exactly the sum of their gains.
+ * Rounds repeat up to opts->rounds (<= 0: 16) or until none is accepted.
+ * lower's parent map and upper's assignment, boxes and outer volumes change
+ * in place; then upper's boxes are updated as opts->refit says (as in
+ * obb_lloyd_step).  A unit may border at most 8 sibling clusters
+ * (OBB_ERR_STATE beyond).  stats may be NULL.  Synchronises. */
+obb_status obb_unit_step(obb_ctx* ctx, obb_layer* upper, obb_layer* lower, const obb_step_opts* opts,
+                         obb_step_stats* stats);
+
 /* Median split of every cluster of the layer into two children, the seeding
  * step of the top-down decomposition (Sec. 4.2.2): triangles of cluster c are
  * ordered by key n_0 . (U_p + U_q + U_r) (the cluster's quantised major axis
@@ -308,6 +332,22 @@ typedef struct {
     int32_t refit;    /* box-parameter update in each iteration (obb_step_opts.refit) */
 } obb_tree_opts;
 
+typedef struct {
+    int32_t sweeps;   /* reciprocating sweeps (bottom-up pass, then top-down pass) */
+    int32_t iters;    /* Lloyd iterations per level visit (stop early when one changes nothing) */
+    int32_t rounds;   /* partition rounds per iteration; <= 0: 16 */
+    int32_t refit;    /* box-parameter update in each iteration (obb_step_opts.refit) */
+} obb_sweep_opts;
+
+typedef struct {
+    double eq7_before;        /* Eq. 7 in lattice points before and after the sweeps */
+    double eq7_after;
+    int64_t unit_moves;       /* moves of whole lower-level boxes */
+    int64_t triangle_moves;   /* moves of triangles at the leaf level */
+    int32_t level_iters;      /* Lloyd iterations run over all level visits */
+    int32_t reserved;
+} obb_sweep_stats;
+
 /* Binary OBB tree by top-down decomposition (Sec. 4.2.2): the root box
  * holds every triangle; each level splits every node into two children at
  * the median of its triangles along the node's major axis (key n_0 . (U_p +
@@ -321,6 +361,8 @@ obb_status obb_build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_o
 obb_status obb_tree_read(obb_ctx* ctx, const obb_tree* tree, int32_t level, int32_t* assign,
                          double* frames, obb_qbox* qboxes, obb_box* boxes, uint64_t* obv);
 int32_t obb_tree_depth(const obb_tree* tree);
+/* Parent map of layer `level` (int32 [2^level], host array; the root's is {0}). */
+obb_status obb_tree_parents(obb_ctx* ctx, const obb_tree* tree, int32_t level, int32_t* parent);
 
 /* Eq. 7 with the layer weights of Sec. 5 (a level's weight = its number of
  * levels to the leaves plus one: leaves 1, their parents 2, ...), each layer's
@@ -328,6 +370,15 @@ int32_t obb_tree_depth(const obb_tree* tree);
  * *points = weighted sum in lattice points, *volume = the same times
  * h_0 h_1 h_2.  Either pointer may be NULL. */
 obb_status obb_tree_score(obb_ctx* ctx, const obb_tree* tree, double* points, double* volume);
+
+/* Reciprocating optimisation between levels (Sec. 4.2.2, Fig. 5): each sweep
+ * first merges bottom-up -- for levels depth-1 .. 1, up to opts->iters
+ * obb_unit_step iterations with the level below as units, stopping the pass
+ * at the first level whose Eq. 7 does not strictly drop -- and then
+ * decomposes top-down: levels 1 .. depth again, unit steps at the inner
+ * levels and obb_lloyd_step (triangles) at the leaves.  Every step keeps the
+ * tree nested and never raises Eq. 7.  stats may be NULL.  Synchronises. */
+obb_status obb_tree_sweep(obb_ctx* ctx, obb_tree* tree, const obb_sweep_opts* opts, obb_sweep_stats* stats);
 void obb_tree_free(obb_tree* tree);
 
 /* ---------------------------------------------------- learned surrogate (e) */

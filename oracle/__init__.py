@@ -77,6 +77,8 @@ def _declare(L):
     L.orc_tight_bounds.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     L.orc_lloyd_moves.argtypes = [vp, vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp, i32, i32, vp]
     L.orc_lloyd_moves.restype = C.c_int
+    L.orc_unit_moves.argtypes = [vp, vp, vp, i64, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, i32, i32, vp]
+    L.orc_unit_moves.restype = C.c_int
     L.orc_moments.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     L.orc_covariance_from_moments.argtypes = [vp, vp]
     L.orc_covariance_from_moments.restype = C.c_int
@@ -444,6 +446,83 @@ def lloyd_step(P: Problem, L: Layer, rounds: int = 16, do_refit=1, descent_steps
         for _ in range(descent_steps):
             descent_step(P, L)
     return st, acc
+
+
+def unit_moves(P: Problem, up: Layer, low: Layer, rounds: int):
+    """Partition rounds between levels (Sec. 4.2.2, bottom-up merging): the
+    clusters of `low` move as whole units between sibling clusters of `up`.
+    Updates low.parent (the unit -> cluster map), up.assign, up.bnd, up.obv in
+    place.  Returns per-round stats."""
+    st = (RoundStats * max(rounds, 1))()
+    T = P.F.shape[0]
+    while True:
+        cl = low.parent.copy()
+        bnd, obv = up.bnd.copy(), up.obv.copy()
+        rc = lib().orc_unit_moves(_p(P.U), _p(P.F), _p(P.adj), T, _p(low.assign), low.K, _p(cl), _p(up.parent),
+                                  up.K, _p(up.n), _p(bnd), _p(obv), _p(P.occ.occ), _p(P.occ.known), P.N,
+                                  int(rounds), st)
+        if rc == -3:
+            P.occ.fill_all()
+            continue
+        if rc < 0:
+            raise RuntimeError(f"orc_unit_moves failed ({rc})")
+        moved = np.nonzero(cl != low.parent)[0]
+        up.level[low.parent[moved]] = 0     # a new member set restarts the descent
+        up.level[cl[moved]] = 0
+        low.parent[:] = cl
+        up.assign[:] = cl[low.assign]
+        up.bnd[:], up.obv[:] = bnd, obv
+        return [dict(proposals=s.proposals, accepted=s.accepted, gain=s.gain, evals=s.evals)
+                for s in st[:rc]]
+
+
+def unit_lloyd_step(P: Problem, up: Layer, low: Layer, rounds: int = 16, do_refit=1, descent_steps: int = 2):
+    """One Lloyd iteration of level `up` with the clusters of `low` as units,
+    then the box update of `up` (same modes as lloyd_step)."""
+    st = unit_moves(P, up, low, rounds)
+    mode = int(do_refit)
+    acc = refit(P, up) if mode & 1 else np.zeros(up.K, dtype=np.uint8)
+    if mode & 2:
+        for _ in range(descent_steps):
+            descent_step(P, up)
+    return st, acc
+
+
+def tree_eq7(layers):
+    """Eq. 7 of a list of layers (root first) in lattice points."""
+    return eq7_score([L.obv for L in layers], len(layers) - 1)
+
+
+def tree_sweeps(P: Problem, layers, sweeps: int = 1, iters: int = 2, rounds: int = 16, do_refit=1):
+    """Reciprocating optimisation between levels (Sec. 4.2.2).  Each sweep
+    first merges bottom-up: for levels D-1 .. 1 the clusters of the level
+    below are the units; the pass stops at the first level whose Eq. 7 does
+    not strictly drop.  Then it decomposes top-down: levels 1 .. D again, with
+    units at the inner levels and triangles at the leaves.  Every level runs
+    up to `iters` Lloyd iterations and stops early on one that changes nothing.
+    Returns Eq. 7 before and after each sweep."""
+    D = len(layers) - 1
+    hist = [tree_eq7(layers)]
+
+    def level(lev):
+        for _ in range(iters):
+            if lev < D:
+                st, acc = unit_lloyd_step(P, layers[lev], layers[lev + 1], rounds, do_refit)
+            else:
+                st, acc = lloyd_step(P, layers[lev], rounds, do_refit)
+            if sum(s["accepted"] for s in st) == 0 and not acc.any():
+                break
+
+    for _ in range(sweeps):
+        for lev in range(D - 1, 0, -1):
+            e0 = tree_eq7(layers)
+            level(lev)
+            if not tree_eq7(layers) < e0:
+                break
+        for lev in range(1, D + 1):
+            level(lev)
+        hist.append(tree_eq7(layers))
+    return hist
 
 
 def median_split(P: Problem, L: Layer):

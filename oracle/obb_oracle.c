@@ -603,6 +603,156 @@ int orc_lloyd_moves(const int32_t* U, const int32_t* F, const int32_t* adj, int6
     return err ? err : ran;
 }
 
+/*
+ * Partition rounds between levels (Sec. 4.2.2, bottom-up merging): the units
+ * are the clusters of the level below (unit_of_tri: [nt] unit ids, Ku units);
+ * cluster_of_unit: [Ku] the cluster of this level each unit belongs to (the
+ * lower level's parent map, updated in place).  A unit u of cluster s moves as
+ * a whole; it may go to a cluster k != s that shares s's parent (parent: [K])
+ * and holds a triangle edge-adjacent to one of u's triangles, if s keeps at
+ * least one other unit.  For each such k:
+ *   gain = [OBV(s) - OBV(s without u)] - [OBV(k with u) - OBV(k)]
+ * with both boxes recomputed from scratch (tight slab of all member
+ * triangles in the cluster's own frame).  u proposes its best k (max gain,
+ * ties -> smallest k) when the gain is > 0, and proposals are matched exactly
+ * as in orc_lloyd_moves (key: gain desc, unit asc).  With one triangle per
+ * unit this is the triangle step.  Returns the number of rounds run, or a
+ * negative error (-3: a needed occupancy column is missing).
+ */
+static void cluster_bounds(const int32_t* U, const int32_t* F, int64_t nt, const int32_t* unit_of_tri,
+                           const int32_t* cluster_of_unit, int32_t k, int32_t skip_unit, int32_t add_unit,
+                           const int32_t* n, int64_t* out)
+{
+    for (int a = 0; a < 3; ++a) {
+        out[2 * a] = INT64_MAX;
+        out[2 * a + 1] = INT64_MIN;
+    }
+    for (int64_t t = 0; t < nt; ++t) {
+        const int32_t u = unit_of_tri[t];
+        const int member = (cluster_of_unit[u] == k && u != skip_unit) || u == add_unit;
+        if (!member) continue;
+        for (int v = 0; v < 3; ++v) {
+            const int32_t* P = U + 3 * (int64_t)F[3 * t + v];
+            for (int a = 0; a < 3; ++a) {
+                int64_t d = (int64_t)n[3 * a] * P[0] + (int64_t)n[3 * a + 1] * P[1] + (int64_t)n[3 * a + 2] * P[2];
+                if (d < out[2 * a]) out[2 * a] = d;
+                if (d > out[2 * a + 1]) out[2 * a + 1] = d;
+            }
+        }
+    }
+}
+
+int orc_unit_moves(const int32_t* U, const int32_t* F, const int32_t* adj, int64_t nt,
+                   const int32_t* unit_of_tri, int32_t Ku, int32_t* cluster_of_unit, const int32_t* parent,
+                   int32_t K, const int32_t* n, int64_t* bnd, uint64_t* obv, const uint8_t* occ,
+                   const uint8_t* colmask, int32_t N, int32_t rounds, orc_round_stats* stats)
+{
+    int64_t* usize = (int64_t*)calloc((size_t)K, sizeof(int64_t));
+    uint8_t* cand = (uint8_t*)calloc((size_t)K, 1);
+    int32_t* pdst = (int32_t*)malloc(sizeof(int32_t) * (size_t)(Ku > 0 ? Ku : 1));
+    int64_t* pgain = (int64_t*)malloc(sizeof(int64_t) * (size_t)(Ku > 0 ? Ku : 1));
+    int64_t* pnewsrc = (int64_t*)malloc(sizeof(int64_t) * 6 * (size_t)(Ku > 0 ? Ku : 1));
+    int64_t* pnewdst = (int64_t*)malloc(sizeof(int64_t) * 6 * (size_t)(Ku > 0 ? Ku : 1));
+    uint64_t* pobvsrc = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(Ku > 0 ? Ku : 1));
+    uint64_t* pobvdst = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(Ku > 0 ? Ku : 1));
+    int32_t* best = (int32_t*)malloc(sizeof(int32_t) * (size_t)(K > 0 ? K : 1));
+    int ran = 0, err = 0;
+    for (int r = 0; r < rounds && !err; ++r) {
+        orc_round_stats st = {0, 0, 0, 0};
+        memset(usize, 0, sizeof(int64_t) * (size_t)K);
+        for (int32_t u = 0; u < Ku; ++u) usize[cluster_of_unit[u]]++;
+        for (int32_t u = 0; u < Ku && !err; ++u) {
+            pdst[u] = -1;
+            const int32_t s = cluster_of_unit[u];
+            if (usize[s] < 2) continue;
+            /* candidate clusters: siblings of s next to one of u's triangles */
+            memset(cand, 0, (size_t)K);
+            int nc = 0;
+            for (int64_t t = 0; t < nt; ++t) {
+                if (unit_of_tri[t] != u) continue;
+                for (int e = 0; e < 3; ++e) {
+                    const int32_t k = cluster_of_unit[unit_of_tri[adj[3 * t + e]]];
+                    if (k == s || parent[k] != parent[s] || cand[k]) continue;
+                    cand[k] = 1;
+                    ++nc;
+                }
+            }
+            if (nc == 0) continue;
+            int64_t shr[6];
+            cluster_bounds(U, F, nt, unit_of_tri, cluster_of_unit, s, u, -1, n + 9 * s, shr);
+            if (same6(shr, bnd + 6 * s)) continue; /* removal gain 0, add cost >= 0 */
+            uint64_t obv_shr;
+            if (count_one(occ, colmask, N, n + 9 * s, shr, &obv_shr)) { err = -3; break; }
+            st.evals++;
+            const int64_t remove_gain = (int64_t)obv[s] - (int64_t)obv_shr;
+            int64_t bestg = 0;
+            int32_t bestk = -1;
+            int64_t bestb[6];
+            uint64_t besto = 0;
+            for (int32_t k = 0; k < K; ++k) {   /* ascending k: ties keep the smallest */
+                if (!cand[k]) continue;
+                int64_t gro[6];
+                cluster_bounds(U, F, nt, unit_of_tri, cluster_of_unit, k, -1, u, n + 9 * k, gro);
+                uint64_t obv_gro = obv[k];
+                if (!same6(gro, bnd + 6 * k)) {
+                    if (count_one(occ, colmask, N, n + 9 * k, gro, &obv_gro)) { err = -3; break; }
+                    st.evals++;
+                }
+                const int64_t g = remove_gain - ((int64_t)obv_gro - (int64_t)obv[k]);
+                if (g > 0 && (bestk < 0 || g > bestg)) {
+                    bestg = g;
+                    bestk = k;
+                    memcpy(bestb, gro, sizeof(bestb));
+                    besto = obv_gro;
+                }
+            }
+            if (err || bestk < 0) continue;
+            pdst[u] = bestk;
+            pgain[u] = bestg;
+            memcpy(pnewsrc + 6 * u, shr, sizeof(shr));
+            memcpy(pnewdst + 6 * u, bestb, sizeof(bestb));
+            pobvsrc[u] = obv_shr;
+            pobvdst[u] = besto;
+            st.proposals++;
+        }
+        if (err) break;
+        for (int32_t k = 0; k < K; ++k) best[k] = -1;
+        for (int32_t u = 0; u < Ku; ++u) {
+            if (pdst[u] < 0) continue;
+            const int32_t ends[2] = {cluster_of_unit[u], pdst[u]};
+            for (int e = 0; e < 2; ++e) {
+                const int32_t c = ends[e];
+                const int32_t o = best[c];
+                if (o < 0 || pgain[u] > pgain[o] || (pgain[u] == pgain[o] && u < o)) best[c] = u;
+            }
+        }
+        int64_t acc = 0;
+        for (int32_t u = 0; u < Ku; ++u) {
+            if (pdst[u] < 0) continue;
+            if (best[cluster_of_unit[u]] == u && best[pdst[u]] == u) pgain[u] = -pgain[u] - 1; /* mark */
+        }
+        for (int32_t u = 0; u < Ku; ++u) {
+            if (pdst[u] < 0 || pgain[u] >= 0) continue;
+            const int64_t g = -(pgain[u] + 1);
+            const int32_t s = cluster_of_unit[u], k = pdst[u];
+            memcpy(bnd + 6 * s, pnewsrc + 6 * u, sizeof(int64_t) * 6);
+            memcpy(bnd + 6 * k, pnewdst + 6 * u, sizeof(int64_t) * 6);
+            obv[s] = pobvsrc[u];
+            obv[k] = pobvdst[u];
+            cluster_of_unit[u] = k;
+            acc++;
+            st.gain += g;
+        }
+        st.accepted = acc;
+        if (stats) stats[r] = st;
+        ran = r + 1;
+        if (acc == 0) break;
+    }
+    free(usize); free(cand); free(pdst); free(pgain); free(pnewsrc); free(pnewdst);
+    free(pobvsrc); free(pobvdst); free(best);
+    return err ? err : ran;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Refit: area-weighted covariance and cyclic Jacobi (FP64)                  */
 /* ------------------------------------------------------------------------- */

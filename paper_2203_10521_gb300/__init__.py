@@ -61,6 +61,18 @@ class TreeOpts(C.Structure):
     _fields_ = [("depth", C.c_int32), ("iters", C.c_int32), ("rounds", C.c_int32), ("refit", C.c_int32)]
 
 
+class SweepOpts(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("iters", C.c_int32), ("rounds", C.c_int32), ("refit", C.c_int32)]
+
+
+class SweepStats(C.Structure):
+    _fields_ = [("eq7_before", C.c_double), ("eq7_after", C.c_double), ("unit_moves", C.c_int64),
+                ("triangle_moves", C.c_int64), ("level_iters", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _lib = None
 
 
@@ -98,6 +110,10 @@ def load(build_if_missing: bool = True):
         "obb_build_tree": [vp, vp, C.POINTER(TreeOpts), C.POINTER(vp)],
         "obb_tree_read": [vp, vp, i32, vp, vp, vp, vp, vp],
         "obb_tree_score": [vp, vp, vp, vp],
+        "obb_tree_parents": [vp, vp, i32, vp],
+        "obb_tree_sweep": [vp, vp, C.POINTER(SweepOpts), C.POINTER(SweepStats)],
+        "obb_layer_parents": [vp, vp, vp],
+        "obb_unit_step": [vp, vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
         "obb_mlp_create": [vp, C.c_uint64, C.POINTER(vp)],
         "obb_mlp_params": [vp, vp, vp, i32],
         "obb_mlp_set_params": [vp, vp, vp, i32],
@@ -136,7 +152,8 @@ def exported_symbols():
             "obb_quantize_boxes", "obb_outer_volume_q", "obb_outer_volume", "obb_outer_volume_q_noalloc",
             "obb_outer_volume_multi", "obb_directional_outer_volume", "obb_layer_init", "obb_lloyd_step",
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
-            "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free",
+            "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free", "obb_tree_parents",
+            "obb_tree_sweep", "obb_layer_parents", "obb_unit_step",
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_mlp_forward", "obb_mlp_gradients", "obb_mlp_train_step",
             "obb_layer_set_surrogate", "obb_layer_last_candidates"]
@@ -341,6 +358,19 @@ class Context:
         self.check(self.lib.obb_lloyd_step(self.h, layer.h, C.byref(o), C.byref(st) if stats else None))
         return st.as_dict() if stats else None
 
+    def unit_step(self, upper, lower, rounds=16, refit=True, stats=True, descent_steps=0):
+        """One Lloyd iteration of `upper` with the clusters of `lower` as units
+        (bottom-up merging, Sec. 4.2.2); refit as in lloyd_step."""
+        o = StepOpts(int(rounds), int(refit), int(descent_steps), 0)
+        st = StepStats()
+        self.check(self.lib.obb_unit_step(self.h, upper.h, lower.h, C.byref(o), C.byref(st) if stats else None))
+        return st.as_dict() if stats else None
+
+    def layer_parents(self, layer):
+        p = np.zeros(layer.K, np.int32)
+        self.check(self.lib.obb_layer_parents(self.h, layer.h, p.ctypes.data_as(C.c_void_p)))
+        return p
+
     def layer_read(self, layer):
         T, K = layer.lat.mesh.nt, layer.K
         assign = np.zeros(T, np.int32)
@@ -463,6 +493,18 @@ class Context:
                                           frames.ctypes.data_as(C.c_void_p), q.ctypes.data_as(C.c_void_p),
                                           boxes.ctypes.data_as(C.c_void_p), obv.ctypes.data_as(C.c_void_p)))
         return dict(assign=assign, frames=frames, qboxes=q, boxes=boxes, obv=obv)
+
+    def tree_parents(self, tree, level):
+        p = np.zeros(1 << level, np.int32)
+        self.check(self.lib.obb_tree_parents(self.h, tree.h, int(level), p.ctypes.data_as(C.c_void_p)))
+        return p
+
+    def tree_sweep(self, tree, sweeps=1, iters=2, rounds=16, refit=True):
+        """Reciprocating bottom-up / top-down sweeps over the tree's levels (Sec. 4.2.2)."""
+        o = SweepOpts(int(sweeps), int(iters), int(rounds), int(refit))
+        st = SweepStats()
+        self.check(self.lib.obb_tree_sweep(self.h, tree.h, C.byref(o), C.byref(st)))
+        return st.as_dict()
 
     def tree_score(self, tree):
         p = C.c_double()

@@ -52,22 +52,24 @@ struct LatticeFrame {
 // moves by qstep_a with remainder carry rstep_a (an integer DDA).
 struct BoxPrep {
     int32_t n[9];
-    int32_t i0, i1;          // index-space AABB along x
+    int32_t i0, span;        // index-space AABB along x: [i0, i0 + span]
     int32_t j0, k0;          // first row
-    int32_t nj, nk;          // rows along y and z
+    int32_t nj, nk;          // rows along y and z (0 = empty box)
     int32_t ntj;             // tiles along y: ceil(nj / wj)
     int32_t lwj;             // log2 of wj, the lanes of a tile along y (wk = 32 / wj along z)
-    int32_t mode;            // bit a: n_a0 != 0 (slab a bounds i by quotients)
-    int32_t pad0;
+    int32_t mode;            // 2 bits per slab: 0 n_a0 = 0, 1 32-bit DDA, 2 per-row clip
     int32_t dd[3];           // |n_a0|
-    int32_t sg[3];           // sign of n_a0
     int32_t rstep[3];        // remainder of that step, in [0, dd)
     int32_t qstep[3];        // quotient of the step between a lane's rows (|.| < 2^25 for DDA slabs)
-    int64_t Lq[3], Hq[3];    // ceil(lo / 256), floor(hi / 256)
-    float rcp[3];            // 1 / dd (seed of the exact initial division)
-    uint64_t rows;           // nj * nk (0 = empty)
     int32_t lat;             // index of the box's lattice in the launch's lattice table
-    int32_t pad1;
+    float rcp[3];            // 1 / dd (seed of the exact initial division)
+    int64_t Lq[3], Hq[3];    // ceil(lo / 256), floor(hi / 256)
+    // Separating axes of the box's shadow on the (j, k) plane: the normals of
+    // its three projected edge directions, and the shadow's extent along each,
+    // widened by two rows.  A tile whose rectangle lies outside one of these
+    // bands holds no row of the box.
+    float sat_nu[3][2];
+    float sat_lo[3], sat_hi[3];
 };
 
 // One lattice as the counting kernel sees it (a table of these lets one launch
@@ -96,7 +98,7 @@ struct obb_ctx {
     int num_sms = 0;
     std::string err;
     int32_t* d_err = nullptr;        // device error word
-    int32_t* h_small = nullptr;      // pinned host staging (64 ints)
+    int32_t* h_small = nullptr;      // pinned host staging (512 bytes; the first 64 hold the error word)
     // scratch reused across calls
     obbv::DevBuf prep, chunk_off, qscratch, cscratch, pscratch, kdev, tmp_a, tmp_b, tmp_c, tmp_d,
         cub_tmp;
@@ -167,6 +169,8 @@ struct obb_tree {
 namespace obbv {
 
 inline void note_launch(obb_ctx* ctx, int n = 1) { ctx->launches += n; }
+// pinned staging for step counters, clear of the error word check_device_error reads
+inline int64_t* host_stats(obb_ctx* ctx) { return reinterpret_cast<int64_t*>(ctx->h_small) + 8; }
 // Number of kernels one library call enqueues, found once per shape by
 // capturing the call into a CUDA graph on a side stream (nothing runs).
 int captured_launches(obb_ctx* ctx, int64_t key0, int key1, const std::function<cudaError_t(cudaStream_t)>& fn);
@@ -218,6 +222,15 @@ obb_status rebuild_members(obb_ctx* ctx, obb_layer* L);
 obb_status layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, int32_t topk);
 obb_status layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox* out, uint64_t* counts, int64_t cap,
                                  int64_t* n);
+// pieces of the Lloyd step that the step between levels (sweep.cu) reuses
+enum { kStProposals = 0, kStAccepted, kStGain, kStEvals, kStRefits, kStPoints, kStCount };
+obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dsteps);
+obb_status layer_finish_stats(obb_ctx* ctx, obb_layer* L, int ran, obb_step_stats* st);
+uint8_t* layer_dirty(obb_layer* L);      // [K] membership changed since the last covariance refit
+int32_t* layer_level(obb_layer* L);      // [K] rotation-descent level
+obb_status layer_members(obb_ctx* ctx, obb_layer* L);   // member lists valid on return
+void layer_members_changed(obb_layer* L);
+void launch_sum_points(obb_ctx* ctx, const uint64_t* d_pts, const int32_t* d_n, int64_t* d_stats);
 
 // surrogate.cu: features of boxes [0, *d_K) and predicted outer volumes (FP16 weights)
 obb_status surrogate_predict(obb_ctx* ctx, const obb_mlp* mlp, const obb_lattice* lat, const obb_qbox* d_boxes,
@@ -226,6 +239,10 @@ obb_status surrogate_predict(obb_ctx* ctx, const obb_mlp* mlp, const obb_lattice
 // directional.cu: Eq. 9-10 estimator
 obb_status directional_outer_volume(obb_ctx* ctx, const obb_mesh* mesh, const obb_box* d_boxes, int64_t K, int32_t m,
                                     double* d_out);
+
+// sweep.cu: steps between levels (Sec. 4.2.2)
+obb_status unit_step(obb_ctx* ctx, obb_layer* up, obb_layer* low, const obb_step_opts* opts, obb_step_stats* st);
+obb_status tree_sweep(obb_ctx* ctx, obb_tree* tree, const obb_sweep_opts* opts, obb_sweep_stats* out);
 
 // tree.cu
 obb_status build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts* opts, obb_tree* tree);

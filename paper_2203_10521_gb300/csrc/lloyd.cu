@@ -29,7 +29,6 @@
 namespace obbv {
 namespace {
 
-enum { kStProposals = 0, kStAccepted, kStGain, kStEvals, kStRefits, kStPoints, kStCount };
 enum { kCtrCand = 0, kCtrEval, kCtrCount };
 
 struct Cand {
@@ -996,7 +995,7 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
     const int refit_mode = opts ? opts->refit : 1;
     const int dsteps = (opts && opts->descent_steps > 0) ? opts->descent_steps : 2;
     OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
-    int64_t* h = reinterpret_cast<int64_t*>(ctx->h_small);
+    int64_t* h = host_stats(ctx);
     int ran = 0;
     for (int r = 0; r < rounds; ++r) {
         if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
@@ -1047,6 +1046,21 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
         if (moved > 0) M->members_valid = false;
         if (moved == 0) break;
     }
+    OBB_TRY(layer_box_update(ctx, L, refit_mode, dsteps));
+    return layer_finish_stats(ctx, L, ran, st);
+}
+
+// Box update of a layer after its partition rounds (Sec. 4.2.1 step 2):
+// refit_mode bit 0 the covariance refit of the clusters whose membership
+// changed, bit 1 `dsteps` rotation-descent steps.  Adds to the layer's
+// device counters.
+obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dsteps)
+{
+    cudaStream_t s = ctx->stream;
+    LayerMem* M = mem_of(L);
+    const obb_lattice* lat = L->lat;
+    const obb_mesh* mesh = lat->mesh;
+    const int K = L->K;
     if (refit_mode & 1) {
         // covariance refit of the clusters whose membership changed (the others
         // would rebuild the frame they already tried and keep their box)
@@ -1107,6 +1121,16 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
         }
         OBB_CK(ctx, cudaGetLastError());
     }
+    return OBB_OK;
+}
+
+// Copies the layer's device counters and total outer volume into *st (if
+// non-null) after a step that ran `ran` partition rounds; synchronises.
+obb_status layer_finish_stats(obb_ctx* ctx, obb_layer* L, int ran, obb_step_stats* st)
+{
+    cudaStream_t s = ctx->stream;
+    const int K = L->K;
+    int64_t* h = host_stats(ctx);
     if (st) {
         OBB_CK(ctx, ctx->tmp_d.reserve(sizeof(int64_t), s));
         k_total<<<1, 1024, 0, s>>>(L->d_obv, K, ctx->tmp_d.as<int64_t>());
@@ -1124,6 +1148,23 @@ obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb
         st->total_obv = (uint64_t)h[kStCount];
     }
     return OBB_OK;
+}
+
+
+uint8_t* layer_dirty(obb_layer* L) { return mem_of(L)->dirty; }
+int32_t* layer_level(obb_layer* L) { return mem_of(L)->level; }
+
+obb_status layer_members(obb_ctx* ctx, obb_layer* L)
+{
+    return mem_of(L)->members_valid ? OBB_OK : rebuild_members(ctx, L);
+}
+
+void layer_members_changed(obb_layer* L) { mem_of(L)->members_valid = false; }
+
+void launch_sum_points(obb_ctx* ctx, const uint64_t* d_pts, const int32_t* d_n, int64_t* d_stats)
+{
+    k_sum_points<<<32, 256, 0, ctx->stream>>>(d_pts, d_n, d_stats);
+    note_launch(ctx);
 }
 
 obb_status layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, int32_t topk)

@@ -27,6 +27,22 @@
 #ifndef OBB_GRAB
 #define OBB_GRAB 1
 #endif
+// OBB_WARP_SEARCH: find a grabbed tile's box by a 32-way warp search (else binary)
+#ifndef OBB_WARP_SEARCH
+#define OBB_WARP_SEARCH 1
+#endif
+// OBB_COUNT_MINB: resident blocks of the counting kernel per SM the register budget aims at
+#ifndef OBB_COUNT_MINB
+#define OBB_COUNT_MINB 4
+#endif
+// OBB_FAST_DDA: a row loop without per-slab dispatch for boxes whose three slabs all step by DDA
+#ifndef OBB_FAST_DDA
+#define OBB_FAST_DDA 1
+#endif
+// OBB_TILE_SKIP: skip tiles that miss the box's shadow on the (j, k) plane
+#ifndef OBB_TILE_SKIP
+#define OBB_TILE_SKIP 1
+#endif
 namespace obbv {
 // tuning parameters: unroll factor of the counting kernel's row loop, tiles per work grab
 constexpr int kCountUnroll = OBB_COUNT_UNROLL;
@@ -108,7 +124,6 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
     const obb_qbox q = boxes[k];
     BoxPrep p;
     p.lat = lat_of_box ? lat_of_box[k] : 0;
-    p.pad1 = 0;
     bool bad_lat = p.lat < 0 || p.lat >= n_lats;
     if (bad_lat) {
         atomicOr(err, kErrArg);
@@ -123,7 +138,6 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
         p.Hq[a] = q.b[2 * a + 1] >> kS;
         empty |= p.Lq[a] > p.Hq[a];
         const int32_t d = p.n[3 * a];
-        p.sg[a] = d > 0 ? 1 : (d < 0 ? -1 : 0);
         p.dd[a] = d >= 0 ? d : -d;
         p.rcp[a] = d != 0 ? 1.0f / (float)p.dd[a] : 0.0f;
         p.qstep[a] = 0;
@@ -133,11 +147,15 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
         const int kind = d == 0 ? 0 : (p.dd[a] >= 32 ? 1 : 2);
         p.mode |= kind << (2 * a);
     }
-    p.rows = 0;
     p.i0 = 0;
-    p.i1 = -1;
+    p.span = -1;
     p.j0 = p.k0 = 0;
     p.nj = p.nk = p.ntj = 0;
+    for (int a = 0; a < 3; ++a) {
+        p.sat_nu[a][0] = p.sat_nu[a][1] = 0.0f;
+        p.sat_lo[a] = -1.0f;
+        p.sat_hi[a] = 1.0f;
+    }
     if (!empty) {
         double M[9];
         for (int i = 0; i < 9; ++i) M[i] = (double)p.n[i];
@@ -181,14 +199,39 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
             }
             if (!empty) {
                 p.i0 = (int32_t)floor(mn[0]) - 2;
-                p.i1 = (int32_t)ceil(mx[0]) + 2;
+                p.span = (int32_t)ceil(mx[0]) + 2 - p.i0;
                 p.j0 = (int32_t)floor(mn[1]) - 2;
                 int32_t j1 = (int32_t)ceil(mx[1]) + 2;
                 p.k0 = (int32_t)floor(mn[2]) - 2;
                 int32_t k1 = (int32_t)ceil(mx[2]) + 2;
                 p.nj = j1 - p.j0 + 1;
                 p.nk = k1 - p.k0 + 1;
-                p.rows = (uint64_t)p.nj * (uint64_t)p.nk;
+                // shadow on the (j, k) plane: edge a of the parallelepiped runs
+                // along column a of M^-1; its normal nu_a in (j, k) is
+                // orthogonal to that edge's shadow, and the shadow's extent
+                // along nu_a is the sum over the other two constraints b of
+                // nu_a . (column b) times [L_b, H_b]
+                for (int a = 0; a < 3; ++a) {
+                    double nj_ = -inv[3 * 2 + a] * id, nk_ = inv[3 * 1 + a] * id;
+                    const double len = sqrt(nj_ * nj_ + nk_ * nk_);
+                    double emax = 0.0;
+                    for (int r = 0; r < 3; ++r) emax = fmax(emax, fabs(inv[3 * r + a] * id));
+                    if (!(len > 1e-6 * emax)) continue;   // edge parallel to x: no axis
+                    nj_ /= len;
+                    nk_ /= len;
+                    double lo = 0.0, hi = 0.0;
+                    for (int b = 0; b < 3; ++b) {
+                        if (b == a) continue;
+                        const double w = nj_ * inv[3 * 1 + b] * id + nk_ * inv[3 * 2 + b] * id;
+                        const double x0 = w * (double)p.Lq[b], x1 = w * (double)p.Hq[b];
+                        lo += fmin(x0, x1);
+                        hi += fmax(x0, x1);
+                    }
+                    p.sat_nu[a][0] = (float)nj_;
+                    p.sat_nu[a][1] = (float)nk_;
+                    p.sat_lo[a] = (float)(lo - 2.0);
+                    p.sat_hi[a] = (float)(hi + 2.0);
+                }
             }
         }
     }
@@ -196,7 +239,7 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
     // (ties to the wider wj, whose rows sit next to each other in memory)
     int best = 5;
     int64_t best_slots = INT64_MAX;
-    if (p.rows) {
+    if (p.nj > 0) {
         for (int l = 5; l >= 0; --l) {
             const int64_t wj = 1 << l, wk = 32 >> l;
             const int64_t slots = ((p.nj + wj - 1) / wj) * wj * ((p.nk + wk * kTileK - 1) / (wk * kTileK)) * wk * kTileK;
@@ -208,18 +251,17 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
     }
     p.lwj = best;
     const int32_t wj = 1 << best, wk = 32 >> best;
-    p.ntj = p.rows ? (p.nj + wj - 1) / wj : 0;
-    p.pad0 = 0;
+    p.ntj = p.nj > 0 ? (p.nj + wj - 1) / wj : 0;
     for (int a = 0; a < 3; ++a)
         if ((p.mode >> (2 * a)) & 3) {
             // between a lane's rows k advances by wk: X_lo and X_hi move by -sign(d) * n_a2 * wk
-            const int64_t delta = -(int64_t)p.sg[a] * (int64_t)p.n[3 * a + 2] * wk;
+            const int64_t delta = -(int64_t)(p.n[3 * a] > 0 ? 1 : -1) * (int64_t)p.n[3 * a + 2] * wk;
             const int64_t qs = floordiv64(delta, p.dd[a]);
             p.qstep[a] = (int32_t)qs;   // |qs| <= 32 * 2^24 / 32 for |n_a0| >= 32
             p.rstep[a] = (int32_t)(delta - qs * p.dd[a]);
         }
     prep[k] = p;
-    tiles[k] = p.rows ? (int64_t)p.ntj * ((p.nk + wk * kTileK - 1) / (wk * kTileK)) : 0;
+    tiles[k] = p.nj > 0 ? (int64_t)p.ntj * ((p.nk + wk * kTileK - 1) / (wk * kTileK)) : 0;
 }
 
 // ------------------------------------------------------------------- scan
@@ -370,7 +412,12 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
     return cnt + __popcll(w0 & m0) + __popcll(w1 & m1);
 }
 
-__global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
+#if OBB_COUNT_MINB > 0
+#define OBB_COUNT_BOUNDS __launch_bounds__(256, OBB_COUNT_MINB)
+#else
+#define OBB_COUNT_BOUNDS __launch_bounds__(256)
+#endif
+__global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                                                const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ d_K,
                                                const LatRef* __restrict__ lats,
@@ -394,12 +441,24 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
             c = (int64_t)__shfl_sync(0xffffffffu, g, 0);
             if (c >= total) break;
             c_end = min(c + (int64_t)kGrab, total);
+#if OBB_WARP_SEARCH
+            // the last box b with off[b] <= c: a 32-way search, one probe per lane
+            int32_t lo = 0, hi = K;   // off[lo] <= c < off[hi]
+            while (hi - lo > 1) {
+                const int32_t st = (hi - lo + 31) >> 5;
+                const int32_t idx = lo + lane * st;
+                const unsigned m = __ballot_sync(0xffffffffu, idx < hi && off[idx] <= c);
+                lo += (31 - __clz(m)) * st;
+                hi = min(hi, lo + st);
+            }
+#else
             int32_t lo = 0, hi = K - 1;
             while (lo < hi) {
                 int32_t mid = (lo + hi + 1) >> 1;
                 if (off[mid] <= c) lo = mid;
                 else hi = mid - 1;
             }
+#endif
             b = lo;
             box_end = off[b + 1];
             const int32_t u = (int32_t)(c - off[b]);
@@ -413,6 +472,29 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
             tj = tk = 0;
         }
         const BoxPrep& p = prep[b];
+#if OBB_TILE_SKIP
+        {
+            // skip a tile whose rectangle misses the box's shadow on (j, k)
+            const int32_t lw = p.lwj, hk = (32 >> lw) * kTileK;
+            const float hj = 0.5f * (float)((1 << lw) - 1), hkf = 0.5f * (float)(hk - 1);
+            const float jc = (float)(p.j0 + (tj << lw)) + hj, kc = (float)(p.k0 + tk * hk) + hkf;
+            bool out = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float u = p.sat_nu[a][0], v = p.sat_nu[a][1];
+                const float cc = u * jc + v * kc, e = fabsf(u) * hj + fabsf(v) * hkf;
+                out |= cc + e < p.sat_lo[a] || cc - e > p.sat_hi[a];
+            }
+            if (out) {
+                if (++tj == p.ntj) {
+                    tj = 0;
+                    ++tk;
+                }
+                ++c;
+                continue;
+            }
+        }
+#endif
         const LatRef lr = lats[p.lat];
         const uint64_t* __restrict__ words = lr.words;
         const int32_t N = lr.N, W = lr.W;
@@ -424,7 +506,7 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
         const bool jvalid = jl < p.nj;
         const int32_t kb = p.k0 + tk * (wk * kTileK) + (lane >> lwj);   // this lane's first row
         const int32_t kend = p.k0 + p.nk;
-        const int32_t i0 = p.i0, span = p.i1 - p.i0;
+        const int32_t i0 = p.i0, span = p.span;
         // Kind-1 slabs carry exact quotient bounds relative to i0 in 32 bits,
         // saturated at +-2^30: a bound that far out moves less than 2^29 within a
         // tile, so it stays outside [0, span].  Kind 0 (n_a0 = 0) and kind 2
@@ -439,8 +521,8 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
                 rs[a] = p.rstep[a];
                 qs[a] = p.qstep[a];
                 const int64_t cc = (int64_t)p.n[3 * a + 1] * j + (int64_t)p.n[3 * a + 2] * kb;
-                const int64_t xlo = p.sg[a] > 0 ? p.Lq[a] - cc : cc - p.Hq[a];
-                const int64_t xhi = p.sg[a] > 0 ? p.Hq[a] - cc : cc - p.Lq[a];
+                const int64_t xlo = p.n[3 * a] > 0 ? p.Lq[a] - cc : cc - p.Hq[a];
+                const int64_t xhi = p.n[3 * a] > 0 ? p.Hq[a] - cc : cc - p.Lq[a];
                 int64_t wlo, whi;
                 floordiv_exact(xlo + dd[a] - 1, dd[a], p.rcp[a], wlo, ra[a]);   // ceil(xlo / dd)
                 floordiv_exact(xhi, dd[a], p.rcp[a], whi, rb[a]);               // floor(xhi / dd)
@@ -451,6 +533,49 @@ __global__ void __launch_bounds__(256) k_count(const BoxPrep* __restrict__ prep,
         }
         uint32_t empty = 0, inbox = 0;
         const bool jin = j >= 0 && j < N;
+#if OBB_FAST_DDA
+        if (mode == 0x15) {
+            // all three slabs step by 32-bit DDA (any rotated box): no per-row
+            // slab dispatch, and the row pointer advances by a fixed stride
+            const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
+            const int64_t rstride = (int64_t)wk * N * W;
+            int32_t k = kb;
+#pragma unroll kCountUnroll
+            for (int r = 0; r < kTileK; ++r, k += wk, rowp += rstride) {
+                const int32_t lo = max(max(qa[0], qa[1]), max(qa[2], 0));
+                const int32_t hi = min(min(qb[0], qb[1]), min(qb[2], span));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    qa[a] += qs[a];
+                    ra[a] += rs[a];
+                    if (ra[a] >= dd[a]) {
+                        ra[a] -= dd[a];
+                        qa[a] += 1;
+                    }
+                    qb[a] += qs[a];
+                    rb[a] += rs[a];
+                    if (rb[a] >= dd[a]) {
+                        rb[a] -= dd[a];
+                        qb[a] += 1;
+                    }
+                }
+                if (jvalid && k < kend && lo <= hi) {
+                    const uint32_t len = (uint32_t)(hi - lo + 1);
+                    uint32_t occ = 0;
+                    if (jin && (uint32_t)k < (uint32_t)N) {
+                        const int32_t a = max(i0 + lo, 0), e = min(i0 + hi, N - 1);
+                        if (a <= e) {
+                            occ = popc_range(rowp, a, e);
+                            my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                        }
+                    }
+                    empty += len - occ;
+                    inbox += len;
+                    my_rows += 1;
+                }
+            }
+        } else
+#endif
 #pragma unroll kCountUnroll
         for (int r = 0; r < kTileK; ++r) {
             const int32_t k = kb + r * wk;

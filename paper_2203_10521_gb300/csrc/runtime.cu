@@ -500,6 +500,22 @@ obb_status obb_lloyd_step(obb_ctx* ctx, obb_layer* layer, const obb_step_opts* o
     return lloyd_step(ctx, layer, opts, stats);
 }
 
+obb_status obb_layer_parents(obb_ctx* ctx, const obb_layer* L, int32_t* parent)
+{
+    if (!ctx || !L || !parent) return fail(ctx, OBB_ERR_ARG, "null argument");
+    OBB_CK(ctx, cudaMemcpyAsync(parent, L->d_parent, sizeof(int32_t) * L->K, cudaMemcpyDeviceToHost, ctx->stream));
+    return check_device_error(ctx);
+}
+
+obb_status obb_unit_step(obb_ctx* ctx, obb_layer* upper, obb_layer* lower, const obb_step_opts* opts,
+                         obb_step_stats* stats)
+{
+    if (!ctx || !upper || !lower) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (upper->ctx != ctx || lower->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
+    if (upper == lower) return fail(ctx, OBB_ERR_ARG, "upper and lower are the same layer");
+    return unit_step(ctx, upper, lower, opts, stats);
+}
+
 obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* L, int32_t* assign, double* frames, obb_qbox* qboxes,
                           obb_box* boxes, uint64_t* obv, int32_t on_device)
 {
@@ -576,7 +592,21 @@ obb_status obb_tree_read(obb_ctx* ctx, const obb_tree* tree, int32_t level, int3
     return obb_layer_read(ctx, tree->layers[level], assign, frames, qboxes, boxes, obv, 0);
 }
 
+obb_status obb_tree_parents(obb_ctx* ctx, const obb_tree* tree, int32_t level, int32_t* parent)
+{
+    if (!ctx || !tree || !parent) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (level < 0 || level >= (int32_t)tree->layers.size()) return fail(ctx, OBB_ERR_ARG, "level out of range");
+    return obb_layer_parents(ctx, tree->layers[level], parent);
+}
+
 int32_t obb_tree_depth(const obb_tree* tree) { return tree ? (int32_t)tree->layers.size() - 1 : -1; }
+
+obb_status obb_tree_sweep(obb_ctx* ctx, obb_tree* tree, const obb_sweep_opts* opts, obb_sweep_stats* stats)
+{
+    if (!ctx || !tree) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (tree->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "tree belongs to another context");
+    return tree_sweep(ctx, tree, opts, stats);
+}
 
 obb_status obb_tree_score(obb_ctx* ctx, const obb_tree* tree, double* points, double* volume)
 {

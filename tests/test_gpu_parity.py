@@ -237,6 +237,8 @@ def test_lloyd_moves_bit_exact(ctx, torus_setup, K, rounds):
     assert np.array_equal(g["obv"], L.obv)
     assert st["moves"] == sum(s["accepted"] for s in so)
     assert st["gain"] == sum(s["gain"] for s in so)
+    assert st["proposals"] == sum(s["proposals"] for s in so)
+    assert st["box_evals"] == sum(s["evals"] for s in so)
     assert st["total_obv"] == int(L.obv.sum())
     layer.free()
 
