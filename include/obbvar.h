@@ -289,6 +289,58 @@ obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* layer, int32_t* assign,
                           obb_qbox* qboxes, obb_box* boxes, uint64_t* obv, int32_t on_device);
 int32_t obb_layer_clusters(const obb_layer* layer);
 
+typedef struct {
+    int32_t waves;       /* flooding waves run */
+    int32_t reserved;
+    int64_t box_evals;   /* grown boxes counted exactly */
+} obb_flood_stats;
+
+/* Patch division by flooding (Sec. 4.2.1 step 1, Eq. 12-13): the layer's
+ * triangles are re-partitioned among its boxes, whose frames and centres stay
+ * fixed; a triangle may only join a box of its group (the parent of its
+ * current cluster).  Priority of a triangle: distance from its centroid (FP64
+ * mean of its three vertices) to the nearest centre of its group's boxes,
+ * rounded to float, ties by triangle index.  Each box first takes the nearest
+ * untaken triangle of its group (boxes in index order); then a triangle
+ * becomes available once an edge neighbour of its group is assigned, and a
+ * taken triangle joins, among the boxes holding such a neighbour, the one
+ * whose exact outer volume grows least (ties -> smaller box); a group with no
+ * available triangle takes its unassigned triangle of smallest priority with
+ * all its boxes as candidates.  mode 0 (exact) takes the available triangle
+ * of smallest priority in every group per wave -- the paper's sequential
+ * priority-queue order -- and mode 1 (wavefront) every available triangle at
+ * once, each judged against its boxes as the wave found them.  centres: [K][3]
+ * world coordinates (FP64, host or device), or NULL for the current boxes'
+ * centres.  The layer's assignment, slabs (tight) and outer volumes are
+ * replaced; its frames are kept and every cluster is marked for the next
+ * refit.  A group may hold at most 8 boxes (OBB_ERR_STATE beyond).  stats may
+ * be NULL.  Synchronises. */
+obb_status obb_flood_partition(obb_ctx* ctx, obb_layer* layer, const double* centres, int32_t mode,
+                               obb_flood_stats* stats);
+
+typedef struct {
+    int32_t kept;            /* 1 if the adjustment lowered the layer's total and was kept */
+    int32_t k;               /* the re-seated box (-1: no box has a sibling) */
+    int32_t m;               /* the sibling that took k's triangles */
+    int32_t j;               /* the sibling that was split to seat k again */
+    uint64_t total_before;   /* the layer's total outer volume before and after */
+    uint64_t total_after;
+} obb_adjust_stats;
+
+/* Adjustment of the layer's boxes out of a local minimum (Sec. 4.2.1 step 3:
+ * the least important box is adjusted; kept only if the error drops).  The
+ * least important box k is the one with fewest triangles (ties -> smaller
+ * index) among boxes with a sibling.  Its triangles go to the sibling m that
+ * shares most triangle edges with it (ties -> smaller index), whose slab is
+ * recomputed; then the sibling j with the largest outer volume (ties ->
+ * smaller index) is split at the median of its triangles along its major axis
+ * (key n_0 . (U_p + U_q + U_r), ties by triangle index): the first ceil(n/2)
+ * stay in j, the rest become box k with j's frame.  `iters` obb_lloyd_step
+ * iterations with `opts` follow; the layer is restored unless its total outer
+ * volume is then strictly smaller.  stats may be NULL.  Synchronises. */
+obb_status obb_layer_adjust(obb_ctx* ctx, obb_layer* layer, const obb_step_opts* opts, int32_t iters,
+                            obb_adjust_stats* stats);
+
 /* The layer's parent map, int32 [K] (host array), as given to obb_layer_init
  * and as changed by obb_unit_step on the layer above.  Synchronises. */
 obb_status obb_layer_parents(obb_ctx* ctx, const obb_layer* layer, int32_t* parent);

@@ -79,6 +79,8 @@ def _declare(L):
     L.orc_lloyd_moves.restype = C.c_int
     L.orc_unit_moves.argtypes = [vp, vp, vp, i64, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, i32, i32, vp]
     L.orc_unit_moves.restype = C.c_int
+    L.orc_flood_partition.argtypes = [vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp, i32, vp, vp, vp]
+    L.orc_flood_partition.restype = C.c_int
     L.orc_moments.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     L.orc_covariance_from_moments.argtypes = [vp, vp]
     L.orc_covariance_from_moments.restype = C.c_int
@@ -523,6 +525,103 @@ def tree_sweeps(P: Problem, layers, sweeps: int = 1, iters: int = 2, rounds: int
             level(lev)
         hist.append(tree_eq7(layers))
     return hist
+
+
+def box_centres(P: Problem, L: Layer):
+    """World-space centres (FP64) of a layer's quantised boxes: the midpoint of
+    each slab, mapped back through the frame."""
+    s = 4294967296.0 / float(np.max(P.h))
+    base = L.frames.reshape(-1, 3, 3) @ (P.lo + 0.5 * P.h)
+    mid = 0.5 * (L.bnd[:, 0::2].astype(np.float64) + L.bnd[:, 1::2].astype(np.float64)) / s + base
+    return np.einsum("kab,ka->kb", L.frames.reshape(-1, 3, 3), mid)
+
+
+def flood_partition(P: Problem, group, box_group, n, centre):
+    """Patch division by flooding (Sec. 4.2.1 step 1), sequential in the
+    paper's priority order; see orc_flood_partition.  Returns (assign, bnd,
+    obv) with exact tight slabs and outer volumes."""
+    T = P.F.shape[0]
+    group = _c(group, np.int32)
+    box_group = _c(box_group, np.int32)
+    n = _c(n, np.int32).reshape(-1, 9)
+    centre = _c(centre, np.float64).reshape(-1, 3)
+    K = box_group.shape[0]
+    while True:
+        assign = np.zeros(T, np.int32)
+        bnd = np.zeros((K, 6), np.int64)
+        obv = np.zeros(K, np.uint64)
+        rc = lib().orc_flood_partition(_p(P.V), _p(P.U), _p(P.F), _p(P.adj), T, _p(group), K, _p(box_group),
+                                       _p(n), _p(centre), _p(P.occ.occ), _p(P.occ.known), P.N, _p(assign),
+                                       _p(bnd), _p(obv))
+        if rc == -3:
+            P.occ.fill_all()
+            continue
+        if rc < 0:
+            raise ValueError("a box has no triangle of its group to seed from")
+        return assign, bnd, obv
+
+
+def adjust_step(P: Problem, L: Layer, iters: int = 2, rounds: int = 16, do_refit=1):
+    """Box adjustment for local minima (Sec. 4.2.1 step 3), in place.  The
+    least important box k (fewest triangles, ties -> smaller index; only boxes
+    with a sibling) gives its triangles to the sibling sharing most triangle
+    edges with it (ties -> smaller index; none -> the smallest sibling index),
+    whose box is recomputed.  Then the sibling j with the largest outer volume
+    (ties -> smaller index) is split at the median of its triangles along its
+    major axis (key n_0 . (U_p + U_q + U_r), ties by triangle index): the
+    first ceil(n / 2) stay in j, the rest form box k, which takes j's frame.
+    `iters` Lloyd iterations follow.  The adjustment is kept only if the
+    layer's total outer volume is then smaller; otherwise the layer is
+    restored.  Returns (kept, k, j)."""
+    saved = L.copy()
+    total0 = int(L.obv.astype(np.int64).sum())
+    K = L.K
+    size = np.bincount(L.assign, minlength=K)
+    nsib = np.bincount(L.parent, minlength=K)[L.parent]
+    elig = np.nonzero(nsib >= 2)[0]
+    if elig.size == 0:
+        return False, -1, -1
+    k = int(elig[np.lexsort((elig, size[elig]))[0]])
+    g = L.parent[k]
+    sibs = [c for c in range(K) if L.parent[c] == g and c != k]
+    edges = np.zeros(K, np.int64)
+    for t in np.nonzero(L.assign == k)[0]:
+        for u in P.adj[t]:
+            c = L.assign[u]
+            if c != k and L.parent[c] == g:
+                edges[c] += 1
+    m = max(sibs, key=lambda c: (edges[c], -c))
+    L.assign[L.assign == k] = m
+
+    def rebox(cs):
+        cs = list(cs)
+        b = tight_bounds(P.U, P.F, L.assign, K, L.n)
+        for c in cs:
+            L.bnd[c] = b[c]
+        L.obv[cs] = outer_volume(P.occ, L.n[cs], L.bnd[cs])[0]
+
+    rebox([m])
+    j = max(sibs, key=lambda c: (int(L.obv[c]), -c))
+    tj = np.nonzero(L.assign == j)[0]
+    if tj.size < 2:
+        L.assign[:], L.frames[:], L.n[:], L.bnd[:], L.obv[:], L.level[:] = (
+            saved.assign, saved.frames, saved.n, saved.bnd, saved.obv, saved.level)
+        return False, k, j
+    S = P.U[P.F[tj]].astype(np.int64).sum(1)
+    key = S @ L.n[j, 0:3].astype(np.int64)
+    order = tj[np.lexsort((tj, key))]
+    L.assign[order[(tj.size + 1) // 2:]] = k
+    L.frames[k] = L.frames[j]
+    L.n[k] = L.n[j]
+    rebox([j, k])
+    L.level[[k, m, j]] = 0
+    for _ in range(iters):
+        lloyd_step(P, L, rounds, do_refit)
+    if int(L.obv.astype(np.int64).sum()) < total0:
+        return True, k, j
+    L.assign[:], L.frames[:], L.n[:], L.bnd[:], L.obv[:], L.level[:] = (
+        saved.assign, saved.frames, saved.n, saved.bnd, saved.obv, saved.level)
+    return False, k, j
 
 
 def median_split(P: Problem, L: Layer):

@@ -754,6 +754,180 @@ int orc_unit_moves(const int32_t* U, const int32_t* F, const int32_t* adj, int64
 }
 
 /* ------------------------------------------------------------------------- */
+/* Flooding partition (Sec. 4.2.1 step 1), sequential, in the paper's order  */
+/* ------------------------------------------------------------------------- */
+
+/* Priority of a triangle: distance from its centroid (world FP64, the mean of
+ * its three float vertices) to the nearest centre of the boxes it may join,
+ * rounded to float; packed with the triangle index as (bits << 32 | t), so
+ * equal distances pop in triangle order. */
+static uint64_t tri_box_key(const float* V, const int32_t* F, int64_t t, const double* c)
+{
+    double d2 = 0.0;
+    for (int b = 0; b < 3; ++b) {
+        double m = (double)V[3 * (int64_t)F[3 * t] + b] + (double)V[3 * (int64_t)F[3 * t + 1] + b];
+        m = m + (double)V[3 * (int64_t)F[3 * t + 2] + b];
+        m = m / 3.0;
+        const double d = m - c[b];
+        d2 = d2 + d * d;
+    }
+    const float f = (float)sqrt(d2);
+    uint32_t bits;
+    memcpy(&bits, &f, 4);
+    return ((uint64_t)bits << 32) | (uint64_t)(uint32_t)t;
+}
+
+static void heap_push(uint64_t* h, int64_t* n, uint64_t v)
+{
+    int64_t i = (*n)++;
+    h[i] = v;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h[p] <= h[i]) break;
+        uint64_t tmp = h[p]; h[p] = h[i]; h[i] = tmp;
+        i = p;
+    }
+}
+
+static uint64_t heap_pop(uint64_t* h, int64_t* n)
+{
+    uint64_t top = h[0];
+    h[0] = h[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *n && h[l] < h[m]) m = l;
+        if (r < *n && h[r] < h[m]) m = r;
+        if (m == i) break;
+        uint64_t tmp = h[m]; h[m] = h[i]; h[i] = tmp;
+        i = m;
+    }
+    return top;
+}
+
+/*
+ * Patch division by flooding.  group[t] is the set triangle t must stay in
+ * (its cluster one level up); box k (frame n_k, centre centre_k in world
+ * coordinates) takes triangles of group box_group[k] only.  Centres and
+ * frames stay fixed.  Every box first takes as seed the triangle of its group
+ * nearest its centre (boxes in index order; a triangle already taken is
+ * skipped).  Then the triangle with the smallest priority (distance to the
+ * nearest centre of its group's boxes) among those edge-adjacent to an
+ * assigned triangle of the same group is taken; it joins, among the boxes
+ * holding such a neighbour, the one whose exact outer volume grows least
+ * (Eq. 12-13: dOBV = OBV(box with t) - OBV(box); ties -> smaller box), and
+ * its unassigned neighbours of the same group become available.  When none is
+ * available but triangles remain (a group in several pieces), the remaining
+ * triangle of smallest priority is taken with every box of its group as a
+ * candidate (an empty box has OBV 0 and grows to the triangle's own slab).
+ * Out: assign [nt], bnd [K][6] (tight slabs; empty boxes lo > hi), obv [K].
+ * Returns 0, -1 (a box without any triangle of its group), -3 (an occupancy
+ * column the count needs is missing).
+ */
+int orc_flood_partition(const float* V, const int32_t* U, const int32_t* F, const int32_t* adj, int64_t nt,
+                        const int32_t* group, int32_t K, const int32_t* box_group, const int32_t* n,
+                        const double* centre, const uint8_t* occ, const uint8_t* colmask, int32_t N,
+                        int32_t* assign, int64_t* bnd, uint64_t* obv)
+{
+    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(nt > 0 ? nt : 1));
+    uint64_t* heap = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(nt > 0 ? nt : 1));
+    uint8_t* queued = (uint8_t*)calloc((size_t)(nt > 0 ? nt : 1), 1);
+    uint8_t* cand = (uint8_t*)calloc((size_t)(K > 0 ? K : 1), 1);
+    int64_t hn = 0, left = nt;
+    int err = 0;
+    for (int64_t t = 0; t < nt; ++t) {
+        assign[t] = -1;
+        key[t] = UINT64_MAX;
+        for (int32_t k = 0; k < K; ++k) {
+            if (box_group[k] != group[t]) continue;
+            const uint64_t kk = tri_box_key(V, F, t, centre + 3 * k);
+            if (kk < key[t]) key[t] = kk;
+        }
+    }
+    for (int32_t k = 0; k < K; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            bnd[6 * k + 2 * a] = INT64_MAX;
+            bnd[6 * k + 2 * a + 1] = INT64_MIN;
+        }
+        obv[k] = 0;
+    }
+    /* seeds */
+    for (int32_t k = 0; k < K && !err; ++k) {
+        int64_t best = -1;
+        uint64_t bk = UINT64_MAX;
+        for (int64_t t = 0; t < nt; ++t) {
+            if (group[t] != box_group[k] || assign[t] >= 0) continue;
+            const uint64_t kk = tri_box_key(V, F, t, centre + 3 * k);
+            if (kk < bk) { bk = kk; best = t; }
+        }
+        if (best < 0) { err = -1; break; }
+        int64_t g[6];
+        bounds_with(U, F, best, n + 9 * k, bnd + 6 * k, g);
+        memcpy(bnd + 6 * k, g, sizeof(g));
+        if (count_one(occ, colmask, N, n + 9 * k, g, obv + k)) { err = -3; break; }
+        assign[best] = k;
+        queued[best] = 1;
+        --left;
+    }
+    for (int32_t k = 0; k < K && !err; ++k)   /* neighbours of the seeds */
+        for (int64_t t = 0; t < nt; ++t) {
+            if (assign[t] != k) continue;
+            for (int e = 0; e < 3; ++e) {
+                const int32_t u = adj[3 * t + e];
+                if (queued[u] || group[u] != group[t]) continue;
+                queued[u] = 1;
+                heap_push(heap, &hn, key[u]);
+            }
+        }
+    while (left > 0 && !err) {
+        int64_t t = -1;
+        if (hn > 0) {
+            t = (int64_t)(uint32_t)(heap_pop(heap, &hn) & 0xffffffffu);
+        } else {
+            uint64_t bk = UINT64_MAX;
+            for (int64_t u = 0; u < nt; ++u)
+                if (assign[u] < 0 && key[u] < bk) { bk = key[u]; t = u; }
+            queued[t] = 1;
+        }
+        memset(cand, 0, (size_t)K);
+        int nc = 0;
+        for (int e = 0; e < 3; ++e) {
+            const int32_t u = adj[3 * t + e];
+            if (assign[u] >= 0 && group[u] == group[t] && !cand[assign[u]]) { cand[assign[u]] = 1; ++nc; }
+        }
+        if (nc == 0)
+            for (int32_t k = 0; k < K; ++k)
+                if (box_group[k] == group[t]) { cand[k] = 1; ++nc; }
+        int32_t bestk = -1;
+        int64_t bestc = 0;
+        int64_t bestb[6];
+        uint64_t besto = 0;
+        for (int32_t k = 0; k < K && !err; ++k) {
+            if (!cand[k]) continue;
+            int64_t g[6];
+            bounds_with(U, F, t, n + 9 * k, bnd + 6 * k, g);
+            uint64_t o = obv[k];
+            if (!same6(g, bnd + 6 * k) && count_one(occ, colmask, N, n + 9 * k, g, &o)) { err = -3; break; }
+            const int64_t c = (int64_t)o - (int64_t)obv[k];
+            if (bestk < 0 || c < bestc) { bestk = k; bestc = c; memcpy(bestb, g, sizeof(g)); besto = o; }
+        }
+        if (err) break;
+        assign[t] = bestk;
+        memcpy(bnd + 6 * bestk, bestb, sizeof(bestb));
+        obv[bestk] = besto;
+        --left;
+        for (int e = 0; e < 3; ++e) {
+            const int32_t u = adj[3 * t + e];
+            if (queued[u] || group[u] != group[t]) continue;
+            queued[u] = 1;
+            heap_push(heap, &hn, key[u]);
+        }
+    }
+    free(key); free(heap); free(queued); free(cand);
+    return err;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Refit: area-weighted covariance and cyclic Jacobi (FP64)                  */
 /* ------------------------------------------------------------------------- */
 

@@ -61,6 +61,18 @@ class TreeOpts(C.Structure):
     _fields_ = [("depth", C.c_int32), ("iters", C.c_int32), ("rounds", C.c_int32), ("refit", C.c_int32)]
 
 
+class FloodStats(C.Structure):
+    _fields_ = [("waves", C.c_int32), ("reserved", C.c_int32), ("box_evals", C.c_int64)]
+
+
+class AdjustStats(C.Structure):
+    _fields_ = [("kept", C.c_int32), ("k", C.c_int32), ("m", C.c_int32), ("j", C.c_int32),
+                ("total_before", C.c_uint64), ("total_after", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SweepOpts(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("iters", C.c_int32), ("rounds", C.c_int32), ("refit", C.c_int32)]
 
@@ -113,6 +125,8 @@ def load(build_if_missing: bool = True):
         "obb_tree_parents": [vp, vp, i32, vp],
         "obb_tree_sweep": [vp, vp, C.POINTER(SweepOpts), C.POINTER(SweepStats)],
         "obb_layer_parents": [vp, vp, vp],
+        "obb_flood_partition": [vp, vp, vp, i32, C.POINTER(FloodStats)],
+        "obb_layer_adjust": [vp, vp, C.POINTER(StepOpts), i32, C.POINTER(AdjustStats)],
         "obb_unit_step": [vp, vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
         "obb_mlp_create": [vp, C.c_uint64, C.POINTER(vp)],
         "obb_mlp_params": [vp, vp, vp, i32],
@@ -153,7 +167,8 @@ def exported_symbols():
             "obb_outer_volume_multi", "obb_directional_outer_volume", "obb_layer_init", "obb_lloyd_step",
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
             "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free", "obb_tree_parents",
-            "obb_tree_sweep", "obb_layer_parents", "obb_unit_step",
+            "obb_tree_sweep", "obb_layer_parents", "obb_unit_step", "obb_flood_partition",
+            "obb_layer_adjust",
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_mlp_forward", "obb_mlp_gradients", "obb_mlp_train_step",
             "obb_layer_set_surrogate", "obb_layer_last_candidates"]
@@ -365,6 +380,27 @@ class Context:
         st = StepStats()
         self.check(self.lib.obb_unit_step(self.h, upper.h, lower.h, C.byref(o), C.byref(st) if stats else None))
         return st.as_dict() if stats else None
+
+    def flood_partition(self, layer, centres=None, mode=0):
+        """Re-partition the layer's triangles by flooding (Sec. 4.2.1 step 1):
+        mode 0 the paper's priority order, 1 the wavefront approximation."""
+        st = FloodStats()
+        c = None
+        if centres is not None:
+            c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+            if len(c) != layer.K:
+                raise ValueError("one centre per box")
+        self.check(self.lib.obb_flood_partition(self.h, layer.h, c.ctypes.data_as(C.c_void_p) if c is not None else None,
+                                                int(mode), C.byref(st)))
+        return {"waves": st.waves, "box_evals": st.box_evals}
+
+    def layer_adjust(self, layer, iters=2, rounds=16, refit=True, descent_steps=0):
+        """Re-seat the least important box (Sec. 4.2.1 step 3); kept only if
+        the layer's total outer volume drops after `iters` Lloyd iterations."""
+        o = StepOpts(int(rounds), int(refit), int(descent_steps), 0)
+        st = AdjustStats()
+        self.check(self.lib.obb_layer_adjust(self.h, layer.h, C.byref(o), int(iters), C.byref(st)))
+        return st.as_dict()
 
     def layer_parents(self, layer):
         p = np.zeros(layer.K, np.int32)

@@ -21,7 +21,7 @@ constexpr int kMaxN = 2048;      // lattice points per axis
 constexpr int kSurrogateInputs = 524;   // 12 box parameters + 8^3 occupancy patch
 constexpr int64_t kBoxRange = int64_t(1) << 20;  // |index-space AABB| limit of a counted box
 #ifndef OBB_TILE_K
-#define OBB_TILE_K 16
+#define OBB_TILE_K 32
 #endif
 constexpr int kTileK = OBB_TILE_K;               // rows along z one lane steps through per tile
 
@@ -62,6 +62,7 @@ struct BoxPrep {
     int32_t rstep[3];        // remainder of that step, in [0, dd)
     int32_t qstep[3];        // quotient of the step between a lane's rows (|.| < 2^25 for DDA slabs)
     int32_t lat;             // index of the box's lattice in the launch's lattice table
+    int32_t tk;              // rows one lane visits per tile (tiles are wj x wk * tk rows)
     float rcp[3];            // 1 / dd (seed of the exact initial division)
     int64_t Lq[3], Hq[3];    // ceil(lo / 256), floor(hi / 256)
     // Separating axes of the box's shadow on the (j, k) plane: the normals of
@@ -228,6 +229,7 @@ obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dste
 obb_status layer_finish_stats(obb_ctx* ctx, obb_layer* L, int ran, obb_step_stats* st);
 uint8_t* layer_dirty(obb_layer* L);      // [K] membership changed since the last covariance refit
 int32_t* layer_level(obb_layer* L);      // [K] rotation-descent level
+const int32_t* layer_dev_K(obb_layer* L);   // device copy of K
 obb_status layer_members(obb_ctx* ctx, obb_layer* L);   // member lists valid on return
 void layer_members_changed(obb_layer* L);
 void launch_sum_points(obb_ctx* ctx, const uint64_t* d_pts, const int32_t* d_n, int64_t* d_stats);
@@ -243,6 +245,12 @@ obb_status directional_outer_volume(obb_ctx* ctx, const obb_mesh* mesh, const ob
 // sweep.cu: steps between levels (Sec. 4.2.2)
 obb_status unit_step(obb_ctx* ctx, obb_layer* up, obb_layer* low, const obb_step_opts* opts, obb_step_stats* st);
 obb_status tree_sweep(obb_ctx* ctx, obb_tree* tree, const obb_sweep_opts* opts, obb_sweep_stats* out);
+
+// flood.cu: patch division by flooding (Sec. 4.2.1 step 1)
+obb_status flood_partition(obb_ctx* ctx, obb_layer* L, const double* d_centres, int32_t mode, obb_flood_stats* out);
+
+// adjust.cu: box adjustment out of local minima (Sec. 4.2.1 step 3)
+obb_status layer_adjust(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, int32_t iters, obb_adjust_stats* out);
 
 // tree.cu
 obb_status build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts* opts, obb_tree* tree);

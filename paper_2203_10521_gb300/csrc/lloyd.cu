@@ -1152,6 +1152,7 @@ obb_status layer_finish_stats(obb_ctx* ctx, obb_layer* L, int ran, obb_step_stat
 
 
 uint8_t* layer_dirty(obb_layer* L) { return mem_of(L)->dirty; }
+const int32_t* layer_dev_K(obb_layer* L) { return mem_of(L)->dK; }
 int32_t* layer_level(obb_layer* L) { return mem_of(L)->level; }
 
 obb_status layer_members(obb_ctx* ctx, obb_layer* L)

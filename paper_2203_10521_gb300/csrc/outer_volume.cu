@@ -35,9 +35,21 @@
 #ifndef OBB_COUNT_MINB
 #define OBB_COUNT_MINB 4
 #endif
+// OBB_POPC_ILP: load a row's chunks up front / in groups of four
+#ifndef OBB_POPC_ILP
+#define OBB_POPC_ILP 1
+#endif
 // OBB_FAST_DDA: a row loop without per-slab dispatch for boxes whose three slabs all step by DDA
 #ifndef OBB_FAST_DDA
 #define OBB_FAST_DDA 1
+#endif
+// OBB_TILE_ADAPT: rows per lane chosen per box (kTileK for large boxes, less for small)
+#ifndef OBB_TILE_ADAPT
+#define OBB_TILE_ADAPT 0
+#endif
+// OBB_ROW_MARGIN: rows added on each side of a box's (j, k) bounding rectangle
+#ifndef OBB_ROW_MARGIN
+#define OBB_ROW_MARGIN 1
 #endif
 // OBB_TILE_SKIP: skip tiles that miss the box's shadow on the (j, k) plane
 #ifndef OBB_TILE_SKIP
@@ -46,6 +58,7 @@
 namespace obbv {
 // tuning parameters: unroll factor of the counting kernel's row loop, tiles per work grab
 constexpr int kCountUnroll = OBB_COUNT_UNROLL;
+constexpr int kRowMargin = OBB_ROW_MARGIN;
 constexpr int kGrab = OBB_GRAB;
 }  // namespace obbv
 
@@ -198,12 +211,14 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
                 }
             }
             if (!empty) {
+                // the corners carry FP64 rounding far below one row; a margin
+                // of kRowMargin rows keeps the AABB conservative
                 p.i0 = (int32_t)floor(mn[0]) - 2;
                 p.span = (int32_t)ceil(mx[0]) + 2 - p.i0;
-                p.j0 = (int32_t)floor(mn[1]) - 2;
-                int32_t j1 = (int32_t)ceil(mx[1]) + 2;
-                p.k0 = (int32_t)floor(mn[2]) - 2;
-                int32_t k1 = (int32_t)ceil(mx[2]) + 2;
+                p.j0 = (int32_t)floor(mn[1]) - kRowMargin;
+                int32_t j1 = (int32_t)ceil(mx[1]) + kRowMargin;
+                p.k0 = (int32_t)floor(mn[2]) - kRowMargin;
+                int32_t k1 = (int32_t)ceil(mx[2]) + kRowMargin;
                 p.nj = j1 - p.j0 + 1;
                 p.nk = k1 - p.k0 + 1;
                 // shadow on the (j, k) plane: edge a of the parallelepiped runs
@@ -235,14 +250,25 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
             }
         }
     }
+    // rows per lane: long tiles amortise the exact initial division over more
+    // rows, short ones spread a small box over more warps
+#if OBB_TILE_ADAPT
+    {
+        const int64_t rows = (int64_t)p.nj * p.nk;
+        p.tk = rows >= (int64_t(1) << 16) ? kTileK : rows >= (int64_t(1) << 13) ? kTileK / 2 : kTileK / 4;
+        if (p.tk < 1) p.tk = 1;
+    }
+#else
+    p.tk = kTileK;
+#endif
     // tile shape: wj lanes along y, wk = 32 / wj along z; the least padding wins
     // (ties to the wider wj, whose rows sit next to each other in memory)
     int best = 5;
     int64_t best_slots = INT64_MAX;
     if (p.nj > 0) {
         for (int l = 5; l >= 0; --l) {
-            const int64_t wj = 1 << l, wk = 32 >> l;
-            const int64_t slots = ((p.nj + wj - 1) / wj) * wj * ((p.nk + wk * kTileK - 1) / (wk * kTileK)) * wk * kTileK;
+            const int64_t wj = 1 << l, hk = (int64_t)(32 >> l) * p.tk;
+            const int64_t slots = ((p.nj + wj - 1) / wj) * wj * ((p.nk + hk - 1) / hk) * hk;
             if (slots < best_slots) {
                 best_slots = slots;
                 best = l;
@@ -261,7 +287,7 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
             p.rstep[a] = (int32_t)(delta - qs * p.dd[a]);
         }
     prep[k] = p;
-    tiles[k] = p.nj > 0 ? (int64_t)p.ntj * ((p.nk + wk * kTileK - 1) / (wk * kTileK)) : 0;
+    tiles[k] = p.nj > 0 ? (int64_t)p.ntj * ((p.nk + wk * p.tk - 1) / (wk * p.tk)) : 0;
 }
 
 // ------------------------------------------------------------------- scan
@@ -383,6 +409,36 @@ __device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64
 }
 
 // popcount of the occupied bits i in [a, e] of one row (0 <= a <= e < N)
+#if OBB_POPC_ILP
+// The first and last 128-bit chunks are loaded up front and the interior in
+// groups of four independent loads, so a long row waits for one or two L2
+// round trips instead of one per chunk.
+__device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
+{
+    const uint4* r4 = reinterpret_cast<const uint4*>(row);
+    const int32_t q0 = a >> 7, q1 = e >> 7;
+    const uint32_t la = a & 127, he = e & 127;
+    const uint4 f = __ldg(r4 + q0);
+    const uint4 l = __ldg(r4 + q1);
+    uint32_t cnt = 0;
+    for (int32_t qq = q0 + 1; qq < q1; qq += 4) {
+        uint4 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = qq + i < q1 ? __ldg(r4 + qq + i) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cnt += __popc(v[i].x) + __popc(v[i].y) + __popc(v[i].z) + __popc(v[i].w);
+    }
+    // keep bits >= la of the first chunk and bits <= he of the last
+    uint64_t m0 = la < 64 ? (~0ull << la) : 0ull;
+    uint64_t m1 = la < 64 ? ~0ull : (~0ull << (la - 64));
+    const uint64_t n0 = he >= 63 ? ~0ull : (~0ull >> (63 - he));
+    const uint64_t n1 = he < 64 ? 0ull : (he >= 127 ? ~0ull : (~0ull >> (127 - he)));
+    const uint64_t f0 = ((uint64_t)f.y << 32) | f.x, f1 = ((uint64_t)f.w << 32) | f.z;
+    if (q0 == q1) return __popcll(f0 & m0 & n0) + __popcll(f1 & m1 & n1);
+    const uint64_t l0 = ((uint64_t)l.y << 32) | l.x, l1 = ((uint64_t)l.w << 32) | l.z;
+    return cnt + __popcll(f0 & m0) + __popcll(f1 & m1) + __popcll(l0 & n0) + __popcll(l1 & n1);
+}
+#else
 __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
 {
     const uint4* r4 = reinterpret_cast<const uint4*>(row);
@@ -411,6 +467,7 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
     m1 = he < 64 ? 0ull : (he >= 127 ? ~0ull : (~0ull >> (127 - he)));
     return cnt + __popcll(w0 & m0) + __popcll(w1 & m1);
 }
+#endif
 
 #if OBB_COUNT_MINB > 0
 #define OBB_COUNT_BOUNDS __launch_bounds__(256, OBB_COUNT_MINB)
@@ -475,7 +532,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
 #if OBB_TILE_SKIP
         {
             // skip a tile whose rectangle misses the box's shadow on (j, k)
-            const int32_t lw = p.lwj, hk = (32 >> lw) * kTileK;
+            const int32_t lw = p.lwj, hk = (32 >> lw) * p.tk;
             const float hj = 0.5f * (float)((1 << lw) - 1), hkf = 0.5f * (float)(hk - 1);
             const float jc = (float)(p.j0 + (tj << lw)) + hj, kc = (float)(p.k0 + tk * hk) + hkf;
             bool out = false;
@@ -504,7 +561,8 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         const int32_t jl = (tj << lwj) + (lane & ((1 << lwj) - 1));
         const int32_t j = p.j0 + jl;
         const bool jvalid = jl < p.nj;
-        const int32_t kb = p.k0 + tk * (wk * kTileK) + (lane >> lwj);   // this lane's first row
+        const int32_t tkr = p.tk;
+        const int32_t kb = p.k0 + tk * (wk * tkr) + (lane >> lwj);   // this lane's first row
         const int32_t kend = p.k0 + p.nk;
         const int32_t i0 = p.i0, span = p.span;
         // Kind-1 slabs carry exact quotient bounds relative to i0 in 32 bits,
@@ -541,7 +599,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
             const int64_t rstride = (int64_t)wk * N * W;
             int32_t k = kb;
 #pragma unroll kCountUnroll
-            for (int r = 0; r < kTileK; ++r, k += wk, rowp += rstride) {
+            for (int r = 0; r < tkr; ++r, k += wk, rowp += rstride) {
                 const int32_t lo = max(max(qa[0], qa[1]), max(qa[2], 0));
                 const int32_t hi = min(min(qb[0], qb[1]), min(qb[2], span));
 #pragma unroll
@@ -577,7 +635,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         } else
 #endif
 #pragma unroll kCountUnroll
-        for (int r = 0; r < kTileK; ++r) {
+        for (int r = 0; r < tkr; ++r) {
             const int32_t k = kb + r * wk;
             int32_t lo = 0, hi = span;
             bool ok = jvalid && k < kend;
@@ -708,7 +766,7 @@ void launch_box_report(obb_ctx* ctx, const obb_lattice* lat, const double* d_fra
                        obb_box* d_out)
 {
     if (K > 0) {
-        k_report<<<(K + 127) / 128, 128, 0, ctx->stream>>>(lat->d_frame, d_frames, d_q, K, d_out);
+        k_report<<<(K + 31) / 32, 32, 0, ctx->stream>>>(lat->d_frame, d_frames, d_q, K, d_out);
         note_launch(ctx);
     }
 }
@@ -717,7 +775,7 @@ obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d
                           obb_qbox* d_out)
 {
     if (K <= 0) return OBB_OK;
-    k_quantize<<<(unsigned)((K + 127) / 128), 128, 0, ctx->stream>>>(d_boxes, K, lat->d_frame, d_out,
+    k_quantize<<<(unsigned)((K + 31) / 32), 32, 0, ctx->stream>>>(d_boxes, K, lat->d_frame, d_out,
                                                                     ctx->d_err);
     note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
@@ -755,7 +813,7 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
     int64_t* off = tiles + K_cap;
     OBB_CK(ctx, cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * K_cap, s));
     if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K_cap, s));
-    k_prep<<<(unsigned)((K_cap + 127) / 128), 128, 0, s>>>(d_boxes, d_K, d_lats, n_lats, d_lat_of_box, prep, tiles,
+    k_prep<<<(unsigned)((K_cap + 31) / 32), 32, 0, s>>>(d_boxes, d_K, d_lats, n_lats, d_lat_of_box, prep, tiles,
                                                           ctx->d_err);
     note_launch(ctx);
     k_scan_i64<<<1, 1024, 0, s>>>(tiles, off, d_K);
@@ -859,7 +917,7 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
     if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K, s));
     k_set_i32<<<1, 1, 0, s>>>(dK, (int32_t)K);
     note_launch(ctx);
-    k_prep<<<(unsigned)((K + 127) / 128), 128, 0, s>>>(d_boxes, dK, lat->d_ref, 1, nullptr, prep, chunks,
+    k_prep<<<(unsigned)((K + 31) / 32), 32, 0, s>>>(d_boxes, dK, lat->d_ref, 1, nullptr, prep, chunks,
                                                       ctx->d_err);
     note_launch(ctx);
     k_scan_i64<<<1, 1024, 0, s>>>(chunks, off, dK);

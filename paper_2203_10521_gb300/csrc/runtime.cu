@@ -507,6 +507,22 @@ obb_status obb_layer_parents(obb_ctx* ctx, const obb_layer* L, int32_t* parent)
     return check_device_error(ctx);
 }
 
+obb_status obb_flood_partition(obb_ctx* ctx, obb_layer* layer, const double* centres, int32_t mode,
+                               obb_flood_stats* stats)
+{
+    if (!ctx || !layer) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (layer->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
+    return flood_partition(ctx, layer, centres, mode, stats);
+}
+
+obb_status obb_layer_adjust(obb_ctx* ctx, obb_layer* layer, const obb_step_opts* opts, int32_t iters,
+                            obb_adjust_stats* stats)
+{
+    if (!ctx || !layer) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (layer->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
+    return layer_adjust(ctx, layer, opts, iters, stats);
+}
+
 obb_status obb_unit_step(obb_ctx* ctx, obb_layer* upper, obb_layer* lower, const obb_step_opts* opts,
                          obb_step_stats* stats)
 {

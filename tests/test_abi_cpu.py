@@ -36,6 +36,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(P.ProfileStats) == 40
     assert ctypes.sizeof(P.SweepOpts) == 16
     assert ctypes.sizeof(P.SweepStats) == 40
+    assert ctypes.sizeof(P.FloodStats) == 16
+    assert ctypes.sizeof(P.AdjustStats) == 32
 
 
 def test_no_gpu_means_no_context():
