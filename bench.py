@@ -336,7 +336,7 @@ def main():
     child = ctx.layer_split(up_layer)
     up_layer.free()
     mlp = None
-    modes = ["plain"] if args.no_surrogate else ["plain", "surrogate"]
+    modes = ["plain", "plain_graph"] if args.no_surrogate else ["plain", "plain_graph", "surrogate"]
     if not args.no_surrogate:
         from paper_2203_10521_gb300 import surrogate as S
         t0 = time.perf_counter()
@@ -356,7 +356,7 @@ def main():
         e0.record(stream)
         evals = 0
         for _ in range(args.lloyd_iters):
-            st = ctx.lloyd_step(lay, rounds=16, refit=2, descent_steps=2)
+            st = ctx.lloyd_step(lay, rounds=16, refit=2, descent_steps=2, graph=(mode == "plain_graph"))
             evals += st["box_evals"]
         e1.record(stream)
         torch.cuda.synchronize()
@@ -365,6 +365,7 @@ def main():
                        "exact_box_counts": int(evals)}
         lay.free()
     lloyd_iter_per_s = lloyd["plain"]["iter_per_s"]
+    lloyd_graph_iter_per_s = lloyd["plain_graph"]["iter_per_s"]
     surrogate_iter_per_s = lloyd["surrogate"]["iter_per_s"] if "surrogate" in lloyd else None
     if "surrogate" in lloyd:
         a, b = lloyd["plain"]["final_total_obv"], lloyd["surrogate"]["final_total_obv"]
@@ -428,6 +429,7 @@ def main():
                           "l2": "flushed between steps (256 MiB write)", "per_rank": "independent mesh (seed + rank)"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_all,
                "clocks": clocks, "lloyd_iter_per_s": lloyd_iter_per_s,
+               "lloyd_graph_iter_per_s": lloyd_graph_iter_per_s,
                "surrogate_lloyd_iter_per_s": surrogate_iter_per_s, "lloyd_comparison": lloyd,
                "lloyd_last_step": lloyd_steps[-1], "tree_setup_s": tree_s, "wall_s_timed": wall}
         print(json.dumps(out), flush=True)

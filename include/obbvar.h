@@ -148,7 +148,10 @@ obb_status obb_build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, ob
 
 /* Recompute the occupancy of an existing lattice from its mesh in place
  * (same N, same buffers, no allocation): the work of obb_build_occupancy
- * without the handle creation.  Synchronises once. */
+ * without the handle creation.  Asynchronous on the context stream: errors
+ * found on the device surface at the next synchronising call, and the host
+ * copy of the frame read by obb_lattice_desc is refreshed when it is next
+ * read. */
 obb_status obb_occupancy_rebuild(obb_ctx* ctx, obb_lattice* lat);
 
 /* Borrowed view of a lattice: frame (lo, h), N, words per row, device
@@ -206,6 +209,20 @@ obb_status obb_outer_volume_multi(obb_ctx* ctx, const obb_lattice* const* lats, 
                                   const int32_t* lattice_of_box, int64_t K, uint64_t* counts, uint64_t* points,
                                   int32_t on_device);
 
+/* Rows one lane visits per counting tile (1..128; default 32).  The count is
+ * exact for every value; only its speed changes.  Steps already captured as
+ * CUDA graphs are recaptured on their next call. */
+obb_status obb_set_counting_tile(obb_ctx* ctx, int32_t tile_k);
+
+/* Autotuner of the counting kernel: times the outer-volume count of the given
+ * quantised boxes with 8, 16, 32 and 64 rows per tile (one warm-up and three
+ * timed runs each, CUDA events on the context stream), keeps the fastest for
+ * the context and returns it in *tile_k; ms (may be NULL) receives the four
+ * average times in milliseconds.  qboxes: [K], host or device (on_device).
+ * Synchronises. */
+obb_status obb_tune_counting(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* qboxes, int64_t K,
+                             int32_t on_device, int32_t* tile_k, float* ms);
+
 /* The paper's own estimator of the outer volume (Sec. 4.1, Eq. 9-10), as ray
  * casting in place of cube-map rasterisation: from each box centre o one ray
  * per texel of a 6 x m x m cube map (through the texel centre, weighted by
@@ -244,7 +261,10 @@ typedef struct {
     int32_t refit;          /* box-parameter update after the rounds: 0 none, 1 covariance frame,
                                2 rotation descent, 3 both (covariance first) */
     int32_t descent_steps;  /* descent steps per iteration when refit & 2; <= 0: 2 */
-    int32_t reserved;
+    int32_t graph;          /* 1: run the iteration as one CUDA graph with a device-side round loop
+                               (captured on first use per rounds / refit / descent_steps, then
+                               relaunched; same kernels, same results, no host round trip per round;
+                               ignored while a surrogate is attached).  0: host-driven rounds. */
 } obb_step_opts;
 
 typedef struct {

@@ -37,7 +37,7 @@ class ObbError(RuntimeError):
 
 class StepOpts(C.Structure):
     _fields_ = [("rounds", C.c_int32), ("refit", C.c_int32), ("descent_steps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("graph", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -127,6 +127,8 @@ def load(build_if_missing: bool = True):
         "obb_layer_parents": [vp, vp, vp],
         "obb_flood_partition": [vp, vp, vp, i32, C.POINTER(FloodStats)],
         "obb_layer_adjust": [vp, vp, C.POINTER(StepOpts), i32, C.POINTER(AdjustStats)],
+        "obb_set_counting_tile": [vp, i32],
+        "obb_tune_counting": [vp, vp, vp, i64, i32, vp, vp],
         "obb_unit_step": [vp, vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
         "obb_mlp_create": [vp, C.c_uint64, C.POINTER(vp)],
         "obb_mlp_params": [vp, vp, vp, i32],
@@ -168,7 +170,7 @@ def exported_symbols():
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
             "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free", "obb_tree_parents",
             "obb_tree_sweep", "obb_layer_parents", "obb_unit_step", "obb_flood_partition",
-            "obb_layer_adjust",
+            "obb_layer_adjust", "obb_set_counting_tile", "obb_tune_counting",
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_mlp_forward", "obb_mlp_gradients", "obb_mlp_train_step",
             "obb_layer_set_surrogate", "obb_layer_last_candidates"]
@@ -296,6 +298,19 @@ class Context:
         K = _count(qboxes, keep, 88)
         return self._ov(self.lib.obb_outer_volume_q, lat, p, dev, K, counts, points, want_points)
 
+    def set_counting_tile(self, tile_k):
+        self.check(self.lib.obb_set_counting_tile(self.h, int(tile_k)))
+
+    def tune_counting(self, lat, qboxes):
+        """Time the count of these quantised boxes with 8/16/32/64 rows per tile and
+        keep the fastest; returns (tile_k, {tile_k: ms})."""
+        q = _host(qboxes, QBOX_DTYPE)
+        tk = C.c_int32()
+        ms = (C.c_float * 4)()
+        self.check(self.lib.obb_tune_counting(self.h, lat.h, q.ctypes.data_as(C.c_void_p), len(q), 0,
+                                              C.byref(tk), ms))
+        return tk.value, dict(zip((8, 16, 32, 64), list(ms)))
+
     def directional_outer_volume(self, mesh, boxes, m=32):
         """The paper's cube-map ray estimator of the outer volume (world units^3), host arrays."""
         b = _host(boxes, BOX_DTYPE)
@@ -366,9 +381,10 @@ class Context:
         self.check(self.lib.obb_layer_init(self.h, lat.h, pa, pp, int(K), pf, dev, C.byref(h)))
         return Layer(self, h, lat, K)
 
-    def lloyd_step(self, layer, rounds=16, refit=True, stats=True, descent_steps=0):
-        """refit: False/0 none, True/1 covariance frame, 2 rotation descent, 3 both."""
-        o = StepOpts(int(rounds), int(refit), int(descent_steps), 0)
+    def lloyd_step(self, layer, rounds=16, refit=True, stats=True, descent_steps=0, graph=False):
+        """refit: False/0 none, True/1 covariance frame, 2 rotation descent, 3 both;
+        graph: run the iteration as one CUDA graph (device-side round loop)."""
+        o = StepOpts(int(rounds), int(refit), int(descent_steps), int(bool(graph)))
         st = StepStats()
         self.check(self.lib.obb_lloyd_step(self.h, layer.h, C.byref(o), C.byref(st) if stats else None))
         return st.as_dict() if stats else None

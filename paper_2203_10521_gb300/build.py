@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libobbvar.so")
-UNITS = ["runtime.cu", "occupancy.cu", "outer_volume.cu", "lloyd.cu", "tree.cu", "surrogate.cu", "directional.cu", "sweep.cu", "flood.cu", "adjust.cu"]
+UNITS = ["runtime.cu", "occupancy.cu", "outer_volume.cu", "lloyd.cu", "tree.cu", "surrogate.cu", "directional.cu", "sweep.cu", "flood.cu", "adjust.cu", "mesh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -82,6 +82,16 @@ struct LatRef {
 };
 
 // Stream-ordered device allocation that only grows.
+// Scratch of the counting path at fixed addresses (used while a step is
+// captured into a CUDA graph): prep [cap], tiles + offsets [2 cap + 2], and a
+// zero-initialised ticket.
+struct CountScratch {
+    BoxPrep* prep = nullptr;
+    int64_t* tiles = nullptr;
+    unsigned int* ticket = nullptr;
+    int64_t cap = 0;
+};
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -99,6 +109,10 @@ struct obb_ctx {
     int num_sms = 0;
     std::string err;
     int32_t* d_err = nullptr;        // device error word
+    unsigned int* d_ticket = nullptr; // finish counter of the box-preparation blocks (zero between launches)
+    const obbv::CountScratch* count_scratch = nullptr;   // set while a step is being captured
+    int32_t tile_k = obbv::kTileK;   // rows per lane per counting tile
+    int32_t tile_gen = 0;            // bumped when tile_k changes (captured steps recapture)
     int32_t* h_small = nullptr;      // pinned host staging (512 bytes; the first 64 hold the error word)
     // scratch reused across calls
     obbv::DevBuf prep, chunk_off, qscratch, cscratch, pscratch, kdev, tmp_a, tmp_b, tmp_c, tmp_d,
@@ -123,7 +137,8 @@ struct obb_mesh {
 struct obb_lattice {
     obb_ctx* ctx = nullptr;
     const obb_mesh* mesh = nullptr;
-    obbv::LatticeFrame frame{};      // host copy
+    mutable obbv::LatticeFrame frame{};   // host copy (lo, h refreshed on demand after a rebuild)
+    mutable bool frame_stale = false;      // a rebuild may have moved lo / h since the last copy
     obbv::LatticeFrame* d_frame = nullptr;
     int32_t* d_fixed = nullptr;      // [nv][3] snapped vertices
     uint64_t* d_words = nullptr;     // occupancy
@@ -179,6 +194,7 @@ int captured_launches(obb_ctx* ctx, int64_t key0, int key1, const std::function<
 obb_status fail(obb_ctx* ctx, obb_status code, const std::string& msg);
 obb_status cuda_fail(obb_ctx* ctx, cudaError_t e, const char* what);
 obb_status check_device_error(obb_ctx* ctx);   // synchronises, reads and clears the error word
+obb_status lattice_frame_host(const obb_lattice* lat);   // refreshes lat->frame if stale (synchronises)
 
 #define OBB_CK(ctx, call)                                              \
     do {                                                               \
@@ -251,6 +267,9 @@ obb_status flood_partition(obb_ctx* ctx, obb_layer* L, const double* d_centres, 
 
 // adjust.cu: box adjustment out of local minima (Sec. 4.2.1 step 3)
 obb_status layer_adjust(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, int32_t iters, obb_adjust_stats* out);
+
+// mesh.cu: upload and device-side validation + adjacency of a closed mesh
+obb_status mesh_upload(obb_ctx* ctx, const float* verts, int64_t nv, const int32_t* tris, int64_t nt, obb_mesh* m);
 
 // tree.cu
 obb_status build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_opts* opts, obb_tree* tree);

@@ -24,6 +24,8 @@
 // the new box is kept iff its outer volume is strictly smaller.
 #include <cub/cub.cuh>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace obbv {
@@ -579,6 +581,22 @@ __global__ void k_total(const uint64_t* __restrict__ obv, int32_t K, int64_t* __
     }
 }
 
+// End of a partition round inside a captured step: rounds run, moves so far,
+// and the two conditions of the graph (run another round; rebuild the member
+// lists first).  loop: [0] rounds run, [1] moves accepted before this round,
+// [2] member-list rebuilds.
+__global__ void k_round_end(const int64_t* __restrict__ stats, int64_t* __restrict__ loop, int32_t rounds,
+                            cudaGraphConditionalHandle again, cudaGraphConditionalHandle rebuild)
+{
+    const int64_t acc = stats[kStAccepted];
+    const int64_t moved = acc - loop[1];
+    loop[1] = acc;
+    loop[0] += 1;
+    if (moved > 0) loop[2] += 1;
+    cudaGraphSetConditional(again, (moved > 0 && loop[0] < rounds) ? 1u : 0u);
+    cudaGraphSetConditional(rebuild, moved > 0 ? 1u : 0u);
+}
+
 // ------------------------------------------------------- surrogate screening
 
 __device__ __forceinline__ uint32_t float_key(float f)
@@ -812,6 +830,13 @@ struct LayerMem {
     obb_qbox* pq = nullptr;         // [K * 6] probe boxes
     unsigned long long* pbest = nullptr;  // [K]
     int32_t cand_cap = 0, eval_cap = 0;
+    // a whole Lloyd iteration captured as one CUDA graph (see lloyd_step_graph)
+    cudaGraphExec_t gexec = nullptr;
+    int gkey[4] = {-1, -1, -1, -1};   // rounds, refit mode, descent steps, counting-tile generation
+    int64_t* loop = nullptr;          // [0] rounds run, [1] moves before the round, [2] rebuilds, [3] total
+    CountScratch cscr{};              // the graph's own counting scratch (fixed addresses)
+    void* cscr_mem = nullptr;
+    int64_t g_round = 0, g_rebuild = 0, g_post = 0;   // kernel launches per round, per rebuild, after the loop
     void* cub_tmp = nullptr;
     size_t cub_bytes = 0;
     int end_bit = 1;
@@ -857,6 +882,9 @@ void layer_destroy(obb_layer* L)
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, s);
     if (M) {
+        if (M->gexec) cudaGraphExecDestroy(M->gexec);
+        if (M->loop) cudaFreeAsync(M->loop, s);
+        if (M->cscr_mem) cudaFreeAsync(M->cscr_mem, s);
         void* mp[] = {M->iota, M->keys_out, M->ctr, M->cand, M->evals, M->ecount, M->epoints, M->mom,
                       M->newframe, M->newq, M->ncount, M->dK, M->cub_tmp, M->feats, M->pred, M->skey,
                       M->kept, M->slot, M->evals2, M->n2, M->map, M->dirty, M->keep, M->level,
@@ -984,70 +1012,249 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     return OBB_OK;
 }
 
-obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb_step_stats* st)
+// One partition round (a6-a8) on ctx->stream, without host synchronisation.
+static obb_status round_body(obb_ctx* ctx, obb_layer* L)
 {
     cudaStream_t s = ctx->stream;
     LayerMem* M = mem_of(L);
     const obb_lattice* lat = L->lat;
     const obb_mesh* mesh = lat->mesh;
     const int K = L->K;
+    k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, L->d_q, L->d_ext);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaMemsetAsync(M->ctr, 0, sizeof(int32_t) * kCtrCount, s));
+    OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
+    k_candidates<<<(unsigned)((L->T + 127) / 128), 128, 0, s>>>(
+        lat->d_fixed, mesh->d_tris, mesh->d_adj, L->T, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
+        M->cand, M->evals, M->ctr, M->cand_cap, M->eval_cap, ctx->d_err);
+    note_launch(ctx);
+    const obb_qbox* evals = M->evals;
+    const int32_t* n_eval = M->ctr + kCtrEval;
+    if (L->mlp && L->topk > 0) {
+        // surrogate screening: predicted gains keep the top-k candidates of each
+        // source cluster; only their boxes are counted exactly
+        OBB_TRY(surrogate_predict(ctx, L->mlp, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->feats, M->pred));
+        const unsigned cb0 = (unsigned)((M->cand_cap + 127) / 128);
+        k_screen_score<<<cb0, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->pred, M->skey, M->kept);
+        note_launch(ctx);
+        for (int pass = 0; pass < L->topk; ++pass) {
+            OBB_CK(ctx, cudaMemsetAsync(M->slot, 0, sizeof(unsigned long long) * K, s));
+            k_screen_pick<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->kept, M->slot);
+            k_screen_mark<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->kept, M->slot);
+            note_launch(ctx, 2);
+        }
+        OBB_CK(ctx, cudaMemsetAsync(M->n2, 0, sizeof(int32_t), s));
+        k_screen_compact<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->kept, M->evals, M->evals2, M->n2);
+        note_launch(ctx);
+        evals = M->evals2;
+        n_eval = M->n2;
+    }
+    OBB_TRY(count_boxes(ctx, lat, evals, n_eval, M->eval_cap, M->ecount, M->epoints));
+    k_sum_points<<<32, 256, 0, s>>>(M->epoints, n_eval, L->d_stats);
+    note_launch(ctx);
+    const unsigned cb = (unsigned)((M->cand_cap + 127) / 128);
+    k_gains<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->ecount, L->d_best, L->d_stats);
+    note_launch(ctx);
+    k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
+                                L->d_size, L->d_stats, M->dirty, M->level);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
+
+static obb_status lloyd_step_graph(obb_ctx* ctx, obb_layer* L, int rounds, int refit_mode, int dsteps,
+                                   obb_step_stats* st);
+
+obb_status lloyd_step(obb_ctx* ctx, obb_layer* L, const obb_step_opts* opts, obb_step_stats* st)
+{
+    cudaStream_t s = ctx->stream;
+    LayerMem* M = mem_of(L);
     const int rounds = (opts && opts->rounds > 0) ? opts->rounds : 16;
     const int refit_mode = opts ? opts->refit : 1;
     const int dsteps = (opts && opts->descent_steps > 0) ? opts->descent_steps : 2;
+    if (opts && opts->graph && !L->mlp) return lloyd_step_graph(ctx, L, rounds, refit_mode, dsteps, st);
     OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
     int64_t* h = host_stats(ctx);
     int ran = 0;
+    int64_t before = 0;
     for (int r = 0; r < rounds; ++r) {
         if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
-        k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, L->d_q, L->d_ext);
-        note_launch(ctx);
-        OBB_CK(ctx, cudaMemsetAsync(M->ctr, 0, sizeof(int32_t) * kCtrCount, s));
-        OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
-        k_candidates<<<(unsigned)((L->T + 127) / 128), 128, 0, s>>>(
-            lat->d_fixed, mesh->d_tris, mesh->d_adj, L->T, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
-            M->cand, M->evals, M->ctr, M->cand_cap, M->eval_cap, ctx->d_err);
-        note_launch(ctx);
-        const obb_qbox* evals = M->evals;
-        const int32_t* n_eval = M->ctr + kCtrEval;
-        if (L->mlp && L->topk > 0) {
-            // surrogate screening: predicted gains keep the top-k candidates of each
-            // source cluster; only their boxes are counted exactly
-            OBB_TRY(surrogate_predict(ctx, L->mlp, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->feats, M->pred));
-            const unsigned cb0 = (unsigned)((M->cand_cap + 127) / 128);
-            k_screen_score<<<cb0, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->pred, M->skey, M->kept);
-            note_launch(ctx);
-            for (int pass = 0; pass < L->topk; ++pass) {
-                OBB_CK(ctx, cudaMemsetAsync(M->slot, 0, sizeof(unsigned long long) * K, s));
-                k_screen_pick<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->kept, M->slot);
-                k_screen_mark<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->kept, M->slot);
-                note_launch(ctx, 2);
-            }
-            OBB_CK(ctx, cudaMemsetAsync(M->n2, 0, sizeof(int32_t), s));
-            k_screen_compact<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->kept, M->evals, M->evals2, M->n2);
-            note_launch(ctx);
-            evals = M->evals2;
-            n_eval = M->n2;
-        }
-        OBB_TRY(count_boxes(ctx, lat, evals, n_eval, M->eval_cap, M->ecount, M->epoints));
-        k_sum_points<<<32, 256, 0, s>>>(M->epoints, n_eval, L->d_stats);
-        note_launch(ctx);
-        const unsigned cb = (unsigned)((M->cand_cap + 127) / 128);
-        k_gains<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->ecount, L->d_best, L->d_stats);
-        note_launch(ctx);
-        const int64_t before = (r == 0) ? 0 : h[1];
-        k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
-                                    L->d_size, L->d_stats, M->dirty, M->level);
-        note_launch(ctx);
-        OBB_CK(ctx, cudaGetLastError());
+        OBB_TRY(round_body(ctx, L));
         OBB_CK(ctx, cudaMemcpyAsync(h, L->d_stats, sizeof(int64_t) * kStCount, cudaMemcpyDeviceToHost, s));
         OBB_CK(ctx, cudaStreamSynchronize(s));
         ++ran;
         const int64_t moved = h[kStAccepted] - before;
+        before = h[kStAccepted];
         if (moved > 0) M->members_valid = false;
         if (moved == 0) break;
     }
     OBB_TRY(layer_box_update(ctx, L, refit_mode, dsteps));
     return layer_finish_stats(ctx, L, ran, st);
+}
+
+// The Lloyd iteration as one CUDA graph: the partition rounds run in a
+// device-side WHILE loop (a conditional node whose condition the last kernel of
+// each round sets), the member lists are rebuilt inside an IF node after a
+// round that moved triangles, and the box update follows.  The graph is
+// captured once per (rounds, refit, descent steps, counting tile) and
+// relaunched; it runs the same kernels in the same order as the host loop, so
+// results are identical, without a host round trip per round.  Its counting
+// launches use scratch of their own (fixed addresses) and are not profiled one
+// by one.
+static obb_status lloyd_step_graph(obb_ctx* ctx, obb_layer* L, int rounds, int refit_mode, int dsteps,
+                                   obb_step_stats* st)
+{
+    LayerMem* M = mem_of(L);
+    const int K = L->K;
+    cudaStream_t s = ctx->stream;
+    if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
+    if (!M->gexec || M->gkey[0] != rounds || M->gkey[1] != refit_mode || M->gkey[2] != dsteps ||
+        M->gkey[3] != ctx->tile_gen) {
+        if (M->gexec) {
+            OBB_CK(ctx, cudaGraphExecDestroy(M->gexec));
+            M->gexec = nullptr;
+        }
+        if (!M->loop) OBB_CK(ctx, cudaMallocAsync((void**)&M->loop, sizeof(int64_t) * 4, s));
+        if (!M->cscr_mem) {
+            const int64_t cap = std::max<int64_t>({(int64_t)M->eval_cap, (int64_t)kProbes * K, (int64_t)K});
+            const size_t pb = (sizeof(BoxPrep) * cap + 255) / 256 * 256;
+            const size_t tb = (sizeof(int64_t) * (2 * cap + 2) + 255) / 256 * 256;
+            OBB_CK(ctx, cudaMallocAsync(&M->cscr_mem, pb + tb + 256, s));
+            char* b = static_cast<char*>(M->cscr_mem);
+            M->cscr.prep = reinterpret_cast<BoxPrep*>(b);
+            M->cscr.tiles = reinterpret_cast<int64_t*>(b + pb);
+            M->cscr.ticket = reinterpret_cast<unsigned int*>(b + pb + tb);
+            M->cscr.cap = cap;
+            OBB_CK(ctx, cudaMemsetAsync(M->cscr.ticket, 0, sizeof(unsigned int), s));
+        }
+        OBB_CK(ctx, cudaStreamSynchronize(s));
+        cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
+        for (auto& c : cs) OBB_CK(ctx, cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+        const cudaStream_t saved_stream = ctx->stream;
+        const bool saved_prof = ctx->prof;
+        const int64_t saved_launches = ctx->launches;
+        ctx->prof = false;
+        ctx->count_scratch = &M->cscr;
+        M->members_valid = true;   // valid on entry; the graph rebuilds them after moving rounds
+        cudaGraph_t g = nullptr;
+        obb_status rc = OBB_OK;
+        cudaError_t e = cudaSuccess;
+        int depth = 0;   // captures still open
+        auto ck = [&](cudaError_t x) {
+            if (e == cudaSuccess && x != cudaSuccess) e = x;
+            return e == cudaSuccess;
+        };
+        do {
+            ctx->stream = cs[0];
+            if (!ck(cudaStreamBeginCapture(cs[0], cudaStreamCaptureModeThreadLocal))) break;
+            depth = 1;
+            ck(cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, cs[0]));
+            ck(cudaMemsetAsync(M->loop, 0, sizeof(int64_t) * 4, cs[0]));
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            if (!ck(cudaStreamGetCaptureInfo(cs[0], &cst, nullptr, &g, &deps, nullptr, &nd))) break;
+            cudaGraphConditionalHandle again, rebuild;
+            if (!ck(cudaGraphConditionalHandleCreate(&again, g, 1, cudaGraphCondAssignDefault))) break;
+            cudaGraphNodeParams wp = {};
+            wp.type = cudaGraphNodeTypeConditional;
+            wp.conditional.handle = again;
+            wp.conditional.type = cudaGraphCondTypeWhile;
+            wp.conditional.size = 1;
+            cudaGraphNode_t wn;
+            if (!ck(cudaGraphAddNode(&wn, g, deps, nullptr, nd, &wp))) break;
+            cudaGraph_t body = wp.conditional.phGraph_out[0];
+            if (!ck(cudaStreamUpdateCaptureDependencies(cs[0], &wn, nullptr, 1, cudaStreamSetCaptureDependencies)))
+                break;
+            if (!ck(cudaGraphConditionalHandleCreate(&rebuild, body, 0, cudaGraphCondAssignDefault))) break;
+            // the round
+            ctx->stream = cs[1];
+            if (!ck(cudaStreamBeginCaptureToGraph(cs[1], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+                break;
+            depth = 2;
+            const int64_t l0 = ctx->launches;
+            rc = round_body(ctx, L);
+            if (rc != OBB_OK) break;
+            k_round_end<<<1, 1, 0, cs[1]>>>(L->d_stats, M->loop, rounds, again, rebuild);
+            note_launch(ctx);
+            if (!ck(cudaGetLastError())) break;
+            M->g_round = ctx->launches - l0;
+            cudaGraph_t bg = nullptr;
+            if (!ck(cudaStreamGetCaptureInfo(cs[1], &cst, nullptr, &bg, &deps, nullptr, &nd))) break;
+            cudaGraphNodeParams ip = {};
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = rebuild;
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            cudaGraphNode_t in;
+            if (!ck(cudaGraphAddNode(&in, bg, deps, nullptr, nd, &ip))) break;
+            cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+            if (!ck(cudaStreamUpdateCaptureDependencies(cs[1], &in, nullptr, 1, cudaStreamSetCaptureDependencies)))
+                break;
+            // the member lists after a round that moved triangles
+            ctx->stream = cs[2];
+            if (!ck(cudaStreamBeginCaptureToGraph(cs[2], ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)))
+                break;
+            depth = 3;
+            const int64_t l1 = ctx->launches;
+            rc = rebuild_members(ctx, L);
+            if (rc != OBB_OK) break;
+            M->g_rebuild = ctx->launches - l1;
+            if (!ck(cudaStreamEndCapture(cs[2], &ibody))) break;
+            depth = 2;
+            if (!ck(cudaStreamEndCapture(cs[1], &bg))) break;
+            depth = 1;
+            // the box update and the layer total
+            ctx->stream = cs[0];
+            const int64_t l2 = ctx->launches;
+            rc = layer_box_update(ctx, L, refit_mode, dsteps);
+            if (rc != OBB_OK) break;
+            k_total<<<1, 1024, 0, cs[0]>>>(L->d_obv, K, M->loop + 3);
+            note_launch(ctx);
+            M->g_post = ctx->launches - l2;
+            if (!ck(cudaGetLastError())) break;
+            if (!ck(cudaStreamEndCapture(cs[0], &g))) break;
+            depth = 0;
+            if (!ck(cudaGraphInstantiate(&M->gexec, g, 0))) break;
+        } while (false);
+        // close whatever capture is still open, innermost first
+        for (int d = depth; d >= 1; --d) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(cs[d - 1], &junk);
+            if (junk && d == 1) cudaGraphDestroy(junk);
+        }
+        if (g && depth == 0) cudaGraphDestroy(g);
+        ctx->stream = saved_stream;
+        ctx->prof = saved_prof;
+        ctx->count_scratch = nullptr;
+        ctx->launches = saved_launches;
+        for (auto& c : cs) cudaStreamDestroy(c);
+        if (rc != OBB_OK) return rc;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "capture of the Lloyd iteration");
+        M->gkey[0] = rounds;
+        M->gkey[1] = refit_mode;
+        M->gkey[2] = dsteps;
+        M->gkey[3] = ctx->tile_gen;
+    }
+    OBB_CK(ctx, cudaGraphLaunch(M->gexec, s));
+    int64_t* h = host_stats(ctx);
+    OBB_CK(ctx, cudaMemcpyAsync(h, L->d_stats, sizeof(int64_t) * kStCount, cudaMemcpyDeviceToHost, s));
+    OBB_CK(ctx, cudaMemcpyAsync(h + kStCount, M->loop, sizeof(int64_t) * 4, cudaMemcpyDeviceToHost, s));
+    OBB_TRY(check_device_error(ctx));
+    M->members_valid = true;
+    const int64_t ran = h[kStCount], rebuilds = h[kStCount + 2];
+    note_launch(ctx, (int)(M->g_round * ran + M->g_rebuild * rebuilds + M->g_post));
+    if (st) {
+        st->rounds_run = (int32_t)ran;
+        st->refits_accepted = (int32_t)h[kStRefits];
+        st->proposals = h[kStProposals];
+        st->moves = h[kStAccepted];
+        st->gain = h[kStGain];
+        st->box_evals = h[kStEvals];
+        st->points_counted = (uint64_t)h[kStPoints];
+        st->total_obv = (uint64_t)h[kStCount + 3];
+    }
+    return OBB_OK;
 }
 
 // Box update of a layer after its partition rounds (Sec. 4.2.1 step 2):

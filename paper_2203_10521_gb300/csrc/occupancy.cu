@@ -237,8 +237,8 @@ obb_status rebuild_occupancy(obb_ctx* ctx, obb_lattice* lat)
     k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, N, W);
     note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
-    OBB_CK(ctx, cudaMemcpyAsync(&lat->frame, lat->d_frame, sizeof(LatticeFrame), cudaMemcpyDeviceToHost, s));
-    return check_device_error(ctx);
+    lat->frame_stale = true;   // the host copy is refreshed when a host reader needs it
+    return OBB_OK;
 }
 
 obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_lattice* lat)
@@ -257,7 +257,9 @@ obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_la
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_ref, sizeof(LatRef), s));
     lat->ref = LatRef{lat->d_words, N, W};
     OBB_CK(ctx, cudaMemcpyAsync(lat->d_ref, &lat->ref, sizeof(LatRef), cudaMemcpyHostToDevice, s));
-    return rebuild_occupancy(ctx, lat);
+    OBB_TRY(rebuild_occupancy(ctx, lat));
+    OBB_TRY(lattice_frame_host(lat));
+    return check_device_error(ctx);
 }
 
 }  // namespace obbv

@@ -2,18 +2,21 @@
 //
 // A box is the integer slab set lo_a <= n_a . (256 p) <= hi_a.  Counting:
 //   prep   per box: index-space bounds Lq = ceil(lo / 256), Hq = floor(hi / 256),
-//          a conservative integer AABB from the FP64 corners (+-2), and the
-//          per-z step of each slab's quotient (exact, int64);
-//   scan   exclusive prefix of the boxes' tile counts (one block);
-//   count  persistent warps over tiles of 32 (j) x kTileK (k) rows of one box.
-//          Each lane owns one j and walks kTileK rows along z: it divides the
-//          six slab bounds exactly once per tile (float seed + int64
-//          correction) and then advances every quotient by an integer DDA
-//          (add the step, carry the remainder), so each row's exact
-//          x-interval costs adds and compares only.  The occupied bits of the
-//          interval are popcounted over 128-bit loads; outer volume = interval
-//          length - occupied bits, and rows or points outside [0, N)^3 are all
-//          empty.
+//          a conservative (j, k) rectangle from the FP64 corners (one-row
+//          margins), the tile shape, the per-row step of each slab's quotient
+//          and three separating axes of the box's shadow on the (j, k) plane;
+//          the last block to finish scans the tile counts into per-box offsets
+//          and clears the work counter;
+//   count  persistent warps take one tile at a time from the counter: wj (y)
+//          x wk * tk (z) rows of one box, wj * wk = 32 lanes.  A tile outside
+//          the box's shadow is skipped.  Each lane owns one j and walks tk
+//          rows along z: it divides the six slab bounds exactly once per tile
+//          (float seed + int64 correction) and then advances every quotient by
+//          an integer DDA (add the step, carry the remainder), so each row's
+//          exact x-interval costs adds and compares only.  The occupied bits of
+//          the interval are popcounted over 128-bit loads; outer volume =
+//          interval length - occupied bits, and rows or points outside
+//          [0, N)^3 are all empty.
 // Counts are integer sums (warp reduction + one 64-bit atomic per tile), so
 // the result does not depend on scheduling.
 #include <mutex>
@@ -43,10 +46,6 @@
 #ifndef OBB_FAST_DDA
 #define OBB_FAST_DDA 1
 #endif
-// OBB_TILE_ADAPT: rows per lane chosen per box (kTileK for large boxes, less for small)
-#ifndef OBB_TILE_ADAPT
-#define OBB_TILE_ADAPT 0
-#endif
 // OBB_ROW_MARGIN: rows added on each side of a box's (j, k) bounding rectangle
 #ifndef OBB_ROW_MARGIN
 #define OBB_ROW_MARGIN 1
@@ -59,6 +58,7 @@ namespace obbv {
 // tuning parameters: unroll factor of the counting kernel's row loop, tiles per work grab
 constexpr int kCountUnroll = OBB_COUNT_UNROLL;
 constexpr int kRowMargin = OBB_ROW_MARGIN;
+constexpr int kPrepThreads = 32;   // one warp per preparation block: its FP64 work spreads over many SMs
 constexpr int kGrab = OBB_GRAB;
 }  // namespace obbv
 
@@ -122,18 +122,11 @@ __global__ void k_quantize(const obb_box* __restrict__ boxes, int64_t K, const L
 
 // ------------------------------------------------------------------- prep
 
-__device__ __forceinline__ int64_t floordiv64(int64_t a, int64_t d)   // d > 0
+__device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int64_t k,
+                                        const LatRef* __restrict__ lats, int32_t n_lats,
+                                        const int32_t* __restrict__ lat_of_box, int32_t tile_k,
+                                        BoxPrep* __restrict__ prep, int64_t* __restrict__ tiles, int32_t* err)
 {
-    int64_t q = a / d;
-    return (q * d > a) ? q - 1 : q;
-}
-
-__global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __restrict__ d_K,
-                       const LatRef* __restrict__ lats, int32_t n_lats, const int32_t* __restrict__ lat_of_box,
-                       BoxPrep* __restrict__ prep, int64_t* __restrict__ tiles, int32_t* err)
-{
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= *d_K) return;
     const obb_qbox q = boxes[k];
     BoxPrep p;
     p.lat = lat_of_box ? lat_of_box[k] : 0;
@@ -226,49 +219,43 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
                 // orthogonal to that edge's shadow, and the shadow's extent
                 // along nu_a is the sum over the other two constraints b of
                 // nu_a . (column b) times [L_b, H_b]
+                // (FP32: the test is conservative by two rows, far above its rounding)
+                float mi[9];
+                for (int i = 0; i < 9; ++i) mi[i] = (float)(inv[i] * id);
                 for (int a = 0; a < 3; ++a) {
-                    double nj_ = -inv[3 * 2 + a] * id, nk_ = inv[3 * 1 + a] * id;
-                    const double len = sqrt(nj_ * nj_ + nk_ * nk_);
-                    double emax = 0.0;
-                    for (int r = 0; r < 3; ++r) emax = fmax(emax, fabs(inv[3 * r + a] * id));
-                    if (!(len > 1e-6 * emax)) continue;   // edge parallel to x: no axis
+                    float nj_ = -mi[3 * 2 + a], nk_ = mi[3 * 1 + a];
+                    const float len = sqrtf(nj_ * nj_ + nk_ * nk_);
+                    const float emax = fmaxf(fabsf(mi[a]), fmaxf(fabsf(mi[3 + a]), fabsf(mi[6 + a])));
+                    if (!(len > 1e-6f * emax)) continue;   // edge parallel to x: no axis
                     nj_ /= len;
                     nk_ /= len;
-                    double lo = 0.0, hi = 0.0;
+                    float lo = 0.0f, hi = 0.0f;
                     for (int b = 0; b < 3; ++b) {
                         if (b == a) continue;
-                        const double w = nj_ * inv[3 * 1 + b] * id + nk_ * inv[3 * 2 + b] * id;
-                        const double x0 = w * (double)p.Lq[b], x1 = w * (double)p.Hq[b];
-                        lo += fmin(x0, x1);
-                        hi += fmax(x0, x1);
+                        const float w = nj_ * mi[3 * 1 + b] + nk_ * mi[3 * 2 + b];
+                        const float x0 = w * (float)p.Lq[b], x1 = w * (float)p.Hq[b];
+                        lo += fminf(x0, x1);
+                        hi += fmaxf(x0, x1);
                     }
-                    p.sat_nu[a][0] = (float)nj_;
-                    p.sat_nu[a][1] = (float)nk_;
-                    p.sat_lo[a] = (float)(lo - 2.0);
-                    p.sat_hi[a] = (float)(hi + 2.0);
+                    p.sat_nu[a][0] = nj_;
+                    p.sat_nu[a][1] = nk_;
+                    p.sat_lo[a] = lo - 2.0f;
+                    p.sat_hi[a] = hi + 2.0f;
                 }
             }
         }
     }
-    // rows per lane: long tiles amortise the exact initial division over more
-    // rows, short ones spread a small box over more warps
-#if OBB_TILE_ADAPT
-    {
-        const int64_t rows = (int64_t)p.nj * p.nk;
-        p.tk = rows >= (int64_t(1) << 16) ? kTileK : rows >= (int64_t(1) << 13) ? kTileK / 2 : kTileK / 4;
-        if (p.tk < 1) p.tk = 1;
-    }
-#else
-    p.tk = kTileK;
-#endif
+    // rows per lane per tile: long tiles amortise the exact initial division
+    // over more rows (set per context; obb_tune_counting picks it by timing)
+    p.tk = tile_k;
     // tile shape: wj lanes along y, wk = 32 / wj along z; the least padding wins
     // (ties to the wider wj, whose rows sit next to each other in memory)
     int best = 5;
     int64_t best_slots = INT64_MAX;
     if (p.nj > 0) {
         for (int l = 5; l >= 0; --l) {
-            const int64_t wj = 1 << l, hk = (int64_t)(32 >> l) * p.tk;
-            const int64_t slots = ((p.nj + wj - 1) / wj) * wj * ((p.nk + hk - 1) / hk) * hk;
+            const int32_t hk = (32 >> l) * p.tk;
+            const int64_t slots = (int64_t)(((p.nj + (1 << l) - 1) >> l) << l) * (int64_t)(((p.nk + hk - 1) / hk) * hk);
             if (slots < best_slots) {
                 best_slots = slots;
                 best = l;
@@ -281,13 +268,81 @@ __global__ void k_prep(const obb_qbox* __restrict__ boxes, const int32_t* __rest
     for (int a = 0; a < 3; ++a)
         if ((p.mode >> (2 * a)) & 3) {
             // between a lane's rows k advances by wk: X_lo and X_hi move by -sign(d) * n_a2 * wk
-            const int64_t delta = -(int64_t)(p.n[3 * a] > 0 ? 1 : -1) * (int64_t)p.n[3 * a + 2] * wk;
-            const int64_t qs = floordiv64(delta, p.dd[a]);
-            p.qstep[a] = (int32_t)qs;   // |qs| <= 32 * 2^24 / 32 for |n_a0| >= 32
-            p.rstep[a] = (int32_t)(delta - qs * p.dd[a]);
+            // |delta| <= 2^24 * 32 and 0 < dd < 2^25: exact in 32 bits
+            const int32_t delta = -(p.n[3 * a] > 0 ? 1 : -1) * p.n[3 * a + 2] * wk;
+            int32_t qs = delta / p.dd[a];
+            if (qs * p.dd[a] > delta) --qs;   // floor
+            p.qstep[a] = qs;
+            p.rstep[a] = delta - qs * p.dd[a];
         }
     prep[k] = p;
     tiles[k] = p.nj > 0 ? (int64_t)p.ntj * ((p.nk + wk * p.tk - 1) / (wk * p.tk)) : 0;
+}
+
+// One box per thread (k_prep_box), counts zeroed on the way; then the last
+// block to finish (an atomic ticket, nothing waits) turns the tile counts into
+// offsets: off[0..K] exclusive, off[K + 1] = 0 (the counting kernel's work
+// counter).
+__global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restrict__ boxes,
+                                                       const int32_t* __restrict__ d_K,
+                                                       const LatRef* __restrict__ lats, int32_t n_lats,
+                                                       const int32_t* __restrict__ lat_of_box, int32_t tile_k,
+                                                       BoxPrep* __restrict__ prep, int64_t* __restrict__ tiles,
+                                                       int64_t* __restrict__ off,
+                                                       unsigned long long* __restrict__ counts,
+                                                       unsigned long long* __restrict__ points,
+                                                       unsigned int* __restrict__ ticket, int32_t* err)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t K = *d_K;
+    if (k < K) {
+        counts[k] = 0;
+        if (points) points[k] = 0;
+        k_prep_box(boxes, k, lats, n_lats, lat_of_box, tile_k, prep, tiles, err);
+    }
+    // the block's writes, then one gpu-scope fence before its ticket
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (last) __threadfence();
+    }
+    __syncthreads();
+    if (!last) return;
+    // exclusive scan of tiles[0..K) by the last block (one warp): chunks of
+    // 4 x 32 consecutive values, a thread's four in registers, a warp scan of
+    // the thread sums, and a running carry
+    const int lane = threadIdx.x & 31;
+    int64_t carry = 0;
+    for (int32_t base = 0; base < K; base += 128) {
+        int64_t v[4];
+        int64_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int32_t i = base + 4 * lane + q;
+            v[q] = i < K ? tiles[i] : 0;
+            sum += v[q];
+        }
+        int64_t x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        int64_t run = carry + x - sum;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int32_t i = base + 4 * lane + q;
+            if (i < K) off[i] = run;
+            run += v[q];
+        }
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (threadIdx.x == 0) {
+        off[K] = carry;
+        off[K + 1] = 0;
+        *ticket = 0;   // ready for the next launch
+    }
 }
 
 // ------------------------------------------------------------------- scan
@@ -318,38 +373,6 @@ __global__ void k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__
         run += in[i];
     }
     if (threadIdx.x == T - 1) out[n] = part[T - 1];
-}
-
-// Exclusive scan of n = *d_n int64 values into out[0..n]; one block.  Also
-// clears out[n + 1], the tile counter the counting kernel hands work out from.
-__global__ void k_scan_i64(const int64_t* __restrict__ in, int64_t* __restrict__ out,
-                           const int32_t* __restrict__ d_n)
-{
-    __shared__ int64_t part[1024];
-    const int32_t n = *d_n;
-    const int T = blockDim.x;
-    const int32_t per = (n + T - 1) / T;
-    const int32_t b0 = threadIdx.x * per;
-    const int32_t b1 = min(n, b0 + per);
-    int64_t s = 0;
-    for (int32_t i = b0; i < b1; ++i) s += in[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < T; off <<= 1) {
-        int64_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int64_t run = part[threadIdx.x] - s;
-    for (int32_t i = b0; i < b1; ++i) {
-        out[i] = run;
-        run += in[i];
-    }
-    if (threadIdx.x == T - 1) {
-        out[n] = part[T - 1];
-        out[n + 1] = 0;   // work counter of the counting kernel
-    }
 }
 
 // ------------------------------------------------------------------ count
@@ -806,17 +829,29 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
     cudaStream_t s = ctx->stream;
     if (K_cap <= 0) return OBB_OK;
     if (K_cap > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_RANGE, "too many boxes in one call");
-    OBB_CK(ctx, ctx->prep.reserve(sizeof(BoxPrep) * K_cap, s));
-    OBB_CK(ctx, ctx->chunk_off.reserve(sizeof(int64_t) * (2 * K_cap + 2), s));
-    BoxPrep* prep = ctx->prep.as<BoxPrep>();
-    int64_t* tiles = ctx->chunk_off.as<int64_t>();
-    int64_t* off = tiles + K_cap;
-    OBB_CK(ctx, cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * K_cap, s));
-    if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K_cap, s));
-    k_prep<<<(unsigned)((K_cap + 31) / 32), 32, 0, s>>>(d_boxes, d_K, d_lats, n_lats, d_lat_of_box, prep, tiles,
-                                                          ctx->d_err);
-    note_launch(ctx);
-    k_scan_i64<<<1, 1024, 0, s>>>(tiles, off, d_K);
+    BoxPrep* prep;
+    int64_t *tiles, *off;
+    unsigned int* ticket = ctx->d_ticket;
+    if (ctx->count_scratch) {
+        // fixed scratch of a step being captured into a graph: its addresses must not move
+        const CountScratch& cs = *ctx->count_scratch;
+        if (K_cap > cs.cap) return fail(ctx, OBB_ERR_STATE, "count scratch of a captured step too small");
+        prep = cs.prep;
+        tiles = cs.tiles;
+        off = cs.tiles + cs.cap;
+        ticket = cs.ticket;
+    } else {
+        OBB_CK(ctx, ctx->prep.reserve(sizeof(BoxPrep) * K_cap, s));
+        OBB_CK(ctx, ctx->chunk_off.reserve(sizeof(int64_t) * (2 * K_cap + 2), s));
+        prep = ctx->prep.as<BoxPrep>();
+        tiles = ctx->chunk_off.as<int64_t>();
+        off = tiles + K_cap;
+    }
+    // the preparation kernel also zeroes counts and points (accumulated with atomics)
+    k_prep<<<(unsigned)((K_cap + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
+        d_boxes, d_K, d_lats, n_lats, d_lat_of_box, ctx->tile_k, prep, tiles, off,
+        reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
+        ctx->d_err);
     note_launch(ctx);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->prof) {
@@ -912,15 +947,16 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
     int64_t* off = reinterpret_cast<int64_t*>(base + kNoAllocOffsetOff);
     int32_t* dK = reinterpret_cast<int32_t*>(base + kNoAllocOffsetK);
     cudaStream_t s = ctx->stream;
-    // counts and points are accumulated with atomics: they must start at zero
-    OBB_CK(ctx, cudaMemsetAsync(d_counts, 0, sizeof(uint64_t) * K, s));
-    if (d_points) OBB_CK(ctx, cudaMemsetAsync(d_points, 0, sizeof(uint64_t) * K, s));
+    // the last 128 bytes of the count's slot hold the preparation blocks' ticket
+    // (zero at load; every launch leaves it at zero again)
+    unsigned int* ticket = reinterpret_cast<unsigned int*>(base + kNoAllocOffsetK + 128);
     k_set_i32<<<1, 1, 0, s>>>(dK, (int32_t)K);
     note_launch(ctx);
-    k_prep<<<(unsigned)((K + 31) / 32), 32, 0, s>>>(d_boxes, dK, lat->d_ref, 1, nullptr, prep, chunks,
-                                                      ctx->d_err);
-    note_launch(ctx);
-    k_scan_i64<<<1, 1024, 0, s>>>(chunks, off, dK);
+    // the preparation kernel also zeroes counts and points (accumulated with atomics)
+    k_prep<<<(unsigned)((K + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
+        d_boxes, dK, lat->d_ref, 1, nullptr, ctx->tile_k, prep, chunks, off,
+        reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
+        ctx->d_err);
     note_launch(ctx);
     k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, dK, lat->d_ref,
                                             reinterpret_cast<unsigned long long*>(d_counts),

@@ -57,6 +57,16 @@ obb_status check_device_error(obb_ctx* ctx)
     return fail(ctx, OBB_ERR_STATE, "internal capacity exceeded");
 }
 
+obb_status lattice_frame_host(const obb_lattice* lat)
+{
+    if (!lat->frame_stale) return OBB_OK;
+    obb_ctx* ctx = lat->ctx;
+    OBB_CK(ctx, cudaMemcpyAsync(&lat->frame, lat->d_frame, sizeof(LatticeFrame), cudaMemcpyDeviceToHost, ctx->stream));
+    OBB_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    lat->frame_stale = false;
+    return OBB_OK;
+}
+
 int captured_launches(obb_ctx* ctx, int64_t key0, int key1, const std::function<cudaError_t(cudaStream_t)>& fn)
 {
     auto key = std::make_pair(key0, key1);
@@ -160,8 +170,10 @@ obb_status obb_create(obb_ctx** out, int32_t device, void* stream)
     c->stream = static_cast<cudaStream_t>(stream);
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_err, sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_ticket, sizeof(unsigned int)) != cudaSuccess ||
         cudaMallocHost(&c->h_small, 64 * sizeof(int64_t)) != cudaSuccess ||
-        cudaMemset(c->d_err, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaMemset(c->d_err, 0, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(c->d_ticket, 0, sizeof(unsigned int)) != cudaSuccess) {
         obb_destroy(c);
         return OBB_ERR_CUDA;
     }
@@ -196,6 +208,7 @@ void obb_destroy(obb_ctx* ctx)
     }
     if (ctx->d_prof) cudaFree(ctx->d_prof);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_ticket) cudaFree(ctx->d_ticket);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
     delete ctx;
 }
@@ -211,58 +224,18 @@ obb_status obb_mesh_create(obb_ctx* ctx, const float* verts, int64_t n_verts, co
     if (!ctx || !out || !verts || !tris) return fail(ctx, OBB_ERR_ARG, "null argument");
     *out = nullptr;
     if (n_verts < 3 || n_tris < 4) return fail(ctx, OBB_ERR_ARG, "a closed mesh needs >= 3 vertices and >= 4 triangles");
-    if (n_tris >= (int64_t(1) << 30) || n_verts >= (int64_t(1) << 31))
+    if (n_tris >= (int64_t(1) << 29) || n_verts >= (int64_t(1) << 31))
         return fail(ctx, OBB_ERR_RANGE, "mesh too large");
-    for (int64_t i = 0; i < 3 * n_verts; ++i)
-        if (!std::isfinite(verts[i])) return fail(ctx, OBB_ERR_ARG, "non-finite vertex coordinate");
-    // undirected edges (key, triangle, edge slot), sorted: every key must appear exactly twice
-    std::vector<uint64_t> key(3 * n_tris);
-    std::vector<int64_t> who(3 * n_tris);
-    for (int64_t t = 0; t < n_tris; ++t)
-        for (int e = 0; e < 3; ++e) {
-            int64_t a = tris[3 * t + e], b = tris[3 * t + (e + 1) % 3];
-            if (a < 0 || a >= n_verts || b < 0 || b >= n_verts)
-                return fail(ctx, OBB_ERR_ARG, "triangle index out of range");
-            if (a == b) return fail(ctx, OBB_ERR_NOT_WATERTIGHT, "triangle with a repeated vertex");
-            uint64_t lo = (uint64_t)std::min(a, b), hi = (uint64_t)std::max(a, b);
-            key[3 * t + e] = (lo << 32) | hi;
-            who[3 * t + e] = 3 * t + e;
-        }
-    std::vector<int64_t> order(3 * n_tris);
-    for (int64_t i = 0; i < 3 * n_tris; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
-        return key[x] != key[y] ? key[x] < key[y] : x < y;
-    });
-    std::vector<int32_t> adj(3 * n_tris, -1);
-    for (int64_t i = 0; i < 3 * n_tris;) {
-        int64_t j = i;
-        while (j < 3 * n_tris && key[order[j]] == key[order[i]]) ++j;
-        if (j - i != 2)
-            return fail(ctx, OBB_ERR_NOT_WATERTIGHT,
-                        "edge (" + std::to_string(key[order[i]] >> 32) + ", " +
-                            std::to_string(key[order[i]] & 0xffffffffu) + ") is shared by " + std::to_string(j - i) +
-                            " triangles (need exactly 2)");
-        int64_t x = who[order[i]], y = who[order[i + 1]];
-        adj[x] = (int32_t)(y / 3);
-        adj[y] = (int32_t)(x / 3);
-        i = j;
-    }
     obb_mesh* m = new (std::nothrow) obb_mesh();
     if (!m) return fail(ctx, OBB_ERR_OOM, "host allocation");
     m->ctx = ctx;
     m->nv = n_verts;
     m->nt = n_tris;
-    cudaStream_t s = ctx->stream;
-    cudaError_t e = cudaMallocAsync((void**)&m->d_verts, sizeof(float) * 3 * n_verts, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_tris, sizeof(int32_t) * 3 * n_tris, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_adj, sizeof(int32_t) * 3 * n_tris, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_verts, verts, sizeof(float) * 3 * n_verts, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_tris, tris, sizeof(int32_t) * 3 * n_tris, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_adj, adj.data(), sizeof(int32_t) * 3 * n_tris, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // adj is a local vector
-    if (e != cudaSuccess) {
+    // upload, then validate and build the adjacency on the device
+    const obb_status st = mesh_upload(ctx, verts, n_verts, tris, n_tris, m);
+    if (st != OBB_OK) {
         obb_mesh_free(m);
-        return cuda_fail(ctx, e, "mesh upload");
+        return st;
     }
     *out = m;
     return OBB_OK;
@@ -340,6 +313,7 @@ obb_status obb_lattice_desc(const obb_lattice* lat, double lo[3], double h[3], i
                             const uint64_t** d_words, const int32_t** d_fixed)
 {
     if (!lat) return OBB_ERR_ARG;
+    if (lo || h) OBB_TRY(obbv::lattice_frame_host(lat));
     for (int b = 0; b < 3; ++b) {
         if (lo) lo[b] = lat->frame.lo[b];
         if (h) h[b] = lat->frame.h[b];
@@ -413,6 +387,64 @@ obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qb
                               uint64_t* counts, uint64_t* points, int32_t on_device)
 {
     return outer_volume_impl(ctx, lat, nullptr, boxes, K, counts, points, on_device);
+}
+
+obb_status obb_set_counting_tile(obb_ctx* ctx, int32_t tile_k)
+{
+    if (!ctx) return OBB_ERR_ARG;
+    if (tile_k < 1 || tile_k > 128) return fail(ctx, OBB_ERR_ARG, "tile_k must be in [1, 128]");
+    if (tile_k != ctx->tile_k) ++ctx->tile_gen;
+    ctx->tile_k = tile_k;
+    return OBB_OK;
+}
+
+obb_status obb_tune_counting(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* qboxes, int64_t K,
+                             int32_t on_device, int32_t* tile_k, float* ms)
+{
+    if (!ctx || !lat || !qboxes || K <= 0) return fail(ctx, OBB_ERR_ARG, "null argument or empty batch");
+    if (K > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_ARG, "K out of range");
+    cudaStream_t s = ctx->stream;
+    HostTmp hb(ctx);
+    const obb_qbox* db;
+    OBB_TRY(to_device(ctx, qboxes, (size_t)K, on_device, hb, &db));
+    OBB_CK(ctx, ctx->cscratch.reserve(sizeof(uint64_t) * K, s));
+    OBB_CK(ctx, ctx->kdev.reserve(sizeof(int32_t), s));
+    int32_t* dK = ctx->kdev.as<int32_t>();
+    OBB_TRY(set_device_int(ctx, dK, (int32_t)K));
+    const int32_t cand[4] = {8, 16, 32, 64};
+    float t[4] = {0, 0, 0, 0};
+    cudaEvent_t e0, e1;
+    OBB_CK(ctx, cudaEventCreate(&e0));
+    OBB_CK(ctx, cudaEventCreate(&e1));
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    obb_status rc = OBB_OK;
+    for (int i = 0; i < 4 && rc == OBB_OK; ++i) {
+        ctx->tile_k = cand[i];
+        rc = count_boxes(ctx, lat, db, dK, K, ctx->cscratch.as<uint64_t>(), nullptr);   // warm-up
+        if (rc != OBB_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && rc == OBB_OK; ++r)
+            rc = count_boxes(ctx, lat, db, dK, K, ctx->cscratch.as<uint64_t>(), nullptr);
+        cudaEventRecord(e1, s);
+        const cudaError_t ee = cudaEventSynchronize(e1);
+        if (ee != cudaSuccess) rc = cuda_fail(ctx, ee, "autotune timing");
+        else cudaEventElapsedTime(&t[i], e0, e1);
+        t[i] /= 3.0f;
+    }
+    ctx->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != OBB_OK) return rc;
+    int best = 0;
+    for (int i = 1; i < 4; ++i)
+        if (t[i] < t[best]) best = i;
+    ctx->tile_k = cand[best];
+    ++ctx->tile_gen;
+    if (tile_k) *tile_k = cand[best];
+    if (ms)
+        for (int i = 0; i < 4; ++i) ms[i] = t[i];
+    return check_device_error(ctx);
 }
 
 obb_status obb_directional_outer_volume(obb_ctx* ctx, const obb_mesh* mesh, const obb_box* boxes, int64_t K,
@@ -640,6 +672,7 @@ obb_status obb_tree_score(obb_ctx* ctx, const obb_tree* tree, double* points, do
     }
     if (points) *points = acc;
     if (volume) {
+        OBB_TRY(obbv::lattice_frame_host(tree->lat));
         const LatticeFrame& f = tree->lat->frame;
         *volume = acc * f.h[0] * f.h[1] * f.h[2];
     }

@@ -208,6 +208,26 @@ def test_mesh_validation(ctx):
     with pytest.raises(PK.ObbError) as e:
         ctx.build_occupancy(mesh, 4096)
     assert e.value.code == -3
+    # checks made on the device while the mesh is uploaded
+    bad = m.tris.copy()
+    bad[3, 1] = 99
+    with pytest.raises(PK.ObbError) as e:
+        ctx.mesh_create(m.verts, bad)
+    assert e.value.code == -1 and "out of range" in str(e.value)
+    V = m.verts.copy()
+    V[2, 1] = np.nan
+    with pytest.raises(PK.ObbError) as e:
+        ctx.mesh_create(V, m.tris)
+    assert e.value.code == -1 and "non-finite" in str(e.value)
+    bad = m.tris.copy()
+    bad[5, 2] = bad[5, 0]
+    with pytest.raises(PK.ObbError) as e:
+        ctx.mesh_create(m.verts, bad)
+    assert e.value.code == -2 and "repeated" in str(e.value)
+    three = np.concatenate([m.tris, m.tris[:1]])          # one edge set shared by three triangles
+    with pytest.raises(PK.ObbError) as e:
+        ctx.mesh_create(m.verts, three)
+    assert e.value.code == -2 and "shared by 3" in str(e.value)
 
 
 # -------------------------------------------------------------------- Lloyd
