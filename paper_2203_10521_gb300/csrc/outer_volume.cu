@@ -42,6 +42,14 @@
 #ifndef OBB_POPC_ILP
 #define OBB_POPC_ILP 1
 #endif
+// OBB_INTERIOR: a row loop without clamps for full-height tiles of boxes inside the lattice
+#ifndef OBB_INTERIOR
+#define OBB_INTERIOR 1
+#endif
+// OBB_DERIVED_QB: in that loop, derive each slab's upper quotient from its lower one
+#ifndef OBB_DERIVED_QB
+#define OBB_DERIVED_QB 1
+#endif
 // OBB_FAST_DDA: a row loop without per-slab dispatch for boxes whose three slabs all step by DDA
 #ifndef OBB_FAST_DDA
 #define OBB_FAST_DDA 1
@@ -261,6 +269,24 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
                 best = l;
             }
         }
+    }
+    // interior box: its whole index rectangle lies in the lattice, so no row
+    // and no x-interval needs clamping to [0, N)
+    if (p.nj > 0 && p.i0 >= 0 && p.i0 + p.span <= N - 1 && p.j0 >= 0 && p.j0 + p.nj <= N && p.k0 >= 0 &&
+        p.k0 + p.nk <= N)
+        p.mode |= 1 << 8;
+    // every quotient of every slab stays within 2^29 of i0 over the box's
+    // rectangle: no saturation, so a slab's upper quotient follows from its
+    // lower one (see k_count)
+    if (p.nj > 0 && (p.mode & 0x3f) == 0x15) {
+        bool small = true;
+        for (int a = 0; a < 3; ++a) {
+            const double reach = fabs((double)p.Lq[a]) + fabs((double)p.Hq[a]) +
+                                 fabs((double)p.n[3 * a + 1]) * (fabs((double)p.j0) + p.nj) +
+                                 fabs((double)p.n[3 * a + 2]) * (fabs((double)p.k0) + p.nk);
+            small &= reach / p.dd[a] + fabs((double)p.i0) + p.span + 2.0 < 536870912.0;
+        }
+        if (small) p.mode |= 1 << 9;
     }
     p.lwj = best;
     const int32_t wj = 1 << best, wk = 32 >> best;
@@ -615,7 +641,88 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         uint32_t empty = 0, inbox = 0;
         const bool jin = j >= 0 && j < N;
 #if OBB_FAST_DDA
-        if (mode == 0x15) {
+#if OBB_INTERIOR && OBB_DERIVED_QB
+        if ((mode & 0x3ff) == 0x315 && (tk + 1) * wk * tkr <= p.nk) {
+            // as below, and no quotient saturates: with D = Hq - Lq = Dq dd + Dr,
+            // the upper quotient is qa + Dq - (ra < dd - 1 - Dr), so only the
+            // lower one steps
+            int32_t Dq[3], Tq[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int64_t q;
+                int32_t r;
+                floordiv_exact(p.Hq[a] - p.Lq[a], dd[a], p.rcp[a], q, r);
+                Dq[a] = (int32_t)q;
+                Tq[a] = dd[a] - 1 - r;
+            }
+            const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
+            const int64_t rstride = (int64_t)wk * N * W;
+            const int32_t spanl = jvalid ? span : -1;
+#pragma unroll kCountUnroll
+            for (int r = 0; r < tkr; ++r, rowp += rstride) {
+                const int32_t lo = max(max(qa[0], qa[1]), max(qa[2], 0));
+                const int32_t b0 = qa[0] + Dq[0] - (ra[0] < Tq[0]);
+                const int32_t b1 = qa[1] + Dq[1] - (ra[1] < Tq[1]);
+                const int32_t b2 = qa[2] + Dq[2] - (ra[2] < Tq[2]);
+                const int32_t hi = min(min(b0, b1), min(b2, spanl));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    qa[a] += qs[a];
+                    ra[a] += rs[a];
+                    if (ra[a] >= dd[a]) {
+                        ra[a] -= dd[a];
+                        qa[a] += 1;
+                    }
+                }
+                if (lo <= hi) {
+                    const int32_t a = i0 + lo, e = i0 + hi;
+                    const uint32_t len = (uint32_t)(hi - lo + 1);
+                    empty += len - popc_range(rowp, a, e);
+                    inbox += len;
+                    my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                    my_rows += 1;
+                }
+            }
+        } else
+#endif
+#if OBB_INTERIOR
+        if ((mode & 0x1ff) == 0x115 && (tk + 1) * wk * tkr <= p.nk) {
+            // an interior box's full-height tile: every row is in the lattice
+            // and so is every x-interval; an idle lane gets an empty range
+            const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
+            const int64_t rstride = (int64_t)wk * N * W;
+            const int32_t spanl = jvalid ? span : -1;
+#pragma unroll kCountUnroll
+            for (int r = 0; r < tkr; ++r, rowp += rstride) {
+                const int32_t lo = max(max(qa[0], qa[1]), max(qa[2], 0));
+                const int32_t hi = min(min(qb[0], qb[1]), min(qb[2], spanl));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    qa[a] += qs[a];
+                    ra[a] += rs[a];
+                    if (ra[a] >= dd[a]) {
+                        ra[a] -= dd[a];
+                        qa[a] += 1;
+                    }
+                    qb[a] += qs[a];
+                    rb[a] += rs[a];
+                    if (rb[a] >= dd[a]) {
+                        rb[a] -= dd[a];
+                        qb[a] += 1;
+                    }
+                }
+                if (lo <= hi) {
+                    const int32_t a = i0 + lo, e = i0 + hi;
+                    const uint32_t len = (uint32_t)(hi - lo + 1);
+                    empty += len - popc_range(rowp, a, e);
+                    inbox += len;
+                    my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                    my_rows += 1;
+                }
+            }
+        } else
+#endif
+        if ((mode & 0xff) == 0x15) {
             // all three slabs step by 32-bit DDA (any rotated box): no per-row
             // slab dispatch, and the row pointer advances by a fixed stride
             const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
