@@ -284,7 +284,7 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
             const double reach = fabs((double)p.Lq[a]) + fabs((double)p.Hq[a]) +
                                  fabs((double)p.n[3 * a + 1]) * (fabs((double)p.j0) + p.nj) +
                                  fabs((double)p.n[3 * a + 2]) * (fabs((double)p.k0) + p.nk);
-            small &= reach / p.dd[a] + fabs((double)p.i0) + p.span + 2.0 < 536870912.0;
+            small &= reach < (536870912.0 - fabs((double)p.i0) - p.span - 2.0) * p.dd[a];   // no FP64 divide
         }
         if (small) p.mode |= 1 << 9;
     }
@@ -337,19 +337,20 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
     __syncthreads();
     if (!last) return;
     // exclusive scan of tiles[0..K) by the last block (one warp): chunks of
-    // 4 x 32 consecutive values, a thread's four in registers, a warp scan of
-    // the thread sums, and a running carry
+    // 8 x 32 consecutive values, a thread's eight in registers (eight loads in
+    // flight), a warp scan of the thread sums, and a running carry
     const int lane = threadIdx.x & 31;
     int64_t carry = 0;
-    for (int32_t base = 0; base < K; base += 128) {
-        int64_t v[4];
+    for (int32_t base = 0; base < K; base += 256) {
+        int64_t v[8];
         int64_t sum = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int32_t i = base + 4 * lane + q;
+        for (int q = 0; q < 8; ++q) {
+            const int32_t i = base + 8 * lane + q;
             v[q] = i < K ? tiles[i] : 0;
-            sum += v[q];
         }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sum += v[q];
         int64_t x = sum;
         for (int o = 1; o < 32; o <<= 1) {
             const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -357,8 +358,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
         }
         int64_t run = carry + x - sum;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int32_t i = base + 4 * lane + q;
+        for (int q = 0; q < 8; ++q) {
+            const int32_t i = base + 8 * lane + q;
             if (i < K) off[i] = run;
             run += v[q];
         }
