@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-topk", type=int, default=3,
+                    help="candidates (and rotation probes) per cluster the surrogate keeps for exact counting")
     ap.add_argument("--lloyd-iters", type=int, default=10,
                     help="Lloyd iterations timed for the plain vs surrogate comparison")
     return ap.parse_args()
@@ -348,7 +350,7 @@ def main():
     for mode in modes:
         lay = ctx.layer_init(lat, child, parent)
         if mode == "surrogate":
-            ctx.layer_set_surrogate(lay, mlp, 3)
+            ctx.layer_set_surrogate(lay, mlp, args.surrogate_topk)
         flush.fill_(1)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -370,6 +372,7 @@ def main():
     if "surrogate" in lloyd:
         a, b = lloyd["plain"]["final_total_obv"], lloyd["surrogate"]["final_total_obv"]
         lloyd["final_obv_rel_diff"] = (b - a) / a
+        lloyd["surrogate_topk"] = args.surrogate_topk
     if mlp is not None:
         mlp.free()
 
