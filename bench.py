@@ -357,9 +357,11 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         evals = 0
+        torch.cuda.nvtx.range_push("lloyd_" + mode)
         for _ in range(args.lloyd_iters):
             st = ctx.lloyd_step(lay, rounds=16, refit=2, descent_steps=2, graph=(mode == "plain_graph"))
             evals += st["box_evals"]
+        torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize()
         lms = e0.elapsed_time(e1)

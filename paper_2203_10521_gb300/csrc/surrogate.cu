@@ -160,12 +160,26 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const float* 
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     float acc[4][4] = {};
     for (int k0 = 0; k0 < K; k0 += 16) {
+        // A is read along its contiguous index (k when sAk = 1, else m) and B
+        // along n, so the loads coalesce; the padded rows of the shared tiles
+        // keep the transposed stores free of bank conflicts
+        if (sAk == 1) {
+            for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+                const int mm = i >> 4, kk = i & 15;
+                const int m = m0 + mm, k = k0 + kk;
+                As[kk][mm] = (m < M && k < K) ? A[m * sAm + k] : 0.f;
+            }
+        } else {
+            for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+                const int kk = i >> 6, mm = i & 63;
+                const int m = m0 + mm, k = k0 + kk;
+                As[kk][mm] = (m < M && k < K) ? A[m * sAm + k * sAk] : 0.f;
+            }
+        }
         for (int i = threadIdx.x; i < 16 * 64; i += 256) {
-            const int kk = i >> 6, mm = i & 63;
-            const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? A[m * sAm + k * sAk] : 0.f;
-            const int n = n0 + mm;
-            Bs[kk][mm] = (n < N && k < K) ? (float)B[k * sBk + n * sBn] : 0.f;
+            const int kk = i >> 6, nn = i & 63;
+            const int n = n0 + nn, k = k0 + kk;
+            Bs[kk][nn] = (n < N && k < K) ? (float)B[k * sBk + n * sBn] : 0.f;
         }
         __syncthreads();
 #pragma unroll
