@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--surrogate-topk", type=int, default=3,
+    ap.add_argument("--surrogate-topk", type=int, default=5,
                     help="candidates (and rotation probes) per cluster the surrogate keeps for exact counting")
     ap.add_argument("--lloyd-iters", type=int, default=10,
                     help="Lloyd iterations timed for the plain vs surrogate comparison")
