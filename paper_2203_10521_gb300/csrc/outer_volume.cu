@@ -38,6 +38,10 @@
 #ifndef OBB_COUNT_MINB
 #define OBB_COUNT_MINB 4
 #endif
+// OBB_POPC64: count a row in 64-bit words with branch-free end masks
+#ifndef OBB_POPC64
+#define OBB_POPC64 1
+#endif
 // OBB_POPC_ILP: load a row's chunks up front / in groups of four
 #ifndef OBB_POPC_ILP
 #define OBB_POPC_ILP 1
@@ -459,7 +463,23 @@ __device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64
 }
 
 // popcount of the occupied bits i in [a, e] of one row (0 <= a <= e < N)
-#if OBB_POPC_ILP
+#if OBB_POPC64
+// 64-bit words: the first and last word carry the masks (merged without a
+// branch when they are the same word), interior words count whole.
+__device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
+{
+    const int32_t wa = a >> 6, we = e >> 6;
+    const uint64_t first = __ldg(row + wa);
+    const uint64_t last = __ldg(row + we);
+    uint64_t mlo = ~0ull << (a & 63);
+    const uint64_t mhi = ~0ull >> (63 - (e & 63));
+    uint32_t cnt = 0;
+    for (int32_t w = wa + 1; w < we; ++w) cnt += __popcll(__ldg(row + w));
+    const bool one = wa == we;
+    mlo = one ? (mlo & mhi) : mlo;
+    return cnt + __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
+}
+#elif OBB_POPC_ILP
 // The first and last 128-bit chunks are loaded up front and the interior in
 // groups of four independent loads, so a long row waits for one or two L2
 // round trips instead of one per chunk.
