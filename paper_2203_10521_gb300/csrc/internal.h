@@ -65,6 +65,8 @@ struct BoxPrep {
     int32_t tk;              // rows one lane visits per tile (tiles are wj x wk * tk rows)
     float rcp[3];            // 1 / dd (seed of the exact initial division)
     int64_t Lq[3], Hq[3];    // ceil(lo / 256), floor(hi / 256)
+    uint64_t fmul[3];        // floor((2^64 - 1) / dd): remainder -> 32-bit fraction
+    int64_t fstep[3];        // floor(step * 2^32), step = qstep + rstep / dd (32.32 fixed point)
     // Separating axes of the box's shadow on the (j, k) plane: the normals of
     // its three projected edge directions, and the shadow's extent along each,
     // widened by two rows.  A tile whose rectangle lies outside one of these

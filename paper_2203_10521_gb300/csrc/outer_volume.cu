@@ -38,6 +38,10 @@
 #ifndef OBB_COUNT_MINB
 #define OBB_COUNT_MINB 4
 #endif
+// OBB_FIXED_DDA: step DDA bounds as 32.32 fixed-point values (two adds per bound and row)
+#ifndef OBB_FIXED_DDA
+#define OBB_FIXED_DDA 1
+#endif
 // OBB_POPC64: count a row in 64-bit words with branch-free end masks
 #ifndef OBB_POPC64
 #define OBB_POPC64 1
@@ -160,6 +164,8 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
         p.rcp[a] = d != 0 ? 1.0f / (float)p.dd[a] : 0.0f;
         p.qstep[a] = 0;
         p.rstep[a] = 0;
+        p.fmul[a] = 0;
+        p.fstep[a] = 0;
         // slab kind: 0 = n_a0 == 0 (a band in (y, z)), 1 = quotient DDA in 32 bits,
         // 2 = quotient DDA in 64 bits (|n_a0| < 32: the slab is almost parallel to x)
         const int kind = d == 0 ? 0 : (p.dd[a] >= 32 ? 1 : 2);
@@ -304,7 +310,22 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
             if (qs * p.dd[a] > delta) --qs;   // floor
             p.qstep[a] = qs;
             p.rstep[a] = delta - qs * p.dd[a];
+            // the same step in 32.32 fixed point, rounded down (exact division:
+            // rstep < dd <= 2^24, so rstep * 2^32 < 2^56)
+            p.fmul[a] = ~0ull / (uint64_t)p.dd[a];
+            p.fstep[a] = (int64_t)qs * 4294967296LL + (int64_t)(((uint64_t)p.rstep[a] << 32) / (uint64_t)p.dd[a]);
         }
+    // A quotient saturated at +-2^30 must stay outside [0, span] for a whole
+    // tile: its tk - 1 steps of at most |qstep| + 1 each stay below 2^29.  With
+    // |qstep| <= 2^24 every tk <= 32 qualifies; taller tiles are cut for steep
+    // slabs.
+    {
+        int64_t smax = 0;
+        for (int a = 0; a < 3; ++a)
+            if (((p.mode >> (2 * a)) & 3) == 1) smax = max(smax, (int64_t)abs(p.qstep[a]) + 1);
+        if (smax > 0 && (int64_t)(p.tk - 1) * smax >= (int64_t(1) << 29))
+            p.tk = (int32_t)max((int64_t)1, min((int64_t)p.tk, (int64_t(1) << 29) / smax));
+    }
     prep[k] = p;
     tiles[k] = p.nj > 0 ? (int64_t)p.ntj * ((p.nk + wk * p.tk - 1) / (wk * p.tk)) : 0;
 }
@@ -427,6 +448,28 @@ __device__ __forceinline__ void floordiv_exact(int64_t x, int32_t d, float rcp, 
     }
     q = q0;
     r = (int32_t)rem;
+}
+
+// 32.32 fixed-point DDA.  A slab bound floor(v), v = q + r / dd, is carried as
+// A = q 2^32 + floor(r M / 2^32) + kFixBias with M = floor((2^64 - 1) / dd),
+// and steps by floor(s 2^32) per row (s the exact rational step).  The seed is
+// at most 1 + 2^-8 units (of 2^-32) below v 2^32 and never above it; each
+// step loses less than one unit.  After r <= 127 steps the error lies in
+// (kFixBias - 1 - 2^-8 - r, kFixBias] = (1.99, 130]: positive, and below
+// 2^32 / dd >= 256, the distance from the largest fraction (dd - 1) / dd to
+// the next integer.  So A >> 32 is exactly floor(v) on every row of a tile
+// of at most 128 rows (the most obb_set_counting_tile allows).
+constexpr int64_t kFixBias = 130;
+
+__device__ __forceinline__ int64_t fixed_frac(int32_t r, uint64_t M)   // 0 <= r < 2^24
+{
+    const uint32_t ru = (uint32_t)r;
+    return (int64_t)((uint64_t)ru * (uint32_t)(M >> 32) + __umulhi(ru, (uint32_t)M));
+}
+
+__device__ __forceinline__ int32_t fixed_int(int64_t A)
+{
+    return (int32_t)(A >> 32);
 }
 
 // Intersect [lo, hi] with { i : L <= d i + c <= H } exactly (d != 0): float
@@ -661,7 +704,73 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         }
         uint32_t empty = 0, inbox = 0;
         const bool jin = j >= 0 && j < N;
-#if OBB_FAST_DDA
+#if OBB_FAST_DDA && OBB_FIXED_DDA
+        if ((mode & 0xff) == 0x15) {
+            // all three slabs step by DDA (any rotated box): each of the six
+            // bounds is a 32.32 fixed-point value whose integer part is the
+            // quotient, so a bound costs one 64-bit add per row
+            int64_t Al[3], Ah[3], Bs[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const uint64_t M = p.fmul[a];
+                Al[a] = (int64_t)qa[a] * 4294967296LL + fixed_frac(ra[a], M) + kFixBias;
+                Ah[a] = (int64_t)qb[a] * 4294967296LL + fixed_frac(rb[a], M) + kFixBias;
+                Bs[a] = p.fstep[a];
+            }
+            const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
+            const int64_t rstride = (int64_t)wk * N * W;
+            if ((mode & 0x100) && (tk + 1) * wk * tkr <= p.nk) {
+                // an interior box's full-height tile: every row is in the
+                // lattice and so is every x-interval; an idle lane gets an
+                // empty range
+                const int32_t spanl = jvalid ? span : -1;
+#pragma unroll kCountUnroll
+                for (int r = 0; r < tkr; ++r, rowp += rstride) {
+                    const int32_t lo = max(max(fixed_int(Al[0]), fixed_int(Al[1])), max(fixed_int(Al[2]), 0));
+                    const int32_t hi = min(min(fixed_int(Ah[0]), fixed_int(Ah[1])), min(fixed_int(Ah[2]), spanl));
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Al[a] += Bs[a];
+                        Ah[a] += Bs[a];
+                    }
+                    if (lo <= hi) {
+                        const int32_t a = i0 + lo, e = i0 + hi;
+                        const uint32_t len = (uint32_t)(hi - lo + 1);
+                        empty += len - popc_range(rowp, a, e);
+                        inbox += len;
+                        my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                        my_rows += 1;
+                    }
+                }
+            } else {
+                int32_t k = kb;
+#pragma unroll kCountUnroll
+                for (int r = 0; r < tkr; ++r, k += wk, rowp += rstride) {
+                    const int32_t lo = max(max(fixed_int(Al[0]), fixed_int(Al[1])), max(fixed_int(Al[2]), 0));
+                    const int32_t hi = min(min(fixed_int(Ah[0]), fixed_int(Ah[1])), min(fixed_int(Ah[2]), span));
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Al[a] += Bs[a];
+                        Ah[a] += Bs[a];
+                    }
+                    if (jvalid && k < kend && lo <= hi) {
+                        const uint32_t len = (uint32_t)(hi - lo + 1);
+                        uint32_t occ = 0;
+                        if (jin && (uint32_t)k < (uint32_t)N) {
+                            const int32_t a = max(i0 + lo, 0), e = min(i0 + hi, N - 1);
+                            if (a <= e) {
+                                occ = popc_range(rowp, a, e);
+                                my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                            }
+                        }
+                        empty += len - occ;
+                        inbox += len;
+                        my_rows += 1;
+                    }
+                }
+            }
+        } else
+#elif OBB_FAST_DDA
 #if OBB_INTERIOR && OBB_DERIVED_QB
         if ((mode & 0x3ff) == 0x315 && (tk + 1) * wk * tkr <= p.nk) {
             // as below, and no quotient saturates: with D = Hq - Lq = Dq dd + Dr,

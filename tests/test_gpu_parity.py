@@ -183,6 +183,42 @@ def test_outer_volume_edge_cases(ctx, torus_setup):
     assert np.array_equal(ctx.outer_volume(lat, boxes), ref)
 
 
+def _steep_qboxes():
+    """Boxes thousands of rows tall whose third slab is almost parallel to x
+    (|n_20| of a few dozen against n_22 = +-2^24): its quotient bounds start far
+    beyond +-2^30 and move by ~2^24 per row of a one-lane-wide tile."""
+    import paper_2203_10521_gb300 as PK
+    big = 1 << 24
+    kl, kh = -3000, 5000
+    rows = []
+    for s0, s2, jrow in [(40, 1, 30), (-40, 1, 12), (33, -1, 47), (-127, -1, 5)]:
+        q = np.zeros((), PK.QBOX_DTYPE)
+        q["n"] = [big, 0, 0, 50, big, 0, s0, 0, s2 * big]
+        z = sorted([s2 * big * kl, s2 * big * kh])
+        lq = [10 * big, jrow * big, z[0] - 5000]
+        hq = [20 * big, jrow * big + 2000, z[1] + 5000]
+        q["b"] = [v for a in range(3) for v in (256 * lq[a], 256 * hq[a])]
+        rows.append(q)
+    return np.array(rows, dtype=PK.QBOX_DTYPE)
+
+
+def test_outer_volume_steep_slabs_tall_tiles(ctx, torus_setup):
+    """Exact at every tile height, up to 128 rows per lane: a saturated quotient
+    must not drift back into the box's x-range within a tile."""
+    m, mesh, lat, P = torus_setup
+    q = _steep_qboxes()
+    ref, tot = O.outer_volume(P.occ, q["n"], q["b"])
+    assert (tot > 50000).all()
+    try:
+        for tk in (32, 64, 128, 7):
+            ctx.set_counting_tile(tk)
+            cnt, pts = ctx.outer_volume_q(lat, q, want_points=True)
+            assert np.array_equal(cnt, ref), tk
+            assert np.array_equal(pts, tot), tk
+    finally:
+        ctx.set_counting_tile(32)
+
+
 def test_outer_volume_config_200k_sampled(ctx):
     """512^3 lattice of the 200k-triangle mesh: leaf-sized boxes, exact."""
     m = M.sdf_union_200k()
