@@ -73,6 +73,11 @@ struct BoxPrep {
     // bands holds no row of the box.
     float sat_nu[3][2];
     float sat_lo[3], sat_hi[3];
+    // The same bands solved for k: rows k - k0 of column j lie within
+    // [kc_lo[a] + kc_s[a] (j - j0), kc_hi[a] + kc_s[a] (j - j0)] for every a
+    // (widened by a rounding margin; an unconstraining band has kc_s = 0 and
+    // infinite bounds).
+    float kc_s[3], kc_lo[3], kc_hi[3];
 };
 
 // One lattice as the counting kernel sees it (a table of these lets one launch

@@ -42,6 +42,15 @@
 #ifndef OBB_FIXED_DDA
 #define OBB_FIXED_DDA 1
 #endif
+// OBB_ROW_CLIP: an all-DDA tile visits only the rows (warp-uniform) that can
+// meet the box's shadow
+#ifndef OBB_ROW_CLIP
+#define OBB_ROW_CLIP 1
+#endif
+// OBB_INT_DIV: exact divisions of the counting kernel by integer reciprocal
+#ifndef OBB_INT_DIV
+#define OBB_INT_DIV 1
+#endif
 // OBB_POPC64: count a row in 64-bit words with branch-free end masks
 #ifndef OBB_POPC64
 #define OBB_POPC64 1
@@ -179,6 +188,9 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
         p.sat_nu[a][0] = p.sat_nu[a][1] = 0.0f;
         p.sat_lo[a] = -1.0f;
         p.sat_hi[a] = 1.0f;
+        p.kc_s[a] = 0.0f;
+        p.kc_lo[a] = -1e30f;
+        p.kc_hi[a] = 1e30f;
     }
     if (!empty) {
         double M[9];
@@ -259,6 +271,19 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
                     p.sat_nu[a][1] = nk_;
                     p.sat_lo[a] = lo - 2.0f;
                     p.sat_hi[a] = hi + 2.0f;
+                    // solved for k relative to (j0, k0), where the band is not
+                    // steep in k (|dk/dj| <= 64): FP64 here, FP32 in the kernel,
+                    // with one row plus a relative margin far above FP32 rounding
+                    if (fabsf(nk_) > 0.0f && fabsf(nj_) <= 64.0f * fabsf(nk_)) {
+                        const double v = (double)nk_, sl = -(double)nj_ / v;
+                        const double b0 = (double)(nk_ > 0.0f ? p.sat_lo[a] : p.sat_hi[a]) / v;
+                        const double b1 = (double)(nk_ > 0.0f ? p.sat_hi[a] : p.sat_lo[a]) / v;
+                        const double c0 = b0 + sl * p.j0 - p.k0, c1 = b1 + sl * p.j0 - p.k0;
+                        const double m = 1.0 + 1e-5 * (fabs(sl) * p.nj + fabs(c0) + fabs(c1));
+                        p.kc_s[a] = (float)sl;
+                        p.kc_lo[a] = (float)(c0 - m);
+                        p.kc_hi[a] = (float)(c1 + m);
+                    }
                 }
             }
         }
@@ -431,7 +456,7 @@ __global__ void k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__
 
 // Exact floor division of a signed int64 by 0 < d < 2^31: a float seed, one
 // float refinement of the remainder, then at most a couple of unit fixes.
-__device__ __forceinline__ void floordiv_exact(int64_t x, int32_t d, float rcp, int64_t& q, int32_t& r)
+[[maybe_unused]] __device__ __forceinline__ void floordiv_exact(int64_t x, int32_t d, float rcp, int64_t& q, int32_t& r)
 {
     int64_t q0 = __float2ll_rd(__ll2float_rn(x) * rcp);
     int64_t rem = x - q0 * (int64_t)d;
@@ -472,10 +497,48 @@ __device__ __forceinline__ int32_t fixed_int(int64_t A)
     return (int32_t)(A >> 32);
 }
 
+// floor(x / d) and its remainder in [0, d), for 0 < d <= 2^24 and |x| < 2^62,
+// by the integer reciprocal M = floor((2^64 - 1) / d): the high half of y M
+// is at most one below floor(y / d) (M d > 2^64 - d - 1, y < 2^63), so one
+// correction makes it exact.  All integer: 64-bit int <-> float conversions
+// issue on the FP64 pipe, a small fraction of the integer rate on this GPU.
+__device__ __forceinline__ void floordiv_rcp(int64_t x, int32_t d, uint64_t M, int64_t& q, int32_t& r)
+{
+    const bool neg = x < 0;
+    const uint64_t y = neg ? (uint64_t)(-x) + (uint64_t)(d - 1) : (uint64_t)x;   // x < 0: floor(x/d) = -floor(y/d)
+    uint64_t qq = __umul64hi(y, M);
+    uint64_t rr = y - qq * (uint64_t)d;
+    if (rr >= (uint64_t)d) {
+        rr -= (uint64_t)d;
+        ++qq;
+    }
+    q = neg ? -(int64_t)qq : (int64_t)qq;
+    r = neg ? d - 1 - (int32_t)rr : (int32_t)rr;
+}
+
+// Intersect [lo, hi] with { i : L <= d i + c <= H } exactly (d != 0), by
+// integer-reciprocal division (M = floor((2^64 - 1) / |d|)).  Used per row for
+// slabs almost parallel to x.
+__device__ __forceinline__ void clip_slab_rcp(int32_t d, uint64_t M, int64_t c, int64_t L, int64_t H, int32_t& lo,
+                                              int32_t& hi)
+{
+    const int32_t dd = d > 0 ? d : -d;
+    const int64_t A = d > 0 ? L - c : c - H;
+    const int64_t B = d > 0 ? H - c : c - L;
+    int64_t qn, qb;
+    int32_t rem;
+    floordiv_rcp(-A, dd, M, qn, rem);   // ceil(A / dd) = -floor(-A / dd)
+    floordiv_rcp(B, dd, M, qb, rem);
+    const int64_t g = min(max(-qn, (int64_t)lo), (int64_t)hi + 1);
+    const int64_t u = max(min(qb, (int64_t)hi), (int64_t)lo - 1);
+    lo = (int32_t)g;
+    hi = (int32_t)u;
+}
+
 // Intersect [lo, hi] with { i : L <= d i + c <= H } exactly (d != 0): float
 // estimates of the two quotients, clamped to [lo - 1, hi + 1] and corrected
 // with exact int64 products.  Used per row for slabs almost parallel to x.
-__device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64_t L, int64_t H, int32_t& lo,
+[[maybe_unused]] __device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64_t L, int64_t H, int32_t& lo,
                                           int32_t& hi)
 {
     int64_t A, B, dd;
@@ -677,6 +740,46 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         const int32_t tkr = p.tk;
         const int32_t kb = p.k0 + tk * (wk * tkr) + (lane >> lwj);   // this lane's first row
         const int32_t kend = p.k0 + p.nk;
+        // rows r0..r1 (warp-uniform) of the tile's tkr are visited
+        int32_t r0 = 0, r1 = tkr - 1;
+#if OBB_ROW_CLIP && OBB_FIXED_DDA && OBB_FAST_DDA
+        if ((mode & 0xff) == 0x15) {
+            // each lane's column meets the shadow in a k-range (the separating
+            // bands solved for k); the warp visits the union of its lanes'
+            // ranges, which skips the empty ends of a tile the shadow crosses
+            const float jr = (float)(j - p.j0);
+            float klo = -1e30f, khi = 1e30f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                klo = fmaxf(klo, fmaf(p.kc_s[a], jr, p.kc_lo[a]));
+                khi = fminf(khi, fmaf(p.kc_s[a], jr, p.kc_hi[a]));
+            }
+            int32_t rl = tkr, rh = -1;
+            if (jvalid && klo <= khi) {
+                const int32_t lwk = 5 - lwj;   // wk = 2^lwk
+                const int32_t kbr = kb - p.k0;
+                const int32_t kl = (int32_t)floorf(fmaxf(klo, -1e9f));
+                const int32_t kh = (int32_t)ceilf(fminf(khi, 1e9f));
+                rl = max(0, -((kbr - kl) >> lwk));    // first r with kb + r wk >= kl
+                rh = min(tkr - 1, (kh - kbr) >> lwk);  // last r with kb + r wk <= kh
+                if (rl > rh) {
+                    rl = tkr;
+                    rh = -1;
+                }
+            }
+            r0 = __reduce_min_sync(0xffffffffu, rl);
+            r1 = __reduce_max_sync(0xffffffffu, rh);
+            if (r0 > r1) {
+                if (++tj == p.ntj) {
+                    tj = 0;
+                    ++tk;
+                }
+                ++c;
+                continue;
+            }
+        }
+#endif
+        const int32_t kb0 = kb + r0 * wk;   // the first row this lane visits
         const int32_t i0 = p.i0, span = p.span;
         // Kind-1 slabs carry exact quotient bounds relative to i0 in 32 bits,
         // saturated at +-2^30: a bound that far out moves less than 2^29 within a
@@ -691,12 +794,17 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 dd[a] = p.dd[a];
                 rs[a] = p.rstep[a];
                 qs[a] = p.qstep[a];
-                const int64_t cc = (int64_t)p.n[3 * a + 1] * j + (int64_t)p.n[3 * a + 2] * kb;
+                const int64_t cc = (int64_t)p.n[3 * a + 1] * j + (int64_t)p.n[3 * a + 2] * kb0;
                 const int64_t xlo = p.n[3 * a] > 0 ? p.Lq[a] - cc : cc - p.Hq[a];
                 const int64_t xhi = p.n[3 * a] > 0 ? p.Hq[a] - cc : cc - p.Lq[a];
                 int64_t wlo, whi;
+#if OBB_INT_DIV
+                floordiv_rcp(xlo + dd[a] - 1, dd[a], p.fmul[a], wlo, ra[a]);   // ceil(xlo / dd)
+                floordiv_rcp(xhi, dd[a], p.fmul[a], whi, rb[a]);               // floor(xhi / dd)
+#else
                 floordiv_exact(xlo + dd[a] - 1, dd[a], p.rcp[a], wlo, ra[a]);   // ceil(xlo / dd)
                 floordiv_exact(xhi, dd[a], p.rcp[a], whi, rb[a]);               // floor(xhi / dd)
+#endif
                 const int64_t lim = int64_t(1) << 30;
                 qa[a] = (int32_t)min(max(wlo - i0, -lim), lim);
                 qb[a] = (int32_t)min(max(whi - i0, -lim), lim);
@@ -717,7 +825,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 Ah[a] = (int64_t)qb[a] * 4294967296LL + fixed_frac(rb[a], M) + kFixBias;
                 Bs[a] = p.fstep[a];
             }
-            const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
+            const uint64_t* rowp = words + ((int64_t)kb0 * N + j) * W;
             const int64_t rstride = (int64_t)wk * N * W;
             if ((mode & 0x100) && (tk + 1) * wk * tkr <= p.nk) {
                 // an interior box's full-height tile: every row is in the
@@ -725,7 +833,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 // empty range
                 const int32_t spanl = jvalid ? span : -1;
 #pragma unroll kCountUnroll
-                for (int r = 0; r < tkr; ++r, rowp += rstride) {
+                for (int r = r0; r <= r1; ++r, rowp += rstride) {
                     const int32_t lo = max(max(fixed_int(Al[0]), fixed_int(Al[1])), max(fixed_int(Al[2]), 0));
                     const int32_t hi = min(min(fixed_int(Ah[0]), fixed_int(Ah[1])), min(fixed_int(Ah[2]), spanl));
 #pragma unroll
@@ -743,9 +851,9 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                     }
                 }
             } else {
-                int32_t k = kb;
+                int32_t k = kb0;
 #pragma unroll kCountUnroll
-                for (int r = 0; r < tkr; ++r, k += wk, rowp += rstride) {
+                for (int r = r0; r <= r1; ++r, k += wk, rowp += rstride) {
                     const int32_t lo = max(max(fixed_int(Al[0]), fixed_int(Al[1])), max(fixed_int(Al[2]), 0));
                     const int32_t hi = min(min(fixed_int(Ah[0]), fixed_int(Ah[1])), min(fixed_int(Ah[2]), span));
 #pragma unroll
@@ -923,7 +1031,11 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                         ok = cc >= p.Lq[a] && cc <= p.Hq[a];
                     } else {
                         int32_t l2 = i0 + lo, h2 = i0 + hi;
+#if OBB_INT_DIV
+                        clip_slab_rcp(p.n[3 * a], p.fmul[a], cc, p.Lq[a], p.Hq[a], l2, h2);
+#else
                         clip_slab(p.n[3 * a], p.rcp[a], cc, p.Lq[a], p.Hq[a], l2, h2);
+#endif
                         lo = l2 - i0;
                         hi = h2 - i0;
                     }

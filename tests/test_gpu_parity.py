@@ -191,7 +191,8 @@ def _steep_qboxes():
     big = 1 << 24
     kl, kh = -3000, 5000
     rows = []
-    for s0, s2, jrow in [(40, 1, 30), (-40, 1, 12), (33, -1, 47), (-127, -1, 5)]:
+    # |n_20| >= 32 steps by DDA; 0 < |n_20| < 32 is clipped exactly per row
+    for s0, s2, jrow in [(40, 1, 30), (-40, 1, 12), (33, -1, 47), (-127, -1, 5), (5, 1, 20), (-7, -1, 40)]:
         q = np.zeros((), PK.QBOX_DTYPE)
         q["n"] = [big, 0, 0, 50, big, 0, s0, 0, s2 * big]
         z = sorted([s2 * big * kl, s2 * big * kh])
