@@ -25,6 +25,29 @@ constexpr int64_t kBoxRange = int64_t(1) << 20;  // |index-space AABB| limit of 
 #endif
 constexpr int kTileK = OBB_TILE_K;               // rows along z one lane steps through per tile
 
+#ifdef __CUDACC__
+// Integer -> FP32 through 32-bit conversions (relative error below 3 * 2^-24,
+// 4 * 2^-24 from 128 bits):
+// 64-bit conversions issue on the FP64 pipe.
+__device__ __forceinline__ float u64_to_float(uint64_t x)
+{
+    return fmaf((float)(uint32_t)(x >> 32), 4294967296.0f, (float)(uint32_t)x);
+}
+
+__device__ __forceinline__ float i64_to_float(int64_t x)
+{
+    const float f = u64_to_float(x < 0 ? 0ull - (uint64_t)x : (uint64_t)x);
+    return x < 0 ? -f : f;
+}
+
+__device__ __forceinline__ float i128_to_float(__int128 x)   // |x| < 2^126
+{
+    const unsigned __int128 a = x < 0 ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    const float f = fmaf(u64_to_float((uint64_t)(a >> 64)), 18446744073709551616.0f, u64_to_float((uint64_t)a));
+    return x < 0 ? -f : f;
+}
+#endif
+
 // device error word bits
 enum : int32_t {
     kErrRange = 1,

@@ -47,11 +47,23 @@ __global__ void k_aabb(const float* __restrict__ V, int64_t nv, uint32_t* keys)
             mn[b] = min(mn[b], __shfl_xor_sync(0xffffffffu, mn[b], o));
             mx[b] = max(mx[b], __shfl_xor_sync(0xffffffffu, mx[b], o));
         }
+    // warp results through shared memory, then six atomics per block (atomics
+    // from every warp to the same six words serialise in L2)
+    __shared__ uint32_t sh[6][32];
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if ((threadIdx.x & 31) == 0)
         for (int b = 0; b < 3; ++b) {
-            atomicMin(&keys[b], mn[b]);
-            atomicMax(&keys[3 + b], mx[b]);
+            sh[b][w] = mn[b];
+            sh[3 + b][w] = mx[b];
         }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int b = threadIdx.x;
+        uint32_t v = sh[b][0];
+        for (int i = 1; i < nw; ++i) v = b < 3 ? min(v, sh[b][i]) : max(v, sh[b][i]);
+        if (b < 3) atomicMin(&keys[b], v);
+        else atomicMax(&keys[b], v);
+    }
 }
 
 __global__ void k_frame(const uint32_t* keys, int32_t N, LatticeFrame* f, int32_t* err)
@@ -106,11 +118,12 @@ __device__ __forceinline__ int sos_side(int32_t ay, int32_t az, int32_t by, int3
 }
 
 // ceil(num / (256 den)) for den > 0, clamped to [-1, N]: a float estimate
-// corrected by exact int64 products (the quotient is a lattice index).
+// (through 32-bit conversions, which stay off the FP64 pipe) corrected by
+// exact int64 products (the quotient is a lattice index).
 __device__ __forceinline__ int32_t first_index_at_or_after(int64_t num, int64_t den, int32_t N)
 {
     const int64_t D = den << kS;
-    float e = __ll2float_rn(num) / __ll2float_rn(D);
+    float e = i64_to_float(num) / i64_to_float(D);
     e = fminf(fmaxf(e, -2.0f), (float)N + 1.0f);
     int32_t q = (int32_t)ceilf(e);
     // smallest q with q * D >= num, searched within [-1, N]

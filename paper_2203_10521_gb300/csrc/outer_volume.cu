@@ -193,65 +193,85 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
         p.kc_hi[a] = 1e30f;
     }
     if (!empty) {
-        double M[9];
-        for (int i = 0; i < 9; ++i) M[i] = (double)p.n[i];
-        double c00 = M[4] * M[8] - M[5] * M[7];
-        double c01 = M[5] * M[6] - M[3] * M[8];
-        double c02 = M[3] * M[7] - M[4] * M[6];
-        double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
-        if (det == 0.0) {
+        // Exact cofactors of the integer normals (|n| <= 2^24: every product is
+        // below 2^48) and the exact determinant in 128 bits; the geometry below
+        // is FP32 with explicit margins (FP64 and 64-bit int <-> float
+        // conversions issue on the FP64 pipe, a small fraction of the FP32
+        // rate on this GPU).
+        int64_t m[9];
+        for (int i = 0; i < 9; ++i) m[i] = p.n[i];
+        // C[3 r + a] = adjugate entry (r, a): M^-1 = C / det
+        const int64_t C[9] = {m[4] * m[8] - m[5] * m[7], m[2] * m[7] - m[1] * m[8], m[1] * m[5] - m[2] * m[4],
+                              m[5] * m[6] - m[3] * m[8], m[0] * m[8] - m[2] * m[6], m[2] * m[3] - m[0] * m[5],
+                              m[3] * m[7] - m[4] * m[6], m[1] * m[6] - m[0] * m[7], m[0] * m[4] - m[1] * m[3]};
+        const __int128 det = (__int128)m[0] * C[0] + (__int128)m[1] * C[3] + (__int128)m[2] * C[6];
+        if (det == 0) {
             atomicOr(err, kErrArg);
             empty = true;
         } else {
-            double inv[9] = {c00, M[2] * M[7] - M[1] * M[8], M[1] * M[5] - M[2] * M[4],
-                             c01, M[0] * M[8] - M[2] * M[6], M[2] * M[3] - M[0] * M[5],
-                             c02, M[1] * M[6] - M[0] * M[7], M[0] * M[4] - M[1] * M[3]};
+            // FP32 inverse (relative error below 10 * 2^-24 per entry) and the
+            // slab bounds: centre (L + H) / 2, half width (H - L) / 2, and
+            // max(|L|, |H|), which bounds both
+            const float id = 1.0f / i128_to_float(det);
+            float mi[9];
+            for (int i = 0; i < 9; ++i) mi[i] = i64_to_float(C[i]) * id;
+            float yc[3], yh[3], ym[3], yl[3], yu[3];
+            for (int a = 0; a < 3; ++a) {
+                yc[a] = 0.5f * i64_to_float(p.Lq[a] + p.Hq[a]);
+                yh[a] = 0.5f * i64_to_float(p.Hq[a] - p.Lq[a]);
+                yl[a] = i64_to_float(p.Lq[a]);
+                yu[a] = i64_to_float(p.Hq[a]);
+                ym[a] = fmaxf(fabsf(yl[a]), fabsf(yu[a]));
+            }
             // the parallelepiped {L <= M p <= H} has centre M^-1 (L + H) / 2 and
-            // half extent sum_a |M^-1_ra| (H_a - L_a) / 2 along index axis r
-            const double id = 1.0 / det;
-            double mn[3], mx[3];
+            // half extent sum_a |M^-1_ra| (H_a - L_a) / 2 along index axis r; the
+            // FP32 error of the two together is below 2e-6 of
+            // sum_a |M^-1_ra| max(|L_a|, |H_a|), and the bounds are widened by
+            // twice that
+            float mn[3], mx[3];
             for (int r = 0; r < 3; ++r) {
-                double cen = 0.0, ext = 0.0;
+                float cen = 0.0f, ext = 0.0f, mag = 0.0f;
                 for (int a = 0; a < 3; ++a) {
-                    const double w = inv[3 * r + a] * id;
-                    cen += w * (0.5 * ((double)p.Lq[a] + (double)p.Hq[a]));
-                    ext += fabs(w) * (0.5 * ((double)p.Hq[a] - (double)p.Lq[a]));
+                    const float w = mi[3 * r + a];
+                    cen = fmaf(w, yc[a], cen);
+                    ext = fmaf(fabsf(w), yh[a], ext);
+                    mag = fmaf(fabsf(w), ym[a], mag);
                 }
-                mn[r] = cen - ext;
-                mx[r] = cen + ext;
+                const float e = 4e-6f * mag + 1e-3f;
+                mn[r] = cen - ext - e;
+                mx[r] = cen + ext + e;
             }
-            const double lim = (double)kBoxRange;
+            const float lim = (float)kBoxRange;
             for (int r = 0; r < 3; ++r)
-                if (!(mn[r] > -lim && mx[r] < lim + N)) {
+                if (!(mn[r] > -lim && mx[r] < lim + (float)N)) {
                     atomicOr(err, kErrRange);
                     empty = true;
                 }
             if (!empty) {
-                const double span_j = mx[1] - mn[1] + 5.0, span_k = mx[2] - mn[2] + 5.0;
-                if (span_j * span_k > 2147483647.0) {
+                const float span_j = mx[1] - mn[1] + 5.0f, span_k = mx[2] - mn[2] + 5.0f;
+                if (span_j * span_k > 2.0e9f) {
                     atomicOr(err, kErrRange);
                     empty = true;
                 }
             }
             if (!empty) {
-                // the corners carry FP64 rounding far below one row; a margin
-                // of kRowMargin rows keeps the AABB conservative
-                p.i0 = (int32_t)floor(mn[0]) - 2;
-                p.span = (int32_t)ceil(mx[0]) + 2 - p.i0;
-                p.j0 = (int32_t)floor(mn[1]) - kRowMargin;
-                int32_t j1 = (int32_t)ceil(mx[1]) + kRowMargin;
-                p.k0 = (int32_t)floor(mn[2]) - kRowMargin;
-                int32_t k1 = (int32_t)ceil(mx[2]) + kRowMargin;
+                // beyond the widening above, a margin of two columns along x
+                // and kRowMargin rows along y and z
+                p.i0 = (int32_t)floorf(mn[0]) - 2;
+                p.span = (int32_t)ceilf(mx[0]) + 2 - p.i0;
+                p.j0 = (int32_t)floorf(mn[1]) - kRowMargin;
+                int32_t j1 = (int32_t)ceilf(mx[1]) + kRowMargin;
+                p.k0 = (int32_t)floorf(mn[2]) - kRowMargin;
+                int32_t k1 = (int32_t)ceilf(mx[2]) + kRowMargin;
                 p.nj = j1 - p.j0 + 1;
                 p.nk = k1 - p.k0 + 1;
                 // shadow on the (j, k) plane: edge a of the parallelepiped runs
                 // along column a of M^-1; its normal nu_a in (j, k) is
                 // orthogonal to that edge's shadow, and the shadow's extent
                 // along nu_a is the sum over the other two constraints b of
-                // nu_a . (column b) times [L_b, H_b]
-                // (FP32: the test is conservative by two rows, far above its rounding)
-                float mi[9];
-                for (int i = 0; i < 9; ++i) mi[i] = (float)(inv[i] * id);
+                // nu_a . (column b) times [L_b, H_b].  Widened by two rows plus
+                // 4e-6 of the terms' magnitude (the FP32 error, including the
+                // neglected term of column a, is below 2e-6 of it).
                 for (int a = 0; a < 3; ++a) {
                     float nj_ = -mi[3 * 2 + a], nk_ = mi[3 * 1 + a];
                     const float len = sqrtf(nj_ * nj_ + nk_ * nk_);
@@ -259,30 +279,35 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
                     if (!(len > 1e-6f * emax)) continue;   // edge parallel to x: no axis
                     nj_ /= len;
                     nk_ /= len;
-                    float lo = 0.0f, hi = 0.0f;
+                    float lo = 0.0f, hi = 0.0f, mg = 0.0f;
                     for (int b = 0; b < 3; ++b) {
+                        mg = fmaf(fabsf(nj_ * mi[3 * 1 + b]) + fabsf(nk_ * mi[3 * 2 + b]), ym[b], mg);
                         if (b == a) continue;
                         const float w = nj_ * mi[3 * 1 + b] + nk_ * mi[3 * 2 + b];
-                        const float x0 = w * (float)p.Lq[b], x1 = w * (float)p.Hq[b];
+                        const float x0 = w * yl[b], x1 = w * yu[b];
                         lo += fminf(x0, x1);
                         hi += fmaxf(x0, x1);
                     }
+                    const float sm = 2.0f + 4e-6f * mg;
                     p.sat_nu[a][0] = nj_;
                     p.sat_nu[a][1] = nk_;
-                    p.sat_lo[a] = lo - 2.0f;
-                    p.sat_hi[a] = hi + 2.0f;
+                    p.sat_lo[a] = lo - sm;
+                    p.sat_hi[a] = hi + sm;
                     // solved for k relative to (j0, k0), where the band is not
-                    // steep in k (|dk/dj| <= 64): FP64 here, FP32 in the kernel,
-                    // with one row plus a relative margin far above FP32 rounding
-                    if (fabsf(nk_) > 0.0f && fabsf(nj_) <= 64.0f * fabsf(nk_)) {
-                        const double v = (double)nk_, sl = -(double)nj_ / v;
-                        const double b0 = (double)(nk_ > 0.0f ? p.sat_lo[a] : p.sat_hi[a]) / v;
-                        const double b1 = (double)(nk_ > 0.0f ? p.sat_hi[a] : p.sat_lo[a]) / v;
-                        const double c0 = b0 + sl * p.j0 - p.k0, c1 = b1 + sl * p.j0 - p.k0;
-                        const double m = 1.0 + 1e-5 * (fabs(sl) * p.nj + fabs(c0) + fabs(c1));
-                        p.kc_s[a] = (float)sl;
-                        p.kc_lo[a] = (float)(c0 - m);
-                        p.kc_hi[a] = (float)(c1 + m);
+                    // steep in k (|dk/dj| <= 64, so |nu_k| >= 1/65), with one
+                    // row plus 1e-5 of the terms' magnitude (above FP32 rounding
+                    // here and in the kernel's evaluation)
+                    if (fabsf(nj_) <= 64.0f * fabsf(nk_)) {
+                        const float sl = -nj_ / nk_;
+                        const float b0 = (nk_ > 0.0f ? p.sat_lo[a] : p.sat_hi[a]) / nk_;
+                        const float b1 = (nk_ > 0.0f ? p.sat_hi[a] : p.sat_lo[a]) / nk_;
+                        const float fj0 = (float)p.j0, fk0 = (float)p.k0;
+                        const float c0 = b0 + sl * fj0 - fk0, c1 = b1 + sl * fj0 - fk0;
+                        const float mm = 1.0f + 1e-5f * (fabsf(sl) * (fabsf(fj0) + (float)p.nj) + fabsf(b0) +
+                                                         fabsf(b1) + fabsf(fk0));
+                        p.kc_s[a] = sl;
+                        p.kc_lo[a] = c0 - mm;
+                        p.kc_hi[a] = c1 + mm;
                     }
                 }
             }
@@ -316,10 +341,11 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     if (p.nj > 0 && (p.mode & 0x3f) == 0x15) {
         bool small = true;
         for (int a = 0; a < 3; ++a) {
-            const double reach = fabs((double)p.Lq[a]) + fabs((double)p.Hq[a]) +
-                                 fabs((double)p.n[3 * a + 1]) * (fabs((double)p.j0) + p.nj) +
-                                 fabs((double)p.n[3 * a + 2]) * (fabs((double)p.k0) + p.nk);
-            small &= reach < (536870912.0 - fabs((double)p.i0) - p.span - 2.0) * p.dd[a];   // no FP64 divide
+            // FP32 with a 1e-4 relative margin (far above its rounding)
+            const float reach = fabsf(i64_to_float(p.Lq[a])) + fabsf(i64_to_float(p.Hq[a])) +
+                                fabsf((float)p.n[3 * a + 1]) * (fabsf((float)p.j0) + (float)p.nj) +
+                                fabsf((float)p.n[3 * a + 2]) * (fabsf((float)p.k0) + (float)p.nk);
+            small &= reach * 1.0001f < (536870912.0f - fabsf((float)p.i0) - (float)p.span - 2.0f) * (float)p.dd[a];
         }
         if (small) p.mode |= 1 << 9;
     }
