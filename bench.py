@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--eager-step", action="store_true",
+                    help="host-driven Lloyd rounds in the timed step (default: the step's CUDA graph)")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--surrogate-topk", type=int, default=5,
                     help="candidates (and rotation probes) per cluster the surrogate keeps for exact counting")
@@ -77,9 +79,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def count_kernel_traffic():
+def count_kernel_traffic(key="dram_bytes_per_launch"):
     """DRAM bytes per launch of the counting kernel from the committed ncu
-    summary, valid only while the kernel source is unchanged."""
+    summary (`key`: the average over a step's launches, or the batch launch
+    alone), valid only while the kernel source is unchanged."""
     p = os.path.join(ROOT, "profiles", "k_count_roofline_inputs.txt")
     src = os.path.join(ROOT, "paper_2203_10521_gb300", "csrc", "outer_volume.cu")
     if not os.path.exists(p):
@@ -93,7 +96,7 @@ def count_kernel_traffic():
     if kv.get("source_sha256_16") != h:
         return None, kv.get("workload")
     try:
-        return float(kv["dram_bytes_per_launch"]), kv.get("workload")
+        return float(kv[key]), kv.get("workload")
     except (KeyError, ValueError):
         return None, None
 
@@ -287,7 +290,7 @@ def main():
     def step():
         ctx.occupancy_rebuild(lat)
         ctx.outer_volume(lat, d_boxes, counts=d_counts, points=d_points)
-        st = ctx.lloyd_step(layer, rounds=16, refit=True)
+        st = ctx.lloyd_step(layer, rounds=16, refit=True, graph=not args.eager_step)
         return st
 
     for _ in range(args.warmup):
@@ -381,10 +384,16 @@ def main():
     # roofline of the counting kernel (the dominant kernel), live over the timed region
     peak, peak_kind = measured_peaks()
     achieved = prof["count_bytes"] / (prof["count_ms"] / 1000.0) / 1e9 if prof["count_ms"] > 0 else 0.0
-    traffic, traffic_wl = count_kernel_traffic()
+    # with the Lloyd step as a CUDA graph, its counting launches run inside the
+    # graph and only the batch launch of each step is bracketed by events
+    traffic, traffic_wl = count_kernel_traffic("dram_bytes_per_launch" if args.eager_step
+                                               else "dram_bytes_batch_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_count (outer-volume counting)", "peak_kind": peak_kind,
+                "launches_timed": ("every counting launch of each step" if args.eager_step else
+                                   f"the {len(boxes):,}-box batch launch of each step (the Lloyd step's "
+                                   "counting launches run inside its CUDA graph)"),
                 "count_launches": prof["count_launches"], "count_ms_total": prof["count_ms"],
                 "count_bytes_total": prof["count_bytes"], "count_rows": prof["count_rows"],
                 "count_share_of_step_time": prof["count_ms"] / sum(ms)}
@@ -440,6 +449,7 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                "config": {"workload": wl["name"], "triangles": m.n_tris, "lattice": N, "tree_depth": depth,
                           "batch_boxes": len(boxes), "lloyd_rounds_per_iter": 16,
+                          "lloyd_step": "host-driven rounds" if args.eager_step else "CUDA graph (conditional rounds)",
                           "l2": "flushed between steps (256 MiB write)", "per_rank": "independent mesh (seed + rank)"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_all,
                "clocks": clocks, "lloyd_iter_per_s": lloyd_iter_per_s,
