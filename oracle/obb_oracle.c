@@ -1164,65 +1164,103 @@ int orc_median_split(const int32_t* U, const int32_t* F, int64_t nt, const int32
 }
 
 /* ------------------------------------------------------------------------- */
-/* Surrogate features (the learned screen's inputs), FP64 in a fixed order    */
+/* Surrogate features (the learned screen's inputs), FP32 in a fixed order    */
 /* ------------------------------------------------------------------------- */
 
+/* Integer -> FP32 as defined for the features: the magnitude's two 32-bit
+ * halves, each converted to the nearest float, joined by one fused
+ * multiply-add (fmaf rounds once). */
+static float feat_f32_u64(uint64_t u)
+{
+    return fmaf((float)(uint32_t)(u >> 32), 4294967296.0f, (float)(uint32_t)u);
+}
+
+static float feat_f32_i64(int64_t x)
+{
+    uint64_t u = x < 0 ? 0ull - (uint64_t)x : (uint64_t)x;
+    float f = feat_f32_u64(u);
+    return x < 0 ? -f : f;
+}
+
+static float feat_f32_i128(__int128 x)
+{
+    unsigned __int128 a = x < 0 ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
+    float f = fmaf(feat_f32_u64((uint64_t)(a >> 64)), 18446744073709551616.0f, feat_f32_u64((uint64_t)a));
+    return x < 0 ? -f : f;
+}
+
 /*
- * For each quantised box: 12 box parameters (centre of the index-space box /
- * N, unit normals of slabs 0 and 1, half widths / N) and the occupancy bits of
- * an 8^3 patch of points M^-1 v, v_a = L_a + (H_a - L_a)(2 s_a + 1)/16, each
- * rounded to the nearest lattice point (floor(p + 1/2)); 0 outside [0,N)^3.
- * Returns 0, or -3 if an in-domain column needed is not computed.
+ * For each quantised box (normals n, integer slab bounds L <= n . p <= H):
+ * 12 box parameters and the occupancy bits of an 8^3 patch.  Exact integers
+ * first: the adjugate A of n (so n^-1 = A / det) in int64, det in 128 bits,
+ * S = L + H and D = H - L.  Then FP32, one rounding per operation, in this
+ * order (no contraction):
+ *   centre   c_r = (((A_r0 S_0 + A_r1 S_1) + A_r2 S_2) / (2 det));
+ *   params   c_r / N (r = 0..2); n_ac / |n_a| (a = 0, 1; c = 0..2), with
+ *            |n_a| = sqrt((n_a0^2 + n_a1^2) + n_a2^2); ((D_a 0.5) / |n_a|) / N;
+ *   edges    E_ra = (A_ra D_a) / det;
+ *   patch    point s = (s_x, s_y, s_z) in 0..7: g_a = (2 s_a - 7) / 16,
+ *            p_r = ((c_r + E_r0 g_0) + E_r1 g_1) + E_r2 g_2, lattice index
+ *            floor(p_r + 1/2); the bit is 0 outside [0,N)^3.
+ * The patch points are the centres of an 8x8x8 subdivision of the box in its
+ * own frame (M^-1 v for v_a = L_a + D_a (2 s_a + 1) / 16).  det = 0 gives
+ * c = E = 0.  Returns 0, or -3 if an in-domain column needed is not computed.
  */
 int orc_surrogate_features(const uint8_t* occ, const uint8_t* colmask, int32_t N, const int32_t* n,
                            const int64_t* bnd, int64_t K, float* feats)
 {
     for (int64_t b = 0; b < K; ++b) {
         const int32_t* nb = n + 9 * b;
-        double M[9], L[3], H[3];
-        for (int i = 0; i < 9; ++i) M[i] = (double)nb[i];
+        int64_t m[9], L[3], H[3];
+        for (int i = 0; i < 9; ++i) m[i] = nb[i];
         for (int a = 0; a < 3; ++a) {
-            L[a] = (double)(-floordiv64(-bnd[6 * b + 2 * a], 256));
-            H[a] = (double)floordiv64(bnd[6 * b + 2 * a + 1], 256);
+            L[a] = -floordiv64(-bnd[6 * b + 2 * a], 256);
+            H[a] = floordiv64(bnd[6 * b + 2 * a + 1], 256);
         }
-        double c00 = M[4] * M[8] - M[5] * M[7];
-        double c01 = M[5] * M[6] - M[3] * M[8];
-        double c02 = M[3] * M[7] - M[4] * M[6];
-        double det = (M[0] * c00 + M[1] * c01) + M[2] * c02;
-        double adj[9] = {c00, M[2] * M[7] - M[1] * M[8], M[1] * M[5] - M[2] * M[4],
-                         c01, M[0] * M[8] - M[2] * M[6], M[2] * M[3] - M[0] * M[5],
-                         c02, M[1] * M[6] - M[0] * M[7], M[0] * M[4] - M[1] * M[3]};
-        double inv[9];
-        for (int i = 0; i < 9; ++i) inv[i] = det != 0.0 ? adj[i] / det : 0.0;
-        float* f = feats + 524 * b;
-        for (int t = 0; t < 12; ++t) {
-            double v;
-            if (t < 3) {
-                double mid[3];
-                for (int a = 0; a < 3; ++a) mid[a] = (L[a] + H[a]) * 0.5;
-                v = (inv[3 * t] * mid[0] + inv[3 * t + 1] * mid[1]) + inv[3 * t + 2] * mid[2];
-                v = v / (double)N;
-            } else if (t < 9) {
-                int a = (t - 3) / 3, c = (t - 3) % 3;
-                double nn = sqrt((M[3 * a] * M[3 * a] + M[3 * a + 1] * M[3 * a + 1]) + M[3 * a + 2] * M[3 * a + 2]);
-                v = nn > 0.0 ? M[3 * a + c] / nn : 0.0;
-            } else {
-                int a = t - 9;
-                double nn = sqrt((M[3 * a] * M[3 * a] + M[3 * a + 1] * M[3 * a + 1]) + M[3 * a + 2] * M[3 * a + 2]);
-                v = nn > 0.0 ? ((H[a] - L[a]) * 0.5 / nn) / (double)N : 0.0;
+        const int64_t A[9] = {m[4] * m[8] - m[5] * m[7], m[2] * m[7] - m[1] * m[8], m[1] * m[5] - m[2] * m[4],
+                              m[5] * m[6] - m[3] * m[8], m[0] * m[8] - m[2] * m[6], m[2] * m[3] - m[0] * m[5],
+                              m[3] * m[7] - m[4] * m[6], m[1] * m[6] - m[0] * m[7], m[0] * m[4] - m[1] * m[3]};
+        const __int128 det = (__int128)m[0] * A[0] + (__int128)m[1] * A[3] + (__int128)m[2] * A[6];
+        const float detf = feat_f32_i128(det);
+        float Af[9], Sf[3], Df[3], c[3] = {0.f, 0.f, 0.f}, E[9];
+        for (int i = 0; i < 9; ++i) Af[i] = feat_f32_i64(A[i]);
+        for (int a = 0; a < 3; ++a) {
+            Sf[a] = feat_f32_i64(L[a] + H[a]);
+            Df[a] = feat_f32_i64(H[a] - L[a]);
+        }
+        for (int r = 0; r < 3; ++r) {
+            if (det != 0) {
+                float t = Af[3 * r] * Sf[0] + Af[3 * r + 1] * Sf[1];
+                t = t + Af[3 * r + 2] * Sf[2];
+                c[r] = t / (2.0f * detf);
             }
-            f[t] = (float)v;
+            for (int a = 0; a < 3; ++a) E[3 * r + a] = det != 0 ? (Af[3 * r + a] * Df[a]) / detf : 0.0f;
+        }
+        float* f = feats + 524 * b;
+        for (int r = 0; r < 3; ++r) f[r] = c[r] / (float)N;
+        for (int a = 0; a < 3; ++a) {
+            const float n0 = (float)nb[3 * a], n1 = (float)nb[3 * a + 1], n2 = (float)nb[3 * a + 2];
+            float q = n0 * n0 + n1 * n1;
+            q = q + n2 * n2;
+            const float nn = sqrtf(q);
+            if (a < 2) {
+                f[3 + 3 * a] = nn > 0.0f ? n0 / nn : 0.0f;
+                f[4 + 3 * a] = nn > 0.0f ? n1 / nn : 0.0f;
+                f[5 + 3 * a] = nn > 0.0f ? n2 / nn : 0.0f;
+            }
+            f[9 + a] = nn > 0.0f ? ((Df[a] * 0.5f) / nn) / (float)N : 0.0f;
         }
         for (int s = 0; s < 512; ++s) {
-            int sx = s & 7, sy = (s >> 3) & 7, sz = s >> 6;
-            double fr[3] = {(double)(2 * sx + 1) / 16.0, (double)(2 * sy + 1) / 16.0, (double)(2 * sz + 1) / 16.0};
-            double v[3];
-            for (int a = 0; a < 3; ++a) v[a] = L[a] + (H[a] - L[a]) * fr[a];
+            const int sv[3] = {s & 7, (s >> 3) & 7, s >> 6};
+            float g[3];
+            for (int a = 0; a < 3; ++a) g[a] = (float)(2 * sv[a] - 7) * 0.0625f;
             int64_t idx[3];
             for (int r = 0; r < 3; ++r) {
-                double p = (inv[3 * r] * v[0] + inv[3 * r + 1] * v[1]) + inv[3 * r + 2] * v[2];
-                double c = floor(p + 0.5);
-                idx[r] = fabs(c) < 1e15 ? (int64_t)c : -1;
+                float p = c[r] + E[3 * r] * g[0];
+                p = p + E[3 * r + 1] * g[1];
+                p = p + E[3 * r + 2] * g[2];
+                const float q = floorf(p + 0.5f);
+                idx[r] = fabsf(q) < 1e9f ? (int64_t)q : -1;
             }
             float bit = 0.f;
             if (idx[0] >= 0 && idx[0] < N && idx[1] >= 0 && idx[1] < N && idx[2] >= 0 && idx[2] < N) {

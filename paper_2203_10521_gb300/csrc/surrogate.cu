@@ -43,81 +43,78 @@ __global__ void k_features(const obb_qbox* __restrict__ boxes, const int32_t* __
 {
     const int64_t b = blockIdx.x;
     if (b >= *d_K) return;
-    // the box's inverse is computed once per block and shared
-    __shared__ double sh_M[9], sh_inv[9], sh_L[3], sh_H[3];
+    // Per box, once: the exact adjugate A of the normals (n^-1 = A / det) in
+    // int64 and det in 128 bits, then FP32 with one rounding per operation in
+    // a fixed order (explicit _rn intrinsics: nothing is fused).  Integers
+    // reach FP32 as two 32-bit halves joined by one fmaf.
+    __shared__ float sh_c[3], sh_E[9];
+    float* f = feats + b * (int64_t)kIn;
     if (threadIdx.x == 0) {
         const obb_qbox q = boxes[b];
-        double M[9];
-        for (int i = 0; i < 9; ++i) M[i] = (double)q.n[i];
+        int64_t m[9], L[3], H[3];
+        for (int i = 0; i < 9; ++i) m[i] = q.n[i];
         for (int a = 0; a < 3; ++a) {
-            sh_L[a] = (double)(-((-q.b[2 * a]) >> kS));
-            sh_H[a] = (double)(q.b[2 * a + 1] >> kS);
+            L[a] = -((-q.b[2 * a]) >> kS);
+            H[a] = q.b[2 * a + 1] >> kS;
         }
-        const double c00 = __dsub_rn(__dmul_rn(M[4], M[8]), __dmul_rn(M[5], M[7]));
-        const double c01 = __dsub_rn(__dmul_rn(M[5], M[6]), __dmul_rn(M[3], M[8]));
-        const double c02 = __dsub_rn(__dmul_rn(M[3], M[7]), __dmul_rn(M[4], M[6]));
-        const double det = __dadd_rn(__dadd_rn(__dmul_rn(M[0], c00), __dmul_rn(M[1], c01)), __dmul_rn(M[2], c02));
-        const double adj[9] = {c00, __dsub_rn(__dmul_rn(M[2], M[7]), __dmul_rn(M[1], M[8])),
-                               __dsub_rn(__dmul_rn(M[1], M[5]), __dmul_rn(M[2], M[4])),
-                               c01, __dsub_rn(__dmul_rn(M[0], M[8]), __dmul_rn(M[2], M[6])),
-                               __dsub_rn(__dmul_rn(M[2], M[3]), __dmul_rn(M[0], M[5])),
-                               c02, __dsub_rn(__dmul_rn(M[1], M[6]), __dmul_rn(M[0], M[7])),
-                               __dsub_rn(__dmul_rn(M[0], M[4]), __dmul_rn(M[1], M[3]))};
-        for (int i = 0; i < 9; ++i) {
-            sh_M[i] = M[i];
-            sh_inv[i] = det != 0.0 ? __ddiv_rn(adj[i], det) : 0.0;
+        const int64_t A[9] = {m[4] * m[8] - m[5] * m[7], m[2] * m[7] - m[1] * m[8], m[1] * m[5] - m[2] * m[4],
+                              m[5] * m[6] - m[3] * m[8], m[0] * m[8] - m[2] * m[6], m[2] * m[3] - m[0] * m[5],
+                              m[3] * m[7] - m[4] * m[6], m[1] * m[6] - m[0] * m[7], m[0] * m[4] - m[1] * m[3]};
+        const __int128 det = (__int128)m[0] * A[0] + (__int128)m[1] * A[3] + (__int128)m[2] * A[6];
+        const float detf = i128_to_float(det);
+        float Af[9], Sf[3], Df[3];
+        for (int i = 0; i < 9; ++i) Af[i] = i64_to_float(A[i]);
+        for (int a = 0; a < 3; ++a) {
+            Sf[a] = i64_to_float(L[a] + H[a]);
+            Df[a] = i64_to_float(H[a] - L[a]);
+        }
+        for (int r = 0; r < 3; ++r) {
+            float c = 0.0f;
+            if (det != 0) {
+                // index-space centre: ((A_r0 S_0 + A_r1 S_1) + A_r2 S_2) / (2 det)
+                const float t = __fadd_rn(__fadd_rn(__fmul_rn(Af[3 * r], Sf[0]), __fmul_rn(Af[3 * r + 1], Sf[1])),
+                                          __fmul_rn(Af[3 * r + 2], Sf[2]));
+                c = __fdiv_rn(t, __fmul_rn(2.0f, detf));
+            }
+            sh_c[r] = c;
+            f[r] = __fdiv_rn(c, (float)N);
+            // edge a of the box in index space: (A_ra D_a) / det
+            for (int a = 0; a < 3; ++a)
+                sh_E[3 * r + a] = det != 0 ? __fdiv_rn(__fmul_rn(Af[3 * r + a], Df[a]), detf) : 0.0f;
+        }
+        for (int a = 0; a < 3; ++a) {
+            const float n0 = (float)q.n[3 * a], n1 = (float)q.n[3 * a + 1], n2 = (float)q.n[3 * a + 2];
+            const float nn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(n0, n0), __fmul_rn(n1, n1)), __fmul_rn(n2, n2)));
+            if (a < 2) {
+                f[3 + 3 * a] = nn > 0.0f ? __fdiv_rn(n0, nn) : 0.0f;
+                f[4 + 3 * a] = nn > 0.0f ? __fdiv_rn(n1, nn) : 0.0f;
+                f[5 + 3 * a] = nn > 0.0f ? __fdiv_rn(n2, nn) : 0.0f;
+            }
+            f[9 + a] = nn > 0.0f ? __fdiv_rn(__fdiv_rn(__fmul_rn(Df[a], 0.5f), nn), (float)N) : 0.0f;
         }
     }
     __syncthreads();
-    double M[9], inv[9], Lq[3], Hq[3];
-    for (int i = 0; i < 9; ++i) {
-        M[i] = sh_M[i];
-        inv[i] = sh_inv[i];
-    }
-    for (int a = 0; a < 3; ++a) {
-        Lq[a] = sh_L[a];
-        Hq[a] = sh_H[a];
-    }
-    float* f = feats + b * (int64_t)kIn;
-    if (threadIdx.x < 12) {
-        const int t = threadIdx.x;
-        double v = 0.0;
-        if (t < 3) {
-            double mid[3];
-            for (int a = 0; a < 3; ++a) mid[a] = __dmul_rn(__dadd_rn(Lq[a], Hq[a]), 0.5);
-            v = __dadd_rn(__dadd_rn(__dmul_rn(inv[3 * t], mid[0]), __dmul_rn(inv[3 * t + 1], mid[1])),
-                          __dmul_rn(inv[3 * t + 2], mid[2]));
-            v = __ddiv_rn(v, (double)N);
-        } else if (t < 9) {
-            const int a = (t - 3) / 3, c = (t - 3) % 3;
-            const double nn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(M[3 * a], M[3 * a]),
-                                                             __dmul_rn(M[3 * a + 1], M[3 * a + 1])),
-                                                   __dmul_rn(M[3 * a + 2], M[3 * a + 2])));
-            v = nn > 0.0 ? __ddiv_rn(M[3 * a + c], nn) : 0.0;
-        } else {
-            const int a = t - 9;
-            const double nn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(M[3 * a], M[3 * a]),
-                                                             __dmul_rn(M[3 * a + 1], M[3 * a + 1])),
-                                                   __dmul_rn(M[3 * a + 2], M[3 * a + 2])));
-            v = nn > 0.0 ? __ddiv_rn(__ddiv_rn(__dmul_rn(__dsub_rn(Hq[a], Lq[a]), 0.5), nn), (double)N) : 0.0;
-        }
-        f[t] = (float)v;
-    }
+    const float c0 = sh_c[0], c1 = sh_c[1], c2 = sh_c[2];
+    float E[9];
+    for (int i = 0; i < 9; ++i) E[i] = sh_E[i];
+    // patch point s: the centre plus the edges times g_a = (2 s_a - 7) / 16,
+    // ((c_r + E_r0 g_0) + E_r1 g_1) + E_r2 g_2, rounded to the nearest lattice
+    // point (floor(p + 1/2)); the bit is 0 outside the lattice
     for (int s = threadIdx.x; s < 512; s += blockDim.x) {
-        const int sx = s & 7, sy = (s >> 3) & 7, sz = s >> 6;
-        const double fr[3] = {(double)(2 * sx + 1) / 16.0, (double)(2 * sy + 1) / 16.0, (double)(2 * sz + 1) / 16.0};
-        double v[3];
-        for (int a = 0; a < 3; ++a) v[a] = __dadd_rn(Lq[a], __dmul_rn(__dsub_rn(Hq[a], Lq[a]), fr[a]));
-        int64_t idx[3];
+        const float g0 = __fmul_rn((float)(2 * (s & 7) - 7), 0.0625f);
+        const float g1 = __fmul_rn((float)(2 * ((s >> 3) & 7) - 7), 0.0625f);
+        const float g2 = __fmul_rn((float)(2 * (s >> 6) - 7), 0.0625f);
+        const float cr[3] = {c0, c1, c2};
+        int32_t idx[3];
         for (int r = 0; r < 3; ++r) {
-            const double p = __dadd_rn(__dadd_rn(__dmul_rn(inv[3 * r], v[0]), __dmul_rn(inv[3 * r + 1], v[1])),
-                                       __dmul_rn(inv[3 * r + 2], v[2]));
-            const double c = floor(__dadd_rn(p, 0.5));
-            idx[r] = (fabs(c) < 1e15) ? (int64_t)c : -1;
+            const float p = __fadd_rn(__fadd_rn(__fadd_rn(cr[r], __fmul_rn(E[3 * r], g0)), __fmul_rn(E[3 * r + 1], g1)),
+                                      __fmul_rn(E[3 * r + 2], g2));
+            const float qf = floorf(__fadd_rn(p, 0.5f));
+            idx[r] = fabsf(qf) < 1e9f ? (int32_t)qf : -1;
         }
         float bit = 0.f;
         if (idx[0] >= 0 && idx[0] < N && idx[1] >= 0 && idx[1] < N && idx[2] >= 0 && idx[2] < N) {
-            const uint64_t w = words[(idx[2] * N + idx[1]) * W + (idx[0] >> 6)];
+            const uint64_t w = words[((int64_t)idx[2] * N + idx[1]) * W + (idx[0] >> 6)];
             bit = (float)((w >> (idx[0] & 63)) & 1ull);
         }
         f[12 + s] = bit;
