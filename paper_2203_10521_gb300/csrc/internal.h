@@ -55,6 +55,7 @@ enum : int32_t {
     kErrEmpty = 4,
     kErrDegenerate = 8,
     kErrOverflow = 16,
+    kErrTimeout = 32,   // a bounded wait in a kernel gave up
 };
 
 // Lattice frame; identical copies on the host and the device.

@@ -52,6 +52,7 @@ obb_status check_device_error(obb_ctx* ctx)
     OBB_CK(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t), ctx->stream));
     if (w & kErrArg) return fail(ctx, OBB_ERR_ARG, "invalid box or assignment (non-finite, negative extent, singular or out of range)");
     if (w & kErrEmpty) return fail(ctx, OBB_ERR_EMPTY_CLUSTER, "a cluster is empty or too small to split");
+    if (w & kErrTimeout) return fail(ctx, OBB_ERR_TIMEOUT, "a tensor-core wait timed out inside a kernel");
     if (w & kErrDegenerate) return fail(ctx, OBB_ERR_RANGE, "degenerate lattice: the vertex AABB has zero extent on an axis");
     if (w & kErrRange) return fail(ctx, OBB_ERR_RANGE, "a box's lattice bounding box exceeds the supported range");
     return fail(ctx, OBB_ERR_STATE, "internal capacity exceeded");

@@ -121,6 +121,279 @@ __global__ void k_features(const obb_qbox* __restrict__ boxes, const int32_t* __
     }
 }
 
+
+// ------------------------------------------------------ tensor-core forward
+//
+// Inference of the screening network on the 5th-generation tensor cores: one
+// CTA (4 warps) carries 128 boxes through all four layers.  Operands are FP16
+// in shared memory in the canonical K-major layout without swizzle (8 x 8
+// "core matrices" of 128 contiguous bytes: core (r / 8, c / 8) of a tile with
+// C columns at ((r / 8) (C / 8) + c / 8) * 128 bytes, so the leading (K)
+// byte offset is 128 and the stride (M/N) byte offset C * 16).  One thread
+// issues tcgen05.mma (kind::f16, M = N = 128, K = 16 per instruction, FP32
+// accumulator in 128 TMEM columns) and commits to an mbarrier; every thread
+// then reads its own row of the accumulator (TMEM lane = box) with
+// tcgen05.ld, adds the bias, applies ReLU and writes FP16 back as the next
+// layer's A operand.  The 128 -> 1 output layer is a dot product per row in
+// registers.  Every wait is bounded; a CTA that allocated TMEM frees it on
+// every path.
+
+constexpr int kTcRows = 128;                    // boxes per CTA (= TMEM lanes)
+constexpr int kTcK1 = 576;                      // layer-1 K (524 features) padded to chunks of 64
+constexpr int kTcChunk = 64;                    // layer-1 K per staged chunk
+constexpr uint32_t kTcCols = 128;               // TMEM columns (one FP32 accumulator)
+// instruction descriptor: D = FP32 (bits 4-5), A = B = FP16 (bits 7-12 zero),
+// both K-major (bits 15, 16 zero), N / 8 at bits 17-22, M / 16 at bits 24-28
+constexpr uint32_t kTcIdesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kTcSpin = 1u << 22;          // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start, leading and stride byte offsets
+// (>> 4), descriptor version 1 (bits 46-47), no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+// byte offset of element (r, c) in a K-major no-swizzle tile of C columns
+__device__ __forceinline__ uint32_t tc_off(int r, int c, int C)
+{
+    return (uint32_t)((((r >> 3) * (C >> 3) + (c >> 3)) << 7) + ((r & 7) << 4) + ((c & 7) << 1));
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// wait for the given phase of the mbarrier; false after kTcSpin rounds
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase)
+{
+    for (uint32_t i = 0; i < kTcSpin; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the tensor core (async proxy)
+__device__ __forceinline__ void tc_fence_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+
+// bulk copy (TMA, untiled) of `bytes` from global to shared memory, completing
+// on `bar` (16-byte aligned addresses, a multiple of 16 bytes)
+__device__ __forceinline__ void tc_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// FP16 weights, transposed (N x K, K-major) and laid out as the kernel's shared
+// tiles: W1 as 9 chunks of 128 x 64 (K zero-padded to 576), then W2, W3 as
+// 128 x 128 tiles
+constexpr int64_t kTcW1Chunk = (int64_t)kH * kTcChunk;               // halves per W1 chunk
+constexpr int64_t kTcPacked = (kTcK1 / kTcChunk) * kTcW1Chunk + 2 * (int64_t)kH * kH;
+
+__global__ void k_pack_tc(const __half* __restrict__ wh, __half* __restrict__ wtc)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n1 = (int64_t)kH * kTcK1;
+    if (i < n1) {
+        const int n = (int)(i % kH), k = (int)(i / kH);
+        const int q = k / kTcChunk, c = k % kTcChunk;
+        wtc[q * kTcW1Chunk + tc_off(n, c, kTcChunk) / 2] = k < kIn ? wh[oW1 + (int64_t)k * kH + n] : __float2half_rn(0.f);
+    } else if (i < n1 + 2 * (int64_t)kH * kH) {
+        const int64_t j = i - n1;
+        const int layer = (int)(j / ((int64_t)kH * kH));
+        const int e = (int)(j % ((int64_t)kH * kH));
+        const int n = e % kH, c = e / kH;
+        const int64_t base = (kTcK1 / kTcChunk) * kTcW1Chunk + layer * (int64_t)kH * kH;
+        wtc[base + tc_off(n, c, kH) / 2] = wh[(layer == 0 ? oW2 : oW3) + (int64_t)c * kH + n];
+    }
+}
+
+constexpr int kTcSmem = 65536 + (4 * kH + 4) * 4;   // A and B tiles, biases, w4, b4
+
+// y = sigmoid(W4 relu(W3 relu(W2 relu(W1 x + b1) + b2) + b3) + b4) for rows
+// [128 blockIdx.x, +128) of X (the live row count is *d_M when given)
+__global__ void __launch_bounds__(kTcRows) k_mlp_tc(const float* __restrict__ X, int M, const int32_t* __restrict__ d_M,
+                                                    const __half* __restrict__ wtc, const __half* __restrict__ wh,
+                                                    const float* __restrict__ w, float* __restrict__ y,
+                                                    int32_t* __restrict__ err)
+{
+    if (d_M) M = min(M, *d_M);
+    const int m0 = blockIdx.x * kTcRows;
+    if (m0 >= M) return;   // uniform: the whole CTA leaves before any TMEM or barrier use
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* sA = tc_smem;            // A operand: layer-1 chunk (128 x 64), then h (128 x 128)
+    unsigned char* sB = tc_smem + 32768;    // B operand: W^T tile
+    float* sBias = reinterpret_cast<float*>(tc_smem + 65536);   // b1, b2, b3, w4 (4 x 128), b4
+    __shared__ __align__(8) uint64_t bar_mma, bar_ld;
+    __shared__ uint32_t s_tmem;
+    const int t = threadIdx.x, warp = t >> 5;
+    for (int i = t; i < kH; i += kTcRows) {
+        sBias[i] = w[oB1 + i];
+        sBias[kH + i] = w[oB2 + i];
+        sBias[2 * kH + i] = w[oB3 + i];
+        sBias[3 * kH + i] = __half2float(wh[oW4 + i]);
+    }
+    if (t == 0) {
+        sBias[4 * kH] = w[oB4];
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_mma)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar_ld)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                     "r"(kTcCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t aS = smem_addr(sA), bS = smem_addr(sB);
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 TMEM lanes
+    uint32_t ph_mma = 0, ph_ld = 0;
+    bool ok = true;
+
+    // layer 1: the W1 chunk arrives by bulk copy while the threads convert
+    // their rows' features to FP16 (16-byte stores of 8 consecutive K)
+    for (int q = 0; q < kTcK1 / kTcChunk && ok; ++q) {
+        const int k0 = q * kTcChunk;
+        if (t == 0) tc_bulk_load(sB, wtc + q * kTcW1Chunk, (uint32_t)(kTcW1Chunk * 2), &bar_ld);
+        for (int i = t; i < kTcRows * (kTcChunk / 8); i += kTcRows) {
+            const int r = i / (kTcChunk / 8), g = i % (kTcChunk / 8);
+            const int m = m0 + r, k = k0 + 8 * g;
+            __align__(16) __half hv[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                hv[e] = __float2half_rn((m < M && k + e < kIn) ? X[(int64_t)m * kIn + k + e] : 0.f);
+            *reinterpret_cast<uint4*>(sA + tc_off(r, 8 * g, kTcChunk)) = *reinterpret_cast<const uint4*>(hv);
+        }
+        tc_fence_smem();
+        const bool got = tc_wait(&bar_ld, ph_ld);
+        ph_ld ^= 1;
+        tc_fence_before();
+        if (!__syncthreads_and(got)) {
+            ok = false;
+            break;
+        }
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int j = 0; j < kTcChunk / 16; ++j)
+                tc_mma(tmem, tc_desc(aS + 256 * j, 128, kTcChunk * 16), tc_desc(bS + 256 * j, 128, kTcChunk * 16),
+                       (q > 0 || j > 0) ? 1u : 0u);
+            tc_commit(&bar_mma);
+        }
+        ok = __syncthreads_and(tc_wait(&bar_mma, ph_mma));
+        ph_mma ^= 1;
+    }
+
+    // layers 2 and 3: the accumulator row of this thread (TMEM lane = row)
+    // becomes FP16 h in the A tile; W^T arrives by bulk copy
+    for (int layer = 0; layer < 2 && ok; ++layer) {
+        if (t == 0)
+            tc_bulk_load(sB, wtc + (kTcK1 / kTcChunk) * kTcW1Chunk + layer * (int64_t)kH * kH,
+                         (uint32_t)(kH * kH * 2), &bar_ld);
+        tc_fence_after();
+        for (int c = 0; c < kH / 32; ++c) {
+            float v[32];
+            tc_ld32(lane_base + 32 * c, v);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                __align__(16) __half hv[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) hv[e] = __float2half_rn(fmaxf(v[8 * g + e] + sBias[layer * kH + 32 * c + 8 * g + e], 0.f));
+                *reinterpret_cast<uint4*>(sA + tc_off(t, 32 * c + 8 * g, kH)) = *reinterpret_cast<const uint4*>(hv);
+            }
+        }
+        tc_fence_smem();
+        const bool got = tc_wait(&bar_ld, ph_ld);
+        ph_ld ^= 1;
+        tc_fence_before();
+        if (!__syncthreads_and(got)) {
+            ok = false;
+            break;
+        }
+        if (t == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int j = 0; j < kH / 16; ++j)
+                tc_mma(tmem, tc_desc(aS + 256 * j, 128, kH * 16), tc_desc(bS + 256 * j, 128, kH * 16), j > 0 ? 1u : 0u);
+            tc_commit(&bar_mma);
+        }
+        ok = __syncthreads_and(tc_wait(&bar_mma, ph_mma));
+        ph_mma ^= 1;
+    }
+
+    if (ok) {
+        // output layer: relu(h3) . w4 + b4 per row, then the sigmoid
+        tc_fence_after();
+        float acc = sBias[4 * kH];
+        for (int c = 0; c < kH / 32; ++c) {
+            float v[32];
+            tc_ld32(lane_base + 32 * c, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                acc = fmaf(fmaxf(v[e] + sBias[2 * kH + 32 * c + e], 0.f), sBias[3 * kH + 32 * c + e], acc);
+        }
+        const int m = m0 + t;
+        if (m < M) y[m] = 1.f / (1.f + __expf(-acc));
+    } else {
+        // a wait gave up: report it, let in-flight tensor-core work and copies
+        // finish (bounded), then free TMEM below
+        if (t == 0) atomicOr(err, kErrTimeout);
+        tc_wait(&bar_mma, ph_mma ^ 1);
+        tc_wait(&bar_ld, ph_ld ^ 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
+}
+
 // box volume in lattice cells: prod (Hq_a - Lq_a + 1) / |det n|
 __device__ __forceinline__ float box_cells(const obb_qbox& q)
 {
@@ -290,6 +563,7 @@ void gemm(obb_ctx* ctx, int M, int N, int K, const float* A, int64_t sAm, int64_
 struct MlpImpl {
     float* w = nullptr;    // FP32 master weights
     __half* wh = nullptr;  // FP16 inference copy
+    __half* wtc = nullptr; // the FP16 weights transposed into the tensor-core kernel's shared tiles
     float* g = nullptr;    // gradients
     float* m = nullptr;    // Adam moments
     float* v = nullptr;
@@ -329,11 +603,11 @@ static obb_status mlp_reserve(obb_ctx* ctx, MlpImpl* P, int64_t B)
 static void mlp_forward(obb_ctx* ctx, const MlpImpl* P, const float* X, int B, const int32_t* d_B, bool half)
 {
     if (half) {
-        const __half* w = P->wh;
-        gemm<__half>(ctx, B, kH, kIn, X, kIn, 1, w + oW1, kH, 1, P->h1, kH, P->w + oB1, 1, nullptr, 0, d_B);
-        gemm<__half>(ctx, B, kH, kH, P->h1, kH, 1, w + oW2, kH, 1, P->h2, kH, P->w + oB2, 1, nullptr, 0, d_B);
-        gemm<__half>(ctx, B, kH, kH, P->h2, kH, 1, w + oW3, kH, 1, P->h3, kH, P->w + oB3, 1, nullptr, 0, d_B);
-        gemm<__half>(ctx, B, 1, kH, P->h3, kH, 1, w + oW4, 1, 1, P->y, 1, P->w + oB4, 2, nullptr, 0, d_B);
+        // all four layers in one tensor-core kernel (FP16 operands, FP32 accumulators)
+        cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+        k_mlp_tc<<<(unsigned)((B + kTcRows - 1) / kTcRows), kTcRows, kTcSmem, ctx->stream>>>(X, B, d_B, P->wtc, P->wh,
+                                                                                           P->w, P->y, ctx->d_err);
+        note_launch(ctx);
     } else {
         const float* w = P->w;
         gemm<float>(ctx, B, kH, kIn, X, kIn, 1, w + oW1, kH, 1, P->h1, kH, w + oB1, 1, nullptr, 0, d_B);
@@ -434,6 +708,7 @@ obb_status obb_mlp_create(obb_ctx* ctx, uint64_t seed, obb_mlp** out)
     cudaStream_t s = ctx->stream;
     cudaError_t e = cudaMallocAsync((void**)&P->w, sizeof(float) * kParams, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->wh, sizeof(__half) * kParams, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->wtc, sizeof(__half) * kTcPacked, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->g, sizeof(float) * kParams, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->m, sizeof(float) * kParams, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->v, sizeof(float) * kParams, s);
@@ -443,7 +718,8 @@ obb_status obb_mlp_create(obb_ctx* ctx, uint64_t seed, obb_mlp** out)
     if (e == cudaSuccess) e = cudaMemsetAsync(P->v, 0, sizeof(float) * kParams, s);
     if (e == cudaSuccess) {
         k_to_half<<<(unsigned)((kParams + 255) / 256), 256, 0, s>>>(P->w, P->wh, kParams);
-        note_launch(ctx);
+        k_pack_tc<<<(unsigned)((kTcPacked + 255) / 256), 256, 0, s>>>(P->wh, P->wtc);
+        note_launch(ctx, 2);
         e = cudaStreamSynchronize(s);
     }
     if (e != cudaSuccess) {
@@ -460,7 +736,7 @@ void obb_mlp_free(obb_mlp* m)
     cudaStream_t s = m->ctx ? m->ctx->stream : nullptr;
     if (m->p) {
         MlpImpl* P = m->p;
-        void* ptrs[] = {P->w, P->wh, P->g, P->m, P->v, P->h1, P->h2, P->h3, P->y, P->d1, P->d2, P->d3, P->dy, P->loss};
+        void* ptrs[] = {P->w, P->wh, P->wtc, P->g, P->m, P->v, P->h1, P->h2, P->h3, P->y, P->d1, P->d2, P->d3, P->dy, P->loss};
         for (void* q : ptrs)
             if (q) cudaFreeAsync(q, s);
         delete P;
@@ -485,6 +761,8 @@ obb_status obb_mlp_set_params(obb_ctx* ctx, obb_mlp* m, const float* in, int32_t
     OBB_CK(ctx, cudaMemcpyAsync(P->w, in, sizeof(float) * kParams,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     k_to_half<<<(unsigned)((kParams + 255) / 256), 256, 0, ctx->stream>>>(P->w, P->wh, kParams);
+    k_pack_tc<<<(unsigned)((kTcPacked + 255) / 256), 256, 0, ctx->stream>>>(P->wh, P->wtc);
+    note_launch(ctx);
     note_launch(ctx);
     OBB_CK(ctx, cudaMemsetAsync(P->m, 0, sizeof(float) * kParams, ctx->stream));
     OBB_CK(ctx, cudaMemsetAsync(P->v, 0, sizeof(float) * kParams, ctx->stream));
@@ -570,7 +848,8 @@ obb_status obb_mlp_train_step(obb_ctx* ctx, obb_mlp* m, const float* feats, cons
     const float b1t = std::pow(0.9f, (float)P->step), b2t = std::pow(0.999f, (float)P->step);
     k_adam<<<(unsigned)((kParams + 255) / 256), 256, 0, ctx->stream>>>(P->w, P->g, P->m, P->v, P->wh, kParams, lr,
                                                                       b1t, b2t);
-    note_launch(ctx);
+    k_pack_tc<<<(unsigned)((kTcPacked + 255) / 256), 256, 0, ctx->stream>>>(P->wh, P->wtc);
+    note_launch(ctx, 2);
     OBB_CK(ctx, cudaGetLastError());
     if (loss)
         OBB_CK(ctx, cudaMemcpyAsync(loss, P->loss, sizeof(float),
