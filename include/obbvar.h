@@ -214,6 +214,19 @@ obb_status obb_outer_volume_multi(obb_ctx* ctx, const obb_lattice* const* lats, 
  * CUDA graphs are recaptured on their next call. */
 obb_status obb_set_counting_tile(obb_ctx* ctx, int32_t tile_k);
 
+/* Row axis of the counting kernel.  By default (axis = 0) every box is counted
+ * in rows along x.  With axis = -1 each box is counted along the index axis
+ * whose perpendicular plane receives its smallest shadow (the fewest rows);
+ * 1 or 2 force rows along y or z.  For these the lattice keeps two more copies
+ * of its occupancy with rows along y and z (bit transposes, 2x the lattice's
+ * memory, refreshed by every rebuild); lattices get them at their next build
+ * or rebuild after the axis is set, and a lattice without them is counted
+ * along x.  Worth it when a lattice is counted many times between rebuilds.
+ * The count is exact for every choice; only its speed changes.  Steps already
+ * captured as CUDA graphs are recaptured on their next call.  OBB_ERR_ARG
+ * outside -1..2. */
+obb_status obb_set_counting_axis(obb_ctx* ctx, int32_t axis);
+
 /* Autotuner of the counting kernel: times the outer-volume count of the given
  * quantised boxes with 8, 16, 32 and 64 rows per tile (one warm-up and three
  * timed runs each, CUDA events on the context stream), keeps the fastest for

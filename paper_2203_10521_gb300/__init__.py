@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True):
         "obb_flood_partition": [vp, vp, vp, i32, C.POINTER(FloodStats)],
         "obb_layer_adjust": [vp, vp, C.POINTER(StepOpts), i32, C.POINTER(AdjustStats)],
         "obb_set_counting_tile": [vp, i32],
+        "obb_set_counting_axis": [vp, i32],
         "obb_tune_counting": [vp, vp, vp, i64, i32, vp, vp],
         "obb_unit_step": [vp, vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
         "obb_mlp_create": [vp, C.c_uint64, C.POINTER(vp)],
@@ -170,7 +171,7 @@ def exported_symbols():
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
             "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free", "obb_tree_parents",
             "obb_tree_sweep", "obb_layer_parents", "obb_unit_step", "obb_flood_partition",
-            "obb_layer_adjust", "obb_set_counting_tile", "obb_tune_counting",
+            "obb_layer_adjust", "obb_set_counting_tile", "obb_set_counting_axis", "obb_tune_counting",
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_mlp_forward", "obb_mlp_gradients", "obb_mlp_train_step",
             "obb_layer_set_surrogate", "obb_layer_last_candidates"]
@@ -300,6 +301,12 @@ class Context:
 
     def set_counting_tile(self, tile_k):
         self.check(self.lib.obb_set_counting_tile(self.h, int(tile_k)))
+
+    def set_counting_axis(self, axis):
+        """Row axis of the counting kernel: 0 (default) x rows; -1 picks per box
+        the axis with the smallest shadow; 1, 2 force y, z rows (lattices built
+        or rebuilt afterwards keep the y- and z-row copies these need)."""
+        self.check(self.lib.obb_set_counting_axis(self.h, int(axis)))
 
     def tune_counting(self, lat, qboxes):
         """Time the count of these quantised boxes with 8/16/32/64 rows per tile and

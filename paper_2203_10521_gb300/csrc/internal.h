@@ -74,23 +74,19 @@ struct LatticeFrame {
 // j and visits kTileK rows spaced wk apart along z.  Slab a bounds i through
 // quotients by dd_a = |n_a0|; from one visited row to the next the quotient
 // moves by qstep_a with remainder carry rstep_a (an integer DDA).
-struct BoxPrep {
-    int32_t n[9];
-    int32_t i0, span;        // index-space AABB along x: [i0, i0 + span]
-    int32_t j0, k0;          // first row
-    int32_t nj, nk;          // rows along y and z (0 = empty box)
+struct alignas(128) BoxPrep {
+    // read by every tile of the box (first two 128-byte lines) ...
+    const uint64_t* words;   // the box's lattice with rows along `axis`
+    int32_t latN, latW;      // its N and words per row
     int32_t ntj;             // tiles along y: ceil(nj / wj)
     int32_t lwj;             // log2 of wj, the lanes of a tile along y (wk = 32 / wj along z)
-    int32_t mode;            // 2 bits per slab: 0 n_a0 = 0, 1 32-bit DDA, 2 per-row clip
-    int32_t dd[3];           // |n_a0|
-    int32_t rstep[3];        // remainder of that step, in [0, dd)
-    int32_t qstep[3];        // quotient of the step between a lane's rows (|.| < 2^25 for DDA slabs)
-    int32_t lat;             // index of the box's lattice in the launch's lattice table
     int32_t tk;              // rows one lane visits per tile (tiles are wj x wk * tk rows)
-    float rcp[3];            // 1 / dd (seed of the exact initial division)
-    int64_t Lq[3], Hq[3];    // ceil(lo / 256), floor(hi / 256)
-    uint64_t fmul[3];        // floor((2^64 - 1) / dd): remainder -> 32-bit fraction
-    int64_t fstep[3];        // floor(step * 2^32), step = qstep + rstep / dd (32.32 fixed point)
+    int32_t mode;            // 2 bits per slab: 0 n_a0 = 0, 1 32-bit DDA, 2 per-row clip
+    int32_t j0, k0;          // first row
+    int32_t nj, nk;          // rows along y and z (0 = empty box)
+    int32_t i0, span;        // index-space AABB along x: [i0, i0 + span]
+    int32_t axis;            // rows run along index axis 0 (x), 1 (y) or 2 (z); n's columns permuted to match
+    int32_t lat;             // index of the box's lattice in the launch's lattice table
     // Separating axes of the box's shadow on the (j, k) plane: the normals of
     // its three projected edge directions, and the shadow's extent along each,
     // widened by two rows.  A tile whose rectangle lies outside one of these
@@ -102,12 +98,24 @@ struct BoxPrep {
     // (widened by a rounding margin; an unconstraining band has kc_s = 0 and
     // infinite bounds).
     float kc_s[3], kc_lo[3], kc_hi[3];
+    int32_t n[9];
+    int32_t dd[3];           // |n_a0|
+    // ... by the exact seeds of a tile's first row
+    int64_t Lq[3], Hq[3];    // ceil(lo / 256), floor(hi / 256)
+    uint64_t fmul[3];        // floor((2^64 - 1) / dd): remainder -> 32-bit fraction
+    int64_t fstep[3];        // floor(step * 2^32), step = qstep + rstep / dd (32.32 fixed point)
+    // ... and by the general row loop only
+    int32_t rstep[3];        // remainder of that step, in [0, dd)
+    int32_t qstep[3];        // quotient of the step between a lane's rows (|.| < 2^25 for DDA slabs)
+    float rcp[3];            // 1 / dd
 };
 
 // One lattice as the counting kernel sees it (a table of these lets one launch
 // count boxes of many meshes).
 struct LatRef {
-    const uint64_t* words;
+    const uint64_t* words;     // rows along x: row (k, j) at (k N + j) W, bit i
+    const uint64_t* words_y;   // rows along y: row (k, i) at (k N + i) W, bit j
+    const uint64_t* words_z;   // rows along z: row (j, i) at (j N + i) W, bit k
     int32_t N;
     int32_t W;
 };
@@ -143,6 +151,7 @@ struct obb_ctx {
     unsigned int* d_ticket = nullptr; // finish counter of the box-preparation blocks (zero between launches)
     const obbv::CountScratch* count_scratch = nullptr;   // set while a step is being captured
     int32_t tile_k = obbv::kTileK;   // rows per lane per counting tile
+    int32_t count_axis = 0;          // row axis of counted boxes (0: x; -1: per box, the smallest shadow)
     int32_t tile_gen = 0;            // bumped when tile_k changes (captured steps recapture)
     int32_t* h_small = nullptr;      // pinned host staging (512 bytes; the first 64 hold the error word)
     // scratch reused across calls
@@ -172,7 +181,9 @@ struct obb_lattice {
     mutable bool frame_stale = false;      // a rebuild may have moved lo / h since the last copy
     obbv::LatticeFrame* d_frame = nullptr;
     int32_t* d_fixed = nullptr;      // [nv][3] snapped vertices
-    uint64_t* d_words = nullptr;     // occupancy
+    uint64_t* d_words = nullptr;     // occupancy, rows along x
+    uint64_t* d_words_y = nullptr;   // the same bits with rows along y, then z (counting boxes
+    uint64_t* d_words_z = nullptr;   // along their shortest-shadow axis)
     size_t n_words = 0;
     obbv::LatRef ref{};              // host copy of the table entry below
     obbv::LatRef* d_ref = nullptr;   // this lattice as a one-entry table

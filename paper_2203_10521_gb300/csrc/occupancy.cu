@@ -225,6 +225,58 @@ __global__ void __launch_bounds__(32 * kFlipWarps) k_flip_balanced(const int32_t
     }
 }
 
+// 64 x 64 bit transpose across a warp: lane l holds rows l (a) and l + 32 (b);
+// afterwards row c holds at bit r what row r held at bit c.  Six rounds swap
+// the off-diagonal halves of 32-, 16-, ..., 1-bit blocks; below 32 the
+// partner row sits in lane l ^ j.
+__device__ __forceinline__ void transpose64(uint64_t& a, uint64_t& b, int lane)
+{
+    const uint64_t t = ((a >> 32) ^ b) & 0x00000000FFFFFFFFull;
+    b ^= t;
+    a ^= t << 32;
+    const uint64_t masks[5] = {0x0000FFFF0000FFFFull, 0x00FF00FF00FF00FFull, 0x0F0F0F0F0F0F0F0Full,
+                               0x3333333333333333ull, 0x5555555555555555ull};
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int j = 16 >> q;
+        const uint64_t m = masks[q];
+        const uint64_t oa = __shfl_xor_sync(0xffffffffu, a, j), ob = __shfl_xor_sync(0xffffffffu, b, j);
+        if (lane & j) {
+            a ^= ((oa >> j) ^ a) & m;
+            b ^= ((ob >> j) ^ b) & m;
+        } else {
+            a ^= (((a >> j) ^ oa) & m) << j;
+            b ^= (((b >> j) ^ ob) & m) << j;
+        }
+    }
+}
+
+// The occupancy with rows along y (mode 0: slice k, row (k, i), bit j) or
+// along z (mode 1: slice j, row (j, i), bit k), from the rows along x (row
+// (k, j), bit i): one warp per (slice, 64 x 64 block).  Bits of rows past N
+// read as 0; words past ceil(N / 64) are never read by the counting kernel.
+__global__ void k_transpose_rows(const uint64_t* __restrict__ xw, uint64_t* __restrict__ dst, int32_t N, int32_t W,
+                                 int mode)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int32_t nb = (N + 63) >> 6;
+    if (warp >= (int64_t)N * nb * nb) return;
+    const int32_t sl = (int32_t)(warp / ((int64_t)nb * nb));
+    const int32_t rem = (int32_t)(warp % ((int64_t)nb * nb));
+    const int32_t R = rem / nb, C = rem % nb;   // source rows 64 R.., source word C
+    const int32_t r0 = 64 * R + lane, r1 = r0 + 32;
+    auto src_row = [&](int32_t r) -> int64_t {
+        return mode == 0 ? ((int64_t)sl * N + r) * W : ((int64_t)r * N + sl) * W;
+    };
+    uint64_t a = r0 < N ? __ldg(xw + src_row(r0) + C) : 0ull;
+    uint64_t b = r1 < N ? __ldg(xw + src_row(r1) + C) : 0ull;
+    transpose64(a, b, lane);
+    const int32_t c0 = 64 * C + lane, c1 = c0 + 32;
+    if (c0 < N) dst[((int64_t)sl * N + c0) * W + R] = a;
+    if (c1 < N) dst[((int64_t)sl * N + c1) * W + R] = b;
+}
+
 __device__ __forceinline__ uint64_t prefix_xor(uint64_t x)
 {
     x ^= x << 1;
@@ -303,6 +355,24 @@ obb_status rebuild_occupancy(obb_ctx* ctx, obb_lattice* lat)
     int64_t warps = ((int64_t)N * N + rpw - 1) / rpw;
     k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, N, W);
     note_launch(ctx);
+    // rows along y and z: kept once a context counts along them, then refreshed
+    // by every rebuild
+    if (ctx->count_axis != 0 && !lat->d_words_y) {
+        OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words_y, sizeof(uint64_t) * lat->n_words, s));
+        OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words_z, sizeof(uint64_t) * lat->n_words, s));
+        // the transposes never write the padding words past ceil(N / 64): zero them once
+        OBB_CK(ctx, cudaMemsetAsync(lat->d_words_y, 0, sizeof(uint64_t) * lat->n_words, s));
+        OBB_CK(ctx, cudaMemsetAsync(lat->d_words_z, 0, sizeof(uint64_t) * lat->n_words, s));
+        lat->ref.words_y = lat->d_words_y;
+        lat->ref.words_z = lat->d_words_z;
+        OBB_CK(ctx, cudaMemcpyAsync(lat->d_ref, &lat->ref, sizeof(LatRef), cudaMemcpyHostToDevice, s));
+    }
+    if (lat->d_words_y) {
+        const int64_t tb = (N + 63) / 64, tw = (int64_t)N * tb * tb;
+        k_transpose_rows<<<(unsigned)((tw + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_words_y, N, W, 0);
+        k_transpose_rows<<<(unsigned)((tw + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_words_z, N, W, 1);
+        note_launch(ctx, 2);
+    }
     OBB_CK(ctx, cudaGetLastError());
     lat->frame_stale = true;   // the host copy is refreshed when a host reader needs it
     return OBB_OK;
@@ -322,7 +392,7 @@ obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_la
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_fixed, sizeof(int32_t) * 3 * mesh->nv, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words, sizeof(uint64_t) * lat->n_words, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_ref, sizeof(LatRef), s));
-    lat->ref = LatRef{lat->d_words, N, W};
+    lat->ref = LatRef{lat->d_words, nullptr, nullptr, N, W};
     OBB_CK(ctx, cudaMemcpyAsync(lat->d_ref, &lat->ref, sizeof(LatRef), cudaMemcpyHostToDevice, s));
     OBB_TRY(rebuild_occupancy(ctx, lat));
     OBB_TRY(lattice_frame_host(lat));

@@ -147,21 +147,72 @@ __global__ void k_quantize(const obb_box* __restrict__ boxes, int64_t K, const L
 
 // ------------------------------------------------------------------- prep
 
+// The index axis along which a box is counted with the fewest rows: the one
+// whose perpendicular plane receives the box's smallest shadow.  The shadow of
+// the parallelepiped with edges e_a (columns of n^-1 scaled by H_a - L_a) on
+// the plane of axes (s, t) has area sum_{a<b} |e_a,s e_b,t - e_a,t e_b,s|
+// (FP32 from exact cofactors; ties to the lower axis).
+__device__ __forceinline__ int choose_axis(const obb_qbox& q)
+{
+    int64_t m[9];
+    for (int i = 0; i < 9; ++i) m[i] = q.n[i];
+    const int64_t C[9] = {m[4] * m[8] - m[5] * m[7], m[2] * m[7] - m[1] * m[8], m[1] * m[5] - m[2] * m[4],
+                          m[5] * m[6] - m[3] * m[8], m[0] * m[8] - m[2] * m[6], m[2] * m[3] - m[0] * m[5],
+                          m[3] * m[7] - m[4] * m[6], m[1] * m[6] - m[0] * m[7], m[0] * m[4] - m[1] * m[3]};
+    const __int128 det = (__int128)m[0] * C[0] + (__int128)m[1] * C[3] + (__int128)m[2] * C[6];
+    if (det == 0) return 0;
+    const float id = 1.0f / i128_to_float(det);
+    float E[9];   // E[3 r + a]: component r of edge a
+    for (int a = 0; a < 3; ++a) {
+        const float d = i64_to_float((q.b[2 * a + 1] >> kS) - (-((-q.b[2 * a]) >> kS)));
+        for (int r = 0; r < 3; ++r) E[3 * r + a] = i64_to_float(C[3 * r + a]) * id * d;
+    }
+    int best = 0;
+    float best_area = 0.0f;
+    for (int ax = 0; ax < 3; ++ax) {
+        const int u = (ax + 1) % 3, v = (ax + 2) % 3;
+        float area = 0.0f;
+        for (int a = 0; a < 3; ++a)
+            for (int b = a + 1; b < 3; ++b) area += fabsf(E[3 * u + a] * E[3 * v + b] - E[3 * v + a] * E[3 * u + b]);
+        if (ax == 0 || area < best_area) {
+            best = ax;
+            best_area = area;
+        }
+    }
+    return best;
+}
+
 __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int64_t k,
                                         const LatRef* __restrict__ lats, int32_t n_lats,
-                                        const int32_t* __restrict__ lat_of_box, int32_t tile_k,
+                                        const int32_t* __restrict__ lat_of_box, int32_t tile_k, int32_t axis_mode,
                                         BoxPrep* __restrict__ prep, int64_t* __restrict__ tiles, int32_t* err)
 {
     const obb_qbox q = boxes[k];
     BoxPrep p;
+    // count along the chosen axis: the index axes are relabelled (axis, then
+    // the other two in order), which permutes the columns of n; the slab
+    // bounds are unchanged
+    p.axis = 0;
+    {
+        const int32_t li = lat_of_box ? lat_of_box[k] : 0;
+        // a lattice without its y- and z-row copies is counted along x
+        if (axis_mode != 0 && li >= 0 && li < n_lats && lats[li].words_y)
+            p.axis = axis_mode > 0 ? axis_mode : choose_axis(q);
+    }
     p.lat = lat_of_box ? lat_of_box[k] : 0;
     bool bad_lat = p.lat < 0 || p.lat >= n_lats;
     if (bad_lat) {
         atomicOr(err, kErrArg);
         p.lat = 0;
     }
-    const int32_t N = lats[p.lat].N;
-    for (int i = 0; i < 9; ++i) p.n[i] = q.n[i];
+    const LatRef lr = lats[p.lat];
+    const int32_t N = lr.N;
+    p.words = p.axis == 0 ? lr.words : (p.axis == 1 ? lr.words_y : lr.words_z);
+    p.latN = lr.N;
+    p.latW = lr.W;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c)   // new axis c is old axis (axis, the others in order)[c]
+            p.n[3 * a + c] = q.n[3 * a + (c == 0 ? p.axis : (c <= p.axis ? c - 1 : c))];
     bool empty = bad_lat;
     p.mode = 0;
     for (int a = 0; a < 3; ++a) {
@@ -389,7 +440,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
                                                        const int32_t* __restrict__ d_K,
                                                        const LatRef* __restrict__ lats, int32_t n_lats,
                                                        const int32_t* __restrict__ lat_of_box, int32_t tile_k,
-                                                       BoxPrep* __restrict__ prep, int64_t* __restrict__ tiles,
+                                                       int32_t axis_mode, BoxPrep* __restrict__ prep,
+                                                       int64_t* __restrict__ tiles,
                                                        int64_t* __restrict__ off,
                                                        unsigned long long* __restrict__ counts,
                                                        unsigned long long* __restrict__ points,
@@ -400,7 +452,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
     if (k < K) {
         counts[k] = 0;
         if (points) points[k] = 0;
-        k_prep_box(boxes, k, lats, n_lats, lat_of_box, tile_k, prep, tiles, err);
+        k_prep_box(boxes, k, lats, n_lats, lat_of_box, tile_k, axis_mode, prep, tiles, err);
     }
     // the block's writes, then one gpu-scope fence before its ticket
     __shared__ bool last;
@@ -679,7 +731,6 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
 __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                                                const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ d_K,
-                                               const LatRef* __restrict__ lats,
                                                unsigned long long* __restrict__ counts,
                                                unsigned long long* __restrict__ points,
                                                unsigned long long* __restrict__ acc)
@@ -754,9 +805,8 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
             }
         }
 #endif
-        const LatRef lr = lats[p.lat];
-        const uint64_t* __restrict__ words = lr.words;
-        const int32_t N = lr.N, W = lr.W;
+        const uint64_t* __restrict__ words = p.words;
+        const int32_t N = p.latN, W = p.latW;
         const int32_t mode = p.mode;
         const int32_t lwj = p.lwj;
         const int32_t wk = 32 >> lwj;
@@ -1224,7 +1274,7 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
     }
     // the preparation kernel also zeroes counts and points (accumulated with atomics)
     k_prep<<<(unsigned)((K_cap + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
-        d_boxes, d_K, d_lats, n_lats, d_lat_of_box, ctx->tile_k, prep, tiles, off,
+        d_boxes, d_K, d_lats, n_lats, d_lat_of_box, ctx->tile_k, ctx->count_axis, prep, tiles, off,
         reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
         ctx->d_err);
     note_launch(ctx);
@@ -1234,7 +1284,7 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
         OBB_CK(ctx, cudaEventCreate(&e1));
         OBB_CK(ctx, cudaEventRecord(e0, s));
     }
-    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, d_lats,
+    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K,
                                             reinterpret_cast<unsigned long long*>(d_counts),
                                             reinterpret_cast<unsigned long long*>(d_points),
                                             ctx->prof ? ctx->d_prof : nullptr);
@@ -1329,11 +1379,11 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
     note_launch(ctx);
     // the preparation kernel also zeroes counts and points (accumulated with atomics)
     k_prep<<<(unsigned)((K + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
-        d_boxes, dK, lat->d_ref, 1, nullptr, ctx->tile_k, prep, chunks, off,
+        d_boxes, dK, lat->d_ref, 1, nullptr, ctx->tile_k, ctx->count_axis, prep, chunks, off,
         reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
         ctx->d_err);
     note_launch(ctx);
-    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, dK, lat->d_ref,
+    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, dK,
                                             reinterpret_cast<unsigned long long*>(d_counts),
                                             reinterpret_cast<unsigned long long*>(d_points), nullptr);
     note_launch(ctx);

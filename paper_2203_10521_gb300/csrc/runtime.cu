@@ -333,6 +333,8 @@ void obb_lattice_free(obb_lattice* lat)
     if (lat->d_frame) cudaFreeAsync(lat->d_frame, s);
     if (lat->d_fixed) cudaFreeAsync(lat->d_fixed, s);
     if (lat->d_words) cudaFreeAsync(lat->d_words, s);
+    if (lat->d_words_y) cudaFreeAsync(lat->d_words_y, s);
+    if (lat->d_words_z) cudaFreeAsync(lat->d_words_z, s);
     if (lat->d_ref) cudaFreeAsync(lat->d_ref, s);
     delete lat;
 }
@@ -388,6 +390,15 @@ obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qb
                               uint64_t* counts, uint64_t* points, int32_t on_device)
 {
     return outer_volume_impl(ctx, lat, nullptr, boxes, K, counts, points, on_device);
+}
+
+obb_status obb_set_counting_axis(obb_ctx* ctx, int32_t axis)
+{
+    if (!ctx) return OBB_ERR_ARG;
+    if (axis < -1 || axis > 2) return fail(ctx, OBB_ERR_ARG, "axis must be -1 (per box), 0, 1 or 2");
+    if (axis != ctx->count_axis) ++ctx->tile_gen;
+    ctx->count_axis = axis;
+    return OBB_OK;
 }
 
 obb_status obb_set_counting_tile(obb_ctx* ctx, int32_t tile_k)

@@ -183,6 +183,44 @@ def test_outer_volume_edge_cases(ctx, torus_setup):
     assert np.array_equal(ctx.outer_volume(lat, boxes), ref)
 
 
+@pytest.mark.parametrize("name,N", [("torus", 64), ("sdf", 37), ("ico", 100)])
+def test_outer_volume_every_row_axis(ctx, name, N):
+    """The lattice's copies with rows along x, y and z (bit transposes of one
+    occupancy) give the oracle's exact counts on rotated boxes, for every
+    forced row axis and for the per-box choice."""
+    if name == "torus":
+        m = M.torus_4096()
+    elif name == "ico":
+        m = M.icosphere(3, radius=1.0)
+    else:
+        m = M.sdf_union_mesh(5, 24, 6, 3, 0)
+    mesh = ctx.mesh_create(m.verts, m.tris)
+    ctx.set_counting_axis(-1)   # lattices built from now on keep their y- and z-row copies
+    lat = ctx.build_occupancy(mesh, N)
+    P = O.Problem(m.verts, m.tris, N)
+    P.occ.fill_all()
+    rng = np.random.Generator(np.random.PCG64(300 + N))
+    lo, hi = m.verts.min(0), m.verts.max(0)
+    ext = hi - lo
+    boxes = random_boxes(rng, 200, lo - 0.1 * ext, hi + 0.1 * ext, 0.0, 0.45 * float(ext.max()))
+    n, bnd = O.quantize_boxes(boxes, P.lo, P.h)
+    ref, tot = O.outer_volume(P.occ, n, bnd)
+    try:
+        for axis in (0, 1, 2, -1):
+            ctx.set_counting_axis(axis)
+            cnt, pts = ctx.outer_volume(lat, boxes, want_points=True)
+            assert np.array_equal(cnt, ref), axis
+            assert np.array_equal(pts, tot), axis
+        # a rebuild refreshes the copies
+        ctx.set_counting_axis(2)
+        ctx.occupancy_rebuild(lat)
+        assert np.array_equal(ctx.outer_volume(lat, boxes), ref)
+    finally:
+        ctx.set_counting_axis(0)
+    lat.free()
+    mesh.free()
+
+
 def _steep_qboxes():
     """Boxes thousands of rows tall whose third slab is almost parallel to x
     (|n_20| of a few dozen against n_22 = +-2^24): its quotient bounds start far
