@@ -325,11 +325,14 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
                 // neglected term of column a, is below 2e-6 of it).
                 for (int a = 0; a < 3; ++a) {
                     float nj_ = -mi[3 * 2 + a], nk_ = mi[3 * 1 + a];
-                    const float len = sqrtf(nj_ * nj_ + nk_ * nk_);
+                    const float len2 = nj_ * nj_ + nk_ * nk_;
                     const float emax = fmaxf(fabsf(mi[a]), fmaxf(fabsf(mi[3 + a]), fabsf(mi[6 + a])));
-                    if (!(len > 1e-6f * emax)) continue;   // edge parallel to x: no axis
-                    nj_ /= len;
-                    nk_ /= len;
+                    if (!(len2 > 1e-12f * emax * emax)) continue;   // edge parallel to x: no axis
+                    // (only the direction matters: the band below is computed
+                    // with this very normal, whatever its length)
+                    const float il = rsqrtf(len2);
+                    nj_ *= il;
+                    nk_ *= il;
                     float lo = 0.0f, hi = 0.0f, mg = 0.0f;
                     for (int b = 0; b < 3; ++b) {
                         mg = fmaf(fabsf(nj_ * mi[3 * 1 + b]) + fabsf(nk_ * mi[3 * 2 + b]), ym[b], mg);
@@ -349,9 +352,10 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
                     // row plus 1e-5 of the terms' magnitude (above FP32 rounding
                     // here and in the kernel's evaluation)
                     if (fabsf(nj_) <= 64.0f * fabsf(nk_)) {
-                        const float sl = -nj_ / nk_;
-                        const float b0 = (nk_ > 0.0f ? p.sat_lo[a] : p.sat_hi[a]) / nk_;
-                        const float b1 = (nk_ > 0.0f ? p.sat_hi[a] : p.sat_lo[a]) / nk_;
+                        const float ivk = 1.0f / nk_;
+                        const float sl = -nj_ * ivk;
+                        const float b0 = (nk_ > 0.0f ? p.sat_lo[a] : p.sat_hi[a]) * ivk;
+                        const float b1 = (nk_ > 0.0f ? p.sat_hi[a] : p.sat_lo[a]) * ivk;
                         const float fj0 = (float)p.j0, fk0 = (float)p.k0;
                         const float c0 = b0 + sl * fj0 - fk0, c1 = b1 + sl * fj0 - fk0;
                         const float mm = 1.0f + 1e-5f * (fabsf(sl) * (fabsf(fj0) + (float)p.nj) + fabsf(b0) +
@@ -372,9 +376,12 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     int best = 5;
     int64_t best_slots = INT64_MAX;
     if (p.nj > 0) {
+        // ceil(nk / ((32 >> l) tk)) = ceil(ceil(nk / tk) / 2^(5 - l)): one division
+        const int32_t nkt = (p.nk + p.tk - 1) / p.tk;
         for (int l = 5; l >= 0; --l) {
-            const int32_t hk = (32 >> l) * p.tk;
-            const int64_t slots = (int64_t)(((p.nj + (1 << l) - 1) >> l) << l) * (int64_t)(((p.nk + hk - 1) / hk) * hk);
+            const int32_t sh = 5 - l;
+            const int64_t slots = (int64_t)(((p.nj + (1 << l) - 1) >> l) << l) *
+                                  ((int64_t)((nkt + (1 << sh) - 1) >> sh) * ((32 >> l) * p.tk));
             if (slots < best_slots) {
                 best_slots = slots;
                 best = l;
@@ -414,8 +421,14 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
             p.rstep[a] = delta - qs * p.dd[a];
             // the same step in 32.32 fixed point, rounded down (exact division:
             // rstep < dd <= 2^24, so rstep * 2^32 < 2^56)
-            p.fmul[a] = ~0ull / (uint64_t)p.dd[a];
-            p.fstep[a] = (int64_t)qs * 4294967296LL + (int64_t)(((uint64_t)p.rstep[a] << 32) / (uint64_t)p.dd[a]);
+            const uint64_t M = ~0ull / (uint64_t)p.dd[a];
+            p.fmul[a] = M;
+            // floor(rstep 2^32 / dd) through the reciprocal: rstep M / 2^32 is
+            // less than 2^-8 below it, so its floor is exact or one short
+            const uint32_t rs = (uint32_t)p.rstep[a];
+            uint64_t fr = (uint64_t)rs * (uint32_t)(M >> 32) + __umulhi(rs, (uint32_t)M);
+            if ((fr + 1) * (uint64_t)p.dd[a] <= ((uint64_t)rs << 32)) ++fr;
+            p.fstep[a] = (int64_t)qs * 4294967296LL + (int64_t)fr;
         }
     // A quotient saturated at +-2^30 must stay outside [0, span] for a whole
     // tile: its tk - 1 steps of at most |qstep| + 1 each stay below 2^29.  With
