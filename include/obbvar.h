@@ -227,6 +227,16 @@ obb_status obb_set_counting_tile(obb_ctx* ctx, int32_t tile_k);
  * outside -1..2. */
 obb_status obb_set_counting_axis(obb_ctx* ctx, int32_t axis);
 
+/* Test hook for the device-side timeouts.  OBB_INJECT_TC_STALL arms the next
+ * launch of the tensor-core network (surrogate inference) to skip its first
+ * group of MMAs and their commit, so its bounded mbarrier wait (250 ms) gives
+ * up: the kernel sets a device error flag, frees its tensor memory and
+ * returns, and the call reports OBB_ERR_TIMEOUT at its next synchronisation.
+ * Nothing is left in flight and the context stays usable.  One launch only;
+ * OBB_ERR_ARG for unknown bits. */
+#define OBB_INJECT_TC_STALL 1
+obb_status obb_test_inject(obb_ctx* ctx, int32_t flags);
+
 /* Autotuner of the counting kernel: times the outer-volume count of the given
  * quantised boxes with 8, 16, 32 and 64 rows per tile (one warm-up and three
  * timed runs each, CUDA events on the context stream), keeps the fastest for

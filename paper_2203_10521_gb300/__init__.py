@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True):
         "obb_layer_adjust": [vp, vp, C.POINTER(StepOpts), i32, C.POINTER(AdjustStats)],
         "obb_set_counting_tile": [vp, i32],
         "obb_set_counting_axis": [vp, i32],
+        "obb_test_inject": [vp, i32],
         "obb_tune_counting": [vp, vp, vp, i64, i32, vp, vp],
         "obb_unit_step": [vp, vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
         "obb_mlp_create": [vp, C.c_uint64, C.POINTER(vp)],
@@ -171,7 +172,8 @@ def exported_symbols():
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
             "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free", "obb_tree_parents",
             "obb_tree_sweep", "obb_layer_parents", "obb_unit_step", "obb_flood_partition",
-            "obb_layer_adjust", "obb_set_counting_tile", "obb_set_counting_axis", "obb_tune_counting",
+            "obb_layer_adjust", "obb_set_counting_tile", "obb_set_counting_axis", "obb_test_inject",
+            "obb_tune_counting",
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_mlp_forward", "obb_mlp_gradients", "obb_mlp_train_step",
             "obb_layer_set_surrogate", "obb_layer_last_candidates"]
@@ -301,6 +303,11 @@ class Context:
 
     def set_counting_tile(self, tile_k):
         self.check(self.lib.obb_set_counting_tile(self.h, int(tile_k)))
+
+    def test_inject(self, flags):
+        """Arm a one-shot test hook (OBB_INJECT_TC_STALL = 1: the next tensor-core
+        network launch times out on purpose, bounded, and reports it)."""
+        self.check(self.lib.obb_test_inject(self.h, int(flags)))
 
     def set_counting_axis(self, axis):
         """Row axis of the counting kernel: 0 (default) x rows; -1 picks per box

@@ -152,6 +152,7 @@ struct obb_ctx {
     const obbv::CountScratch* count_scratch = nullptr;   // set while a step is being captured
     int32_t tile_k = obbv::kTileK;   // rows per lane per counting tile
     int32_t count_axis = 0;          // row axis of counted boxes (0: x; -1: per box, the smallest shadow)
+    int32_t inject = 0;              // test hooks armed by obb_test_inject (OBB_INJECT_*)
     int32_t tile_gen = 0;            // bumped when tile_k changes (captured steps recapture)
     int32_t* h_small = nullptr;      // pinned host staging (512 bytes; the first 64 hold the error word)
     // scratch reused across calls

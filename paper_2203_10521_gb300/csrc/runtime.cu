@@ -392,6 +392,14 @@ obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qb
     return outer_volume_impl(ctx, lat, nullptr, boxes, K, counts, points, on_device);
 }
 
+obb_status obb_test_inject(obb_ctx* ctx, int32_t flags)
+{
+    if (!ctx) return OBB_ERR_ARG;
+    if (flags & ~OBB_INJECT_TC_STALL) return fail(ctx, OBB_ERR_ARG, "unknown injection flag");
+    ctx->inject = flags;
+    return OBB_OK;
+}
+
 obb_status obb_set_counting_axis(obb_ctx* ctx, int32_t axis)
 {
     if (!ctx) return OBB_ERR_ARG;

@@ -145,7 +145,7 @@ constexpr uint32_t kTcCols = 128;               // TMEM columns (one FP32 accumu
 // instruction descriptor: D = FP32 (bits 4-5), A = B = FP16 (bits 7-12 zero),
 // both K-major (bits 15, 16 zero), N / 8 at bits 17-22, M / 16 at bits 24-28
 constexpr uint32_t kTcIdesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-constexpr uint32_t kTcSpin = 1u << 22;          // try_wait rounds before giving up
+constexpr uint64_t kTcWaitNs = 250000000ull;    // a wait gives up after 250 ms (device global timer)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -180,10 +180,18 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar)
                  : "memory");
 }
 
-// wait for the given phase of the mbarrier; false after kTcSpin rounds
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the given phase of the mbarrier; false once kTcWaitNs have passed
 __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase)
 {
-    for (uint32_t i = 0; i < kTcSpin; ++i) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -192,8 +200,8 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t phase)
             : "r"(smem_addr(bar)), "r"(phase)
             : "memory");
         if (ok) return true;
+        if (global_ns() - t0 > kTcWaitNs) return false;
     }
-    return false;
 }
 
 // 32 consecutive FP32 accumulator columns of this thread's TMEM lane
@@ -259,8 +267,10 @@ constexpr int kTcSmem = 65536 + (4 * kH + 4) * 4;   // A and B tiles, biases, w4
 __global__ void __launch_bounds__(kTcRows) k_mlp_tc(const float* __restrict__ X, int M, const int32_t* __restrict__ d_M,
                                                     const __half* __restrict__ wtc, const __half* __restrict__ wh,
                                                     const float* __restrict__ w, float* __restrict__ y,
-                                                    int32_t* __restrict__ err)
+                                                    int32_t* __restrict__ err, int32_t stall)
 {
+    // stall (test hook): the first MMA group is neither issued nor committed,
+    // so its wait can only give up; nothing is left in flight
     if (d_M) M = min(M, *d_M);
     const int m0 = blockIdx.x * kTcRows;
     if (m0 >= M) return;   // uniform: the whole CTA leaves before any TMEM or barrier use
@@ -319,7 +329,7 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_tc(const float* __restrict__ X,
             ok = false;
             break;
         }
-        if (t == 0) {
+        if (t == 0 && !(stall && q == 0)) {
             tc_fence_after();
 #pragma unroll
             for (int j = 0; j < kTcChunk / 16; ++j)
@@ -605,8 +615,10 @@ static void mlp_forward(obb_ctx* ctx, const MlpImpl* P, const float* X, int B, c
     if (half) {
         // all four layers in one tensor-core kernel (FP16 operands, FP32 accumulators)
         cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+        const int32_t stall = (ctx->inject & OBB_INJECT_TC_STALL) ? 1 : 0;
+        ctx->inject &= ~OBB_INJECT_TC_STALL;   // one launch only
         k_mlp_tc<<<(unsigned)((B + kTcRows - 1) / kTcRows), kTcRows, kTcSmem, ctx->stream>>>(X, B, d_B, P->wtc, P->wh,
-                                                                                           P->w, P->y, ctx->d_err);
+                                                                                           P->w, P->y, ctx->d_err, stall);
         note_launch(ctx);
     } else {
         const float* w = P->w;

@@ -124,3 +124,22 @@ def test_train_and_screen(ctx, torus):
     assert es < ep
     tree.free()
     mlp.free()
+
+
+def test_tensor_core_wait_timeout_is_reported(ctx):
+    """A tensor-core wait that can never complete (the test hook skips the first
+    MMA commit, so nothing is in flight) gives up after its time limit: the call
+    reports OBB_ERR_TIMEOUT and the context stays usable."""
+    import paper_2203_10521_gb300 as PK
+    mlp = ctx.mlp_create(0)
+    p = SP.mlp_params(11)
+    ctx.mlp_set_params(mlp, p)
+    X = SP.features(12, 257)
+    ctx.test_inject(1)
+    with pytest.raises(PK.ObbError) as e:
+        ctx.mlp_forward(mlp, X, half=True)
+    assert e.value.code == -6
+    y_ref, _ = O.mlp_forward(p.astype(np.float64), X.astype(np.float64))
+    y16 = ctx.mlp_forward(mlp, X, half=True)
+    assert np.max(np.abs(y16 - y_ref) / np.maximum(np.abs(y_ref), 1e-3)) <= 2e-2
+    mlp.free()
