@@ -51,6 +51,10 @@
 #ifndef OBB_INT_DIV
 #define OBB_INT_DIV 1
 #endif
+// OBB_BIG_TK_ROWS: boxes with at least this many (j, k) rows use tiles twice as tall (0: off)
+#ifndef OBB_BIG_TK_ROWS
+#define OBB_BIG_TK_ROWS 16384
+#endif
 // OBB_POPC64: count a row in 64-bit words with branch-free end masks
 #ifndef OBB_POPC64
 #define OBB_POPC64 1
@@ -371,6 +375,11 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     // rows per lane per tile: long tiles amortise the exact initial division
     // over more rows (set per context; obb_tune_counting picks it by timing)
     p.tk = tile_k;
+#if OBB_BIG_TK_ROWS
+    // boxes with many rows take tiles twice as tall (fewer tile setups; the
+    // row clipping trims their empty ends)
+    if ((int64_t)p.nj * p.nk >= OBB_BIG_TK_ROWS && 2 * tile_k <= 128) p.tk = 2 * tile_k;
+#endif
     // tile shape: wj lanes along y, wk = 32 / wj along z; the least padding wins
     // (ties to the wider wj, whose rows sit next to each other in memory)
     int best = 5;
