@@ -70,10 +70,11 @@ struct LatticeFrame {
 
 // Per-box data the counting kernel needs, prepared once per box.
 // Rows (j, k) of the box's index-space AABB are cut into tiles of wj rows
-// along y by wk * kTileK rows along z (wj * wk = 32 lanes); each lane owns one
-// j and visits kTileK rows spaced wk apart along z.  Slab a bounds i through
+// along y by wk * tk rows along z (wj * wk = 32 lanes); each lane owns one j
+// and visits tk rows spaced wk apart along z.  Slab a bounds i through
 // quotients by dd_a = |n_a0|; from one visited row to the next the quotient
-// moves by qstep_a with remainder carry rstep_a (an integer DDA).
+// moves by qstep_a with remainder carry rstep_a, or by fstep_a in 32.32 fixed
+// point (an integer DDA either way).
 struct alignas(128) BoxPrep {
     // read by every tile of the box (first two 128-byte lines) ...
     const uint64_t* words;   // the box's lattice with rows along `axis`
@@ -107,7 +108,6 @@ struct alignas(128) BoxPrep {
     // ... and by the general row loop only
     int32_t rstep[3];        // remainder of that step, in [0, dd)
     int32_t qstep[3];        // quotient of the step between a lane's rows (|.| < 2^25 for DDA slabs)
-    float rcp[3];            // 1 / dd
 };
 
 // One lattice as the counting kernel sees it (a table of these lets one launch

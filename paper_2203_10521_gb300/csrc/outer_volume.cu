@@ -2,20 +2,23 @@
 //
 // A box is the integer slab set lo_a <= n_a . (256 p) <= hi_a.  Counting:
 //   prep   per box: index-space bounds Lq = ceil(lo / 256), Hq = floor(hi / 256),
-//          a conservative (j, k) rectangle from the FP64 corners (one-row
-//          margins), the tile shape, the per-row step of each slab's quotient
-//          and three separating axes of the box's shadow on the (j, k) plane;
-//          the last block to finish scans the tile counts into per-box offsets
-//          and clears the work counter;
+//          a conservative (j, k) rectangle (exact integer cofactors, FP32
+//          geometry with explicit margins), the row axis (x unless the context
+//          counts along the axis of the smallest shadow), the tile shape, the
+//          per-row step of each slab's quotient (remainder and 32.32 forms) and
+//          three separating bands of the box's shadow on the (j, k) plane; the
+//          last block to finish scans the tile counts into per-box offsets and
+//          clears the work counter;
 //   count  persistent warps take one tile at a time from the counter: wj (y)
 //          x wk * tk (z) rows of one box, wj * wk = 32 lanes.  A tile outside
-//          the box's shadow is skipped.  Each lane owns one j and walks tk
-//          rows along z: it divides the six slab bounds exactly once per tile
-//          (float seed + int64 correction) and then advances every quotient by
-//          an integer DDA (add the step, carry the remainder), so each row's
-//          exact x-interval costs adds and compares only.  The occupied bits of
-//          the interval are popcounted over 128-bit loads; outer volume =
-//          interval length - occupied bits, and rows or points outside
+//          the box's shadow is skipped and the rows of a tile are clipped to
+//          it.  Each lane owns one j and walks tk rows along z: it divides the
+//          six slab bounds exactly once per tile (integer reciprocal) and then
+//          steps them as 32.32 fixed-point values (boxes whose three slabs are
+//          DDA slabs) or with a remainder carry (the general loop), so each
+//          row's exact x-interval costs adds and compares only.  The occupied
+//          bits of the interval are popcounted over 64-bit words; outer volume
+//          = interval length - occupied bits, and rows or points outside
 //          [0, N)^3 are all empty.
 // Counts are integer sums (warp reduction + one 64-bit atomic per tile), so
 // the result does not depend on scheduling.
@@ -30,64 +33,23 @@
 #ifndef OBB_GRAB
 #define OBB_GRAB 1
 #endif
-// OBB_WARP_SEARCH: find a grabbed tile's box by a 32-way warp search (else binary)
-#ifndef OBB_WARP_SEARCH
-#define OBB_WARP_SEARCH 1
-#endif
 // OBB_COUNT_MINB: resident blocks of the counting kernel per SM the register budget aims at
 #ifndef OBB_COUNT_MINB
 #define OBB_COUNT_MINB 4
-#endif
-// OBB_FIXED_DDA: step DDA bounds as 32.32 fixed-point values (two adds per bound and row)
-#ifndef OBB_FIXED_DDA
-#define OBB_FIXED_DDA 1
-#endif
-// OBB_ROW_CLIP: an all-DDA tile visits only the rows (warp-uniform) that can
-// meet the box's shadow
-#ifndef OBB_ROW_CLIP
-#define OBB_ROW_CLIP 1
-#endif
-// OBB_INT_DIV: exact divisions of the counting kernel by integer reciprocal
-#ifndef OBB_INT_DIV
-#define OBB_INT_DIV 1
 #endif
 // OBB_BIG_TK_ROWS: boxes with at least this many (j, k) rows use tiles twice as tall (0: off)
 #ifndef OBB_BIG_TK_ROWS
 #define OBB_BIG_TK_ROWS 16384
 #endif
-// OBB_POPC64: count a row in 64-bit words with branch-free end masks
-#ifndef OBB_POPC64
-#define OBB_POPC64 1
-#endif
-// OBB_POPC_ILP: load a row's chunks up front / in groups of four
-#ifndef OBB_POPC_ILP
-#define OBB_POPC_ILP 1
-#endif
-// OBB_INTERIOR: a row loop without clamps for full-height tiles of boxes inside the lattice
-#ifndef OBB_INTERIOR
-#define OBB_INTERIOR 1
-#endif
-// OBB_DERIVED_QB: in that loop, derive each slab's upper quotient from its lower one
-#ifndef OBB_DERIVED_QB
-#define OBB_DERIVED_QB 1
-#endif
-// OBB_FAST_DDA: a row loop without per-slab dispatch for boxes whose three slabs all step by DDA
-#ifndef OBB_FAST_DDA
-#define OBB_FAST_DDA 1
-#endif
 // OBB_ROW_MARGIN: rows added on each side of a box's (j, k) bounding rectangle
 #ifndef OBB_ROW_MARGIN
 #define OBB_ROW_MARGIN 1
-#endif
-// OBB_TILE_SKIP: skip tiles that miss the box's shadow on the (j, k) plane
-#ifndef OBB_TILE_SKIP
-#define OBB_TILE_SKIP 1
 #endif
 namespace obbv {
 // tuning parameters: unroll factor of the counting kernel's row loop, tiles per work grab
 constexpr int kCountUnroll = OBB_COUNT_UNROLL;
 constexpr int kRowMargin = OBB_ROW_MARGIN;
-constexpr int kPrepThreads = 32;   // one warp per preparation block: its FP64 work spreads over many SMs
+constexpr int kPrepThreads = 32;   // one warp per preparation block: its per-box work spreads over many SMs
 constexpr int kGrab = OBB_GRAB;
 }  // namespace obbv
 
@@ -225,7 +187,6 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
         empty |= p.Lq[a] > p.Hq[a];
         const int32_t d = p.n[3 * a];
         p.dd[a] = d >= 0 ? d : -d;
-        p.rcp[a] = d != 0 ? 1.0f / (float)p.dd[a] : 0.0f;
         p.qstep[a] = 0;
         p.rstep[a] = 0;
         p.fmul[a] = 0;
@@ -402,20 +363,6 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     if (p.nj > 0 && p.i0 >= 0 && p.i0 + p.span <= N - 1 && p.j0 >= 0 && p.j0 + p.nj <= N && p.k0 >= 0 &&
         p.k0 + p.nk <= N)
         p.mode |= 1 << 8;
-    // every quotient of every slab stays within 2^29 of i0 over the box's
-    // rectangle: no saturation, so a slab's upper quotient follows from its
-    // lower one (see k_count)
-    if (p.nj > 0 && (p.mode & 0x3f) == 0x15) {
-        bool small = true;
-        for (int a = 0; a < 3; ++a) {
-            // FP32 with a 1e-4 relative margin (far above its rounding)
-            const float reach = fabsf(i64_to_float(p.Lq[a])) + fabsf(i64_to_float(p.Hq[a])) +
-                                fabsf((float)p.n[3 * a + 1]) * (fabsf((float)p.j0) + (float)p.nj) +
-                                fabsf((float)p.n[3 * a + 2]) * (fabsf((float)p.k0) + (float)p.nk);
-            small &= reach * 1.0001f < (536870912.0f - fabsf((float)p.i0) - (float)p.span - 2.0f) * (float)p.dd[a];
-        }
-        if (small) p.mode |= 1 << 9;
-    }
     p.lwj = best;
     const int32_t wj = 1 << best, wk = 32 >> best;
     p.ntj = p.nj > 0 ? (p.nj + wj - 1) / wj : 0;
@@ -554,27 +501,6 @@ __global__ void k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__
 
 // ------------------------------------------------------------------ count
 
-// Exact floor division of a signed int64 by 0 < d < 2^31: a float seed, one
-// float refinement of the remainder, then at most a couple of unit fixes.
-[[maybe_unused]] __device__ __forceinline__ void floordiv_exact(int64_t x, int32_t d, float rcp, int64_t& q, int32_t& r)
-{
-    int64_t q0 = __float2ll_rd(__ll2float_rn(x) * rcp);
-    int64_t rem = x - q0 * (int64_t)d;
-    int64_t q1 = __float2ll_rd(__ll2float_rn(rem) * rcp);
-    q0 += q1;
-    rem -= q1 * (int64_t)d;
-    while (rem < 0) {
-        rem += d;
-        --q0;
-    }
-    while (rem >= d) {
-        rem -= d;
-        ++q0;
-    }
-    q = q0;
-    r = (int32_t)rem;
-}
-
 // 32.32 fixed-point DDA.  A slab bound floor(v), v = q + r / dd, is carried as
 // A = q 2^32 + floor(r M / 2^32) + kFixBias with M = floor((2^64 - 1) / dd),
 // and steps by floor(s 2^32) per row (s the exact rational step).  The seed is
@@ -635,41 +561,7 @@ __device__ __forceinline__ void clip_slab_rcp(int32_t d, uint64_t M, int64_t c, 
     hi = (int32_t)u;
 }
 
-// Intersect [lo, hi] with { i : L <= d i + c <= H } exactly (d != 0): float
-// estimates of the two quotients, clamped to [lo - 1, hi + 1] and corrected
-// with exact int64 products.  Used per row for slabs almost parallel to x.
-[[maybe_unused]] __device__ __forceinline__ void clip_slab(int32_t d, float rcp, int64_t c, int64_t L, int64_t H, int32_t& lo,
-                                          int32_t& hi)
-{
-    int64_t A, B, dd;
-    float r;
-    if (d > 0) {
-        A = L - c;
-        B = H - c;
-        dd = d;
-        r = rcp;
-    } else {
-        A = c - H;
-        B = c - L;
-        dd = -(int64_t)d;
-        r = rcp;
-    }
-    // g = max(ceil(A / dd), lo), capped at hi + 1
-    float fl = fminf(fmaxf(ceilf(__ll2float_rn(A) * r), (float)lo), (float)hi + 1.0f);
-    int32_t g = (int32_t)fl;
-    while (g > lo && (int64_t)(g - 1) * dd >= A) --g;
-    while (g <= hi && (int64_t)g * dd < A) ++g;
-    // u = min(floor(B / dd), hi), floored at lo - 1
-    float fu = fminf(fmaxf(floorf(__ll2float_rn(B) * r), (float)lo - 1.0f), (float)hi);
-    int32_t u = (int32_t)fu;
-    while (u < hi && (int64_t)(u + 1) * dd <= B) ++u;
-    while (u >= lo && (int64_t)u * dd > B) --u;
-    lo = g;
-    hi = u;
-}
-
 // popcount of the occupied bits i in [a, e] of one row (0 <= a <= e < N)
-#if OBB_POPC64
 // 64-bit words: the first and last word carry the masks (merged without a
 // branch when they are the same word), interior words count whole.
 __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
@@ -685,65 +577,6 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
     mlo = one ? (mlo & mhi) : mlo;
     return cnt + __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
 }
-#elif OBB_POPC_ILP
-// The first and last 128-bit chunks are loaded up front and the interior in
-// groups of four independent loads, so a long row waits for one or two L2
-// round trips instead of one per chunk.
-__device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
-{
-    const uint4* r4 = reinterpret_cast<const uint4*>(row);
-    const int32_t q0 = a >> 7, q1 = e >> 7;
-    const uint32_t la = a & 127, he = e & 127;
-    const uint4 f = __ldg(r4 + q0);
-    const uint4 l = __ldg(r4 + q1);
-    uint32_t cnt = 0;
-    for (int32_t qq = q0 + 1; qq < q1; qq += 4) {
-        uint4 v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = qq + i < q1 ? __ldg(r4 + qq + i) : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) cnt += __popc(v[i].x) + __popc(v[i].y) + __popc(v[i].z) + __popc(v[i].w);
-    }
-    // keep bits >= la of the first chunk and bits <= he of the last
-    uint64_t m0 = la < 64 ? (~0ull << la) : 0ull;
-    uint64_t m1 = la < 64 ? ~0ull : (~0ull << (la - 64));
-    const uint64_t n0 = he >= 63 ? ~0ull : (~0ull >> (63 - he));
-    const uint64_t n1 = he < 64 ? 0ull : (he >= 127 ? ~0ull : (~0ull >> (127 - he)));
-    const uint64_t f0 = ((uint64_t)f.y << 32) | f.x, f1 = ((uint64_t)f.w << 32) | f.z;
-    if (q0 == q1) return __popcll(f0 & m0 & n0) + __popcll(f1 & m1 & n1);
-    const uint64_t l0 = ((uint64_t)l.y << 32) | l.x, l1 = ((uint64_t)l.w << 32) | l.z;
-    return cnt + __popcll(f0 & m0) + __popcll(f1 & m1) + __popcll(l0 & n0) + __popcll(l1 & n1);
-}
-#else
-__device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
-{
-    const uint4* r4 = reinterpret_cast<const uint4*>(row);
-    const int32_t q0 = a >> 7, q1 = e >> 7;
-    // first and last 128-bit chunks carry masks; interior chunks count whole
-    const uint32_t la = a & 127, he = e & 127;
-    uint4 v = __ldg(r4 + q0);
-    uint64_t w0 = ((uint64_t)v.y << 32) | v.x, w1 = ((uint64_t)v.w << 32) | v.z;
-    // keep bits >= la of the first chunk
-    uint64_t m0 = la < 64 ? (~0ull << la) : 0ull;
-    uint64_t m1 = la < 64 ? ~0ull : (~0ull << (la - 64));
-    if (q0 == q1) {
-        m0 &= he >= 63 ? ~0ull : (~0ull >> (63 - he));
-        m1 &= he < 64 ? 0ull : (he >= 127 ? ~0ull : (~0ull >> (127 - he)));
-        return __popcll(w0 & m0) + __popcll(w1 & m1);
-    }
-    uint32_t cnt = __popcll(w0 & m0) + __popcll(w1 & m1);
-    for (int32_t qq = q0 + 1; qq < q1; ++qq) {
-        v = __ldg(r4 + qq);
-        cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-    }
-    v = __ldg(r4 + q1);
-    w0 = ((uint64_t)v.y << 32) | v.x;
-    w1 = ((uint64_t)v.w << 32) | v.z;
-    m0 = he >= 63 ? ~0ull : (~0ull >> (63 - he));
-    m1 = he < 64 ? 0ull : (he >= 127 ? ~0ull : (~0ull >> (127 - he)));
-    return cnt + __popcll(w0 & m0) + __popcll(w1 & m1);
-}
-#endif
 
 #if OBB_COUNT_MINB > 0
 #define OBB_COUNT_BOUNDS __launch_bounds__(256, OBB_COUNT_MINB)
@@ -773,7 +606,6 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
             c = (int64_t)__shfl_sync(0xffffffffu, g, 0);
             if (c >= total) break;
             c_end = min(c + (int64_t)kGrab, total);
-#if OBB_WARP_SEARCH
             // the last box b with off[b] <= c: a 32-way search, one probe per lane
             int32_t lo = 0, hi = K;   // off[lo] <= c < off[hi]
             while (hi - lo > 1) {
@@ -783,14 +615,6 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 lo += (31 - __clz(m)) * st;
                 hi = min(hi, lo + st);
             }
-#else
-            int32_t lo = 0, hi = K - 1;
-            while (lo < hi) {
-                int32_t mid = (lo + hi + 1) >> 1;
-                if (off[mid] <= c) lo = mid;
-                else hi = mid - 1;
-            }
-#endif
             b = lo;
             box_end = off[b + 1];
             const int32_t u = (int32_t)(c - off[b]);
@@ -804,7 +628,6 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
             tj = tk = 0;
         }
         const BoxPrep& p = prep[b];
-#if OBB_TILE_SKIP
         {
             // skip a tile whose rectangle misses the box's shadow on (j, k)
             const int32_t lw = p.lwj, hk = (32 >> lw) * p.tk;
@@ -826,7 +649,6 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 continue;
             }
         }
-#endif
         const uint64_t* __restrict__ words = p.words;
         const int32_t N = p.latN, W = p.latW;
         const int32_t mode = p.mode;
@@ -840,7 +662,6 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         const int32_t kend = p.k0 + p.nk;
         // rows r0..r1 (warp-uniform) of the tile's tkr are visited
         int32_t r0 = 0, r1 = tkr - 1;
-#if OBB_ROW_CLIP && OBB_FIXED_DDA && OBB_FAST_DDA
         if ((mode & 0xff) == 0x15) {
             // each lane's column meets the shadow in a k-range (the separating
             // bands solved for k); the warp visits the union of its lanes'
@@ -876,7 +697,6 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 continue;
             }
         }
-#endif
         const int32_t kb0 = kb + r0 * wk;   // the first row this lane visits
         const int32_t i0 = p.i0, span = p.span;
         // Kind-1 slabs carry exact quotient bounds relative to i0 in 32 bits,
@@ -896,13 +716,8 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 const int64_t xlo = p.n[3 * a] > 0 ? p.Lq[a] - cc : cc - p.Hq[a];
                 const int64_t xhi = p.n[3 * a] > 0 ? p.Hq[a] - cc : cc - p.Lq[a];
                 int64_t wlo, whi;
-#if OBB_INT_DIV
                 floordiv_rcp(xlo + dd[a] - 1, dd[a], p.fmul[a], wlo, ra[a]);   // ceil(xlo / dd)
                 floordiv_rcp(xhi, dd[a], p.fmul[a], whi, rb[a]);               // floor(xhi / dd)
-#else
-                floordiv_exact(xlo + dd[a] - 1, dd[a], p.rcp[a], wlo, ra[a]);   // ceil(xlo / dd)
-                floordiv_exact(xhi, dd[a], p.rcp[a], whi, rb[a]);               // floor(xhi / dd)
-#endif
                 const int64_t lim = int64_t(1) << 30;
                 qa[a] = (int32_t)min(max(wlo - i0, -lim), lim);
                 qb[a] = (int32_t)min(max(whi - i0, -lim), lim);
@@ -910,7 +725,6 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         }
         uint32_t empty = 0, inbox = 0;
         const bool jin = j >= 0 && j < N;
-#if OBB_FAST_DDA && OBB_FIXED_DDA
         if ((mode & 0xff) == 0x15) {
             // all three slabs step by DDA (any rotated box): each of the six
             // bounds is a 32.32 fixed-point value whose integer part is the
@@ -976,130 +790,6 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 }
             }
         } else
-#elif OBB_FAST_DDA
-#if OBB_INTERIOR && OBB_DERIVED_QB
-        if ((mode & 0x3ff) == 0x315 && (tk + 1) * wk * tkr <= p.nk) {
-            // as below, and no quotient saturates: with D = Hq - Lq = Dq dd + Dr,
-            // the upper quotient is qa + Dq - (ra < dd - 1 - Dr), so only the
-            // lower one steps
-            int32_t Dq[3], Tq[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                int64_t q;
-                int32_t r;
-                floordiv_exact(p.Hq[a] - p.Lq[a], dd[a], p.rcp[a], q, r);
-                Dq[a] = (int32_t)q;
-                Tq[a] = dd[a] - 1 - r;
-            }
-            const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
-            const int64_t rstride = (int64_t)wk * N * W;
-            const int32_t spanl = jvalid ? span : -1;
-#pragma unroll kCountUnroll
-            for (int r = 0; r < tkr; ++r, rowp += rstride) {
-                const int32_t lo = max(max(qa[0], qa[1]), max(qa[2], 0));
-                const int32_t b0 = qa[0] + Dq[0] - (ra[0] < Tq[0]);
-                const int32_t b1 = qa[1] + Dq[1] - (ra[1] < Tq[1]);
-                const int32_t b2 = qa[2] + Dq[2] - (ra[2] < Tq[2]);
-                const int32_t hi = min(min(b0, b1), min(b2, spanl));
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    qa[a] += qs[a];
-                    ra[a] += rs[a];
-                    if (ra[a] >= dd[a]) {
-                        ra[a] -= dd[a];
-                        qa[a] += 1;
-                    }
-                }
-                if (lo <= hi) {
-                    const int32_t a = i0 + lo, e = i0 + hi;
-                    const uint32_t len = (uint32_t)(hi - lo + 1);
-                    empty += len - popc_range(rowp, a, e);
-                    inbox += len;
-                    my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
-                    my_rows += 1;
-                }
-            }
-        } else
-#endif
-#if OBB_INTERIOR
-        if ((mode & 0x1ff) == 0x115 && (tk + 1) * wk * tkr <= p.nk) {
-            // an interior box's full-height tile: every row is in the lattice
-            // and so is every x-interval; an idle lane gets an empty range
-            const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
-            const int64_t rstride = (int64_t)wk * N * W;
-            const int32_t spanl = jvalid ? span : -1;
-#pragma unroll kCountUnroll
-            for (int r = 0; r < tkr; ++r, rowp += rstride) {
-                const int32_t lo = max(max(qa[0], qa[1]), max(qa[2], 0));
-                const int32_t hi = min(min(qb[0], qb[1]), min(qb[2], spanl));
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    qa[a] += qs[a];
-                    ra[a] += rs[a];
-                    if (ra[a] >= dd[a]) {
-                        ra[a] -= dd[a];
-                        qa[a] += 1;
-                    }
-                    qb[a] += qs[a];
-                    rb[a] += rs[a];
-                    if (rb[a] >= dd[a]) {
-                        rb[a] -= dd[a];
-                        qb[a] += 1;
-                    }
-                }
-                if (lo <= hi) {
-                    const int32_t a = i0 + lo, e = i0 + hi;
-                    const uint32_t len = (uint32_t)(hi - lo + 1);
-                    empty += len - popc_range(rowp, a, e);
-                    inbox += len;
-                    my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
-                    my_rows += 1;
-                }
-            }
-        } else
-#endif
-        if ((mode & 0xff) == 0x15) {
-            // all three slabs step by 32-bit DDA (any rotated box): no per-row
-            // slab dispatch, and the row pointer advances by a fixed stride
-            const uint64_t* rowp = words + ((int64_t)kb * N + j) * W;
-            const int64_t rstride = (int64_t)wk * N * W;
-            int32_t k = kb;
-#pragma unroll kCountUnroll
-            for (int r = 0; r < tkr; ++r, k += wk, rowp += rstride) {
-                const int32_t lo = max(max(qa[0], qa[1]), max(qa[2], 0));
-                const int32_t hi = min(min(qb[0], qb[1]), min(qb[2], span));
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    qa[a] += qs[a];
-                    ra[a] += rs[a];
-                    if (ra[a] >= dd[a]) {
-                        ra[a] -= dd[a];
-                        qa[a] += 1;
-                    }
-                    qb[a] += qs[a];
-                    rb[a] += rs[a];
-                    if (rb[a] >= dd[a]) {
-                        rb[a] -= dd[a];
-                        qb[a] += 1;
-                    }
-                }
-                if (jvalid && k < kend && lo <= hi) {
-                    const uint32_t len = (uint32_t)(hi - lo + 1);
-                    uint32_t occ = 0;
-                    if (jin && (uint32_t)k < (uint32_t)N) {
-                        const int32_t a = max(i0 + lo, 0), e = min(i0 + hi, N - 1);
-                        if (a <= e) {
-                            occ = popc_range(rowp, a, e);
-                            my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
-                        }
-                    }
-                    empty += len - occ;
-                    inbox += len;
-                    my_rows += 1;
-                }
-            }
-        } else
-#endif
 #pragma unroll kCountUnroll
         for (int r = 0; r < tkr; ++r) {
             const int32_t k = kb + r * wk;
@@ -1129,11 +819,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                         ok = cc >= p.Lq[a] && cc <= p.Hq[a];
                     } else {
                         int32_t l2 = i0 + lo, h2 = i0 + hi;
-#if OBB_INT_DIV
                         clip_slab_rcp(p.n[3 * a], p.fmul[a], cc, p.Lq[a], p.Hq[a], l2, h2);
-#else
-                        clip_slab(p.n[3 * a], p.rcp[a], cc, p.Lq[a], p.Hq[a], l2, h2);
-#endif
                         lo = l2 - i0;
                         hi = h2 - i0;
                     }
