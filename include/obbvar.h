@@ -189,7 +189,7 @@ obb_status obb_outer_volume_q(obb_ctx* ctx, const obb_lattice* lat, const obb_qb
  * Results equal obb_outer_volume_q's.  boxes, counts and points (optional)
  * are device arrays the caller provides; K <= OBB_NOALLOC_MAX_BOXES, larger K
  * is rejected with OBB_ERR_RANGE.  The per-box scratch lives in one fixed
- * device array inside the library (under 1 MB), held by every GPU that
+ * device array inside the library (about 1.6 MB), held by every GPU that
  * loads the library until the process exits.  The first call on a device
  * looks up that array's device address; make that first call before any
  * stream capture.  All calls share the array and it keeps the last call's
