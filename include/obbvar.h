@@ -103,7 +103,8 @@ const char* obb_last_error(const obb_ctx* ctx);
 /* Instrumentation.  `launches` counts every kernel this context has enqueued
  * (library kernels and the radix-sort kernels compiled into the library).
  * With profiling enabled, each launch of the outer-volume counting kernel is
- * bracketed by CUDA events on the context stream and the kernel adds up its
+ * bracketed by CUDA events on the context stream (launches inside a Lloyd
+ * iteration run as a CUDA graph are not) and the kernel adds up its
  * algorithmic traffic (16 bytes per 128-bit occupancy chunk that a box row's
  * x-interval touches inside the lattice) and the rows with a non-empty
  * interval.  obb_profile_enable resets the totals; obb_profile_read
@@ -487,13 +488,17 @@ void obb_tree_free(obb_tree* tree);
  * (H_a - L_a) / (2 |n_a|) / N (3), then an 8^3 patch of occupancy bits sampled
  * at the points M^-1 v, v_a = L_a + (H_a - L_a)(2 s_a + 1) / 16 (x fastest),
  * rounded to the nearest lattice point (0 outside [0, N)^3); L = ceil(lo/256),
- * H = floor(hi/256), M = n; FP64 in a fixed order.
+ * H = floor(hi/256), M = n.  Arithmetic: the exact integer adjugate and
+ * determinant of n, then FP32 with one rounding per operation in a fixed
+ * order (centre plus edge vectors times (2 s_a - 7) / 16), so the features are
+ * reproducible bit for bit.
  * Network: 524 -> 128 -> 128 -> 128 -> 1, ReLU, sigmoid output = predicted
  * empty fraction; predicted outer volume = fraction x prod(H_a - L_a + 1) /
  * |det n|.  Parameters (flat float32, obb_mlp_num_params()): W1 [524][128],
  * b1, W2 [128][128], b2, W3 [128][128], b3, W4 [128][1], b4.  Training: mean
  * squared error of the fraction, Adam (0.9, 0.999, 1e-8) on FP32 master
- * weights; inference with half_weights uses an FP16 copy, FP32 accumulation. */
+ * weights; inference with half_weights uses FP16 weights and activations on
+ * the tensor cores with FP32 accumulation (the screening path). */
 #define OBB_SURROGATE_INPUTS 524
 obb_status obb_mlp_create(obb_ctx* ctx, uint64_t seed, obb_mlp** out);
 void obb_mlp_free(obb_mlp* mlp);
