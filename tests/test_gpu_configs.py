@@ -123,3 +123,37 @@ def test_sweeps_at_scale(ctx):
     tree.free()
     lat.free()
     mesh.free()
+
+
+def test_benchmark_batch_invariant_at_scale(ctx):
+    """The benchmark's batch at full size: the 2,047 boxes of a depth-10 tree on
+    the ~200k-triangle union at 512^3 (up to the whole lattice, so large boxes
+    take the doubled tile height) count the same, box by box, for every tile
+    height, for rows along each axis and for the per-box axis; leaf boxes of
+    this tree are checked against the oracle in test_sweeps_at_scale."""
+    m = M.sdf_union_200k()
+    mesh = ctx.mesh_create(m.verts, m.tris)
+    try:
+        ctx.set_counting_axis(-1)   # this lattice keeps its y- and z-row copies
+        lat = ctx.build_occupancy(mesh, 512)
+        ctx.set_counting_axis(0)
+        tree = ctx.build_tree(lat, 10, 1)
+        q = np.concatenate([ctx.tree_read(tree, lev)["qboxes"] for lev in range(11)])
+        assert len(q) == 2047
+        base, bpts = ctx.outer_volume_q(lat, q, want_points=True)
+        assert (bpts > 0).all() and (base <= bpts).all()
+        for tk in (8, 16, 64):
+            ctx.set_counting_tile(tk)
+            c, p = ctx.outer_volume_q(lat, q, want_points=True)
+            assert np.array_equal(c, base) and np.array_equal(p, bpts), tk
+        ctx.set_counting_tile(32)
+        for axis in (1, 2, -1):
+            ctx.set_counting_axis(axis)
+            c, p = ctx.outer_volume_q(lat, q, want_points=True)
+            assert np.array_equal(c, base) and np.array_equal(p, bpts), axis
+    finally:
+        ctx.set_counting_axis(0)
+        ctx.set_counting_tile(32)
+    tree.free()
+    lat.free()
+    mesh.free()
