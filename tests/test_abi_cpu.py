@@ -59,3 +59,49 @@ def test_product_never_imports_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "obb_oracle" not in text and "orc_" not in text, f
+
+
+def _prototypes():
+    """(return type, name, [parameter types]) of every function the header declares."""
+    src = open(os.path.join(ROOT, "include", "obbvar.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"^\s*#[^\n]*", "", src, flags=re.M)
+    out = []
+    for ret, name, params in re.findall(r"([A-Za-z_][\w\s\*]*?)\b(obb_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", src):
+        ps = [] if params.strip() in ("", "void") else [" ".join(p.split()) for p in params.split(",")]
+        out.append((" ".join(ret.split()), name, ps))
+    return out
+
+
+def _ctype_of(decl):
+    """The ctypes class a C parameter or return declaration marshals as ('ptr' for any pointer)."""
+    if "*" in decl or "[" in decl:
+        return "ptr"
+    base = decl.replace("const ", "").split()[0]
+    return {"obb_status": ctypes.c_int32, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64,
+            "uint64_t": ctypes.c_uint64, "float": ctypes.c_float, "double": ctypes.c_double,
+            "void": None}[base]
+
+
+def _same(expected, actual):
+    if expected == "ptr":
+        return actual is ctypes.c_void_p or actual is ctypes.c_char_p or (
+            isinstance(actual, type) and issubclass(actual, ctypes._Pointer))
+    return actual is expected
+
+
+def test_binding_signatures_match_header():
+    """Every ctypes signature in the binding has the header's arity, integer widths and return type, so
+    no argument is marshalled at the wrong width."""
+    import paper_2203_10521_gb300 as P
+    L = P.load()
+    protos = _prototypes()
+    assert sorted(n for _, n, _ in protos) == sorted(P.exported_symbols())
+    for ret, name, params in protos:
+        f = getattr(L, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == len(params), (name, params, f.argtypes)
+        for p, a in zip(params, f.argtypes):
+            assert _same(_ctype_of(p), a), (name, p, a)
+        assert _same(_ctype_of(ret), f.restype), (name, ret, f.restype)
