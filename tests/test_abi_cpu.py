@@ -105,3 +105,47 @@ def test_binding_signatures_match_header():
         for p, a in zip(params, f.argtypes):
             assert _same(_ctype_of(p), a), (name, p, a)
         assert _same(_ctype_of(ret), f.restype), (name, ret, f.restype)
+
+
+def test_struct_offsets_and_status_codes_match_compiled_header(tmp_path):
+    """A C program compiled against the header prints sizeof and every field offset of the public structs
+    and the status codes; the binding's ctypes structures and numpy dtypes must agree field by field (a
+    field the binding names that the header lacks fails the compile)."""
+    import shutil
+    import subprocess
+    import paper_2203_10521_gb300 as P
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    ctypes_structs = {"obb_step_opts": P.StepOpts, "obb_step_stats": P.StepStats,
+                      "obb_profile_stats": P.ProfileStats, "obb_tree_opts": P.TreeOpts,
+                      "obb_flood_stats": P.FloodStats, "obb_adjust_stats": P.AdjustStats,
+                      "obb_sweep_opts": P.SweepOpts, "obb_sweep_stats": P.SweepStats}
+    dtypes = {"obb_box": P.BOX_DTYPE, "obb_qbox": P.QBOX_DTYPE}
+    expect, lines = {}, []
+    for cname, S in ctypes_structs.items():
+        expect[f"{cname} size"] = ctypes.sizeof(S)
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in S._fields_:
+            expect[f"{cname} {f}"] = getattr(S, f).offset
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    for cname, dt in dtypes.items():
+        expect[f"{cname} size"] = dt.itemsize
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in dt.names:
+            expect[f"{cname} {f}"] = dt.fields[f][1]
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    for code, name in list(P._ERRORS.items()) + [(P.OBB_OK, "OBB_OK")]:
+        expect[f"{name} value"] = code
+        lines.append(f'printf("{name} value %d\\n", (int){name});')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "obbvar.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                    "-o", str(exe)], check=True, capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        key, val = line.rsplit(" ", 1)
+        got[key] = int(val)
+    assert got == expect
