@@ -177,3 +177,42 @@ def test_quantize_rejects_bad_boxes():
     bad[0, 9] = np.nan
     with pytest.raises(ValueError):
         O.quantize_boxes(bad, P.lo, P.h)
+
+
+def _axis_box(lo, h, a, b):
+    """FP32 axis-aligned box whose faces sit at lo + a h and lo + b h (per axis)."""
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    c = lo + 0.5 * (a + b) * h
+    half = 0.5 * (b - a) * h
+    box = np.concatenate([c, [1, 0, 0], [0, 1, 0], half]).astype(np.float32)
+    assert np.array_equal(box.astype(np.float64)[[0, 1, 2, 9, 10, 11]], np.concatenate([c, half]))
+    return box
+
+
+def test_axis_aligned_box_counts_closed_form_on_anisotropic_lattice():
+    """Axis-aligned FP32 boxes on an anisotropic lattice (h = 1/16, 1/32, 1/64; every value dyadic, so
+    the quantisation is exact).  Lattice point i sits at lo + (i + 1/2) h (R1), so a box with faces at
+    lo + a h and lo + b h holds the indices a..b-1 per axis, and a face through lattice points
+    (a = i + 1/2) keeps them (closed box, R7).  The cube mesh fills every in-domain point, so the outer
+    volume is exactly the box's points outside [0, N)^3 (R2).  A transposed or inverted h_b / h_max scale
+    in the normals, an open box or a half-cell offset in the snap changes these products."""
+    m = M.cube((0, 0, 0), (4.0, 2.0, 1.0))
+    N = 64
+    P = O.Problem(m.verts, m.tris, N)
+    assert np.array_equal(P.h, [1 / 16, 1 / 32, 1 / 64]) and np.array_equal(P.lo, [0, 0, 0])
+    n, _ = O.quantize_boxes(_axis_box(P.lo, P.h, [1, 1, 1], [2, 2, 2])[None], P.lo, P.h)
+    assert np.array_equal(n[0], [2 ** 24, 0, 0, 0, 2 ** 23, 0, 0, 0, 2 ** 22])
+    cases = [([3, 5, 7], [10, 9, 40]),          # inside the domain: no outer volume
+             ([-4, 2, 60], [5, 70, 71]),        # poking out on three sides
+             ([-9, -3, -7], [-1, -1, -2]),      # entirely outside
+             ([2.5, 0.5, 10.5], [6.5, 3.5, 12.5])]  # faces through lattice points: closed
+    for a, b in cases:
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        qn, bnd = O.quantize_boxes(_axis_box(P.lo, P.h, a, b)[None], P.lo, P.h)
+        cnt, tot = O.outer_volume(P.occ, qn, bnd)
+        first = np.ceil(a - 0.5).astype(np.int64)       # smallest i with i + 1/2 >= a
+        last = np.floor(b - 0.5).astype(np.int64)       # largest i with i + 1/2 <= b
+        ext = np.maximum(last - first + 1, 0)
+        indom = np.maximum(np.minimum(last, N - 1) - np.maximum(first, 0) + 1, 0)
+        assert int(tot[0]) == int(np.prod(ext)), (a, b)
+        assert int(cnt[0]) == int(np.prod(ext)) - int(np.prod(indom)), (a, b)
