@@ -353,7 +353,7 @@ typedef struct {
  * all its boxes as candidates.  mode 0 (exact) takes the available triangle
  * of smallest priority in every group per wave -- the paper's sequential
  * priority-queue order -- and mode 1 (wavefront) every available triangle at
- * once, each judged against its boxes as the wave found them.  centres: [K][3]
+ * once, each evaluated against its boxes as the wave found them.  centres: [K][3]
  * world coordinates (FP64, host or device), or NULL for the current boxes'
  * centres.  The layer's assignment, slabs (tight) and outer volumes are
  * replaced; its frames are kept and every cluster is marked for the next

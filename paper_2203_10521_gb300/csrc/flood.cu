@@ -18,7 +18,7 @@
 //              triangle joins the candidate box (boxes holding one of its
 //              neighbours) whose exact outer volume grows least (Eq. 12-13,
 //              ties -> smaller box); in the wavefront mode several triangles
-//              may join one box in a wave, each judged against the box as the
+//              may join one box in a wave, each evaluated against the box as the
 //              wave found it, and the box is recounted afterwards.
 #include <algorithm>
 #include <vector>
