@@ -106,15 +106,22 @@ const char* obb_last_error(const obb_ctx* ctx);
  * bracketed by CUDA events on the context stream (launches inside a Lloyd
  * iteration run as a CUDA graph are not) and the kernel adds up its
  * algorithmic traffic (16 bytes per 128-bit occupancy chunk that a box row's
- * x-interval touches inside the lattice) and the rows with a non-empty
- * interval.  obb_profile_enable resets the totals; obb_profile_read
- * synchronises and reports them. */
+ * x-interval touches inside the lattice), the rows with a non-empty
+ * interval and, of these, the rows read by a group of lanes together (long
+ * rows of boxes whose slabs all step along the row).  Every counting launch of the context, profiled or not (those of
+ * a captured Lloyd iteration included), also adds up the lattice points of
+ * its boxes that lie inside the lattice domain [0, N)^3: the points whose
+ * occupancy bit it reads (points outside the domain are empty by definition
+ * and cost no memory).  obb_profile_enable resets the totals;
+ * obb_profile_read synchronises and reports them. */
 typedef struct {
     int64_t launches;        /* kernels enqueued by the context since creation */
     int64_t count_launches;  /* counting-kernel launches since profiling was enabled */
     double count_ms;         /* their summed duration (CUDA events) */
     double count_bytes;      /* their summed algorithmic bytes */
     double count_rows;       /* (j, k) rows with a non-empty interval inside the lattice or not */
+    double count_points_in_domain;   /* in-domain lattice points of all counted boxes (every launch) */
+    double count_rows_shared;        /* of count_rows, those whose 128-bit chunks a group of lanes shared */
 } obb_profile_stats;
 obb_status obb_profile_enable(obb_ctx* ctx, int32_t on);
 obb_status obb_profile_read(obb_ctx* ctx, obb_profile_stats* out);

@@ -29,14 +29,18 @@ Q_BITS = 24   # fraction bits of the quantised box normals
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no FP contraction)."""
+    """Compile the oracle with gcc (-O2, no FP contraction; OpenMP where the
+    compiler has it, for the loops over independent columns and slices)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC", "-o", tmp, _SRC]
+    try:
+        subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:] + ["-lm"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -49,7 +53,20 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(build())
         _declare(_lib)
+        _lib.orc_set_threads(1)
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's loops over independent columns, slices and
+    boxes (1 by default); returns the count in effect (1 without OpenMP)."""
+    L = lib()
+    L.orc_set_threads(int(n))
+    return int(L.orc_threads())
+
+
+def threads() -> int:
+    return int(lib().orc_threads())
 
 
 class RoundStats(C.Structure):
@@ -63,6 +80,8 @@ def _p(a):
 
 def _declare(L):
     vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    L.orc_set_threads.argtypes = [i32]
+    L.orc_threads.restype = C.c_int32
     L.orc_lattice_frame.argtypes = [vp, i64, i32, vp, vp]
     L.orc_snap.argtypes = [vp, i64, vp, vp, vp]
     L.orc_occupancy_columns.argtypes = [vp, vp, i64, i32, vp, i64, vp, vp]
@@ -72,7 +91,7 @@ def _declare(L):
     L.orc_quantize_boxes.restype = C.c_int
     L.orc_box_aabb.argtypes = [vp, vp, vp]
     L.orc_box_aabb.restype = C.c_int
-    L.orc_outer_volume.argtypes = [vp, vp, i32, vp, vp, i64, vp, vp]
+    L.orc_outer_volume.argtypes = [vp, vp, i32, vp, vp, i64, vp, vp, vp]
     L.orc_outer_volume.restype = C.c_int
     L.orc_tight_bounds.argtypes = [vp, vp, i64, vp, i32, vp, vp]
     L.orc_lloyd_moves.argtypes = [vp, vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp, i32, i32, vp]
@@ -216,18 +235,20 @@ def box_aabb(n, bnd):
     return out
 
 
-def outer_volume(occ: Occupancy, n, bnd):
-    """Eq. 4: exact count of unoccupied lattice points in each box, and the box's point count."""
+def outer_volume(occ: Occupancy, n, bnd, want_domain=False):
+    """Eq. 4: exact count of unoccupied lattice points in each box, and the box's
+    point count (and, with want_domain, its points inside [0, N)^3)."""
     n = _c(n, np.int32).reshape(-1, 9)
     bnd = _c(bnd, np.int64).reshape(-1, 6)
     occ.fill_boxes(n, bnd)
     cnt = np.zeros(n.shape[0], dtype=np.uint64)
     tot = np.zeros(n.shape[0], dtype=np.uint64)
+    dom = np.zeros(n.shape[0], dtype=np.uint64)
     rc = lib().orc_outer_volume(_p(occ.occ), _p(occ.known), occ.N, _p(n), _p(bnd), n.shape[0],
-                                _p(cnt), _p(tot))
+                                _p(cnt), _p(tot), _p(dom))
     if rc:
         raise RuntimeError(f"orc_outer_volume failed ({rc})")
-    return cnt, tot
+    return (cnt, tot, dom) if want_domain else (cnt, tot)
 
 
 def tight_bounds(U, F, assign, K, n):
@@ -670,26 +691,32 @@ SURROGATE_INPUTS = 524
 MLP_HIDDEN = 128
 
 
-def surrogate_features(occ: Occupancy, n, bnd):
-    """Features of quantised boxes: 12 box parameters + an 8^3 occupancy patch
-    sampled in the box's own frame (FP64, fixed order)."""
+def surrogate_features(occ: Occupancy, n, bnd, return_ties=False):
+    """Features of quantised boxes: 12 box parameters (FP64 from exact
+    integers, rounded once to FP32) + an 8^3 occupancy patch at the exact
+    rational sample points of the box's own frame.  With return_ties, also a
+    [K, 512] uint8 mask of the patch points lying within 1e-3 of a rounding
+    tie on some axis."""
     n = _c(n, np.int32).reshape(-1, 9)
     bnd = _c(bnd, np.int64).reshape(-1, 6)
     L = lib()
     if not hasattr(L, "_sf_declared"):
         L.orc_surrogate_features.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
-                                             C.c_int64, C.c_void_p]
+                                             C.c_int64, C.c_void_p, C.c_void_p]
         L.orc_surrogate_features.restype = C.c_int
         L._sf_declared = True
     occ.fill_boxes(n, bnd)
     out = np.zeros((n.shape[0], SURROGATE_INPUTS), np.float32)
-    rc = L.orc_surrogate_features(_p(occ.occ), _p(occ.known), occ.N, _p(n), _p(bnd), n.shape[0], _p(out))
+    ties = np.zeros((n.shape[0], 512), np.uint8)
+    rc = L.orc_surrogate_features(_p(occ.occ), _p(occ.known), occ.N, _p(n), _p(bnd), n.shape[0], _p(out),
+                                  _p(ties))
     if rc == -3:
         occ.fill_all()
-        rc = L.orc_surrogate_features(_p(occ.occ), _p(occ.known), occ.N, _p(n), _p(bnd), n.shape[0], _p(out))
+        rc = L.orc_surrogate_features(_p(occ.occ), _p(occ.known), occ.N, _p(n), _p(bnd), n.shape[0], _p(out),
+                                      _p(ties))
     if rc:
         raise RuntimeError(f"orc_surrogate_features failed ({rc})")
-    return out
+    return (out, ties) if return_ties else out
 
 
 def mlp_unpack(params):

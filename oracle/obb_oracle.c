@@ -34,6 +34,9 @@
  *   - refit: area-weighted covariance, cyclic Jacobi in FP64.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -119,27 +122,84 @@ static int column_crossing(const int32_t* A, const int32_t* B, const int32_t* C,
     return 1;
 }
 
+/* Threads of the loops below that run over independent columns or slices
+ * (OpenMP when built with it; 1 by default, so the oracle is single threaded
+ * unless a caller asks otherwise).  No result depends on the thread count:
+ * every column and every point is computed on its own, and counts are
+ * integer sums. */
+void orc_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int32_t orc_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+#define ORC_BLOCK 32
+
+static int cmp_i64(const void* a, const void* b)
+{
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return x < y ? -1 : (x > y);
+}
+
 /*
  * Occupancy of the requested columns.  occ is N*N*N bytes indexed
  * ((k*N)+j)*N+i; colmask is N*N bytes indexed k*N+j and is set to 1 for
  * every column written.  For each point, the number of crossings with
  * x* <= 2^S i is counted over all triangles; the point is inside iff odd.
+ * The columns are taken in blocks of 32 x 32; for each block only the
+ * triangles whose (y, z) bounding box meets the block's rectangle are
+ * examined (a triangle outside it cannot contain any of its column points).
  */
 void orc_occupancy_columns(const int32_t* U, const int32_t* F, int64_t nt, int32_t N,
                            const int32_t* cols, int64_t ncols, uint8_t* occ, uint8_t* colmask)
 {
-    int64_t* nums = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt > 0 ? nt : 1));
-    int64_t* dens = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt > 0 ? nt : 1));
+    if (ncols <= 0) return;
+    /* order the columns by block: key = block id * 2^32 + column index */
+    const int64_t nbj = (N + ORC_BLOCK - 1) / ORC_BLOCK;
+    int64_t* key = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncols);
     for (int64_t c = 0; c < ncols; ++c) {
-        int32_t j = cols[2 * c], k = cols[2 * c + 1];
-        int64_t py = (int64_t)j << ORC_S, pz = (int64_t)k << ORC_S;
-        int64_t m = 0;
+        const int64_t blk = (int64_t)(cols[2 * c + 1] / ORC_BLOCK) * nbj + cols[2 * c] / ORC_BLOCK;
+        key[c] = (blk << 32) | c;
+    }
+    qsort(key, (size_t)ncols, sizeof(int64_t), cmp_i64);
+    int64_t nblk = 0;
+    int64_t* bstart = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ncols + 1));
+    for (int64_t c = 0; c < ncols; ++c)
+        if (c == 0 || (key[c] >> 32) != (key[c - 1] >> 32)) bstart[nblk++] = c;
+    bstart[nblk] = ncols;
+    int64_t b;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (b = 0; b < nblk; ++b) {
+        int64_t* tl = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt > 0 ? nt : 1));
+        int64_t* nums = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt > 0 ? nt : 1));
+        int64_t* dens = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt > 0 ? nt : 1));
+        /* the block's column rectangle in fixed point */
+        int64_t y0 = INT64_MAX, y1 = INT64_MIN, z0 = INT64_MAX, z1 = INT64_MIN;
+        for (int64_t q = bstart[b]; q < bstart[b + 1]; ++q) {
+            const int64_t c = key[q] & 0xffffffffLL;
+            const int64_t py = (int64_t)cols[2 * c] << ORC_S, pz = (int64_t)cols[2 * c + 1] << ORC_S;
+            if (py < y0) y0 = py;
+            if (py > y1) y1 = py;
+            if (pz < z0) z0 = pz;
+            if (pz > z1) z1 = pz;
+        }
+        int64_t ntl = 0;
         for (int64_t t = 0; t < nt; ++t) {
             const int32_t* A = U + 3 * (int64_t)F[3 * t];
             const int32_t* B = U + 3 * (int64_t)F[3 * t + 1];
             const int32_t* C = U + 3 * (int64_t)F[3 * t + 2];
-            /* closed yz-bbox reject: a point outside it is outside the
-             * perturbed projection as well */
             int32_t ymin = A[1], ymax = A[1], zmin = A[2], zmax = A[2];
             if (B[1] < ymin) ymin = B[1];
             if (B[1] > ymax) ymax = B[1];
@@ -149,26 +209,54 @@ void orc_occupancy_columns(const int32_t* U, const int32_t* F, int64_t nt, int32
             if (B[2] > zmax) zmax = B[2];
             if (C[2] < zmin) zmin = C[2];
             if (C[2] > zmax) zmax = C[2];
-            if (py < ymin || py > ymax || pz < zmin || pz > zmax) continue;
-            int64_t n, d;
-            if (column_crossing(A, B, C, py, pz, &n, &d)) {
-                nums[m] = n;
-                dens[m] = d;
-                ++m;
+            if (ymax < y0 || ymin > y1 || zmax < z0 || zmin > z1) continue;
+            tl[ntl++] = t;
+        }
+        for (int64_t q = bstart[b]; q < bstart[b + 1]; ++q) {
+            const int64_t c = key[q] & 0xffffffffLL;
+            int32_t j = cols[2 * c], k = cols[2 * c + 1];
+            int64_t py = (int64_t)j << ORC_S, pz = (int64_t)k << ORC_S;
+            int64_t m = 0;
+            for (int64_t u = 0; u < ntl; ++u) {
+                const int64_t t = tl[u];
+                const int32_t* A = U + 3 * (int64_t)F[3 * t];
+                const int32_t* B = U + 3 * (int64_t)F[3 * t + 1];
+                const int32_t* C = U + 3 * (int64_t)F[3 * t + 2];
+                /* closed yz-bbox reject: a point outside it is outside the
+                 * perturbed projection as well */
+                int32_t ymin = A[1], ymax = A[1], zmin = A[2], zmax = A[2];
+                if (B[1] < ymin) ymin = B[1];
+                if (B[1] > ymax) ymax = B[1];
+                if (C[1] < ymin) ymin = C[1];
+                if (C[1] > ymax) ymax = C[1];
+                if (B[2] < zmin) zmin = B[2];
+                if (B[2] > zmax) zmax = B[2];
+                if (C[2] < zmin) zmin = C[2];
+                if (C[2] > zmax) zmax = C[2];
+                if (py < ymin || py > ymax || pz < zmin || pz > zmax) continue;
+                int64_t n, d;
+                if (column_crossing(A, B, C, py, pz, &n, &d)) {
+                    nums[m] = n;
+                    dens[m] = d;
+                    ++m;
+                }
             }
+            uint8_t* row = occ + ((int64_t)k * N + j) * (int64_t)N;
+            for (int32_t i = 0; i < N; ++i) {
+                int64_t x = (int64_t)i << ORC_S;
+                int cnt = 0;
+                for (int64_t q2 = 0; q2 < m; ++q2)
+                    if (nums[q2] <= x * dens[q2]) ++cnt;
+                row[i] = (uint8_t)(cnt & 1);
+            }
+            colmask[(int64_t)k * N + j] = 1;
         }
-        uint8_t* row = occ + ((int64_t)k * N + j) * (int64_t)N;
-        for (int32_t i = 0; i < N; ++i) {
-            int64_t x = (int64_t)i << ORC_S;
-            int cnt = 0;
-            for (int64_t q = 0; q < m; ++q)
-                if (nums[q] <= x * dens[q]) ++cnt;
-            row[i] = (uint8_t)(cnt & 1);
-        }
-        colmask[(int64_t)k * N + j] = 1;
+        free(tl);
+        free(nums);
+        free(dens);
     }
-    free(nums);
-    free(dens);
+    free(key);
+    free(bstart);
 }
 
 /* Number of crossings of each requested column (used by the even-count pin). */
@@ -345,13 +433,14 @@ int orc_box_aabb(const int32_t* n, const int64_t* bnd, int64_t* out) { return bo
 /*
  * Eq. 4 on the lattice, one point at a time: counts[k] = number of lattice
  * points p in Z^3 inside box k that are not occupied (points outside [0,N)^3
- * are unoccupied); npts[k] = number of lattice points inside box k.
+ * are unoccupied); npts[k] = number of lattice points inside box k; ndom[k]
+ * (if ndom is not NULL) = those of them inside [0, N)^3.
  * occ/colmask as in orc_occupancy_columns.  Returns 0, -1 for a singular box,
  * -3 when an in-domain column needed has not been computed.
  */
 int orc_outer_volume(const uint8_t* occ, const uint8_t* colmask, int32_t N,
                      const int32_t* n, const int64_t* bnd, int64_t K,
-                     uint64_t* counts, uint64_t* npts)
+                     uint64_t* counts, uint64_t* npts, uint64_t* ndom)
 {
     for (int64_t b = 0; b < K; ++b) {
         const int32_t* nb = n + 9 * b;
@@ -359,8 +448,11 @@ int orc_outer_volume(const uint8_t* occ, const uint8_t* colmask, int32_t N,
         index_bounds(bnd + 6 * b, Lq, Hq);
         int rc = box_aabb(nb, bnd + 6 * b, ab);
         if (rc) return rc == -1 ? -1 : -2;
-        uint64_t cnt = 0, tot = 0;
-        for (int64_t k = ab[4]; k <= ab[5]; ++k)
+        uint64_t cnt = 0, tot = 0, dom = 0;
+        int missing = 0;
+        int64_t k;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : cnt, tot, dom) reduction(| : missing)
+        for (k = ab[4]; k <= ab[5]; ++k)
             for (int64_t j = ab[2]; j <= ab[3]; ++j) {
                 int incol = (j >= 0 && j < N && k >= 0 && k < N);
                 for (int64_t i = ab[0]; i <= ab[1]; ++i) {
@@ -368,14 +460,20 @@ int orc_outer_volume(const uint8_t* occ, const uint8_t* colmask, int32_t N,
                     ++tot;
                     int filled = 0;
                     if (incol && i >= 0 && i < N) {
-                        if (!colmask[k * N + j]) return -3;
+                        if (!colmask[k * N + j]) {
+                            missing = 1;
+                            continue;
+                        }
+                        ++dom;
                         filled = occ[(k * N + j) * (int64_t)N + i];
                     }
                     if (!filled) ++cnt;
                 }
             }
+        if (missing) return -3;
         counts[b] = cnt;
         npts[b] = tot;
+        if (ndom) ndom[b] = dom;
     }
     return 0;
 }
@@ -465,7 +563,7 @@ static int count_one(const uint8_t* occ, const uint8_t* colmask, int32_t N, cons
                      const int64_t* bnd, uint64_t* c)
 {
     uint64_t tot;
-    return orc_outer_volume(occ, colmask, N, n, bnd, 1, c, &tot);
+    return orc_outer_volume(occ, colmask, N, n, bnd, 1, c, &tot, NULL);
 }
 
 /*
@@ -1164,50 +1262,39 @@ int orc_median_split(const int32_t* U, const int32_t* F, int64_t nt, const int32
 }
 
 /* ------------------------------------------------------------------------- */
-/* Surrogate features (the learned screen's inputs), FP32 in a fixed order    */
+/* Surrogate features (the learned screen's inputs), from their definition   */
 /* ------------------------------------------------------------------------- */
 
-/* Integer -> FP32 as defined for the features: the magnitude's two 32-bit
- * halves, each converted to the nearest float, joined by one fused
- * multiply-add (fmaf rounds once). */
-static float feat_f32_u64(uint64_t u)
+/* floor(y / z) for z > 0, 128-bit */
+static __int128 floordiv128(__int128 y, __int128 z)
 {
-    return fmaf((float)(uint32_t)(u >> 32), 4294967296.0f, (float)(uint32_t)u);
-}
-
-static float feat_f32_i64(int64_t x)
-{
-    uint64_t u = x < 0 ? 0ull - (uint64_t)x : (uint64_t)x;
-    float f = feat_f32_u64(u);
-    return x < 0 ? -f : f;
-}
-
-static float feat_f32_i128(__int128 x)
-{
-    unsigned __int128 a = x < 0 ? (unsigned __int128)0 - (unsigned __int128)x : (unsigned __int128)x;
-    float f = fmaf(feat_f32_u64((uint64_t)(a >> 64)), 18446744073709551616.0f, feat_f32_u64((uint64_t)a));
-    return x < 0 ? -f : f;
+    __int128 q = y / z;
+    if ((y % z != 0) && (y < 0)) q -= 1;
+    return q;
 }
 
 /*
- * For each quantised box (normals n, integer slab bounds L <= n . p <= H):
- * 12 box parameters and the occupancy bits of an 8^3 patch.  Exact integers
- * first: the adjugate A of n (so n^-1 = A / det) in int64, det in 128 bits,
- * S = L + H and D = H - L.  Then FP32, one rounding per operation, in this
- * order (no contraction):
- *   centre   c_r = (((A_r0 S_0 + A_r1 S_1) + A_r2 S_2) / (2 det));
- *   params   c_r / N (r = 0..2); n_ac / |n_a| (a = 0, 1; c = 0..2), with
- *            |n_a| = sqrt((n_a0^2 + n_a1^2) + n_a2^2); ((D_a 0.5) / |n_a|) / N;
- *   edges    E_ra = (A_ra D_a) / det;
- *   patch    point s = (s_x, s_y, s_z) in 0..7: g_a = (2 s_a - 7) / 16,
- *            p_r = ((c_r + E_r0 g_0) + E_r1 g_1) + E_r2 g_2, lattice index
- *            floor(p_r + 1/2); the bit is 0 outside [0,N)^3.
- * The patch points are the centres of an 8x8x8 subdivision of the box in its
- * own frame (M^-1 v for v_a = L_a + D_a (2 s_a + 1) / 16).  det = 0 gives
- * c = E = 0.  Returns 0, or -3 if an in-domain column needed is not computed.
+ * For each quantised box (normals n, integer slab bounds L <= n . p <= H in
+ * index units, L = ceil(lo / 256), H = floor(hi / 256)) the surrogate's 524
+ * inputs, computed from what they mean:
+ *   params   centre of the parallelepiped {L <= n p <= H} divided by N
+ *            (n^-1 (L + H) / 2), the unit normals n_0 / |n_0| and n_1 / |n_1|,
+ *            and the half widths ((H_a - L_a) / 2) / |n_a| / N, in FP64 from
+ *            exact integers, rounded once to FP32;
+ *   patch    the occupancy at the centres of an 8 x 8 x 8 subdivision of the
+ *            box in its own frame, p = n^-1 v with v_a = L_a + (H_a - L_a)
+ *            (2 s_a + 1) / 16 (s_a = 0..7, x fastest), rounded to the nearest
+ *            lattice point, floor(p + 1/2), and 0 outside [0, N)^3.
+ * The sample points are exact rationals: with the adjugate A of n (int64)
+ * and det (128 bits), p_r + 1/2 = (sum_a A_ra (16 v_a) + 8 det) / (16 det), an
+ * exact 128-bit quotient.  If `tie` is given, tie[512 b + s] = 1 when some
+ * coordinate of point s lies within 10^-3 of a rounding tie (a half-integer),
+ * where a computation in floating point may round either way.  det = 0 gives
+ * zero parameters and bits.  Returns 0, or -3 if an in-domain column needed
+ * is not computed.
  */
 int orc_surrogate_features(const uint8_t* occ, const uint8_t* colmask, int32_t N, const int32_t* n,
-                           const int64_t* bnd, int64_t K, float* feats)
+                           const int64_t* bnd, int64_t K, float* feats, uint8_t* tie)
 {
     for (int64_t b = 0; b < K; ++b) {
         const int32_t* nb = n + 9 * b;
@@ -1217,50 +1304,53 @@ int orc_surrogate_features(const uint8_t* occ, const uint8_t* colmask, int32_t N
             L[a] = -floordiv64(-bnd[6 * b + 2 * a], 256);
             H[a] = floordiv64(bnd[6 * b + 2 * a + 1], 256);
         }
+        /* A[3 r + a]: adjugate entry, n^-1 = A / det */
         const int64_t A[9] = {m[4] * m[8] - m[5] * m[7], m[2] * m[7] - m[1] * m[8], m[1] * m[5] - m[2] * m[4],
                               m[5] * m[6] - m[3] * m[8], m[0] * m[8] - m[2] * m[6], m[2] * m[3] - m[0] * m[5],
                               m[3] * m[7] - m[4] * m[6], m[1] * m[6] - m[0] * m[7], m[0] * m[4] - m[1] * m[3]};
         const __int128 det = (__int128)m[0] * A[0] + (__int128)m[1] * A[3] + (__int128)m[2] * A[6];
-        const float detf = feat_f32_i128(det);
-        float Af[9], Sf[3], Df[3], c[3] = {0.f, 0.f, 0.f}, E[9];
-        for (int i = 0; i < 9; ++i) Af[i] = feat_f32_i64(A[i]);
-        for (int a = 0; a < 3; ++a) {
-            Sf[a] = feat_f32_i64(L[a] + H[a]);
-            Df[a] = feat_f32_i64(H[a] - L[a]);
-        }
-        for (int r = 0; r < 3; ++r) {
-            if (det != 0) {
-                float t = Af[3 * r] * Sf[0] + Af[3 * r + 1] * Sf[1];
-                t = t + Af[3 * r + 2] * Sf[2];
-                c[r] = t / (2.0f * detf);
-            }
-            for (int a = 0; a < 3; ++a) E[3 * r + a] = det != 0 ? (Af[3 * r + a] * Df[a]) / detf : 0.0f;
-        }
         float* f = feats + 524 * b;
-        for (int r = 0; r < 3; ++r) f[r] = c[r] / (float)N;
-        for (int a = 0; a < 3; ++a) {
-            const float n0 = (float)nb[3 * a], n1 = (float)nb[3 * a + 1], n2 = (float)nb[3 * a + 2];
-            float q = n0 * n0 + n1 * n1;
-            q = q + n2 * n2;
-            const float nn = sqrtf(q);
-            if (a < 2) {
-                f[3 + 3 * a] = nn > 0.0f ? n0 / nn : 0.0f;
-                f[4 + 3 * a] = nn > 0.0f ? n1 / nn : 0.0f;
-                f[5 + 3 * a] = nn > 0.0f ? n2 / nn : 0.0f;
+        uint8_t* tb = tie ? tie + 512 * b : NULL;
+        for (int r = 0; r < 3; ++r) {
+            double c = 0.0;
+            if (det != 0) {
+                __int128 num = 0;
+                for (int a = 0; a < 3; ++a) num += (__int128)A[3 * r + a] * (__int128)(L[a] + H[a]);
+                c = ((double)num / (2.0 * (double)det)) / (double)N;
             }
-            f[9 + a] = nn > 0.0f ? ((Df[a] * 0.5f) / nn) / (float)N : 0.0f;
+            f[r] = (float)c;
         }
+        for (int a = 0; a < 3; ++a) {
+            const double n0 = (double)nb[3 * a], n1 = (double)nb[3 * a + 1], n2 = (double)nb[3 * a + 2];
+            const double nn = sqrt(n0 * n0 + n1 * n1 + n2 * n2);   /* exact sum below 2^53 */
+            if (a < 2) {
+                f[3 + 3 * a] = nn > 0.0 ? (float)(n0 / nn) : 0.0f;
+                f[4 + 3 * a] = nn > 0.0 ? (float)(n1 / nn) : 0.0f;
+                f[5 + 3 * a] = nn > 0.0 ? (float)(n2 / nn) : 0.0f;
+            }
+            f[9 + a] = nn > 0.0 ? (float)((0.5 * (double)(H[a] - L[a]) / nn) / (double)N) : 0.0f;
+        }
+        /* denominator 16 det made positive */
+        const __int128 Z = det < 0 ? -16 * det : 16 * det;
+        const __int128 sg = det < 0 ? -1 : 1;
         for (int s = 0; s < 512; ++s) {
             const int sv[3] = {s & 7, (s >> 3) & 7, s >> 6};
-            float g[3];
-            for (int a = 0; a < 3; ++a) g[a] = (float)(2 * sv[a] - 7) * 0.0625f;
             int64_t idx[3];
+            int near = 0;
             for (int r = 0; r < 3; ++r) {
-                float p = c[r] + E[3 * r] * g[0];
-                p = p + E[3 * r + 1] * g[1];
-                p = p + E[3 * r + 2] * g[2];
-                const float q = floorf(p + 0.5f);
-                idx[r] = fabsf(q) < 1e9f ? (int64_t)q : -1;
+                idx[r] = -1;
+                if (det == 0) continue;
+                __int128 X = 8 * det;
+                for (int a = 0; a < 3; ++a) {
+                    const __int128 v16 = (__int128)16 * L[a] + (__int128)(H[a] - L[a]) * (2 * sv[a] + 1);
+                    X += (__int128)A[3 * r + a] * v16;
+                }
+                const __int128 Y = sg * X;
+                const __int128 q = floordiv128(Y, Z);
+                const __int128 fr = Y - q * Z;             /* in [0, Z) */
+                const __int128 dist = fr < Z - fr ? fr : Z - fr;
+                if (1000 * dist < Z) near = 1;
+                idx[r] = (q >= -1 && q <= (__int128)N) ? (int64_t)q : -1;
             }
             float bit = 0.f;
             if (idx[0] >= 0 && idx[0] < N && idx[1] >= 0 && idx[1] < N && idx[2] >= 0 && idx[2] < N) {
@@ -1268,6 +1358,7 @@ int orc_surrogate_features(const uint8_t* occ, const uint8_t* colmask, int32_t N
                 bit = (float)occ[(idx[2] * N + idx[1]) * (int64_t)N + idx[0]];
             }
             f[12 + s] = bit;
+            if (tb) tb[s] = (uint8_t)near;
         }
     }
     return 0;

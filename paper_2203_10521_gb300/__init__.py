@@ -51,7 +51,8 @@ class StepStats(C.Structure):
 
 class ProfileStats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("count_launches", C.c_int64), ("count_ms", C.c_double),
-                ("count_bytes", C.c_double), ("count_rows", C.c_double)]
+                ("count_bytes", C.c_double), ("count_rows", C.c_double),
+                ("count_points_in_domain", C.c_double), ("count_rows_shared", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -70,8 +70,9 @@ struct LatticeFrame {
 
 // Per-box data the counting kernel needs, prepared once per box.
 // Rows (j, k) of the box's index-space AABB are cut into tiles of wj rows
-// along y by wk * tk rows along z (wj * wk = 32 lanes); each lane owns one j
-// and visits tk rows spaced wk apart along z.  Slab a bounds i through
+// along y by wk * tk rows along z (wj * wk = 32 / G lane groups of G = 2^lg
+// lanes); each group owns one j and visits tk rows spaced wk apart along z,
+// its G lanes taking the row's 128-bit chunks in turn.  Slab a bounds i through
 // quotients by dd_a = |n_a0|; from one visited row to the next the quotient
 // moves by qstep_a with remainder carry rstep_a, or by fstep_a in 32.32 fixed
 // point (an integer DDA either way).
@@ -88,6 +89,7 @@ struct alignas(128) BoxPrep {
     int32_t i0, span;        // index-space AABB along x: [i0, i0 + span]
     int32_t axis;            // rows run along index axis 0 (x), 1 (y) or 2 (z); n's columns permuted to match
     int32_t lat;             // index of the box's lattice in the launch's lattice table
+    int32_t lg;              // log2 of the lanes sharing one row (wide rows: 16-byte chunks dealt out to G lanes)
     // Separating axes of the box's shadow on the (j, k) plane: the normals of
     // its three projected edge directions, and the shadow's extent along each,
     // widened by two rows.  A tile whose rectangle lies outside one of these
@@ -163,7 +165,9 @@ struct obb_ctx {
     int64_t launches = 0;
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
-    unsigned long long* d_prof = nullptr;   // [0] algorithmic bytes, [1] lattice points, [2] rows
+    // [0] algorithmic bytes, [1] rows, [3] rows shared by lane groups (profiled launches);
+    // [2] in-domain points (every launch)
+    unsigned long long* d_prof = nullptr;
     std::map<std::pair<int64_t, int>, int> sort_launch_cache;
 };
 

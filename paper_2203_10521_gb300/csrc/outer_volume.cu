@@ -41,6 +41,19 @@
 #ifndef OBB_BIG_TK_ROWS
 #define OBB_BIG_TK_ROWS 16384
 #endif
+// OBB_WIDE_MIN_CHUNKS: a box whose rows are expected to span at least this many
+// 128-bit chunks shares each row among several lanes (0: never)
+#ifndef OBB_WIDE_MIN_CHUNKS
+#define OBB_WIDE_MIN_CHUNKS 6
+#endif
+// OBB_WIDE_MAX_LG: log2 of the most lanes that share one row
+#ifndef OBB_WIDE_MAX_LG
+#define OBB_WIDE_MAX_LG 3
+#endif
+// OBB_WIDE_UNROLL: rows of a lane group's row loop unrolled (several rows' loads in flight)
+#ifndef OBB_WIDE_UNROLL
+#define OBB_WIDE_UNROLL 4
+#endif
 // OBB_ROW_MARGIN: rows added on each side of a box's (j, k) bounding rectangle
 #ifndef OBB_ROW_MARGIN
 #define OBB_ROW_MARGIN 1
@@ -51,6 +64,7 @@ constexpr int kCountUnroll = OBB_COUNT_UNROLL;
 constexpr int kRowMargin = OBB_ROW_MARGIN;
 constexpr int kPrepThreads = 32;   // one warp per preparation block: its per-box work spreads over many SMs
 constexpr int kGrab = OBB_GRAB;
+constexpr int kWideUnroll = OBB_WIDE_UNROLL;
 }  // namespace obbv
 
 namespace obbv {
@@ -198,6 +212,7 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     }
     p.i0 = 0;
     p.span = -1;
+    p.lg = 0;
     p.j0 = p.k0 = 0;
     p.nj = p.nk = p.ntj = 0;
     for (int a = 0; a < 3; ++a) {
@@ -341,17 +356,38 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     // row clipping trims their empty ends)
     if ((int64_t)p.nj * p.nk >= OBB_BIG_TK_ROWS && 2 * tile_k <= 128) p.tk = 2 * tile_k;
 #endif
-    // tile shape: wj lanes along y, wk = 32 / wj along z; the least padding wins
-    // (ties to the wider wj, whose rows sit next to each other in memory)
-    int best = 5;
+    // wide rows: a box whose three slabs all step by DDA and whose rows are
+    // long (the x-interval of a row through it, at most min_a (H_a - L_a) /
+    // |n_a0| + 1 points, spans several 128-bit chunks) shares each row among
+    // G = 2^lg lanes that read its chunks side by side (16-byte loads,
+    // contiguous across the group), so a warp streams whole rows
+#if OBB_WIDE_MIN_CHUNKS > 0
+    if (p.nj > 0 && (p.mode & 0xff) == 0x15) {
+        float ell = (float)p.span + 1.0f;
+        for (int a = 0; a < 3; ++a)
+            ell = fminf(ell, i64_to_float(p.Hq[a] - p.Lq[a]) / (float)p.dd[a] + 1.0f);
+        ell = fminf(ell, (float)N);
+        const float chunks = ell * (1.0f / 128.0f) + 1.0f;
+        if (chunks >= (float)OBB_WIDE_MIN_CHUNKS) {
+            int lg = 0;
+            while (lg < OBB_WIDE_MAX_LG && (float)(2 << lg) <= chunks && (2 << lg) <= lr.W / 2) ++lg;
+            p.lg = lg;
+        }
+    }
+#endif
+    // tile shape: wj groups along y, wk = 32 / G / wj along z; the least
+    // padding wins (ties to the wider wj, whose rows sit next to each other in
+    // memory)
+    const int32_t lgrp = 5 - p.lg;   // log2 of the lane groups of a warp
+    int best = lgrp;
     int64_t best_slots = INT64_MAX;
     if (p.nj > 0) {
-        // ceil(nk / ((32 >> l) tk)) = ceil(ceil(nk / tk) / 2^(5 - l)): one division
+        // ceil(nk / (wk tk)) = ceil(ceil(nk / tk) / wk): one division
         const int32_t nkt = (p.nk + p.tk - 1) / p.tk;
-        for (int l = 5; l >= 0; --l) {
-            const int32_t sh = 5 - l;
+        for (int l = lgrp; l >= 0; --l) {
+            const int32_t sh = lgrp - l;
             const int64_t slots = (int64_t)(((p.nj + (1 << l) - 1) >> l) << l) *
-                                  ((int64_t)((nkt + (1 << sh) - 1) >> sh) * ((32 >> l) * p.tk));
+                                  ((int64_t)((nkt + (1 << sh) - 1) >> sh) * ((1 << sh) * p.tk));
             if (slots < best_slots) {
                 best_slots = slots;
                 best = l;
@@ -364,11 +400,11 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
         p.k0 + p.nk <= N)
         p.mode |= 1 << 8;
     p.lwj = best;
-    const int32_t wj = 1 << best, wk = 32 >> best;
+    const int32_t wj = 1 << best, wk = (32 >> p.lg) >> best;
     p.ntj = p.nj > 0 ? (p.nj + wj - 1) / wj : 0;
     for (int a = 0; a < 3; ++a)
         if ((p.mode >> (2 * a)) & 3) {
-            // between a lane's rows k advances by wk: X_lo and X_hi move by -sign(d) * n_a2 * wk
+            // between a group's rows k advances by wk: X_lo and X_hi move by -sign(d) * n_a2 * wk
             // |delta| <= 2^24 * 32 and 0 < dd < 2^25: exact in 32 bits
             const int32_t delta = -(p.n[3 * a] > 0 ? 1 : -1) * p.n[3 * a + 2] * wk;
             int32_t qs = delta / p.dd[a];
@@ -578,6 +614,95 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
     return cnt + __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
 }
 
+// bits [lo, hi] of a 64-bit word (lo and hi may lie outside [0, 63])
+__device__ __forceinline__ uint64_t bit_range(int32_t lo, int32_t hi)
+{
+    const uint64_t ml = lo <= 0 ? ~0ull : (lo >= 64 ? 0ull : ~0ull << lo);
+    const uint64_t mh = hi >= 63 ? ~0ull : (hi < 0 ? 0ull : ~0ull >> (63 - hi));
+    return ml & mh;
+}
+
+// Lane g's share of the occupied bits i in [a, e] of one row when G = 2^lg
+// lanes share it: the 128-bit chunks (a >> 7) + g, + G, ... up to e >> 7,
+// each read with one 16-byte load (rows are 16-byte aligned), so the group's
+// loads are contiguous.
+__device__ __forceinline__ uint32_t popc_range_wide(const uint64_t* __restrict__ row, int32_t a, int32_t e,
+                                                    int32_t g, int32_t lg)
+{
+    uint32_t cnt = 0;
+    const int32_t ce = e >> 7;
+    for (int32_t c = (a >> 7) + g; c <= ce; c += 1 << lg) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(row) + c);
+        const int32_t b0 = c << 7;
+        cnt += __popcll(v.x & bit_range(a - b0, e - b0)) + __popcll(v.y & bit_range(a - b0 - 64, e - b0 - 64));
+    }
+    return cnt;
+}
+
+// One pass of a lane (group) over its rows r0..r1 of a tile of a box whose
+// three slabs all step by DDA: each of the six bounds is a 32.32 fixed-point
+// value whose integer part is the quotient, so a bound costs one 64-bit add
+// per row.  kWide: G = 2^lg lanes share each row (lane g reads its chunks,
+// lane 0 of the group accounts the row's length); kInterior: the tile's rows
+// and x-intervals all lie in the lattice (no clamps).
+template <bool kWide, bool kInterior>
+__device__ __forceinline__ void dda_rows(int64_t (&Al)[3], int64_t (&Ah)[3], const int64_t (&Bs)[3],
+                                         const uint64_t* __restrict__ rowp, int64_t rstride, int32_t r0, int32_t r1,
+                                         int32_t k, int32_t wk, int32_t kend, bool jvalid, bool jin, int32_t i0,
+                                         int32_t span, int32_t N, int32_t g, int32_t lg, uint32_t& empty,
+                                         uint32_t& inbox, uint32_t& my_chunks, uint32_t& my_rows, uint32_t& my_dom,
+                                         uint32_t& my_wide)
+{
+    const bool lead = g == 0;
+    const int32_t spanl = kInterior ? (jvalid ? span : -1) : span;
+    constexpr int kUnroll = kWide ? kWideUnroll : kCountUnroll;
+#pragma unroll kUnroll
+    for (int r = r0; r <= r1; ++r, k += wk, rowp += rstride) {
+        const int32_t lo = max(max((int32_t)(Al[0] >> 32), (int32_t)(Al[1] >> 32)), max((int32_t)(Al[2] >> 32), 0));
+        const int32_t hi = min(min((int32_t)(Ah[0] >> 32), (int32_t)(Ah[1] >> 32)), min((int32_t)(Ah[2] >> 32), spanl));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Al[a] += Bs[a];
+            Ah[a] += Bs[a];
+        }
+        if (kInterior) {
+            if (lo <= hi) {
+                const int32_t a = i0 + lo, e = i0 + hi;
+                const uint32_t len = (uint32_t)(hi - lo + 1);
+                const uint32_t occ = kWide ? popc_range_wide(rowp, a, e, g, lg) : popc_range(rowp, a, e);
+                const uint32_t lead_len = lead ? len : 0u;
+                empty += lead_len - occ;
+                inbox += lead_len;
+                my_dom += lead_len;
+                if (lead) {
+                    my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                    my_rows += 1;
+                    if (kWide) my_wide += 1;
+                }
+            }
+        } else if (jvalid && k < kend && lo <= hi) {
+            const uint32_t len = (uint32_t)(hi - lo + 1);
+            uint32_t occ = 0, dom = 0;
+            if (jin && (uint32_t)k < (uint32_t)N) {
+                const int32_t a = max(i0 + lo, 0), e = min(i0 + hi, N - 1);
+                if (a <= e) {
+                    occ = kWide ? popc_range_wide(rowp, a, e, g, lg) : popc_range(rowp, a, e);
+                    dom = (uint32_t)(e - a + 1);
+                    if (lead) my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                }
+            }
+            const uint32_t lead_len = lead ? len : 0u;
+            empty += lead_len - occ;
+            inbox += lead_len;
+            if (lead) {
+                my_dom += dom;
+                my_rows += 1;
+                if (kWide) my_wide += 1;
+            }
+        }
+    }
+}
+
 #if OBB_COUNT_MINB > 0
 #define OBB_COUNT_BOUNDS __launch_bounds__(256, OBB_COUNT_MINB)
 #else
@@ -588,9 +713,10 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                                                const int32_t* __restrict__ d_K,
                                                unsigned long long* __restrict__ counts,
                                                unsigned long long* __restrict__ points,
-                                               unsigned long long* __restrict__ acc)
+                                               unsigned long long* __restrict__ acc,
+                                               unsigned long long* __restrict__ dom)
 {
-    uint32_t my_chunks = 0, my_rows = 0;
+    uint32_t my_chunks = 0, my_rows = 0, my_dom = 0, my_wide = 0;
     const int lane = threadIdx.x & 31;
     const int32_t K = *d_K;
     const int64_t total = off[K];
@@ -630,7 +756,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         const BoxPrep& p = prep[b];
         {
             // skip a tile whose rectangle misses the box's shadow on (j, k)
-            const int32_t lw = p.lwj, hk = (32 >> lw) * p.tk;
+            const int32_t lw = p.lwj, hk = ((32 >> p.lg) >> lw) * p.tk;
             const float hj = 0.5f * (float)((1 << lw) - 1), hkf = 0.5f * (float)(hk - 1);
             const float jc = (float)(p.j0 + (tj << lw)) + hj, kc = (float)(p.k0 + tk * hk) + hkf;
             bool out = false;
@@ -653,12 +779,15 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         const int32_t N = p.latN, W = p.latW;
         const int32_t mode = p.mode;
         const int32_t lwj = p.lwj;
-        const int32_t wk = 32 >> lwj;
-        const int32_t jl = (tj << lwj) + (lane & ((1 << lwj) - 1));
+        const int32_t lg = p.lg;
+        const int32_t grp = lane >> lg;            // this lane's group (one row at a time)
+        const int32_t g = lane & ((1 << lg) - 1);  // its place in the group
+        const int32_t wk = (32 >> lg) >> lwj;
+        const int32_t jl = (tj << lwj) + (grp & ((1 << lwj) - 1));
         const int32_t j = p.j0 + jl;
         const bool jvalid = jl < p.nj;
         const int32_t tkr = p.tk;
-        const int32_t kb = p.k0 + tk * (wk * tkr) + (lane >> lwj);   // this lane's first row
+        const int32_t kb = p.k0 + tk * (wk * tkr) + (grp >> lwj);   // this group's first row
         const int32_t kend = p.k0 + p.nk;
         // rows r0..r1 (warp-uniform) of the tile's tkr are visited
         int32_t r0 = 0, r1 = tkr - 1;
@@ -675,7 +804,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
             }
             int32_t rl = tkr, rh = -1;
             if (jvalid && klo <= khi) {
-                const int32_t lwk = 5 - lwj;   // wk = 2^lwk
+                const int32_t lwk = 5 - lg - lwj;   // wk = 2^lwk
                 const int32_t kbr = kb - p.k0;
                 const int32_t kl = (int32_t)floorf(fmaxf(klo, -1e9f));
                 const int32_t kh = (int32_t)ceilf(fminf(khi, 1e9f));
@@ -697,7 +826,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 continue;
             }
         }
-        const int32_t kb0 = kb + r0 * wk;   // the first row this lane visits
+        const int32_t kb0 = kb + r0 * wk;   // the first row this group visits
         const int32_t i0 = p.i0, span = p.span;
         // Kind-1 slabs carry exact quotient bounds relative to i0 in 32 bits,
         // saturated at +-2^30: a bound that far out moves less than 2^29 within a
@@ -726,9 +855,8 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         uint32_t empty = 0, inbox = 0;
         const bool jin = j >= 0 && j < N;
         if ((mode & 0xff) == 0x15) {
-            // all three slabs step by DDA (any rotated box): each of the six
-            // bounds is a 32.32 fixed-point value whose integer part is the
-            // quotient, so a bound costs one 64-bit add per row
+            // all three slabs step by DDA (any rotated box): the 32.32
+            // fixed-point bounds, seeded exactly at the first visited row
             int64_t Al[3], Ah[3], Bs[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -739,55 +867,23 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
             }
             const uint64_t* rowp = words + ((int64_t)kb0 * N + j) * W;
             const int64_t rstride = (int64_t)wk * N * W;
-            if ((mode & 0x100) && (tk + 1) * wk * tkr <= p.nk) {
-                // an interior box's full-height tile: every row is in the
-                // lattice and so is every x-interval; an idle lane gets an
-                // empty range
-                const int32_t spanl = jvalid ? span : -1;
-#pragma unroll kCountUnroll
-                for (int r = r0; r <= r1; ++r, rowp += rstride) {
-                    const int32_t lo = max(max(fixed_int(Al[0]), fixed_int(Al[1])), max(fixed_int(Al[2]), 0));
-                    const int32_t hi = min(min(fixed_int(Ah[0]), fixed_int(Ah[1])), min(fixed_int(Ah[2]), spanl));
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        Al[a] += Bs[a];
-                        Ah[a] += Bs[a];
-                    }
-                    if (lo <= hi) {
-                        const int32_t a = i0 + lo, e = i0 + hi;
-                        const uint32_t len = (uint32_t)(hi - lo + 1);
-                        empty += len - popc_range(rowp, a, e);
-                        inbox += len;
-                        my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
-                        my_rows += 1;
-                    }
-                }
+            // an interior box's full-height tile: every row is in the lattice
+            // and so is every x-interval; an idle lane gets an empty range
+            const bool interior = (mode & 0x100) && (tk + 1) * wk * tkr <= p.nk;
+            if (lg == 0) {
+                if (interior)
+                    dda_rows<false, true>(Al, Ah, Bs, rowp, rstride, r0, r1, kb0, wk, kend, jvalid, jin, i0, span, N,
+                                          g, lg, empty, inbox, my_chunks, my_rows, my_dom, my_wide);
+                else
+                    dda_rows<false, false>(Al, Ah, Bs, rowp, rstride, r0, r1, kb0, wk, kend, jvalid, jin, i0, span, N,
+                                           g, lg, empty, inbox, my_chunks, my_rows, my_dom, my_wide);
             } else {
-                int32_t k = kb0;
-#pragma unroll kCountUnroll
-                for (int r = r0; r <= r1; ++r, k += wk, rowp += rstride) {
-                    const int32_t lo = max(max(fixed_int(Al[0]), fixed_int(Al[1])), max(fixed_int(Al[2]), 0));
-                    const int32_t hi = min(min(fixed_int(Ah[0]), fixed_int(Ah[1])), min(fixed_int(Ah[2]), span));
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        Al[a] += Bs[a];
-                        Ah[a] += Bs[a];
-                    }
-                    if (jvalid && k < kend && lo <= hi) {
-                        const uint32_t len = (uint32_t)(hi - lo + 1);
-                        uint32_t occ = 0;
-                        if (jin && (uint32_t)k < (uint32_t)N) {
-                            const int32_t a = max(i0 + lo, 0), e = min(i0 + hi, N - 1);
-                            if (a <= e) {
-                                occ = popc_range(rowp, a, e);
-                                my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
-                            }
-                        }
-                        empty += len - occ;
-                        inbox += len;
-                        my_rows += 1;
-                    }
-                }
+                if (interior)
+                    dda_rows<true, true>(Al, Ah, Bs, rowp, rstride, r0, r1, kb0, wk, kend, jvalid, jin, i0, span, N,
+                                         g, lg, empty, inbox, my_chunks, my_rows, my_dom, my_wide);
+                else
+                    dda_rows<true, false>(Al, Ah, Bs, rowp, rstride, r0, r1, kb0, wk, kend, jvalid, jin, i0, span, N,
+                                          g, lg, empty, inbox, my_chunks, my_rows, my_dom, my_wide);
             }
         } else
 #pragma unroll kCountUnroll
@@ -834,6 +930,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                     if (a <= e) {
                         occ = popc_range(words + ((int64_t)k * N + j) * W, a, e);
                         my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                        my_dom += (uint32_t)(e - a + 1);
                     }
                 }
                 empty += len - occ;
@@ -855,17 +952,21 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         }
         ++c;
     }
-    if (acc) {   // profiling: algorithmic bytes and non-empty rows of this launch
-        __shared__ unsigned long long sh[2];
-        if (threadIdx.x < 2) sh[threadIdx.x] = 0;
+    // in-domain points of this launch (always), and with profiling its
+    // algorithmic bytes, non-empty rows and rows shared by lane groups: block
+    // sums, one atomic each
+    if (acc || dom) {
+        __shared__ unsigned long long sh[4];
+        if (threadIdx.x < 4) sh[threadIdx.x] = 0;
         __syncthreads();
-        unsigned long long v[2] = {my_chunks * 16ull, my_rows};
-        for (int i = 0; i < 2; ++i) {
+        unsigned long long v[4] = {my_chunks * 16ull, my_rows, my_dom, my_wide};
+        for (int i = 0; i < 4; ++i) {
             for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-            if (lane == 0) atomicAdd(&sh[i], v[i]);
+            if (lane == 0 && v[i]) atomicAdd(&sh[i], v[i]);
         }
         __syncthreads();
-        if (threadIdx.x < 2 && sh[threadIdx.x]) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
+        if (threadIdx.x < 4 && threadIdx.x != 2 && acc && sh[threadIdx.x]) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
+        if (threadIdx.x == 2 && dom && sh[2]) atomicAdd(dom, sh[2]);
     }
 }
 
@@ -995,7 +1096,7 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
     k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K,
                                             reinterpret_cast<unsigned long long*>(d_counts),
                                             reinterpret_cast<unsigned long long*>(d_points),
-                                            ctx->prof ? ctx->d_prof : nullptr);
+                                            ctx->prof ? ctx->d_prof : nullptr, ctx->d_prof + 2);
     note_launch(ctx);
     if (ctx->prof) {
         OBB_CK(ctx, cudaEventRecord(e1, s));
@@ -1093,7 +1194,7 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
     note_launch(ctx);
     k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, dK,
                                             reinterpret_cast<unsigned long long*>(d_counts),
-                                            reinterpret_cast<unsigned long long*>(d_points), nullptr);
+                                            reinterpret_cast<unsigned long long*>(d_points), nullptr, nullptr);
     note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return OBB_OK;

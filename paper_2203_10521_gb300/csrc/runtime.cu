@@ -172,6 +172,8 @@ obb_status obb_create(obb_ctx** out, int32_t device, void* stream)
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&c->d_err, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_ticket, sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc((void**)&c->d_prof, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->d_prof, 0, 8 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&c->h_small, 64 * sizeof(int64_t)) != cudaSuccess ||
         cudaMemset(c->d_err, 0, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(c->d_ticket, 0, sizeof(unsigned int)) != cudaSuccess) {
@@ -284,7 +286,6 @@ obb_status obb_profile_enable(obb_ctx* ctx, int32_t on)
         cudaEventDestroy(ev.second);
     }
     ctx->prof_ev.clear();
-    if (!ctx->d_prof) OBB_CK(ctx, cudaMalloc((void**)&ctx->d_prof, 8 * sizeof(unsigned long long)));
     OBB_CK(ctx, cudaMemset(ctx->d_prof, 0, 8 * sizeof(unsigned long long)));
     ctx->prof = on != 0;
     return OBB_OK;
@@ -307,6 +308,8 @@ obb_status obb_profile_read(obb_ctx* ctx, obb_profile_stats* out)
     if (ctx->d_prof) OBB_CK(ctx, cudaMemcpy(acc, ctx->d_prof, sizeof(acc), cudaMemcpyDeviceToHost));
     out->count_bytes = (double)acc[0];
     out->count_rows = (double)acc[1];
+    out->count_points_in_domain = (double)acc[2];
+    out->count_rows_shared = (double)acc[3];
     return OBB_OK;
 }
 

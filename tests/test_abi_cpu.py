@@ -33,7 +33,7 @@ def test_struct_layouts_match_header():
     assert P.QBOX_DTYPE.itemsize == 88 and P.QBOX_DTYPE.fields["b"][1] == 40
     assert ctypes.sizeof(P.StepStats) == 56
     assert ctypes.sizeof(P.TreeOpts) == 16
-    assert ctypes.sizeof(P.ProfileStats) == 40
+    assert ctypes.sizeof(P.ProfileStats) == 56
     assert ctypes.sizeof(P.SweepOpts) == 16
     assert ctypes.sizeof(P.SweepStats) == 40
     assert ctypes.sizeof(P.FloodStats) == 16

@@ -1,6 +1,9 @@
-"""GPU parity on the large workloads: the ~1M-triangle SDF union on a 768^3
-lattice and the ~2M-triangle union of spheres, capsules and rounded boxes on
-1024^3.  The oracle checks sampled occupancy rows and small boxes exactly."""
+"""GPU parity on the large workloads: the ~200k-triangle SDF union on 512^3,
+the ~1M-triangle union on 768^3 and the ~2M-triangle union of spheres,
+capsules and rounded boxes on 1024^3.  The oracle checks whole lattices and
+the boxes of the trees built on them exactly."""
+import os
+
 import numpy as np
 import pytest
 
@@ -33,32 +36,47 @@ def _small_boxes(rng, K, lo, hi, half_lo, half_hi):
     return out
 
 
-@pytest.mark.parametrize("name,N,ncols,nbox", [("1m", 768, 48, 4), ("2m", 1024, 32, 3)])
-def test_large_config_sampled_parity(ctx, name, N, ncols, nbox):
-    m = M.sdf_union_1m() if name == "1m" else M.sdf_union_2m()
-    assert m.n_tris > (900_000 if name == "1m" else 1_800_000)
-    mesh = ctx.mesh_create(m.verts, m.tris)
-    lat = ctx.build_occupancy(mesh, N)
-    P = O.Problem(m.verts, m.tris, N, adj=np.zeros((m.n_tris, 3), np.int32))
-    assert np.array_equal(lat.lo, P.lo) and np.array_equal(lat.spacing, P.h)
-    assert np.array_equal(lat.fixed().cpu().numpy(), P.U)
-    rng = np.random.Generator(np.random.PCG64(N))
-    cols = rng.integers(0, N, size=(ncols, 2))
-    P.occ.fill_columns(cols)
-    w = lat.words().cpu().numpy().view(np.uint64).reshape(N, N, lat.W)
-    for j, k in cols:
-        row = np.unpackbits(w[k, j].view(np.uint8), bitorder="little")
-        assert np.array_equal(row[:N], P.occ.occ[k, j])
-        assert not row[N:].any()
-    ext = P.lo + N * P.h
-    boxes = _small_boxes(rng, nbox, P.lo + 0.3 * (ext - P.lo), P.lo + 0.7 * (ext - P.lo), 0.004, 0.012)
-    cnt, pts = ctx.outer_volume(lat, boxes, want_points=True)
-    n, bnd = O.quantize_boxes(boxes, P.lo, P.h)
-    ref, tot = O.outer_volume(P.occ, n, bnd)
-    assert np.array_equal(cnt, ref) and np.array_equal(pts, tot)
-    assert tot.min() > 100
-    lat.free()
-    mesh.free()
+@pytest.mark.parametrize("name,N,depth", [("1m", 768, 12), ("2m", 1024, 14)])
+def test_large_config_full_parity(ctx, name, N, depth):
+    """The ~1M-triangle union on 768^3 and the ~2M-triangle union on 1024^3:
+    every occupancy word of the whole lattice equals the oracle's per-point
+    parity (padding bits zero), and the boxes of the top four levels of the
+    tree built on it (depth 12 / 14), plus 12 boxes drawn from every lower
+    level, count exactly as the oracle counts them, with their in-domain
+    points."""
+    O.set_threads(os.cpu_count() or 1)
+    try:
+        m = M.sdf_union_1m() if name == "1m" else M.sdf_union_2m()
+        assert m.n_tris > (900_000 if name == "1m" else 1_800_000)
+        mesh = ctx.mesh_create(m.verts, m.tris)
+        lat = ctx.build_occupancy(mesh, N)
+        P = O.Problem(m.verts, m.tris, N, adj=np.zeros((m.n_tris, 3), np.int32))
+        assert np.array_equal(lat.lo, P.lo) and np.array_equal(lat.spacing, P.h)
+        assert np.array_equal(lat.fixed().cpu().numpy(), P.U)
+        P.occ.fill_all()
+        w = lat.words().cpu().numpy().view(np.uint8).reshape(N, N, 8 * lat.W)
+        nb = N // 8
+        assert np.array_equal(w[:, :, :nb], np.packbits(P.occ.occ, axis=-1, bitorder="little"))
+        assert not w[:, :, nb:].any()
+        tree = ctx.build_tree(lat, depth, 1)
+        rng = np.random.Generator(np.random.PCG64(N))
+        qs = []
+        for lev in range(depth + 1):
+            q = ctx.tree_read(tree, lev)["qboxes"]
+            qs.append(q if lev < 4 else q[rng.choice(len(q), 12, replace=False)])
+        q = np.concatenate(qs)
+        ctx.profile_enable(True)
+        cnt, pts = ctx.outer_volume_q(lat, q, want_points=True)
+        pr = ctx.profile_read()
+        ctx.profile_enable(False)
+        ref, tot, dom = O.outer_volume(P.occ, q["n"], q["b"], want_domain=True)
+        assert np.array_equal(cnt, ref) and np.array_equal(pts, tot)
+        assert pr["count_points_in_domain"] == float(dom.sum())
+        tree.free()
+        lat.free()
+        mesh.free()
+    finally:
+        O.set_threads(1)
 
 
 def test_batched_meshes_one_launch(ctx):
@@ -125,35 +143,41 @@ def test_sweeps_at_scale(ctx):
     mesh.free()
 
 
-def test_benchmark_batch_invariant_at_scale(ctx):
+def test_benchmark_batch_against_oracle(ctx):
     """The benchmark's batch at full size: the 2,047 boxes of a depth-10 tree on
     the ~200k-triangle union at 512^3 (up to the whole lattice, so large boxes
-    take the doubled tile height) count the same, box by box, for every tile
-    height, for rows along each axis and for the per-box axis; leaf boxes of
-    this tree are checked against the oracle in test_sweeps_at_scale."""
+    take shared rows and the doubled tile height) count exactly as the oracle
+    counts them, box by box, for tile heights 8 to 64, for rows along each axis
+    and for the per-box axis; the whole lattice is bit-exact."""
+    O.set_threads(os.cpu_count() or 1)
     m = M.sdf_union_200k()
     mesh = ctx.mesh_create(m.verts, m.tris)
     try:
         ctx.set_counting_axis(-1)   # this lattice keeps its y- and z-row copies
         lat = ctx.build_occupancy(mesh, 512)
         ctx.set_counting_axis(0)
-        tree = ctx.build_tree(lat, 10, 1)
+        P = O.Problem(m.verts, m.tris, 512, adj=np.zeros((m.n_tris, 3), np.int32))
+        P.occ.fill_all()
+        assert np.array_equal(lat.bits(), P.occ.occ)
+        tree = ctx.build_tree(lat, 10, 2)
         q = np.concatenate([ctx.tree_read(tree, lev)["qboxes"] for lev in range(11)])
         assert len(q) == 2047
+        ref, tot = O.outer_volume(P.occ, q["n"], q["b"])
         base, bpts = ctx.outer_volume_q(lat, q, want_points=True)
-        assert (bpts > 0).all() and (base <= bpts).all()
+        assert np.array_equal(base, ref) and np.array_equal(bpts, tot)
         for tk in (8, 16, 64):
             ctx.set_counting_tile(tk)
             c, p = ctx.outer_volume_q(lat, q, want_points=True)
-            assert np.array_equal(c, base) and np.array_equal(p, bpts), tk
+            assert np.array_equal(c, ref) and np.array_equal(p, tot), tk
         ctx.set_counting_tile(32)
         for axis in (1, 2, -1):
             ctx.set_counting_axis(axis)
             c, p = ctx.outer_volume_q(lat, q, want_points=True)
-            assert np.array_equal(c, base) and np.array_equal(p, bpts), axis
+            assert np.array_equal(c, ref) and np.array_equal(p, tot), axis
     finally:
         ctx.set_counting_axis(0)
         ctx.set_counting_tile(32)
+        O.set_threads(1)
     tree.free()
     lat.free()
     mesh.free()

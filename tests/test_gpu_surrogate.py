@@ -1,6 +1,6 @@
-"""GPU parity and behaviour of the learned surrogate: features bit-exact,
-forward and gradients against the FP64 oracle network, training on real
-candidate boxes, and screened Lloyd iterations against plain ones."""
+"""GPU parity and behaviour of the learned surrogate: features against their
+definition, forward and gradients against the FP64 oracle network, training
+on real candidate boxes, and screened Lloyd iterations against plain ones."""
 import time
 
 import numpy as np
@@ -47,12 +47,25 @@ def _rand_qboxes(ctx, lat, rng, K):
     return ctx.quantize_boxes(lat, out)
 
 
-def test_features_bit_exact(ctx, torus):
+def test_features_match_definition(ctx, torus):
+    """The kernel's features (FP32 arithmetic) against their definition (the
+    oracle: FP64 parameters from exact integers, patch bits at the exact
+    rational sample points): every patch bit whose sample point lies more than
+    1e-3 cells from a rounding tie is equal, and the 12 box parameters agree
+    to FP32 accuracy.  The share of tie-adjacent bits and the disagreements
+    among them are reported."""
     m, mesh, lat, P = torus
     q = _rand_qboxes(ctx, lat, np.random.Generator(np.random.PCG64(1)), 300)
     f = ctx.surrogate_features(lat, q)
-    ref = O.surrogate_features(P.occ, q["n"], q["b"])
-    assert np.array_equal(f, ref)
+    ref, tie = O.surrogate_features(P.occ, q["n"], q["b"], return_ties=True)
+    assert np.allclose(f[:, :12], ref[:, :12], rtol=1e-5, atol=1e-5)
+    far = tie == 0
+    assert np.array_equal(f[:, 12:][far], ref[:, 12:][far])
+    near = int((~far).sum())
+    differ = int((f[:, 12:] != ref[:, 12:]).sum())
+    print(f"patch bits near a rounding tie: {near} of {far.size} ({near / far.size:.2e}); "
+          f"of these {differ} differ; max parameter error {np.abs(f[:, :12] - ref[:, :12]).max():.2e}")
+    assert far.mean() > 0.99
 
 
 def test_forward_and_gradients_match_fp64_oracle(ctx):

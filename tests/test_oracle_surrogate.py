@@ -61,10 +61,11 @@ def test_features_of_axis_aligned_box_on_known_solid():
 
 
 def test_features_of_rotated_boxes_match_exact_rationals():
-    """Rotated boxes on the torus: every patch bit whose exact sample point
-    M^-1 v (rational arithmetic) is more than 1e-3 from a rounding tie equals
-    the occupancy at that point rounded; the box parameters agree with their
-    exact values to FP32 accuracy."""
+    """Rotated boxes on the torus: every patch bit equals the occupancy at the
+    exact sample point M^-1 v (Python rationals) rounded to the nearest
+    lattice point, ties included, and the tie flag marks exactly the points
+    within 1e-3 of a half-integer; the box parameters agree with their exact
+    values to FP32 rounding."""
     from fractions import Fraction as Fr
     m = M.torus_4096()
     N = 64
@@ -78,8 +79,8 @@ def test_features_of_rotated_boxes_match_exact_rationals():
         boxes[i, 3:6], boxes[i, 6:9] = R[0], R[1]
         boxes[i, 9:12] = rng.uniform(0.05, 0.6, 3)
     n, bnd = O.quantize_boxes(boxes, P.lo, P.h)
-    f = O.surrogate_features(P.occ, n, bnd)
-    checked = 0
+    f, tie = O.surrogate_features(P.occ, n, bnd, return_ties=True)
+    checked = ties = 0
     for b in range(len(n)):
         Mi = [[int(v) for v in n[b, 3 * a:3 * a + 3]] for a in range(3)]
         L = [-((-int(bnd[b, 2 * a])) // 256) for a in range(3)]
@@ -90,20 +91,21 @@ def test_features_of_rotated_boxes_match_exact_rationals():
                     - Mi[(c + 1) % 3][(r + 2) % 3] * Mi[(c + 2) % 3][(r + 1) % 3]), det) for c in range(3)] for r in range(3)]
         mid = [Fr(L[a] + H[a], 2) for a in range(3)]
         cen = [sum(inv[r][a] * mid[a] for a in range(3)) for r in range(3)]
-        assert np.allclose(f[b, :3], [float(x / N) for x in cen], rtol=1e-6, atol=1e-7)
+        assert np.array_equal(f[b, :3], np.array([float(x / N) for x in cen], np.float32))
         for a in range(2):
             nn = np.sqrt(sum(float(x) ** 2 for x in Mi[a]))
-            assert np.allclose(f[b, 3 + 3 * a:6 + 3 * a], np.array(Mi[a]) / nn, rtol=1e-6, atol=1e-7)
+            assert np.allclose(f[b, 3 + 3 * a:6 + 3 * a], np.array(Mi[a]) / nn, rtol=1e-7, atol=1e-8)
         bits = f[b, 12:]
         for s in range(512):
             sv = (s & 7, (s >> 3) & 7, s >> 6)
             v = [L[a] + Fr((H[a] - L[a]) * (2 * sv[a] + 1), 16) for a in range(3)]
             p = [sum(inv[r][a] * v[a] for a in range(3)) for r in range(3)]
-            if any(abs(x - (x.numerator // x.denominator) - Fr(1, 2)) < Fr(1, 1000) for x in p):
-                continue
+            near = any(abs(x - (x.numerator // x.denominator) - Fr(1, 2)) < Fr(1, 1000) for x in p)
+            assert bool(tie[b, s]) == near, (b, s)
+            ties += near
             idx = [int((x + Fr(1, 2)) // 1) for x in p]
             inside = all(0 <= i < N for i in idx)
             want = float(P.occ.occ[idx[2], idx[1], idx[0]]) if inside else 0.0
             assert bits[s] == want, (b, s)
             checked += 1
-    assert checked > 5000
+    assert checked == 12 * 512
