@@ -2,20 +2,29 @@
 """Benchmark of the outer-volume / Lloyd hot path on one GB300 per rank.
 
 One step = one pass of the whole path over the workload's batch:
-  occupancy rebuild of the 512^3 lattice from the resident mesh (snap,
-  column crossings, row scan), exact outer volume of every box of the
-  depth-10 tree (2047 FP32 boxes: quantise + count), and one Lloyd iteration
-  on the 1,024-leaf layer (partition rounds with exact gains + covariance /
-  Jacobi refit), whose layer total is the Eq. 7 leaf term.
-value = lattice points counted by the outer-volume kernel per second of
-step time (whole job: summed over ranks, divided by the slowest rank).
+  occupancy rebuild of the lattice from the resident mesh (snap, column
+  crossings, row scan with the rank tables), exact outer volume of every box
+  of the tree (FP32 boxes: quantise + count; Eq. 4), and one Lloyd iteration
+  on the leaf layer (partition rounds with exact gains + covariance / Jacobi
+  refit, as the library's CUDA graph), whose layer total is the Eq. 7 leaf
+  term.
+value = in-domain lattice points counted by the outer-volume kernel (every
+counting launch of the step, the Lloyd iteration's included) per second of
+step time; whole job: summed over ranks, divided by the slowest rank.
 
-Workload: the seeded SDF union of 40 spheres + 20 capsules, ~200k
-watertight triangles (marching tetrahedra), 512^3 lattice, binary tree of
-depth 10.  --small runs the 4,096-triangle torus on 64^3, depth 4.
+Workloads (--workload):
+  sdf2m-1024   (default) the seeded SDF union of 200 spheres + 100 capsules +
+               50 rounded boxes, 2,029,088 watertight triangles (marching
+               tetrahedra), 1024^3 lattice (128 MiB, larger than L2), binary
+               tree of depth 14 (16,384 leaves), three reciprocating
+               bottom-up / top-down sweeps after the top-down build;
+  sdf200k-512  the union of 40 spheres + 20 capsules, 202,244 triangles,
+               512^3 lattice, depth 10;
+  torus4k-64   (--small) the 4,096-triangle torus on 64^3, depth 4.
 
 --impl reference times the CPU oracle (the plain per-point restatement) on a
-bounded sample of the same workload.
+bounded sample of the same workload, the same way as the GPU line's
+cpu_baseline.
 """
 from __future__ import annotations
 
@@ -42,14 +51,15 @@ UNIT = "lattice pts/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--small", action="store_true", help="4,096-triangle torus on 64^3 (the oracle-sized case)")
-    ap.add_argument("--setup-iters", type=int, default=2, help="Lloyd iterations per level while seeding the tree")
+    ap.add_argument("--workload", default="sdf2m-1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--small", action="store_true", help="the 4,096-triangle torus on 64^3 (--workload torus4k-64)")
+    ap.add_argument("--setup-iters", type=int, default=2, help="Lloyd iterations per level while building the tree")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="oracle time per thread count in cpu_baseline")
     ap.add_argument("--eager-step", action="store_true",
                     help="host-driven Lloyd rounds in the timed step (default: the step's CUDA graph)")
     ap.add_argument("--no-surrogate", action="store_true")
@@ -57,18 +67,49 @@ def parse():
                     help="candidates (and rotation probes) per cluster the surrogate keeps for exact counting")
     ap.add_argument("--lloyd-iters", type=int, default=10,
                     help="Lloyd iterations timed for the plain vs surrogate comparison")
-    return ap.parse_args()
+    ap.add_argument("--walk", action="store_true", help="count every row word by word (no rank tables)")
+    ap.add_argument("--profile-batch", metavar="BOXES",
+                    help="profiling aid: count the tree batch twice and exit; the tree's boxes are read from "
+                         "BOXES (.npy) when it exists, else built and written there")
+    a = ap.parse_args()
+    if a.small:
+        a.workload = "torus4k-64"
+    return a
 
 
-def workload(small: bool, rank: int):
+def _torus(rank):
     from synth import meshes as M
-    if small:
-        m = M.torus(1.0, 0.3, 64, 32, jitter=0.002, seed=1000 + rank)
-        return dict(name="torus R=1 r=0.3, 4,096 triangles, 64^3 lattice, depth 4", mesh=m, N=64, depth=4,
-                    iters=10)
-    m = M.sdf_union_200k(seed=2000 + rank)
-    return dict(name=f"SDF union 40 spheres + 20 capsules, {m.n_tris:,} triangles, 512^3 lattice, depth 10 "
-                     f"(1,024 leaves)", mesh=m, N=512, depth=10, iters=20)
+    return M.torus(1.0, 0.3, 64, 32, jitter=0.002, seed=1000 + rank)
+
+
+def _sdf200k(rank):
+    from synth import meshes as M
+    return M.sdf_union_200k(seed=2000 + rank)
+
+
+def _sdf2m(rank):
+    from synth import meshes as M
+    return M.sdf_union_2m(seed=5000 + rank)
+
+
+WORKLOADS = {
+    "sdf2m-1024": dict(desc="SDF union 200 spheres + 100 capsules + 50 rounded boxes, {T:,} triangles, 1024^3 "
+                            "lattice, depth 14 (16,384 leaves), 3 up/down sweeps", mesh=_sdf2m, N=1024, depth=14,
+                       sweeps=3),
+    "sdf200k-512": dict(desc="SDF union 40 spheres + 20 capsules, {T:,} triangles, 512^3 lattice, depth 10 "
+                             "(1,024 leaves)", mesh=_sdf200k, N=512, depth=10, sweeps=0),
+    "torus4k-64": dict(desc="torus R=1 r=0.3, {T:,} triangles, 64^3 lattice, depth 4", mesh=_torus, N=64, depth=4,
+                       sweeps=0),
+}
+
+
+def workload(name: str, rank: int):
+    w = dict(WORKLOADS[name])
+    m = w["mesh"](rank)
+    w["mesh"] = m
+    w["name"] = w["desc"].format(T=m.n_tris)
+    w["key"] = name
+    return w
 
 
 def measured_peaks():
@@ -79,14 +120,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def count_kernel_traffic(key="dram_bytes_per_launch"):
-    """DRAM bytes per launch of the counting kernel from the committed ncu
-    summary (`key`: the average over a step's launches, or the batch launch
-    alone), valid only while the kernel source is unchanged."""
-    p = os.path.join(ROOT, "profiles", "k_count_roofline_inputs.txt")
+def roofline_inputs(workload_key):
+    """DRAM bytes and warp instructions per batch launch of the counting kernel
+    from the committed ncu summary of this workload; valid only while the
+    kernel source is unchanged (else the values are null)."""
+    p = os.path.join(ROOT, "profiles", f"k_count_{workload_key}_roofline_inputs.txt")
     src = os.path.join(ROOT, "paper_2203_10521_gb300", "csrc", "outer_volume.cu")
     if not os.path.exists(p):
-        return None, None
+        return {}
     kv = {}
     for line in open(p):
         if "=" in line and not line.startswith("#"):
@@ -94,11 +135,14 @@ def count_kernel_traffic(key="dram_bytes_per_launch"):
             kv[k.strip()] = v.strip()
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if kv.get("source_sha256_16") != h:
-        return None, kv.get("workload")
-    try:
-        return float(kv[key]), kv.get("workload")
-    except (KeyError, ValueError):
-        return None, None
+        return {"stale": True}
+    out = {}
+    for k in ("dram_bytes_batch_launch", "warp_inst_batch_launch", "alu_pipe_pct", "issue_active_pct"):
+        try:
+            out[k] = float(kv[k])
+        except (KeyError, ValueError):
+            pass
+    return out
 
 
 class ClockSampler:
@@ -170,173 +214,163 @@ def tree_boxes(ctx, tree, depth):
     return np.ascontiguousarray(np.concatenate(boxes))
 
 
-def cpu_oracle_sample(wl, boxes_q_n, boxes_q_b, budget_s):
-    """The oracle as it stands, single threaded: per-point occupancy of the
-    columns a box needs, then the per-point count, box by box until the time
-    budget is spent.  Returns (points/s, points, boxes, seconds)."""
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_leaf_boxes(P, depth):
+    """The oracle's own leaf boxes of the workload: median splits (Sec. 4.2.2
+    top-down decomposition, reading R18) of every node down to `depth`, each
+    child's frame from the area-weighted covariance and its tight slab bounds.
+    No counting happens here."""
     import oracle as O
-    m = wl["mesh"]
-    P = O.Problem(m.verts, m.tris, wl["N"], adj=np.zeros((m.n_tris, 3), np.int32))
-    pts = 0
-    nb = 0
+    T = P.F.shape[0]
+    assign = np.zeros(T, np.int32)
+    fr = O.cluster_frames(P.V, P.F, assign, 1, P.center)
+    n = O.frame_normals(fr, P.h)
+    L = O.Layer(assign, np.zeros(1, np.int32), fr, n, O.tight_bounds(P.U, P.F, assign, 1, n), np.zeros(1, np.uint64))
+    K = 1
+    for _ in range(depth):
+        child = O.median_split(P, L)
+        K *= 2
+        fr = O.cluster_frames(P.V, P.F, child, K, P.center, fallback=np.repeat(L.frames, 2, axis=0))
+        n = O.frame_normals(fr, P.h)
+        L = O.Layer(child, (np.arange(K) // 2).astype(np.int32), fr, n, O.tight_bounds(P.U, P.F, child, K, n),
+                    np.zeros(K, np.uint64))
+    return L.n, L.bnd
+
+
+def oracle_rate(m, N, n, bnd, order, budget_s, threads):
+    """The oracle as it stands on a fresh Problem (no column computed yet):
+    leaf boxes in the seeded order, each one per-point occupancy of the
+    columns it covers + per-point count (Eq. 4), until the time budget is
+    spent.  Returns (in-domain points/s, points, boxes, seconds, threads)."""
+    import oracle as O
+    used = O.set_threads(threads)
+    P = O.Problem(m.verts, m.tris, N, adj=np.zeros((m.n_tris, 3), np.int32))
+    pts = nb = 0
     t0 = time.perf_counter()
-    for i in range(len(boxes_q_n)):
-        cnt, tot = O.outer_volume(P.occ, boxes_q_n[i:i + 1], boxes_q_b[i:i + 1])
-        pts += int(tot[0])
+    for k in order:
+        _, _, dom = O.outer_volume(P.occ, n[k:k + 1], bnd[k:k + 1], want_domain=True)
+        pts += int(dom[0])
         nb += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return pts / dt, pts, nb, dt
+    O.set_threads(1)
+    return pts / dt, pts, nb, dt, used
+
+
+def oracle_setup(wl):
+    import oracle as O
+    O.build()
+    m = wl["mesh"]
+    P = O.Problem(m.verts, m.tris, wl["N"], adj=np.zeros((m.n_tris, 3), np.int32))
+    t0 = time.perf_counter()
+    n, bnd = oracle_leaf_boxes(P, wl["depth"])
+    order = np.random.Generator(np.random.PCG64(7)).permutation(len(n))
+    return n, bnd, order, time.perf_counter() - t0
+
+
+def cpu_baseline(wl, budget_s):
+    n, bnd, order, tree_s = oracle_setup(wl)
+    cores = os.cpu_count() or 1
+    v1, p1, nb1, dt1, _ = oracle_rate(wl["mesh"], wl["N"], n, bnd, order, budget_s, 1)
+    va, pa, nba, dta, used = oracle_rate(wl["mesh"], wl["N"], n, bnd, order, budget_s, cores)
+    return {"value": va, "unit": UNIT, "cores": used, "kind": "oracle",
+            "single_thread_value": v1, "nproc": cores,
+            "sample": (f"leaf boxes of the oracle's own depth-{wl['depth']} median-split tree in a seeded order, each "
+                       f"per-point occupancy of its columns + per-point count, in-domain points: {nba} boxes "
+                       f"({pa:,} points) in {dta:.1f} s on {used} threads; {nb1} boxes ({p1:,} points) in "
+                       f"{dt1:.1f} s on 1 thread; oracle tree {tree_s:.1f} s (untimed)")}
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle, timed on this host, rank 0 only."""
+    """Reference arm: the CPU oracle on this host's cores, rank 0 only; each
+    step a bounded sample of the workload, timed as the GPU line's
+    cpu_baseline times it (all cores)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle as O
-    O.build()
-    wl = workload(args.small, 0)
-    m = wl["mesh"]
-    N = wl["N"]
-    # boxes: leaf-sized boxes of the workload -- the oracle's own tree is far too
-    # slow at this size, so use median-split boxes of the oracle's root frame
-    P = O.Problem(m.verts, m.tris, N, adj=np.zeros((m.n_tris, 3), np.int32))
-    T = m.n_tris
-    fr = O.cluster_frames(P.V, P.F, np.zeros(T, np.int32), 1, P.center)
-    L = O.Layer(np.zeros(T, np.int32), np.zeros(1, np.int32), fr, O.frame_normals(fr, P.h),
-                O.tight_bounds(P.U, P.F, np.zeros(T, np.int32), 1, O.frame_normals(fr, P.h)), np.zeros(1, np.uint64))
-    assign = np.zeros(T, np.int32)
-    K = 1
-    for _ in range(wl["depth"]):
-        child = O.median_split(P, L)
-        K *= 2
-        fr = np.repeat(L.frames, 2, axis=0)
-        n = O.frame_normals(fr, P.h)
-        L = O.Layer(child, (np.arange(K) // 2).astype(np.int32), fr, n, O.tight_bounds(P.U, P.F, child, K, n),
-                    np.zeros(K, np.uint64))
-    rng = np.random.Generator(np.random.PCG64(7))
-    order = rng.permutation(K)
-    per_step = max(args.cpu_seconds / max(args.steps + args.warmup, 1), 0.5)
-    vals, times = [], []
-    i = 0
+    wl = workload(args.workload, 0)
+    n, bnd, order, tree_s = oracle_setup(wl)
+    cores = os.cpu_count() or 1
+    per_step = max(min(args.cpu_seconds, 120.0 / max(args.steps + args.warmup, 1)), 0.5)
+    vals, times, pts_all, nb_all, used = [], [], 0, 0, 1
+    at = 0
     for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        pts = 0
-        while time.perf_counter() - t0 < per_step:
-            k = order[i % K]
-            i += 1
-            cnt, tot = O.outer_volume(P.occ, L.n[k:k + 1], L.bnd[k:k + 1])
-            pts += int(tot[0])
-        dt = time.perf_counter() - t0
+        sl = np.roll(order, -at)
+        v, pts, nb, dt, used = oracle_rate(wl["mesh"], wl["N"], n, bnd, sl, per_step, cores)
+        at = (at + nb) % len(order)
         if s >= args.warmup:
-            vals.append(pts / dt)
+            vals.append(v)
             times.append(dt)
-    v = float(np.mean(vals))
-    sample = (f"{i} leaf boxes (median-split seeds of the {K:,}-leaf level), per-point occupancy of their "
-              f"columns + per-point count, single thread, about {per_step:.1f} s per step")
+            pts_all += pts
+            nb_all += nb
+    v = float(np.sum(pts_all) / np.sum(times))
+    sample = (f"{nb_all} leaf boxes of the oracle's own depth-{wl['depth']} median-split tree over {args.steps} "
+              f"steps of about {per_step:.1f} s, each box per-point occupancy of its columns + per-point count, "
+              f"in-domain points, {used} threads (nproc {cores})")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * float(np.mean(times)),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
            "data": "synthetic", "config": {"workload": wl["name"]},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def profile_batch(args):
+    """Two counts of the tree batch on the resident lattice (for ncu); the
+    boxes come from the file when it exists (few launches before the
+    counts), else from the tree built here, which is then saved."""
     import torch
-    import torch.distributed as dist
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-
     import paper_2203_10521_gb300 as P
-
-    wl = workload(args.small, rank)
+    torch.cuda.set_device(0)
+    wl = workload(args.workload, 0)
     m = wl["mesh"]
-    N, depth = wl["N"], wl["depth"]
-    ctx = P.Context(local)
+    ctx = P.Context(0)
+    if args.walk:
+        ctx.set_counting_rank(0)
     mesh = ctx.mesh_create(m.verts, m.tris)
-    lat = ctx.build_occupancy(mesh, N)
-    t0 = time.perf_counter()
-    tree = ctx.build_tree(lat, depth, args.setup_iters)
+    lat = ctx.build_occupancy(mesh, wl["N"])
+    path = args.profile_batch
+    if os.path.exists(path):
+        boxes = np.load(path)
+    else:
+        tree = ctx.build_tree(lat, wl["depth"], args.setup_iters)
+        if wl["sweeps"]:
+            ctx.tree_sweep(tree, sweeps=wl["sweeps"], iters=1)
+        boxes = tree_boxes(ctx, tree, wl["depth"])
+        np.save(path, boxes)
+        tree.free()
+    d = torch.from_numpy(boxes).cuda()
+    c = ctx.outer_volume(lat, d)
+    torch.cuda.nvtx.range_push("profile_batch")
+    ctx.outer_volume(lat, d, counts=c)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
-    tree_s = time.perf_counter() - t0
-    boxes = tree_boxes(ctx, tree, depth)
-    d_boxes = torch.from_numpy(boxes).cuda()
-    d_counts = torch.empty(len(boxes), dtype=torch.int64, device="cuda")
-    d_points = torch.empty(len(boxes), dtype=torch.int64, device="cuda")
-    leaf = ctx.tree_read(tree, depth)
-    K = 1 << depth
-    parent = (np.arange(K) // 2).astype(np.int32)
-    layer = ctx.layer_init(lat, leaf["assign"], parent, leaf["frames"])
-    # lattice points of the batch (constant: same boxes on the same lattice)
-    _, pts0 = ctx.outer_volume(lat, boxes, want_points=True)
-    batch_points = int(pts0.sum())
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    print(json.dumps({"boxes": len(boxes), "total_obv": int(c.sum().item())}))
+    lat.free()
+    mesh.free()
+    ctx.close()
 
-    stream = torch.cuda.current_stream()
 
-    def step():
-        ctx.occupancy_rebuild(lat)
-        ctx.outer_volume(lat, d_boxes, counts=d_counts, points=d_points)
-        st = ctx.lloyd_step(layer, rounds=16, refit=True, graph=not args.eager_step)
-        return st
-
-    for _ in range(args.warmup):
-        step()
-        flush.fill_(1)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    ctx.profile_enable(True)
-    launches0 = ctx.profile_read()["launches"]
-    evs = []
-    pts_total = 0
-    lloyd_steps = []
-    wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("timed_step")
-        e0.record(stream)
-        st = step()
-        e1.record(stream)
-        torch.cuda.nvtx.range_pop()
-        evs.append((e0, e1))
-        pts_total += batch_points + st["points_counted"]
-        lloyd_steps.append(st)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    prof = ctx.profile_read()
-    ctx.profile_enable(False)
-    clocks = sampler.stop()
-    ms = [a.elapsed_time(b) for a, b in evs]
-    t_rank = sum(ms) / 1000.0
-    launches = prof["launches"] - launches0
-    t_max, pts_all, launches_all = reduce_ranks(t_rank, pts_total, launches, world, "cuda")
-    value = pts_all / t_max
-
-    # Lloyd iterations per second, plain vs surrogate-screened: the same freshly
-    # split leaf layer, the rotation-descent box update (6 probes per cluster,
-    # 2 steps), timed with CUDA events; final layer totals compared
+def lloyd_comparison(ctx, lat, tree, depth, args, flush, stream):
+    """Lloyd iterations per second on the same freshly split leaf layer: plain
+    host-driven, plain as one CUDA graph, and with the trained surrogate
+    screening candidates and probes (rotation-descent box update, 2 steps);
+    final layer totals and exact box counts compared."""
+    import torch
     lloyd = {}
     up = ctx.tree_read(tree, depth - 1)
     Kp = 1 << (depth - 1)
+    K = 1 << depth
+    parent = (np.arange(K) // 2).astype(np.int32)
     up_layer = ctx.layer_init(lat, up["assign"], (np.arange(Kp) // 2).astype(np.int32), up["frames"])
     child = ctx.layer_split(up_layer)
     up_layer.free()
@@ -371,37 +405,153 @@ def main():
         lloyd[mode] = {"iter_per_s": 1000.0 * args.lloyd_iters / lms, "final_total_obv": int(st["total_obv"]),
                        "exact_box_counts": int(evals)}
         lay.free()
-    lloyd_iter_per_s = lloyd["plain"]["iter_per_s"]
-    lloyd_graph_iter_per_s = lloyd["plain_graph"]["iter_per_s"]
-    surrogate_iter_per_s = lloyd["surrogate"]["iter_per_s"] if "surrogate" in lloyd else None
     if "surrogate" in lloyd:
         a, b = lloyd["plain"]["final_total_obv"], lloyd["surrogate"]["final_total_obv"]
         lloyd["final_obv_rel_diff"] = (b - a) / a
         lloyd["surrogate_topk"] = args.surrogate_topk
     if mlp is not None:
         mlp.free()
+    return lloyd
 
-    # roofline of the counting kernel (the dominant kernel), live over the timed region
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.profile_batch:
+        profile_batch(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    import paper_2203_10521_gb300 as P
+
+    wl = workload(args.workload, rank)
+    m = wl["mesh"]
+    N, depth = wl["N"], wl["depth"]
+    ctx = P.Context(local)
+    if args.walk:
+        ctx.set_counting_rank(0)
+    mesh = ctx.mesh_create(m.verts, m.tris)
+    lat = ctx.build_occupancy(mesh, N)
+    t0 = time.perf_counter()
+    tree = ctx.build_tree(lat, depth, args.setup_iters)
+    torch.cuda.synchronize()
+    tree_s = time.perf_counter() - t0
+    sweep = None
+    if wl["sweeps"]:
+        t0 = time.perf_counter()
+        sweep = ctx.tree_sweep(tree, sweeps=wl["sweeps"], iters=1)
+        torch.cuda.synchronize()
+        sweep["seconds"] = time.perf_counter() - t0
+    boxes = tree_boxes(ctx, tree, depth)
+    # the counting kernel's rows per tile, chosen by the library's autotuner on this batch
+    tile_k, tune_ms = ctx.tune_counting(lat, ctx.quantize_boxes(lat, boxes))
+    d_boxes = torch.from_numpy(boxes).cuda()
+    d_counts = torch.empty(len(boxes), dtype=torch.int64, device="cuda")
+    d_points = torch.empty(len(boxes), dtype=torch.int64, device="cuda")
+    leaf = ctx.tree_read(tree, depth)
+    K = 1 << depth
+    parent = (np.arange(K) // 2).astype(np.int32)
+    layer = ctx.layer_init(lat, leaf["assign"], parent, leaf["frames"])
+    # the batch's algorithmic bytes, rows and in-domain points (constant: the
+    # same boxes on the same lattice every step), from one profiled launch
+    ctx.profile_enable(1)
+    _, pts0 = ctx.outer_volume(lat, boxes, want_points=True)
+    batch_prof = ctx.profile_read()
+    ctx.profile_enable(0)
+    batch_points = int(pts0.sum())
+    batch_dom = int(batch_prof["count_points_in_domain"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.occupancy_rebuild(lat)
+        ctx.outer_volume(lat, d_boxes, counts=d_counts, points=d_points)
+        return ctx.lloyd_step(layer, rounds=16, refit=True, graph=not args.eager_step)
+
+    for _ in range(args.warmup):
+        step()
+        flush.fill_(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    # events around every counting launch outside a CUDA graph (the batch
+    # launch of each step), the kernel without its profiling counters; the
+    # in-domain point total covers every counting launch
+    ctx.profile_enable(2)
+    launches0 = ctx.profile_read()["launches"]
+    evs = []
+    lloyd_steps = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed_step")
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        evs.append((e0, e1))
+        lloyd_steps.append(st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    prof = ctx.profile_read()
+    ctx.profile_enable(0)
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    t_rank = sum(ms) / 1000.0
+    launches = prof["launches"] - launches0
+    pts_dom = prof["count_points_in_domain"]
+    t_max, pts_all, launches_all = reduce_ranks(t_rank, pts_dom, launches, world, "cuda")
+    value = pts_all / t_max
+
+    lloyd = lloyd_comparison(ctx, lat, tree, depth, args, flush, stream)
+
+    # roofline of the counting kernel: algorithmic bytes of the batch launch
+    # over its event-timed duration in the timed region
     peak, peak_kind = measured_peaks()
-    achieved = prof["count_bytes"] / (prof["count_ms"] / 1000.0) / 1e9 if prof["count_ms"] > 0 else 0.0
-    # with the Lloyd step as a CUDA graph, its counting launches run inside the
-    # graph and only the batch launch of each step is bracketed by events
-    traffic, traffic_wl = count_kernel_traffic("dram_bytes_per_launch" if args.eager_step
-                                               else "dram_bytes_batch_launch")
+    n_batch = prof["count_launches"]
+    batch_ms = prof["count_ms"] / max(n_batch, 1)
+    achieved = batch_prof["count_bytes"] / (batch_ms / 1000.0) / 1e9 if batch_ms > 0 else 0.0
+    ri = {} if args.eager_step or args.walk else roofline_inputs(wl["key"])
+    traffic = ri.get("dram_bytes_batch_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_count (outer-volume counting)", "peak_kind": peak_kind,
-                "launches_timed": ("every counting launch of each step" if args.eager_step else
-                                   f"the {len(boxes):,}-box batch launch of each step (the Lloyd step's "
+                "launches_timed": (f"the {len(boxes):,}-box tree batch launch of each step (the Lloyd iteration's "
                                    "counting launches run inside its CUDA graph)"),
-                "count_launches": prof["count_launches"], "count_ms_total": prof["count_ms"],
-                "count_bytes_total": prof["count_bytes"], "count_rows": prof["count_rows"],
-                "count_share_of_step_time": prof["count_ms"] / sum(ms)}
+                "batch_launch_ms": batch_ms, "batch_bytes": batch_prof["count_bytes"],
+                "batch_rows": batch_prof["count_rows"], "batch_rows_rank": batch_prof["count_rows_rank"],
+                "batch_share_of_step_time": prof["count_ms"] / sum(ms)}
+    if traffic:
+        roofline["dram_gbs"] = traffic / (batch_ms / 1000.0) / 1e9
+        roofline["dram_frac"] = roofline["dram_gbs"] / peak
+    if ri.get("warp_inst_batch_launch"):
+        # integer issue: 152 SMs x 4 schedulers x 1 warp instruction per cycle at the sampled SM clock
+        mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        ceiling = 152 * 4 * mhz * 1e6
+        roofline["issue"] = {"warp_inst_per_launch": ri["warp_inst_batch_launch"], "ceiling_per_s": ceiling,
+                             "frac": ri["warp_inst_batch_launch"] / (batch_ms / 1000.0) / ceiling,
+                             "alu_pipe_pct": ri.get("alu_pipe_pct"), "issue_active_pct": ri.get("issue_active_pct")}
 
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e_t, e2e_pts, h2d, d2h = [], 0, 0, 0
+        e2e_t, h2d, d2h, e2e_pts = [], 0, 0, []
 
         def pinned(a):
             # the step's inputs live in page-locked host memory, as a caller
@@ -412,6 +562,7 @@ def main():
         p_assign, p_parent, p_frames = pinned(leaf["assign"]), pinned(parent), pinned(leaf["frames"])
         for _ in range(max(2, min(args.steps, 5))):
             torch.cuda.synchronize()
+            ctx.profile_enable(2)
             t0 = time.perf_counter()
             mh = ctx.mesh_create(p_verts, p_tris)
             lt_ = ctx.build_occupancy(mh, N)
@@ -420,42 +571,47 @@ def main():
             st = ctx.lloyd_step(ly, rounds=16, refit=True)
             out = ctx.layer_read(ly)
             e2e_t.append(time.perf_counter() - t0)
-            e2e_pts = int(pt.sum()) + st["points_counted"]
+            e2e_pts.append(ctx.profile_read()["count_points_in_domain"])
+            ctx.profile_enable(0)
             h2d = (m.verts.nbytes + m.tris.nbytes + boxes.nbytes + leaf["assign"].nbytes + parent.nbytes
                    + leaf["frames"].nbytes)
             d2h = cnt.nbytes + pt.nbytes + sum(v.nbytes for v in out.values())
             ly.free()
             lt_.free()
             mh.free()
-        e2e = {"value": e2e_pts / statistics.median(e2e_t), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * statistics.median(e2e_t),
+        tm = statistics.median(e2e_t)
+        e2e = {"value": statistics.median(e2e_pts) / tm, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * tm,
                "includes": "mesh upload from pinned host memory + device-side validation, occupancy, outer volume "
                            "of the tree batch (pinned host boxes -> host counts), layer init from pinned host "
                            "arrays, one Lloyd iteration, layer read-back"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        q = leaf["qboxes"]
-        rng = np.random.Generator(np.random.PCG64(7))
-        order = rng.permutation(len(q))
-        v, p_, nb, dt = cpu_oracle_sample(wl, q["n"][order], q["b"][order], args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nb} leaf boxes of the 1,024-leaf layer ({p_:,} lattice points): per-point occupancy "
-                         f"of their columns + per-point count, single thread, {dt:.1f} s"}
+        cpu = cpu_baseline(wl, args.cpu_seconds)
 
     if rank == 0:
+        last = lloyd_steps[-1]
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                "config": {"workload": wl["name"], "triangles": m.n_tris, "lattice": N, "tree_depth": depth,
-                          "batch_boxes": len(boxes), "lloyd_rounds_per_iter": 16,
+                          "batch_boxes": len(boxes), "sweeps": wl["sweeps"], "lloyd_rounds_per_iter": 16,
                           "lloyd_step": "host-driven rounds" if args.eager_step else "CUDA graph (conditional rounds)",
+                          "row_counting": "every word" if args.walk else "rank tables for long rows",
+                          "tile_rows_autotuned": tile_k, "autotune_ms": tune_ms,
                           "l2": "flushed between steps (256 MiB write)", "per_rank": "independent mesh (seed + rank)"},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_all,
-               "clocks": clocks, "lloyd_iter_per_s": lloyd_iter_per_s,
-               "lloyd_graph_iter_per_s": lloyd_graph_iter_per_s,
-               "surrogate_lloyd_iter_per_s": surrogate_iter_per_s, "lloyd_comparison": lloyd,
-               "lloyd_last_step": lloyd_steps[-1], "tree_setup_s": tree_s, "wall_s_timed": wall}
+               "clocks": clocks,
+               "points": {"in_domain_per_step": pts_dom / args.steps, "batch_in_domain": batch_dom,
+                          "batch_out_of_domain": batch_points - batch_dom,
+                          "note": "value counts in-domain points only; out-of-domain points are empty by "
+                                  "definition and read no memory"},
+               "lloyd_iter_per_s": lloyd["plain"]["iter_per_s"],
+               "lloyd_graph_iter_per_s": lloyd["plain_graph"]["iter_per_s"],
+               "surrogate_lloyd_iter_per_s": lloyd["surrogate"]["iter_per_s"] if "surrogate" in lloyd else None,
+               "lloyd_comparison": lloyd, "lloyd_last_step": last,
+               "setup": {"tree_s": tree_s, "sweeps": sweep}, "wall_s_timed": wall}
         print(json.dumps(out), flush=True)
     layer.free()
     tree.free()

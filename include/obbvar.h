@@ -106,14 +106,18 @@ const char* obb_last_error(const obb_ctx* ctx);
  * bracketed by CUDA events on the context stream (launches inside a Lloyd
  * iteration run as a CUDA graph are not) and the kernel adds up its
  * algorithmic traffic (16 bytes per 128-bit occupancy chunk that a box row's
- * x-interval touches inside the lattice), the rows with a non-empty
- * interval and, of these, the rows read by a group of lanes together (long
- * rows of boxes whose slabs all step along the row).  Every counting launch of the context, profiled or not (those of
+ * x-interval touches inside the lattice; a row counted through the rank
+ * table touches its first and last word's chunks and two 2-byte rank
+ * entries), the rows with a non-empty interval and, of these, the rows
+ * counted through the rank table.  Every counting launch of the context, profiled or not (those of
  * a captured Lloyd iteration included), also adds up the lattice points of
  * its boxes that lie inside the lattice domain [0, N)^3: the points whose
  * occupancy bit it reads (points outside the domain are empty by definition
- * and cost no memory).  obb_profile_enable resets the totals;
- * obb_profile_read synchronises and reports them. */
+ * and cost no memory).  obb_profile_enable resets the totals: on = 1 times
+ * every counting launch and adds up its bytes and rows, on = 2 only times it
+ * (the kernel then runs without the byte and row counters, as it does with
+ * profiling off), on = 0 stops; obb_profile_read synchronises and reports
+ * the totals. */
 typedef struct {
     int64_t launches;        /* kernels enqueued by the context since creation */
     int64_t count_launches;  /* counting-kernel launches since profiling was enabled */
@@ -121,7 +125,7 @@ typedef struct {
     double count_bytes;      /* their summed algorithmic bytes */
     double count_rows;       /* (j, k) rows with a non-empty interval inside the lattice or not */
     double count_points_in_domain;   /* in-domain lattice points of all counted boxes (every launch) */
-    double count_rows_shared;        /* of count_rows, those whose 128-bit chunks a group of lanes shared */
+    double count_rows_rank;          /* of count_rows, those counted from their end words and the rank table */
 } obb_profile_stats;
 obb_status obb_profile_enable(obb_ctx* ctx, int32_t on);
 obb_status obb_profile_read(obb_ctx* ctx, obb_profile_stats* out);
@@ -221,6 +225,24 @@ obb_status obb_outer_volume_multi(obb_ctx* ctx, const obb_lattice* const* lats, 
  * exact for every value; only its speed changes.  Steps already captured as
  * CUDA graphs are recaptured on their next call. */
 obb_status obb_set_counting_tile(obb_ctx* ctx, int32_t tile_k);
+
+/* Rank tables (default on = 1): every lattice keeps, per row, the number of
+ * occupied bits before each 64-bit word (2 bytes per word, rebuilt with the
+ * occupancy), and a box whose rows are long is counted from each row's two
+ * end words and two rank entries instead of every word of the interval
+ * (constant work per row).  on = 0 reads every word.  The count is exact
+ * either way; only its speed changes.  Steps already captured as CUDA graphs
+ * are recaptured on their next call.  OBB_ERR_ARG unless 0 or 1. */
+obb_status obb_set_counting_rank(obb_ctx* ctx, int32_t on);
+
+/* Spatial order (default on = 1): a batch of at least 1,024 boxes on lattices
+ * of at least 64 MiB of occupancy words (larger than about half the L2),
+ * counted outside a CUDA-graph capture, is scheduled by the 16^3 Morton cell
+ * of each box's centre, so that boxes of every size over one region of the
+ * lattice are counted together and reuse its words from L2.  on = 0 counts the boxes
+ * in the caller's order.  Counts do not depend on it.  OBB_ERR_ARG unless 0
+ * or 1. */
+obb_status obb_set_counting_order(obb_ctx* ctx, int32_t on);
 
 /* Row axis of the counting kernel.  By default (axis = 0) every box is counted
  * in rows along x.  With axis = -1 each box is counted along the index axis

@@ -52,7 +52,7 @@ class StepStats(C.Structure):
 class ProfileStats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("count_launches", C.c_int64), ("count_ms", C.c_double),
                 ("count_bytes", C.c_double), ("count_rows", C.c_double),
-                ("count_points_in_domain", C.c_double), ("count_rows_shared", C.c_double)]
+                ("count_points_in_domain", C.c_double), ("count_rows_rank", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True):
         "obb_layer_adjust": [vp, vp, C.POINTER(StepOpts), i32, C.POINTER(AdjustStats)],
         "obb_set_counting_tile": [vp, i32],
         "obb_set_counting_axis": [vp, i32],
+        "obb_set_counting_rank": [vp, i32],
+        "obb_set_counting_order": [vp, i32],
         "obb_test_inject": [vp, i32],
         "obb_tune_counting": [vp, vp, vp, i64, i32, vp, vp],
         "obb_unit_step": [vp, vp, vp, C.POINTER(StepOpts), C.POINTER(StepStats)],
@@ -173,7 +175,8 @@ def exported_symbols():
             "obb_layer_read", "obb_layer_clusters", "obb_layer_split", "obb_layer_free", "obb_build_tree",
             "obb_tree_read", "obb_tree_depth", "obb_tree_score", "obb_tree_free", "obb_tree_parents",
             "obb_tree_sweep", "obb_layer_parents", "obb_unit_step", "obb_flood_partition",
-            "obb_layer_adjust", "obb_set_counting_tile", "obb_set_counting_axis", "obb_test_inject",
+            "obb_layer_adjust", "obb_set_counting_tile", "obb_set_counting_axis", "obb_set_counting_rank",
+            "obb_set_counting_order", "obb_test_inject",
             "obb_tune_counting",
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_mlp_forward", "obb_mlp_gradients", "obb_mlp_train_step",
@@ -275,7 +278,9 @@ class Context:
 
     # ------------------------------------------------------- instrumentation
     def profile_enable(self, on=True):
-        self.check(self.lib.obb_profile_enable(self.h, 1 if on else 0))
+        """True/1: time every counting launch and add up its algorithmic bytes
+        and rows; 2: time only (the kernel without its counters); False/0: off."""
+        self.check(self.lib.obb_profile_enable(self.h, int(on)))
 
     def profile_read(self):
         st = ProfileStats()
@@ -315,6 +320,16 @@ class Context:
         the axis with the smallest shadow; 1, 2 force y, z rows (lattices built
         or rebuilt afterwards keep the y- and z-row copies these need)."""
         self.check(self.lib.obb_set_counting_axis(self.h, int(axis)))
+
+    def set_counting_rank(self, on):
+        """1 (default): long rows counted from their end words and the rank
+        table; 0: every word of every row interval read."""
+        self.check(self.lib.obb_set_counting_rank(self.h, int(on)))
+
+    def set_counting_order(self, on):
+        """1 (default): batches of at least 1,024 boxes on lattices of at least
+        64 MiB counted in spatial order; 0: in the caller's order."""
+        self.check(self.lib.obb_set_counting_order(self.h, int(on)))
 
     def tune_counting(self, lat, qboxes):
         """Time the count of these quantised boxes with 8/16/32/64 rows per tile and

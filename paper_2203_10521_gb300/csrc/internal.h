@@ -24,6 +24,7 @@ constexpr int64_t kBoxRange = int64_t(1) << 20;  // |index-space AABB| limit of 
 #define OBB_TILE_K 32
 #endif
 constexpr int kTileK = OBB_TILE_K;               // rows along z one lane steps through per tile
+constexpr int kOrderBuckets = 4096;              // spatial-order buckets of a counting launch (16^3 Morton cells)
 
 #ifdef __CUDACC__
 // Integer -> FP32 through 32-bit conversions (relative error below 3 * 2^-24,
@@ -70,9 +71,8 @@ struct LatticeFrame {
 
 // Per-box data the counting kernel needs, prepared once per box.
 // Rows (j, k) of the box's index-space AABB are cut into tiles of wj rows
-// along y by wk * tk rows along z (wj * wk = 32 / G lane groups of G = 2^lg
-// lanes); each group owns one j and visits tk rows spaced wk apart along z,
-// its G lanes taking the row's 128-bit chunks in turn.  Slab a bounds i through
+// along y by wk * tk rows along z (wj * wk = 32 lanes); each lane owns one j
+// and visits tk rows spaced wk apart along z.  Slab a bounds i through
 // quotients by dd_a = |n_a0|; from one visited row to the next the quotient
 // moves by qstep_a with remainder carry rstep_a, or by fstep_a in 32.32 fixed
 // point (an integer DDA either way).
@@ -89,7 +89,8 @@ struct alignas(128) BoxPrep {
     int32_t i0, span;        // index-space AABB along x: [i0, i0 + span]
     int32_t axis;            // rows run along index axis 0 (x), 1 (y) or 2 (z); n's columns permuted to match
     int32_t lat;             // index of the box's lattice in the launch's lattice table
-    int32_t lg;              // log2 of the lanes sharing one row (wide rows: 16-byte chunks dealt out to G lanes)
+    int32_t rank;            // row counting: 0 every word, 1 end words + rank table, 2 end words (rows <= 64 points)
+    const uint16_t* ranks;   // the rank table of `words` (ones before each word of a row)
     // Separating axes of the box's shadow on the (j, k) plane: the normals of
     // its three projected edge directions, and the shadow's extent along each,
     // widened by two rows.  A tile whose rectangle lies outside one of these
@@ -118,6 +119,11 @@ struct LatRef {
     const uint64_t* words;     // rows along x: row (k, j) at (k N + j) W, bit i
     const uint64_t* words_y;   // rows along y: row (k, i) at (k N + i) W, bit j
     const uint64_t* words_z;   // rows along z: row (j, i) at (j N + i) W, bit k
+    // rank tables of the three: entry (row, w) = occupied bits in words 0..w-1
+    // of that row (uint16, the words' layout)
+    const uint16_t* rank;
+    const uint16_t* rank_y;
+    const uint16_t* rank_z;
     int32_t N;
     int32_t W;
 };
@@ -154,19 +160,22 @@ struct obb_ctx {
     const obbv::CountScratch* count_scratch = nullptr;   // set while a step is being captured
     int32_t tile_k = obbv::kTileK;   // rows per lane per counting tile
     int32_t count_axis = 0;          // row axis of counted boxes (0: x; -1: per box, the smallest shadow)
+    int32_t count_rank = 1;          // long rows counted from their end words and the rank table (0: every word)
+    int32_t count_order = 1;         // large batches counted in spatial order (0: in the caller's order)
     int32_t inject = 0;              // test hooks armed by obb_test_inject (OBB_INJECT_*)
     int32_t tile_gen = 0;            // bumped when tile_k changes (captured steps recapture)
     int32_t* h_small = nullptr;      // pinned host staging (512 bytes; the first 64 hold the error word)
     // scratch reused across calls
     obbv::DevBuf prep, chunk_off, qscratch, cscratch, pscratch, kdev, tmp_a, tmp_b, tmp_c, tmp_d,
-        cub_tmp;
+        cub_tmp, order;
+    unsigned int* d_order_hist = nullptr;   // spatial-order buckets of the counting path
     // instrumentation: kernels launched by this context, and the optional
     // profile of the outer-volume counting kernel (CUDA events + byte totals)
     int64_t launches = 0;
-    bool prof = false;
+    int32_t prof = 0;                // 0 off, 1 events and counters, 2 events only
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
-    // [0] algorithmic bytes, [1] rows, [3] rows shared by lane groups (profiled launches);
-    // [2] in-domain points (every launch)
+    // [0] algorithmic bytes, [1] rows, [3] rows counted with the rank table (profiled
+    // launches); [2] in-domain points (every launch)
     unsigned long long* d_prof = nullptr;
     std::map<std::pair<int64_t, int>, int> sort_launch_cache;
 };
@@ -189,6 +198,9 @@ struct obb_lattice {
     uint64_t* d_words = nullptr;     // occupancy, rows along x
     uint64_t* d_words_y = nullptr;   // the same bits with rows along y, then z (counting boxes
     uint64_t* d_words_z = nullptr;   // along their shortest-shadow axis)
+    uint16_t* d_rank = nullptr;      // rank tables of the rows along x, y, z
+    uint16_t* d_rank_y = nullptr;
+    uint16_t* d_rank_z = nullptr;
     size_t n_words = 0;
     obbv::LatRef ref{};              // host copy of the table entry below
     obbv::LatRef* d_ref = nullptr;   // this lattice as a one-entry table
@@ -266,10 +278,11 @@ obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d
 // d_K (int32); K_cap bounds it for scratch sizing.  counts/points are zeroed here.
 obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes,
                        const int32_t* d_K, int64_t K_cap, uint64_t* d_counts, uint64_t* d_points);
-// the same over boxes of several lattices: box k uses d_lats[d_lat_of_box[k]]
+// the same over boxes of several lattices: box k uses d_lats[d_lat_of_box[k]];
+// lattice_bytes (the lattices' occupancy words together) decides the spatial order
 obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats, const int32_t* d_lat_of_box,
                              const obb_qbox* d_boxes, const int32_t* d_K, int64_t K_cap, uint64_t* d_counts,
-                             uint64_t* d_points);
+                             uint64_t* d_points, int64_t lattice_bytes);
 obb_status set_device_int(obb_ctx* ctx, int32_t* d_dst, int32_t value);
 // exclusive scan of n int32 values into out[n + 1] (out[n] = total), single block
 void launch_scan_i32(obb_ctx* ctx, const int32_t* in, int32_t* out, const int32_t* d_n);

@@ -1131,9 +1131,9 @@ static obb_status lloyd_step_graph(obb_ctx* ctx, obb_layer* L, int rounds, int r
         cudaStream_t cs[3] = {nullptr, nullptr, nullptr};
         for (auto& c : cs) OBB_CK(ctx, cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
         const cudaStream_t saved_stream = ctx->stream;
-        const bool saved_prof = ctx->prof;
+        const int32_t saved_prof = ctx->prof;
         const int64_t saved_launches = ctx->launches;
-        ctx->prof = false;
+        ctx->prof = 0;
         ctx->count_scratch = &M->cscr;
         M->members_valid = true;   // valid on entry; the graph rebuilds them after moving rounds
         cudaGraph_t g = nullptr;

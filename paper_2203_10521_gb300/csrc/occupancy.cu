@@ -288,8 +288,23 @@ __device__ __forceinline__ uint64_t prefix_xor(uint64_t x)
     return x;
 }
 
-// One lane per 128-bit chunk; a row's G = W / 2 chunks sit on consecutive lanes.
-__global__ void k_row_scan(uint64_t* __restrict__ words, int32_t N, int32_t W)
+// Exclusive prefix of v over the G lanes of a row (lanes lr G .. lr G + G - 1;
+// c = the lane's place in the row); every lane of the warp takes part.
+__device__ __forceinline__ uint32_t row_exclusive_sum(uint32_t v, int c, int G)
+{
+    uint32_t x = v;
+    for (int off = 1; off < G; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (c >= off) x += y;
+    }
+    return x - v;
+}
+
+// One lane per 128-bit chunk; a row's G = W / 2 chunks sit on consecutive
+// lanes.  The prefix XOR along the row turns the crossing flips into
+// occupancy; the same pass writes the row's rank table (occupied bits before
+// each 64-bit word).
+__global__ void k_row_scan(uint64_t* __restrict__ words, uint16_t* __restrict__ rank, int32_t N, int32_t W)
 {
     const int G = W >> 1;
     const int rpw = 32 / G;
@@ -323,7 +338,33 @@ __global__ void k_row_scan(uint64_t* __restrict__ words, int32_t N, int32_t W)
     uint64_t m1 = (base + 128 <= N) ? ~0ull : (base + 64 >= N ? 0ull : ((1ull << (N - base - 64)) - 1));
     p0 &= m0;
     p1 &= m1;
-    if (active) *p = make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), (uint32_t)p1, (uint32_t)(p1 >> 32));
+    const uint32_t n0 = (uint32_t)__popcll(p0);
+    const uint32_t before = row_exclusive_sum(n0 + (uint32_t)__popcll(p1), c, G);
+    if (active) {
+        *p = make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), (uint32_t)p1, (uint32_t)(p1 >> 32));
+        reinterpret_cast<uint32_t*>(rank + row * W)[c] = before | ((before + n0) << 16);
+    }
+}
+
+// The rank table of finished rows (the y- and z-row copies), laid out as
+// k_row_scan lays it out.
+__global__ void k_row_rank(const uint64_t* __restrict__ words, uint16_t* __restrict__ rank, int32_t N, int32_t W)
+{
+    const int G = W >> 1;
+    const int rpw = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lr = lane / G, c = lane - lr * G;
+    const int64_t row = warp * rpw + lr;
+    const bool active = lr < rpw && row < (int64_t)N * N;
+    uint32_t n0 = 0, n1 = 0;
+    if (active) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(words + row * W) + c);
+        n0 = (uint32_t)__popcll(v.x);
+        n1 = (uint32_t)__popcll(v.y);
+    }
+    const uint32_t before = row_exclusive_sum(n0 + n1, c, G);
+    if (active) reinterpret_cast<uint32_t*>(rank + row * W)[c] = before | ((before + n0) << 16);
 }
 
 }  // namespace
@@ -353,25 +394,31 @@ obb_status rebuild_occupancy(obb_ctx* ctx, obb_lattice* lat)
     note_launch(ctx);
     const int G = W / 2, rpw = 32 / G;
     int64_t warps = ((int64_t)N * N + rpw - 1) / rpw;
-    k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, N, W);
+    k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_rank, N, W);
     note_launch(ctx);
     // rows along y and z: kept once a context counts along them, then refreshed
     // by every rebuild
     if (ctx->count_axis != 0 && !lat->d_words_y) {
         OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words_y, sizeof(uint64_t) * lat->n_words, s));
         OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words_z, sizeof(uint64_t) * lat->n_words, s));
+        OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_rank_y, sizeof(uint16_t) * lat->n_words, s));
+        OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_rank_z, sizeof(uint16_t) * lat->n_words, s));
         // the transposes never write the padding words past ceil(N / 64): zero them once
         OBB_CK(ctx, cudaMemsetAsync(lat->d_words_y, 0, sizeof(uint64_t) * lat->n_words, s));
         OBB_CK(ctx, cudaMemsetAsync(lat->d_words_z, 0, sizeof(uint64_t) * lat->n_words, s));
         lat->ref.words_y = lat->d_words_y;
         lat->ref.words_z = lat->d_words_z;
+        lat->ref.rank_y = lat->d_rank_y;
+        lat->ref.rank_z = lat->d_rank_z;
         OBB_CK(ctx, cudaMemcpyAsync(lat->d_ref, &lat->ref, sizeof(LatRef), cudaMemcpyHostToDevice, s));
     }
     if (lat->d_words_y) {
         const int64_t tb = (N + 63) / 64, tw = (int64_t)N * tb * tb;
         k_transpose_rows<<<(unsigned)((tw + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_words_y, N, W, 0);
         k_transpose_rows<<<(unsigned)((tw + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_words_z, N, W, 1);
-        note_launch(ctx, 2);
+        k_row_rank<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words_y, lat->d_rank_y, N, W);
+        k_row_rank<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words_z, lat->d_rank_z, N, W);
+        note_launch(ctx, 4);
     }
     OBB_CK(ctx, cudaGetLastError());
     lat->frame_stale = true;   // the host copy is refreshed when a host reader needs it
@@ -391,8 +438,9 @@ obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_la
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_frame, sizeof(LatticeFrame), s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_fixed, sizeof(int32_t) * 3 * mesh->nv, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words, sizeof(uint64_t) * lat->n_words, s));
+    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_rank, sizeof(uint16_t) * lat->n_words, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_ref, sizeof(LatRef), s));
-    lat->ref = LatRef{lat->d_words, nullptr, nullptr, N, W};
+    lat->ref = LatRef{lat->d_words, nullptr, nullptr, lat->d_rank, nullptr, nullptr, N, W};
     OBB_CK(ctx, cudaMemcpyAsync(lat->d_ref, &lat->ref, sizeof(LatRef), cudaMemcpyHostToDevice, s));
     OBB_TRY(rebuild_occupancy(ctx, lat));
     OBB_TRY(lattice_frame_host(lat));

@@ -41,30 +41,32 @@
 #ifndef OBB_BIG_TK_ROWS
 #define OBB_BIG_TK_ROWS 16384
 #endif
-// OBB_WIDE_MIN_CHUNKS: a box whose rows are expected to span at least this many
-// 128-bit chunks shares each row among several lanes (0: never)
-#ifndef OBB_WIDE_MIN_CHUNKS
-#define OBB_WIDE_MIN_CHUNKS 6
-#endif
-// OBB_WIDE_MAX_LG: log2 of the most lanes that share one row
-#ifndef OBB_WIDE_MAX_LG
-#define OBB_WIDE_MAX_LG 3
-#endif
-// OBB_WIDE_UNROLL: rows of a lane group's row loop unrolled (several rows' loads in flight)
-#ifndef OBB_WIDE_UNROLL
-#define OBB_WIDE_UNROLL 4
+// OBB_RANK_MIN_BITS: a box whose rows may be at least this long (in lattice
+// points) is counted through the rank table; shorter rows (at most 64 points,
+// two words) are counted from their two end words
+#ifndef OBB_RANK_MIN_BITS
+#define OBB_RANK_MIN_BITS 128
 #endif
 // OBB_ROW_MARGIN: rows added on each side of a box's (j, k) bounding rectangle
 #ifndef OBB_ROW_MARGIN
 #define OBB_ROW_MARGIN 1
 #endif
+// OBB_ORDER_MIN_BOXES, OBB_ORDER_MIN_MB: batches of at least this many boxes on
+// lattices of at least this many MiB of occupancy words are counted in spatial order
+#ifndef OBB_ORDER_MIN_BOXES
+#define OBB_ORDER_MIN_BOXES 1024
+#endif
+#ifndef OBB_ORDER_MIN_MB
+#define OBB_ORDER_MIN_MB 64
+#endif
 namespace obbv {
+constexpr int64_t kOrderMinBoxes = OBB_ORDER_MIN_BOXES;
+constexpr int64_t kOrderMinLatticeBytes = int64_t(OBB_ORDER_MIN_MB) << 20;
 // tuning parameters: unroll factor of the counting kernel's row loop, tiles per work grab
 constexpr int kCountUnroll = OBB_COUNT_UNROLL;
 constexpr int kRowMargin = OBB_ROW_MARGIN;
 constexpr int kPrepThreads = 32;   // one warp per preparation block: its per-box work spreads over many SMs
 constexpr int kGrab = OBB_GRAB;
-constexpr int kWideUnroll = OBB_WIDE_UNROLL;
 }  // namespace obbv
 
 namespace obbv {
@@ -165,7 +167,8 @@ __device__ __forceinline__ int choose_axis(const obb_qbox& q)
 __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int64_t k,
                                         const LatRef* __restrict__ lats, int32_t n_lats,
                                         const int32_t* __restrict__ lat_of_box, int32_t tile_k, int32_t axis_mode,
-                                        BoxPrep* __restrict__ prep, int64_t* __restrict__ tiles, int32_t* err)
+                                        int32_t count_rank, BoxPrep* __restrict__ prep,
+                                        int64_t* __restrict__ tiles, int32_t* err)
 {
     const obb_qbox q = boxes[k];
     BoxPrep p;
@@ -188,6 +191,7 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     const LatRef lr = lats[p.lat];
     const int32_t N = lr.N;
     p.words = p.axis == 0 ? lr.words : (p.axis == 1 ? lr.words_y : lr.words_z);
+    p.ranks = p.axis == 0 ? lr.rank : (p.axis == 1 ? lr.rank_y : lr.rank_z);
     p.latN = lr.N;
     p.latW = lr.W;
     for (int a = 0; a < 3; ++a)
@@ -212,7 +216,7 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     }
     p.i0 = 0;
     p.span = -1;
-    p.lg = 0;
+    p.rank = 0;
     p.j0 = p.k0 = 0;
     p.nj = p.nk = p.ntj = 0;
     for (int a = 0; a < 3; ++a) {
@@ -356,38 +360,29 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
     // row clipping trims their empty ends)
     if ((int64_t)p.nj * p.nk >= OBB_BIG_TK_ROWS && 2 * tile_k <= 128) p.tk = 2 * tile_k;
 #endif
-    // wide rows: a box whose three slabs all step by DDA and whose rows are
-    // long (the x-interval of a row through it, at most min_a (H_a - L_a) /
-    // |n_a0| + 1 points, spans several 128-bit chunks) shares each row among
-    // G = 2^lg lanes that read its chunks side by side (16-byte loads,
-    // contiguous across the group), so a warp streams whole rows
-#if OBB_WIDE_MIN_CHUNKS > 0
-    if (p.nj > 0 && (p.mode & 0xff) == 0x15) {
-        float ell = (float)p.span + 1.0f;
+    // row counting: a box's rows are at most ell points long, the smallest of
+    // span + 1 and (H_a - L_a) / |n_a0| + 1 over the slabs that step along x.
+    // With rank tables, long rows (ell >= OBB_RANK_MIN_BITS) are counted from
+    // their two end words and the rank table, and rows of at most 64 points
+    // (ell < 63.5, well clear of FP32 rounding) from their two end words; both
+    // at a fixed cost per row.
+    if (p.nj > 0 && count_rank && p.ranks) {
+        float ell = fminf((float)p.span + 1.0f, (float)N);
         for (int a = 0; a < 3; ++a)
-            ell = fminf(ell, i64_to_float(p.Hq[a] - p.Lq[a]) / (float)p.dd[a] + 1.0f);
-        ell = fminf(ell, (float)N);
-        const float chunks = ell * (1.0f / 128.0f) + 1.0f;
-        if (chunks >= (float)OBB_WIDE_MIN_CHUNKS) {
-            int lg = 0;
-            while (lg < OBB_WIDE_MAX_LG && (float)(2 << lg) <= chunks && (2 << lg) <= lr.W / 2) ++lg;
-            p.lg = lg;
-        }
+            if (p.dd[a] > 0) ell = fminf(ell, i64_to_float(p.Hq[a] - p.Lq[a]) / (float)p.dd[a] + 1.0f);
+        p.rank = ell >= (float)OBB_RANK_MIN_BITS ? 1 : (ell < 63.5f ? 2 : 0);
     }
-#endif
-    // tile shape: wj groups along y, wk = 32 / G / wj along z; the least
-    // padding wins (ties to the wider wj, whose rows sit next to each other in
-    // memory)
-    const int32_t lgrp = 5 - p.lg;   // log2 of the lane groups of a warp
-    int best = lgrp;
+    // tile shape: wj lanes along y, wk = 32 / wj along z; the least padding wins
+    // (ties to the wider wj, whose rows sit next to each other in memory)
+    int best = 5;
     int64_t best_slots = INT64_MAX;
     if (p.nj > 0) {
-        // ceil(nk / (wk tk)) = ceil(ceil(nk / tk) / wk): one division
+        // ceil(nk / ((32 >> l) tk)) = ceil(ceil(nk / tk) / 2^(5 - l)): one division
         const int32_t nkt = (p.nk + p.tk - 1) / p.tk;
-        for (int l = lgrp; l >= 0; --l) {
-            const int32_t sh = lgrp - l;
+        for (int l = 5; l >= 0; --l) {
+            const int32_t sh = 5 - l;
             const int64_t slots = (int64_t)(((p.nj + (1 << l) - 1) >> l) << l) *
-                                  ((int64_t)((nkt + (1 << sh) - 1) >> sh) * ((1 << sh) * p.tk));
+                                  ((int64_t)((nkt + (1 << sh) - 1) >> sh) * ((32 >> l) * p.tk));
             if (slots < best_slots) {
                 best_slots = slots;
                 best = l;
@@ -400,11 +395,11 @@ __device__ __noinline__ void k_prep_box(const obb_qbox* __restrict__ boxes, int6
         p.k0 + p.nk <= N)
         p.mode |= 1 << 8;
     p.lwj = best;
-    const int32_t wj = 1 << best, wk = (32 >> p.lg) >> best;
+    const int32_t wj = 1 << best, wk = 32 >> best;
     p.ntj = p.nj > 0 ? (p.nj + wj - 1) / wj : 0;
     for (int a = 0; a < 3; ++a)
         if ((p.mode >> (2 * a)) & 3) {
-            // between a group's rows k advances by wk: X_lo and X_hi move by -sign(d) * n_a2 * wk
+            // between a lane's rows k advances by wk: X_lo and X_hi move by -sign(d) * n_a2 * wk
             // |delta| <= 2^24 * 32 and 0 < dd < 2^25: exact in 32 bits
             const int32_t delta = -(p.n[3 * a] > 0 ? 1 : -1) * p.n[3 * a + 2] * wk;
             int32_t qs = delta / p.dd[a];
@@ -445,19 +440,36 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
                                                        const int32_t* __restrict__ d_K,
                                                        const LatRef* __restrict__ lats, int32_t n_lats,
                                                        const int32_t* __restrict__ lat_of_box, int32_t tile_k,
-                                                       int32_t axis_mode, BoxPrep* __restrict__ prep,
+                                                       int32_t axis_mode, int32_t count_rank,
+                                                       BoxPrep* __restrict__ prep,
                                                        int64_t* __restrict__ tiles,
                                                        int64_t* __restrict__ off,
                                                        unsigned long long* __restrict__ counts,
                                                        unsigned long long* __restrict__ points,
-                                                       unsigned int* __restrict__ ticket, int32_t* err)
+                                                       unsigned int* __restrict__ ticket,
+                                                       uint32_t* __restrict__ bucket, unsigned int* __restrict__ hist,
+                                                       int32_t* err)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int32_t K = *d_K;
     if (k < K) {
         counts[k] = 0;
         if (points) points[k] = 0;
-        k_prep_box(boxes, k, lats, n_lats, lat_of_box, tile_k, axis_mode, prep, tiles, err);
+        k_prep_box(boxes, k, lats, n_lats, lat_of_box, tile_k, axis_mode, count_rank, prep, tiles, err);
+        if (bucket) {
+            // spatial order: the 16^3 Morton cell of the centre of the box's
+            // index-space rectangle (clamped to the lattice)
+            const BoxPrep& p = prep[k];
+            const int32_t N = max(p.latN, 1);
+            const int64_t c[3] = {(int64_t)p.i0 + p.span / 2, (int64_t)p.j0 + p.nj / 2, (int64_t)p.k0 + p.nk / 2};
+            uint32_t key = 0;
+            for (int a = 0; a < 3; ++a) {
+                const uint32_t q = (uint32_t)min(max(c[a] * 16 / N, (int64_t)0), (int64_t)15);
+                for (int bit = 0; bit < 4; ++bit) key |= ((q >> bit) & 1u) << (3 * bit + a);
+            }
+            bucket[k] = key;
+            atomicAdd(&hist[key], 1u);
+        }
     }
     // the block's writes, then one gpu-scope fence before its ticket
     __shared__ bool last;
@@ -469,6 +481,28 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
     }
     __syncthreads();
     if (!last) return;
+    if (bucket) {
+        // spatial order: the bucket counts become bucket starts (exclusive
+        // scan, one warp, 128 buckets a lane); k_order_scatter and
+        // k_order_scan follow
+        const int lane = threadIdx.x & 31;
+        constexpr int per = kOrderBuckets / 32;
+        unsigned int run = 0;
+        for (int q = 0; q < per; ++q) run += hist[lane * per + q];
+        unsigned int x = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        unsigned int start = x - run;
+        for (int q = 0; q < per; ++q) {
+            const unsigned int v = hist[lane * per + q];
+            hist[lane * per + q] = start;
+            start += v;
+        }
+        if (threadIdx.x == 0) *ticket = 0;   // ready for the next launch
+        return;
+    }
     // exclusive scan of tiles[0..K) by the last block (one warp): chunks of
     // 8 x 32 consecutive values, a thread's eight in registers (eight loads in
     // flight), a warp scan of the thread sums, and a running carry
@@ -502,6 +536,53 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
         off[K] = carry;
         off[K + 1] = 0;
         *ticket = 0;   // ready for the next launch
+    }
+}
+
+// ---------------------------------------------------------- spatial order
+
+// perm[start of the box's bucket + its place] = box (the place within a
+// bucket depends on scheduling; counts do not depend on the order)
+__global__ void k_order_scatter(const uint32_t* __restrict__ bucket, const int32_t* __restrict__ d_K,
+                                unsigned int* __restrict__ hist, int32_t* __restrict__ perm)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t K = *d_K;
+    if (k >= K) return;
+    const unsigned int pos = atomicAdd(&hist[bucket[k]], 1u);
+    if (pos < (unsigned int)K) perm[pos] = (int32_t)k;
+}
+
+// off[i] = tiles of boxes perm[0..i-1] (one block of 1024 threads, each a
+// contiguous run of positions); off[K] = all tiles, off[K + 1] = 0 (the
+// counting kernel's work counter)
+__global__ void __launch_bounds__(1024) k_order_scan(const int64_t* __restrict__ tiles,
+                                                     const int32_t* __restrict__ perm,
+                                                     const int32_t* __restrict__ d_K, int64_t* __restrict__ off)
+{
+    __shared__ int64_t part[1024];
+    const int32_t K = *d_K;
+    const int t = threadIdx.x;
+    const int32_t per = (K + 1023) / 1024;
+    const int32_t b0 = min(K, t * per), b1 = min(K, b0 + per);
+    int64_t sum = 0;
+    for (int32_t i = b0; i < b1; ++i) sum += tiles[perm[i]];
+    part[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - sum;
+    for (int32_t i = b0; i < b1; ++i) {
+        off[i] = run;
+        run += tiles[perm[i]];
+    }
+    if (t == 1023) {
+        off[K] = part[1023];
+        off[K + 1] = 0;
     }
 }
 
@@ -552,11 +633,6 @@ __device__ __forceinline__ int64_t fixed_frac(int32_t r, uint64_t M)   // 0 <= r
 {
     const uint32_t ru = (uint32_t)r;
     return (int64_t)((uint64_t)ru * (uint32_t)(M >> 32) + __umulhi(ru, (uint32_t)M));
-}
-
-__device__ __forceinline__ int32_t fixed_int(int64_t A)
-{
-    return (int32_t)(A >> 32);
 }
 
 // floor(x / d) and its remainder in [0, d), for 0 < d <= 2^24 and |x| < 2^62,
@@ -614,50 +690,76 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
     return cnt + __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
 }
 
-// bits [lo, hi] of a 64-bit word (lo and hi may lie outside [0, 63])
-__device__ __forceinline__ uint64_t bit_range(int32_t lo, int32_t hi)
+// The same count through the row's rank table (rk[w] = occupied bits in words
+// 0..w-1): the two end words with their masks plus the whole words between
+// them, rk[we] - rk[min(wa + 1, we)] -- four loads whatever the row's length.
+__device__ __forceinline__ uint32_t popc_rank(const uint64_t* __restrict__ row, const uint16_t* __restrict__ rk,
+                                              int32_t a, int32_t e)
 {
-    const uint64_t ml = lo <= 0 ? ~0ull : (lo >= 64 ? 0ull : ~0ull << lo);
-    const uint64_t mh = hi >= 63 ? ~0ull : (hi < 0 ? 0ull : ~0ull >> (63 - hi));
-    return ml & mh;
+    const int32_t wa = a >> 6, we = e >> 6;
+    const uint64_t first = __ldg(row + wa);
+    const uint64_t last = __ldg(row + we);
+    const uint32_t mid = (uint32_t)__ldg(rk + we) - (uint32_t)__ldg(rk + min(wa + 1, we));
+    uint64_t mlo = ~0ull << (a & 63);
+    const uint64_t mhi = ~0ull >> (63 - (e & 63));
+    const bool one = wa == we;
+    mlo = one ? (mlo & mhi) : mlo;
+    return mid + __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
 }
 
-// Lane g's share of the occupied bits i in [a, e] of one row when G = 2^lg
-// lanes share it: the 128-bit chunks (a >> 7) + g, + G, ... up to e >> 7,
-// each read with one 16-byte load (rows are 16-byte aligned), so the group's
-// loads are contiguous.
-__device__ __forceinline__ uint32_t popc_range_wide(const uint64_t* __restrict__ row, int32_t a, int32_t e,
-                                                    int32_t g, int32_t lg)
+// occupied bits of [a, e] when it lies within two consecutive words
+__device__ __forceinline__ uint32_t popc_short(const uint64_t* __restrict__ row, int32_t a, int32_t e)
 {
-    uint32_t cnt = 0;
-    const int32_t ce = e >> 7;
-    for (int32_t c = (a >> 7) + g; c <= ce; c += 1 << lg) {
-        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(row) + c);
-        const int32_t b0 = c << 7;
-        cnt += __popcll(v.x & bit_range(a - b0, e - b0)) + __popcll(v.y & bit_range(a - b0 - 64, e - b0 - 64));
-    }
-    return cnt;
+    const int32_t wa = a >> 6, we = e >> 6;
+    const uint64_t first = __ldg(row + wa);
+    const uint64_t last = __ldg(row + we);
+    uint64_t mlo = ~0ull << (a & 63);
+    const uint64_t mhi = ~0ull >> (63 - (e & 63));
+    const bool one = wa == we;
+    mlo = one ? (mlo & mhi) : mlo;
+    return __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
 }
 
-// One pass of a lane (group) over its rows r0..r1 of a tile of a box whose
-// three slabs all step by DDA: each of the six bounds is a 32.32 fixed-point
-// value whose integer part is the quotient, so a bound costs one 64-bit add
-// per row.  kWide: G = 2^lg lanes share each row (lane g reads its chunks,
-// lane 0 of the group accounts the row's length); kInterior: the tile's rows
-// and x-intervals all lie in the lattice (no clamps).
-template <bool kWide, bool kInterior>
+// Row counting modes of a box (BoxPrep::rank).
+enum { kRowWalk = 0, kRowRank = 1, kRowShort = 2 };
+
+// algorithmic bytes of one counted row [a, e]: every 16-byte chunk the
+// interval touches; through the rank table, the end words' chunks and two
+// 2-byte rank entries
+template <int kMode>
+__device__ __forceinline__ uint32_t row_bytes(int32_t a, int32_t e)
+{
+    const int32_t ca = a >> 7, ce = e >> 7;
+    return kMode == kRowRank ? (ca == ce ? 16u : 32u) + 4u : (uint32_t)(ce - ca + 1) * 16u;
+}
+
+// occupied bits of [a, e] by the box's row counting mode
+template <int kMode>
+__device__ __forceinline__ uint32_t popc_mode(const uint64_t* __restrict__ row, const uint16_t* __restrict__ rk,
+                                              int32_t a, int32_t e)
+{
+    if constexpr (kMode == kRowRank) return popc_rank(row, rk, a, e);
+    else if constexpr (kMode == kRowShort) return popc_short(row, a, e);
+    else return popc_range(row, a, e);
+}
+
+// One pass of a lane over its rows r0..r1 of a tile of a box whose three
+// slabs all step by DDA: each of the six bounds is a 32.32 fixed-point value
+// whose integer part is the quotient, so a bound costs one 64-bit add per
+// row.  kMode: how a row's occupied bits are counted; kInterior: the tile's
+// rows and x-intervals all lie in the lattice (no clamps); kProf: algorithmic
+// bytes and rows are added up.
+template <int kMode, bool kInterior, bool kProf>
 __device__ __forceinline__ void dda_rows(int64_t (&Al)[3], int64_t (&Ah)[3], const int64_t (&Bs)[3],
-                                         const uint64_t* __restrict__ rowp, int64_t rstride, int32_t r0, int32_t r1,
-                                         int32_t k, int32_t wk, int32_t kend, bool jvalid, bool jin, int32_t i0,
-                                         int32_t span, int32_t N, int32_t g, int32_t lg, uint32_t& empty,
-                                         uint32_t& inbox, uint32_t& my_chunks, uint32_t& my_rows, uint32_t& my_dom,
-                                         uint32_t& my_wide)
+                                         const uint64_t* __restrict__ rowp, const uint16_t* __restrict__ rkp,
+                                         int64_t rstride, int32_t r0, int32_t r1, int32_t k, int32_t wk, int32_t kend,
+                                         bool jvalid, bool jin, int32_t i0, int32_t span, int32_t N,
+                                         uint32_t& empty, uint32_t& inbox, uint32_t& my_bytes, uint32_t& my_rows,
+                                         uint32_t& my_rank, uint32_t& my_dom)
 {
-    const bool lead = g == 0;
     const int32_t spanl = kInterior ? (jvalid ? span : -1) : span;
-    constexpr int kUnroll = kWide ? kWideUnroll : kCountUnroll;
-#pragma unroll kUnroll
-    for (int r = r0; r <= r1; ++r, k += wk, rowp += rstride) {
+#pragma unroll kCountUnroll
+    for (int r = r0; r <= r1; ++r, k += wk, rowp += rstride, rkp += rstride) {
         const int32_t lo = max(max((int32_t)(Al[0] >> 32), (int32_t)(Al[1] >> 32)), max((int32_t)(Al[2] >> 32), 0));
         const int32_t hi = min(min((int32_t)(Ah[0] >> 32), (int32_t)(Ah[1] >> 32)), min((int32_t)(Ah[2] >> 32), spanl));
 #pragma unroll
@@ -669,35 +771,31 @@ __device__ __forceinline__ void dda_rows(int64_t (&Al)[3], int64_t (&Ah)[3], con
             if (lo <= hi) {
                 const int32_t a = i0 + lo, e = i0 + hi;
                 const uint32_t len = (uint32_t)(hi - lo + 1);
-                const uint32_t occ = kWide ? popc_range_wide(rowp, a, e, g, lg) : popc_range(rowp, a, e);
-                const uint32_t lead_len = lead ? len : 0u;
-                empty += lead_len - occ;
-                inbox += lead_len;
-                my_dom += lead_len;
-                if (lead) {
-                    my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                empty += len - popc_mode<kMode>(rowp, rkp, a, e);
+                inbox += len;
+                my_dom += len;
+                if (kProf) {
+                    my_bytes += row_bytes<kMode>(a, e);
                     my_rows += 1;
-                    if (kWide) my_wide += 1;
+                    my_rank += kMode == kRowRank ? 1u : 0u;
                 }
             }
         } else if (jvalid && k < kend && lo <= hi) {
             const uint32_t len = (uint32_t)(hi - lo + 1);
-            uint32_t occ = 0, dom = 0;
+            uint32_t occ = 0;
             if (jin && (uint32_t)k < (uint32_t)N) {
                 const int32_t a = max(i0 + lo, 0), e = min(i0 + hi, N - 1);
                 if (a <= e) {
-                    occ = kWide ? popc_range_wide(rowp, a, e, g, lg) : popc_range(rowp, a, e);
-                    dom = (uint32_t)(e - a + 1);
-                    if (lead) my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                    occ = popc_mode<kMode>(rowp, rkp, a, e);
+                    my_dom += (uint32_t)(e - a + 1);
+                    if (kProf) my_bytes += row_bytes<kMode>(a, e);
                 }
             }
-            const uint32_t lead_len = lead ? len : 0u;
-            empty += lead_len - occ;
-            inbox += lead_len;
-            if (lead) {
-                my_dom += dom;
+            empty += len - occ;
+            inbox += len;
+            if (kProf) {
                 my_rows += 1;
-                if (kWide) my_wide += 1;
+                my_rank += kMode == kRowRank ? 1u : 0u;
             }
         }
     }
@@ -708,23 +806,28 @@ __device__ __forceinline__ void dda_rows(int64_t (&Al)[3], int64_t (&Ah)[3], con
 #else
 #define OBB_COUNT_BOUNDS __launch_bounds__(256)
 #endif
+// kProf: the launch adds up its algorithmic bytes, rows and rank rows into
+// acc[0], acc[1], acc[3]; every launch adds its in-domain points into *dom
+template <bool kProf>
 __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                                                const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ d_K,
                                                unsigned long long* __restrict__ counts,
                                                unsigned long long* __restrict__ points,
                                                unsigned long long* __restrict__ acc,
-                                               unsigned long long* __restrict__ dom)
+                                               unsigned long long* __restrict__ dom,
+                                               const int32_t* __restrict__ perm)
 {
-    uint32_t my_chunks = 0, my_rows = 0, my_dom = 0, my_wide = 0;
+    uint32_t my_bytes = 0, my_rows = 0, my_rank = 0, my_dom = 0;
     const int lane = threadIdx.x & 31;
     const int32_t K = *d_K;
     const int64_t total = off[K];
     unsigned long long* next = reinterpret_cast<unsigned long long*>(const_cast<int64_t*>(off + K + 1));
     // warps take runs of kGrab consecutive tiles from a global counter; within a
     // run the box and the tile coordinates advance incrementally
+    // b: position in the launch's order; bi: the box there (perm[b], or b)
     int64_t c = 0, c_end = 0, box_end = 0;
-    int32_t b = 0, tj = 0, tk = 0;
+    int32_t b = 0, bi = 0, tj = 0, tk = 0;
     for (;;) {
         if (c == c_end) {
             unsigned long long g = 0;
@@ -742,21 +845,23 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 hi = min(hi, lo + st);
             }
             b = lo;
+            bi = perm ? perm[b] : b;
             box_end = off[b + 1];
             const int32_t u = (int32_t)(c - off[b]);
-            const int32_t ntj0 = prep[b].ntj;
+            const int32_t ntj0 = prep[bi].ntj;
             tk = u / ntj0;
             tj = u - tk * ntj0;
         } else if (c >= box_end) {
             ++b;
             while (off[b + 1] <= c) ++b;   // skip boxes without tiles
+            bi = perm ? perm[b] : b;
             box_end = off[b + 1];
             tj = tk = 0;
         }
-        const BoxPrep& p = prep[b];
+        const BoxPrep& p = prep[bi];
         {
             // skip a tile whose rectangle misses the box's shadow on (j, k)
-            const int32_t lw = p.lwj, hk = ((32 >> p.lg) >> lw) * p.tk;
+            const int32_t lw = p.lwj, hk = (32 >> lw) * p.tk;
             const float hj = 0.5f * (float)((1 << lw) - 1), hkf = 0.5f * (float)(hk - 1);
             const float jc = (float)(p.j0 + (tj << lw)) + hj, kc = (float)(p.k0 + tk * hk) + hkf;
             bool out = false;
@@ -779,15 +884,12 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         const int32_t N = p.latN, W = p.latW;
         const int32_t mode = p.mode;
         const int32_t lwj = p.lwj;
-        const int32_t lg = p.lg;
-        const int32_t grp = lane >> lg;            // this lane's group (one row at a time)
-        const int32_t g = lane & ((1 << lg) - 1);  // its place in the group
-        const int32_t wk = (32 >> lg) >> lwj;
-        const int32_t jl = (tj << lwj) + (grp & ((1 << lwj) - 1));
+        const int32_t wk = 32 >> lwj;
+        const int32_t jl = (tj << lwj) + (lane & ((1 << lwj) - 1));
         const int32_t j = p.j0 + jl;
         const bool jvalid = jl < p.nj;
         const int32_t tkr = p.tk;
-        const int32_t kb = p.k0 + tk * (wk * tkr) + (grp >> lwj);   // this group's first row
+        const int32_t kb = p.k0 + tk * (wk * tkr) + (lane >> lwj);   // this lane's first row
         const int32_t kend = p.k0 + p.nk;
         // rows r0..r1 (warp-uniform) of the tile's tkr are visited
         int32_t r0 = 0, r1 = tkr - 1;
@@ -804,7 +906,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
             }
             int32_t rl = tkr, rh = -1;
             if (jvalid && klo <= khi) {
-                const int32_t lwk = 5 - lg - lwj;   // wk = 2^lwk
+                const int32_t lwk = 5 - lwj;   // wk = 2^lwk
                 const int32_t kbr = kb - p.k0;
                 const int32_t kl = (int32_t)floorf(fmaxf(klo, -1e9f));
                 const int32_t kh = (int32_t)ceilf(fminf(khi, 1e9f));
@@ -826,7 +928,7 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 continue;
             }
         }
-        const int32_t kb0 = kb + r0 * wk;   // the first row this group visits
+        const int32_t kb0 = kb + r0 * wk;   // the first row this lane visits
         const int32_t i0 = p.i0, span = p.span;
         // Kind-1 slabs carry exact quotient bounds relative to i0 in 32 bits,
         // saturated at +-2^30: a bound that far out moves less than 2^29 within a
@@ -865,26 +967,25 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 Ah[a] = (int64_t)qb[a] * 4294967296LL + fixed_frac(rb[a], M) + kFixBias;
                 Bs[a] = p.fstep[a];
             }
-            const uint64_t* rowp = words + ((int64_t)kb0 * N + j) * W;
+            const int64_t roff = ((int64_t)kb0 * N + j) * W;
             const int64_t rstride = (int64_t)wk * N * W;
             // an interior box's full-height tile: every row is in the lattice
             // and so is every x-interval; an idle lane gets an empty range
             const bool interior = (mode & 0x100) && (tk + 1) * wk * tkr <= p.nk;
-            if (lg == 0) {
-                if (interior)
-                    dda_rows<false, true>(Al, Ah, Bs, rowp, rstride, r0, r1, kb0, wk, kend, jvalid, jin, i0, span, N,
-                                          g, lg, empty, inbox, my_chunks, my_rows, my_dom, my_wide);
-                else
-                    dda_rows<false, false>(Al, Ah, Bs, rowp, rstride, r0, r1, kb0, wk, kend, jvalid, jin, i0, span, N,
-                                           g, lg, empty, inbox, my_chunks, my_rows, my_dom, my_wide);
+#define OBB_DDA_ROWS(MODE, INTERIOR)                                                                             \
+    dda_rows<MODE, INTERIOR, kProf>(Al, Ah, Bs, words + roff, p.ranks + roff, rstride, r0, r1, kb0, wk, kend, jvalid, \
+                                    jin, i0, span, N, empty, inbox, my_bytes, my_rows, my_rank, my_dom)
+            if (p.rank == kRowRank) {
+                if (interior) OBB_DDA_ROWS(kRowRank, true);
+                else OBB_DDA_ROWS(kRowRank, false);
+            } else if (p.rank == kRowShort) {
+                if (interior) OBB_DDA_ROWS(kRowShort, true);
+                else OBB_DDA_ROWS(kRowShort, false);
             } else {
-                if (interior)
-                    dda_rows<true, true>(Al, Ah, Bs, rowp, rstride, r0, r1, kb0, wk, kend, jvalid, jin, i0, span, N,
-                                         g, lg, empty, inbox, my_chunks, my_rows, my_dom, my_wide);
-                else
-                    dda_rows<true, false>(Al, Ah, Bs, rowp, rstride, r0, r1, kb0, wk, kend, jvalid, jin, i0, span, N,
-                                          g, lg, empty, inbox, my_chunks, my_rows, my_dom, my_wide);
+                if (interior) OBB_DDA_ROWS(kRowWalk, true);
+                else OBB_DDA_ROWS(kRowWalk, false);
             }
+#undef OBB_DDA_ROWS
         } else
 #pragma unroll kCountUnroll
         for (int r = 0; r < tkr; ++r) {
@@ -928,14 +1029,23 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 if (jin && k >= 0 && k < N) {
                     const int32_t a = max(ia, 0), e = min(ie, N - 1);
                     if (a <= e) {
-                        occ = popc_range(words + ((int64_t)k * N + j) * W, a, e);
-                        my_chunks += (uint32_t)((e >> 7) - (a >> 7) + 1);
+                        const int64_t roff = ((int64_t)k * N + j) * W;
+                        if (p.rank == kRowRank) {
+                            occ = popc_rank(words + roff, p.ranks + roff, a, e);
+                            if (kProf) my_bytes += row_bytes<kRowRank>(a, e);
+                        } else {
+                            occ = popc_range(words + roff, a, e);
+                            if (kProf) my_bytes += row_bytes<kRowWalk>(a, e);
+                        }
                         my_dom += (uint32_t)(e - a + 1);
                     }
                 }
                 empty += len - occ;
                 inbox += len;
-                my_rows += 1;
+                if (kProf) {
+                    my_rows += 1;
+                    my_rank += p.rank == kRowRank ? 1u : 0u;
+                }
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -943,8 +1053,8 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
             inbox += __shfl_xor_sync(0xffffffffu, inbox, o);
         }
         if (lane == 0) {
-            if (empty) atomicAdd(&counts[b], (unsigned long long)empty);
-            if (points && inbox) atomicAdd(&points[b], (unsigned long long)inbox);
+            if (empty) atomicAdd(&counts[bi], (unsigned long long)empty);
+            if (points && inbox) atomicAdd(&points[bi], (unsigned long long)inbox);
         }
         if (++tj == p.ntj) {
             tj = 0;
@@ -953,19 +1063,22 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
         ++c;
     }
     // in-domain points of this launch (always), and with profiling its
-    // algorithmic bytes, non-empty rows and rows shared by lane groups: block
-    // sums, one atomic each
-    if (acc || dom) {
+    // algorithmic bytes, non-empty rows and rank rows: block sums, one atomic
+    // each
+    if (kProf || dom) {
         __shared__ unsigned long long sh[4];
         if (threadIdx.x < 4) sh[threadIdx.x] = 0;
         __syncthreads();
-        unsigned long long v[4] = {my_chunks * 16ull, my_rows, my_dom, my_wide};
+        unsigned long long v[4] = {my_bytes, my_rows, my_dom, my_rank};
+#pragma unroll
         for (int i = 0; i < 4; ++i) {
+            if (!kProf && i != 2) continue;
             for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
             if (lane == 0 && v[i]) atomicAdd(&sh[i], v[i]);
         }
         __syncthreads();
-        if (threadIdx.x < 4 && threadIdx.x != 2 && acc && sh[threadIdx.x]) atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
+        if (kProf && threadIdx.x < 4 && threadIdx.x != 2 && acc && sh[threadIdx.x])
+            atomicAdd(&acc[threadIdx.x], sh[threadIdx.x]);
         if (threadIdx.x == 2 && dom && sh[2]) atomicAdd(dom, sh[2]);
     }
 }
@@ -1044,7 +1157,8 @@ static int count_grid(obb_ctx* ctx)
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count, 256, 0) != cudaSuccess || nb < 1) nb = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count<false>, 256, 0) != cudaSuccess || nb < 1)
+            nb = 1;
         blocks_per_sm = nb;
     }
     return blocks_per_sm * ctx->num_sms;
@@ -1053,12 +1167,13 @@ static int count_grid(obb_ctx* ctx)
 obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes, const int32_t* d_K,
                        int64_t K_cap, uint64_t* d_counts, uint64_t* d_points)
 {
-    return count_boxes_multi(ctx, lat->d_ref, 1, nullptr, d_boxes, d_K, K_cap, d_counts, d_points);
+    return count_boxes_multi(ctx, lat->d_ref, 1, nullptr, d_boxes, d_K, K_cap, d_counts, d_points,
+                             (int64_t)lat->n_words * 8);
 }
 
 obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats, const int32_t* d_lat_of_box,
                              const obb_qbox* d_boxes, const int32_t* d_K, int64_t K_cap, uint64_t* d_counts,
-                             uint64_t* d_points)
+                             uint64_t* d_points, int64_t lattice_bytes)
 {
     cudaStream_t s = ctx->stream;
     if (K_cap <= 0) return OBB_OK;
@@ -1066,6 +1181,8 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
     BoxPrep* prep;
     int64_t *tiles, *off;
     unsigned int* ticket = ctx->d_ticket;
+    uint32_t* bucket = nullptr;
+    int32_t* perm = nullptr;
     if (ctx->count_scratch) {
         // fixed scratch of a step being captured into a graph: its addresses must not move
         const CountScratch& cs = *ctx->count_scratch;
@@ -1080,12 +1197,27 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
         prep = ctx->prep.as<BoxPrep>();
         tiles = ctx->chunk_off.as<int64_t>();
         off = tiles + K_cap;
+        if (ctx->count_order && K_cap >= kOrderMinBoxes && lattice_bytes >= kOrderMinLatticeBytes) {
+            // large batches on lattices too large for L2 are counted in
+            // spatial order (boxes of every size over one region together, so
+            // the region's lattice words are reused from L2)
+            OBB_CK(ctx, ctx->order.reserve(2 * sizeof(int32_t) * K_cap, s));
+            bucket = ctx->order.as<uint32_t>();
+            perm = reinterpret_cast<int32_t*>(bucket + K_cap);
+            OBB_CK(ctx, cudaMemsetAsync(ctx->d_order_hist, 0, kOrderBuckets * sizeof(unsigned int), s));
+        }
     }
     // the preparation kernel also zeroes counts and points (accumulated with atomics)
     k_prep<<<(unsigned)((K_cap + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
-        d_boxes, d_K, d_lats, n_lats, d_lat_of_box, ctx->tile_k, ctx->count_axis, prep, tiles, off,
+        d_boxes, d_K, d_lats, n_lats, d_lat_of_box, ctx->tile_k, ctx->count_axis, ctx->count_rank, prep, tiles, off,
         reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
-        ctx->d_err);
+        bucket, bucket ? ctx->d_order_hist : nullptr, ctx->d_err);
+    note_launch(ctx);
+    if (perm) {
+        k_order_scatter<<<(unsigned)((K_cap + 255) / 256), 256, 0, s>>>(bucket, d_K, ctx->d_order_hist, perm);
+        k_order_scan<<<1, 1024, 0, s>>>(tiles, perm, d_K, off);
+        note_launch(ctx, 2);
+    }
     note_launch(ctx);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->prof) {
@@ -1093,10 +1225,14 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
         OBB_CK(ctx, cudaEventCreate(&e1));
         OBB_CK(ctx, cudaEventRecord(e0, s));
     }
-    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K,
-                                            reinterpret_cast<unsigned long long*>(d_counts),
-                                            reinterpret_cast<unsigned long long*>(d_points),
-                                            ctx->prof ? ctx->d_prof : nullptr, ctx->d_prof + 2);
+    if (ctx->prof == 1)
+        k_count<true><<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, reinterpret_cast<unsigned long long*>(d_counts),
+                                                      reinterpret_cast<unsigned long long*>(d_points), ctx->d_prof,
+                                                      ctx->d_prof + 2, perm);
+    else
+        k_count<false><<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, reinterpret_cast<unsigned long long*>(d_counts),
+                                                       reinterpret_cast<unsigned long long*>(d_points), nullptr,
+                                                       ctx->d_prof + 2, perm);
     note_launch(ctx);
     if (ctx->prof) {
         OBB_CK(ctx, cudaEventRecord(e1, s));
@@ -1188,13 +1324,13 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
     note_launch(ctx);
     // the preparation kernel also zeroes counts and points (accumulated with atomics)
     k_prep<<<(unsigned)((K + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
-        d_boxes, dK, lat->d_ref, 1, nullptr, ctx->tile_k, ctx->count_axis, prep, chunks, off,
+        d_boxes, dK, lat->d_ref, 1, nullptr, ctx->tile_k, ctx->count_axis, ctx->count_rank, prep, chunks, off,
         reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
-        ctx->d_err);
+        nullptr, nullptr, ctx->d_err);
     note_launch(ctx);
-    k_count<<<count_grid(ctx), 256, 0, s>>>(prep, off, dK,
-                                            reinterpret_cast<unsigned long long*>(d_counts),
-                                            reinterpret_cast<unsigned long long*>(d_points), nullptr, nullptr);
+    k_count<false><<<count_grid(ctx), 256, 0, s>>>(prep, off, dK, reinterpret_cast<unsigned long long*>(d_counts),
+                                                   reinterpret_cast<unsigned long long*>(d_points), nullptr, nullptr,
+                                                   nullptr);
     note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return OBB_OK;

@@ -173,6 +173,8 @@ obb_status obb_create(obb_ctx** out, int32_t device, void* stream)
     if (cudaMalloc(&c->d_err, sizeof(int32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_ticket, sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc((void**)&c->d_prof, 8 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void**)&c->d_order_hist, kOrderBuckets * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(c->d_order_hist, 0, kOrderBuckets * sizeof(unsigned int)) != cudaSuccess ||
         cudaMemset(c->d_prof, 0, 8 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMallocHost(&c->h_small, 64 * sizeof(int64_t)) != cudaSuccess ||
         cudaMemset(c->d_err, 0, sizeof(int32_t)) != cudaSuccess ||
@@ -202,7 +204,7 @@ void obb_destroy(obb_ctx* ctx)
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->prep, &ctx->chunk_off, &ctx->qscratch, &ctx->cscratch, &ctx->pscratch, &ctx->kdev,
-                      &ctx->tmp_a, &ctx->tmp_b, &ctx->tmp_c, &ctx->tmp_d, &ctx->cub_tmp};
+                      &ctx->tmp_a, &ctx->tmp_b, &ctx->tmp_c, &ctx->tmp_d, &ctx->cub_tmp, &ctx->order};
     for (DevBuf* b : bufs) b->release(ctx->stream);
     cudaStreamSynchronize(ctx->stream);
     for (auto& ev : ctx->prof_ev) {
@@ -212,6 +214,7 @@ void obb_destroy(obb_ctx* ctx)
     if (ctx->d_prof) cudaFree(ctx->d_prof);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_ticket) cudaFree(ctx->d_ticket);
+    if (ctx->d_order_hist) cudaFree(ctx->d_order_hist);
     if (ctx->h_small) cudaFreeHost(ctx->h_small);
     delete ctx;
 }
@@ -286,8 +289,9 @@ obb_status obb_profile_enable(obb_ctx* ctx, int32_t on)
         cudaEventDestroy(ev.second);
     }
     ctx->prof_ev.clear();
+    if (on < 0 || on > 2) return fail(ctx, OBB_ERR_ARG, "profiling mode must be 0, 1 or 2");
     OBB_CK(ctx, cudaMemset(ctx->d_prof, 0, 8 * sizeof(unsigned long long)));
-    ctx->prof = on != 0;
+    ctx->prof = on;
     return OBB_OK;
 }
 
@@ -309,7 +313,7 @@ obb_status obb_profile_read(obb_ctx* ctx, obb_profile_stats* out)
     out->count_bytes = (double)acc[0];
     out->count_rows = (double)acc[1];
     out->count_points_in_domain = (double)acc[2];
-    out->count_rows_shared = (double)acc[3];
+    out->count_rows_rank = (double)acc[3];
     return OBB_OK;
 }
 
@@ -338,6 +342,9 @@ void obb_lattice_free(obb_lattice* lat)
     if (lat->d_words) cudaFreeAsync(lat->d_words, s);
     if (lat->d_words_y) cudaFreeAsync(lat->d_words_y, s);
     if (lat->d_words_z) cudaFreeAsync(lat->d_words_z, s);
+    if (lat->d_rank) cudaFreeAsync(lat->d_rank, s);
+    if (lat->d_rank_y) cudaFreeAsync(lat->d_rank_y, s);
+    if (lat->d_rank_z) cudaFreeAsync(lat->d_rank_z, s);
     if (lat->d_ref) cudaFreeAsync(lat->d_ref, s);
     delete lat;
 }
@@ -412,6 +419,23 @@ obb_status obb_set_counting_axis(obb_ctx* ctx, int32_t axis)
     return OBB_OK;
 }
 
+obb_status obb_set_counting_order(obb_ctx* ctx, int32_t on)
+{
+    if (!ctx) return OBB_ERR_ARG;
+    if (on != 0 && on != 1) return fail(ctx, OBB_ERR_ARG, "order mode must be 0 or 1");
+    ctx->count_order = on;
+    return OBB_OK;
+}
+
+obb_status obb_set_counting_rank(obb_ctx* ctx, int32_t on)
+{
+    if (!ctx) return OBB_ERR_ARG;
+    if (on != 0 && on != 1) return fail(ctx, OBB_ERR_ARG, "rank mode must be 0 or 1");
+    if (on != ctx->count_rank) ++ctx->tile_gen;
+    ctx->count_rank = on;
+    return OBB_OK;
+}
+
 obb_status obb_set_counting_tile(obb_ctx* ctx, int32_t tile_k)
 {
     if (!ctx) return OBB_ERR_ARG;
@@ -439,8 +463,8 @@ obb_status obb_tune_counting(obb_ctx* ctx, const obb_lattice* lat, const obb_qbo
     cudaEvent_t e0, e1;
     OBB_CK(ctx, cudaEventCreate(&e0));
     OBB_CK(ctx, cudaEventCreate(&e1));
-    const bool prof = ctx->prof;
-    ctx->prof = false;
+    const int32_t prof = ctx->prof;
+    ctx->prof = 0;
     obb_status rc = OBB_OK;
     for (int i = 0; i < 4 && rc == OBB_OK; ++i) {
         ctx->tile_k = cand[i];
@@ -496,10 +520,12 @@ obb_status obb_outer_volume_multi(obb_ctx* ctx, const obb_lattice* const* lats, 
     if (K < 0 || K > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_ARG, "K out of range");
     if (K == 0) return OBB_OK;
     std::vector<LatRef> table(n_lats);
+    int64_t lattice_bytes = 0;
     for (int32_t i = 0; i < n_lats; ++i) {
         if (!lats[i]) return fail(ctx, OBB_ERR_ARG, "null lattice in the table");
         if (lats[i]->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
         table[i] = lats[i]->ref;
+        lattice_bytes += (int64_t)lats[i]->n_words * 8;
     }
     HostTmp ht(ctx), hb(ctx), hl(ctx), hc(ctx), hp(ctx);
     const LatRef* dt;
@@ -513,7 +539,7 @@ obb_status obb_outer_volume_multi(obb_ctx* ctx, const obb_lattice* const* lats, 
     OBB_TRY(out_device(ctx, points, (size_t)K, on_device, hp, &dp));
     OBB_CK(ctx, ctx->kdev.reserve(sizeof(int32_t), ctx->stream));
     OBB_TRY(set_device_int(ctx, ctx->kdev.as<int32_t>(), (int32_t)K));
-    OBB_TRY(count_boxes_multi(ctx, dt, n_lats, dl, db, ctx->kdev.as<int32_t>(), K, dc, dp));
+    OBB_TRY(count_boxes_multi(ctx, dt, n_lats, dl, db, ctx->kdev.as<int32_t>(), K, dc, dp, lattice_bytes));
     OBB_TRY(copy_back(ctx, counts, dc, (size_t)K, on_device));
     OBB_TRY(copy_back(ctx, points, dp, (size_t)K, on_device));
     // the lattice table lives in a temporary: wait before it is released

@@ -41,9 +41,9 @@ def test_large_config_full_parity(ctx, name, N, depth):
     """The ~1M-triangle union on 768^3 and the ~2M-triangle union on 1024^3:
     every occupancy word of the whole lattice equals the oracle's per-point
     parity (padding bits zero), and the boxes of the top four levels of the
-    tree built on it (depth 12 / 14), plus 12 boxes drawn from every lower
-    level, count exactly as the oracle counts them, with their in-domain
-    points."""
+    tree built on it (depth 12 / 14), plus up to 160 boxes drawn from every
+    lower level, count exactly as the oracle counts them, with their in-domain
+    points, in spatial order and in the caller's order."""
     O.set_threads(os.cpu_count() or 1)
     try:
         m = M.sdf_union_1m() if name == "1m" else M.sdf_union_2m()
@@ -63,15 +63,21 @@ def test_large_config_full_parity(ctx, name, N, depth):
         qs = []
         for lev in range(depth + 1):
             q = ctx.tree_read(tree, lev)["qboxes"]
-            qs.append(q if lev < 4 else q[rng.choice(len(q), 12, replace=False)])
+            qs.append(q if lev < 4 else q[rng.choice(len(q), min(len(q), 160), replace=False)])
         q = np.concatenate(qs)
-        ctx.profile_enable(True)
-        cnt, pts = ctx.outer_volume_q(lat, q, want_points=True)
-        pr = ctx.profile_read()
-        ctx.profile_enable(False)
+        assert len(q) >= 1024
         ref, tot, dom = O.outer_volume(P.occ, q["n"], q["b"], want_domain=True)
-        assert np.array_equal(cnt, ref) and np.array_equal(pts, tot)
-        assert pr["count_points_in_domain"] == float(dom.sum())
+        try:
+            for order in (1, 0):    # 1024^3 batches of 1,024 boxes or more: spatial order, then the caller's
+                ctx.set_counting_order(order)
+                ctx.profile_enable(True)
+                cnt, pts = ctx.outer_volume_q(lat, q, want_points=True)
+                pr = ctx.profile_read()
+                ctx.profile_enable(False)
+                assert np.array_equal(cnt, ref) and np.array_equal(pts, tot), order
+                assert pr["count_points_in_domain"] == float(dom.sum()), order
+        finally:
+            ctx.set_counting_order(1)
         tree.free()
         lat.free()
         mesh.free()
@@ -148,7 +154,8 @@ def test_benchmark_batch_against_oracle(ctx):
     the ~200k-triangle union at 512^3 (up to the whole lattice, so large boxes
     take shared rows and the doubled tile height) count exactly as the oracle
     counts them, box by box, for tile heights 8 to 64, for rows along each axis
-    and for the per-box axis; the whole lattice is bit-exact."""
+    and for the per-box axis, in spatial order and in the caller's order, with
+    and without the rank tables; the whole lattice is bit-exact."""
     O.set_threads(os.cpu_count() or 1)
     m = M.sdf_union_200k()
     mesh = ctx.mesh_create(m.verts, m.tris)
@@ -174,9 +181,17 @@ def test_benchmark_batch_against_oracle(ctx):
             ctx.set_counting_axis(axis)
             c, p = ctx.outer_volume_q(lat, q, want_points=True)
             assert np.array_equal(c, ref) and np.array_equal(p, tot), axis
+        ctx.set_counting_axis(0)
+        for order, rank in ((0, 1), (0, 0), (1, 0)):   # the caller's order; every word read
+            ctx.set_counting_order(order)
+            ctx.set_counting_rank(rank)
+            c, p = ctx.outer_volume_q(lat, q, want_points=True)
+            assert np.array_equal(c, ref) and np.array_equal(p, tot), (order, rank)
     finally:
         ctx.set_counting_axis(0)
         ctx.set_counting_tile(32)
+        ctx.set_counting_order(1)
+        ctx.set_counting_rank(1)
         O.set_threads(1)
     tree.free()
     lat.free()
