@@ -67,6 +67,11 @@ def parse():
                     help="candidates (and rotation probes) per cluster the surrogate keeps for exact counting")
     ap.add_argument("--lloyd-iters", type=int, default=10,
                     help="Lloyd iterations timed for the plain vs surrogate comparison")
+    ap.add_argument("--surrogate-pairs", type=int, default=2_000_000,
+                    help="training pairs generated on the 202,244-triangle union at 512^3")
+    ap.add_argument("--surrogate-steps", type=int, default=2000, help="Adam steps of surrogate training")
+    ap.add_argument("--no-second-workload", action="store_true",
+                    help="skip the plain vs surrogate comparison on the 1M-triangle union at 768^3")
     ap.add_argument("--walk", action="store_true", help="count every row word by word (no rank tables)")
     ap.add_argument("--profile-batch", metavar="BOXES",
                     help="profiling aid: count the tree batch twice and exit; the tree's boxes are read from "
@@ -87,6 +92,11 @@ def _sdf200k(rank):
     return M.sdf_union_200k(seed=2000 + rank)
 
 
+def _sdf1m(rank):
+    from synth import meshes as M
+    return M.sdf_union_1m(seed=4000 + rank)
+
+
 def _sdf2m(rank):
     from synth import meshes as M
     return M.sdf_union_2m(seed=5000 + rank)
@@ -96,6 +106,8 @@ WORKLOADS = {
     "sdf2m-1024": dict(desc="SDF union 200 spheres + 100 capsules + 50 rounded boxes, {T:,} triangles, 1024^3 "
                             "lattice, depth 14 (16,384 leaves), 3 up/down sweeps", mesh=_sdf2m, N=1024, depth=14,
                        sweeps=3),
+    "sdf1m-768": dict(desc="SDF union 40 spheres + 20 capsules, {T:,} triangles, 768^3 lattice, depth 12 "
+                           "(4,096 leaves)", mesh=_sdf1m, N=768, depth=12, sweeps=0),
     "sdf200k-512": dict(desc="SDF union 40 spheres + 20 capsules, {T:,} triangles, 512^3 lattice, depth 10 "
                              "(1,024 leaves)", mesh=_sdf200k, N=512, depth=10, sweeps=0),
     "torus4k-64": dict(desc="torus R=1 r=0.3, {T:,} triangles, 64^3 lattice, depth 4", mesh=_torus, N=64, depth=4,
@@ -360,9 +372,32 @@ def profile_batch(args):
     ctx.close()
 
 
-def lloyd_comparison(ctx, lat, tree, depth, args, flush, stream):
+def train_surrogate(ctx, args):
+    """The surrogate network trained on (box, exact outer volume) pairs from
+    runs of the method on the 202,244-triangle union at 512^3 (a depth-10
+    tree: Lloyd candidate boxes of every level and perturbed tree boxes),
+    features and targets by the library; returns (mlp, training record)."""
+    from paper_2203_10521_gb300 import surrogate as S
+    t0 = time.perf_counter()
+    w = workload("sdf200k-512", 0)
+    mesh = ctx.mesh_create(w["mesh"].verts, w["mesh"].tris)
+    lat = ctx.build_occupancy(mesh, w["N"])
+    tree = ctx.build_tree(lat, w["depth"], 2)
+    q, c = S.collect_pairs(ctx, lat, tree, w["depth"], iters=2, perturb=6, seed=3, target_pairs=args.surrogate_pairs)
+    t1 = time.perf_counter()
+    mlp = ctx.mlp_create(7)
+    _, mse0, mse1 = S.train(ctx, mlp, lat, q, c, steps=args.surrogate_steps, batch=1024, lr=2e-3, seed=4)
+    rec = {"pairs": int(len(q)), "pairs_from": w["name"], "heldout_mse_before": mse0, "heldout_mse_after": mse1,
+           "steps": args.surrogate_steps, "batch": 1024, "collect_s": t1 - t0, "train_s": time.perf_counter() - t1}
+    tree.free()
+    lat.free()
+    mesh.free()
+    return mlp, rec
+
+
+def lloyd_comparison(ctx, lat, tree, depth, args, flush, stream, mlp=None):
     """Lloyd iterations per second on the same freshly split leaf layer: plain
-    host-driven, plain as one CUDA graph, and with the trained surrogate
+    host-driven, plain as one CUDA graph, and (with a trained surrogate)
     screening candidates and probes (rotation-descent box update, 2 steps);
     final layer totals and exact box counts compared."""
     import torch
@@ -374,16 +409,7 @@ def lloyd_comparison(ctx, lat, tree, depth, args, flush, stream):
     up_layer = ctx.layer_init(lat, up["assign"], (np.arange(Kp) // 2).astype(np.int32), up["frames"])
     child = ctx.layer_split(up_layer)
     up_layer.free()
-    mlp = None
-    modes = ["plain", "plain_graph"] if args.no_surrogate else ["plain", "plain_graph", "surrogate"]
-    if not args.no_surrogate:
-        from paper_2203_10521_gb300 import surrogate as S
-        t0 = time.perf_counter()
-        mlp = ctx.mlp_create(7)
-        q, c = S.collect_pairs(ctx, lat, tree, depth, iters=2, perturb=6, seed=3)
-        _, mse0, mse1 = S.train(ctx, mlp, lat, q, c, steps=400, batch=1024, lr=2e-3, seed=4)
-        lloyd["surrogate_training"] = {"pairs": int(len(q)), "heldout_mse_before": mse0, "heldout_mse_after": mse1,
-                                       "seconds": time.perf_counter() - t0}
+    modes = ["plain", "plain_graph"] + (["surrogate"] if mlp is not None else [])
     for mode in modes:
         lay = ctx.layer_init(lat, child, parent)
         if mode == "surrogate":
@@ -409,9 +435,23 @@ def lloyd_comparison(ctx, lat, tree, depth, args, flush, stream):
         a, b = lloyd["plain"]["final_total_obv"], lloyd["surrogate"]["final_total_obv"]
         lloyd["final_obv_rel_diff"] = (b - a) / a
         lloyd["surrogate_topk"] = args.surrogate_topk
-    if mlp is not None:
-        mlp.free()
+        lloyd["surrogate_vs_plain_iter_ratio"] = lloyd["surrogate"]["iter_per_s"] / lloyd["plain"]["iter_per_s"]
     return lloyd
+
+
+def lloyd_on_workload(ctx, key, args, flush, stream, mlp):
+    """The plain vs screened comparison on another workload (its own mesh,
+    lattice and tree, freed afterwards)."""
+    w = workload(key, 0)
+    mesh = ctx.mesh_create(w["mesh"].verts, w["mesh"].tris)
+    lat = ctx.build_occupancy(mesh, w["N"])
+    tree = ctx.build_tree(lat, w["depth"], args.setup_iters)
+    out = lloyd_comparison(ctx, lat, tree, w["depth"], args, flush, stream, mlp)
+    out["workload"] = w["name"]
+    tree.free()
+    lat.free()
+    mesh.free()
+    return out
 
 
 def main():
@@ -519,7 +559,14 @@ def main():
     t_max, pts_all, launches_all = reduce_ranks(t_rank, pts_dom, launches, world, "cuda")
     value = pts_all / t_max
 
-    lloyd = lloyd_comparison(ctx, lat, tree, depth, args, flush, stream)
+    mlp, training = (None, None) if args.no_surrogate else train_surrogate(ctx, args)
+    lloyd = lloyd_comparison(ctx, lat, tree, depth, args, flush, stream, mlp)
+    lloyd["workload"] = wl["name"]
+    lloyd_other = None
+    if mlp is not None and wl["key"] == "sdf2m-1024" and not args.no_second_workload:
+        lloyd_other = lloyd_on_workload(ctx, "sdf1m-768", args, flush, stream, mlp)
+    if mlp is not None:
+        mlp.free()
 
     # roofline of the counting kernel: algorithmic bytes of the batch launch
     # over its event-timed duration in the timed region
@@ -610,7 +657,8 @@ def main():
                "lloyd_iter_per_s": lloyd["plain"]["iter_per_s"],
                "lloyd_graph_iter_per_s": lloyd["plain_graph"]["iter_per_s"],
                "surrogate_lloyd_iter_per_s": lloyd["surrogate"]["iter_per_s"] if "surrogate" in lloyd else None,
-               "lloyd_comparison": lloyd, "lloyd_last_step": last,
+               "lloyd_comparison": lloyd, "lloyd_comparison_1m_768": lloyd_other,
+               "surrogate_training": training, "lloyd_last_step": last,
                "setup": {"tree_s": tree_s, "sweeps": sweep}, "wall_s_timed": wall}
         print(json.dumps(out), flush=True)
     layer.free()

@@ -534,6 +534,12 @@ void obb_mlp_free(obb_mlp* mlp);
 int64_t obb_mlp_num_params(void);
 obb_status obb_mlp_params(obb_ctx* ctx, const obb_mlp* mlp, float* out, int32_t on_device);
 obb_status obb_mlp_set_params(obb_ctx* ctx, obb_mlp* mlp, const float* in, int32_t on_device);
+/* Training targets of K quantised boxes with exact outer volumes counts
+ * (uint64 [K]): out[k] = counts[k] / (prod_a (H_a - L_a + 1) / |det n|),
+ * clipped to [0, 1] -- the empty fraction in the very cell volume the screen
+ * multiplies a prediction by (float [K]). */
+obb_status obb_surrogate_targets(obb_ctx* ctx, const obb_qbox* boxes, const uint64_t* counts, int64_t K, float* out,
+                                 int32_t on_device);
 /* features float [K][524] of K quantised boxes on a lattice */
 obb_status obb_surrogate_features(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* boxes, int64_t K, float* feats,
                                   int32_t on_device);
@@ -549,7 +555,8 @@ obb_status obb_mlp_train_step(obb_ctx* ctx, obb_mlp* mlp, const float* feats, co
                               float lr, float* loss, int32_t on_device);
 /* Screen the layer's Lloyd iterations with a surrogate (mlp = NULL turns it
  * off): in the partition rounds keep, per source cluster, the topk candidate
- * moves by predicted gain (topk = 0: no move screening); in the refit count
+ * moves by predicted gain (topk = 0: no move screening; at most 16,
+ * OBB_ERR_ARG beyond); in the refit count
  * exactly only the new boxes whose predicted outer volume is below 1.05 x the
  * current exact one.  Every accepted move and refit is still decided by the
  * exact count.  The surrogate must outlive its use by the layer. */

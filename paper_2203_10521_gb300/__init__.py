@@ -139,6 +139,7 @@ def load(build_if_missing: bool = True):
         "obb_mlp_params": [vp, vp, vp, i32],
         "obb_mlp_set_params": [vp, vp, vp, i32],
         "obb_surrogate_features": [vp, vp, vp, i64, vp, i32],
+        "obb_surrogate_targets": [vp, vp, vp, i64, vp, i32],
         "obb_mlp_forward": [vp, vp, vp, i64, vp, i32, i32],
         "obb_mlp_gradients": [vp, vp, vp, vp, i64, vp, vp, i32],
         "obb_mlp_train_step": [vp, vp, vp, vp, i64, C.c_float, vp, i32],
@@ -179,7 +180,8 @@ def exported_symbols():
             "obb_set_counting_order", "obb_test_inject",
             "obb_tune_counting",
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
-            "obb_surrogate_features", "obb_mlp_forward", "obb_mlp_gradients", "obb_mlp_train_step",
+            "obb_surrogate_features", "obb_surrogate_targets", "obb_mlp_forward", "obb_mlp_gradients",
+            "obb_mlp_train_step",
             "obb_layer_set_surrogate", "obb_layer_last_candidates"]
 
 
@@ -363,10 +365,34 @@ class Context:
         return (cnt, pts) if want_points else cnt
 
     def outer_volume_q_noalloc(self, lat, qboxes, counts, points=None):
-        """Device-only variant that allocates nothing (see obbvar.h); qboxes, counts
-        and points are torch CUDA tensors the caller owns."""
-        K = qboxes.numel() * qboxes.element_size() // 88
-        pp = C.c_void_p(points.data_ptr()) if points is not None else None
+        """Device-only variant that allocates nothing (see obbvar.h); qboxes
+        (88-byte records), counts and points (8-byte elements) are contiguous
+        torch CUDA tensors on this context's device that the caller owns."""
+        import torch
+        dev = torch.device(f"cuda:{self.device}")
+
+        def check(t, name, itemsize):
+            if not (_is_torch(t) and t.is_cuda and t.device == dev):
+                raise ValueError(f"{name} must be a CUDA tensor on {dev}")
+            if not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+            if itemsize and t.element_size() != itemsize:
+                raise ValueError(f"{name} must have {itemsize}-byte elements")
+
+        check(qboxes, "qboxes", 0)
+        nbytes = qboxes.numel() * qboxes.element_size()
+        if nbytes % 88:
+            raise ValueError("qboxes must hold whole 88-byte box records")
+        K = nbytes // 88
+        check(counts, "counts", 8)
+        if counts.numel() < K:
+            raise ValueError(f"counts holds {counts.numel()} values for {K} boxes")
+        pp = None
+        if points is not None:
+            check(points, "points", 8)
+            if points.numel() < K:
+                raise ValueError(f"points holds {points.numel()} values for {K} boxes")
+            pp = C.c_void_p(points.data_ptr())
         self.check(self.lib.obb_outer_volume_q_noalloc(self.h, lat.h, C.c_void_p(qboxes.data_ptr()), K,
                                                          C.c_void_p(counts.data_ptr()), pp))
         return counts
@@ -503,6 +529,23 @@ class Context:
                 out = np.zeros((K, self.SURROGATE_INPUTS), np.float32)
         po = C.c_void_p(out.data_ptr()) if dev else out.ctypes.data_as(C.c_void_p)
         self.check(self.lib.obb_surrogate_features(self.h, lat.h, p, K, po, dev))
+        return out
+
+    def surrogate_targets(self, qboxes, counts):
+        """Training targets: exact outer volume / the box's cell volume (the
+        screen's scale), clipped to [0, 1].  CUDA tensors in -> CUDA tensor out
+        (qboxes as bytes, counts int64), numpy -> numpy."""
+        p, dev, keep = _arg(qboxes, QBOX_DTYPE)
+        K = _count(qboxes, keep, 88)
+        pc, _, keepc = _arg(counts, np.uint64)
+        if dev:
+            import torch
+            out = torch.empty(K, dtype=torch.float32, device=f"cuda:{self.device}")
+            po = C.c_void_p(out.data_ptr())
+        else:
+            out = np.zeros(K, np.float32)
+            po = out.ctypes.data_as(C.c_void_p)
+        self.check(self.lib.obb_surrogate_targets(self.h, p, pc, K, po, dev))
         return out
 
     def mlp_forward(self, mlp, feats, half=True):

@@ -33,6 +33,8 @@ namespace {
 
 enum { kCtrCand = 0, kCtrEval, kCtrCount };
 
+constexpr int kMaxTopk = 16;   // candidates a surrogate may keep per source cluster
+
 struct Cand {
     int32_t t, s;
     int32_t k[3];
@@ -608,7 +610,7 @@ __device__ __forceinline__ uint32_t float_key(float f)
 // predicted gain of each candidate record from predicted outer volumes of its boxes
 __global__ void k_screen_score(const Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
                                const uint64_t* __restrict__ obv, const float* __restrict__ pred,
-                               unsigned long long* __restrict__ key, uint8_t* __restrict__ kept)
+                               unsigned long long* __restrict__ key)
 {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ctr[kCtrCand]) return;
@@ -620,36 +622,39 @@ __global__ void k_screen_score(const Cand* __restrict__ cand, const int32_t* __r
         best = fmaxf(best, rem - add);
     }
     key[r] = ((unsigned long long)float_key(best) << 32) | (unsigned long long)(0xffffffffu - (uint32_t)c.t);
-    kept[r] = 0;
 }
 
-__global__ void k_screen_pick(const Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
-                              const unsigned long long* __restrict__ key, const uint8_t* __restrict__ kept,
-                              unsigned long long* __restrict__ slot)
+// Top-k of each source cluster in one pass: a record's key is inserted into
+// its cluster's k slots (kept in descending order) by a chain of atomicMax
+// operations, each slot keeping the larger of its value and the carried one
+// and passing the smaller on; after every record has gone through, the slots
+// hold the k largest keys of the cluster (keys are distinct: they end with the
+// record's triangle).
+__global__ void k_screen_insert(const Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
+                                const unsigned long long* __restrict__ key, int32_t topk,
+                                unsigned long long* __restrict__ slot)
 {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= ctr[kCtrCand] || kept[r]) return;
-    atomicMax(&slot[cand[r].s], key[r]);
+    if (r >= ctr[kCtrCand]) return;
+    unsigned long long v = key[r];
+    unsigned long long* sl = slot + (int64_t)cand[r].s * kMaxTopk;
+    for (int i = 0; i < topk && v; ++i) {
+        const unsigned long long old = atomicMax(&sl[i], v);
+        v = old < v ? old : v;
+    }
 }
 
-__global__ void k_screen_mark(const Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
-                              const unsigned long long* __restrict__ key, uint8_t* __restrict__ kept,
-                              const unsigned long long* __restrict__ slot)
-{
-    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= ctr[kCtrCand] || kept[r]) return;
-    if (slot[cand[r].s] == key[r]) kept[r] = 1;
-}
-
-// keep the selected records' boxes in a new evaluation list; the others propose nothing
+// keep the records among their source cluster's top k (key at least the k-th
+// slot) with their boxes in a new evaluation list; the others propose nothing
 __global__ void k_screen_compact(Cand* __restrict__ cand, const int32_t* __restrict__ ctr,
-                                 const uint8_t* __restrict__ kept, const obb_qbox* __restrict__ evals,
-                                 obb_qbox* __restrict__ evals2, int32_t* __restrict__ n2)
+                                 const unsigned long long* __restrict__ key, const unsigned long long* __restrict__ slot,
+                                 int32_t topk, const obb_qbox* __restrict__ evals, obb_qbox* __restrict__ evals2,
+                                 int32_t* __restrict__ n2)
 {
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ctr[kCtrCand]) return;
     Cand c = cand[r];
-    if (!kept[r]) {
+    if (key[r] < slot[(int64_t)c.s * kMaxTopk + topk - 1]) {
         cand[r].nk = 0;
         return;
     }
@@ -818,7 +823,6 @@ struct LayerMem {
     float* feats = nullptr;
     float* pred = nullptr;
     unsigned long long* skey = nullptr;
-    uint8_t* kept = nullptr;
     unsigned long long* slot = nullptr;
     obb_qbox* evals2 = nullptr;
     int32_t* n2 = nullptr;
@@ -887,7 +891,7 @@ void layer_destroy(obb_layer* L)
         if (M->cscr_mem) cudaFreeAsync(M->cscr_mem, s);
         void* mp[] = {M->iota, M->keys_out, M->ctr, M->cand, M->evals, M->ecount, M->epoints, M->mom,
                       M->newframe, M->newq, M->ncount, M->dK, M->cub_tmp, M->feats, M->pred, M->skey,
-                      M->kept, M->slot, M->evals2, M->n2, M->map, M->dirty, M->keep, M->level,
+                      M->slot, M->evals2, M->n2, M->map, M->dirty, M->keep, M->level,
                       M->pframes, M->pq, M->pbest, M->pcount};
         for (void* p : mp)
             if (p) cudaFreeAsync(p, s);
@@ -1035,17 +1039,12 @@ static obb_status round_body(obb_ctx* ctx, obb_layer* L)
         // source cluster; only their boxes are counted exactly
         OBB_TRY(surrogate_predict(ctx, L->mlp, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->feats, M->pred));
         const unsigned cb0 = (unsigned)((M->cand_cap + 127) / 128);
-        k_screen_score<<<cb0, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->pred, M->skey, M->kept);
-        note_launch(ctx);
-        for (int pass = 0; pass < L->topk; ++pass) {
-            OBB_CK(ctx, cudaMemsetAsync(M->slot, 0, sizeof(unsigned long long) * K, s));
-            k_screen_pick<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->kept, M->slot);
-            k_screen_mark<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->kept, M->slot);
-            note_launch(ctx, 2);
-        }
+        k_screen_score<<<cb0, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->pred, M->skey);
+        OBB_CK(ctx, cudaMemsetAsync(M->slot, 0, sizeof(unsigned long long) * kMaxTopk * K, s));
+        k_screen_insert<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, L->topk, M->slot);
         OBB_CK(ctx, cudaMemsetAsync(M->n2, 0, sizeof(int32_t), s));
-        k_screen_compact<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->kept, M->evals, M->evals2, M->n2);
-        note_launch(ctx);
+        k_screen_compact<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->slot, L->topk, M->evals, M->evals2, M->n2);
+        note_launch(ctx, 3);
         evals = M->evals2;
         n_eval = M->n2;
     }
@@ -1379,13 +1378,13 @@ obb_status layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, i
 {
     cudaStream_t s = ctx->stream;
     LayerMem* M = mem_of(L);
+    if (topk < 0 || topk > kMaxTopk) return fail(ctx, OBB_ERR_ARG, "topk must be in [0, 16]");
     if (mlp && !M->feats) {
         const size_t cap2 = (size_t)std::max<int64_t>(M->eval_cap, (int64_t)kProbes * L->K);
         cudaError_t e = dalloc(&M->feats, cap2 * kSurrogateInputs, s);
         if (e == cudaSuccess) e = dalloc(&M->pred, cap2, s);
         if (e == cudaSuccess) e = dalloc(&M->skey, M->cand_cap, s);
-        if (e == cudaSuccess) e = dalloc(&M->kept, M->cand_cap, s);
-        if (e == cudaSuccess) e = dalloc(&M->slot, L->K, s);
+        if (e == cudaSuccess) e = dalloc(&M->slot, (size_t)kMaxTopk * L->K, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "surrogate screening scratch");
     }
     L->mlp = mlp;

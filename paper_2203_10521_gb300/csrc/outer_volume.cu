@@ -1303,6 +1303,7 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
 {
     using namespace obbv;
     if (!ctx || !lat) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (lat->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
     if (K < 0) return fail(ctx, OBB_ERR_ARG, "negative K");
     if (K > kNoAllocMaxBoxes)
         return fail(ctx, OBB_ERR_RANGE,

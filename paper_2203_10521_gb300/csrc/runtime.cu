@@ -371,6 +371,7 @@ static obb_status outer_volume_impl(obb_ctx* ctx, const obb_lattice* lat, const 
                                     int32_t on_device)
 {
     if (!ctx || !lat || (K > 0 && (!counts || !(boxes || qboxes)))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (lat->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
     if (K < 0 || K > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_ARG, "K out of range");
     if (K == 0) return OBB_OK;
     HostTmp hb(ctx), hc(ctx), hp(ctx);

@@ -558,6 +558,17 @@ __global__ void k_pred_obv(const float* __restrict__ frac, const obb_qbox* __res
     pred[i] = frac[i] * box_cells(boxes[i]);
 }
 
+// training target = exact outer volume / the same cell volume the screen scales by, in [0, 1]
+__global__ void k_targets(const uint64_t* __restrict__ counts, const obb_qbox* __restrict__ boxes, int64_t K,
+                          float* __restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= K) return;
+    const float cells = box_cells(boxes[i]);
+    const float t = cells > 0.f ? (float)counts[i] / cells : 0.f;
+    out[i] = fminf(fmaxf(t, 0.f), 1.f);
+}
+
 template <typename TB>
 void gemm(obb_ctx* ctx, int M, int N, int K, const float* A, int64_t sAm, int64_t sAk, const TB* B, int64_t sBk,
           int64_t sBn, float* C, int64_t ldc, const float* bias, int act, const float* mask, int64_t ldm,
@@ -803,6 +814,30 @@ obb_status obb_surrogate_features(obb_ctx* ctx, const obb_lattice* lat, const ob
         cudaFreeAsync(df, ctx->stream);
     }
     if (hb) cudaFreeAsync(hb, ctx->stream);
+    return on_device ? OBB_OK : check_device_error(ctx);
+}
+
+obb_status obb_surrogate_targets(obb_ctx* ctx, const obb_qbox* boxes, const uint64_t* counts, int64_t K, float* out,
+                                 int32_t on_device)
+{
+    if (!ctx || (K > 0 && (!boxes || !counts || !out))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (K <= 0) return OBB_OK;
+    void *hb = nullptr, *hc = nullptr;
+    const obb_qbox* db;
+    const uint64_t* dc;
+    OBB_TRY(dev_in(ctx, boxes, (size_t)K, on_device, &hb, &db));
+    OBB_TRY(dev_in(ctx, counts, (size_t)K, on_device, &hc, &dc));
+    float* dout = out;
+    if (!on_device) OBB_CK(ctx, cudaMallocAsync((void**)&dout, sizeof(float) * K, ctx->stream));
+    k_targets<<<(unsigned)((K + 255) / 256), 256, 0, ctx->stream>>>(dc, db, K, dout);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    if (!on_device) {
+        OBB_CK(ctx, cudaMemcpyAsync(out, dout, sizeof(float) * K, cudaMemcpyDeviceToHost, ctx->stream));
+        cudaFreeAsync(dout, ctx->stream);
+    }
+    if (hb) cudaFreeAsync(hb, ctx->stream);
+    if (hc) cudaFreeAsync(hc, ctx->stream);
     return on_device ? OBB_OK : check_device_error(ctx);
 }
 

@@ -68,6 +68,29 @@ def test_features_match_definition(ctx, torus):
     assert far.mean() > 0.99
 
 
+def test_targets_are_exact_counts_over_cell_volume(ctx, torus):
+    """The library's training targets are the exact outer volume divided by
+    the box's cell volume prod(H_a - L_a + 1) / |det n| (the scale the screen
+    multiplies its prediction by), clipped to [0, 1]: checked against exact
+    rational arithmetic on the oracle's counts."""
+    from fractions import Fraction as Fr
+    m, mesh, lat, P = torus
+    q = _rand_qboxes(ctx, lat, np.random.Generator(np.random.PCG64(5)), 200)
+    ref, _ = O.outer_volume(P.occ, q["n"], q["b"])
+    t = ctx.surrogate_targets(q, ref)
+    for i in range(len(q)):
+        n = [[int(v) for v in q["n"][i, 3 * a:3 * a + 3]] for a in range(3)]
+        det = (n[0][0] * (n[1][1] * n[2][2] - n[1][2] * n[2][1]) - n[0][1] * (n[1][0] * n[2][2] - n[1][2] * n[2][0])
+               + n[0][2] * (n[1][0] * n[2][1] - n[1][1] * n[2][0]))
+        w = 1
+        for a in range(3):
+            L = -((-int(q["b"][i, 2 * a])) // 256)
+            H = int(q["b"][i, 2 * a + 1]) // 256
+            w *= max(H - L + 1, 0)
+        want = 0.0 if w == 0 else float(min(max(Fr(int(ref[i]) * abs(det), w), Fr(0)), Fr(1)))
+        assert abs(float(t[i]) - want) <= 1e-6 * max(want, 1e-6), (i, float(t[i]), want)
+
+
 def test_forward_and_gradients_match_fp64_oracle(ctx):
     mlp = ctx.mlp_create(0)
     p = SP.mlp_params(11)

@@ -64,6 +64,35 @@ def test_noalloc_matches_regular_entry_point_on_consecutive_calls():
     with pytest.raises(P.ObbError) as e:
         ctx.outer_volume_q_noalloc(lat, big, out)
     assert e.value.code == -3 and "4096" in str(e.value)
+    # the largest batch allowed fills every scratch region
+    q = ctx.quantize_boxes(lat, _boxes(rng, 4096, [-1.6, -1.6, -0.6], [1.6, 1.6, 0.6], 0.0, 0.8))
+    dq = torch.from_numpy(q.view(np.uint8).copy()).cuda()
+    ref_c, ref_p = ctx.outer_volume_q(lat, dq, want_points=True)
+    cnt = torch.full((4096,), -1, dtype=torch.int64, device="cuda")
+    pts = torch.full((4096,), -1, dtype=torch.int64, device="cuda")
+    ctx.outer_volume_q_noalloc(lat, dq, cnt, pts)
+    ctx.synchronize()
+    assert torch.equal(cnt, ref_c) and torch.equal(pts, ref_p)
+    # arrays the entry point cannot use are refused before any launch
+    with pytest.raises(ValueError):
+        ctx.outer_volume_q_noalloc(lat, dq.cpu(), cnt)
+    with pytest.raises(ValueError):
+        ctx.outer_volume_q_noalloc(lat, dq, cnt[:100])
+    with pytest.raises(ValueError):
+        ctx.outer_volume_q_noalloc(lat, dq[:-1], cnt)
+    lat.free()
+    # the per-box row axis reads the lattice's y- and z-row copies through the same scratch
+    try:
+        ctx.set_counting_axis(-1)
+        lat = ctx.build_occupancy(mesh, 64)
+        dq = torch.from_numpy(ctx.quantize_boxes(lat, batches[0]).view(np.uint8).copy()).cuda()
+        ref_c = ctx.outer_volume_q(lat, dq)
+        cnt = torch.full((len(batches[0]),), -1, dtype=torch.int64, device="cuda")
+        ctx.outer_volume_q_noalloc(lat, dq, cnt)
+        ctx.synchronize()
+        assert torch.equal(cnt, ref_c)
+    finally:
+        ctx.set_counting_axis(0)
     lat.free()
     mesh.free()
     ctx.close()
