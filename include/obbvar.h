@@ -360,6 +360,17 @@ obb_status obb_lloyd_step(obb_ctx* ctx, obb_layer* layer, const obb_step_opts* o
  * Any output may be NULL. */
 obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* layer, int32_t* assign, double* frames,
                           obb_qbox* qboxes, obb_box* boxes, uint64_t* obv, int32_t on_device);
+
+/* Moments of the layer's clusters (the input of the covariance refit,
+ * Gottschalk-style continuous triangle surface, coordinates relative to the
+ * cluster's own origin: the first vertex of its lowest-numbered triangle):
+ * out float64 [K][10] = {sum A, sum A m (3),
+ * sum A/12 (9 m m^T + p p^T + q q^T + r r^T) (6: xx yy zz xy xz yz)}, host
+ * memory.  compensated = 1 sums them as the refit does (FP32 products and
+ * sums with error-free transformations, Knuth's TwoSum and Dekker's
+ * TwoProduct); 0 sums the same terms in plain FP32 (a diagnostic of what the
+ * compensation buys).  Synchronises. */
+obb_status obb_layer_moments(obb_ctx* ctx, obb_layer* layer, int32_t compensated, double* out);
 int32_t obb_layer_clusters(const obb_layer* layer);
 
 typedef struct {
@@ -555,7 +566,7 @@ obb_status obb_mlp_train_step(obb_ctx* ctx, obb_mlp* mlp, const float* feats, co
                               float lr, float* loss, int32_t on_device);
 /* Screen the layer's Lloyd iterations with a surrogate (mlp = NULL turns it
  * off): in the partition rounds keep, per source cluster, the topk candidate
- * moves by predicted gain (topk = 0: no move screening; at most 16,
+ * moves by predicted gain (topk = 0: no move screening; at most 6,
  * OBB_ERR_ARG beyond); in the refit count
  * exactly only the new boxes whose predicted outer volume is below 1.05 x the
  * current exact one.  Every accepted move and refit is still decided by the

@@ -145,6 +145,7 @@ def load(build_if_missing: bool = True):
         "obb_mlp_train_step": [vp, vp, vp, vp, i64, C.c_float, vp, i32],
         "obb_layer_set_surrogate": [vp, vp, vp, i32],
         "obb_layer_last_candidates": [vp, vp, vp, vp, i64, C.POINTER(i64)],
+        "obb_layer_moments": [vp, vp, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -182,7 +183,7 @@ def exported_symbols():
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_surrogate_targets", "obb_mlp_forward", "obb_mlp_gradients",
             "obb_mlp_train_step",
-            "obb_layer_set_surrogate", "obb_layer_last_candidates"]
+            "obb_layer_set_surrogate", "obb_layer_last_candidates", "obb_layer_moments"]
 
 
 def _is_torch(x):
@@ -490,6 +491,14 @@ class Context:
                                            frames.ctypes.data_as(C.c_void_p), q.ctypes.data_as(C.c_void_p),
                                            boxes.ctypes.data_as(C.c_void_p), obv.ctypes.data_as(C.c_void_p), 0))
         return dict(assign=assign, frames=frames, qboxes=q, boxes=boxes, obv=obv)
+
+    def layer_moments(self, layer, compensated=True):
+        """Cluster moments float64 [K, 10] as the refit sums them (compensated
+        FP32) or in plain FP32 (compensated=False)."""
+        out = np.zeros((layer.K, 10), np.float64)
+        self.check(self.lib.obb_layer_moments(self.h, layer.h, 1 if compensated else 0,
+                                              out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def layer_split(self, layer):
         child = np.zeros(layer.lat.mesh.nt, np.int32)

@@ -299,6 +299,8 @@ obb_status rebuild_members(obb_ctx* ctx, obb_layer* L);
 obb_status layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, int32_t topk);
 obb_status layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox* out, uint64_t* counts, int64_t cap,
                                  int64_t* n);
+// cluster moments [K][10] (host) summed as the refit sums them (compensated) or in plain FP32
+obb_status layer_moments(obb_ctx* ctx, obb_layer* L, int32_t compensated, double* out);
 // pieces of the Lloyd step that the step between levels (sweep.cu) reuses
 enum { kStProposals = 0, kStAccepted, kStGain, kStEvals, kStRefits, kStPoints, kStCount };
 obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dsteps);

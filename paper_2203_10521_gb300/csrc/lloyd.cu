@@ -368,7 +368,9 @@ __device__ __forceinline__ Comp comp_merge(Comp a, Comp b)
     return Comp{s, __fadd_rn(__fadd_rn(a.c, b.c), e)};
 }
 
-template <int NT>
+// kComp = false: the same sums in plain FP32 (one rounding per fused
+// multiply-add, no error terms) -- kept only to measure what compensation buys
+template <int NT, bool kComp = true>
 __global__ void __launch_bounds__(NT) k_moments(const float* __restrict__ V, const int32_t* __restrict__ F,
                                                 const int32_t* __restrict__ members,
                                                 const int32_t* __restrict__ start,
@@ -378,7 +380,18 @@ __global__ void __launch_bounds__(NT) k_moments(const float* __restrict__ V, con
     const int32_t k = blockIdx.x;
     if (dirty && !dirty[k]) return;
     const int32_t b0 = start[k], b1 = start[k + 1];
-    const double cx = f->center[0], cy = f->center[1], cz = f->center[2];
+    // coordinates relative to the cluster's own origin (the first vertex of
+    // its first member), subtracted exactly in FP64 and rounded once to FP32:
+    // small clusters far from the lattice centre keep their spread instead of
+    // losing it to cancellation in sum M / sum A - mu mu^T (the covariance
+    // does not depend on the origin)
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    if (b1 > b0) {
+        const float* O0 = V + 3 * (int64_t)F[3 * (int64_t)members[b0]];
+        cx = (double)O0[0];
+        cy = (double)O0[1];
+        cz = (double)O0[2];
+    }
     Comp acc[10];
     for (int i = 0; i < 10; ++i) acc[i] = Comp{0.f, 0.f};
     for (int32_t i = b0 + threadIdx.x; i < b1; i += NT) {
@@ -401,14 +414,18 @@ __global__ void __launch_bounds__(NT) k_moments(const float* __restrict__ V, con
         float A = 0.5f * sqrtf(nx * nx + ny * ny + nz * nz);
         float m[3];
         for (int b = 0; b < 3; ++b) m[b] = (P[0][b] + P[1][b] + P[2][b]) / 3.0f;
-        comp_fma(acc[0], A, 1.0f);
-        for (int b = 0; b < 3; ++b) comp_fma(acc[1 + b], A, m[b]);
+        auto add = [&](Comp& a, float x, float y) {
+            if constexpr (kComp) comp_fma(a, x, y);
+            else a.s = __fmaf_rn(x, y, a.s);
+        };
+        add(acc[0], A, 1.0f);
+        for (int b = 0; b < 3; ++b) add(acc[1 + b], A, m[b]);
         const float a12 = A / 12.0f;
         const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
         for (int qd = 0; qd < 6; ++qd) {
             const int x = ia[qd], y = ib[qd];
             float sxy = 9.0f * m[x] * m[y] + P[0][x] * P[0][y] + P[1][x] * P[1][y] + P[2][x] * P[2][y];
-            comp_fma(acc[4 + qd], a12, sxy);
+            add(acc[4 + qd], a12, sxy);
         }
     }
     __shared__ Comp sh[10][NT / 32];
@@ -418,14 +435,18 @@ __global__ void __launch_bounds__(NT) k_moments(const float* __restrict__ V, con
         for (int o = 16; o > 0; o >>= 1) {
             Comp y{__shfl_xor_sync(0xffffffffu, x.s, o), __shfl_xor_sync(0xffffffffu, x.c, o)};
             // combine in lane order so every lane holds the same bits
-            x = (lane & o) ? comp_merge(y, x) : comp_merge(x, y);
+            if constexpr (kComp) x = (lane & o) ? comp_merge(y, x) : comp_merge(x, y);
+            else x = Comp{(lane & o) ? __fadd_rn(y.s, x.s) : __fadd_rn(x.s, y.s), 0.f};
         }
         if (lane == 0) sh[i][w] = x;
     }
     __syncthreads();
     if (threadIdx.x < 10) {
         Comp x = sh[threadIdx.x][0];
-        for (int i = 1; i < NT / 32; ++i) x = comp_merge(x, sh[threadIdx.x][i]);
+        for (int i = 1; i < NT / 32; ++i) {
+            if constexpr (kComp) x = comp_merge(x, sh[threadIdx.x][i]);
+            else x.s = __fadd_rn(x.s, sh[threadIdx.x][i].s);
+        }
         mom[10 * (int64_t)k + threadIdx.x] = (double)x.s + (double)x.c;
     }
 }
@@ -1390,6 +1411,26 @@ obb_status layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, i
     L->mlp = mlp;
     L->topk = topk;
     return OBB_OK;
+}
+
+obb_status layer_moments(obb_ctx* ctx, obb_layer* L, int32_t compensated, double* out)
+{
+    cudaStream_t s = ctx->stream;
+    OBB_TRY(layer_members(ctx, L));
+    const obb_lattice* lat = L->lat;
+    double* d = nullptr;
+    OBB_CK(ctx, cudaMallocAsync((void**)&d, sizeof(double) * 10 * L->K, s));
+    if (compensated)
+        k_moments<kNT, true><<<L->K, kNT, 0, s>>>(lat->mesh->d_verts, lat->mesh->d_tris, L->d_members, L->d_start,
+                                                  lat->d_frame, d, nullptr);
+    else
+        k_moments<kNT, false><<<L->K, kNT, 0, s>>>(lat->mesh->d_verts, lat->mesh->d_tris, L->d_members, L->d_start,
+                                                   lat->d_frame, d, nullptr);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaGetLastError());
+    OBB_CK(ctx, cudaMemcpyAsync(out, d, sizeof(double) * 10 * L->K, cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(d, s);
+    return check_device_error(ctx);
 }
 
 obb_status layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox* out, uint64_t* counts, int64_t cap,

@@ -653,6 +653,13 @@ obb_status obb_layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox*
     return layer_last_candidates(ctx, L, boxes, counts, cap, n);
 }
 
+obb_status obb_layer_moments(obb_ctx* ctx, obb_layer* L, int32_t compensated, double* out)
+{
+    if (!ctx || !L || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (L->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
+    return layer_moments(ctx, L, compensated, out);
+}
+
 void obb_layer_free(obb_layer* L) { layer_destroy(L); }
 
 obb_status obb_layer_split(obb_ctx* ctx, const obb_layer* L, int32_t* child, int32_t on_device)
