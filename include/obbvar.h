@@ -68,6 +68,7 @@ typedef struct obb_lattice obb_lattice;
 typedef struct obb_layer obb_layer;
 typedef struct obb_tree obb_tree;
 typedef struct obb_mlp obb_mlp;
+typedef struct obb_batch obb_batch;
 
 /* A world-space oriented box: centre, first two unit axes (axis2 = axis0 x
  * axis1), half extents along the three axes.  48 bytes. */
@@ -516,6 +517,24 @@ obb_status obb_tree_score(obb_ctx* ctx, const obb_tree* tree, double* points, do
  * tree nested and never raises Eq. 7.  stats may be NULL.  Synchronises. */
 obb_status obb_tree_sweep(obb_ctx* ctx, obb_tree* tree, const obb_sweep_opts* opts, obb_sweep_stats* stats);
 void obb_tree_free(obb_tree* tree);
+
+/* ------------------------------------------------------- batched layers */
+
+/* Many layers stepped together -- of many meshes, each on its own lattice, or
+ * several layers of one tree (Sec. 4.2.1 per layer, batched).  A batch holds
+ * borrowed layers of this context (each at most once; they must outlive the
+ * batch).  obb_batch_lloyd_step runs one Lloyd iteration of every layer: in
+ * each partition round the layers still moving run their kernels, and all
+ * their exact outer-volume counts go into one counting launch over all their
+ * lattices (a device-side gather of every layer's boxes, one multi-lattice
+ * count, a scatter back); the covariance refit of all layers likewise shares
+ * one counting launch; the rotation descent (refit mode bit 1) runs layer by
+ * layer.  Every layer's state and statistics equal those of obb_lloyd_step
+ * with the same options (opts->graph is ignored).  stats: [n] or NULL.
+ * Synchronises once per round. */
+obb_status obb_batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_batch** out);
+obb_status obb_batch_lloyd_step(obb_ctx* ctx, obb_batch* batch, const obb_step_opts* opts, obb_step_stats* stats);
+void obb_batch_free(obb_batch* batch);
 
 /* ---------------------------------------------------- learned surrogate (e) */
 

@@ -146,6 +146,8 @@ def load(build_if_missing: bool = True):
         "obb_layer_set_surrogate": [vp, vp, vp, i32],
         "obb_layer_last_candidates": [vp, vp, vp, vp, i64, C.POINTER(i64)],
         "obb_layer_moments": [vp, vp, i32, vp],
+        "obb_batch_create": [vp, vp, i32, C.POINTER(vp)],
+        "obb_batch_lloyd_step": [vp, vp, C.POINTER(StepOpts), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -154,7 +156,7 @@ def load(build_if_missing: bool = True):
     L.obb_mlp_num_params.argtypes = []
     L.obb_mlp_num_params.restype = C.c_int64
     for name in ("obb_destroy", "obb_mesh_free", "obb_lattice_free", "obb_layer_free", "obb_tree_free",
-                 "obb_mlp_free"):
+                 "obb_mlp_free", "obb_batch_free"):
         getattr(L, name).argtypes = [vp]
         getattr(L, name).restype = None
     L.obb_last_error.argtypes = [vp]
@@ -183,7 +185,8 @@ def exported_symbols():
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_surrogate_targets", "obb_mlp_forward", "obb_mlp_gradients",
             "obb_mlp_train_step",
-            "obb_layer_set_surrogate", "obb_layer_last_candidates", "obb_layer_moments"]
+            "obb_layer_set_surrogate", "obb_layer_last_candidates", "obb_layer_moments",
+            "obb_batch_create", "obb_batch_lloyd_step", "obb_batch_free"]
 
 
 def _is_torch(x):
@@ -492,6 +495,21 @@ class Context:
                                            boxes.ctypes.data_as(C.c_void_p), obv.ctypes.data_as(C.c_void_p), 0))
         return dict(assign=assign, frames=frames, qboxes=q, boxes=boxes, obv=obv)
 
+    def batch_create(self, layers):
+        """A batch of layers (of one or many meshes) stepped together."""
+        arr = (C.c_void_p * len(layers))(*[l.h.value for l in layers])
+        h = C.c_void_p()
+        self.check(self.lib.obb_batch_create(self.h, arr, len(layers), C.byref(h)))
+        return Batch(self, h, list(layers))
+
+    def batch_lloyd_step(self, batch, rounds=16, refit=True, descent_steps=0):
+        """One Lloyd iteration of every layer of the batch, each round's exact
+        counts of all layers in one counting launch; returns a list of stats."""
+        o = StepOpts(int(rounds), int(refit), int(descent_steps), 0)
+        st = (StepStats * len(batch.layers))()
+        self.check(self.lib.obb_batch_lloyd_step(self.h, batch.h, C.byref(o), st))
+        return [x.as_dict() for x in st]
+
     def layer_moments(self, layer, compensated=True):
         """Cluster moments float64 [K, 10] as the refit sums them (compensated
         FP32) or in plain FP32 (compensated=False)."""
@@ -720,6 +738,14 @@ class Layer(_Handle):
 
 class Mlp(_Handle):
     _free = "obb_mlp_free"
+
+
+class Batch(_Handle):
+    _free = "obb_batch_free"
+
+    def __init__(self, ctx, h, layers):
+        super().__init__(ctx, h)
+        self.layers = layers
 
 
 class Tree(_Handle):

@@ -139,6 +139,29 @@ struct CountScratch {
     int64_t cap = 0;
 };
 
+// A counting request recorded instead of launched while a batched step
+// collects the requests of many layers (obb_batch_lloyd_step): K = *d_K boxes
+// (at most K_cap) of one lattice into counts / points (points may be null).
+struct CountReq {
+    const ::obb_lattice* lat;
+    const obb_qbox* boxes;
+    const int32_t* d_K;
+    int64_t K_cap;
+    uint64_t* counts;
+    uint64_t* points;
+};
+
+// The same request as the flush kernels read it (device copy).
+struct BatchReq {
+    const obb_qbox* boxes;
+    const int32_t* d_K;
+    uint64_t* counts;
+    uint64_t* points;
+    int64_t cap;
+    int32_t lat;      // index into the flush's lattice table
+    int32_t pad;
+};
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -158,6 +181,7 @@ struct obb_ctx {
     int32_t* d_err = nullptr;        // device error word
     unsigned int* d_ticket = nullptr; // finish counter of the box-preparation blocks (zero between launches)
     const obbv::CountScratch* count_scratch = nullptr;   // set while a step is being captured
+    std::vector<obbv::CountReq>* count_defer = nullptr;  // set while a batched step collects counting requests
     int32_t tile_k = obbv::kTileK;   // rows per lane per counting tile
     int32_t count_axis = 0;          // row axis of counted boxes (0: x; -1: per box, the smallest shadow)
     int32_t count_rank = 1;          // long rows counted from their end words and the rank table (0: every word)
@@ -235,6 +259,14 @@ struct obb_layer {
     int32_t topk = 0;                // candidates kept per source cluster when screening
 };
 
+struct obb_batch {
+    obb_ctx* ctx = nullptr;
+    std::vector<obb_layer*> layers;
+    obbv::DevBuf tables, scratch;    // counting requests of a batched phase, and their gathered boxes
+    obbv::DevBuf stat_ptrs;          // the layers' device counters, then their accepted-move totals
+    int64_t* h_acc = nullptr;        // pinned host copy of the accepted-move totals
+};
+
 struct obb_tree {
     obb_ctx* ctx = nullptr;
     const obb_lattice* lat = nullptr;
@@ -284,6 +316,12 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
                              const obb_qbox* d_boxes, const int32_t* d_K, int64_t K_cap, uint64_t* d_counts,
                              uint64_t* d_points, int64_t lattice_bytes);
 obb_status set_device_int(obb_ctx* ctx, int32_t* d_dst, int32_t value);
+// Count the recorded requests in one multi-lattice launch: their boxes are
+// gathered into one list (device-side offsets from each request's box count),
+// counted, and the counts scattered back.  `tables` (device, held by the
+// caller) must hold at least reqs.size() BatchReq; `scratch` (device, held by
+// the caller) grows as needed.
+obb_status count_flush(obb_ctx* ctx, const std::vector<CountReq>& reqs, DevBuf& tables, DevBuf& scratch);
 // exclusive scan of n int32 values into out[n + 1] (out[n] = total), single block
 void launch_scan_i32(obb_ctx* ctx, const int32_t* in, int32_t* out, const int32_t* d_n);
 void launch_box_report(obb_ctx* ctx, const obb_lattice* lat, const double* d_frames, const obb_qbox* d_q,
@@ -301,6 +339,10 @@ obb_status layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox* out
                                  int64_t* n);
 // cluster moments [K][10] (host) summed as the refit sums them (compensated) or in plain FP32
 obb_status layer_moments(obb_ctx* ctx, obb_layer* L, int32_t compensated, double* out);
+// batched layers (obb_batch_*)
+obb_status batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_batch* B);
+void batch_destroy(obb_batch* B);
+obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opts, obb_step_stats* stats);
 // pieces of the Lloyd step that the step between levels (sweep.cu) reuses
 enum { kStProposals = 0, kStAccepted, kStGain, kStEvals, kStRefits, kStPoints, kStCount };
 obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dsteps);

@@ -1037,47 +1037,56 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     return OBB_OK;
 }
 
+// Phases of a step around its exact counts: a batched step runs every
+// layer's kPre part (which records its counting request), counts all the
+// requests in one launch, then runs every layer's kPost part.
+enum { kPre = 1, kPost = 2, kWhole = 3 };
+
 // One partition round (a6-a8) on ctx->stream, without host synchronisation.
-static obb_status round_body(obb_ctx* ctx, obb_layer* L)
+static obb_status round_body(obb_ctx* ctx, obb_layer* L, int phase = kWhole)
 {
     cudaStream_t s = ctx->stream;
     LayerMem* M = mem_of(L);
     const obb_lattice* lat = L->lat;
     const obb_mesh* mesh = lat->mesh;
     const int K = L->K;
-    k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, L->d_q, L->d_ext);
-    note_launch(ctx);
-    OBB_CK(ctx, cudaMemsetAsync(M->ctr, 0, sizeof(int32_t) * kCtrCount, s));
-    OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
-    k_candidates<<<(unsigned)((L->T + 127) / 128), 128, 0, s>>>(
-        lat->d_fixed, mesh->d_tris, mesh->d_adj, L->T, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
-        M->cand, M->evals, M->ctr, M->cand_cap, M->eval_cap, ctx->d_err);
-    note_launch(ctx);
-    const obb_qbox* evals = M->evals;
-    const int32_t* n_eval = M->ctr + kCtrEval;
-    if (L->mlp && L->topk > 0) {
-        // surrogate screening: predicted gains keep the top-k candidates of each
-        // source cluster; only their boxes are counted exactly
-        OBB_TRY(surrogate_predict(ctx, L->mlp, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->feats, M->pred));
-        const unsigned cb0 = (unsigned)((M->cand_cap + 127) / 128);
-        k_screen_score<<<cb0, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->pred, M->skey);
-        OBB_CK(ctx, cudaMemsetAsync(M->slot, 0, sizeof(unsigned long long) * kMaxTopk * K, s));
-        k_screen_insert<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, L->topk, M->slot);
-        OBB_CK(ctx, cudaMemsetAsync(M->n2, 0, sizeof(int32_t), s));
-        k_screen_compact<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->slot, L->topk, M->evals, M->evals2, M->n2);
-        note_launch(ctx, 3);
-        evals = M->evals2;
-        n_eval = M->n2;
+    const bool screened = L->mlp && L->topk > 0;
+    const obb_qbox* evals = screened ? M->evals2 : M->evals;
+    const int32_t* n_eval = screened ? M->n2 : M->ctr + kCtrEval;
+    if (phase & kPre) {
+        k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, L->d_q, L->d_ext);
+        note_launch(ctx);
+        OBB_CK(ctx, cudaMemsetAsync(M->ctr, 0, sizeof(int32_t) * kCtrCount, s));
+        OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
+        k_candidates<<<(unsigned)((L->T + 127) / 128), 128, 0, s>>>(
+            lat->d_fixed, mesh->d_tris, mesh->d_adj, L->T, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
+            M->cand, M->evals, M->ctr, M->cand_cap, M->eval_cap, ctx->d_err);
+        note_launch(ctx);
+        if (screened) {
+            // surrogate screening: predicted gains keep the top-k candidates of each
+            // source cluster; only their boxes are counted exactly
+            OBB_TRY(surrogate_predict(ctx, L->mlp, lat, M->evals, M->ctr + kCtrEval, M->eval_cap, M->feats, M->pred));
+            const unsigned cb0 = (unsigned)((M->cand_cap + 127) / 128);
+            k_screen_score<<<cb0, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->pred, M->skey);
+            OBB_CK(ctx, cudaMemsetAsync(M->slot, 0, sizeof(unsigned long long) * kMaxTopk * K, s));
+            k_screen_insert<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, L->topk, M->slot);
+            OBB_CK(ctx, cudaMemsetAsync(M->n2, 0, sizeof(int32_t), s));
+            k_screen_compact<<<cb0, 128, 0, s>>>(M->cand, M->ctr, M->skey, M->slot, L->topk, M->evals, M->evals2,
+                                                 M->n2);
+            note_launch(ctx, 3);
+        }
+        OBB_TRY(count_boxes(ctx, lat, evals, n_eval, M->eval_cap, M->ecount, M->epoints));
     }
-    OBB_TRY(count_boxes(ctx, lat, evals, n_eval, M->eval_cap, M->ecount, M->epoints));
-    k_sum_points<<<32, 256, 0, s>>>(M->epoints, n_eval, L->d_stats);
-    note_launch(ctx);
-    const unsigned cb = (unsigned)((M->cand_cap + 127) / 128);
-    k_gains<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->ecount, L->d_best, L->d_stats);
-    note_launch(ctx);
-    k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
-                                L->d_size, L->d_stats, M->dirty, M->level);
-    note_launch(ctx);
+    if (phase & kPost) {
+        k_sum_points<<<32, 256, 0, s>>>(M->epoints, n_eval, L->d_stats);
+        note_launch(ctx);
+        const unsigned cb = (unsigned)((M->cand_cap + 127) / 128);
+        k_gains<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->ecount, L->d_best, L->d_stats);
+        note_launch(ctx);
+        k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
+                                    L->d_size, L->d_stats, M->dirty, M->level);
+        note_launch(ctx);
+    }
     OBB_CK(ctx, cudaGetLastError());
     return OBB_OK;
 }
@@ -1277,20 +1286,17 @@ static obb_status lloyd_step_graph(obb_ctx* ctx, obb_layer* L, int rounds, int r
     return OBB_OK;
 }
 
-// Box update of a layer after its partition rounds (Sec. 4.2.1 step 2):
-// refit_mode bit 0 the covariance refit of the clusters whose membership
-// changed, bit 1 `dsteps` rotation-descent steps.  Adds to the layer's
-// device counters.
-obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dsteps)
+// Covariance refit (a9-a11) of the clusters whose membership changed (the
+// others would rebuild the frame they already tried and keep their box), in
+// the phases of a batched step.
+static obb_status refit_covariance(obb_ctx* ctx, obb_layer* L, int phase)
 {
     cudaStream_t s = ctx->stream;
     LayerMem* M = mem_of(L);
     const obb_lattice* lat = L->lat;
     const obb_mesh* mesh = lat->mesh;
     const int K = L->K;
-    if (refit_mode & 1) {
-        // covariance refit of the clusters whose membership changed (the others
-        // would rebuild the frame they already tried and keep their box)
+    if (phase & kPre) {
         if (!M->members_valid) OBB_TRY(rebuild_members(ctx, L));
         k_moments<kNT><<<K, kNT, 0, s>>>(mesh->d_verts, mesh->d_tris, L->d_members, L->d_start, lat->d_frame,
                                          M->mom, M->dirty);
@@ -1310,13 +1316,30 @@ obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dste
         k_dirty_compact<<<(K + 127) / 128, 128, 0, s>>>(M->dirty, screen, K, M->newq, M->evals2, M->map, M->n2);
         note_launch(ctx);
         OBB_TRY(count_boxes(ctx, lat, M->evals2, M->n2, K, M->ncount, M->epoints));
+    }
+    if (phase & kPost) {
         k_sum_points<<<32, 256, 0, s>>>(M->epoints, M->n2, L->d_stats);
         k_refit_accept_mapped<<<(K + 127) / 128, 128, 0, s>>>(M->newframe, M->newq, M->ncount, M->map, M->n2,
                                                               L->d_frames, L->d_q, L->d_obv, L->d_stats);
         note_launch(ctx, 2);
         OBB_CK(ctx, cudaMemsetAsync(M->dirty, 0, K, s));
-        OBB_CK(ctx, cudaGetLastError());
     }
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
+
+// Box update of a layer after its partition rounds (Sec. 4.2.1 step 2):
+// refit_mode bit 0 the covariance refit of the clusters whose membership
+// changed, bit 1 `dsteps` rotation-descent steps.  Adds to the layer's
+// device counters.
+obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dsteps)
+{
+    cudaStream_t s = ctx->stream;
+    LayerMem* M = mem_of(L);
+    const obb_lattice* lat = L->lat;
+    const obb_mesh* mesh = lat->mesh;
+    const int K = L->K;
+    if (refit_mode & 1) OBB_TRY(refit_covariance(ctx, L, kWhole));
     if (refit_mode & 2) {
         // box-parameter descent: six rotation probes per cluster per step, the
         // best kept when its exact outer volume is strictly smaller
@@ -1349,6 +1372,118 @@ obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dste
         OBB_CK(ctx, cudaGetLastError());
     }
     return OBB_OK;
+}
+
+// ------------------------------------------------------- batched layers
+
+namespace {
+__global__ void k_gather_accepted(int64_t* const* __restrict__ stats, int32_t n, int64_t* __restrict__ out)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = stats[i][kStAccepted];
+}
+
+// resets the context's request list on every path out of a collecting phase
+struct DeferGuard {
+    obb_ctx* ctx;
+    DeferGuard(obb_ctx* c, std::vector<CountReq>* reqs) : ctx(c) { ctx->count_defer = reqs; }
+    ~DeferGuard() { ctx->count_defer = nullptr; }
+};
+}  // namespace
+
+obb_status batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_batch* B)
+{
+    cudaStream_t s = ctx->stream;
+    B->ctx = ctx;
+    B->layers.assign(layers, layers + n);
+    std::vector<int64_t*> ptrs(n);
+    for (int32_t i = 0; i < n; ++i) ptrs[i] = layers[i]->d_stats;
+    OBB_CK(ctx, B->stat_ptrs.reserve(sizeof(int64_t*) * n + sizeof(int64_t) * n, s));
+    OBB_CK(ctx, cudaMemcpyAsync(B->stat_ptrs.p, ptrs.data(), sizeof(int64_t*) * n, cudaMemcpyHostToDevice, s));
+    OBB_CK(ctx, cudaMallocHost((void**)&B->h_acc, sizeof(int64_t) * n));
+    OBB_CK(ctx, cudaStreamSynchronize(s));
+    return OBB_OK;
+}
+
+void batch_destroy(obb_batch* B)
+{
+    if (!B) return;
+    cudaStream_t s = B->ctx ? B->ctx->stream : nullptr;
+    B->tables.release(s);
+    B->scratch.release(s);
+    B->stat_ptrs.release(s);
+    if (B->h_acc) cudaFreeHost(B->h_acc);
+    delete B;
+}
+
+// One Lloyd iteration of every layer of the batch: the partition rounds of
+// all layers still moving run together, each round's exact counts of all of
+// them in one counting launch (count_flush); then the covariance refit of all
+// layers, again with one counting launch; the rotation descent, when asked
+// for, runs layer by layer.  Each layer runs the same kernels in the same
+// order as obb_lloyd_step, so its state and statistics are the same.
+obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opts, obb_step_stats* stats)
+{
+    cudaStream_t s = ctx->stream;
+    const int32_t n = (int32_t)B->layers.size();
+    const int rounds = (opts && opts->rounds > 0) ? opts->rounds : 16;
+    const int refit_mode = opts ? opts->refit : 1;
+    const int dsteps = (opts && opts->descent_steps > 0) ? opts->descent_steps : 2;
+    std::vector<int64_t> before(n, 0);
+    std::vector<int> ran(n, 0);
+    std::vector<char> active(n, 1);
+    for (obb_layer* L : B->layers) OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
+    std::vector<CountReq> reqs;
+    int64_t* const* d_ptrs = B->stat_ptrs.as<int64_t*>();
+    int64_t* d_acc = reinterpret_cast<int64_t*>(B->stat_ptrs.as<char>() + sizeof(int64_t*) * n);
+    for (int r = 0; r < rounds; ++r) {
+        reqs.clear();
+        {
+            DeferGuard guard(ctx, &reqs);
+            for (int32_t i = 0; i < n; ++i) {
+                if (!active[i]) continue;
+                obb_layer* L = B->layers[i];
+                if (!mem_of(L)->members_valid) OBB_TRY(rebuild_members(ctx, L));
+                OBB_TRY(round_body(ctx, L, kPre));
+            }
+        }
+        OBB_TRY(count_flush(ctx, reqs, B->tables, B->scratch));
+        for (int32_t i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            OBB_TRY(round_body(ctx, B->layers[i], kPost));
+            ++ran[i];
+        }
+        k_gather_accepted<<<(n + 127) / 128, 128, 0, s>>>(d_ptrs, n, d_acc);
+        note_launch(ctx);
+        OBB_CK(ctx, cudaMemcpyAsync(B->h_acc, d_acc, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+        OBB_CK(ctx, cudaStreamSynchronize(s));
+        bool any = false;
+        for (int32_t i = 0; i < n; ++i) {
+            if (!active[i]) continue;
+            const int64_t moved = B->h_acc[i] - before[i];
+            before[i] = B->h_acc[i];
+            if (moved > 0) {
+                mem_of(B->layers[i])->members_valid = false;
+                any = true;
+            } else {
+                active[i] = 0;
+            }
+        }
+        if (!any) break;
+    }
+    if (refit_mode & 1) {
+        reqs.clear();
+        {
+            DeferGuard guard(ctx, &reqs);
+            for (obb_layer* L : B->layers) OBB_TRY(refit_covariance(ctx, L, kPre));
+        }
+        OBB_TRY(count_flush(ctx, reqs, B->tables, B->scratch));
+        for (obb_layer* L : B->layers) OBB_TRY(refit_covariance(ctx, L, kPost));
+    }
+    if (refit_mode & 2)
+        for (obb_layer* L : B->layers) OBB_TRY(layer_box_update(ctx, L, 2, dsteps));
+    for (int32_t i = 0; i < n; ++i) OBB_TRY(layer_finish_stats(ctx, B->layers[i], ran[i], stats ? &stats[i] : nullptr));
+    return check_device_error(ctx);
 }
 
 // Copies the layer's device counters and total outer volume into *st (if

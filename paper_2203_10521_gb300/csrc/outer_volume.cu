@@ -22,8 +22,11 @@
 //          [0, N)^3 are all empty.
 // Counts are integer sums (warp reduction + one 64-bit atomic per tile), so
 // the result does not depend on scheduling.
+#include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -467,6 +470,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
                 const uint32_t q = (uint32_t)min(max(c[a] * 16 / N, (int64_t)0), (int64_t)15);
                 for (int bit = 0; bit < 4; ++bit) key |= ((q >> bit) & 1u) << (3 * bit + a);
             }
+            if (n_lats > 1) {
+                // several lattices: lattice-major, each lattice's share of the
+                // buckets split by the top bits of the Morton cell
+                int sub = 0;
+                while (sub < 12 && (n_lats << (sub + 1)) <= kOrderBuckets) ++sub;
+                key = (uint32_t)(((int64_t)p.lat * kOrderBuckets) / n_lats) + (key >> (12 - sub));
+                key = min(key, (uint32_t)kOrderBuckets - 1);
+            }
             bucket[k] = key;
             atomicAdd(&hist[key], 1u);
         }
@@ -583,6 +594,73 @@ __global__ void __launch_bounds__(1024) k_order_scan(const int64_t* __restrict__
     if (t == 1023) {
         off[K] = part[1023];
         off[K + 1] = 0;
+    }
+}
+
+// ------------------------------------------------------- batched requests
+
+// off[r] = boxes of requests 0..r-1 (each request's count clamped to its
+// capacity), off[n] and *d_total = all of them; one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_batch_offsets(const BatchReq* __restrict__ reqs, int32_t n,
+                                                        int64_t* __restrict__ off, int32_t* __restrict__ d_total)
+{
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    const int32_t per = (n + 1023) / 1024;
+    const int32_t b0 = min(n, t * per), b1 = min(n, b0 + per);
+    int64_t sum = 0;
+    for (int32_t r = b0; r < b1; ++r) sum += min((int64_t)max(*reqs[r].d_K, 0), reqs[r].cap);
+    part[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int64_t v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int64_t run = part[t] - sum;
+    for (int32_t r = b0; r < b1; ++r) {
+        off[r] = run;
+        run += min((int64_t)max(*reqs[r].d_K, 0), reqs[r].cap);
+    }
+    if (t == 1023) {
+        off[n] = part[1023];
+        *d_total = (int32_t)part[1023];
+    }
+}
+
+// the request of combined position j: the last r with off[r] <= j
+__device__ __forceinline__ int32_t batch_request(const int64_t* __restrict__ off, int32_t n, int64_t j)
+{
+    int32_t lo = 0, hi = n;   // off[lo] <= j < off[hi]
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_batch_gather(const BatchReq* __restrict__ reqs, int32_t n, const int64_t* __restrict__ off,
+                               obb_qbox* __restrict__ boxes, int32_t* __restrict__ lat_of_box)
+{
+    const int64_t total = off[n];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = batch_request(off, n, j);
+        boxes[j] = reqs[r].boxes[j - off[r]];
+        lat_of_box[j] = reqs[r].lat;
+    }
+}
+
+__global__ void k_batch_scatter(const BatchReq* __restrict__ reqs, int32_t n, const int64_t* __restrict__ off,
+                                const uint64_t* __restrict__ counts, const uint64_t* __restrict__ points)
+{
+    const int64_t total = off[n];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = batch_request(off, n, j);
+        const int64_t i = j - off[r];
+        reqs[r].counts[i] = counts[j];
+        if (reqs[r].points) reqs[r].points[i] = points[j];
     }
 }
 
@@ -1167,6 +1245,11 @@ static int count_grid(obb_ctx* ctx)
 obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes, const int32_t* d_K,
                        int64_t K_cap, uint64_t* d_counts, uint64_t* d_points)
 {
+    if (ctx->count_defer) {
+        // a batched step counts every layer's requests together (count_flush)
+        ctx->count_defer->push_back(CountReq{lat, d_boxes, d_K, K_cap, d_counts, d_points});
+        return OBB_OK;
+    }
     return count_boxes_multi(ctx, lat->d_ref, 1, nullptr, d_boxes, d_K, K_cap, d_counts, d_points,
                              (int64_t)lat->n_words * 8);
 }
@@ -1238,6 +1321,69 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
         OBB_CK(ctx, cudaEventRecord(e1, s));
         ctx->prof_ev.emplace_back(e0, e1);
     }
+    OBB_CK(ctx, cudaGetLastError());
+    return OBB_OK;
+}
+
+obb_status count_flush(obb_ctx* ctx, const std::vector<CountReq>& reqs, DevBuf& tables, DevBuf& scratch)
+{
+    cudaStream_t s = ctx->stream;
+    const int32_t n = (int32_t)reqs.size();
+    if (n == 0) return OBB_OK;
+    if (n > (1 << 20)) return fail(ctx, OBB_ERR_RANGE, "too many counting requests in one batch");
+    // lattice table and request table (host), uploaded into `tables`
+    std::vector<const obb_lattice*> lats;
+    std::vector<BatchReq> hreq(n);
+    int64_t cap = 0, lattice_bytes = 0;
+    for (int32_t r = 0; r < n; ++r) {
+        const CountReq& q = reqs[r];
+        int32_t li = 0;
+        while (li < (int32_t)lats.size() && lats[li] != q.lat) ++li;
+        if (li == (int32_t)lats.size()) {
+            lats.push_back(q.lat);
+            lattice_bytes += (int64_t)q.lat->n_words * 8;
+        }
+        hreq[r] = BatchReq{q.boxes, q.d_K, q.counts, q.points, q.K_cap, li, 0};
+        cap += q.K_cap;
+    }
+    if (cap > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_RANGE, "too many boxes in one batch");
+    const size_t req_bytes = (sizeof(BatchReq) * n + 255) / 256 * 256;
+    const size_t lat_bytes = (sizeof(LatRef) * lats.size() + 255) / 256 * 256;
+    OBB_CK(ctx, tables.reserve(req_bytes + lat_bytes, s));
+    BatchReq* d_req = tables.as<BatchReq>();
+    LatRef* d_lat = reinterpret_cast<LatRef*>(tables.as<char>() + req_bytes);
+    std::vector<LatRef> hlat(lats.size());
+    for (size_t i = 0; i < lats.size(); ++i) hlat[i] = lats[i]->ref;
+    // pinned staging keeps the copies asynchronous (the tables are small)
+    void* h = nullptr;
+    OBB_CK(ctx, cudaMallocHost(&h, req_bytes + lat_bytes));
+    memcpy(h, hreq.data(), sizeof(BatchReq) * n);
+    memcpy(static_cast<char*>(h) + req_bytes, hlat.data(), sizeof(LatRef) * hlat.size());
+    cudaError_t e = cudaMemcpyAsync(d_req, h, req_bytes + lat_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the staging is freed below
+    cudaFreeHost(h);
+    OBB_CK(ctx, e);
+    // combined scratch: offsets [n + 1], total, boxes [cap], lattice of box [cap], counts and points [cap]
+    const size_t off_b = (sizeof(int64_t) * (n + 1) + 255) / 256 * 256;
+    const size_t box_b = (sizeof(obb_qbox) * cap + 255) / 256 * 256;
+    const size_t li_b = (sizeof(int32_t) * cap + 255) / 256 * 256;
+    const size_t cnt_b = (sizeof(uint64_t) * cap + 255) / 256 * 256;
+    OBB_CK(ctx, scratch.reserve(off_b + 256 + box_b + li_b + 2 * cnt_b, s));
+    char* b = scratch.as<char>();
+    int64_t* off = reinterpret_cast<int64_t*>(b);
+    int32_t* d_total = reinterpret_cast<int32_t*>(b + off_b);
+    obb_qbox* boxes = reinterpret_cast<obb_qbox*>(b + off_b + 256);
+    int32_t* lat_of_box = reinterpret_cast<int32_t*>(b + off_b + 256 + box_b);
+    uint64_t* counts = reinterpret_cast<uint64_t*>(b + off_b + 256 + box_b + li_b);
+    uint64_t* points = counts + cnt_b / sizeof(uint64_t);
+    k_batch_offsets<<<1, 1024, 0, s>>>(d_req, n, off, d_total);
+    const unsigned gb = (unsigned)std::min<int64_t>((cap + 255) / 256, 4 * (int64_t)ctx->num_sms);
+    k_batch_gather<<<std::max(gb, 1u), 256, 0, s>>>(d_req, n, off, boxes, lat_of_box);
+    note_launch(ctx, 2);
+    OBB_TRY(count_boxes_multi(ctx, d_lat, (int32_t)lats.size(), lat_of_box, boxes, d_total, cap, counts, points,
+                              lattice_bytes));
+    k_batch_scatter<<<std::max(gb, 1u), 256, 0, s>>>(d_req, n, off, counts, points);
+    note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return OBB_OK;
 }

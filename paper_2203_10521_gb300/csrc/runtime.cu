@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <unordered_set>
+
 #include "internal.h"
 
 namespace obbv {
@@ -661,6 +663,37 @@ obb_status obb_layer_moments(obb_ctx* ctx, obb_layer* L, int32_t compensated, do
 }
 
 void obb_layer_free(obb_layer* L) { layer_destroy(L); }
+
+obb_status obb_batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_batch** out)
+{
+    if (!ctx || !layers || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (n < 1 || n > (1 << 20)) return fail(ctx, OBB_ERR_ARG, "a batch holds 1 to 2^20 layers");
+    std::unordered_set<const obb_layer*> seen;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!layers[i]) return fail(ctx, OBB_ERR_ARG, "null layer in the batch");
+        if (layers[i]->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
+        if (!seen.insert(layers[i]).second) return fail(ctx, OBB_ERR_ARG, "a layer appears twice in the batch");
+    }
+    obb_batch* B = new (std::nothrow) obb_batch();
+    if (!B) return fail(ctx, OBB_ERR_OOM, "batch");
+    obb_status st = batch_create(ctx, layers, n, B);
+    if (st != OBB_OK) {
+        batch_destroy(B);
+        return st;
+    }
+    *out = B;
+    return OBB_OK;
+}
+
+obb_status obb_batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opts, obb_step_stats* stats)
+{
+    if (!ctx || !B) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (B->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "batch belongs to another context");
+    return batch_lloyd_step(ctx, B, opts, stats);
+}
+
+void obb_batch_free(obb_batch* B) { batch_destroy(B); }
 
 obb_status obb_layer_split(obb_ctx* ctx, const obb_layer* L, int32_t* child, int32_t on_device)
 {
