@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--surrogate-pairs", type=int, default=2_000_000,
                     help="training pairs generated on the 202,244-triangle union at 512^3")
     ap.add_argument("--surrogate-steps", type=int, default=2000, help="Adam steps of surrogate training")
+    ap.add_argument("--batch-meshes", type=int, default=256, help="meshes of the batched Lloyd comparison (0: skip)")
+    ap.add_argument("--batch-iters", type=int, default=3, help="Lloyd iterations timed in the batched comparison")
     ap.add_argument("--no-second-workload", action="store_true",
                     help="skip the plain vs surrogate comparison on the 1M-triangle union at 768^3")
     ap.add_argument("--walk", action="store_true", help="count every row word by word (no rank tables)")
@@ -454,6 +456,86 @@ def lloyd_on_workload(ctx, key, args, flush, stream, mlp):
     return out
 
 
+def batch_depths(meshes, seed):
+    """Tree depth per mesh of the batched workload: log-uniform in 6..9 and at
+    most log2(T / 16)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for m, _ in meshes:
+        d = int(np.floor(np.exp(rng.uniform(np.log(6), np.log(10)))))
+        out.append(max(2, min(d, int(np.log2(m.n_tris / 16)))))
+    return out
+
+
+def batched_lloyd(ctx, args, flush, stream):
+    """The batched workload: seeded SDF unions of uneven size (about 1k to
+    185k triangles, lattices 128^3 to 384^3, depths 6 to 9), the leaf level of
+    each freshly split from its parent level; Lloyd iterations (covariance
+    refit) of all of them as one batch -- every round's exact counts of all
+    meshes in one counting launch -- against the same iterations mesh by mesh,
+    from identical states."""
+    import torch
+    from synth import meshes as M
+    t0 = time.perf_counter()
+    meshes = M.sdf_batch(args.batch_meshes, seed=3000)
+    depths = batch_depths(meshes, 31)
+    objs, A, B = [], [], []
+    for (m, N), d in zip(meshes, depths):
+        mesh = ctx.mesh_create(m.verts, m.tris)
+        lat = ctx.build_occupancy(mesh, N)
+        tree = ctx.build_tree(lat, d - 1, 1)
+        up = ctx.tree_read(tree, d - 1)
+        Kp = 1 << (d - 1)
+        up_layer = ctx.layer_init(lat, up["assign"], (np.arange(Kp) // 2).astype(np.int32), up["frames"])
+        child = ctx.layer_split(up_layer)
+        up_layer.free()
+        tree.free()
+        parent = (np.arange(2 * Kp) // 2).astype(np.int32)
+        A.append(ctx.layer_init(lat, child, parent))
+        B.append(ctx.layer_init(lat, child, parent))
+        objs.append((mesh, lat))
+    batch = ctx.batch_create(A)
+    setup_s = time.perf_counter() - t0
+    res = {}
+    for mode in ("batched", "per_mesh"):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        ctx.profile_enable(2)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        moves = 0
+        for _ in range(args.batch_iters):
+            if mode == "batched":
+                st = ctx.batch_lloyd_step(batch, rounds=16, refit=1)
+            else:
+                st = [ctx.lloyd_step(L, rounds=16, refit=1) for L in B]
+            moves += sum(x["moves"] for x in st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pr = ctx.profile_read()
+        ctx.profile_enable(0)
+        sec = e0.elapsed_time(e1) / 1000.0
+        res[mode] = {"iter_per_s": args.batch_iters / sec, "points_per_s": pr["count_points_in_domain"] / sec,
+                     "counting_launches_per_iter": pr["count_launches"] / args.batch_iters, "moves": int(moves),
+                     "final_total_obv": int(sum(x["total_obv"] for x in st))}
+    same = all(np.array_equal(ctx.layer_read(a)["obv"], ctx.layer_read(b)["obv"]) for a, b in zip(A, B))
+    out = {"meshes": len(meshes), "triangles": int(sum(m.n_tris for m, _ in meshes)),
+           "triangles_range": [int(min(m.n_tris for m, _ in meshes)), int(max(m.n_tris for m, _ in meshes))],
+           "lattices": sorted({int(N) for _, N in meshes}), "depths": sorted(set(depths)),
+           "leaves": int(sum(1 << d for d in depths)), "iters": args.batch_iters, "setup_s": setup_s,
+           "batched": res["batched"], "per_mesh": res["per_mesh"],
+           "speedup": res["batched"]["iter_per_s"] / res["per_mesh"]["iter_per_s"],
+           "identical_results": bool(same)}
+    batch.free()
+    for L in A + B:
+        L.free()
+    for mesh, lat in objs:
+        lat.free()
+        mesh.free()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -567,6 +649,7 @@ def main():
         lloyd_other = lloyd_on_workload(ctx, "sdf1m-768", args, flush, stream, mlp)
     if mlp is not None:
         mlp.free()
+    batched = batched_lloyd(ctx, args, flush, stream) if args.batch_meshes > 0 else None
 
     # roofline of the counting kernel: algorithmic bytes of the batch launch
     # over its event-timed duration in the timed region
@@ -658,7 +741,7 @@ def main():
                "lloyd_graph_iter_per_s": lloyd["plain_graph"]["iter_per_s"],
                "surrogate_lloyd_iter_per_s": lloyd["surrogate"]["iter_per_s"] if "surrogate" in lloyd else None,
                "lloyd_comparison": lloyd, "lloyd_comparison_1m_768": lloyd_other,
-               "surrogate_training": training, "lloyd_last_step": last,
+               "surrogate_training": training, "batched_lloyd": batched, "lloyd_last_step": last,
                "setup": {"tree_s": tree_s, "sweeps": sweep}, "wall_s_timed": wall}
         print(json.dumps(out), flush=True)
     layer.free()
