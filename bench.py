@@ -362,6 +362,7 @@ def profile_batch(args):
         boxes = tree_boxes(ctx, tree, wl["depth"])
         np.save(path, boxes)
         tree.free()
+    ctx.tune_counting(lat, ctx.quantize_boxes(lat, boxes))   # the tile height the benchmark runs with
     d = torch.from_numpy(boxes).cuda()
     c = ctx.outer_volume(lat, d)
     torch.cuda.nvtx.range_push("profile_batch")
