@@ -25,6 +25,7 @@ constexpr int64_t kBoxRange = int64_t(1) << 20;  // |index-space AABB| limit of 
 #endif
 constexpr int kTileK = OBB_TILE_K;               // rows along z one lane steps through per tile
 constexpr int kOrderBuckets = 4096;              // spatial-order buckets of a counting launch (16^3 Morton cells)
+constexpr int kScanBlock = 2048;                 // positions per block of the counting path's two-pass offset scan
 
 #ifdef __CUDACC__
 // Integer -> FP32 through 32-bit conversions (relative error below 3 * 2^-24,
@@ -64,7 +65,8 @@ struct LatticeFrame {
     double lo[3];
     double h[3];
     double hmax;
-    double center[3];   // lo + N h / 2, origin of the covariance moments
+    double center[3];   // lo + N h / 2
+    double inv_h[3];    // 1 / h, correctly rounded (the snap's fast path)
     int32_t N;
     int32_t W;          // uint64 words per row (even)
 };
@@ -130,12 +132,12 @@ struct LatRef {
 
 // Stream-ordered device allocation that only grows.
 // Scratch of the counting path at fixed addresses (used while a step is
-// captured into a CUDA graph): prep [cap], tiles + offsets [2 cap + 2], and a
-// zero-initialised ticket.
+// captured into a CUDA graph): prep [cap], tiles + offsets [2 cap + 2] and
+// the offset scan's block totals.
 struct CountScratch {
     BoxPrep* prep = nullptr;
     int64_t* tiles = nullptr;
-    unsigned int* ticket = nullptr;
+    int64_t* bsum = nullptr;          // [cap / kScanBlock + 1] block totals of the offset scan
     int64_t cap = 0;
 };
 

@@ -1147,14 +1147,13 @@ static obb_status lloyd_step_graph(obb_ctx* ctx, obb_layer* L, int rounds, int r
         if (!M->cscr_mem) {
             const int64_t cap = std::max<int64_t>({(int64_t)M->eval_cap, (int64_t)kProbes * K, (int64_t)K});
             const size_t pb = (sizeof(BoxPrep) * cap + 255) / 256 * 256;
-            const size_t tb = (sizeof(int64_t) * (2 * cap + 2) + 255) / 256 * 256;
-            OBB_CK(ctx, cudaMallocAsync(&M->cscr_mem, pb + tb + 256, s));
+            const size_t tb = sizeof(int64_t) * (2 * cap + 2 + cap / kScanBlock + 1);
+            OBB_CK(ctx, cudaMallocAsync(&M->cscr_mem, pb + tb, s));
             char* b = static_cast<char*>(M->cscr_mem);
             M->cscr.prep = reinterpret_cast<BoxPrep*>(b);
             M->cscr.tiles = reinterpret_cast<int64_t*>(b + pb);
-            M->cscr.ticket = reinterpret_cast<unsigned int*>(b + pb + tb);
+            M->cscr.bsum = M->cscr.tiles + 2 * cap + 2;
             M->cscr.cap = cap;
-            OBB_CK(ctx, cudaMemsetAsync(M->cscr.ticket, 0, sizeof(unsigned int), s));
         }
         OBB_CK(ctx, cudaStreamSynchronize(s));
         cudaStream_t cs[3] = {nullptr, nullptr, nullptr};

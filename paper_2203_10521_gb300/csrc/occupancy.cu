@@ -80,21 +80,33 @@ __global__ void k_frame(const uint32_t* keys, int32_t N, LatticeFrame* f, int32_
         hm = fmax(hm, h);
     }
     f->hmax = hm;
-    for (int b = 0; b < 3; ++b) f->center[b] = __dadd_rn(f->lo[b], __dmul_rn(0.5 * N, f->h[b]));
+    for (int b = 0; b < 3; ++b) {
+        f->center[b] = __dadd_rn(f->lo[b], __dmul_rn(0.5 * N, f->h[b]));
+        f->inv_h[b] = f->h[b] > 0.0 ? __drcp_rn(f->h[b]) : 0.0;
+    }
     f->N = N;
     f->W = 2 * ((N + 127) / 128);
 }
 
+// U = rint(((x - lo) / h - 1/2) 256), each step a correctly rounded FP64 op.
+// The quotient through the reciprocal, d (1/h), is within 2 ulps of d / h,
+// so (q - 1/2) 256 moves by less than 2^-30 (q < 2^12): whenever that value
+// lies farther than 2^-29 from a half-integer both round to the same integer;
+// otherwise the defining sequence, with the division, decides.
 __global__ void k_snap(const float* __restrict__ V, int64_t nv, const LatticeFrame* __restrict__ f,
                        int32_t* __restrict__ U)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= 3 * nv) return;
     int b = (int)(i % 3);
-    double d = __dsub_rn((double)V[i], f->lo[b]);
-    double q = __ddiv_rn(d, f->h[b]);
-    q = __dsub_rn(q, 0.5);
-    q = __dmul_rn(q, 256.0);
+    const double d = __dsub_rn((double)V[i], f->lo[b]);
+    double q = __dmul_rn(__dsub_rn(__dmul_rn(d, f->inv_h[b]), 0.5), 256.0);
+    const double t = q - floor(q);   // exact
+    if (!(fabs(t - 0.5) > 0x1p-29) || !(fabs(q) < 0x1p30)) {
+        q = __ddiv_rn(d, f->h[b]);
+        q = __dsub_rn(q, 0.5);
+        q = __dmul_rn(q, 256.0);
+    }
     U[i] = (int32_t)rint(q);
 }
 

@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
                                                        unsigned long long* __restrict__ points,
                                                        unsigned int* __restrict__ ticket,
                                                        uint32_t* __restrict__ bucket, unsigned int* __restrict__ hist,
-                                                       int32_t* err)
+                                                       int32_t scan_tiles, int32_t* err)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int32_t K = *d_K;
@@ -482,6 +482,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
             atomicAdd(&hist[key], 1u);
         }
     }
+    // the last block's work: the spatial order's bucket starts, or (scan_tiles)
+    // the tile offsets in the caller's order; otherwise the offsets come from
+    // k_tile_sums / k_tile_offsets
+    if (!bucket && !scan_tiles) return;
     // the block's writes, then one gpu-scope fence before its ticket
     __shared__ bool last;
     __syncthreads();
@@ -494,8 +498,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
     if (!last) return;
     if (bucket) {
         // spatial order: the bucket counts become bucket starts (exclusive
-        // scan, one warp, 128 buckets a lane); k_order_scatter and
-        // k_order_scan follow
+        // scan, one warp, 128 buckets a lane); k_order_scatter,
+        // k_tile_sums and k_tile_offsets follow
         const int lane = threadIdx.x & 31;
         constexpr int per = kOrderBuckets / 32;
         unsigned int run = 0;
@@ -552,47 +556,104 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(const obb_qbox* __restric
 
 // ---------------------------------------------------------- spatial order
 
-// perm[start of the box's bucket + its place] = box (the place within a
-// bucket depends on scheduling; counts do not depend on the order)
-__global__ void k_order_scatter(const uint32_t* __restrict__ bucket, const int32_t* __restrict__ d_K,
-                                unsigned int* __restrict__ hist, int32_t* __restrict__ perm)
+// perm[start of the box's bucket + its place] = box, and the box's tile count
+// at the same place (the place within a bucket depends on scheduling; counts
+// do not depend on the order)
+__global__ void k_order_scatter(const uint32_t* __restrict__ bucket, const int64_t* __restrict__ tiles,
+                                const int32_t* __restrict__ d_K, unsigned int* __restrict__ hist,
+                                int32_t* __restrict__ perm, int64_t* __restrict__ ptiles)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int32_t K = *d_K;
     if (k >= K) return;
     const unsigned int pos = atomicAdd(&hist[bucket[k]], 1u);
-    if (pos < (unsigned int)K) perm[pos] = (int32_t)k;
+    if (pos < (unsigned int)K) {
+        perm[pos] = (int32_t)k;
+        ptiles[pos] = tiles[k];
+    }
 }
 
-// off[i] = tiles of boxes perm[0..i-1] (one block of 1024 threads, each a
-// contiguous run of positions); off[K] = all tiles, off[K + 1] = 0 (the
-// counting kernel's work counter)
-__global__ void __launch_bounds__(1024) k_order_scan(const int64_t* __restrict__ tiles,
-                                                     const int32_t* __restrict__ perm,
-                                                     const int32_t* __restrict__ d_K, int64_t* __restrict__ off)
+// ---------------------------------------------------------- tile offsets
+
+// Tile offsets in counting order (the boxes' own, or the spatial order's
+// permuted copy), in two passes over blocks of 2,048
+// positions (256 threads, 8 consecutive positions each): k_tile_sums writes
+// each block's total; k_tile_offsets adds up the totals of the blocks before
+// its own and scans its positions.  off[i] = tiles of the boxes at positions
+// 0..i-1, off[K] = all tiles, off[K + 1] = 0 (the counting kernel's work
+// counter).
+constexpr int kScanPer = 8;
+static_assert(256 * kScanPer == kScanBlock, "offset scan: 256 threads x kScanPer positions per block");
+
+__global__ void __launch_bounds__(256) k_tile_sums(const int64_t* __restrict__ tiles,
+                                                    const int32_t* __restrict__ d_K, int64_t* __restrict__ bsum)
 {
-    __shared__ int64_t part[1024];
+    __shared__ int64_t ws[8];
     const int32_t K = *d_K;
-    const int t = threadIdx.x;
-    const int32_t per = (K + 1023) / 1024;
-    const int32_t b0 = min(K, t * per), b1 = min(K, b0 + per);
-    int64_t sum = 0;
-    for (int32_t i = b0; i < b1; ++i) sum += tiles[perm[i]];
-    part[t] = sum;
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+    int64_t v = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) v += base + q < K ? tiles[base + q] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const int64_t v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < 8; ++w) t += ws[w];
+        bsum[blockIdx.x] = t;
     }
-    int64_t run = part[t] - sum;
-    for (int32_t i = b0; i < b1; ++i) {
-        off[i] = run;
-        run += tiles[perm[i]];
+}
+
+__global__ void __launch_bounds__(256) k_tile_offsets(const int64_t* __restrict__ tiles,
+                                                       const int64_t* __restrict__ bsum,
+                                                       const int32_t* __restrict__ d_K, int64_t* __restrict__ off)
+{
+    __shared__ int64_t ws[8];
+    __shared__ int64_t before;
+    const int32_t K = *d_K;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // the totals of the blocks before this one
+    int64_t p = 0;
+    for (int32_t b = threadIdx.x; b < (int32_t)blockIdx.x; b += 256) p += bsum[b];
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    if (lane == 0) ws[w] = p;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int i = 0; i < 8; ++i) t += ws[i];
+        before = t;
     }
-    if (t == 1023) {
-        off[K] = part[1023];
+    __syncthreads();
+    // this block's positions: a thread's eight in registers, then an exclusive
+    // scan of the thread sums (warp shuffles, then across the 8 warps)
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+    int64_t v[kScanPer];
+    int64_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        v[q] = base + q < K ? tiles[base + q] : 0;
+        sum += v[q];
+    }
+    int64_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();   // ws is reused
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    int64_t wbefore = 0;
+    for (int i = 0; i < w; ++i) wbefore += ws[i];
+    int64_t run = before + wbefore + x - sum;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        if (base + q < K) off[base + q] = run;
+        run += v[q];
+    }
+    // positions past K hold 0, so the thread whose eight positions include K
+    // ends with run = off[K] (the launch has K_cap / 2048 + 1 blocks, so it exists)
+    if (base <= K && K < base + kScanPer) {
+        off[K] = run;
         off[K + 1] = 0;
     }
 }
@@ -1266,6 +1327,7 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
     unsigned int* ticket = ctx->d_ticket;
     uint32_t* bucket = nullptr;
     int32_t* perm = nullptr;
+    int64_t *ptiles = nullptr, *bsum = nullptr;
     if (ctx->count_scratch) {
         // fixed scratch of a step being captured into a graph: its addresses must not move
         const CountScratch& cs = *ctx->count_scratch;
@@ -1273,19 +1335,22 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
         prep = cs.prep;
         tiles = cs.tiles;
         off = cs.tiles + cs.cap;
-        ticket = cs.ticket;
+        bsum = cs.bsum;
     } else {
+        const int64_t nb = K_cap / kScanBlock + 1;
         OBB_CK(ctx, ctx->prep.reserve(sizeof(BoxPrep) * K_cap, s));
-        OBB_CK(ctx, ctx->chunk_off.reserve(sizeof(int64_t) * (2 * K_cap + 2), s));
+        OBB_CK(ctx, ctx->chunk_off.reserve(sizeof(int64_t) * (2 * K_cap + 2 + nb), s));
         prep = ctx->prep.as<BoxPrep>();
         tiles = ctx->chunk_off.as<int64_t>();
         off = tiles + K_cap;
+        bsum = off + K_cap + 2;
         if (ctx->count_order && K_cap >= kOrderMinBoxes && lattice_bytes >= kOrderMinLatticeBytes) {
             // large batches on lattices too large for L2 are counted in
             // spatial order (boxes of every size over one region together, so
             // the region's lattice words are reused from L2)
-            OBB_CK(ctx, ctx->order.reserve(2 * sizeof(int32_t) * K_cap, s));
-            bucket = ctx->order.as<uint32_t>();
+            OBB_CK(ctx, ctx->order.reserve((2 * sizeof(int32_t) + sizeof(int64_t)) * K_cap, s));
+            ptiles = reinterpret_cast<int64_t*>(ctx->order.as<char>());
+            bucket = reinterpret_cast<uint32_t*>(ptiles + K_cap);
             perm = reinterpret_cast<int32_t*>(bucket + K_cap);
             OBB_CK(ctx, cudaMemsetAsync(ctx->d_order_hist, 0, kOrderBuckets * sizeof(unsigned int), s));
         }
@@ -1294,14 +1359,21 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
     k_prep<<<(unsigned)((K_cap + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
         d_boxes, d_K, d_lats, n_lats, d_lat_of_box, ctx->tile_k, ctx->count_axis, ctx->count_rank, prep, tiles, off,
         reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
-        bucket, bucket ? ctx->d_order_hist : nullptr, ctx->d_err);
+        bucket, bucket ? ctx->d_order_hist : nullptr, 0, ctx->d_err);
     note_launch(ctx);
+    // tile offsets: an exclusive scan of the tile counts in counting order
+    // (the spatial order's permuted copy, else the boxes' own order)
+    const int64_t* scan_in = tiles;
     if (perm) {
-        k_order_scatter<<<(unsigned)((K_cap + 255) / 256), 256, 0, s>>>(bucket, d_K, ctx->d_order_hist, perm);
-        k_order_scan<<<1, 1024, 0, s>>>(tiles, perm, d_K, off);
-        note_launch(ctx, 2);
+        k_order_scatter<<<(unsigned)((K_cap + 255) / 256), 256, 0, s>>>(bucket, tiles, d_K, ctx->d_order_hist, perm,
+                                                                      ptiles);
+        note_launch(ctx);
+        scan_in = ptiles;
     }
-    note_launch(ctx);
+    const unsigned nsb = (unsigned)(K_cap / kScanBlock + 1);
+    k_tile_sums<<<nsb, 256, 0, s>>>(scan_in, d_K, bsum);
+    k_tile_offsets<<<nsb, 256, 0, s>>>(scan_in, bsum, d_K, off);
+    note_launch(ctx, 2);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->prof) {
         OBB_CK(ctx, cudaEventCreate(&e0));
@@ -1473,7 +1545,7 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
     k_prep<<<(unsigned)((K + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
         d_boxes, dK, lat->d_ref, 1, nullptr, ctx->tile_k, ctx->count_axis, ctx->count_rank, prep, chunks, off,
         reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
-        nullptr, nullptr, ctx->d_err);
+        nullptr, nullptr, 1, ctx->d_err);
     note_launch(ctx);
     k_count<false><<<count_grid(ctx), 256, 0, s>>>(prep, off, dK, reinterpret_cast<unsigned long long*>(d_counts),
                                                    reinterpret_cast<unsigned long long*>(d_points), nullptr, nullptr,
