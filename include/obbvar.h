@@ -374,6 +374,15 @@ obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* layer, int32_t* assign,
 obb_status obb_layer_moments(obb_ctx* ctx, obb_layer* layer, int32_t compensated, double* out);
 int32_t obb_layer_clusters(const obb_layer* layer);
 
+/* The layer's member lists, the order every per-cluster reduction of the
+ * Lloyd step (Sec. 4.2.1: extents, covariance sums, tight bounds) walks:
+ * members int32 [n_tris] = the triangles sorted by cluster, ascending
+ * triangle index within a cluster (a stable sort of the assignment);
+ * start int32 [K + 1] = where each cluster's triangles begin (start[K] =
+ * n_tris).  Host arrays; either may be NULL.  Rebuilt first if the
+ * assignment changed since the last rebuild.  Synchronises. */
+obb_status obb_layer_members(obb_ctx* ctx, obb_layer* layer, int32_t* members, int32_t* start);
+
 typedef struct {
     int32_t waves;       /* flooding waves run */
     int32_t reserved;

@@ -146,6 +146,7 @@ def load(build_if_missing: bool = True):
         "obb_layer_set_surrogate": [vp, vp, vp, i32],
         "obb_layer_last_candidates": [vp, vp, vp, vp, i64, C.POINTER(i64)],
         "obb_layer_moments": [vp, vp, i32, vp],
+        "obb_layer_members": [vp, vp, vp, vp],
         "obb_batch_create": [vp, vp, i32, C.POINTER(vp)],
         "obb_batch_lloyd_step": [vp, vp, C.POINTER(StepOpts), vp],
     }
@@ -185,7 +186,7 @@ def exported_symbols():
             "obb_mlp_create", "obb_mlp_free", "obb_mlp_num_params", "obb_mlp_params", "obb_mlp_set_params",
             "obb_surrogate_features", "obb_surrogate_targets", "obb_mlp_forward", "obb_mlp_gradients",
             "obb_mlp_train_step",
-            "obb_layer_set_surrogate", "obb_layer_last_candidates", "obb_layer_moments",
+            "obb_layer_set_surrogate", "obb_layer_last_candidates", "obb_layer_moments", "obb_layer_members",
             "obb_batch_create", "obb_batch_lloyd_step", "obb_batch_free"]
 
 
@@ -517,6 +518,15 @@ class Context:
         self.check(self.lib.obb_layer_moments(self.h, layer.h, 1 if compensated else 0,
                                               out.ctypes.data_as(C.c_void_p)))
         return out
+
+    def layer_members(self, layer):
+        """Member lists: (members int32 [n_tris], triangles sorted by cluster,
+        ascending within a cluster; start int32 [K + 1])."""
+        members = np.zeros(layer.lat.mesh.nt, np.int32)
+        start = np.zeros(layer.K + 1, np.int32)
+        self.check(self.lib.obb_layer_members(self.h, layer.h, members.ctypes.data_as(C.c_void_p),
+                                              start.ctypes.data_as(C.c_void_p)))
+        return members, start
 
     def layer_split(self, layer):
         child = np.zeros(layer.lat.mesh.nt, np.int32)

@@ -22,8 +22,9 @@
 // Refit: area-weighted covariance with compensated FP32 sums (TwoProduct +
 // TwoSum), cyclic Jacobi in FP64, quantised normals, tight bounds, exact count;
 // the new box is kept iff its outer volume is strictly smaller.
-#include <cub/cub.cuh>
-
+// Member lists: a stable least-significant-digit radix sort of the triangles
+// by cluster (per-tile digit counts, their exclusive scan, a stable scatter
+// that ranks equal digits with warp matches in triangle order).
 #include <algorithm>
 
 #include "internal.h"
@@ -87,10 +88,240 @@ __global__ void k_check_nonempty(const int32_t* __restrict__ size, int32_t K, in
     if (k < K && size[k] == 0) atomicOr(err, kErrEmpty);
 }
 
-__global__ void k_iota(int32_t* p, int64_t n)
+// Member lists: triangles sorted by cluster, ascending triangle index within
+// a cluster.  Each pass of the radix sort orders the (cluster, triangle) pairs
+// stably by one digit of the cluster (at most 10 bits, lowest digit first),
+// over tiles of kSortTile consecutive positions:
+//   k_sort_count    digit counts of every tile, cnt[digit * ntiles + tile];
+//                   for a small table its last block (an atomic ticket,
+//                   nothing waits) also scans them;
+//   k_sort_sums /   otherwise the exclusive scan of cnt in that order, in two
+//   k_sort_offsets  passes: where each tile's items of each digit start;
+//   k_sort_scatter  the tile's items in order, rounds of 256: equal digits of
+//                   a warp ranked by __match_any_sync, warps after one another
+//                   per digit, rounds after one another.
+// The first pass takes the triangle index as its value; the last writes only
+// the values (the member list).  With one pass the digit is the cluster, so
+// the offsets of the first tile are the cluster starts.
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+constexpr int kSortMaxBits = 10;
+constexpr int kSortScanPer = 8;
+constexpr int kSortScanBlock = kSortThreads * kSortScanPer;
+constexpr int64_t kSortFusedScanMax = 8192;   // largest table the count kernel's last block scans
+
+__device__ __forceinline__ int sort_digit(int32_t key, int shift, int bins)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) p[i] = (int32_t)i;
+    return (int)(((uint32_t)key >> shift) & (uint32_t)(bins - 1));
+}
+
+// exclusive scan of in[0..n) into out by one block, chunks of kSortScanBlock
+// (a thread's eight consecutive values in registers), with a running carry
+__device__ void block_scan_i32(const int32_t* in, int64_t n, int32_t* out, int32_t* ws)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t carry = 0;
+    for (int64_t c = 0; c < n; c += kSortScanBlock) {
+        const int64_t base = c + threadIdx.x * kSortScanPer;
+        int32_t v[kSortScanPer];
+        int32_t sum = 0;
+#pragma unroll
+        for (int q = 0; q < kSortScanPer; ++q) {
+            v[q] = base + q < n ? __ldcg(in + base + q) : 0;
+            sum += v[q];
+        }
+        int32_t x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        int32_t run = carry + x - sum, tot = 0;
+        for (int i = 0; i < kSortThreads / 32; ++i) {
+            if (i < w) run += ws[i];
+            tot += ws[i];
+        }
+#pragma unroll
+        for (int q = 0; q < kSortScanPer; ++q) {
+            if (base + q < n) out[base + q] = run;
+            run += v[q];
+        }
+        carry += tot;
+        __syncthreads();   // ws is reused
+    }
+}
+
+// K > 0: keys outside [0, K) raise kErrArg.  scan_out != nullptr: the last
+// block to finish scans the counts into scan_out.
+__global__ void __launch_bounds__(kSortThreads) k_sort_count(const int32_t* __restrict__ keys, int64_t n, int shift,
+                                                             int bins, int32_t ntiles, int32_t K,
+                                                             int32_t* __restrict__ cnt, int32_t* __restrict__ scan_out,
+                                                             unsigned int* __restrict__ ticket, int32_t* err)
+{
+    extern __shared__ int32_t h[];   // [bins]
+    __shared__ int32_t ws[kSortThreads / 32];
+    __shared__ bool last;
+    for (int i = threadIdx.x; i < bins; i += kSortThreads) h[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t i = base + r * kSortThreads + threadIdx.x;
+        int d = -1;
+        if (i < n) {
+            const int32_t key = keys[i];
+            if (K > 0 && (key < 0 || key >= K)) atomicOr(err, kErrArg);
+            d = sort_digit(key, shift, bins);
+        }
+        // equal digits of a warp (neighbouring triangles mostly share a
+        // cluster) add once
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < bins; i += kSortThreads) cnt[(int64_t)i * ntiles + blockIdx.x] = h[i];
+    if (!scan_out) return;
+    // the block's writes, then one gpu-scope fence before its ticket
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (last) __threadfence();
+    }
+    __syncthreads();
+    if (!last) return;
+    block_scan_i32(cnt, (int64_t)bins * ntiles, scan_out, ws);
+    if (threadIdx.x == 0) *ticket = 0;   // ready for the next launch
+}
+
+// bsum[b] = sum of in[b * kSortScanBlock .. (b + 1) * kSortScanBlock)
+__global__ void __launch_bounds__(kSortThreads) k_sort_sums(const int32_t* __restrict__ in, int64_t n,
+                                                            int32_t* __restrict__ bsum)
+{
+    __shared__ int32_t ws[kSortThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kSortScanBlock + threadIdx.x * kSortScanPer;
+    int32_t v = 0;
+#pragma unroll
+    for (int q = 0; q < kSortScanPer; ++q) v += base + q < n ? in[base + q] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int w = 0; w < kSortThreads / 32; ++w) t += ws[w];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+// out = exclusive scan of in (the block totals before this block, then the
+// block's own positions)
+__global__ void __launch_bounds__(kSortThreads) k_sort_offsets(const int32_t* __restrict__ in, int64_t n,
+                                                               const int32_t* __restrict__ bsum,
+                                                               int32_t* __restrict__ out)
+{
+    __shared__ int32_t ws[kSortThreads / 32];
+    __shared__ int32_t before;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t p = 0;
+    for (int32_t b = threadIdx.x; b < (int32_t)blockIdx.x; b += kSortThreads) p += bsum[b];
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    if (lane == 0) ws[w] = p;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t t = 0;
+        for (int i = 0; i < kSortThreads / 32; ++i) t += ws[i];
+        before = t;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortScanBlock + threadIdx.x * kSortScanPer;
+    int32_t v[kSortScanPer];
+    int32_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kSortScanPer; ++q) {
+        v[q] = base + q < n ? in[base + q] : 0;
+        sum += v[q];
+    }
+    int32_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();   // ws is reused
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    int32_t run = before + x - sum;
+    for (int i = 0; i < w; ++i) run += ws[i];
+#pragma unroll
+    for (int q = 0; q < kSortScanPer; ++q) {
+        if (base + q < n) out[base + q] = run;
+        run += v[q];
+    }
+}
+
+// dynamic shared memory of k_sort_scatter for 2^bits digits
+static size_t sort_scatter_smem(int bins)
+{
+    return sizeof(int32_t) * ((size_t)(kSortThreads / 32) * (2 * bins + 1) + bins);
+}
+
+// One pass's stable scatter of a tile.  vals == nullptr: the value is the
+// position (the triangle index); keys_out == nullptr: keys are not written.
+// start != nullptr (one pass, digit = cluster): block 0 also writes the
+// cluster starts start[0..K] and sizes size[0..K).
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* __restrict__ keys,
+                                                               const int32_t* __restrict__ vals, int64_t n,
+                                                               int shift, int bins, int32_t ntiles,
+                                                               const int32_t* __restrict__ off,
+                                                               int32_t* __restrict__ keys_out,
+                                                               int32_t* __restrict__ vals_out, int32_t K,
+                                                               int32_t* __restrict__ start,
+                                                               int32_t* __restrict__ size)
+{
+    constexpr int kW = kSortThreads / 32;
+    extern __shared__ int32_t sm[];
+    int32_t* wc = sm;                          // [kW][bins + 1] a warp's count of each digit (column bins: past the end)
+    int32_t* wo = wc + kW * (bins + 1);        // [kW][bins] where the warp's items of each digit start
+    int32_t* run = wo + kW * bins;             // [bins] next free position of each digit for this tile
+    for (int i = threadIdx.x; i < kW * (bins + 1); i += kSortThreads) wc[i] = 0;
+    for (int i = threadIdx.x; i < bins; i += kSortThreads) run[i] = off[(int64_t)i * ntiles + blockIdx.x];
+    if (start && blockIdx.x == 0)
+        for (int k = threadIdx.x; k <= K; k += kSortThreads) {
+            const int32_t a = k < bins ? off[(int64_t)k * ntiles] : (int32_t)n;
+            start[k] = a;
+            if (k < K) size[k] = (k + 1 < bins ? off[(int64_t)(k + 1) * ntiles] : (int32_t)n) - a;
+        }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t i = base + r * kSortThreads + threadIdx.x;
+        const bool ok = i < n;
+        const int32_t key = ok ? keys[i] : 0;
+        const int32_t val = ok ? (vals ? vals[i] : (int32_t)i) : 0;
+        const int d = ok ? sort_digit(key, shift, bins) : bins;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (rank == 0) wc[w * (bins + 1) + d] = __popc(peers);
+        __syncthreads();
+        for (int q = threadIdx.x; q < bins; q += kSortThreads) {
+            int32_t x = run[q];
+            for (int v = 0; v < kW; ++v) {
+                wo[v * bins + q] = x;
+                x += wc[v * (bins + 1) + q];
+            }
+            run[q] = x;
+        }
+        __syncthreads();
+        if (ok) {
+            const int32_t pos = wo[w * bins + d] + rank;
+            if (keys_out) keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        if (rank == 0) wc[w * (bins + 1) + d] = 0;
+        __syncthreads();   // wo is rewritten by the next round
+    }
 }
 
 // ------------------------------------------------------- extents (a6)
@@ -827,8 +1058,13 @@ constexpr int kNT = 128;
 
 // Per-layer scratch that is not part of the layer's state, allocated with it.
 struct LayerMem {
-    int32_t* iota = nullptr;
-    int32_t* keys_out = nullptr;
+    int32_t* skeys[2] = {nullptr, nullptr};   // radix sort: keys and values between passes
+    int32_t* svals[2] = {nullptr, nullptr};
+    int32_t* scnt = nullptr;                   // [bins * tiles] digit counts, then offsets
+    int32_t* soff = nullptr;
+    int32_t* sbsum = nullptr;
+    unsigned int* sticket = nullptr;           // zero between launches (the fused scan's ticket)
+    int sort_passes = 1, sort_bits = 0;
     int32_t* ctr = nullptr;
     Cand* cand = nullptr;
     obb_qbox* evals = nullptr;
@@ -862,9 +1098,6 @@ struct LayerMem {
     CountScratch cscr{};              // the graph's own counting scratch (fixed addresses)
     void* cscr_mem = nullptr;
     int64_t g_round = 0, g_rebuild = 0, g_post = 0;   // kernel launches per round, per rebuild, after the loop
-    void* cub_tmp = nullptr;
-    size_t cub_bytes = 0;
-    int end_bit = 1;
     bool members_valid = false;
 };
 
@@ -880,18 +1113,42 @@ obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
 {
     cudaStream_t s = ctx->stream;
     LayerMem* M = mem_of(L);
-    OBB_CK(ctx, cudaMemsetAsync(L->d_size, 0, sizeof(int32_t) * L->K, s));
-    k_hist<<<(unsigned)((L->T + 255) / 256), 256, 0, s>>>(L->d_assign, L->T, L->K, L->d_size, ctx->d_err);
-    note_launch(ctx);
-    launch_scan_i32(ctx, L->d_size, L->d_start, M->dK);
-    note_launch(ctx);
-    auto sort = [&](cudaStream_t cs) {
-        size_t bytes = M->cub_bytes;
-        return cub::DeviceRadixSort::SortPairs(M->cub_tmp, bytes, L->d_assign, M->keys_out, M->iota, L->d_members,
-                                               (int)L->T, 0, M->end_bit, cs);
-    };
-    OBB_CK(ctx, sort(s));
-    note_launch(ctx, captured_launches(ctx, L->T, M->end_bit, sort));
+    const int64_t T = L->T;
+    const bool one_pass = M->sort_passes == 1;
+    if (!one_pass) {
+        // cluster sizes and starts (with one pass the sort's own offsets give them)
+        OBB_CK(ctx, cudaMemsetAsync(L->d_size, 0, sizeof(int32_t) * L->K, s));
+        k_hist<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(L->d_assign, T, L->K, L->d_size, ctx->d_err);
+        note_launch(ctx);
+        launch_scan_i32(ctx, L->d_size, L->d_start, M->dK);
+    }
+    // the member list: a stable radix sort of the triangles by cluster
+    const int32_t ntiles = (int32_t)((T + kSortTile - 1) / kSortTile);
+    const int bins = 1 << M->sort_bits;
+    const int64_t nc = (int64_t)bins * ntiles;
+    const bool fused = nc <= kSortFusedScanMax;
+    const unsigned nsb = (unsigned)((nc + kSortScanBlock - 1) / kSortScanBlock);
+    const int32_t* kin = L->d_assign;
+    const int32_t* vin = nullptr;
+    for (int p = 0; p < M->sort_passes; ++p) {
+        const bool last = p + 1 == M->sort_passes;
+        const int shift = p * M->sort_bits;
+        int32_t* kout = last ? nullptr : M->skeys[p & 1];
+        int32_t* vout = last ? L->d_members : M->svals[p & 1];
+        k_sort_count<<<ntiles, kSortThreads, sizeof(int32_t) * bins, s>>>(
+            kin, T, shift, bins, ntiles, one_pass ? L->K : 0, M->scnt, fused ? M->soff : nullptr, M->sticket,
+            ctx->d_err);
+        if (!fused) {
+            k_sort_sums<<<nsb, kSortThreads, 0, s>>>(M->scnt, nc, M->sbsum);
+            k_sort_offsets<<<nsb, kSortThreads, 0, s>>>(M->scnt, nc, M->sbsum, M->soff);
+        }
+        k_sort_scatter<<<ntiles, kSortThreads, sort_scatter_smem(bins), s>>>(
+            kin, vin, T, shift, bins, ntiles, M->soff, kout, vout, L->K, one_pass ? L->d_start : nullptr,
+            one_pass ? L->d_size : nullptr);
+        note_launch(ctx, fused ? 2 : 4);
+        kin = kout;
+        vin = vout;
+    }
     OBB_CK(ctx, cudaGetLastError());
     M->members_valid = true;
     return OBB_OK;
@@ -910,8 +1167,8 @@ void layer_destroy(obb_layer* L)
         if (M->gexec) cudaGraphExecDestroy(M->gexec);
         if (M->loop) cudaFreeAsync(M->loop, s);
         if (M->cscr_mem) cudaFreeAsync(M->cscr_mem, s);
-        void* mp[] = {M->iota, M->keys_out, M->ctr, M->cand, M->evals, M->ecount, M->epoints, M->mom,
-                      M->newframe, M->newq, M->ncount, M->dK, M->cub_tmp, M->feats, M->pred, M->skey,
+        void* mp[] = {M->skeys[0], M->skeys[1], M->svals[0], M->svals[1], M->scnt, M->soff, M->sbsum, M->sticket, M->ctr, M->cand, M->evals, M->ecount, M->epoints, M->mom,
+                      M->newframe, M->newq, M->ncount, M->dK, M->feats, M->pred, M->skey,
                       M->slot, M->evals2, M->n2, M->map, M->dirty, M->keep, M->level,
                       M->pframes, M->pq, M->pbest, M->pcount};
         for (void* p : mp)
@@ -962,7 +1219,14 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     L->T = T;
     M->cand_cap = 6 * K + 32;
     M->eval_cap = 4 * M->cand_cap;
-    while ((1 << M->end_bit) < K) ++M->end_bit;
+    {
+        int end_bit = 0;   // cluster indices < 2^end_bit
+        while ((1 << end_bit) < K) ++end_bit;
+        M->sort_passes = std::max(1, (end_bit + kSortMaxBits - 1) / kSortMaxBits);
+        M->sort_bits = (end_bit + M->sort_passes - 1) / M->sort_passes;
+    }
+    const int64_t sort_tiles = (T + kSortTile - 1) / kSortTile;
+    const int64_t sort_nc = ((int64_t)1 << M->sort_bits) * sort_tiles;
     cudaError_t e = cudaSuccess;
 #define A_(x)                        \
     if (e == cudaSuccess) e = (x);
@@ -977,8 +1241,18 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     A_(dalloc(&L->d_ext, K, s));
     A_(dalloc(&L->d_best, K, s));
     A_(dalloc(&L->d_stats, kStCount, s));
-    A_(dalloc(&M->iota, T, s));
-    A_(dalloc(&M->keys_out, T, s));
+    for (int p = 0; p + 1 < M->sort_passes; ++p) {
+        A_(dalloc(&M->skeys[p], T, s));
+        A_(dalloc(&M->svals[p], T, s));
+    }
+    A_(dalloc(&M->scnt, sort_nc, s));
+    A_(dalloc(&M->soff, sort_nc, s));
+    A_(dalloc(&M->sbsum, (sort_nc + kSortScanBlock - 1) / kSortScanBlock, s));
+    A_(dalloc(&M->sticket, 1, s));
+    if (e == cudaSuccess) e = cudaMemsetAsync(M->sticket, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sort_scatter_smem(1 << kSortMaxBits));
     A_(dalloc(&M->ctr, kCtrCount, s));
     A_(dalloc(&M->cand, M->cand_cap, s));
     A_(dalloc(&M->evals, M->eval_cap, s));
@@ -1001,13 +1275,6 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     A_(dalloc(&M->pbest, K, s));
     A_(dalloc(&M->pcount, (size_t)kProbes * K, s));
 #undef A_
-    if (e == cudaSuccess) {
-        size_t bytes = 0;
-        e = cub::DeviceRadixSort::SortPairs(nullptr, bytes, (int32_t*)nullptr, (int32_t*)nullptr,
-                                            (int32_t*)nullptr, (int32_t*)nullptr, (int)T, 0, M->end_bit, s);
-        M->cub_bytes = bytes;
-        if (e == cudaSuccess) e = cudaMallocAsync(&M->cub_tmp, bytes > 0 ? bytes : 16, s);
-    }
     if (e != cudaSuccess) {
         layer_destroy(L);
         return cuda_fail(ctx, e, "layer allocation");
@@ -1018,8 +1285,6 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     OBB_CK(ctx, cudaMemsetAsync(L->d_stats, 0, sizeof(int64_t) * kStCount, s));
     OBB_CK(ctx, cudaMemsetAsync(M->dirty, 1, K, s));
     OBB_CK(ctx, cudaMemsetAsync(M->level, 0, sizeof(int32_t) * K, s));
-    k_iota<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(M->iota, T);
-    note_launch(ctx);
     obb_status st = set_device_int(ctx, M->dK, K);
     if (st == OBB_OK) st = rebuild_members(ctx, L);
     if (st == OBB_OK) {

@@ -90,9 +90,11 @@ __global__ void k_frame(const uint32_t* keys, int32_t N, LatticeFrame* f, int32_
 
 // U = rint(((x - lo) / h - 1/2) 256), each step a correctly rounded FP64 op.
 // The quotient through the reciprocal, d (1/h), is within 2 ulps of d / h,
-// so (q - 1/2) 256 moves by less than 2^-30 (q < 2^12): whenever that value
-// lies farther than 2^-29 from a half-integer both round to the same integer;
-// otherwise the defining sequence, with the division, decides.
+// so while d / h < 2^12 (|(q - 1/2) 256| < 2^20; a vertex of the lattice's
+// own frame has d / h <= N + 1 <= 2049) the value (q - 1/2) 256 moves by
+// less than 2^-30: whenever it lies farther than 2^-29 from a half-integer
+// both round to the same integer; otherwise, or out of that range, the
+// defining sequence, with the division, decides.
 __global__ void k_snap(const float* __restrict__ V, int64_t nv, const LatticeFrame* __restrict__ f,
                        int32_t* __restrict__ U)
 {
@@ -102,7 +104,7 @@ __global__ void k_snap(const float* __restrict__ V, int64_t nv, const LatticeFra
     const double d = __dsub_rn((double)V[i], f->lo[b]);
     double q = __dmul_rn(__dsub_rn(__dmul_rn(d, f->inv_h[b]), 0.5), 256.0);
     const double t = q - floor(q);   // exact
-    if (!(fabs(t - 0.5) > 0x1p-29) || !(fabs(q) < 0x1p30)) {
+    if (!(fabs(t - 0.5) > 0x1p-29) || !(fabs(q) < 0x1p20)) {
         q = __ddiv_rn(d, f->h[b]);
         q = __dsub_rn(q, 0.5);
         q = __dmul_rn(q, 256.0);

@@ -662,6 +662,21 @@ obb_status obb_layer_moments(obb_ctx* ctx, obb_layer* L, int32_t compensated, do
     return layer_moments(ctx, L, compensated, out);
 }
 
+obb_status obb_layer_members(obb_ctx* ctx, obb_layer* L, int32_t* members, int32_t* start)
+{
+    if (!ctx || !L) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (L->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
+    OBB_TRY(layer_members(ctx, L));
+    if (members)
+        OBB_CK(ctx, cudaMemcpyAsync(members, L->d_members, sizeof(int32_t) * L->T, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+    if (start)
+        OBB_CK(ctx, cudaMemcpyAsync(start, L->d_start, sizeof(int32_t) * (L->K + 1), cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+    OBB_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+
 void obb_layer_free(obb_layer* L) { layer_destroy(L); }
 
 obb_status obb_batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_batch** out)
