@@ -117,12 +117,15 @@ struct alignas(128) BoxPrep {
 
 // One lattice as the counting kernel sees it (a table of these lets one launch
 // count boxes of many meshes).
+// The counting copies interleave the rows of a slice by column: word w of
+// row (slice s, column c) at (s W + w) N + c, so that the lanes of a warp,
+// which count neighbouring columns, read neighbouring words.
 struct LatRef {
-    const uint64_t* words;     // rows along x: row (k, j) at (k N + j) W, bit i
-    const uint64_t* words_y;   // rows along y: row (k, i) at (k N + i) W, bit j
-    const uint64_t* words_z;   // rows along z: row (j, i) at (j N + i) W, bit k
+    const uint64_t* words;     // rows along x: row (k, j), bit i (slice k, column j)
+    const uint64_t* words_y;   // rows along y: row (k, i), bit j (slice k, column i)
+    const uint64_t* words_z;   // rows along z: row (j, i), bit k (slice j, column i)
     // rank tables of the three: entry (row, w) = occupied bits in words 0..w-1
-    // of that row (uint16, the words' layout)
+    // of that row (uint16, the same interleaved layout)
     const uint16_t* rank;
     const uint16_t* rank_y;
     const uint16_t* rank_z;
@@ -221,10 +224,11 @@ struct obb_lattice {
     mutable bool frame_stale = false;      // a rebuild may have moved lo / h since the last copy
     obbv::LatticeFrame* d_frame = nullptr;
     int32_t* d_fixed = nullptr;      // [nv][3] snapped vertices
-    uint64_t* d_words = nullptr;     // occupancy, rows along x
-    uint64_t* d_words_y = nullptr;   // the same bits with rows along y, then z (counting boxes
+    uint64_t* d_words = nullptr;     // occupancy, rows along x: row (k, j) at (k N + j) W, bit i
+    uint64_t* d_cwords = nullptr;    // its counting copy, rows interleaved by column (LatRef)
+    uint64_t* d_words_y = nullptr;   // counting copies with rows along y, then z (counting boxes
     uint64_t* d_words_z = nullptr;   // along their shortest-shadow axis)
-    uint16_t* d_rank = nullptr;      // rank tables of the rows along x, y, z
+    uint16_t* d_rank = nullptr;      // rank tables of the counting copies along x, y, z
     uint16_t* d_rank_y = nullptr;
     uint16_t* d_rank_z = nullptr;
     size_t n_words = 0;

@@ -267,8 +267,10 @@ __device__ __forceinline__ void transpose64(uint64_t& a, uint64_t& b, int lane)
 
 // The occupancy with rows along y (mode 0: slice k, row (k, i), bit j) or
 // along z (mode 1: slice j, row (j, i), bit k), from the rows along x (row
-// (k, j), bit i): one warp per (slice, 64 x 64 block).  Bits of rows past N
-// read as 0; words past ceil(N / 64) are never read by the counting kernel.
+// (k, j), bit i): one warp per (slice, 64 x 64 block).  The copies are for
+// counting and interleave a slice's rows by column: word w of row (slice s,
+// column c) at (s W + w) N + c.  Bits of rows past N read as 0; words past
+// ceil(N / 64) are never read by the counting kernel.
 __global__ void k_transpose_rows(const uint64_t* __restrict__ xw, uint64_t* __restrict__ dst, int32_t N, int32_t W,
                                  int mode)
 {
@@ -287,8 +289,8 @@ __global__ void k_transpose_rows(const uint64_t* __restrict__ xw, uint64_t* __re
     uint64_t b = r1 < N ? __ldg(xw + src_row(r1) + C) : 0ull;
     transpose64(a, b, lane);
     const int32_t c0 = 64 * C + lane, c1 = c0 + 32;
-    if (c0 < N) dst[((int64_t)sl * N + c0) * W + R] = a;
-    if (c1 < N) dst[((int64_t)sl * N + c1) * W + R] = b;
+    if (c0 < N) dst[((int64_t)sl * W + R) * N + c0] = a;
+    if (c1 < N) dst[((int64_t)sl * W + R) * N + c1] = b;
 }
 
 __device__ __forceinline__ uint64_t prefix_xor(uint64_t x)
@@ -316,9 +318,11 @@ __device__ __forceinline__ uint32_t row_exclusive_sum(uint32_t v, int c, int G)
 
 // One lane per 128-bit chunk; a row's G = W / 2 chunks sit on consecutive
 // lanes.  The prefix XOR along the row turns the crossing flips into
-// occupancy; the same pass writes the row's rank table (occupied bits before
-// each 64-bit word).
-__global__ void k_row_scan(uint64_t* __restrict__ words, uint16_t* __restrict__ rank, int32_t N, int32_t W)
+// occupancy; the same pass writes the counting copy of the words and the
+// rank table (occupied bits before each 64-bit word), both interleaved by
+// column: word w of row (k, j) at (k W + w) N + j.
+__global__ void k_row_scan(uint64_t* __restrict__ words, uint64_t* __restrict__ cwords,
+                           uint16_t* __restrict__ rank, int32_t N, int32_t W)
 {
     const int G = W >> 1;
     const int rpw = 32 / G;
@@ -356,29 +360,28 @@ __global__ void k_row_scan(uint64_t* __restrict__ words, uint16_t* __restrict__ 
     const uint32_t before = row_exclusive_sum(n0 + (uint32_t)__popcll(p1), c, G);
     if (active) {
         *p = make_uint4((uint32_t)p0, (uint32_t)(p0 >> 32), (uint32_t)p1, (uint32_t)(p1 >> 32));
-        reinterpret_cast<uint32_t*>(rank + row * W)[c] = before | ((before + n0) << 16);
+        const int64_t k = row / N, j = row - k * N;
+        const int64_t i0 = (k * W + 2 * c) * N + j;
+        cwords[i0] = p0;
+        cwords[i0 + N] = p1;
+        rank[i0] = (uint16_t)before;
+        rank[i0 + N] = (uint16_t)(before + n0);
     }
 }
 
-// The rank table of finished rows (the y- and z-row copies), laid out as
-// k_row_scan lays it out.
+// The rank table of finished interleaved rows (the y- and z-row copies): one
+// thread per row (slice s, column c), columns on consecutive threads.
 __global__ void k_row_rank(const uint64_t* __restrict__ words, uint16_t* __restrict__ rank, int32_t N, int32_t W)
 {
-    const int G = W >> 1;
-    const int rpw = 32 / G;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lr = lane / G, c = lane - lr * G;
-    const int64_t row = warp * rpw + lr;
-    const bool active = lr < rpw && row < (int64_t)N * N;
-    uint32_t n0 = 0, n1 = 0;
-    if (active) {
-        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(words + row * W) + c);
-        n0 = (uint32_t)__popcll(v.x);
-        n1 = (uint32_t)__popcll(v.y);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * N) return;
+    const int64_t sl = t / N, c = t - sl * N;
+    const int64_t base = sl * W * N + c;
+    uint32_t run = 0;
+    for (int32_t w = 0; w < W; ++w) {
+        rank[base + (int64_t)w * N] = (uint16_t)run;
+        run += (uint32_t)__popcll(__ldg(words + base + (int64_t)w * N));
     }
-    const uint32_t before = row_exclusive_sum(n0 + n1, c, G);
-    if (active) reinterpret_cast<uint32_t*>(rank + row * W)[c] = before | ((before + n0) << 16);
 }
 
 }  // namespace
@@ -408,7 +411,7 @@ obb_status rebuild_occupancy(obb_ctx* ctx, obb_lattice* lat)
     note_launch(ctx);
     const int G = W / 2, rpw = 32 / G;
     int64_t warps = ((int64_t)N * N + rpw - 1) / rpw;
-    k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_rank, N, W);
+    k_row_scan<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_cwords, lat->d_rank, N, W);
     note_launch(ctx);
     // rows along y and z: kept once a context counts along them, then refreshed
     // by every rebuild
@@ -430,8 +433,9 @@ obb_status rebuild_occupancy(obb_ctx* ctx, obb_lattice* lat)
         const int64_t tb = (N + 63) / 64, tw = (int64_t)N * tb * tb;
         k_transpose_rows<<<(unsigned)((tw + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_words_y, N, W, 0);
         k_transpose_rows<<<(unsigned)((tw + 7) / 8), 256, 0, s>>>(lat->d_words, lat->d_words_z, N, W, 1);
-        k_row_rank<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words_y, lat->d_rank_y, N, W);
-        k_row_rank<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(lat->d_words_z, lat->d_rank_z, N, W);
+        const unsigned rb = (unsigned)(((int64_t)N * N + 255) / 256);
+        k_row_rank<<<rb, 256, 0, s>>>(lat->d_words_y, lat->d_rank_y, N, W);
+        k_row_rank<<<rb, 256, 0, s>>>(lat->d_words_z, lat->d_rank_z, N, W);
         note_launch(ctx, 4);
     }
     OBB_CK(ctx, cudaGetLastError());
@@ -452,9 +456,10 @@ obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_la
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_frame, sizeof(LatticeFrame), s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_fixed, sizeof(int32_t) * 3 * mesh->nv, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words, sizeof(uint64_t) * lat->n_words, s));
+    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_cwords, sizeof(uint64_t) * lat->n_words, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_rank, sizeof(uint16_t) * lat->n_words, s));
     OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_ref, sizeof(LatRef), s));
-    lat->ref = LatRef{lat->d_words, nullptr, nullptr, lat->d_rank, nullptr, nullptr, N, W};
+    lat->ref = LatRef{lat->d_cwords, nullptr, nullptr, lat->d_rank, nullptr, nullptr, N, W};
     OBB_CK(ctx, cudaMemcpyAsync(lat->d_ref, &lat->ref, sizeof(LatRef), cudaMemcpyHostToDevice, s));
     OBB_TRY(rebuild_occupancy(ctx, lat));
     OBB_TRY(lattice_frame_host(lat));

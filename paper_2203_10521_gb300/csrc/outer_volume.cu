@@ -38,7 +38,7 @@
 #endif
 // OBB_COUNT_MINB: resident blocks of the counting kernel per SM the register budget aims at
 #ifndef OBB_COUNT_MINB
-#define OBB_COUNT_MINB 4
+#define OBB_COUNT_MINB 5
 #endif
 // OBB_BIG_TK_ROWS: boxes with at least this many (j, k) rows use tiles twice as tall (0: off)
 #ifndef OBB_BIG_TK_ROWS
@@ -812,18 +812,19 @@ __device__ __forceinline__ void clip_slab_rcp(int32_t d, uint64_t M, int64_t c, 
     hi = (int32_t)u;
 }
 
-// popcount of the occupied bits i in [a, e] of one row (0 <= a <= e < N)
-// 64-bit words: the first and last word carry the masks (merged without a
-// branch when they are the same word), interior words count whole.
-__device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t a, int32_t e)
+// popcount of the occupied bits i in [a, e] of one row (0 <= a <= e < N) of
+// a counting copy, the row's word w at row[w ws] (ws = N, the copy's column
+// interleave); 64-bit words: the first and last word carry the masks (merged
+// without a branch when they are the same word), interior words count whole.
+__device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row, int32_t ws, int32_t a, int32_t e)
 {
     const int32_t wa = a >> 6, we = e >> 6;
-    const uint64_t first = __ldg(row + wa);
-    const uint64_t last = __ldg(row + we);
+    const uint64_t first = __ldg(row + wa * ws);
+    const uint64_t last = __ldg(row + we * ws);
     uint64_t mlo = ~0ull << (a & 63);
     const uint64_t mhi = ~0ull >> (63 - (e & 63));
     uint32_t cnt = 0;
-    for (int32_t w = wa + 1; w < we; ++w) cnt += __popcll(__ldg(row + w));
+    for (int32_t w = wa + 1; w < we; ++w) cnt += __popcll(__ldg(row + w * ws));
     const bool one = wa == we;
     mlo = one ? (mlo & mhi) : mlo;
     return cnt + __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
@@ -833,12 +834,12 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
 // 0..w-1): the two end words with their masks plus the whole words between
 // them, rk[we] - rk[min(wa + 1, we)] -- four loads whatever the row's length.
 __device__ __forceinline__ uint32_t popc_rank(const uint64_t* __restrict__ row, const uint16_t* __restrict__ rk,
-                                              int32_t a, int32_t e)
+                                              int32_t ws, int32_t a, int32_t e)
 {
     const int32_t wa = a >> 6, we = e >> 6;
-    const uint64_t first = __ldg(row + wa);
-    const uint64_t last = __ldg(row + we);
-    const uint32_t mid = (uint32_t)__ldg(rk + we) - (uint32_t)__ldg(rk + min(wa + 1, we));
+    const uint64_t first = __ldg(row + wa * ws);
+    const uint64_t last = __ldg(row + we * ws);
+    const uint32_t mid = (uint32_t)__ldg(rk + we * ws) - (uint32_t)__ldg(rk + min(wa + 1, we) * ws);
     uint64_t mlo = ~0ull << (a & 63);
     const uint64_t mhi = ~0ull >> (63 - (e & 63));
     const bool one = wa == we;
@@ -847,11 +848,11 @@ __device__ __forceinline__ uint32_t popc_rank(const uint64_t* __restrict__ row, 
 }
 
 // occupied bits of [a, e] when it lies within two consecutive words
-__device__ __forceinline__ uint32_t popc_short(const uint64_t* __restrict__ row, int32_t a, int32_t e)
+__device__ __forceinline__ uint32_t popc_short(const uint64_t* __restrict__ row, int32_t ws, int32_t a, int32_t e)
 {
     const int32_t wa = a >> 6, we = e >> 6;
-    const uint64_t first = __ldg(row + wa);
-    const uint64_t last = __ldg(row + we);
+    const uint64_t first = __ldg(row + wa * ws);
+    const uint64_t last = __ldg(row + we * ws);
     uint64_t mlo = ~0ull << (a & 63);
     const uint64_t mhi = ~0ull >> (63 - (e & 63));
     const bool one = wa == we;
@@ -875,11 +876,11 @@ __device__ __forceinline__ uint32_t row_bytes(int32_t a, int32_t e)
 // occupied bits of [a, e] by the box's row counting mode
 template <int kMode>
 __device__ __forceinline__ uint32_t popc_mode(const uint64_t* __restrict__ row, const uint16_t* __restrict__ rk,
-                                              int32_t a, int32_t e)
+                                              int32_t ws, int32_t a, int32_t e)
 {
-    if constexpr (kMode == kRowRank) return popc_rank(row, rk, a, e);
-    else if constexpr (kMode == kRowShort) return popc_short(row, a, e);
-    else return popc_range(row, a, e);
+    if constexpr (kMode == kRowRank) return popc_rank(row, rk, ws, a, e);
+    else if constexpr (kMode == kRowShort) return popc_short(row, ws, a, e);
+    else return popc_range(row, ws, a, e);
 }
 
 // One pass of a lane over its rows r0..r1 of a tile of a box whose three
@@ -910,7 +911,7 @@ __device__ __forceinline__ void dda_rows(int64_t (&Al)[3], int64_t (&Ah)[3], con
             if (lo <= hi) {
                 const int32_t a = i0 + lo, e = i0 + hi;
                 const uint32_t len = (uint32_t)(hi - lo + 1);
-                empty += len - popc_mode<kMode>(rowp, rkp, a, e);
+                empty += len - popc_mode<kMode>(rowp, rkp, N, a, e);
                 inbox += len;
                 my_dom += len;
                 if (kProf) {
@@ -925,7 +926,7 @@ __device__ __forceinline__ void dda_rows(int64_t (&Al)[3], int64_t (&Ah)[3], con
             if (jin && (uint32_t)k < (uint32_t)N) {
                 const int32_t a = max(i0 + lo, 0), e = min(i0 + hi, N - 1);
                 if (a <= e) {
-                    occ = popc_mode<kMode>(rowp, rkp, a, e);
+                    occ = popc_mode<kMode>(rowp, rkp, N, a, e);
                     my_dom += (uint32_t)(e - a + 1);
                     if (kProf) my_bytes += row_bytes<kMode>(a, e);
                 }
@@ -1106,8 +1107,10 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 Ah[a] = (int64_t)qb[a] * 4294967296LL + fixed_frac(rb[a], M) + kFixBias;
                 Bs[a] = p.fstep[a];
             }
-            const int64_t roff = ((int64_t)kb0 * N + j) * W;
-            const int64_t rstride = (int64_t)wk * N * W;
+            // count copies interleave the rows of a slice by column: word w of
+            // row (slice k, column j) at (k W + w) N + j
+            const int64_t roff = (int64_t)kb0 * W * N + j;
+            const int64_t rstride = (int64_t)wk * W * N;
             // an interior box's full-height tile: every row is in the lattice
             // and so is every x-interval; an idle lane gets an empty range
             const bool interior = (mode & 0x100) && (tk + 1) * wk * tkr <= p.nk;
@@ -1168,12 +1171,12 @@ __global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
                 if (jin && k >= 0 && k < N) {
                     const int32_t a = max(ia, 0), e = min(ie, N - 1);
                     if (a <= e) {
-                        const int64_t roff = ((int64_t)k * N + j) * W;
+                        const int64_t roff = (int64_t)k * W * N + j;
                         if (p.rank == kRowRank) {
-                            occ = popc_rank(words + roff, p.ranks + roff, a, e);
+                            occ = popc_rank(words + roff, p.ranks + roff, N, a, e);
                             if (kProf) my_bytes += row_bytes<kRowRank>(a, e);
                         } else {
-                            occ = popc_range(words + roff, a, e);
+                            occ = popc_range(words + roff, N, a, e);
                             if (kProf) my_bytes += row_bytes<kRowWalk>(a, e);
                         }
                         my_dom += (uint32_t)(e - a + 1);

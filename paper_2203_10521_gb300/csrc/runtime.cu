@@ -342,6 +342,7 @@ void obb_lattice_free(obb_lattice* lat)
     if (lat->d_frame) cudaFreeAsync(lat->d_frame, s);
     if (lat->d_fixed) cudaFreeAsync(lat->d_fixed, s);
     if (lat->d_words) cudaFreeAsync(lat->d_words, s);
+    if (lat->d_cwords) cudaFreeAsync(lat->d_cwords, s);
     if (lat->d_words_y) cudaFreeAsync(lat->d_words_y, s);
     if (lat->d_words_z) cudaFreeAsync(lat->d_words_z, s);
     if (lat->d_rank) cudaFreeAsync(lat->d_rank, s);
