@@ -134,12 +134,25 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+COUNTING_SOURCES = ("outer_volume.cu", "occupancy.cu", "internal.h")
+
+
+def counting_source_hash():
+    """First 16 hex digits of the SHA-256 of the counting kernel's sources (the
+    kernel, the occupancy pass that writes its lattice copies, their shared
+    types), concatenated in that order."""
+    h = hashlib.sha256()
+    for f in COUNTING_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2203_10521_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def roofline_inputs(workload_key):
     """DRAM bytes and warp instructions per batch launch of the counting kernel
     from the committed ncu summary of this workload; valid only while the
-    kernel source is unchanged (else the values are null)."""
+    kernel and the layout of the lattice copies it reads are unchanged (else
+    the values are null)."""
     p = os.path.join(ROOT, "profiles", f"k_count_{workload_key}_roofline_inputs.txt")
-    src = os.path.join(ROOT, "paper_2203_10521_gb300", "csrc", "outer_volume.cu")
     if not os.path.exists(p):
         return {}
     kv = {}
@@ -147,8 +160,7 @@ def roofline_inputs(workload_key):
         if "=" in line and not line.startswith("#"):
             k, v = line.strip().split("=", 1)
             kv[k.strip()] = v.strip()
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if kv.get("source_sha256_16") != h:
+    if kv.get("source_sha256_16") != counting_source_hash():
         return {"stale": True}
     out = {}
     for k in ("dram_bytes_batch_launch", "warp_inst_batch_launch", "alu_pipe_pct", "issue_active_pct"):

@@ -830,21 +830,19 @@ __device__ __forceinline__ uint32_t popc_range(const uint64_t* __restrict__ row,
     return cnt + __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
 }
 
-// The same count through the row's rank table (rk[w] = occupied bits in words
-// 0..w-1): the two end words with their masks plus the whole words between
-// them, rk[we] - rk[min(wa + 1, we)] -- four loads whatever the row's length.
+// The same count through the row's rank table (rk[w ws] = occupied bits in
+// words 0..w-1): the bits before e + 1 minus the bits before a, each a rank
+// entry plus the popcount of its word below the bit -- four loads whatever
+// the row's length, and no case for an interval inside one word.
 __device__ __forceinline__ uint32_t popc_rank(const uint64_t* __restrict__ row, const uint16_t* __restrict__ rk,
                                               int32_t ws, int32_t a, int32_t e)
 {
     const int32_t wa = a >> 6, we = e >> 6;
     const uint64_t first = __ldg(row + wa * ws);
     const uint64_t last = __ldg(row + we * ws);
-    const uint32_t mid = (uint32_t)__ldg(rk + we * ws) - (uint32_t)__ldg(rk + min(wa + 1, we) * ws);
-    uint64_t mlo = ~0ull << (a & 63);
-    const uint64_t mhi = ~0ull >> (63 - (e & 63));
-    const bool one = wa == we;
-    mlo = one ? (mlo & mhi) : mlo;
-    return mid + __popcll(first & mlo) + __popcll(last & (one ? 0ull : mhi));
+    const uint32_t ra = __ldg(rk + wa * ws), rb = __ldg(rk + we * ws);
+    return rb - ra + (uint32_t)__popcll(last & (~0ull >> (63 - (e & 63)))) -
+           (uint32_t)__popcll(first & ~(~0ull << (a & 63)));
 }
 
 // occupied bits of [a, e] when it lies within two consecutive words
