@@ -69,19 +69,6 @@ __device__ __forceinline__ void proj3(const int32_t* __restrict__ U, const int32
 
 // ------------------------------------------------------- membership
 
-__global__ void k_hist(const int32_t* __restrict__ assign, int64_t T, int32_t K, int32_t* __restrict__ size,
-                       int32_t* err)
-{
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= T) return;
-    int32_t k = assign[t];
-    if (k < 0 || k >= K) {
-        atomicOr(err, kErrArg);
-        return;
-    }
-    atomicAdd(&size[k], 1);
-}
-
 __global__ void k_check_nonempty(const int32_t* __restrict__ size, int32_t K, int32_t* err)
 {
     int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,10 +140,13 @@ __device__ void block_scan_i32(const int32_t* in, int64_t n, int32_t* out, int32
     }
 }
 
-// K > 0: keys outside [0, K) raise kErrArg.  scan_out != nullptr: the last
-// block to finish scans the counts into scan_out.
+// K > 0: keys outside [0, K) raise kErrArg.  size != nullptr: the cluster
+// sizes are added up as well (keys = clusters; size zeroed beforehand).
+// scan_out != nullptr: the last block to finish scans the counts into
+// scan_out.
 __global__ void __launch_bounds__(kSortThreads) k_sort_count(const int32_t* __restrict__ keys, int64_t n, int shift,
                                                              int bins, int32_t ntiles, int32_t K,
+                                                             int32_t* __restrict__ size,
                                                              int32_t* __restrict__ cnt, int32_t* __restrict__ scan_out,
                                                              unsigned int* __restrict__ ticket, int32_t* err)
 {
@@ -167,13 +157,28 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_count(const int32_t* __re
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
     const int lane = threadIdx.x & 31;
+    int32_t kr[kSortRounds];   // every load issued before the first is used
+#pragma unroll
     for (int r = 0; r < kSortRounds; ++r) {
         const int64_t i = base + r * kSortThreads + threadIdx.x;
+        kr[r] = i < n ? keys[i] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortRounds; ++r) {
+        const int64_t i = base + r * kSortThreads + threadIdx.x;
+        // the digit of every key, valid or not, as k_sort_scatter takes it;
+        // a key outside [0, K) is reported and left out of the sizes
         int d = -1;
+        int32_t cl = -1;
         if (i < n) {
-            const int32_t key = keys[i];
+            const int32_t key = kr[r];
             if (K > 0 && (key < 0 || key >= K)) atomicOr(err, kErrArg);
+            else cl = key;
             d = sort_digit(key, shift, bins);
+        }
+        if (size) {
+            const unsigned same = __match_any_sync(0xffffffffu, cl);
+            if (cl >= 0 && lane == __ffs(same) - 1) atomicAdd(&size[cl], __popc(same));
         }
         // equal digits of a warp (neighbouring triangles mostly share a
         // cluster) add once
@@ -263,14 +268,19 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_offsets(const int32_t* __
 // dynamic shared memory of k_sort_scatter for 2^bits digits
 static size_t sort_scatter_smem(int bins)
 {
-    return sizeof(int32_t) * ((size_t)(kSortThreads / 32) * (2 * bins + 1) + bins);
+    return sizeof(int32_t) * (size_t)(kSortThreads / 32) * bins;
 }
 
-// One pass's stable scatter of a tile.  vals == nullptr: the value is the
-// position (the triangle index); keys_out == nullptr: keys are not written.
-// start != nullptr (one pass, digit = cluster): block 0 also writes the
-// cluster starts start[0..K] and sizes size[0..K).
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* __restrict__ keys,
+// One pass's stable scatter of a tile.  Each warp owns kSortTile / 8
+// consecutive positions of the tile: it counts their digits into its own
+// row of shared memory, the rows become per-digit starts (the tile's offset
+// plus the items of the warps before), and the warp places its items in
+// order, ranking equal digits within a round by __match_any_sync.
+// vals == nullptr: the value is the position (the triangle index);
+// keys_out == nullptr: keys are not written.  start != nullptr (one pass,
+// digit = cluster): block 0 also writes the cluster starts start[0..K] and
+// sizes size[0..K).
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const int32_t* __restrict__ keys,
                                                                const int32_t* __restrict__ vals, int64_t n,
                                                                int shift, int bins, int32_t ntiles,
                                                                const int32_t* __restrict__ off,
@@ -280,12 +290,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* __
                                                                int32_t* __restrict__ size)
 {
     constexpr int kW = kSortThreads / 32;
-    extern __shared__ int32_t sm[];
-    int32_t* wc = sm;                          // [kW][bins + 1] a warp's count of each digit (column bins: past the end)
-    int32_t* wo = wc + kW * (bins + 1);        // [kW][bins] where the warp's items of each digit start
-    int32_t* run = wo + kW * bins;             // [bins] next free position of each digit for this tile
-    for (int i = threadIdx.x; i < kW * (bins + 1); i += kSortThreads) wc[i] = 0;
-    for (int i = threadIdx.x; i < bins; i += kSortThreads) run[i] = off[(int64_t)i * ntiles + blockIdx.x];
+    constexpr int kSub = kSortTile / kW;
+    extern __shared__ int32_t wb[];   // [kW][bins]: a warp's count of each digit, then where the next one goes
+    for (int i = threadIdx.x; i < kW * bins; i += kSortThreads) wb[i] = 0;
     if (start && blockIdx.x == 0)
         for (int k = threadIdx.x; k <= K; k += kSortThreads) {
             const int32_t a = k < bins ? off[(int64_t)k * ntiles] : (int32_t)n;
@@ -294,33 +301,51 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* __
         }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    for (int r = 0; r < kSortRounds; ++r) {
-        const int64_t i = base + r * kSortThreads + threadIdx.x;
-        const bool ok = i < n;
-        const int32_t key = ok ? keys[i] : 0;
-        const int32_t val = ok ? (vals ? vals[i] : (int32_t)i) : 0;
-        const int d = ok ? sort_digit(key, shift, bins) : bins;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + w * kSub;
+    int32_t* mine = wb + w * bins;
+    // the warp's items in registers, every load issued before the first is used
+    constexpr int kR = kSub / 32;
+    int32_t kr[kR], vr[kR];
+    const int32_t left = (int32_t)min((int64_t)kSub, max(n - base, (int64_t)0));   // the warp's items
+    const int32_t* kp = keys + base;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int32_t o = r * 32 + lane;
+        kr[r] = o < left ? kp[o] : 0;
+        vr[r] = o < left ? (vals ? vals[base + o] : (int32_t)(base + o)) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int d = r * 32 + lane < left ? sort_digit(kr[r], shift, bins) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d >= 0 && lane == __ffs(peers) - 1) mine[d] += __popc(peers);   // distinct digits: distinct words
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < bins; q += kSortThreads) {
+        int32_t x = off[(int64_t)q * ntiles + blockIdx.x];
+        for (int v = 0; v < kW; ++v) {
+            const int32_t c = wb[v * bins + q];
+            wb[v * bins + q] = x;
+            x += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const bool ok = r * 32 + lane < left;
+        const int32_t key = kr[r], val = vr[r];
+        const int d = ok ? sort_digit(key, shift, bins) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int rank = __popc(peers & ((1u << lane) - 1u));
-        if (rank == 0) wc[w * (bins + 1) + d] = __popc(peers);
-        __syncthreads();
-        for (int q = threadIdx.x; q < bins; q += kSortThreads) {
-            int32_t x = run[q];
-            for (int v = 0; v < kW; ++v) {
-                wo[v * bins + q] = x;
-                x += wc[v * (bins + 1) + q];
-            }
-            run[q] = x;
-        }
-        __syncthreads();
+        const int32_t pos = ok ? mine[d] + rank : 0;
+        __syncwarp();
+        if (ok && rank == 0) mine[d] += __popc(peers);
+        __syncwarp();
         if (ok) {
-            const int32_t pos = wo[w * bins + d] + rank;
             if (keys_out) keys_out[pos] = key;
             vals_out[pos] = val;
         }
-        if (rank == 0) wc[w * (bins + 1) + d] = 0;
-        __syncthreads();   // wo is rewritten by the next round
     }
 }
 
@@ -1115,13 +1140,9 @@ obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
     LayerMem* M = mem_of(L);
     const int64_t T = L->T;
     const bool one_pass = M->sort_passes == 1;
-    if (!one_pass) {
-        // cluster sizes and starts (with one pass the sort's own offsets give them)
-        OBB_CK(ctx, cudaMemsetAsync(L->d_size, 0, sizeof(int32_t) * L->K, s));
-        k_hist<<<(unsigned)((T + 255) / 256), 256, 0, s>>>(L->d_assign, T, L->K, L->d_size, ctx->d_err);
-        note_launch(ctx);
-        launch_scan_i32(ctx, L->d_size, L->d_start, M->dK);
-    }
+    // cluster sizes: added up by the first pass's counts (with one pass the
+    // sort's own offsets give sizes and starts)
+    if (!one_pass) OBB_CK(ctx, cudaMemsetAsync(L->d_size, 0, sizeof(int32_t) * L->K, s));
     // the member list: a stable radix sort of the triangles by cluster
     const int32_t ntiles = (int32_t)((T + kSortTile - 1) / kSortTile);
     const int bins = 1 << M->sort_bits;
@@ -1136,8 +1157,8 @@ obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
         int32_t* kout = last ? nullptr : M->skeys[p & 1];
         int32_t* vout = last ? L->d_members : M->svals[p & 1];
         k_sort_count<<<ntiles, kSortThreads, sizeof(int32_t) * bins, s>>>(
-            kin, T, shift, bins, ntiles, one_pass ? L->K : 0, M->scnt, fused ? M->soff : nullptr, M->sticket,
-            ctx->d_err);
+            kin, T, shift, bins, ntiles, p == 0 ? L->K : 0, p == 0 && !one_pass ? L->d_size : nullptr, M->scnt,
+            fused ? M->soff : nullptr, M->sticket, ctx->d_err);
         if (!fused) {
             k_sort_sums<<<nsb, kSortThreads, 0, s>>>(M->scnt, nc, M->sbsum);
             k_sort_offsets<<<nsb, kSortThreads, 0, s>>>(M->scnt, nc, M->sbsum, M->soff);
@@ -1146,6 +1167,7 @@ obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
             kin, vin, T, shift, bins, ntiles, M->soff, kout, vout, L->K, one_pass ? L->d_start : nullptr,
             one_pass ? L->d_size : nullptr);
         note_launch(ctx, fused ? 2 : 4);
+        if (p == 0 && !one_pass) launch_scan_i32(ctx, L->d_size, L->d_start, M->dK);   // cluster starts
         kin = kout;
         vin = vout;
     }

@@ -728,31 +728,53 @@ __global__ void k_batch_scatter(const BatchReq* __restrict__ reqs, int32_t n, co
 // ------------------------------------------------------------------- scan
 
 // Exclusive scan of n = *d_n int32 values (n <= cap) into out[0..n]; one block.
-__global__ void k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__ out,
-                           const int32_t* __restrict__ d_n)
+// out[0..n] = exclusive scan of in[0..n) (n = *d_n), one block of 1,024
+// threads: chunks of 4,096 consecutive values (four per thread), a scan of
+// the warp sums, and a running carry.
+__global__ void __launch_bounds__(1024) k_scan_i32(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                                  const int32_t* __restrict__ d_n)
 {
-    __shared__ int32_t part[1024];
+    __shared__ int32_t ws[32];
+    __shared__ int32_t chunk_total;
     const int32_t n = *d_n;
-    const int T = blockDim.x;
-    const int32_t per = (n + T - 1) / T;
-    const int32_t b0 = threadIdx.x * per;
-    const int32_t b1 = min(n, b0 + per);
-    int32_t s = 0;
-    for (int32_t i = b0; i < b1; ++i) s += in[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < T; off <<= 1) {
-        int32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t carry = 0;
+    for (int32_t c = 0; c < n; c += 4096) {
+        const int32_t b = c + 4 * threadIdx.x;
+        int32_t v[4], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[q] = b + q < n ? in[b + q] : 0;
+            sum += v[q];
+        }
+        int32_t x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[w] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
+        if (w == 0) {
+            const int32_t t = ws[lane];
+            int32_t u = t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, u, o);
+                if (lane >= o) u += y;
+            }
+            ws[lane] = u - t;   // warps before
+            if (lane == 31) chunk_total = u;
+        }
         __syncthreads();
+        int32_t run = carry + ws[w] + x - sum;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (b + q < n) out[b + q] = run;
+            run += v[q];
+        }
+        carry += chunk_total;
+        __syncthreads();   // ws and chunk_total are rewritten by the next chunk
     }
-    int32_t run = part[threadIdx.x] - s;
-    for (int32_t i = b0; i < b1; ++i) {
-        out[i] = run;
-        run += in[i];
-    }
-    if (threadIdx.x == T - 1) out[n] = part[T - 1];
+    if (threadIdx.x == 0) out[n] = carry;
 }
 
 // ------------------------------------------------------------------ count
