@@ -271,6 +271,17 @@ struct obb_batch {
     obbv::DevBuf tables, scratch;    // counting requests of a batched phase, and their gathered boxes
     obbv::DevBuf stat_ptrs;          // the layers' device counters, then their accepted-move totals
     int64_t* h_acc = nullptr;        // pinned host copy of the accepted-move totals
+    // Each layer's partition round as CUDA graphs, captured on first use: the
+    // phase before the counting launch (with and without the member-list
+    // rebuild) and the phase after it, with their kernel counts and the
+    // layer's counting request; replayed over kBatchStreams streams.
+    static constexpr int kBatchStreams = 8;
+    bool graphs = false;
+    std::vector<cudaGraphExec_t> g_pre, g_pre_rebuild, g_post;
+    std::vector<int32_t> k_pre, k_pre_rebuild, k_post;
+    std::vector<obbv::CountReq> req;
+    cudaStream_t par[kBatchStreams] = {};
+    cudaEvent_t ev[kBatchStreams + 1] = {};
 };
 
 struct obb_tree {

@@ -1691,10 +1691,91 @@ obb_status batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_b
     return OBB_OK;
 }
 
+// Captures every layer's partition-round phases as CUDA graphs (nothing
+// runs): round_body's phase before the counting launch, once with the
+// member-list rebuild in front, and its phase after the counting launch.
+// Each layer's counting request is recorded by the capture (the counting
+// itself stays deferred to the batch's one counting launch per round).
+static obb_status batch_capture(obb_ctx* ctx, obb_batch* B)
+{
+    const int32_t n = (int32_t)B->layers.size();
+    B->g_pre.assign(n, nullptr);
+    B->g_pre_rebuild.assign(n, nullptr);
+    B->g_post.assign(n, nullptr);
+    B->k_pre.assign(n, 0);
+    B->k_pre_rebuild.assign(n, 0);
+    B->k_post.assign(n, 0);
+    B->req.assign(n, CountReq{});
+    for (int p = 0; p < obb_batch::kBatchStreams; ++p)
+        if (!B->par[p]) OBB_CK(ctx, cudaStreamCreateWithFlags(&B->par[p], cudaStreamNonBlocking));
+    for (auto& e : B->ev)
+        if (!e) OBB_CK(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    OBB_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaStream_t cs = nullptr;
+    OBB_CK(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const cudaStream_t saved_stream = ctx->stream;
+    const int32_t saved_prof = ctx->prof;
+    const int64_t saved_launches = ctx->launches;
+    ctx->prof = 0;
+    ctx->stream = cs;
+    obb_status rc = OBB_OK;
+    cudaError_t e = cudaSuccess;
+    for (int32_t i = 0; i < n && rc == OBB_OK && e == cudaSuccess; ++i) {
+        obb_layer* L = B->layers[i];
+        LayerMem* M = mem_of(L);
+        const bool valid = M->members_valid;
+        for (int kind = 0; kind < 3 && rc == OBB_OK && e == cudaSuccess; ++kind) {
+            std::vector<CountReq> rq;
+            ctx->count_defer = kind < 2 ? &rq : nullptr;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) break;
+            const int64_t l0 = ctx->launches;
+            if (kind == 1) rc = rebuild_members(ctx, L);
+            if (rc == OBB_OK) rc = round_body(ctx, L, kind < 2 ? kPre : kPost);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+            if (e == cudaSuccess) e = e2;
+            cudaGraphExec_t x = nullptr;
+            if (rc == OBB_OK && e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+            if (g) cudaGraphDestroy(g);
+            const int32_t nk = (int32_t)(ctx->launches - l0);
+            if (kind == 0) {
+                B->g_pre[i] = x;
+                B->k_pre[i] = nk;
+                if (rq.size() == 1) B->req[i] = rq[0];
+                else if (rc == OBB_OK) rc = fail(ctx, OBB_ERR_STATE, "a batched round phase made other than one count");
+            } else if (kind == 1) {
+                B->g_pre_rebuild[i] = x;
+                B->k_pre_rebuild[i] = nk;
+            } else {
+                B->g_post[i] = x;
+                B->k_post[i] = nk;
+            }
+        }
+        M->members_valid = valid;   // the captures ran nothing
+    }
+    ctx->count_defer = nullptr;
+    ctx->stream = saved_stream;
+    ctx->prof = saved_prof;
+    ctx->launches = saved_launches;
+    cudaStreamDestroy(cs);
+    if (rc != OBB_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "capture of the batched rounds");
+    B->graphs = true;
+    return OBB_OK;
+}
+
 void batch_destroy(obb_batch* B)
 {
     if (!B) return;
     cudaStream_t s = B->ctx ? B->ctx->stream : nullptr;
+    for (auto* v : {&B->g_pre, &B->g_pre_rebuild, &B->g_post})
+        for (cudaGraphExec_t x : *v)
+            if (x) cudaGraphExecDestroy(x);
+    for (cudaStream_t p : B->par)
+        if (p) cudaStreamDestroy(p);
+    for (cudaEvent_t e : B->ev)
+        if (e) cudaEventDestroy(e);
     B->tables.release(s);
     B->scratch.release(s);
     B->stat_ptrs.release(s);
@@ -1722,9 +1803,42 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
     std::vector<CountReq> reqs;
     int64_t* const* d_ptrs = B->stat_ptrs.as<int64_t*>();
     int64_t* d_acc = reinterpret_cast<int64_t*>(B->stat_ptrs.as<char>() + sizeof(int64_t*) * n);
+    // rounds as per-layer graphs (not with surrogate screening, whose
+    // prediction allocates on first use)
+    bool use_graphs = true;
+    for (obb_layer* L : B->layers) use_graphs = use_graphs && !(L->mlp && L->topk > 0);
+    if (use_graphs && !B->graphs) OBB_TRY(batch_capture(ctx, B));
+    constexpr int P = obb_batch::kBatchStreams;
+    // the parallel streams start after everything on the context stream, and it waits for them
+    auto fork = [&]() -> cudaError_t {
+        cudaError_t x = cudaEventRecord(B->ev[P], s);
+        for (int p = 0; p < P && x == cudaSuccess; ++p) x = cudaStreamWaitEvent(B->par[p], B->ev[P], 0);
+        return x;
+    };
+    auto join = [&]() -> cudaError_t {
+        cudaError_t x = cudaSuccess;
+        for (int p = 0; p < P && x == cudaSuccess; ++p) {
+            x = cudaEventRecord(B->ev[p], B->par[p]);
+            if (x == cudaSuccess) x = cudaStreamWaitEvent(s, B->ev[p], 0);
+        }
+        return x;
+    };
     for (int r = 0; r < rounds; ++r) {
         reqs.clear();
-        {
+        if (use_graphs) {
+            OBB_CK(ctx, fork());
+            int j = 0;
+            for (int32_t i = 0; i < n; ++i) {
+                if (!active[i]) continue;
+                LayerMem* M = mem_of(B->layers[i]);
+                const bool rb = !M->members_valid;
+                OBB_CK(ctx, cudaGraphLaunch(rb ? B->g_pre_rebuild[i] : B->g_pre[i], B->par[j++ % P]));
+                note_launch(ctx, rb ? B->k_pre_rebuild[i] : B->k_pre[i]);
+                M->members_valid = true;
+                reqs.push_back(B->req[i]);
+            }
+            OBB_CK(ctx, join());
+        } else {
             DeferGuard guard(ctx, &reqs);
             for (int32_t i = 0; i < n; ++i) {
                 if (!active[i]) continue;
@@ -1734,11 +1848,18 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
             }
         }
         OBB_TRY(count_flush(ctx, reqs, B->tables, B->scratch));
-        for (int32_t i = 0; i < n; ++i) {
+        if (use_graphs) OBB_CK(ctx, fork());
+        for (int32_t i = 0, j = 0; i < n; ++i) {
             if (!active[i]) continue;
-            OBB_TRY(round_body(ctx, B->layers[i], kPost));
+            if (use_graphs) {
+                OBB_CK(ctx, cudaGraphLaunch(B->g_post[i], B->par[j++ % P]));
+                note_launch(ctx, B->k_post[i]);
+            } else {
+                OBB_TRY(round_body(ctx, B->layers[i], kPost));
+            }
             ++ran[i];
         }
+        if (use_graphs) OBB_CK(ctx, join());
         k_gather_accepted<<<(n + 127) / 128, 128, 0, s>>>(d_ptrs, n, d_acc);
         note_launch(ctx);
         OBB_CK(ctx, cudaMemcpyAsync(B->h_acc, d_acc, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
