@@ -277,9 +277,12 @@ struct obb_batch {
     // layer's counting request; replayed over kBatchStreams streams.
     static constexpr int kBatchStreams = 8;
     bool graphs = false;
-    std::vector<cudaGraphExec_t> g_pre, g_pre_rebuild, g_post;
-    std::vector<int32_t> k_pre, k_pre_rebuild, k_post;
-    std::vector<obbv::CountReq> req;
+    // the same for the covariance refit after the rounds (g_rpre*, g_rpost)
+    std::vector<cudaGraphExec_t> g_pre, g_pre_rebuild, g_post, g_rpre, g_rpre_rebuild, g_rpost;
+    std::vector<int32_t> k_pre, k_pre_rebuild, k_post, k_rpre, k_rpre_rebuild, k_rpost;
+    std::vector<obbv::CountReq> req, rreq;
+    obbv::DevBuf fin;                // the layers' outer-volume pointers and K, then their counters + totals
+    int64_t* h_fin = nullptr;        // pinned host copy of the counters + totals
     cudaStream_t par[kBatchStreams] = {};
     cudaEvent_t ev[kBatchStreams + 1] = {};
 };

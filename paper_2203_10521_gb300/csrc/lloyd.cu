@@ -1669,6 +1669,29 @@ __global__ void k_gather_accepted(int64_t* const* __restrict__ stats, int32_t n,
     if (i < n) out[i] = stats[i][kStAccepted];
 }
 
+// Block per layer of a batch: its device counters and its total outer
+// volume (as k_total sums it) into out[i][0..kStCount], one copy for all.
+__global__ void k_batch_totals(int64_t* const* __restrict__ stats, const uint64_t* const* __restrict__ obv,
+                               const int32_t* __restrict__ Ks, int64_t* __restrict__ out)
+{
+    const int32_t i = blockIdx.x;
+    const uint64_t* o = obv[i];
+    const int32_t K = Ks[i];
+    unsigned long long s = 0;
+    for (int32_t k = threadIdx.x; k < K; k += blockDim.x) s += o[k];
+    for (int q = 16; q > 0; q >>= 1) s += __shfl_xor_sync(0xffffffffu, s, q);
+    __shared__ unsigned long long sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    int64_t* row = out + (int64_t)i * (kStCount + 1);
+    if (threadIdx.x < kStCount) row[threadIdx.x] = stats[i][threadIdx.x];
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        row[kStCount] = (int64_t)t;
+    }
+}
+
 // resets the context's request list on every path out of a collecting phase
 struct DeferGuard {
     obb_ctx* ctx;
@@ -1687,6 +1710,19 @@ obb_status batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_b
     OBB_CK(ctx, B->stat_ptrs.reserve(sizeof(int64_t*) * n + sizeof(int64_t) * n, s));
     OBB_CK(ctx, cudaMemcpyAsync(B->stat_ptrs.p, ptrs.data(), sizeof(int64_t*) * n, cudaMemcpyHostToDevice, s));
     OBB_CK(ctx, cudaMallocHost((void**)&B->h_acc, sizeof(int64_t) * n));
+    // the totals of all layers in one launch: outer-volume pointers, K, then [n][kStCount + 1] results
+    std::vector<const uint64_t*> obv(n);
+    std::vector<int32_t> Ks(n);
+    for (int32_t i = 0; i < n; ++i) {
+        obv[i] = layers[i]->d_obv;
+        Ks[i] = layers[i]->K;
+    }
+    const size_t fo = (sizeof(uint64_t*) * n + sizeof(int32_t) * n + 255) / 256 * 256;
+    OBB_CK(ctx, B->fin.reserve(fo + sizeof(int64_t) * (kStCount + 1) * n, s));
+    OBB_CK(ctx, cudaMemcpyAsync(B->fin.p, obv.data(), sizeof(uint64_t*) * n, cudaMemcpyHostToDevice, s));
+    OBB_CK(ctx, cudaMemcpyAsync(B->fin.as<char>() + sizeof(uint64_t*) * n, Ks.data(), sizeof(int32_t) * n,
+                                cudaMemcpyHostToDevice, s));
+    OBB_CK(ctx, cudaMallocHost((void**)&B->h_fin, sizeof(int64_t) * (kStCount + 1) * n));
     OBB_CK(ctx, cudaStreamSynchronize(s));
     return OBB_OK;
 }
@@ -1699,13 +1735,12 @@ obb_status batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_b
 static obb_status batch_capture(obb_ctx* ctx, obb_batch* B)
 {
     const int32_t n = (int32_t)B->layers.size();
-    B->g_pre.assign(n, nullptr);
-    B->g_pre_rebuild.assign(n, nullptr);
-    B->g_post.assign(n, nullptr);
-    B->k_pre.assign(n, 0);
-    B->k_pre_rebuild.assign(n, 0);
-    B->k_post.assign(n, 0);
+    for (auto* v : {&B->g_pre, &B->g_pre_rebuild, &B->g_post, &B->g_rpre, &B->g_rpre_rebuild, &B->g_rpost})
+        v->assign(n, nullptr);
+    for (auto* v : {&B->k_pre, &B->k_pre_rebuild, &B->k_post, &B->k_rpre, &B->k_rpre_rebuild, &B->k_rpost})
+        v->assign(n, 0);
     B->req.assign(n, CountReq{});
+    B->rreq.assign(n, CountReq{});
     for (int p = 0; p < obb_batch::kBatchStreams; ++p)
         if (!B->par[p]) OBB_CK(ctx, cudaStreamCreateWithFlags(&B->par[p], cudaStreamNonBlocking));
     for (auto& e : B->ev)
@@ -1724,32 +1759,35 @@ static obb_status batch_capture(obb_ctx* ctx, obb_batch* B)
         obb_layer* L = B->layers[i];
         LayerMem* M = mem_of(L);
         const bool valid = M->members_valid;
-        for (int kind = 0; kind < 3 && rc == OBB_OK && e == cudaSuccess; ++kind) {
+        // kinds: 0 round before the count, 1 the same after a rebuild, 2 round
+        // after the count; 3, 4, 5 the same for the covariance refit
+        cudaGraphExec_t* gx[6] = {&B->g_pre[i], &B->g_pre_rebuild[i], &B->g_post[i],
+                                  &B->g_rpre[i], &B->g_rpre_rebuild[i], &B->g_rpost[i]};
+        int32_t* kx[6] = {&B->k_pre[i], &B->k_pre_rebuild[i], &B->k_post[i],
+                          &B->k_rpre[i], &B->k_rpre_rebuild[i], &B->k_rpost[i]};
+        for (int kind = 0; kind < 6 && rc == OBB_OK && e == cudaSuccess; ++kind) {
+            const bool before_count = kind % 3 < 2, refit = kind >= 3;
             std::vector<CountReq> rq;
-            ctx->count_defer = kind < 2 ? &rq : nullptr;
+            ctx->count_defer = before_count ? &rq : nullptr;
             e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) break;
             const int64_t l0 = ctx->launches;
-            if (kind == 1) rc = rebuild_members(ctx, L);
-            if (rc == OBB_OK) rc = round_body(ctx, L, kind < 2 ? kPre : kPost);
+            M->members_valid = kind % 3 != 1;   // rebuilt first in kinds 1 and 4
+            if (kind % 3 == 1) rc = rebuild_members(ctx, L);
+            if (rc == OBB_OK)
+                rc = refit ? refit_covariance(ctx, L, before_count ? kPre : kPost)
+                           : round_body(ctx, L, before_count ? kPre : kPost);
             cudaGraph_t g = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (e == cudaSuccess) e = e2;
             cudaGraphExec_t x = nullptr;
             if (rc == OBB_OK && e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
             if (g) cudaGraphDestroy(g);
-            const int32_t nk = (int32_t)(ctx->launches - l0);
-            if (kind == 0) {
-                B->g_pre[i] = x;
-                B->k_pre[i] = nk;
-                if (rq.size() == 1) B->req[i] = rq[0];
-                else if (rc == OBB_OK) rc = fail(ctx, OBB_ERR_STATE, "a batched round phase made other than one count");
-            } else if (kind == 1) {
-                B->g_pre_rebuild[i] = x;
-                B->k_pre_rebuild[i] = nk;
-            } else {
-                B->g_post[i] = x;
-                B->k_post[i] = nk;
+            *gx[kind] = x;
+            *kx[kind] = (int32_t)(ctx->launches - l0);
+            if (kind % 3 == 0 && rc == OBB_OK) {
+                if (rq.size() == 1) (refit ? B->rreq : B->req)[i] = rq[0];
+                else rc = fail(ctx, OBB_ERR_STATE, "a batched phase made other than one count");
             }
         }
         M->members_valid = valid;   // the captures ran nothing
@@ -1769,9 +1807,11 @@ void batch_destroy(obb_batch* B)
 {
     if (!B) return;
     cudaStream_t s = B->ctx ? B->ctx->stream : nullptr;
-    for (auto* v : {&B->g_pre, &B->g_pre_rebuild, &B->g_post})
+    for (auto* v : {&B->g_pre, &B->g_pre_rebuild, &B->g_post, &B->g_rpre, &B->g_rpre_rebuild, &B->g_rpost})
         for (cudaGraphExec_t x : *v)
             if (x) cudaGraphExecDestroy(x);
+    B->fin.release(s);
+    if (B->h_fin) cudaFreeHost(B->h_fin);
     for (cudaStream_t p : B->par)
         if (p) cudaStreamDestroy(p);
     for (cudaEvent_t e : B->ev)
@@ -1806,7 +1846,7 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
     // rounds as per-layer graphs (not with surrogate screening, whose
     // prediction allocates on first use)
     bool use_graphs = true;
-    for (obb_layer* L : B->layers) use_graphs = use_graphs && !(L->mlp && L->topk > 0);
+    for (obb_layer* L : B->layers) use_graphs = use_graphs && !L->mlp;
     if (use_graphs && !B->graphs) OBB_TRY(batch_capture(ctx, B));
     constexpr int P = obb_batch::kBatchStreams;
     // the parallel streams start after everything on the context stream, and it waits for them
@@ -1880,16 +1920,59 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
     }
     if (refit_mode & 1) {
         reqs.clear();
-        {
+        if (use_graphs) {
+            OBB_CK(ctx, fork());
+            for (int32_t i = 0; i < n; ++i) {
+                LayerMem* M = mem_of(B->layers[i]);
+                const bool rb = !M->members_valid;
+                OBB_CK(ctx, cudaGraphLaunch(rb ? B->g_rpre_rebuild[i] : B->g_rpre[i], B->par[i % P]));
+                note_launch(ctx, rb ? B->k_rpre_rebuild[i] : B->k_rpre[i]);
+                M->members_valid = true;
+                reqs.push_back(B->rreq[i]);
+            }
+            OBB_CK(ctx, join());
+        } else {
             DeferGuard guard(ctx, &reqs);
             for (obb_layer* L : B->layers) OBB_TRY(refit_covariance(ctx, L, kPre));
         }
         OBB_TRY(count_flush(ctx, reqs, B->tables, B->scratch));
-        for (obb_layer* L : B->layers) OBB_TRY(refit_covariance(ctx, L, kPost));
+        if (use_graphs) {
+            OBB_CK(ctx, fork());
+            for (int32_t i = 0; i < n; ++i) {
+                OBB_CK(ctx, cudaGraphLaunch(B->g_rpost[i], B->par[i % P]));
+                note_launch(ctx, B->k_rpost[i]);
+            }
+            OBB_CK(ctx, join());
+        } else {
+            for (obb_layer* L : B->layers) OBB_TRY(refit_covariance(ctx, L, kPost));
+        }
     }
     if (refit_mode & 2)
         for (obb_layer* L : B->layers) OBB_TRY(layer_box_update(ctx, L, 2, dsteps));
-    for (int32_t i = 0; i < n; ++i) OBB_TRY(layer_finish_stats(ctx, B->layers[i], ran[i], stats ? &stats[i] : nullptr));
+    if (stats) {
+        // every layer's counters and total in one launch and one copy
+        const size_t fo = (sizeof(uint64_t*) * n + sizeof(int32_t) * n + 255) / 256 * 256;
+        int64_t* d_fin = reinterpret_cast<int64_t*>(B->fin.as<char>() + fo);
+        k_batch_totals<<<n, 256, 0, s>>>(d_ptrs, B->fin.as<const uint64_t*>(),
+                                          reinterpret_cast<const int32_t*>(B->fin.as<char>() + sizeof(uint64_t*) * n),
+                                          d_fin);
+        note_launch(ctx);
+        OBB_CK(ctx, cudaMemcpyAsync(B->h_fin, d_fin, sizeof(int64_t) * (kStCount + 1) * n, cudaMemcpyDeviceToHost,
+                                    s));
+        OBB_TRY(check_device_error(ctx));
+        for (int32_t i = 0; i < n; ++i) {
+            const int64_t* h = B->h_fin + (int64_t)i * (kStCount + 1);
+            obb_step_stats& st = stats[i];
+            st.rounds_run = ran[i];
+            st.refits_accepted = (int32_t)h[kStRefits];
+            st.proposals = h[kStProposals];
+            st.moves = h[kStAccepted];
+            st.gain = h[kStGain];
+            st.box_evals = h[kStEvals];
+            st.points_counted = (uint64_t)h[kStPoints];
+            st.total_obv = (uint64_t)h[kStCount];
+        }
+    }
     return check_device_error(ctx);
 }
 
