@@ -701,8 +701,15 @@ def main():
             # streaming meshes to the GPU would keep them
             return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
 
+        def pinned_like(a):
+            # a page-locked array of a's dtype (structured ones included) and shape
+            buf = torch.empty(a.nbytes, dtype=torch.uint8).pin_memory().numpy()
+            return buf.view(a.dtype).reshape(a.shape)
+
         p_verts, p_tris, p_boxes = pinned(m.verts), pinned(m.tris), pinned(boxes)
         p_assign, p_parent, p_frames = pinned(leaf["assign"]), pinned(parent), pinned(leaf["frames"])
+        # the step's results land in page-locked host arrays too
+        p_out = {k: pinned_like(v) for k, v in ctx.layer_read(layer).items()}
         for _ in range(max(2, min(args.steps, 5))):
             torch.cuda.synchronize()
             ctx.profile_enable(2)
@@ -712,7 +719,7 @@ def main():
             cnt, pt = ctx.outer_volume(lt_, p_boxes, want_points=True)
             ly = ctx.layer_init(lt_, p_assign, p_parent, p_frames)
             st = ctx.lloyd_step(ly, rounds=16, refit=True)
-            out = ctx.layer_read(ly)
+            out = ctx.layer_read(ly, out=p_out)
             e2e_t.append(time.perf_counter() - t0)
             e2e_pts.append(ctx.profile_read()["count_points_in_domain"])
             ctx.profile_enable(0)

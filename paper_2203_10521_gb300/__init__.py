@@ -484,13 +484,26 @@ class Context:
         self.check(self.lib.obb_layer_parents(self.h, layer.h, p.ctypes.data_as(C.c_void_p)))
         return p
 
-    def layer_read(self, layer):
+    def layer_read(self, layer, out=None):
+        """The layer's state as host arrays; `out` may supply them (e.g. in
+        page-locked memory, which the copies reach faster): a dict with
+        assign int32 [T], frames float64 [K, 9], qboxes, boxes, obv uint64 [K]."""
         T, K = layer.lat.mesh.nt, layer.K
-        assign = np.zeros(T, np.int32)
-        frames = np.zeros((K, 9), np.float64)
-        q = np.zeros(K, QBOX_DTYPE)
-        boxes = np.zeros(K, BOX_DTYPE)
-        obv = np.zeros(K, np.uint64)
+        if out is not None:
+            want = {"assign": ((T,), np.int32), "frames": ((K, 9), np.float64), "qboxes": ((K,), QBOX_DTYPE),
+                    "boxes": ((K,), BOX_DTYPE), "obv": ((K,), np.uint64)}
+            for k, (shape, dt) in want.items():
+                a = out.get(k)
+                if not (isinstance(a, np.ndarray) and a.shape == shape and a.dtype == dt and a.flags.c_contiguous
+                        and a.flags.writeable):
+                    raise ValueError(f"out[{k!r}] must be a writeable contiguous {np.dtype(dt)} array of shape {shape}")
+            assign, frames, q, boxes, obv = (out[k] for k in want)
+        else:
+            assign = np.zeros(T, np.int32)
+            frames = np.zeros((K, 9), np.float64)
+            q = np.zeros(K, QBOX_DTYPE)
+            boxes = np.zeros(K, BOX_DTYPE)
+            obv = np.zeros(K, np.uint64)
         self.check(self.lib.obb_layer_read(self.h, layer.h, assign.ctypes.data_as(C.c_void_p),
                                            frames.ctypes.data_as(C.c_void_p), q.ctypes.data_as(C.c_void_p),
                                            boxes.ctypes.data_as(C.c_void_p), obv.ctypes.data_as(C.c_void_p), 0))

@@ -202,7 +202,7 @@ struct AdjMem {
     T* get(size_t n)
     {
         void* p = nullptr;
-        if (e == cudaSuccess) e = cudaMallocAsync(&p, sizeof(T) * (n > 0 ? n : 1), ctx->stream);
+        if (e == cudaSuccess) e = pool_alloc(&p, sizeof(T) * (n > 0 ? n : 1), ctx->stream);
         if (e == cudaSuccess) ptrs.push_back(p);
         return static_cast<T*>(p);
     }

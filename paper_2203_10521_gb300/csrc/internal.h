@@ -167,6 +167,19 @@ struct BatchReq {
     int32_t pad;
 };
 
+// Stream-ordered device allocation from the library's own memory pool of the
+// current device (created by obb_create; freed memory stays reserved in the
+// pool for the next allocation instead of going back to the driver at every
+// synchronisation).  Same contract as cudaMallocAsync; cudaFreeAsync frees.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+template <class T>
+inline cudaError_t pool_alloc(T** p, size_t bytes, cudaStream_t s)
+{
+    return pool_alloc(reinterpret_cast<void**>(p), bytes, s);
+}
+// creates (once per device) the pool pool_alloc draws on
+cudaError_t pool_init(int device);
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;

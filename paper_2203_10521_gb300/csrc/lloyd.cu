@@ -1131,7 +1131,7 @@ static LayerMem* mem_of(const obb_layer* L) { return static_cast<LayerMem*>(L->a
 template <class T>
 static cudaError_t dalloc(T** p, size_t n, cudaStream_t s)
 {
-    return cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(T) * (n > 0 ? n : 1), s);
+    return pool_alloc(reinterpret_cast<void**>(p), sizeof(T) * (n > 0 ? n : 1), s);
 }
 
 obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
@@ -1430,12 +1430,12 @@ static obb_status lloyd_step_graph(obb_ctx* ctx, obb_layer* L, int rounds, int r
             OBB_CK(ctx, cudaGraphExecDestroy(M->gexec));
             M->gexec = nullptr;
         }
-        if (!M->loop) OBB_CK(ctx, cudaMallocAsync((void**)&M->loop, sizeof(int64_t) * 4, s));
+        if (!M->loop) OBB_CK(ctx, pool_alloc((void**)&M->loop, sizeof(int64_t) * 4, s));
         if (!M->cscr_mem) {
             const int64_t cap = std::max<int64_t>({(int64_t)M->eval_cap, (int64_t)kProbes * K, (int64_t)K});
             const size_t pb = (sizeof(BoxPrep) * cap + 255) / 256 * 256;
             const size_t tb = sizeof(int64_t) * (2 * cap + 2 + cap / kScanBlock + 1);
-            OBB_CK(ctx, cudaMallocAsync(&M->cscr_mem, pb + tb, s));
+            OBB_CK(ctx, pool_alloc(&M->cscr_mem, pb + tb, s));
             char* b = static_cast<char*>(M->cscr_mem);
             M->cscr.prep = reinterpret_cast<BoxPrep*>(b);
             M->cscr.tiles = reinterpret_cast<int64_t*>(b + pb);
@@ -2044,7 +2044,7 @@ obb_status layer_moments(obb_ctx* ctx, obb_layer* L, int32_t compensated, double
     OBB_TRY(layer_members(ctx, L));
     const obb_lattice* lat = L->lat;
     double* d = nullptr;
-    OBB_CK(ctx, cudaMallocAsync((void**)&d, sizeof(double) * 10 * L->K, s));
+    OBB_CK(ctx, pool_alloc((void**)&d, sizeof(double) * 10 * L->K, s));
     if (compensated)
         k_moments<kNT, true><<<L->K, kNT, 0, s>>>(lat->mesh->d_verts, lat->mesh->d_tris, L->d_members, L->d_start,
                                                   lat->d_frame, d, nullptr);

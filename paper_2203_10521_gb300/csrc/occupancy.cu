@@ -416,10 +416,10 @@ obb_status rebuild_occupancy(obb_ctx* ctx, obb_lattice* lat)
     // rows along y and z: kept once a context counts along them, then refreshed
     // by every rebuild
     if (ctx->count_axis != 0 && !lat->d_words_y) {
-        OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words_y, sizeof(uint64_t) * lat->n_words, s));
-        OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words_z, sizeof(uint64_t) * lat->n_words, s));
-        OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_rank_y, sizeof(uint16_t) * lat->n_words, s));
-        OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_rank_z, sizeof(uint16_t) * lat->n_words, s));
+        OBB_CK(ctx, pool_alloc((void**)&lat->d_words_y, sizeof(uint64_t) * lat->n_words, s));
+        OBB_CK(ctx, pool_alloc((void**)&lat->d_words_z, sizeof(uint64_t) * lat->n_words, s));
+        OBB_CK(ctx, pool_alloc((void**)&lat->d_rank_y, sizeof(uint16_t) * lat->n_words, s));
+        OBB_CK(ctx, pool_alloc((void**)&lat->d_rank_z, sizeof(uint16_t) * lat->n_words, s));
         // the transposes never write the padding words past ceil(N / 64): zero them once
         OBB_CK(ctx, cudaMemsetAsync(lat->d_words_y, 0, sizeof(uint64_t) * lat->n_words, s));
         OBB_CK(ctx, cudaMemsetAsync(lat->d_words_z, 0, sizeof(uint64_t) * lat->n_words, s));
@@ -453,12 +453,12 @@ obb_status build_occupancy(obb_ctx* ctx, const obb_mesh* mesh, int32_t N, obb_la
     lat->n_words = (size_t)N * N * W;
     lat->frame.N = N;
     lat->frame.W = W;
-    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_frame, sizeof(LatticeFrame), s));
-    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_fixed, sizeof(int32_t) * 3 * mesh->nv, s));
-    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_words, sizeof(uint64_t) * lat->n_words, s));
-    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_cwords, sizeof(uint64_t) * lat->n_words, s));
-    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_rank, sizeof(uint16_t) * lat->n_words, s));
-    OBB_CK(ctx, cudaMallocAsync((void**)&lat->d_ref, sizeof(LatRef), s));
+    OBB_CK(ctx, pool_alloc((void**)&lat->d_frame, sizeof(LatticeFrame), s));
+    OBB_CK(ctx, pool_alloc((void**)&lat->d_fixed, sizeof(int32_t) * 3 * mesh->nv, s));
+    OBB_CK(ctx, pool_alloc((void**)&lat->d_words, sizeof(uint64_t) * lat->n_words, s));
+    OBB_CK(ctx, pool_alloc((void**)&lat->d_cwords, sizeof(uint64_t) * lat->n_words, s));
+    OBB_CK(ctx, pool_alloc((void**)&lat->d_rank, sizeof(uint16_t) * lat->n_words, s));
+    OBB_CK(ctx, pool_alloc((void**)&lat->d_ref, sizeof(LatRef), s));
     lat->ref = LatRef{lat->d_cwords, nullptr, nullptr, lat->d_rank, nullptr, nullptr, N, W};
     OBB_CK(ctx, cudaMemcpyAsync(lat->d_ref, &lat->ref, sizeof(LatRef), cudaMemcpyHostToDevice, s));
     OBB_TRY(rebuild_occupancy(ctx, lat));

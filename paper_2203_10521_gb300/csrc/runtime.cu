@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -13,6 +14,48 @@
 
 namespace obbv {
 
+namespace {
+std::mutex g_pool_mu;
+std::vector<cudaMemPool_t> g_pools;   // per device, created once, kept for the process
+}  // namespace
+
+cudaError_t pool_init(int device)
+{
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if ((int)g_pools.size() <= device) g_pools.resize(device + 1, nullptr);
+    if (g_pools[device]) return cudaSuccess;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;   // never hand freed memory back on synchronisation
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return e;
+    }
+    g_pools[device] = pool;
+    return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (dev < (int)g_pools.size()) pool = g_pools[dev];
+    }
+    if (!pool) return cudaMallocAsync(p, bytes, s);   // a device no context was created on
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 cudaError_t DevBuf::reserve(size_t n, cudaStream_t s)
 {
     if (n <= bytes && p) return cudaSuccess;
@@ -20,7 +63,7 @@ cudaError_t DevBuf::reserve(size_t n, cudaStream_t s)
     p = nullptr;
     bytes = 0;
     size_t want = n < 256 ? 256 : n + n / 4;
-    cudaError_t e = cudaMallocAsync(&p, want, s);
+    cudaError_t e = pool_alloc(&p, want, s);
     if (e == cudaSuccess) bytes = want;
     return e;
 }
@@ -124,7 +167,7 @@ obb_status to_device(obb_ctx* ctx, const T* src, size_t n, int on_device, HostTm
         *out = src;
         return OBB_OK;
     }
-    OBB_CK(ctx, cudaMallocAsync(&hold.p, sizeof(T) * n, ctx->stream));
+    OBB_CK(ctx, pool_alloc(&hold.p, sizeof(T) * n, ctx->stream));
     OBB_CK(ctx, cudaMemcpyAsync(hold.p, src, sizeof(T) * n, cudaMemcpyHostToDevice, ctx->stream));
     *out = static_cast<const T*>(hold.p);
     return OBB_OK;
@@ -142,7 +185,7 @@ obb_status out_device(obb_ctx* ctx, T* dst, size_t n, int on_device, HostTmp& ho
         *out = dst;
         return OBB_OK;
     }
-    OBB_CK(ctx, cudaMallocAsync(&hold.p, sizeof(T) * (n > 0 ? n : 1), ctx->stream));
+    OBB_CK(ctx, pool_alloc(&hold.p, sizeof(T) * (n > 0 ? n : 1), ctx->stream));
     *out = static_cast<T*>(hold.p);
     return OBB_OK;
 }
@@ -167,6 +210,7 @@ obb_status obb_create(obb_ctx** out, int32_t device, void* stream)
     if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return OBB_ERR_CUDA;
     if (device < 0 || device >= n) return OBB_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) return OBB_ERR_CUDA;
+    if (pool_init(device) != cudaSuccess) return OBB_ERR_CUDA;
     obb_ctx* c = new (std::nothrow) obb_ctx();
     if (!c) return OBB_ERR_OOM;
     c->device = device;

@@ -610,12 +610,12 @@ static obb_status mlp_reserve(obb_ctx* ctx, MlpImpl* P, int64_t B)
     float** bufs[] = {&P->h1, &P->h2, &P->h3, &P->d1, &P->d2, &P->d3};
     for (float** b : bufs) {
         if (*b) cudaFreeAsync(*b, s);
-        OBB_CK(ctx, cudaMallocAsync((void**)b, sizeof(float) * kH * B, s));
+        OBB_CK(ctx, pool_alloc((void**)b, sizeof(float) * kH * B, s));
     }
     if (P->y) cudaFreeAsync(P->y, s);
     if (P->dy) cudaFreeAsync(P->dy, s);
-    OBB_CK(ctx, cudaMallocAsync((void**)&P->y, sizeof(float) * B, s));
-    OBB_CK(ctx, cudaMallocAsync((void**)&P->dy, sizeof(float) * B, s));
+    OBB_CK(ctx, pool_alloc((void**)&P->y, sizeof(float) * B, s));
+    OBB_CK(ctx, pool_alloc((void**)&P->dy, sizeof(float) * B, s));
     P->cap = B;
     return OBB_OK;
 }
@@ -700,7 +700,7 @@ obb_status dev_in(obb_ctx* ctx, const T* src, size_t n, int on_device, void** ho
         *out = src;
         return OBB_OK;
     }
-    OBB_CK(ctx, cudaMallocAsync(hold, sizeof(T) * n, ctx->stream));
+    OBB_CK(ctx, pool_alloc(hold, sizeof(T) * n, ctx->stream));
     OBB_CK(ctx, cudaMemcpyAsync(*hold, src, sizeof(T) * n, cudaMemcpyHostToDevice, ctx->stream));
     *out = static_cast<const T*>(*hold);
     return OBB_OK;
@@ -729,13 +729,13 @@ obb_status obb_mlp_create(obb_ctx* ctx, uint64_t seed, obb_mlp** out)
     m->p = new MlpImpl();
     MlpImpl* P = m->p;
     cudaStream_t s = ctx->stream;
-    cudaError_t e = cudaMallocAsync((void**)&P->w, sizeof(float) * kParams, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->wh, sizeof(__half) * kParams, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->wtc, sizeof(__half) * kTcPacked, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->g, sizeof(float) * kParams, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->m, sizeof(float) * kParams, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->v, sizeof(float) * kParams, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P->loss, sizeof(float), s);
+    cudaError_t e = pool_alloc((void**)&P->w, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = pool_alloc((void**)&P->wh, sizeof(__half) * kParams, s);
+    if (e == cudaSuccess) e = pool_alloc((void**)&P->wtc, sizeof(__half) * kTcPacked, s);
+    if (e == cudaSuccess) e = pool_alloc((void**)&P->g, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = pool_alloc((void**)&P->m, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = pool_alloc((void**)&P->v, sizeof(float) * kParams, s);
+    if (e == cudaSuccess) e = pool_alloc((void**)&P->loss, sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->w, w.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->m, 0, sizeof(float) * kParams, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->v, 0, sizeof(float) * kParams, s);
@@ -802,7 +802,7 @@ obb_status obb_surrogate_features(obb_ctx* ctx, const obb_lattice* lat, const ob
     const obb_qbox* db;
     OBB_TRY(dev_in(ctx, boxes, (size_t)K, on_device, &hb, &db));
     float* df = feats;
-    if (!on_device) OBB_CK(ctx, cudaMallocAsync((void**)&df, sizeof(float) * kIn * K, ctx->stream));
+    if (!on_device) OBB_CK(ctx, pool_alloc((void**)&df, sizeof(float) * kIn * K, ctx->stream));
     OBB_CK(ctx, ctx->kdev.reserve(sizeof(int32_t), ctx->stream));
     OBB_TRY(set_device_int(ctx, ctx->kdev.as<int32_t>(), (int32_t)K));
     k_features<<<(unsigned)K, 128, 0, ctx->stream>>>(db, ctx->kdev.as<int32_t>(), lat->d_words, lat->frame.N,
@@ -828,7 +828,7 @@ obb_status obb_surrogate_targets(obb_ctx* ctx, const obb_qbox* boxes, const uint
     OBB_TRY(dev_in(ctx, boxes, (size_t)K, on_device, &hb, &db));
     OBB_TRY(dev_in(ctx, counts, (size_t)K, on_device, &hc, &dc));
     float* dout = out;
-    if (!on_device) OBB_CK(ctx, cudaMallocAsync((void**)&dout, sizeof(float) * K, ctx->stream));
+    if (!on_device) OBB_CK(ctx, pool_alloc((void**)&dout, sizeof(float) * K, ctx->stream));
     k_targets<<<(unsigned)((K + 255) / 256), 256, 0, ctx->stream>>>(dc, db, K, dout);
     note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());

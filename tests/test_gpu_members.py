@@ -120,3 +120,26 @@ def test_members_after_lloyd_moves(ctx, large):
     finally:
         layer.free()
         tree.free()
+
+
+def test_layer_read_into_caller_arrays(ctx, small):
+    """layer_read(out=...) fills the caller's arrays with what it returns
+    otherwise, and refuses arrays of the wrong shape or type."""
+    lat, T = small
+    K = 37
+    layer = ctx.layer_init(lat, _assignment(T, K, 5, True), np.zeros(K, np.int32))
+    try:
+        ref = ctx.layer_read(layer)
+        out = {k: np.full_like(v, 0) for k, v in ref.items()}
+        got = ctx.layer_read(layer, out=out)
+        for k in ref:
+            assert got[k] is out[k]
+            assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), k
+        bad = dict(out, obv=np.zeros(K + 1, np.uint64))
+        with pytest.raises(ValueError):
+            ctx.layer_read(layer, out=bad)
+        bad = dict(out, assign=np.zeros(T, np.int64))
+        with pytest.raises(ValueError):
+            ctx.layer_read(layer, out=bad)
+    finally:
+        layer.free()

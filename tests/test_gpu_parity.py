@@ -303,6 +303,10 @@ def test_mesh_validation(ctx):
     with pytest.raises(PK.ObbError) as e:
         ctx.mesh_create(m.verts, three)
     assert e.value.code == -2 and "shared by 3" in str(e.value)
+    # the reported edge is the smallest of the repeated triangle's edges
+    t = three[-1]
+    edges = sorted((min(t[q], t[(q + 1) % 3]), max(t[q], t[(q + 1) % 3])) for q in range(3))
+    assert f"edge ({edges[0][0]}, {edges[0][1]})" in str(e.value)
 
 
 # -------------------------------------------------------------------- Lloyd
