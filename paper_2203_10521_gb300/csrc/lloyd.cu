@@ -32,6 +32,8 @@
 namespace obbv {
 namespace {
 
+constexpr int kNT = 128;   // threads of the block-per-cluster kernels
+
 enum { kCtrCand = 0, kCtrEval, kCtrCount };
 
 constexpr int kMaxTopk = 16;   // candidates a surrogate may keep per source cluster
@@ -351,17 +353,90 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const int32_t*
 
 // ------------------------------------------------------- extents (a6)
 
-struct VT {
-    int64_t v;
-    int32_t t;
+// Per slab side of a cluster, in one pass over its members: the extreme
+// projection v1 with the smallest triangle t1 attaining it, and v2, the
+// extreme over every member but t1.  A member (v, t) that beats (v1, t1)
+// demotes v1 into v2; any other only updates v2.  Two partial states merge
+// the same way: the better best wins, and v2 is the extreme of both v2 and
+// the loser's v1.  Low sides minimise, high sides maximise.
+struct Top2 {
+    int64_t v1, v2;
+    int32_t t1;
 };
 
-__device__ __forceinline__ bool better(const VT& a, const VT& b, bool lowside)
+__device__ __forceinline__ bool beats(int64_t v, int32_t t, const Top2& b, bool lowside)
 {
-    if (a.v != b.v) return lowside ? (a.v < b.v) : (a.v > b.v);
-    return a.t < b.t;
+    if (v != b.v1) return lowside ? (v < b.v1) : (v > b.v1);
+    return t < b.t1;
 }
 
+__device__ __forceinline__ int64_t extreme(int64_t a, int64_t b, bool lowside) { return lowside ? min(a, b) : max(a, b); }
+
+__device__ __forceinline__ void top2_add(Top2& b, int64_t v, int32_t t, bool lowside)
+{
+    if (beats(v, t, b, lowside)) {
+        b.v2 = extreme(b.v2, b.v1, lowside);
+        b.v1 = v;
+        b.t1 = t;
+    } else {
+        b.v2 = extreme(b.v2, v, lowside);
+    }
+}
+
+__device__ __forceinline__ void top2_merge(Top2& a, const Top2& b, bool lowside)
+{
+    if (beats(b.v1, b.t1, a, lowside)) {
+        a.v2 = extreme(extreme(a.v2, b.v2, lowside), a.v1, lowside);
+        a.v1 = b.v1;
+        a.t1 = b.t1;
+    } else {
+        a.v2 = extreme(extreme(a.v2, b.v2, lowside), b.v1, lowside);
+    }
+}
+
+__device__ __forceinline__ Top2 top2_shfl(const Top2& x, int o)
+{
+    Top2 y;
+    y.v1 = (int64_t)__shfl_xor_sync(0xffffffffu, (long long)x.v1, o);
+    y.v2 = (int64_t)__shfl_xor_sync(0xffffffffu, (long long)x.v2, o);
+    y.t1 = __shfl_xor_sync(0xffffffffu, x.t1, o);
+    return y;
+}
+
+__device__ __forceinline__ void top2_init(Top2 (&b)[6])
+{
+    for (int s = 0; s < 6; ++s) {
+        const int64_t e = (s & 1) ? INT64_MIN : INT64_MAX;
+        b[s] = Top2{e, e, INT32_MAX};
+    }
+}
+
+// one thread's members [i0, b1) with stride st into its six states
+__device__ __forceinline__ void top2_members(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
+                                             const int32_t* __restrict__ members, const int32_t (&n)[9], int32_t i0,
+                                             int32_t b1, int32_t st, Top2 (&b)[6])
+{
+    for (int32_t i = i0; i < b1; i += st) {
+        const int32_t t = members[i];
+        int64_t dmin[3], dmax[3];
+        proj3(U, F, t, n, dmin, dmax);
+        for (int a = 0; a < 3; ++a) {
+            top2_add(b[2 * a], dmin[a], t, true);
+            top2_add(b[2 * a + 1], dmax[a], t, false);
+        }
+    }
+}
+
+__device__ __forceinline__ void top2_store(const Top2 (&b)[6], ClusterExt& e)
+{
+    for (int s = 0; s < 6; ++s) {
+        e.v1[s] = b[s].v1;
+        e.arg[s] = b[s].t1;
+        e.v2[s] = b[s].v2;
+    }
+}
+
+// Large clusters: a block of NT threads per cluster.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_extents(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
                                                 const int32_t* __restrict__ members,
@@ -369,71 +444,65 @@ __global__ void __launch_bounds__(NT) k_extents(const int32_t* __restrict__ U, c
                                                 const obb_qbox* __restrict__ q, ClusterExt* __restrict__ ext)
 {
     const int32_t k = blockIdx.x;
-    const int32_t b0 = start[k], b1 = start[k + 1];
     int32_t n[9];
     for (int i = 0; i < 9; ++i) n[i] = q[k].n[i];
-    VT best[6];
-    for (int s = 0; s < 6; ++s) best[s] = VT{(s & 1) ? INT64_MIN : INT64_MAX, INT32_MAX};
-    for (int32_t i = b0 + threadIdx.x; i < b1; i += NT) {
-        int32_t t = members[i];
-        int64_t dmin[3], dmax[3];
-        proj3(U, F, t, n, dmin, dmax);
-        for (int a = 0; a < 3; ++a) {
-            VT lo{dmin[a], t}, hi{dmax[a], t};
-            if (better(lo, best[2 * a], true)) best[2 * a] = lo;
-            if (better(hi, best[2 * a + 1], false)) best[2 * a + 1] = hi;
-        }
-    }
-    __shared__ VT sh[6][NT / 32];
-    __shared__ VT fin[6];
+    Top2 b[6];
+    top2_init(b);
+    top2_members(U, F, members, n, start[k] + threadIdx.x, start[k + 1], NT, b);
+    __shared__ Top2 sh[6][NT / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int s = 0; s < 6; ++s) {
-        VT x = best[s];
-        for (int o = 16; o > 0; o >>= 1) {
-            VT y{(int64_t)__shfl_xor_sync(0xffffffffu, (long long)x.v, o), __shfl_xor_sync(0xffffffffu, x.t, o)};
-            if (better(y, x, (s & 1) == 0)) x = y;
-        }
-        if (lane == 0) sh[s][w] = x;
+        for (int o = 16; o > 0; o >>= 1) top2_merge(b[s], top2_shfl(b[s], o), (s & 1) == 0);
+        if (lane == 0) sh[s][w] = b[s];
     }
     __syncthreads();
     if (threadIdx.x < 6) {
         const int s = threadIdx.x;
-        VT x = sh[s][0];
-        for (int i = 1; i < NT / 32; ++i)
-            if (better(sh[s][i], x, (s & 1) == 0)) x = sh[s][i];
-        fin[s] = x;
+        Top2 x = sh[s][0];
+        for (int i = 1; i < NT / 32; ++i) top2_merge(x, sh[s][i], (s & 1) == 0);
+        ext[k].v1[s] = x.v1;
+        ext[k].arg[s] = x.t1;
+        ext[k].v2[s] = x.v2;
     }
-    __syncthreads();
-    // second pass: extreme over members other than the arg of each side
-    int64_t v2[6];
-    for (int s = 0; s < 6; ++s) v2[s] = (s & 1) ? INT64_MIN : INT64_MAX;
-    for (int32_t i = b0 + threadIdx.x; i < b1; i += NT) {
-        int32_t t = members[i];
-        int64_t dmin[3], dmax[3];
-        proj3(U, F, t, n, dmin, dmax);
-        for (int a = 0; a < 3; ++a) {
-            if (t != fin[2 * a].t) v2[2 * a] = min(v2[2 * a], dmin[a]);
-            if (t != fin[2 * a + 1].t) v2[2 * a + 1] = max(v2[2 * a + 1], dmax[a]);
-        }
+}
+
+// Small clusters: G lanes of a warp per cluster (32 / G clusters a warp), no
+// block barrier.
+template <int G>
+__global__ void __launch_bounds__(128) k_extents_small(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
+                                                       const int32_t* __restrict__ members,
+                                                       const int32_t* __restrict__ start, int32_t K,
+                                                       const obb_qbox* __restrict__ q, ClusterExt* __restrict__ ext)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t k = (int32_t)(g / G);
+    const int32_t l = (int32_t)(g % G);
+    const bool live = k < K;   // every lane of the warp takes part in the shuffles
+    int32_t n[9];
+    for (int i = 0; i < 9; ++i) n[i] = live ? q[k].n[i] : 0;
+    Top2 b[6];
+    top2_init(b);
+    if (live) top2_members(U, F, members, n, start[k] + l, start[k + 1], G, b);
+    for (int s = 0; s < 6; ++s)
+        for (int o = G / 2; o > 0; o >>= 1) top2_merge(b[s], top2_shfl(b[s], o), (s & 1) == 0);
+    if (live && l == 0) top2_store(b, ext[k]);
+}
+
+// the extents of a layer's clusters, by their average size
+void launch_extents(obb_ctx* ctx, const obb_layer* L, cudaStream_t s)
+{
+    const obb_lattice* lat = L->lat;
+    const int32_t K = L->K;
+    if (L->T <= (int64_t)512 * K) {
+        constexpr int G = 8;
+        const int64_t th = (int64_t)K * G;
+        k_extents_small<G><<<(unsigned)((th + 127) / 128), 128, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members,
+                                                                         L->d_start, K, L->d_q, L->d_ext);
+    } else {
+        k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, L->d_q,
+                                         L->d_ext);
     }
-    __shared__ int64_t sh2[6][NT / 32];
-    for (int s = 0; s < 6; ++s) {
-        int64_t x = v2[s];
-        for (int o = 16; o > 0; o >>= 1) {
-            int64_t y = (int64_t)__shfl_xor_sync(0xffffffffu, (long long)x, o);
-            x = (s & 1) ? max(x, y) : min(x, y);
-        }
-        if (lane == 0) sh2[s][w] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        const int s = threadIdx.x;
-        int64_t x = sh2[s][0];
-        for (int i = 1; i < NT / 32; ++i) x = (s & 1) ? max(x, sh2[s][i]) : min(x, sh2[s][i]);
-        ext[k].v1[s] = fin[s].v;
-        ext[k].arg[s] = fin[s].t;
-        ext[k].v2[s] = x;
-    }
+    note_launch(ctx);
 }
 
 // ------------------------------------------------------- candidates (a7)
@@ -1075,8 +1144,6 @@ __global__ void k_probe_apply(const unsigned long long* __restrict__ best, const
     }
 }
 
-constexpr int kNT = 128;
-
 }  // namespace
 
 // -------------------------------------------------------------- host side
@@ -1341,8 +1408,7 @@ static obb_status round_body(obb_ctx* ctx, obb_layer* L, int phase = kWhole)
     const obb_qbox* evals = screened ? M->evals2 : M->evals;
     const int32_t* n_eval = screened ? M->n2 : M->ctr + kCtrEval;
     if (phase & kPre) {
-        k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, L->d_q, L->d_ext);
-        note_launch(ctx);
+        launch_extents(ctx, L, s);
         OBB_CK(ctx, cudaMemsetAsync(M->ctr, 0, sizeof(int32_t) * kCtrCount, s));
         OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
         k_candidates<<<(unsigned)((L->T + 127) / 128), 128, 0, s>>>(

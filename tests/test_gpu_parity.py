@@ -317,8 +317,11 @@ def _wedges(m, K):
     return np.minimum(((ang + np.pi) / (2 * np.pi) * K).astype(np.int32), K - 1)
 
 
-@pytest.mark.parametrize("K,rounds", [(8, 1), (16, 3), (16, 16)])
+@pytest.mark.parametrize("K,rounds", [(4, 2), (8, 1), (16, 3), (16, 16)])
 def test_lloyd_moves_bit_exact(ctx, torus_setup, K, rounds):
+    """The partition rounds' moves, boxes and statistics equal the oracle's
+    (Eq. 11-13); K = 4 (1,024 triangles a cluster) takes the extents kernel
+    with a block per cluster, the others the one with 8 lanes per cluster."""
     m, mesh, lat, P = torus_setup
     assign = _wedges(m, K)
     parent = (np.arange(K) // 2).astype(np.int32)
