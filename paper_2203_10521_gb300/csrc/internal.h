@@ -66,7 +66,7 @@ struct LatticeFrame {
     double h[3];
     double hmax;
     double center[3];   // lo + N h / 2
-    double inv_h[3];    // 1 / h, correctly rounded (the snap's fast path)
+    double s256[3];     // 256 rn(1 / h) (the snap's fast path)
     int32_t N;
     int32_t W;          // uint64 words per row (even)
 };

@@ -82,18 +82,19 @@ __global__ void k_frame(const uint32_t* keys, int32_t N, LatticeFrame* f, int32_
     f->hmax = hm;
     for (int b = 0; b < 3; ++b) {
         f->center[b] = __dadd_rn(f->lo[b], __dmul_rn(0.5 * N, f->h[b]));
-        f->inv_h[b] = f->h[b] > 0.0 ? __drcp_rn(f->h[b]) : 0.0;
+        f->s256[b] = f->h[b] > 0.0 ? __dmul_rn(__drcp_rn(f->h[b]), 256.0) : 0.0;   // 256 rn(1/h), exact scaling
     }
     f->N = N;
     f->W = 2 * ((N + 127) / 128);
 }
 
-// U = rint(((x - lo) / h - 1/2) 256), each step a correctly rounded FP64 op.
-// The quotient through the reciprocal, d (1/h), is within 2 ulps of d / h,
-// so while d / h < 2^12 (|(q - 1/2) 256| < 2^20; a vertex of the lattice's
-// own frame has d / h <= N + 1 <= 2049) the value (q - 1/2) 256 moves by
-// less than 2^-30: whenever it lies farther than 2^-29 from a half-integer
-// both round to the same integer; otherwise, or out of that range, the
+// U = rint(((x - lo) / h - 1/2) 256), each step a correctly rounded FP64 op
+// (the definition: Q = 256 rn(rn(d / h) - 1/2), d = x - lo).  With
+// X = d / h <= 2^12 (|Q| < 2^20; a vertex of the lattice's own frame has
+// X <= N + 1 <= 2049), Q lies within 2^-32 of 256 (X - 1/2), and so does the
+// fast value q = rn(d s256 - 128), s256 = 256 rn(1/h): one fused
+// multiply-add, within 2^-31 of Q.  Whenever q lies farther than 2^-29 from
+// a half-integer, rint(q) = rint(Q); otherwise, or out of that range, the
 // defining sequence, with the division, decides.
 __global__ void k_snap(const float* __restrict__ V, int64_t nv, const LatticeFrame* __restrict__ f,
                        int32_t* __restrict__ U)
@@ -102,14 +103,15 @@ __global__ void k_snap(const float* __restrict__ V, int64_t nv, const LatticeFra
     if (i >= 3 * nv) return;
     int b = (int)(i % 3);
     const double d = __dsub_rn((double)V[i], f->lo[b]);
-    double q = __dmul_rn(__dsub_rn(__dmul_rn(d, f->inv_h[b]), 0.5), 256.0);
-    const double t = q - floor(q);   // exact
-    if (!(fabs(t - 0.5) > 0x1p-29) || !(fabs(q) < 0x1p20)) {
+    double q = __fma_rn(d, f->s256[b], -128.0);
+    double r = rint(q);
+    if (!(fabs(q - r) < 0.5 - 0x1p-29) || !(fabs(q) < 0x1p20)) {
         q = __ddiv_rn(d, f->h[b]);
         q = __dsub_rn(q, 0.5);
         q = __dmul_rn(q, 256.0);
+        r = rint(q);
     }
-    U[i] = (int32_t)rint(q);
+    U[i] = (int32_t)r;
 }
 
 // orient2d in the (y, z) plane; coordinates are |U| <= 2^19, so every factor

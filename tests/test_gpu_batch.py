@@ -115,3 +115,40 @@ def test_batched_moves_match_oracle(ctx):
     for _, mesh, lat in probs:
         lat.free()
         mesh.free()
+
+
+def test_batch_with_a_screened_layer_equals_per_layer_steps(ctx):
+    """A batch holding a surrogate-screened layer (which the batch steps
+    without its per-layer graphs) still leaves every layer as the per-layer
+    iterations do, screened layer included."""
+    meshes = [mn for mn in M.sdf_batch(32, seed=3000) if mn[0].n_tris <= 8000][:3]
+    assert len(meshes) == 3
+    mlp = ctx.mlp_create(7)
+    objs, As, Bs = [], [], []
+    for i, (m, N) in enumerate(meshes):
+        mesh = ctx.mesh_create(m.verts, m.tris)
+        lat = ctx.build_occupancy(mesh, N)
+        child, parent = fresh_leaf_split(ctx, lat, 5)
+        A, B = ctx.layer_init(lat, child, parent), ctx.layer_init(lat, child, parent)
+        if i == 1:
+            ctx.layer_set_surrogate(A, mlp, 2)
+            ctx.layer_set_surrogate(B, mlp, 2)
+        As.append(A)
+        Bs.append(B)
+        objs.append((mesh, lat))
+    batch = ctx.batch_create(As)
+    sa = ctx.batch_lloyd_step(batch, rounds=16, refit=1)
+    sb = [ctx.lloyd_step(B, rounds=16, refit=1) for B in Bs]
+    assert sa == sb
+    for A, B in zip(As, Bs):
+        ga, gb = ctx.layer_read(A), ctx.layer_read(B)
+        for key in ("assign", "frames", "obv"):
+            assert np.array_equal(ga[key], gb[key]), key
+    batch.free()
+    for A, B in zip(As, Bs):
+        A.free()
+        B.free()
+    for mesh, lat in objs:
+        lat.free()
+        mesh.free()
+    mlp.free()
