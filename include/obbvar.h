@@ -92,7 +92,11 @@ typedef struct {
 
 /* Create a context on CUDA device `device`, enqueuing on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The stream may be
- * one owned by another framework; it must outlive the context. */
+ * one owned by another framework; it must outlive the context.  The first
+ * context on a device creates the library's device memory pool, from which
+ * every library allocation on that device comes; memory the library frees
+ * stays reserved in the pool for its next allocations (until the process
+ * ends).  The device's default memory pool is not touched. */
 obb_status obb_create(obb_ctx** out, int32_t device, void* stream);
 /* Point the context at another stream (same device). */
 obb_status obb_set_stream(obb_ctx* ctx, void* stream);
