@@ -278,6 +278,9 @@ struct obb_layer {
     int32_t topk = 0;                // candidates kept per source cluster when screening
 };
 
+#ifndef OBB_BATCH_STREAMS
+#define OBB_BATCH_STREAMS 16   // streams a batched step spreads its layers' graphs over
+#endif
 struct obb_batch {
     obb_ctx* ctx = nullptr;
     std::vector<obb_layer*> layers;
@@ -288,7 +291,7 @@ struct obb_batch {
     // phase before the counting launch (with and without the member-list
     // rebuild) and the phase after it, with their kernel counts and the
     // layer's counting request; replayed over kBatchStreams streams.
-    static constexpr int kBatchStreams = 8;
+    static constexpr int kBatchStreams = OBB_BATCH_STREAMS;
     bool graphs = false;
     // the same for the covariance refit after the rounds (g_rpre*, g_rpost)
     std::vector<cudaGraphExec_t> g_pre, g_pre_rebuild, g_post, g_rpre, g_rpre_rebuild, g_rpost;
