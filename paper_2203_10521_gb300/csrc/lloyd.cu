@@ -507,27 +507,32 @@ void launch_extents(obb_ctx* ctx, const obb_layer* L, cudaStream_t s)
 
 // ------------------------------------------------------- candidates (a7)
 
+// One thread per (cluster s, slab side): only a triangle that alone attains
+// a side of its cluster's box shrinks the box when it leaves, so the
+// candidates are the clusters' side extremes.  A triangle extreme on several
+// sides is taken by the thread of the first of them, and its shrunk box moves
+// all those sides.
 __global__ void k_candidates(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
-                             const int32_t* __restrict__ adj, int64_t T, const int32_t* __restrict__ assign,
+                             const int32_t* __restrict__ adj, int32_t K, const int32_t* __restrict__ assign,
                              const int32_t* __restrict__ parent, const int32_t* __restrict__ size,
                              const ClusterExt* __restrict__ ext, const obb_qbox* __restrict__ q,
                              Cand* __restrict__ cand, obb_qbox* __restrict__ evals, int32_t* __restrict__ ctr,
                              int32_t cand_cap, int32_t eval_cap, int32_t* err)
 {
-    int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (tt >= T) return;
-    const int32_t t = (int32_t)tt;
-    const int32_t s = assign[t];
+    const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= 6 * (int64_t)K) return;
+    const int32_t s = (int32_t)(id / 6);
+    const int my_side = (int)(id - 6 * (int64_t)s);
     if (size[s] < 2) return;
     const ClusterExt& e = ext[s];
+    const int32_t t = e.arg[my_side];
+    if (e.v2[my_side] == e.v1[my_side]) return;
     obb_qbox shr = q[s];
-    bool changed = false;
     for (int side = 0; side < 6; ++side)
         if (e.arg[side] == t && e.v2[side] != e.v1[side]) {
+            if (side < my_side) return;   // the first such side's thread takes t
             shr.b[side] = e.v2[side];
-            changed = true;
         }
-    if (!changed) return;
     int32_t ks[3];
     int nk = 0;
     const int32_t ps = parent[s];
@@ -1411,8 +1416,8 @@ static obb_status round_body(obb_ctx* ctx, obb_layer* L, int phase = kWhole)
         launch_extents(ctx, L, s);
         OBB_CK(ctx, cudaMemsetAsync(M->ctr, 0, sizeof(int32_t) * kCtrCount, s));
         OBB_CK(ctx, cudaMemsetAsync(L->d_best, 0, sizeof(unsigned long long) * K, s));
-        k_candidates<<<(unsigned)((L->T + 127) / 128), 128, 0, s>>>(
-            lat->d_fixed, mesh->d_tris, mesh->d_adj, L->T, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
+        k_candidates<<<(unsigned)((6 * (int64_t)K + 127) / 128), 128, 0, s>>>(
+            lat->d_fixed, mesh->d_tris, mesh->d_adj, K, L->d_assign, L->d_parent, L->d_size, L->d_ext, L->d_q,
             M->cand, M->evals, M->ctr, M->cand_cap, M->eval_cap, ctx->d_err);
         note_launch(ctx);
         if (screened) {
