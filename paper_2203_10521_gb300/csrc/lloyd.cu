@@ -466,8 +466,8 @@ __global__ void __launch_bounds__(NT) k_extents(const int32_t* __restrict__ U, c
     }
 }
 
-// Small clusters: G lanes of a warp per cluster (32 / G clusters a warp), no
-// block barrier.
+// Small clusters: G lanes of a warp per cluster (32 / G clusters a warp; G
+// divides 32), no block barrier.
 template <int G>
 __global__ void __launch_bounds__(128) k_extents_small(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
                                                        const int32_t* __restrict__ members,
@@ -488,13 +488,14 @@ __global__ void __launch_bounds__(128) k_extents_small(const int32_t* __restrict
     if (live && l == 0) top2_store(b, ext[k]);
 }
 
-// the extents of a layer's clusters, by their average size
+// the extents of a layer's clusters, by their average size: a warp a
+// cluster up to 1,024 triangles, else a block
 void launch_extents(obb_ctx* ctx, const obb_layer* L, cudaStream_t s)
 {
     const obb_lattice* lat = L->lat;
     const int32_t K = L->K;
-    if (L->T <= (int64_t)512 * K) {
-        constexpr int G = 8;
+    if (L->T <= (int64_t)1024 * K) {
+        constexpr int G = 32;
         const int64_t th = (int64_t)K * G;
         k_extents_small<G><<<(unsigned)((th + 127) / 128), 128, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members,
                                                                          L->d_start, K, L->d_q, L->d_ext);

@@ -317,11 +317,12 @@ def _wedges(m, K):
     return np.minimum(((ang + np.pi) / (2 * np.pi) * K).astype(np.int32), K - 1)
 
 
-@pytest.mark.parametrize("K,rounds", [(4, 2), (8, 1), (16, 3), (16, 16)])
+@pytest.mark.parametrize("K,rounds", [(2, 2), (8, 1), (16, 3), (16, 16), (48, 3)])
 def test_lloyd_moves_bit_exact(ctx, torus_setup, K, rounds):
     """The partition rounds' moves, boxes and statistics equal the oracle's
-    (Eq. 11-13); K = 4 (1,024 triangles a cluster) takes the extents kernel
-    with a block per cluster, the others the one with 8 lanes per cluster."""
+    (Eq. 11-13) on the 4,096-triangle torus; the cluster extents run with a
+    block per cluster at K = 2 (2,048 triangles a cluster) and a warp per
+    cluster at K = 8, 16 and 48 (512 to 85)."""
     m, mesh, lat, P = torus_setup
     assign = _wedges(m, K)
     parent = (np.arange(K) // 2).astype(np.int32)
