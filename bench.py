@@ -716,13 +716,14 @@ def main():
         p_assign, p_parent, p_frames = pinned(leaf["assign"]), pinned(parent), pinned(leaf["frames"])
         # the step's results land in page-locked host arrays too
         p_out = {k: pinned_like(v) for k, v in ctx.layer_read(layer).items()}
+        p_cnt, p_pts = pinned_like(np.zeros(len(boxes), np.uint64)), pinned_like(np.zeros(len(boxes), np.uint64))
         for _ in range(max(2, min(args.steps, 5))):
             torch.cuda.synchronize()
             ctx.profile_enable(2)
             t0 = time.perf_counter()
             mh = ctx.mesh_create(p_verts, p_tris)
             lt_ = ctx.build_occupancy(mh, N)
-            cnt, pt = ctx.outer_volume(lt_, p_boxes, want_points=True)
+            cnt, pt = ctx.outer_volume(lt_, p_boxes, counts=p_cnt, points=p_pts)
             ly = ctx.layer_init(lt_, p_assign, p_parent, p_frames)
             st = ctx.lloyd_step(ly, rounds=16, refit=True)
             out = ctx.layer_read(ly, out=p_out)

@@ -410,6 +410,21 @@ class Context:
             return torch.empty(K * itemsize, dtype=torch.uint8, device=f"cuda:{self.device}")
         return np.zeros(K, dtype=dtype)
 
+    def _check_out(self, name, a, K, dev):
+        """An output of K 8-byte integers on the inputs' side: a contiguous
+        CUDA tensor of this context's device, or a writeable contiguous numpy
+        array on the host."""
+        if dev:
+            ok = (_is_torch(a) and a.is_cuda and a.device.index == self.device and a.is_contiguous()
+                  and a.element_size() == 8 and a.numel() >= K)
+            want = f"a contiguous 8-byte CUDA tensor on cuda:{self.device} with at least {K} elements"
+        else:
+            ok = (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.flags.writeable and a.itemsize == 8
+                  and a.size >= K)
+            want = f"a writeable contiguous numpy array of 8-byte integers with at least {K} elements"
+        if not ok:
+            raise ValueError(f"{name} must be {want}")
+
     def _ov(self, fn, lat, p, dev, K, counts, points, want_points):
         import_torch = dev
         if counts is None:
@@ -424,6 +439,9 @@ class Context:
                 points = torch.empty(K, dtype=torch.int64, device=f"cuda:{self.device}")
             else:
                 points = np.zeros(K, dtype=np.uint64)
+        for name, a in (("counts", counts), ("points", points)):
+            if a is not None:
+                self._check_out(name, a, K, dev)
         pc = C.c_void_p(counts.data_ptr()) if dev else counts.ctypes.data_as(C.c_void_p)
         pp = None
         if points is not None:

@@ -143,3 +143,28 @@ def test_layer_read_into_caller_arrays(ctx, small):
             ctx.layer_read(layer, out=bad)
     finally:
         layer.free()
+
+
+def test_outer_volume_refuses_unusable_outputs(ctx, small):
+    """Caller-provided counts / points must hold K 8-byte integers on the
+    boxes' side; anything else is refused before the library writes."""
+    import torch
+    lat, _ = small
+    boxes = np.zeros(5, dtype=[("c", "<f4", (3,)), ("axis0", "<f4", (3,)), ("axis1", "<f4", (3,)),
+                               ("half", "<f4", (3,))])
+    boxes["axis0"] = (1, 0, 0)
+    boxes["axis1"] = (0, 1, 0)
+    boxes["half"] = 0.2
+    ref = ctx.outer_volume(lat, boxes)
+    out = np.zeros(5, np.uint64)
+    got = ctx.outer_volume(lat, boxes, counts=out)
+    assert got is out and np.array_equal(out, ref)
+    for bad in (np.zeros(4, np.uint64), np.zeros(5, np.int32), np.zeros(10, np.uint64)[::2],
+                torch.zeros(5, dtype=torch.int64, device="cuda")):
+        with pytest.raises(ValueError):
+            ctx.outer_volume(lat, boxes, counts=bad)
+    d = torch.from_numpy(boxes.view(np.float32).reshape(5, 12)).cuda()
+    with pytest.raises(ValueError):
+        ctx.outer_volume(lat, d, counts=torch.zeros(4, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        ctx.outer_volume(lat, d, counts=np.zeros(5, np.uint64))
