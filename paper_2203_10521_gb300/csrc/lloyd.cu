@@ -351,6 +351,41 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const int32_t*
     }
 }
 
+// Member lists after one round's accepted moves (each cluster lost at most
+// one triangle, mv[c], or gained at most one, mv[K + c]; -1 = none): a warp
+// per cluster copies its old segment to its new start, dropping the leaver
+// and opening the place of the joiner, which keeps every segment ascending
+// -- the stable sort of the new assignment.  Consumes the records (-1).
+__global__ void k_members_update(const int32_t* __restrict__ old_members, const int32_t* __restrict__ old_start,
+                                 const int32_t* __restrict__ new_start, int32_t* __restrict__ mv, int32_t K,
+                                 int32_t* __restrict__ out)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t c = (int32_t)(g >> 5);
+    const int lane = (int)(g & 31);
+    if (c >= K) return;   // warp-uniform
+    const int32_t so = old_start[c], n = old_start[c + 1] - so, sn = new_start[c];
+    const int32_t t_out = mv[c], t_in = mv[K + c];
+    int32_t below = 0;   // old members below the joiner, the leaver excepted
+    for (int32_t b = 0; b < n; b += 32) {
+        const int32_t i = b + lane;
+        if (i >= n) break;
+        const int32_t x = old_members[so + i];
+        if (x == t_out) continue;
+        const int32_t dst = i - (t_out >= 0 && x > t_out ? 1 : 0) + (t_in >= 0 && x > t_in ? 1 : 0);
+        out[sn + dst] = x;
+        below += t_in >= 0 && x < t_in ? 1 : 0;
+    }
+    if (t_in >= 0) {
+        for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+        if (lane == 0) out[sn + below] = t_in;
+    }
+    if (lane == 0) {
+        mv[c] = -1;
+        mv[K + c] = -1;
+    }
+}
+
 // ------------------------------------------------------- extents (a6)
 
 // Per slab side of a cluster, in one pass over its members: the extreme
@@ -631,7 +666,8 @@ __global__ void k_accept(const Cand* __restrict__ cand, const int32_t* __restric
                          const unsigned long long* __restrict__ best, const obb_qbox* __restrict__ evals,
                          const uint64_t* __restrict__ ecount, int32_t* __restrict__ assign,
                          obb_qbox* __restrict__ q, uint64_t* __restrict__ obv, int32_t* __restrict__ size,
-                         int64_t* __restrict__ stats, uint8_t* __restrict__ dirty, int32_t* __restrict__ level)
+                         int64_t* __restrict__ stats, uint8_t* __restrict__ dirty, int32_t* __restrict__ level,
+                         int32_t K, int32_t* __restrict__ mv)
 {
     int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= ctr[kCtrCand]) return;
@@ -640,6 +676,9 @@ __global__ void k_accept(const Cand* __restrict__ cand, const int32_t* __restric
     const int32_t k = c.k[c.best];
     if (best[c.s] != c.key || best[k] != c.key) return;
     assign[c.t] = k;
+    // accepted moves touch disjoint clusters: one leaver or one joiner each
+    mv[c.s] = c.t;
+    mv[K + k] = c.t;
     for (int i = 0; i < 6; ++i) q[c.s].b[i] = evals[c.e_shr].b[i];
     obv[c.s] = ecount[c.e_shr];
     const int32_t eg = c.e_gro[c.best];
@@ -1197,6 +1236,12 @@ struct LayerMem {
     void* cscr_mem = nullptr;
     int64_t g_round = 0, g_rebuild = 0, g_post = 0;   // kernel launches per round, per rebuild, after the loop
     bool members_valid = false;
+    // incremental member lists: mv [2K] the last round's leavers and joiners
+    // per cluster (-1 = none), the new list and starts built beside the old
+    int32_t* mv = nullptr;
+    int32_t* mnew = nullptr;   // [T]
+    int32_t* snew = nullptr;   // [K + 1]
+    bool incr_ok = false;      // the lists were valid before the moves mv records (and nothing else moved)
 };
 
 static LayerMem* mem_of(const obb_layer* L) { return static_cast<LayerMem*>(L->aux); }
@@ -1207,12 +1252,44 @@ static cudaError_t dalloc(T** p, size_t n, cudaStream_t s)
     return pool_alloc(reinterpret_cast<void**>(p), sizeof(T) * (n > 0 ? n : 1), s);
 }
 
+static obb_status sort_members(obb_ctx* ctx, obb_layer* L);
+
+// The member lists after the moves of one round (mv), from the lists
+// before them: new starts from the sizes k_accept kept, the segments moved
+// into place by k_members_update, copied back (the lists' addresses are
+// fixed: captured graphs read them).
+static obb_status update_members(obb_ctx* ctx, obb_layer* L)
+{
+    cudaStream_t s = ctx->stream;
+    LayerMem* M = mem_of(L);
+    const int32_t K = L->K;
+    launch_scan_i32(ctx, L->d_size, M->snew, M->dK);
+    k_members_update<<<(unsigned)(((int64_t)K * 32 + 255) / 256), 256, 0, s>>>(L->d_members, L->d_start, M->snew,
+                                                                               M->mv, K, M->mnew);
+    note_launch(ctx);
+    OBB_CK(ctx, cudaMemcpyAsync(L->d_members, M->mnew, sizeof(int32_t) * L->T, cudaMemcpyDeviceToDevice, s));
+    OBB_CK(ctx, cudaMemcpyAsync(L->d_start, M->snew, sizeof(int32_t) * (K + 1), cudaMemcpyDeviceToDevice, s));
+    OBB_CK(ctx, cudaGetLastError());
+    M->members_valid = true;
+    return OBB_OK;
+}
+
 obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
+{
+    LayerMem* M = mem_of(L);
+    if (M->incr_ok) return update_members(ctx, L);
+    return sort_members(ctx, L);
+}
+
+// The member lists from scratch: a stable radix sort of the triangles by
+// cluster; the move records are cleared.
+static obb_status sort_members(obb_ctx* ctx, obb_layer* L)
 {
     cudaStream_t s = ctx->stream;
     LayerMem* M = mem_of(L);
     const int64_t T = L->T;
     const bool one_pass = M->sort_passes == 1;
+    OBB_CK(ctx, cudaMemsetAsync(M->mv, 0xff, sizeof(int32_t) * 2 * L->K, s));
     // cluster sizes: added up by the first pass's counts (with one pass the
     // sort's own offsets give sizes and starts)
     if (!one_pass) OBB_CK(ctx, cudaMemsetAsync(L->d_size, 0, sizeof(int32_t) * L->K, s));
@@ -1246,6 +1323,7 @@ obb_status rebuild_members(obb_ctx* ctx, obb_layer* L)
     }
     OBB_CK(ctx, cudaGetLastError());
     M->members_valid = true;
+    M->incr_ok = true;
     return OBB_OK;
 }
 
@@ -1265,7 +1343,7 @@ void layer_destroy(obb_layer* L)
         void* mp[] = {M->skeys[0], M->skeys[1], M->svals[0], M->svals[1], M->scnt, M->soff, M->sbsum, M->sticket, M->ctr, M->cand, M->evals, M->ecount, M->epoints, M->mom,
                       M->newframe, M->newq, M->ncount, M->dK, M->feats, M->pred, M->skey,
                       M->slot, M->evals2, M->n2, M->map, M->dirty, M->keep, M->level,
-                      M->pframes, M->pq, M->pbest, M->pcount};
+                      M->pframes, M->pq, M->pbest, M->pcount, M->mv, M->mnew, M->snew};
         for (void* p : mp)
             if (p) cudaFreeAsync(p, s);
         delete M;
@@ -1369,6 +1447,9 @@ obb_status layer_create(obb_ctx* ctx, const obb_lattice* lat, const int32_t* d_a
     A_(dalloc(&M->pq, (size_t)kProbes * K, s));
     A_(dalloc(&M->pbest, K, s));
     A_(dalloc(&M->pcount, (size_t)kProbes * K, s));
+    A_(dalloc(&M->mv, 2 * (size_t)K, s));
+    A_(dalloc(&M->mnew, T, s));
+    A_(dalloc(&M->snew, (size_t)K + 1, s));
 #undef A_
     if (e != cudaSuccess) {
         layer_destroy(L);
@@ -1443,7 +1524,7 @@ static obb_status round_body(obb_ctx* ctx, obb_layer* L, int phase = kWhole)
         k_gains<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_obv, M->ecount, L->d_best, L->d_stats);
         note_launch(ctx);
         k_accept<<<cb, 128, 0, s>>>(M->cand, M->ctr, L->d_best, evals, M->ecount, L->d_assign, L->d_q, L->d_obv,
-                                    L->d_size, L->d_stats, M->dirty, M->level);
+                                    L->d_size, L->d_stats, M->dirty, M->level, K, M->mv);
         note_launch(ctx);
     }
     OBB_CK(ctx, cudaGetLastError());
@@ -1844,8 +1925,8 @@ static obb_status batch_capture(obb_ctx* ctx, obb_batch* B)
             e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) break;
             const int64_t l0 = ctx->launches;
-            M->members_valid = kind % 3 != 1;   // rebuilt first in kinds 1 and 4
-            if (kind % 3 == 1) rc = rebuild_members(ctx, L);
+            M->members_valid = kind % 3 != 1;   // updated first in kinds 1 and 4 (after a moving round)
+            if (kind % 3 == 1) rc = update_members(ctx, L);
             if (rc == OBB_OK)
                 rc = refit ? refit_covariance(ctx, L, before_count ? kPre : kPost)
                            : round_body(ctx, L, before_count ? kPre : kPost);
@@ -1935,9 +2016,19 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
         }
         return x;
     };
+    // lists moved by something other than Lloyd moves are sorted from scratch
+    // on the context stream, before the graphs (whose rebuild is the update)
+    auto sort_stale = [&]() -> obb_status {
+        for (obb_layer* L : B->layers) {
+            LayerMem* M = mem_of(L);
+            if (!M->members_valid && !M->incr_ok) OBB_TRY(sort_members(ctx, L));
+        }
+        return OBB_OK;
+    };
     for (int r = 0; r < rounds; ++r) {
         reqs.clear();
         if (use_graphs) {
+            OBB_TRY(sort_stale());
             OBB_CK(ctx, fork());
             int j = 0;
             for (int32_t i = 0; i < n; ++i) {
@@ -1993,6 +2084,7 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
     if (refit_mode & 1) {
         reqs.clear();
         if (use_graphs) {
+            OBB_TRY(sort_stale());
             OBB_CK(ctx, fork());
             for (int32_t i = 0; i < n; ++i) {
                 LayerMem* M = mem_of(B->layers[i]);
@@ -2084,7 +2176,11 @@ obb_status layer_members(obb_ctx* ctx, obb_layer* L)
     return mem_of(L)->members_valid ? OBB_OK : rebuild_members(ctx, L);
 }
 
-void layer_members_changed(obb_layer* L) { mem_of(L)->members_valid = false; }
+void layer_members_changed(obb_layer* L)
+{
+    mem_of(L)->members_valid = false;
+    mem_of(L)->incr_ok = false;   // moved by something that keeps no move records
+}
 
 void launch_sum_points(obb_ctx* ctx, const uint64_t* d_pts, const int32_t* d_n, int64_t* d_stats)
 {
