@@ -168,3 +168,34 @@ def test_outer_volume_refuses_unusable_outputs(ctx, small):
         ctx.outer_volume(lat, d, counts=torch.zeros(4, dtype=torch.int64, device="cuda"))
     with pytest.raises(ValueError):
         ctx.outer_volume(lat, d, counts=np.zeros(5, np.uint64))
+
+
+def test_members_across_lloyd_flood_lloyd(ctx, large):
+    """Lists updated from Lloyd moves, then re-sorted after a flooding
+    re-partition (which keeps no move records), then updated again: each
+    time the stable sort of the current assignment."""
+    lat, T = large
+    tree = ctx.build_tree(lat, 7, 0)
+    leaf = ctx.tree_read(tree, 7)
+    K = len(leaf["frames"])
+    layer = ctx.layer_init(lat, leaf["assign"], (np.arange(K) // 2).astype(np.int32), leaf["frames"])
+
+    def check():
+        assign = ctx.layer_read(layer)["assign"]
+        members, start = ctx.layer_members(layer)
+        em, es = _expect(assign, K)
+        np.testing.assert_array_equal(start, es)
+        np.testing.assert_array_equal(members, em)
+
+    try:
+        moved = ctx.lloyd_step(layer, rounds=3, refit=False)["moves"]
+        check()
+        ctx.flood_partition(layer, mode=1)
+        check()
+        for _ in range(2):
+            moved += ctx.lloyd_step(layer, rounds=2, refit=True)["moves"]
+            check()
+        assert moved > 0
+    finally:
+        layer.free()
+        tree.free()
