@@ -1882,7 +1882,8 @@ obb_status batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_b
 
 // Captures every layer's partition-round phases as CUDA graphs (nothing
 // runs): round_body's phase before the counting launch, once with the
-// member-list rebuild in front, and its phase after the counting launch.
+// member-list update after a moving round in front, and its phase after the
+// counting launch.
 // Each layer's counting request is recorded by the capture (the counting
 // itself stays deferred to the batch's one counting launch per round).
 static obb_status batch_capture(obb_ctx* ctx, obb_batch* B)
@@ -1912,8 +1913,9 @@ static obb_status batch_capture(obb_ctx* ctx, obb_batch* B)
         obb_layer* L = B->layers[i];
         LayerMem* M = mem_of(L);
         const bool valid = M->members_valid;
-        // kinds: 0 round before the count, 1 the same after a rebuild, 2 round
-        // after the count; 3, 4, 5 the same for the covariance refit
+        // kinds: 0 round before the count, 1 the same after the member-list
+        // update, 2 round after the count; 3, 4, 5 the same for the covariance
+        // refit
         cudaGraphExec_t* gx[6] = {&B->g_pre[i], &B->g_pre_rebuild[i], &B->g_post[i],
                                   &B->g_rpre[i], &B->g_rpre_rebuild[i], &B->g_rpost[i]};
         int32_t* kx[6] = {&B->k_pre[i], &B->k_pre_rebuild[i], &B->k_post[i],
