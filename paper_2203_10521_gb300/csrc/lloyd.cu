@@ -959,6 +959,60 @@ __global__ void __launch_bounds__(NT) k_tight(const int32_t* __restrict__ U, con
     }
 }
 
+// The same with a warp per box (clusters of up to about a thousand
+// triangles): no block barrier; min / max are exact, so the bounds are those
+// of k_tight.
+__global__ void __launch_bounds__(256) k_tight_warp(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
+                                                    const int32_t* __restrict__ members,
+                                                    const int32_t* __restrict__ start, obb_qbox* __restrict__ q,
+                                                    int32_t per_cluster, int32_t nbox,
+                                                    const uint8_t* __restrict__ active)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t k = (int32_t)(g >> 5);
+    const int lane = (int)(g & 31);
+    if (k >= nbox) return;                 // warp-uniform
+    if (active && !active[k]) return;      // warp-uniform
+    const int32_t cl = k / per_cluster;
+    const int32_t b0 = start[cl], b1 = start[cl + 1];
+    int32_t n[9];
+    for (int i = 0; i < 9; ++i) n[i] = q[k].n[i];
+    int64_t v[6];
+    for (int s = 0; s < 6; ++s) v[s] = (s & 1) ? INT64_MIN : INT64_MAX;
+    for (int32_t i = b0 + lane; i < b1; i += 32) {
+        int64_t dmin[3], dmax[3];
+        proj3(U, F, members[i], n, dmin, dmax);
+        for (int a = 0; a < 3; ++a) {
+            v[2 * a] = min(v[2 * a], dmin[a]);
+            v[2 * a + 1] = max(v[2 * a + 1], dmax[a]);
+        }
+    }
+    for (int s = 0; s < 6; ++s) {
+        int64_t x = v[s];
+        for (int o = 16; o > 0; o >>= 1) {
+            const int64_t y = (int64_t)__shfl_xor_sync(0xffffffffu, (long long)x, o);
+            x = (s & 1) ? max(x, y) : min(x, y);
+        }
+        if (lane == 0) q[k].b[s] = x;
+    }
+}
+
+// Tight bounds of the layer's boxes q (per_cluster a cluster, active = null
+// for all): a warp per box when clusters average up to 1,024 triangles,
+// else a block.
+void launch_tight(obb_ctx* ctx, const obb_layer* L, obb_qbox* q, int32_t per_cluster, const uint8_t* active,
+                  cudaStream_t s)
+{
+    const obb_lattice* lat = L->lat;
+    const int32_t nbox = L->K * per_cluster;
+    if (L->T <= (int64_t)1024 * L->K)
+        k_tight_warp<<<(unsigned)(((int64_t)nbox * 32 + 255) / 256), 256, 0, s>>>(
+            lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, q, per_cluster, nbox, active);
+    else
+        k_tight<128><<<nbox, 128, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, q, per_cluster,
+                                          active);
+}
+
 __global__ void k_total(const uint64_t* __restrict__ obv, int32_t K, int64_t* __restrict__ out)
 {
     unsigned long long s = 0;
@@ -1369,7 +1423,7 @@ static obb_status init_boxes(obb_ctx* ctx, obb_layer* L, const double* d_frames,
     }
     k_normals<<<(K + 31) / 32, 32, 0, s>>>(L->d_frames, K, lat->d_frame, L->d_q, nullptr);
     note_launch(ctx);
-    k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, L->d_q, 1, nullptr);
+    launch_tight(ctx, L, L->d_q, 1, nullptr, s);
     note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return count_boxes(ctx, lat, L->d_q, M->dK, K, L->d_obv, nullptr);
@@ -1741,7 +1795,7 @@ static obb_status refit_covariance(obb_ctx* ctx, obb_layer* L, int phase)
                                          M->mom, M->dirty);
         k_frames_from_moments<<<(K + 31) / 32, 32, 0, s>>>(M->mom, L->d_frames, K, M->newframe, M->dirty);
         k_normals<<<(K + 31) / 32, 32, 0, s>>>(M->newframe, K, lat->d_frame, M->newq, M->dirty);
-        k_tight<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, M->newq, 1, M->dirty);
+        launch_tight(ctx, L, M->newq, 1, M->dirty, s);
         note_launch(ctx, 4);
         const uint8_t* screen = nullptr;
         if (L->mlp) {
@@ -1787,8 +1841,7 @@ obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dste
         for (int step = 0; step < dsteps; ++step) {
             k_probe_frames<<<(KP + 127) / 128, 128, 0, s>>>(L->d_frames, M->level, K, M->pframes, M->keep);
             k_normals<<<(KP + 31) / 32, 32, 0, s>>>(M->pframes, KP, lat->d_frame, M->pq, M->keep);
-            k_tight<kNT><<<KP, kNT, 0, s>>>(lat->d_fixed, mesh->d_tris, L->d_members, L->d_start, M->pq, kProbes,
-                                            M->keep);
+            launch_tight(ctx, L, M->pq, kProbes, M->keep, s);
             note_launch(ctx, 3);
             if (L->mlp) {
                 OBB_CK(ctx, ctx->kdev.reserve(sizeof(int32_t), s));
