@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -149,3 +150,20 @@ def test_struct_offsets_and_status_codes_match_compiled_header(tmp_path):
         key, val = line.rsplit(" ", 1)
         got[key] = int(val)
     assert got == expect
+
+
+def test_output_checks_refuse_unusable_arrays():
+    """The binding's check of caller-provided outputs (no device needed for
+    host arrays): K 8-byte integers, contiguous and writeable, else ValueError."""
+    import types
+    import paper_2203_10521_gb300 as P
+    fake = types.SimpleNamespace(device=0)
+    P.Context._check_out(fake, "counts", np.zeros(5, np.uint64), 5, 0)
+    P.Context._check_out(fake, "counts", np.zeros(7, np.int64), 5, 0)
+    ro = np.zeros(5, np.uint64)
+    ro.flags.writeable = False
+    for bad in (np.zeros(4, np.uint64), np.zeros(5, np.int32), np.zeros(10, np.uint64)[::2], ro, [0] * 5):
+        with pytest.raises(ValueError):
+            P.Context._check_out(fake, "counts", bad, 5, 0)
+    with pytest.raises(ValueError):
+        P.Context._check_out(fake, "counts", np.zeros(5, np.uint64), 5, 1)   # host array for device boxes
