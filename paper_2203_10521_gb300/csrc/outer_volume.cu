@@ -36,9 +36,14 @@
 #ifndef OBB_GRAB
 #define OBB_GRAB 1
 #endif
-// OBB_COUNT_MINB: resident blocks of the counting kernel per SM the register budget aims at
+// OBB_COUNT_MINB, OBB_COUNT_MINB_SMALL: resident blocks of the counting kernel
+// per SM the register budget aims at, on lattices of at least
+// OBB_ORDER_MIN_MB MiB and on smaller ones
 #ifndef OBB_COUNT_MINB
 #define OBB_COUNT_MINB 5
+#endif
+#ifndef OBB_COUNT_MINB_SMALL
+#define OBB_COUNT_MINB_SMALL 4
 #endif
 // OBB_BIG_TK_ROWS: boxes with at least this many (j, k) rows use tiles twice as tall (0: off)
 #ifndef OBB_BIG_TK_ROWS
@@ -961,15 +966,11 @@ __device__ __forceinline__ void dda_rows(int64_t (&Al)[3], int64_t (&Ah)[3], con
     }
 }
 
-#if OBB_COUNT_MINB > 0
-#define OBB_COUNT_BOUNDS __launch_bounds__(256, OBB_COUNT_MINB)
-#else
-#define OBB_COUNT_BOUNDS __launch_bounds__(256)
-#endif
 // kProf: the launch adds up its algorithmic bytes, rows and rank rows into
-// acc[0], acc[1], acc[3]; every launch adds its in-domain points into *dom
-template <bool kProf>
-__global__ void OBB_COUNT_BOUNDS k_count(const BoxPrep* __restrict__ prep,
+// acc[0], acc[1], acc[3]; every launch adds its in-domain points into *dom.
+// kMinB: resident blocks per SM the register budget aims at.
+template <bool kProf, int kMinB>
+__global__ void __launch_bounds__(256, kMinB) k_count(const BoxPrep* __restrict__ prep,
                                                const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ d_K,
                                                unsigned long long* __restrict__ counts,
@@ -1314,16 +1315,41 @@ obb_status quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_box* d
     return OBB_OK;
 }
 
-static int count_grid(obb_ctx* ctx)
+// The counting kernel as a persistent grid (every resident block of every
+// SM), in the register budget for the lattices' size: 5 blocks per SM for
+// lattices of at least kOrderMinLatticeBytes (DRAM-resident: more warps to
+// cover the loads), 4 below (L2-resident: more registers per thread).
+template <bool kProf, int kMinB>
+static void launch_count_v(obb_ctx* ctx, cudaStream_t s, const BoxPrep* prep, const int64_t* off, const int32_t* d_K,
+                           uint64_t* counts, uint64_t* points, unsigned long long* acc, unsigned long long* dom,
+                           const int32_t* perm)
 {
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count<false>, 256, 0) != cudaSuccess || nb < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_count<kProf, kMinB>, 256, 0) != cudaSuccess ||
+            nb < 1)
             nb = 1;
         blocks_per_sm = nb;
     }
-    return blocks_per_sm * ctx->num_sms;
+    k_count<kProf, kMinB><<<blocks_per_sm * ctx->num_sms, 256, 0, s>>>(
+        prep, off, d_K, reinterpret_cast<unsigned long long*>(counts), reinterpret_cast<unsigned long long*>(points),
+        acc, dom, perm);
+}
+
+static void launch_count(obb_ctx* ctx, cudaStream_t s, bool prof, int64_t lattice_bytes, const BoxPrep* prep,
+                         const int64_t* off, const int32_t* d_K, uint64_t* counts, uint64_t* points,
+                         unsigned long long* acc, unsigned long long* dom, const int32_t* perm)
+{
+    constexpr int kLarge = OBB_COUNT_MINB, kSmall = OBB_COUNT_MINB_SMALL;
+    const bool large = lattice_bytes >= kOrderMinLatticeBytes;
+    if (prof) {
+        if (large) launch_count_v<true, kLarge>(ctx, s, prep, off, d_K, counts, points, acc, dom, perm);
+        else launch_count_v<true, kSmall>(ctx, s, prep, off, d_K, counts, points, acc, dom, perm);
+    } else {
+        if (large) launch_count_v<false, kLarge>(ctx, s, prep, off, d_K, counts, points, acc, dom, perm);
+        else launch_count_v<false, kSmall>(ctx, s, prep, off, d_K, counts, points, acc, dom, perm);
+    }
 }
 
 obb_status count_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_qbox* d_boxes, const int32_t* d_K,
@@ -1403,14 +1429,8 @@ obb_status count_boxes_multi(obb_ctx* ctx, const LatRef* d_lats, int32_t n_lats,
         OBB_CK(ctx, cudaEventCreate(&e1));
         OBB_CK(ctx, cudaEventRecord(e0, s));
     }
-    if (ctx->prof == 1)
-        k_count<true><<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, reinterpret_cast<unsigned long long*>(d_counts),
-                                                      reinterpret_cast<unsigned long long*>(d_points), ctx->d_prof,
-                                                      ctx->d_prof + 2, perm);
-    else
-        k_count<false><<<count_grid(ctx), 256, 0, s>>>(prep, off, d_K, reinterpret_cast<unsigned long long*>(d_counts),
-                                                       reinterpret_cast<unsigned long long*>(d_points), nullptr,
-                                                       ctx->d_prof + 2, perm);
+    launch_count(ctx, s, ctx->prof == 1, lattice_bytes, prep, off, d_K, d_counts, d_points,
+                 ctx->prof == 1 ? ctx->d_prof : nullptr, ctx->d_prof + 2, perm);
     note_launch(ctx);
     if (ctx->prof) {
         OBB_CK(ctx, cudaEventRecord(e1, s));
@@ -1570,9 +1590,8 @@ extern "C" obb_status obb_outer_volume_q_noalloc(obb_ctx* ctx, const obb_lattice
         reinterpret_cast<unsigned long long*>(d_counts), reinterpret_cast<unsigned long long*>(d_points), ticket,
         nullptr, nullptr, 1, ctx->d_err);
     note_launch(ctx);
-    k_count<false><<<count_grid(ctx), 256, 0, s>>>(prep, off, dK, reinterpret_cast<unsigned long long*>(d_counts),
-                                                   reinterpret_cast<unsigned long long*>(d_points), nullptr, nullptr,
-                                                   nullptr);
+    launch_count(ctx, s, false, (int64_t)lat->n_words * 8, prep, off, dK, d_counts, d_points, nullptr, nullptr,
+                 nullptr);
     note_launch(ctx);
     OBB_CK(ctx, cudaGetLastError());
     return OBB_OK;
