@@ -61,3 +61,16 @@ def test_cpu_baseline_and_reference_time_the_same_work():
     cb = bench.cpu_baseline(wl, 0.5)
     assert cb["cores"] >= 1 and cb["nproc"] == (os.cpu_count() or 1)
     assert cb["value"] > 0 and cb["single_thread_value"] > 0
+
+
+def test_roofline_inputs_match_the_counting_sources():
+    """The committed ncu figures the benchmark reports (DRAM traffic and
+    instruction count of the counting kernel's batch launch) were captured
+    from the current counting sources: a change to the kernel, the occupancy
+    pass that writes its lattice copies or their shared types needs a new
+    capture."""
+    import bench
+    for wl in ("sdf2m-1024", "sdf200k-512"):
+        ri = bench.roofline_inputs(wl)
+        assert not ri.get("stale"), wl
+        assert ri.get("dram_bytes_batch_launch", 0) > 0 and ri.get("warp_inst_batch_launch", 0) > 0, wl
