@@ -1939,13 +1939,18 @@ obb_status batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_b
 // counting launch.
 // Each layer's counting request is recorded by the capture (the counting
 // itself stays deferred to the batch's one counting launch per round).
+// The same six kinds are also captured for the whole batch at once, each
+// layer on one of the batch's streams, for the phases in which every layer
+// runs with its list in the same state: one graph launch instead of n.
 static obb_status batch_capture(obb_ctx* ctx, obb_batch* B)
 {
     const int32_t n = (int32_t)B->layers.size();
+    // entries 0..n-1 of each kind's vector are the layers' graphs, entry n
+    // the whole batch's
     for (auto* v : {&B->g_pre, &B->g_pre_rebuild, &B->g_post, &B->g_rpre, &B->g_rpre_rebuild, &B->g_rpost})
-        v->assign(n, nullptr);
+        v->assign(n + 1, nullptr);
     for (auto* v : {&B->k_pre, &B->k_pre_rebuild, &B->k_post, &B->k_rpre, &B->k_rpre_rebuild, &B->k_rpost})
-        v->assign(n, 0);
+        v->assign(n + 1, 0);
     B->req.assign(n, CountReq{});
     B->rreq.assign(n, CountReq{});
     for (int p = 0; p < obb_batch::kBatchStreams; ++p)
@@ -1999,6 +2004,48 @@ static obb_status batch_capture(obb_ctx* ctx, obb_batch* B)
             }
         }
         M->members_valid = valid;   // the captures ran nothing
+    }
+    // the whole-batch graphs: every layer's phase on the batch's streams,
+    // forked from and joined to the capture origin inside the graph
+    constexpr int P = obb_batch::kBatchStreams;
+    for (int kind = 0; kind < 6 && rc == OBB_OK && e == cudaSuccess; ++kind) {
+        const bool before_count = kind % 3 < 2, refit = kind >= 3;
+        std::vector<CountReq> rq;
+        ctx->count_defer = before_count ? &rq : nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        const int64_t l0 = ctx->launches;
+        cudaError_t x = cudaEventRecord(B->ev[P], cs);
+        for (int p = 0; p < P && x == cudaSuccess; ++p) x = cudaStreamWaitEvent(B->par[p], B->ev[P], 0);
+        for (int32_t i = 0; i < n && rc == OBB_OK && x == cudaSuccess; ++i) {
+            obb_layer* L = B->layers[i];
+            LayerMem* M = mem_of(L);
+            const bool valid = M->members_valid;
+            M->members_valid = kind % 3 != 1;
+            ctx->stream = B->par[i % P];
+            if (kind % 3 == 1) rc = update_members(ctx, L);
+            if (rc == OBB_OK)
+                rc = refit ? refit_covariance(ctx, L, before_count ? kPre : kPost)
+                           : round_body(ctx, L, before_count ? kPre : kPost);
+            M->members_valid = valid;
+        }
+        for (int p = 0; p < P && x == cudaSuccess; ++p) {
+            x = cudaEventRecord(B->ev[p], B->par[p]);
+            if (x == cudaSuccess) x = cudaStreamWaitEvent(cs, B->ev[p], 0);
+        }
+        ctx->stream = cs;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        e = x != cudaSuccess ? x : e2;
+        cudaGraphExec_t* gx[6] = {&B->g_pre[n], &B->g_pre_rebuild[n], &B->g_post[n],
+                                  &B->g_rpre[n], &B->g_rpre_rebuild[n], &B->g_rpost[n]};
+        int32_t* kx[6] = {&B->k_pre[n], &B->k_pre_rebuild[n], &B->k_post[n],
+                          &B->k_rpre[n], &B->k_rpre_rebuild[n], &B->k_rpost[n]};
+        if (rc == OBB_OK && e == cudaSuccess) e = cudaGraphInstantiate(gx[kind], g, 0);
+        if (g) cudaGraphDestroy(g);
+        *kx[kind] = (int32_t)(ctx->launches - l0);
+        if (before_count && rc == OBB_OK && (int32_t)rq.size() != n)
+            rc = fail(ctx, OBB_ERR_STATE, "a whole-batch phase made other than one count per layer");
     }
     ctx->count_defer = nullptr;
     ctx->stream = saved_stream;
@@ -2080,10 +2127,36 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
         }
         return OBB_OK;
     };
+    // a phase where every layer runs and every list is in the same state
+    // (all valid, or all to be updated) is one whole-batch graph launch:
+    // -1 none, else the per-layer kind offset (0 valid, 1 update first)
+    auto uniform = [&](bool all_active) -> int {
+        if (!all_active || n == 0) return -1;
+        const bool v0 = mem_of(B->layers[0])->members_valid;
+        for (obb_layer* L : B->layers)
+            if (mem_of(L)->members_valid != v0) return -1;
+        return v0 ? 0 : 1;
+    };
+    auto launch_all = [&](int kind) -> cudaError_t {
+        const cudaGraphExec_t gx[6] = {B->g_pre[n], B->g_pre_rebuild[n], B->g_post[n],
+                                       B->g_rpre[n], B->g_rpre_rebuild[n], B->g_rpost[n]};
+        const int32_t kx[6] = {B->k_pre[n], B->k_pre_rebuild[n], B->k_post[n],
+                               B->k_rpre[n], B->k_rpre_rebuild[n], B->k_rpost[n]};
+        note_launch(ctx, kx[kind]);
+        return cudaGraphLaunch(gx[kind], s);
+    };
+    int32_t n_active = n;
     for (int r = 0; r < rounds; ++r) {
         reqs.clear();
-        if (use_graphs) {
-            OBB_TRY(sort_stale());
+        if (use_graphs) OBB_TRY(sort_stale());
+        const int u = use_graphs ? uniform(n_active == n) : -1;
+        if (u >= 0) {
+            OBB_CK(ctx, launch_all(u));
+            for (int32_t i = 0; i < n; ++i) {
+                mem_of(B->layers[i])->members_valid = true;
+                reqs.push_back(B->req[i]);
+            }
+        } else if (use_graphs) {
             OBB_CK(ctx, fork());
             int j = 0;
             for (int32_t i = 0; i < n; ++i) {
@@ -2106,10 +2179,14 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
             }
         }
         OBB_TRY(count_flush(ctx, reqs, B->tables, B->scratch));
-        if (use_graphs) OBB_CK(ctx, fork());
+        const bool post_all = use_graphs && n_active == n;
+        if (post_all) OBB_CK(ctx, launch_all(2));
+        else if (use_graphs) OBB_CK(ctx, fork());
         for (int32_t i = 0, j = 0; i < n; ++i) {
             if (!active[i]) continue;
-            if (use_graphs) {
+            if (post_all) {
+                // launched above
+            } else if (use_graphs) {
                 OBB_CK(ctx, cudaGraphLaunch(B->g_post[i], B->par[j++ % P]));
                 note_launch(ctx, B->k_post[i]);
             } else {
@@ -2117,7 +2194,7 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
             }
             ++ran[i];
         }
-        if (use_graphs) OBB_CK(ctx, join());
+        if (use_graphs && !post_all) OBB_CK(ctx, join());
         k_gather_accepted<<<(n + 127) / 128, 128, 0, s>>>(d_ptrs, n, d_acc);
         note_launch(ctx);
         OBB_CK(ctx, cudaMemcpyAsync(B->h_acc, d_acc, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
@@ -2132,14 +2209,22 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
                 any = true;
             } else {
                 active[i] = 0;
+                --n_active;
             }
         }
         if (!any) break;
     }
     if (refit_mode & 1) {
         reqs.clear();
-        if (use_graphs) {
-            OBB_TRY(sort_stale());
+        if (use_graphs) OBB_TRY(sort_stale());
+        const int u = use_graphs ? uniform(true) : -1;
+        if (u >= 0) {
+            OBB_CK(ctx, launch_all(3 + u));
+            for (int32_t i = 0; i < n; ++i) {
+                mem_of(B->layers[i])->members_valid = true;
+                reqs.push_back(B->rreq[i]);
+            }
+        } else if (use_graphs) {
             OBB_CK(ctx, fork());
             for (int32_t i = 0; i < n; ++i) {
                 LayerMem* M = mem_of(B->layers[i]);
@@ -2156,12 +2241,7 @@ obb_status batch_lloyd_step(obb_ctx* ctx, obb_batch* B, const obb_step_opts* opt
         }
         OBB_TRY(count_flush(ctx, reqs, B->tables, B->scratch));
         if (use_graphs) {
-            OBB_CK(ctx, fork());
-            for (int32_t i = 0; i < n; ++i) {
-                OBB_CK(ctx, cudaGraphLaunch(B->g_rpost[i], B->par[i % P]));
-                note_launch(ctx, B->k_rpost[i]);
-            }
-            OBB_CK(ctx, join());
+            OBB_CK(ctx, launch_all(5));
         } else {
             for (obb_layer* L : B->layers) OBB_TRY(refit_covariance(ctx, L, kPost));
         }
