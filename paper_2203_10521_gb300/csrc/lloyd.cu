@@ -462,15 +462,6 @@ __device__ __forceinline__ void top2_members(const int32_t* __restrict__ U, cons
     }
 }
 
-__device__ __forceinline__ void top2_store(const Top2 (&b)[6], ClusterExt& e)
-{
-    for (int s = 0; s < 6; ++s) {
-        e.v1[s] = b[s].v1;
-        e.arg[s] = b[s].t1;
-        e.v2[s] = b[s].v2;
-    }
-}
-
 // Large clusters: a block of NT threads per cluster.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_extents(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
@@ -501,26 +492,116 @@ __global__ void __launch_bounds__(NT) k_extents(const int32_t* __restrict__ U, c
     }
 }
 
-// Small clusters: G lanes of a warp per cluster (32 / G clusters a warp; G
-// divides 32), no block barrier.
-template <int G>
+// the three vertices of triangle t projected on the box's axes: per axis the
+// smallest and the largest of the three (the coordinates already loaded)
+__device__ __forceinline__ void proj_loaded(const int32_t (&P)[9], const int32_t (&n)[9], int64_t (&dmin)[3],
+                                            int64_t (&dmax)[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        int64_t lo = INT64_MAX, hi = INT64_MIN;
+        for (int q = 0; q < 3; ++q) {
+            const int64_t d = (int64_t)n[3 * a] * P[3 * q] + (int64_t)n[3 * a + 1] * P[3 * q + 1] +
+                              (int64_t)n[3 * a + 2] * P[3 * q + 2];
+            lo = min(lo, d);
+            hi = max(hi, d);
+        }
+        dmin[a] = lo;
+        dmax[a] = hi;
+    }
+}
+
+__device__ __forceinline__ void load_tri(const int32_t* __restrict__ U, const int32_t* __restrict__ F, int32_t t,
+                                         int32_t (&P)[9])
+{
+    const int32_t v0 = __ldg(F + 3 * (int64_t)t), v1 = __ldg(F + 3 * (int64_t)t + 1),
+                  v2 = __ldg(F + 3 * (int64_t)t + 2);
+    const int32_t v[3] = {v0, v1, v2};
+    for (int q = 0; q < 3; ++q)
+        for (int c = 0; c < 3; ++c) P[3 * q + c] = __ldg(U + 3 * (int64_t)v[q] + c);
+}
+
+__device__ __forceinline__ void top2_add6(Top2 (&b)[8], const int64_t (&dmin)[3], const int64_t (&dmax)[3], int32_t t)
+{
+    for (int a = 0; a < 3; ++a) {
+        top2_add(b[2 * a], dmin[a], t, true);
+        top2_add(b[2 * a + 1], dmax[a], t, false);
+    }
+}
+
+// Small clusters: a warp per cluster, no block barrier.  Each lane takes
+// every 32nd member, two at a time with both triangles' loads issued before
+// either is projected.  The six states (padded to eight) are then reduced
+// and scattered over the warp: at lane offsets 16, 8 and 4 a lane keeps half
+// of its states, hands the other half to its partner and merges what it
+// receives (4 + 2 + 1 merges instead of 6 a level), so lane l ends with
+// state (l >> 2) & 7 over eight lanes; offsets 2 and 1 finish it.  Every
+// order of merges gives the same state (the extreme, its smallest triangle,
+// the extreme of the rest), so the result is that of a sequential pass.
 __global__ void __launch_bounds__(128) k_extents_small(const int32_t* __restrict__ U, const int32_t* __restrict__ F,
                                                        const int32_t* __restrict__ members,
                                                        const int32_t* __restrict__ start, int32_t K,
                                                        const obb_qbox* __restrict__ q, ClusterExt* __restrict__ ext)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int32_t k = (int32_t)(g / G);
-    const int32_t l = (int32_t)(g % G);
+    const int32_t k = (int32_t)(g >> 5);
+    const int l = (int)(g & 31);
     const bool live = k < K;   // every lane of the warp takes part in the shuffles
-    int32_t n[9];
-    for (int i = 0; i < 9; ++i) n[i] = live ? q[k].n[i] : 0;
-    Top2 b[6];
-    top2_init(b);
-    if (live) top2_members(U, F, members, n, start[k] + l, start[k + 1], G, b);
-    for (int s = 0; s < 6; ++s)
-        for (int o = G / 2; o > 0; o >>= 1) top2_merge(b[s], top2_shfl(b[s], o), (s & 1) == 0);
-    if (live && l == 0) top2_store(b, ext[k]);
+    Top2 b[8];
+    for (int s = 0; s < 8; ++s) {
+        const int64_t e = (s & 1) ? INT64_MIN : INT64_MAX;
+        b[s] = Top2{e, e, INT32_MAX};
+    }
+    if (live) {
+        int32_t n[9];
+        for (int i = 0; i < 9; ++i) n[i] = q[k].n[i];
+        const int32_t b1 = start[k + 1];
+        int32_t i = start[k] + l;
+        for (; i + 32 < b1; i += 64) {
+            const int32_t ta = __ldg(members + i), tb = __ldg(members + i + 32);
+            int32_t Pa[9], Pb[9];
+            load_tri(U, F, ta, Pa);
+            load_tri(U, F, tb, Pb);
+            int64_t dmin[3], dmax[3];
+            proj_loaded(Pa, n, dmin, dmax);
+            top2_add6(b, dmin, dmax, ta);
+            proj_loaded(Pb, n, dmin, dmax);
+            top2_add6(b, dmin, dmax, tb);
+        }
+        if (i < b1) {
+            const int32_t ta = __ldg(members + i);
+            int32_t Pa[9];
+            load_tri(U, F, ta, Pa);
+            int64_t dmin[3], dmax[3];
+            proj_loaded(Pa, n, dmin, dmax);
+            top2_add6(b, dmin, dmax, ta);
+        }
+    }
+    // offset 16: keep states 0-3 (lanes 0-15) or 4-7; state parity (low or
+    // high side) is that of j
+    const bool u16 = (l >> 4) & 1, u8 = (l >> 3) & 1, u4 = (l >> 2) & 1;
+    Top2 t4[4];
+    for (int j = 0; j < 4; ++j) {
+        Top2 keep = u16 ? b[4 + j] : b[j];
+        top2_merge(keep, top2_shfl(u16 ? b[j] : b[4 + j], 16), (j & 1) == 0);
+        t4[j] = keep;
+    }
+    Top2 t2[2];
+    for (int j = 0; j < 2; ++j) {
+        Top2 keep = u8 ? t4[2 + j] : t4[j];
+        top2_merge(keep, top2_shfl(u8 ? t4[j] : t4[2 + j], 8), (j & 1) == 0);
+        t2[j] = keep;
+    }
+    Top2 w = u4 ? t2[1] : t2[0];
+    const bool low = !u4;
+    top2_merge(w, top2_shfl(u4 ? t2[0] : t2[1], 4), low);
+    top2_merge(w, top2_shfl(w, 2), low);
+    top2_merge(w, top2_shfl(w, 1), low);
+    const int s = (l >> 2) & 7;
+    if (live && (l & 3) == 0 && s < 6) {
+        ext[k].v1[s] = w.v1;
+        ext[k].arg[s] = w.t1;
+        ext[k].v2[s] = w.v2;
+    }
 }
 
 // the extents of a layer's clusters, by their average size: a warp a
@@ -530,10 +611,9 @@ void launch_extents(obb_ctx* ctx, const obb_layer* L, cudaStream_t s)
     const obb_lattice* lat = L->lat;
     const int32_t K = L->K;
     if (L->T <= (int64_t)1024 * K) {
-        constexpr int G = 32;
-        const int64_t th = (int64_t)K * G;
-        k_extents_small<G><<<(unsigned)((th + 127) / 128), 128, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members,
-                                                                         L->d_start, K, L->d_q, L->d_ext);
+        const int64_t th = (int64_t)K * 32;
+        k_extents_small<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members,
+                                                                      L->d_start, K, L->d_q, L->d_ext);
     } else {
         k_extents<kNT><<<K, kNT, 0, s>>>(lat->d_fixed, lat->mesh->d_tris, L->d_members, L->d_start, L->d_q,
                                          L->d_ext);
@@ -1830,7 +1910,6 @@ obb_status layer_box_update(obb_ctx* ctx, obb_layer* L, int refit_mode, int dste
     cudaStream_t s = ctx->stream;
     LayerMem* M = mem_of(L);
     const obb_lattice* lat = L->lat;
-    const obb_mesh* mesh = lat->mesh;
     const int K = L->K;
     if (refit_mode & 1) OBB_TRY(refit_covariance(ctx, L, kWhole));
     if (refit_mode & 2) {
