@@ -544,7 +544,10 @@ void obb_tree_free(obb_tree* tree);
  * one counting launch; the rotation descent (refit mode bit 1) runs layer by
  * layer.  Every layer's state and statistics equal those of obb_lloyd_step
  * with the same options (opts->graph is ignored).  stats: [n] or NULL.
- * Synchronises once per round. */
+ * Synchronises once per round.  The first step captures each layer's round
+ * and refit phases as CUDA graphs, and the same phases of the whole batch
+ * (a phase every layer runs alike is then one graph launch); a batch holding
+ * a surrogate-screened layer runs without graphs. */
 obb_status obb_batch_create(obb_ctx* ctx, obb_layer* const* layers, int32_t n, obb_batch** out);
 obb_status obb_batch_lloyd_step(obb_ctx* ctx, obb_batch* batch, const obb_step_opts* opts, obb_step_stats* stats);
 void obb_batch_free(obb_batch* batch);
