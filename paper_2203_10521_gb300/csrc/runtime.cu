@@ -143,6 +143,8 @@ int captured_launches(obb_ctx* ctx, int64_t key0, int key1, const std::function<
     return n;
 }
 
+const obb_ctx* mlp_owner(const obb_mlp* m);   // surrogate.cu, where the network type is complete
+
 }  // namespace obbv
 
 using namespace obbv;
@@ -400,6 +402,7 @@ obb_status obb_quantize_boxes(obb_ctx* ctx, const obb_lattice* lat, const obb_bo
                               int32_t on_device)
 {
     if (!ctx || !lat || (K > 0 && (!boxes || !out))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (lat->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
     if (K < 0) return fail(ctx, OBB_ERR_ARG, "negative K");
     if (K == 0) return OBB_OK;
     HostTmp hb(ctx), hq(ctx);
@@ -497,6 +500,7 @@ obb_status obb_tune_counting(obb_ctx* ctx, const obb_lattice* lat, const obb_qbo
                              int32_t on_device, int32_t* tile_k, float* ms)
 {
     if (!ctx || !lat || !qboxes || K <= 0) return fail(ctx, OBB_ERR_ARG, "null argument or empty batch");
+    if (lat->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
     if (K > (int64_t(1) << 30)) return fail(ctx, OBB_ERR_ARG, "K out of range");
     cudaStream_t s = ctx->stream;
     HostTmp hb(ctx);
@@ -546,6 +550,7 @@ obb_status obb_directional_outer_volume(obb_ctx* ctx, const obb_mesh* mesh, cons
                                         int32_t m, double* out, int32_t on_device)
 {
     if (!ctx || !mesh || (K > 0 && (!boxes || !out))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (mesh->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "mesh belongs to another context");
     if (m < 1 || m > 256) return fail(ctx, OBB_ERR_ARG, "m must be in [1, 256]");
     if (K < 0 || K > (int64_t(1) << 24)) return fail(ctx, OBB_ERR_ARG, "K out of range");
     if (K == 0) return OBB_OK;
@@ -606,6 +611,7 @@ obb_status obb_layer_init(obb_ctx* ctx, const obb_lattice* lat, const int32_t* a
 {
     if (!ctx || !lat || !assign || !parent || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
     *out = nullptr;
+    if (lat->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
     if (K < 1) return fail(ctx, OBB_ERR_ARG, "K must be >= 1");
     const int64_t T = lat->mesh->nt;
     HostTmp ha(ctx), hp(ctx), hf(ctx);
@@ -632,6 +638,7 @@ obb_status obb_lloyd_step(obb_ctx* ctx, obb_layer* layer, const obb_step_opts* o
 obb_status obb_layer_parents(obb_ctx* ctx, const obb_layer* L, int32_t* parent)
 {
     if (!ctx || !L || !parent) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (L->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
     OBB_CK(ctx, cudaMemcpyAsync(parent, L->d_parent, sizeof(int32_t) * L->K, cudaMemcpyDeviceToHost, ctx->stream));
     return check_device_error(ctx);
 }
@@ -665,6 +672,7 @@ obb_status obb_layer_read(obb_ctx* ctx, const obb_layer* L, int32_t* assign, dou
                           obb_box* boxes, uint64_t* obv, int32_t on_device)
 {
     if (!ctx || !L) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (L->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
     cudaStream_t s = ctx->stream;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (assign) OBB_CK(ctx, cudaMemcpyAsync(assign, L->d_assign, sizeof(int32_t) * L->T, kind, s));
@@ -689,6 +697,8 @@ int32_t obb_layer_clusters(const obb_layer* L) { return L ? L->K : 0; }
 obb_status obb_layer_set_surrogate(obb_ctx* ctx, obb_layer* L, const obb_mlp* mlp, int32_t topk)
 {
     if (!ctx || !L) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (L->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
+    if (mlp && obbv::mlp_owner(mlp) != ctx) return fail(ctx, OBB_ERR_STATE, "network belongs to another context");
     if (topk < 0 || topk > 6) return fail(ctx, OBB_ERR_ARG, "topk must be in [0, 6]");
     return layer_set_surrogate(ctx, L, mlp, topk);
 }
@@ -697,6 +707,7 @@ obb_status obb_layer_last_candidates(obb_ctx* ctx, const obb_layer* L, obb_qbox*
                                      int64_t* n)
 {
     if (!ctx || !L || !n || (cap > 0 && !boxes)) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (L->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
     return layer_last_candidates(ctx, L, boxes, counts, cap, n);
 }
 
@@ -758,6 +769,7 @@ void obb_batch_free(obb_batch* B) { batch_destroy(B); }
 obb_status obb_layer_split(obb_ctx* ctx, const obb_layer* L, int32_t* child, int32_t on_device)
 {
     if (!ctx || !L || !child) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (L->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "layer belongs to another context");
     HostTmp hc(ctx);
     int32_t* dc;
     OBB_TRY(out_device(ctx, child, (size_t)L->T, on_device, hc, &dc));
@@ -770,6 +782,7 @@ obb_status obb_build_tree(obb_ctx* ctx, const obb_lattice* lat, const obb_tree_o
 {
     if (!ctx || !lat || !opts || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
     *out = nullptr;
+    if (lat->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
     obb_tree* t = new (std::nothrow) obb_tree();
     if (!t) return fail(ctx, OBB_ERR_OOM, "host allocation");
     obb_status st = build_tree(ctx, lat, opts, t);
@@ -786,6 +799,7 @@ obb_status obb_tree_read(obb_ctx* ctx, const obb_tree* tree, int32_t level, int3
                          obb_qbox* qboxes, obb_box* boxes, uint64_t* obv)
 {
     if (!ctx || !tree) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (tree->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "tree belongs to another context");
     if (level < 0 || level >= (int32_t)tree->layers.size()) return fail(ctx, OBB_ERR_ARG, "level out of range");
     return obb_layer_read(ctx, tree->layers[level], assign, frames, qboxes, boxes, obv, 0);
 }
@@ -793,6 +807,7 @@ obb_status obb_tree_read(obb_ctx* ctx, const obb_tree* tree, int32_t level, int3
 obb_status obb_tree_parents(obb_ctx* ctx, const obb_tree* tree, int32_t level, int32_t* parent)
 {
     if (!ctx || !tree || !parent) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (tree->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "tree belongs to another context");
     if (level < 0 || level >= (int32_t)tree->layers.size()) return fail(ctx, OBB_ERR_ARG, "level out of range");
     return obb_layer_parents(ctx, tree->layers[level], parent);
 }
@@ -809,6 +824,7 @@ obb_status obb_tree_sweep(obb_ctx* ctx, obb_tree* tree, const obb_sweep_opts* op
 obb_status obb_tree_score(obb_ctx* ctx, const obb_tree* tree, double* points, double* volume)
 {
     if (!ctx || !tree) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (tree->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "tree belongs to another context");
     const int depth = (int)tree->layers.size() - 1;
     double acc = 0.0;
     for (int L = 0; L <= depth; ++L) {

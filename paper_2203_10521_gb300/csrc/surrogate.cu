@@ -603,6 +603,10 @@ struct obb_mlp {
 
 namespace obbv {
 
+// the context a network was created in (the entry points of other units
+// check ownership through this; the type is complete only here)
+const obb_ctx* mlp_owner(const obb_mlp* m) { return m ? m->ctx : nullptr; }
+
 static obb_status mlp_reserve(obb_ctx* ctx, MlpImpl* P, int64_t B)
 {
     if (B <= P->cap) return OBB_OK;
@@ -772,6 +776,7 @@ int64_t obb_mlp_num_params(void) { return kParams; }
 obb_status obb_mlp_params(obb_ctx* ctx, const obb_mlp* m, float* out, int32_t on_device)
 {
     if (!ctx || !m || !out) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (m->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "network belongs to another context");
     OBB_CK(ctx, cudaMemcpyAsync(out, m->p->w, sizeof(float) * kParams,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
     return on_device ? OBB_OK : check_device_error(ctx);
@@ -780,6 +785,7 @@ obb_status obb_mlp_params(obb_ctx* ctx, const obb_mlp* m, float* out, int32_t on
 obb_status obb_mlp_set_params(obb_ctx* ctx, obb_mlp* m, const float* in, int32_t on_device)
 {
     if (!ctx || !m || !in) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (m->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "network belongs to another context");
     MlpImpl* P = m->p;
     OBB_CK(ctx, cudaMemcpyAsync(P->w, in, sizeof(float) * kParams,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
@@ -797,6 +803,7 @@ obb_status obb_surrogate_features(obb_ctx* ctx, const obb_lattice* lat, const ob
                                   int32_t on_device)
 {
     if (!ctx || !lat || (K > 0 && (!boxes || !feats))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (lat->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "lattice belongs to another context");
     if (K <= 0) return OBB_OK;
     void* hb = nullptr;
     const obb_qbox* db;
@@ -845,6 +852,7 @@ obb_status obb_mlp_forward(obb_ctx* ctx, const obb_mlp* m, const float* feats, i
                            int32_t half_weights, int32_t on_device)
 {
     if (!ctx || !m || (B > 0 && (!feats || !out))) return fail(ctx, OBB_ERR_ARG, "null argument");
+    if (m->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "network belongs to another context");
     if (B <= 0) return OBB_OK;
     if (B > (1 << 24)) return fail(ctx, OBB_ERR_RANGE, "batch too large");
     void* hx = nullptr;
@@ -863,6 +871,7 @@ obb_status obb_mlp_gradients(obb_ctx* ctx, obb_mlp* m, const float* feats, const
                              float* grads, float* loss, int32_t on_device)
 {
     if (!ctx || !m || !feats || !target || B <= 0) return fail(ctx, OBB_ERR_ARG, "bad argument");
+    if (m->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "network belongs to another context");
     if (B > (1 << 24)) return fail(ctx, OBB_ERR_RANGE, "batch too large");
     void *hx = nullptr, *ht = nullptr;
     const float *dx, *dt;
@@ -882,6 +891,7 @@ obb_status obb_mlp_train_step(obb_ctx* ctx, obb_mlp* m, const float* feats, cons
                               float* loss, int32_t on_device)
 {
     if (!ctx || !m || !feats || !target || B <= 0) return fail(ctx, OBB_ERR_ARG, "bad argument");
+    if (m->ctx != ctx) return fail(ctx, OBB_ERR_STATE, "network belongs to another context");
     if (B > (1 << 24)) return fail(ctx, OBB_ERR_RANGE, "batch too large");
     void *hx = nullptr, *ht = nullptr;
     const float *dx, *dt;
