@@ -195,33 +195,86 @@ def _is_torch(x):
 
 
 def _host(x, dtype):
-    """Contiguous numpy copy/view of x with the given dtype (boxes may be [K, 12] float32)."""
+    """Contiguous numpy copy/view of x with the given dtype.  Boxes may come
+    as [K, 12] numbers (converted to float32); records of any other form are
+    taken as their raw bytes (e.g. quantised boxes as uint8), never converted
+    field by field."""
     a = np.asarray(x)
-    if dtype is BOX_DTYPE and a.dtype != BOX_DTYPE:
-        a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1, 12).view(BOX_DTYPE).reshape(-1)
-    elif dtype is not None and a.dtype != dtype:
+    dtype = np.dtype(dtype)
+    if dtype.fields is not None and a.dtype != dtype:
+        if dtype == BOX_DTYPE and a.dtype != np.uint8:
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            if a.size % 12:
+                raise ValueError("boxes must be records or rows of 12 numbers")
+            return a.reshape(-1, 12).view(BOX_DTYPE).reshape(-1)
+        b = np.ascontiguousarray(a).reshape(-1).view(np.uint8)
+        if b.size % dtype.itemsize:
+            raise ValueError(f"{b.size} bytes do not make whole {dtype.itemsize}-byte records")
+        return b.view(dtype)
+    if a.dtype != dtype:
         a = a.astype(dtype)
     return np.ascontiguousarray(a)
 
 
-def _arg(x, dtype=None):
-    """(pointer, on_device, keepalive) for a numpy array or a torch CUDA tensor."""
-    if x is None:
-        return None, 0, None
-    if _is_torch(x):
-        if x.is_cuda:
-            if not x.is_contiguous():
-                raise ValueError("CUDA tensors must be contiguous")
-            return C.c_void_p(x.data_ptr()), 1, x
-        x = x.numpy()
-    a = _host(x, dtype)
-    return a.ctypes.data_as(C.c_void_p), 0, a
+# the torch element types a plain input of each numpy type may have on the device
+_TORCH_TYPES = {np.dtype(np.int32): ("int32",), np.dtype(np.float32): ("float32",),
+                np.dtype(np.float64): ("float64",), np.dtype(np.uint64): ("int64", "uint64"),
+                np.dtype(np.int64): ("int64", "uint64")}
 
 
-def _count(x, keep, itemsize):
+def _input(name, x, dtype, device, n=None, dev=None, row=1):
+    """(pointer, on_device, keepalive, count) of an input array.  A torch CUDA
+    tensor must be contiguous and on `device`; for a record type (boxes) any
+    element type whose bytes make whole records, else the element type the
+    C call reads.  Anything else goes through numpy as a contiguous copy of
+    `dtype`.  count = elements of `dtype`; n: the count the call reads; dev:
+    the placement of the call's other arrays (0 host, 1 device); row: count
+    must be a multiple of it (rows of a matrix)."""
+    dtype = np.dtype(dtype)
     if _is_torch(x) and x.is_cuda:
-        return x.numel() * x.element_size() // itemsize
-    return len(keep)
+        if x.device.index != device:
+            raise ValueError(f"{name} is on {x.device}; this context is on cuda:{device}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if dtype.fields is None and str(x.dtype).replace("torch.", "") not in _TORCH_TYPES.get(dtype, ()):
+            raise ValueError(f"{name} must be a {' or '.join(_TORCH_TYPES.get(dtype, ('?',)))} tensor")
+        nbytes = x.numel() * x.element_size()
+        if nbytes % dtype.itemsize:
+            raise ValueError(f"{name} must hold whole {dtype.itemsize}-byte elements")
+        p, on, keep, count = C.c_void_p(x.data_ptr()), 1, x, nbytes // dtype.itemsize
+    else:
+        if _is_torch(x):
+            x = x.numpy()
+        a = _host(x, dtype)
+        p, on, keep, count = a.ctypes.data_as(C.c_void_p), 0, a, a.nbytes // dtype.itemsize
+    if dev is not None and on != dev:
+        raise ValueError(f"{name} must be {'a CUDA tensor' if dev else 'a host array'}, like the call's other arrays")
+    if n is not None and count != n:
+        raise ValueError(f"{name} holds {count} elements; the call reads {n}")
+    if count % row:
+        raise ValueError(f"{name} must hold whole rows of {row} elements")
+    return p, on, keep, count
+
+
+def _output(name, a, n, dtype, dev, device):
+    """Pointer to a caller-supplied output of n elements of dtype on the
+    inputs' side: a contiguous CUDA tensor of `device` with room for them
+    (records: any element type; plain types: elements of the same size), or
+    a writeable contiguous numpy array with room for them."""
+    dtype = np.dtype(dtype)
+    need = n * dtype.itemsize
+    if dev:
+        ok = (_is_torch(a) and a.is_cuda and a.device.index == device and a.is_contiguous()
+              and a.numel() * a.element_size() >= need
+              and (dtype.fields is not None or a.element_size() == dtype.itemsize))
+        where = f"a contiguous CUDA tensor on cuda:{device}"
+    else:
+        ok = (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.flags.writeable and a.nbytes >= need
+              and (dtype.fields is not None or a.itemsize == dtype.itemsize))
+        where = "a writeable contiguous numpy array"
+    if not ok:
+        raise ValueError(f"{name} must be {where} with room for {n} elements of {dtype.itemsize} bytes")
+    return C.c_void_p(a.data_ptr()) if dev else a.ctypes.data_as(C.c_void_p)
 
 
 class _DevArray:
@@ -296,22 +349,19 @@ class Context:
 
     # ---------------------------------------------------------- outer volume
     def quantize_boxes(self, lat, boxes, out=None):
-        p, dev, keep = _arg(boxes, BOX_DTYPE)
-        K = _count(boxes, keep, 48)
+        p, dev, keep, K = _input("boxes", boxes, BOX_DTYPE, self.device)
         if out is None:
             out = self._out_like(dev, K, QBOX_DTYPE, 88)
-        po, _, _ = _arg(out) if dev else (out.ctypes.data_as(C.c_void_p), 0, out)
+        po = _output("out", out, K, QBOX_DTYPE, dev, self.device)
         self.check(self.lib.obb_quantize_boxes(self.h, lat.h, p, K, po, dev))
         return out
 
     def outer_volume(self, lat, boxes, counts=None, points=None, want_points=False):
-        p, dev, keep = _arg(boxes, BOX_DTYPE)
-        K = _count(boxes, keep, 48)
+        p, dev, keep, K = _input("boxes", boxes, BOX_DTYPE, self.device)
         return self._ov(self.lib.obb_outer_volume, lat, p, dev, K, counts, points, want_points)
 
     def outer_volume_q(self, lat, qboxes, counts=None, points=None, want_points=False):
-        p, dev, keep = _arg(qboxes, QBOX_DTYPE)
-        K = _count(qboxes, keep, 88)
+        p, dev, keep, K = _input("qboxes", qboxes, QBOX_DTYPE, self.device)
         return self._ov(self.lib.obb_outer_volume_q, lat, p, dev, K, counts, points, want_points)
 
     def set_counting_tile(self, tile_k):
@@ -359,8 +409,8 @@ class Context:
     def outer_volume_multi(self, lats, qboxes, lattice_of_box, want_points=False):
         """Counts of quantised boxes on several lattices in one launch (host arrays)."""
         q = _host(qboxes, QBOX_DTYPE)
-        li = np.ascontiguousarray(lattice_of_box, dtype=np.int32)
         K = len(q)
+        _, _, li, _ = _input("lattice_of_box", lattice_of_box, np.int32, self.device, n=K, dev=0)
         table = (C.c_void_p * len(lats))(*[l.h.value for l in lats])
         cnt = np.zeros(K, np.uint64)
         pts = np.zeros(K, np.uint64) if want_points else None
@@ -451,11 +501,13 @@ class Context:
 
     # ----------------------------------------------------------------- layer
     def layer_init(self, lat, assign, parent, frames=None):
-        dev = 1 if _is_torch(assign) and assign.is_cuda else 0
-        pa, _, ka = _arg(assign, np.int32)
-        pp, _, kp = _arg(parent, np.int32)
-        pf, _, kf = _arg(frames, np.float64)
-        K = len(parent)
+        """assign int32 [n_tris] cluster of each triangle, parent int32 [K],
+        frames float64 [K, 9] or None: all host arrays or all CUDA tensors."""
+        pa, dev, ka, _ = _input("assign", assign, np.int32, self.device, n=lat.mesh.nt)
+        pp, _, kp, K = _input("parent", parent, np.int32, self.device, dev=dev)
+        pf, kf = None, None
+        if frames is not None:
+            pf, _, kf, _ = _input("frames", frames, np.float64, self.device, n=9 * K, dev=dev)
         h = C.c_void_p()
         self.check(self.lib.obb_layer_init(self.h, lat.h, pa, pp, int(K), pf, dev, C.byref(h)))
         return Layer(self, h, lat, K)
@@ -582,20 +634,20 @@ class Context:
 
     def mlp_set_params(self, mlp, params):
         p = np.ascontiguousarray(params, dtype=np.float32)
-        assert p.size == self.mlp_num_params()
+        if p.size != self.mlp_num_params():
+            raise ValueError(f"params holds {p.size} values; the network has {self.mlp_num_params()}")
         self.check(self.lib.obb_mlp_set_params(self.h, mlp.h, p.ctypes.data_as(C.c_void_p), 0))
 
     def surrogate_features(self, lat, qboxes, out=None):
         """[K, 524] float32 features (numpy in -> numpy out, CUDA tensors -> CUDA tensor)."""
-        p, dev, keep = _arg(qboxes, QBOX_DTYPE)
-        K = _count(qboxes, keep, 88)
+        p, dev, keep, K = _input("qboxes", qboxes, QBOX_DTYPE, self.device)
         if out is None:
             if dev:
                 import torch
                 out = torch.empty((K, self.SURROGATE_INPUTS), dtype=torch.float32, device=f"cuda:{self.device}")
             else:
                 out = np.zeros((K, self.SURROGATE_INPUTS), np.float32)
-        po = C.c_void_p(out.data_ptr()) if dev else out.ctypes.data_as(C.c_void_p)
+        po = _output("out", out, K * self.SURROGATE_INPUTS, np.float32, dev, self.device)
         self.check(self.lib.obb_surrogate_features(self.h, lat.h, p, K, po, dev))
         return out
 
@@ -603,9 +655,8 @@ class Context:
         """Training targets: exact outer volume / the box's cell volume (the
         screen's scale), clipped to [0, 1].  CUDA tensors in -> CUDA tensor out
         (qboxes as bytes, counts int64), numpy -> numpy."""
-        p, dev, keep = _arg(qboxes, QBOX_DTYPE)
-        K = _count(qboxes, keep, 88)
-        pc, _, keepc = _arg(counts, np.uint64)
+        p, dev, keep, K = _input("qboxes", qboxes, QBOX_DTYPE, self.device)
+        pc, _, keepc, _ = _input("counts", counts, np.uint64, self.device, n=K, dev=dev)
         if dev:
             import torch
             out = torch.empty(K, dtype=torch.float32, device=f"cuda:{self.device}")
@@ -617,8 +668,9 @@ class Context:
         return out
 
     def mlp_forward(self, mlp, feats, half=True):
-        p, dev, keep = _arg(feats, np.float32)
-        B = (feats.shape[0] if dev else keep.shape[0])
+        """Predicted empty fractions [B] of features [B, 524] (numpy or a CUDA tensor)."""
+        p, dev, keep, n = _input("feats", feats, np.float32, self.device, row=self.SURROGATE_INPUTS)
+        B = n // self.SURROGATE_INPUTS
         if dev:
             import torch
             out = torch.empty(B, dtype=torch.float32, device=f"cuda:{self.device}")
@@ -630,28 +682,27 @@ class Context:
         return out
 
     def mlp_gradients(self, mlp, feats, target):
-        X = np.ascontiguousarray(feats, np.float32)
-        T = np.ascontiguousarray(target, np.float32)
+        """Gradients of the mean squared error over a host batch: (grads, loss)."""
+        px, _, kx, n = _input("feats", feats, np.float32, self.device, dev=0, row=self.SURROGATE_INPUTS)
+        B = n // self.SURROGATE_INPUTS
+        pt, _, kt, _ = _input("target", target, np.float32, self.device, n=B, dev=0)
         g = np.zeros(self.mlp_num_params(), np.float32)
         loss = np.zeros(1, np.float32)
-        self.check(self.lib.obb_mlp_gradients(self.h, mlp.h, X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p),
-                                              X.shape[0], g.ctypes.data_as(C.c_void_p),
+        self.check(self.lib.obb_mlp_gradients(self.h, mlp.h, px, pt, B, g.ctypes.data_as(C.c_void_p),
                                               loss.ctypes.data_as(C.c_void_p), 0))
         return g, float(loss[0])
 
     def mlp_train_step(self, mlp, feats, target, lr, want_loss=False):
-        """One Adam step; feats/target are CUDA tensors (device) or numpy arrays."""
-        if _is_torch(feats) and feats.is_cuda:
-            loss = np.zeros(1, np.float32)
-            self.check(self.lib.obb_mlp_train_step(self.h, mlp.h, C.c_void_p(feats.data_ptr()),
-                                                   C.c_void_p(target.data_ptr()), feats.shape[0], C.c_float(lr),
-                                                   None, 1))
+        """One Adam step; feats [B, 524] / target [B] are both CUDA tensors
+        (device; no loss returned) or both host arrays."""
+        px, dev, kx, n = _input("feats", feats, np.float32, self.device, row=self.SURROGATE_INPUTS)
+        B = n // self.SURROGATE_INPUTS
+        pt, _, kt, _ = _input("target", target, np.float32, self.device, n=B, dev=dev)
+        if dev:
+            self.check(self.lib.obb_mlp_train_step(self.h, mlp.h, px, pt, B, C.c_float(lr), None, 1))
             return None
-        X = np.ascontiguousarray(feats, np.float32)
-        T = np.ascontiguousarray(target, np.float32)
         loss = np.zeros(1, np.float32)
-        self.check(self.lib.obb_mlp_train_step(self.h, mlp.h, X.ctypes.data_as(C.c_void_p),
-                                               T.ctypes.data_as(C.c_void_p), X.shape[0], C.c_float(lr),
+        self.check(self.lib.obb_mlp_train_step(self.h, mlp.h, px, pt, B, C.c_float(lr),
                                                loss.ctypes.data_as(C.c_void_p), 0))
         return float(loss[0])
 

@@ -167,3 +167,61 @@ def test_output_checks_refuse_unusable_arrays():
             P.Context._check_out(fake, "counts", bad, 5, 0)
     with pytest.raises(ValueError):
         P.Context._check_out(fake, "counts", np.zeros(5, np.uint64), 5, 1)   # host array for device boxes
+
+
+def test_input_checks_host_arrays():
+    """The binding's check of inputs before any call reads them (host arrays
+    and CPU tensors; no device needed): lengths the call reads, one placement
+    for all of a call's arrays, whole rows, records from raw bytes."""
+    import paper_2203_10521_gb300 as P
+    torch = pytest.importorskip("torch")
+    p, dev, keep, n = P._input("assign", np.arange(7, dtype=np.int64), np.int32, 0, n=7)
+    assert dev == 0 and n == 7 and keep.dtype == np.int32 and np.array_equal(keep, np.arange(7))
+    _, _, keep, n = P._input("frames", np.zeros((3, 9)), np.float64, 0, n=27, dev=0)
+    assert n == 27
+    _, dev, keep, n = P._input("assign", torch.arange(5, dtype=torch.int32), np.int32, 0, n=5)
+    assert dev == 0 and n == 5
+    with pytest.raises(ValueError, match="reads 8"):
+        P._input("assign", np.zeros(7, np.int32), np.int32, 0, n=8)
+    with pytest.raises(ValueError, match="a CUDA tensor"):
+        P._input("parent", np.zeros(4, np.int32), np.int32, 0, dev=1)
+    with pytest.raises(ValueError, match="whole rows of 524"):
+        P._input("feats", np.zeros((2, 100), np.float32), np.float32, 0, row=524)
+    _, _, _, n = P._input("feats", np.zeros((3, 524), np.float32), np.float32, 0, row=524)
+    assert n == 3 * 524
+
+
+def test_record_inputs_from_bytes_and_rows():
+    """Boxes as [K, 12] numbers, quantised boxes as raw bytes: both become
+    whole records, never a field-by-field conversion."""
+    import paper_2203_10521_gb300 as P
+    q = np.zeros(3, P.QBOX_DTYPE)
+    q["b"] = np.arange(18).reshape(3, 6)
+    q["n"][:, 0] = [5, 6, 7]
+    _, _, keep, n = P._input("qboxes", q.view(np.uint8), P.QBOX_DTYPE, 0)
+    assert n == 3 and np.array_equal(keep["b"], q["b"]) and np.array_equal(keep["n"], q["n"])
+    with pytest.raises(ValueError, match="whole 88-byte records"):
+        P._input("qboxes", np.zeros(100, np.uint8), P.QBOX_DTYPE, 0)
+    rows = np.arange(24, dtype=np.float64).reshape(2, 12)
+    _, _, keep, n = P._input("boxes", rows, P.BOX_DTYPE, 0)
+    assert n == 2 and keep["half"][1].tolist() == [21.0, 22.0, 23.0]
+    with pytest.raises(ValueError, match="12 numbers"):
+        P._input("boxes", np.zeros(13, np.float32), P.BOX_DTYPE, 0)
+
+
+def test_output_checks_host_arrays():
+    """Caller-supplied outputs: room for the elements, the element size of
+    plain types, contiguous and writeable, on the inputs' side."""
+    import paper_2203_10521_gb300 as P
+    P._output("out", np.zeros(4, P.QBOX_DTYPE), 4, P.QBOX_DTYPE, 0, 0)
+    P._output("out", np.zeros(4 * 88, np.uint8), 4, P.QBOX_DTYPE, 0, 0)   # records: any element type
+    P._output("out", np.zeros((2, 524), np.float32), 2 * 524, np.float32, 0, 0)
+    ro = np.zeros(4, P.QBOX_DTYPE)
+    ro.flags.writeable = False
+    for bad, n, dt in ((np.zeros(3, P.QBOX_DTYPE), 4, P.QBOX_DTYPE), (ro, 4, P.QBOX_DTYPE),
+                       (np.zeros((2, 524), np.float64), 2 * 524, np.float32),
+                       (np.zeros((2, 600), np.float32)[:, :524], 2 * 524, np.float32)):
+        with pytest.raises(ValueError):
+            P._output("out", bad, n, dt, 0, 0)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        P._output("out", np.zeros(4, P.QBOX_DTYPE), 4, P.QBOX_DTYPE, 1, 0)

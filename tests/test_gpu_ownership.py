@@ -91,3 +91,44 @@ def test_owner_still_works_after_refusals(two):
     assert st["total_obv"] == int(a.layer_read(layer)["obv"].sum())
     pts, _ = a.tree_score(tree)
     assert pts > 0
+
+
+def test_device_inputs_are_checked_before_any_call(two):
+    """CUDA-tensor inputs: element type, length, whole rows, contiguity and
+    one placement for all of a call's arrays are checked in the binding
+    (ValueError, nothing called); well-formed device inputs give the same
+    layer as host inputs."""
+    import torch
+    a, lat, r, parents = two["a"], two["lat"], two["r"], two["parents"]
+    dev = f"cuda:{a.device}"
+    d_assign = torch.from_numpy(r["assign"]).to(dev)
+    d_parent = torch.from_numpy(parents).to(dev)
+    d_frames = torch.from_numpy(np.ascontiguousarray(r["frames"])).to(dev)
+    bad = [
+        lambda: a.layer_init(lat, d_assign, parents),                                  # mixed placement
+        lambda: a.layer_init(lat, d_assign.long(), d_parent),                          # element type
+        lambda: a.layer_init(lat, d_assign[:-1].contiguous(), d_parent),               # length
+        lambda: a.layer_init(lat, d_assign, d_parent, d_frames[:-1].contiguous()),     # frames length
+        lambda: a.mlp_forward(two["mlp_a"], torch.zeros((2, 100), dtype=torch.float32, device=dev)),
+        lambda: a.mlp_train_step(two["mlp_a"], torch.zeros((2, 524), dtype=torch.float32, device=dev),
+                                 torch.zeros(3, dtype=torch.float32, device=dev), 1e-3),
+        lambda: a.surrogate_targets(torch.from_numpy(r["qboxes"].view(np.uint8).copy()).to(dev),
+                                    r["obv"].astype(np.uint64)),
+        lambda: a.outer_volume(lat, torch.from_numpy(np.ascontiguousarray(
+            r["boxes"]).view(np.float32).reshape(-1, 12)).to(dev).t()),               # not contiguous
+        lambda: a.quantize_boxes(lat, torch.from_numpy(np.ascontiguousarray(r["boxes"]).view(np.float32)).to(dev),
+                                 out=torch.zeros(len(r["boxes"]) * 88 - 1, dtype=torch.uint8, device=dev)),
+    ]
+    for fn in bad:
+        with pytest.raises(ValueError):
+            fn()
+    host = a.layer_init(lat, r["assign"], parents, r["frames"])
+    on_dev = a.layer_init(lat, d_assign, d_parent, d_frames)
+    try:
+        x, y = a.layer_read(host), a.layer_read(on_dev)
+        for k in ("assign", "frames", "obv"):
+            np.testing.assert_array_equal(x[k], y[k])
+        np.testing.assert_array_equal(x["qboxes"].view(np.uint8), y["qboxes"].view(np.uint8))
+    finally:
+        host.free()
+        on_dev.free()
