@@ -9,10 +9,12 @@
  *  - Every function returning obb_status returns OBB_OK (0) or a negative
  *    code; obb_last_error(ctx) gives a one-line explanation of the last
  *    failure on that context.  No exception crosses the ABI.
- *  - Opaque handles (obb_ctx, obb_mesh, obb_lattice, obb_layer, obb_tree) are
- *    owned by the library and released with their *_free / obb_destroy call.
- *    A lattice borrows its mesh, a layer its lattice, a tree its lattice:
- *    free in the reverse order of creation.
+ *  - Opaque handles (obb_ctx, obb_mesh, obb_lattice, obb_layer, obb_tree,
+ *    obb_batch, obb_mlp) are owned by the library and released with their
+ *    *_free / obb_destroy call.  A lattice borrows its mesh, a layer its
+ *    lattice, a tree its lattice: free in the reverse order of creation.
+ *    Every handle belongs to the context that created it; a call given a
+ *    handle of another context returns OBB_ERR_STATE before any work.
  *  - Input arrays are borrowed for the duration of the call.  Output arrays
  *    are owned by the caller.  Arguments named on_device say whether the
  *    caller's arrays live in device memory (1) or host memory (0).
