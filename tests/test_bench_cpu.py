@@ -74,3 +74,55 @@ def test_roofline_inputs_match_the_counting_sources():
         ri = bench.roofline_inputs(wl)
         assert not ri.get("stale"), wl
         assert ri.get("dram_bytes_batch_launch", 0) > 0 and ri.get("warp_inst_batch_launch", 0) > 0, wl
+
+
+def _profile_commands():
+    """The shell commands quoted in profiles/ (code fences of the .md
+    summaries, '#' lines of the .txt inputs), continuation lines joined."""
+    cmds = []
+    pdir = os.path.join(ROOT, "profiles")
+    for name in sorted(os.listdir(pdir)):
+        text = open(os.path.join(pdir, name)).read()
+        if name.endswith(".md"):
+            parts = text.split("```")
+            lines = [ln for block in parts[1::2] for ln in block.splitlines()]
+        else:
+            lines = [ln.lstrip("#").strip() for ln in text.splitlines() if ln.startswith("#")]
+        cur = ""
+        for ln in lines:
+            ln = ln.strip()
+            cur = (cur + " " + ln[:-1]).strip() if ln.endswith("\\") else (cur + " " + ln).strip()
+            if not ln.endswith("\\"):
+                if cur.split(" ", 1)[0] in ("python", "ncu", "nvcc"):
+                    cmds.append((name, cur))
+                cur = ""
+    return cmds
+
+
+def test_profile_commands_run_the_committed_benchmark():
+    """Every bench.py command a profile summary quotes is accepted by
+    bench.py's own argument parser, and every ncu command leaves the clocks
+    alone (--clock-control none)."""
+    import shlex
+    sys.path.insert(0, ROOT)
+    import bench
+    cmds = _profile_commands()
+    n_bench = n_ncu = 0
+    for name, cmd in cmds:
+        toks = shlex.split(cmd)
+        if toks and toks[0] == "ncu" and "-i" not in toks:   # a capture (-i only reads a saved report)
+            n_ncu += 1
+            i = toks.index("--clock-control")
+            assert toks[i + 1] == "none", (name, cmd)
+        for i, t in enumerate(toks):
+            if t == "bench.py" and i > 0 and toks[i - 1] == "python":
+                n_bench += 1
+                old = sys.argv
+                try:
+                    sys.argv = ["bench.py"] + toks[i + 1:]
+                    bench.parse()
+                except SystemExit as e:
+                    raise AssertionError(f"{name}: bench.py rejects {cmd!r}") from e
+                finally:
+                    sys.argv = old
+    assert n_bench >= 8 and n_ncu >= 4, (n_bench, n_ncu)
